@@ -1,0 +1,187 @@
+/*
+ * a3fr.h -- C ABI of libA3FR.so, the GB300 (sm_103a) foveated 3D Gaussian Splatting
+ * forward rasterizer of A3FR (arXiv 2507.04147).
+ *
+ * What one render computes (per eye), in the paper's order:
+ *   projection of every Gaussian to a 2-D ellipse and its tile overlap (Sec. 2.3,
+ *   "Projection"), a per-tile depth sort (Sec. 2.3, "Sorting"), front-to-back
+ *   volume rendering of each pixel (Sec. 2.3, "Rasterization"), with the tiles
+ *   labelled by eccentricity from the gaze (Eq. 1, Sec. 3.4) so that a level-k tile
+ *   renders k of the 4 pixels of every 2x2 block and the other pixels inherit the
+ *   block's top-left pixel (Sec. 3.4, Sec. 3.5).  All foveation layers of all eyes
+ *   form one canvas, written in one pass.
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns A3FR_OK (0) or a negative A3FR_ERR_* code; nothing is thrown
+ *     across the ABI and the library never exits the process.
+ *   - Pointers documented as DEVICE point to global memory of the current CUDA
+ *     device; pointers documented as HOST are ordinary host memory.
+ *   - `stream` arguments are cudaStream_t handles passed as void* (NULL = the legacy
+ *     default stream).  Rendering is asynchronous on that stream; the caller keeps
+ *     inputs alive and outputs untouched until the stream reaches the render.
+ *   - Device-side failures (instance-capacity overflow, a bounded wait that gave up)
+ *     set bits of a per-scene status word; a3fr_get_stats reads it.
+ *   - One scene is used by one host thread at a time.
+ */
+#ifndef A3FR_H
+#define A3FR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define A3FR_OK 0
+#define A3FR_ERR_INVALID_ARG (-1) /* a null pointer, a size out of range, an unset camera */
+#define A3FR_ERR_CUDA (-2)        /* a CUDA runtime call failed; see a3fr_last_error_detail */
+#define A3FR_ERR_OOM (-3)         /* device or pinned-host allocation failed */
+#define A3FR_ERR_CAPACITY (-4)    /* more tile-Gaussian instances than the scene's capacity */
+#define A3FR_ERR_TIMEOUT (-5)     /* a bounded device-side wait gave up */
+#define A3FR_ERR_NOT_READY (-6)   /* render_foveated before any set_gaze */
+
+/* bits of a3fr_stats.status */
+#define A3FR_STATUS_CAPACITY 1u   /* some instances were dropped: the image is incomplete */
+#define A3FR_STATUS_TIMEOUT 2u    /* a look-back wait of the radix sort gave up */
+
+typedef struct a3fr_scene a3fr_scene; /* opaque, library-owned */
+
+/* The Gaussians of a scene (Sec. 2.3: position, scales, rotation, opacity, SH colour).
+ * All arrays are DEVICE fp32, caller-owned and borrowed: they must stay allocated and
+ * unchanged while the scene renders.  Arrays must be 16-byte aligned. */
+typedef struct {
+  int32_t n;                    /* number of Gaussians, 0 <= n < 2^30 */
+  int32_t sh_degree;            /* 0..3 */
+  int32_t tile;                 /* tile edge in pixels: 16 (0 selects 16) */
+  int32_t reserved;             /* must be 0 */
+  const float *means;           /* [n][3] world position */
+  const float *log_scales;      /* [n][3] log standard deviation per axis */
+  const float *quats;           /* [n][4] rotation (w, x, y, z); normalised by the library */
+  const float *opacity_logits;  /* [n] opacity = sigmoid(logit) */
+  const float *sh;              /* [n][(sh_degree+1)^2][3] SH coefficients, channel fastest */
+} a3fr_scene_desc;
+
+/* Pinhole camera: x_cam = R x_world + t with world_to_cam = [R | t] row-major 3x4;
+ * pixel (i, j) samples the image plane at (i, j); +z forward, +y down. */
+typedef struct {
+  int32_t width, height;        /* pixels, 1..16384 */
+  float fx, fy, cx, cy;         /* focal lengths and principal point, pixels */
+  float znear;                  /* Gaussians with camera depth <= znear are culled */
+  float world_to_cam[12];
+} a3fr_camera;
+
+/* Foveation layers (Eq. 1, Sec. 3.4).  Layer k < n_layers-1 covers the tiles whose
+ * nearest pixel centre lies within r_k = fx * tan(theta_deg[k] + dtheta_deg) pixels
+ * of the gaze (and not within an inner layer); the last layer covers the rest.
+ * Layer k renders its tiles at pixel-density level level[k] in 1..4. */
+typedef struct {
+  int32_t n_layers;             /* 1..4 */
+  float theta_deg[3];           /* increasing eccentricity boundaries, degrees */
+  float dtheta_deg;             /* gaze-tracking error margin of Eq. 1, degrees */
+  int32_t level[4];             /* e.g. {4, 2, 1} for three layers */
+} a3fr_fovea;
+
+typedef struct {
+  uint32_t status;              /* A3FR_STATUS_* bits accumulated since the last reset */
+  int32_t n_eyes;               /* eyes rendered by the last render */
+  int64_t instances;            /* tile-Gaussian pairs of the last render (all eyes) */
+  int64_t instances_eye[2];     /* the same per eye */
+  int64_t capacity;             /* instance capacity of the scene */
+  uint64_t evaluations;         /* (pixel, Gaussian) evaluations since the last reset */
+  uint64_t records_staged;      /* Gaussian records staged by tile blocks since the reset */
+  uint64_t renders;             /* renders since the last reset */
+  uint64_t kernel_launches;     /* kernels this library launched since the last reset */
+} a3fr_stats;
+
+/* Create a scene over caller-owned Gaussians.  instance_capacity bounds the number of
+ * tile-Gaussian pairs per render over all eyes; 0 sizes it at the first render from the
+ * measured count (that render synchronises once).  *out receives the scene. */
+int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3fr_scene **out);
+
+/* Free the scene and its library-owned device workspace (synchronises the device). */
+int a3fr_destroy_scene(a3fr_scene *scene);
+
+/* Set the camera of eye 0 or 1 (copied; HOST struct).  The eyes rendered are 0..k where
+ * k is the highest eye with a camera; all eyes must have the same width and height. */
+int a3fr_set_camera(a3fr_scene *scene, int eye, const a3fr_camera *camera);
+
+/* Post the gaze of every eye, HOST float[n_eyes][2] in pixels, into the scene's device
+ * mailbox: an asynchronous host-to-device copy on side_stream followed by an event.  A
+ * later render_foveated waits for that event before its first gaze-dependent step
+ * (Sec. 3.3.3: the latest gaze prediction is stored in GPU memory). */
+int a3fr_set_gaze(a3fr_scene *scene, const float *gaze_px, void *side_stream);
+
+/* Render every eye foveated into out_rgb, DEVICE fp32 [n_eyes][height][width][3]. */
+int a3fr_render_foveated(a3fr_scene *scene, const a3fr_fovea *fovea, float *out_rgb,
+                         void *stream);
+
+/* Render every eye at full resolution (every tile at level 4, no gaze), same layout. */
+int a3fr_render_full(a3fr_scene *scene, float *out_rgb, void *stream);
+
+/* Synchronise the scene's last stream and report counters; reset != 0 clears them. */
+int a3fr_get_stats(a3fr_scene *scene, a3fr_stats *stats, int reset);
+
+/* Keep per-pixel transmittance and contributor counts of the next renders (aux buffers,
+ * see a3fr_copy_buffer); off by default because they cost 8 bytes per pixel. */
+int a3fr_set_keep_aux(a3fr_scene *scene, int keep);
+
+/* Stages of a render timed by a3fr_set_stage_timing, in launch order. */
+#define A3FR_STAGE_PREPROCESS 0  /* projection, EWA, SH colour, tile rectangles */
+#define A3FR_STAGE_SCAN 1        /* instance offsets */
+#define A3FR_STAGE_EMIT 2        /* (tile << 32 | depth) keys */
+#define A3FR_STAGE_SORT 3        /* onesweep radix sort */
+#define A3FR_STAGE_RANGES 4      /* per-tile ranges */
+#define A3FR_STAGE_COMPOSITE 5   /* level map + front-to-back blending + inheritance */
+#define A3FR_N_STAGES 6
+
+/* Record CUDA events around every stage of the next renders on their stream, keeping the
+ * last `ring` renders (0 turns timing off and frees the events). */
+int a3fr_set_stage_timing(a3fr_scene *scene, int ring);
+
+/* Synchronise and write the stage durations (ms) of the last min(max_renders, available)
+ * timed renders, oldest first, into HOST ms[k][A3FR_N_STAGES]; *n_out (HOST) receives k. */
+int a3fr_get_stage_times(a3fr_scene *scene, int max_renders, float *ms, int *n_out);
+
+/* Internal buffers of the last render that a3fr_copy_buffer can copy out. */
+#define A3FR_BUF_RECORDS 1    /* fp32 [n_eyes][n][12]: u v conic(a b c) opacity r g b depth radius visible */
+#define A3FR_BUF_RECTS 2      /* uint16 [n_eyes][n][4]: tile x0 y0 x1 y1, half-open */
+#define A3FR_BUF_KEYS 3       /* uint64 [instances]: sorted (eye*tiles + tile) << 32 | depth bits */
+#define A3FR_BUF_VALUES 4     /* uint32 [instances]: Gaussian index of each sorted key */
+#define A3FR_BUF_RANGES 5     /* uint32 [n_eyes*tiles][2]: [start, end) of each tile's run */
+#define A3FR_BUF_LEVELS 6     /* uint8 [n_eyes*tiles]: pixel-density level of each tile */
+#define A3FR_BUF_T_FINAL 7    /* fp32 [n_eyes][height][width] (keep_aux only) */
+#define A3FR_BUF_N_CONTRIB 8  /* uint32 [n_eyes][height][width] (keep_aux only) */
+
+/* Copy `bytes` bytes of internal buffer `which` (A3FR_BUF_*) of the last render into the
+ * DEVICE buffer dst, asynchronously on `stream`.  *needed (HOST, may be NULL) receives the
+ * buffer's size; bytes larger than that is an error. */
+int a3fr_copy_buffer(a3fr_scene *scene, int which, void *dst, size_t bytes, size_t *needed,
+                     void *stream);
+
+/* ---- building blocks on caller buffers (also used by the scene path) ---- */
+
+/* Workspace bytes a3fr_sort_pairs needs for n pairs. */
+size_t a3fr_sort_pairs_workspace_bytes(size_t n);
+
+/* Stable least-significant-digit radix sort (8-bit digits, one onesweep pass per digit)
+ * of n (key, value) pairs by the low key_bits bits of the keys (1..64): the 3DGS depth
+ * sort keyed by tile and depth (Sec. 2.3, "Sorting").  keys/vals (DEVICE uint64/uint32
+ * [n]) hold the input and receive the result; keys_alt/vals_alt (DEVICE, [n]) and the
+ * DEVICE workspace of a3fr_sort_pairs_workspace_bytes(n) bytes are scratch.  Bits above
+ * key_bits must be zero. */
+int a3fr_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                    size_t n, int key_bits, void *workspace, size_t workspace_bytes,
+                    void *stream);
+
+/* Human-readable name of an A3FR_* code (static storage). */
+const char *a3fr_error_string(int code);
+
+/* Detail of the last A3FR_ERR_CUDA raised on the calling thread (static storage). */
+const char *a3fr_last_error_detail(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* A3FR_H */

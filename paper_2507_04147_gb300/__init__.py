@@ -1,0 +1,248 @@
+"""A3FR foveated 3D Gaussian Splatting forward rasterizer for GB300 (sm_103a).
+
+Python binding of libA3FR.so.  The functions below carry the names of the C ABI
+(``include/a3fr.h``) and only marshal arguments: PyTorch supplies device memory and
+streams, every step of a render runs in the library's CUDA kernels.
+
+    scene = Scene(means, log_scales, quats, opacity_logits, sh)   # CUDA fp32 tensors
+    scene.set_camera(0, cam_left); scene.set_camera(1, cam_right)
+    scene.set_gaze([[gx0, gy0], [gx1, gy1]], side_stream)
+    img = scene.render_foveated(Fovea())     # [eyes, H, W, 3] on the current stream
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import A3FRError, BUF_KEYS, BUF_LEVELS, BUF_N_CONTRIB, BUF_RANGES, BUF_RECORDS, \
+    BUF_RECTS, BUF_T_FINAL, BUF_VALUES, STATUS_CAPACITY, STATUS_TIMEOUT
+
+__all__ = ["Scene", "Fovea", "A3FRError", "camera_struct", "create_scene", "destroy_scene",
+           "set_camera", "set_gaze", "render_foveated", "render_full", "get_stats",
+           "set_keep_aux", "set_stage_timing", "get_stage_times", "copy_buffer", "sort_pairs", "sort_pairs_workspace_bytes",
+           "error_string"]
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return _torch().cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int:
+    return t.data_ptr()
+
+
+def Fovea(theta_deg=(18.0, 36.0), dtheta_deg: float = 0.0, levels=(4, 2, 1)) -> _lib.Fovea:
+    """Foveation layers (Eq. 1 radii from eccentricity angles; Sec. 3.4 levels)."""
+    f = _lib.Fovea()
+    f.n_layers = len(levels)
+    for k, t in enumerate(theta_deg):
+        f.theta_deg[k] = float(t)
+    f.dtheta_deg = float(dtheta_deg)
+    for k, lv in enumerate(levels):
+        f.level[k] = int(lv)
+    return f
+
+
+def camera_struct(cam) -> _lib.Camera:
+    """Camera (any object with width/height/fx/fy/cx/cy/znear/world_to_cam) -> C struct."""
+    c = _lib.Camera()
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.fx, c.fy, c.cx, c.cy, c.znear = (float(cam.fx), float(cam.fy), float(cam.cx),
+                                       float(cam.cy), float(cam.znear))
+    w = np.ascontiguousarray(cam.world_to_cam, dtype=np.float32).reshape(12)
+    for i in range(12):
+        c.world_to_cam[i] = float(w[i])
+    return c
+
+
+# ------------------------------------------------------------ C-ABI names
+def create_scene(desc: _lib.SceneDesc, instance_capacity: int = 0) -> int:
+    lib = _lib.load()
+    out = ctypes.c_void_p()
+    _lib.check(lib.a3fr_create_scene(ctypes.byref(desc), instance_capacity, ctypes.byref(out)),
+               "a3fr_create_scene")
+    return out.value
+
+
+def destroy_scene(handle: int) -> None:
+    _lib.check(_lib.load().a3fr_destroy_scene(handle), "a3fr_destroy_scene")
+
+
+def set_camera(handle: int, eye: int, cam: _lib.Camera) -> None:
+    _lib.check(_lib.load().a3fr_set_camera(handle, eye, ctypes.byref(cam)), "a3fr_set_camera")
+
+
+def set_gaze(handle: int, gaze_px, side_stream=None) -> None:
+    g = np.ascontiguousarray(np.asarray(gaze_px, dtype=np.float32).reshape(-1))
+    _lib.check(_lib.load().a3fr_set_gaze(handle, g.ctypes.data, _stream_ptr(side_stream)),
+               "a3fr_set_gaze")
+
+
+def render_foveated(handle: int, fovea: _lib.Fovea, out_rgb, stream=None) -> None:
+    _lib.check(_lib.load().a3fr_render_foveated(handle, ctypes.byref(fovea), _ptr(out_rgb),
+                                                _stream_ptr(stream)), "a3fr_render_foveated")
+
+
+def render_full(handle: int, out_rgb, stream=None) -> None:
+    _lib.check(_lib.load().a3fr_render_full(handle, _ptr(out_rgb), _stream_ptr(stream)),
+               "a3fr_render_full")
+
+
+def get_stats(handle: int, reset: bool = False) -> dict:
+    st = _lib.Stats()
+    _lib.check(_lib.load().a3fr_get_stats(handle, ctypes.byref(st), int(reset)), "a3fr_get_stats")
+    return {"status": st.status, "n_eyes": st.n_eyes, "instances": st.instances,
+            "instances_eye": [st.instances_eye[0], st.instances_eye[1]],
+            "capacity": st.capacity, "evaluations": st.evaluations,
+            "records_staged": st.records_staged, "renders": st.renders,
+            "kernel_launches": st.kernel_launches}
+
+
+def set_stage_timing(handle: int, ring: int) -> None:
+    _lib.check(_lib.load().a3fr_set_stage_timing(handle, ring), "a3fr_set_stage_timing")
+
+
+def get_stage_times(handle: int, max_renders: int) -> np.ndarray:
+    """Stage durations (ms) of the last timed renders, [k, 6] oldest first."""
+    ms = np.zeros((max_renders, len(_lib.STAGES)), dtype=np.float32)
+    k = ctypes.c_int(0)
+    _lib.check(_lib.load().a3fr_get_stage_times(handle, max_renders, ms.ctypes.data,
+                                                ctypes.byref(k)), "a3fr_get_stage_times")
+    return ms[:k.value]
+
+
+def set_keep_aux(handle: int, keep: bool) -> None:
+    _lib.check(_lib.load().a3fr_set_keep_aux(handle, int(keep)), "a3fr_set_keep_aux")
+
+
+def copy_buffer(handle: int, which: int, dst=None, stream=None) -> int:
+    """Copy an internal buffer into the CUDA tensor dst; returns the buffer size in bytes."""
+    lib = _lib.load()
+    needed = ctypes.c_size_t(0)
+    if dst is None:
+        _lib.check(lib.a3fr_copy_buffer(handle, which, None, 0, ctypes.byref(needed), None),
+                   "a3fr_copy_buffer")
+        return needed.value
+    nbytes = dst.numel() * dst.element_size()
+    _lib.check(lib.a3fr_copy_buffer(handle, which, _ptr(dst), nbytes, ctypes.byref(needed),
+                                    _stream_ptr(stream)), "a3fr_copy_buffer")
+    return needed.value
+
+
+def sort_pairs_workspace_bytes(n: int) -> int:
+    return int(_lib.load().a3fr_sort_pairs_workspace_bytes(n))
+
+
+def sort_pairs(keys, vals, keys_alt, vals_alt, key_bits: int, workspace, stream=None) -> None:
+    """Stable radix sort of (uint64 key, uint32 value) CUDA tensors by the low key_bits bits."""
+    n = keys.numel()
+    _lib.check(_lib.load().a3fr_sort_pairs(_ptr(keys), _ptr(vals), _ptr(keys_alt), _ptr(vals_alt),
+                                           n, key_bits, _ptr(workspace), workspace.numel(),
+                                           _stream_ptr(stream)), "a3fr_sort_pairs")
+
+
+def error_string(code: int) -> str:
+    return _lib.load().a3fr_error_string(code).decode()
+
+
+# ------------------------------------------------------------ convenience object
+class Scene:
+    """Owns a library scene over CUDA fp32 tensors (kept alive by this object)."""
+
+    def __init__(self, means, log_scales, quats, opacity_logits, sh, sh_degree: int | None = None,
+                 instance_capacity: int = 0, tile: int = 16):
+        torch = _torch()
+        ts = [means, log_scales, quats, opacity_logits, sh]
+        for t in ts:
+            if not (t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()):
+                raise ValueError("scene tensors must be contiguous CUDA float32")
+        self._tensors = ts
+        n = means.shape[0]
+        if sh_degree is None:
+            sh_degree = int(round((sh.shape[1]) ** 0.5)) - 1
+        self.n, self.sh_degree = n, sh_degree
+        d = _lib.SceneDesc()
+        d.n, d.sh_degree, d.tile, d.reserved = n, sh_degree, tile, 0
+        d.means, d.log_scales, d.quats = _ptr(means), _ptr(log_scales), _ptr(quats)
+        d.opacity_logits, d.sh = _ptr(opacity_logits), _ptr(sh)
+        self.handle = create_scene(d, instance_capacity)
+        self.cams = {}
+
+    @classmethod
+    def from_numpy(cls, scene, device="cuda", **kw) -> "Scene":
+        torch = _torch()
+        f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(device)
+        return cls(f(scene.means), f(scene.log_scales), f(scene.quats), f(scene.opacity_logits),
+                   f(scene.sh), scene.sh_degree, **kw)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            destroy_scene(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def n_eyes(self) -> int:
+        return 2 if 1 in self.cams else 1
+
+    def set_camera(self, eye: int, cam):
+        self.cams[eye] = cam
+        set_camera(self.handle, eye, camera_struct(cam))
+
+    def set_gaze(self, gaze_px, side_stream=None):
+        set_gaze(self.handle, gaze_px, side_stream)
+
+    def _out(self, out):
+        if out is not None:
+            return out
+        c = self.cams[0]
+        return _torch().empty((self.n_eyes, c.height, c.width, 3), device="cuda",
+                              dtype=_torch().float32)
+
+    def render_foveated(self, fovea=None, out=None, stream=None):
+        out = self._out(out)
+        render_foveated(self.handle, fovea if fovea is not None else Fovea(), out, stream)
+        return out
+
+    def render_full(self, out=None, stream=None):
+        out = self._out(out)
+        render_full(self.handle, out, stream)
+        return out
+
+    def stats(self, reset: bool = False) -> dict:
+        return get_stats(self.handle, reset)
+
+    def stage_timing(self, ring: int):
+        set_stage_timing(self.handle, ring)
+
+    def stage_times(self, max_renders: int) -> np.ndarray:
+        return get_stage_times(self.handle, max_renders)
+
+    def keep_aux(self, keep: bool = True):
+        set_keep_aux(self.handle, keep)
+
+    def buffer(self, which: int, dtype, shape=None, stream=None):
+        """Copy of an internal buffer of the last render as a CUDA tensor."""
+        torch = _torch()
+        nbytes = copy_buffer(self.handle, which)
+        itemsize = torch.empty((), dtype=dtype).element_size()
+        t = torch.empty(nbytes // itemsize, dtype=dtype, device="cuda")
+        if nbytes:
+            copy_buffer(self.handle, which, t, stream)
+        return t.reshape(shape) if shape is not None else t

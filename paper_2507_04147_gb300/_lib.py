@@ -1,0 +1,107 @@
+"""ctypes binding of libA3FR.so: the C structs of include/a3fr.h and the raw entry points.
+
+Argument marshalling only.  Every step of a render runs in the CUDA library; if the
+library is missing or fails to load this module raises -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libA3FR.so")
+
+A3FR_OK = 0
+ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "CAPACITY", -5: "TIMEOUT", -6: "NOT_READY"}
+STATUS_CAPACITY = 1
+STATUS_TIMEOUT = 2
+
+STAGES = ("preprocess", "scan", "emit", "sort", "ranges", "composite")
+
+BUF_RECORDS, BUF_RECTS, BUF_KEYS, BUF_VALUES, BUF_RANGES, BUF_LEVELS, BUF_T_FINAL, BUF_N_CONTRIB = range(1, 9)
+
+
+class SceneDesc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("sh_degree", ctypes.c_int32), ("tile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("means", ctypes.c_void_p),
+                ("log_scales", ctypes.c_void_p), ("quats", ctypes.c_void_p),
+                ("opacity_logits", ctypes.c_void_p), ("sh", ctypes.c_void_p)]
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("fx", ctypes.c_float),
+                ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("znear", ctypes.c_float), ("world_to_cam", ctypes.c_float * 12)]
+
+
+class Fovea(ctypes.Structure):
+    _fields_ = [("n_layers", ctypes.c_int32), ("theta_deg", ctypes.c_float * 3),
+                ("dtheta_deg", ctypes.c_float), ("level", ctypes.c_int32 * 4)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_uint32), ("n_eyes", ctypes.c_int32),
+                ("instances", ctypes.c_int64), ("instances_eye", ctypes.c_int64 * 2),
+                ("capacity", ctypes.c_int64), ("evaluations", ctypes.c_uint64),
+                ("records_staged", ctypes.c_uint64), ("renders", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64)]
+
+
+class A3FRError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = f"{where} failed: A3FR_ERR_{ERRORS.get(code, code)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+_lib = None
+
+# name -> (argtypes, restype)
+_SIGS = {
+    "a3fr_create_scene": ([ctypes.POINTER(SceneDesc), ctypes.c_size_t, ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "a3fr_destroy_scene": ([ctypes.c_void_p], ctypes.c_int),
+    "a3fr_set_camera": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(Camera)], ctypes.c_int),
+    "a3fr_set_gaze": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "a3fr_render_foveated": ([ctypes.c_void_p, ctypes.POINTER(Fovea), ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "a3fr_render_full": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "a3fr_get_stats": ([ctypes.c_void_p, ctypes.POINTER(Stats), ctypes.c_int], ctypes.c_int),
+    "a3fr_set_keep_aux": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "a3fr_copy_buffer": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                          ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p], ctypes.c_int),
+    "a3fr_sort_pairs_workspace_bytes": ([ctypes.c_size_t], ctypes.c_size_t),
+    "a3fr_sort_pairs": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+                         ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
+                         ctypes.c_void_p], ctypes.c_int),
+    "a3fr_set_stage_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "a3fr_get_stage_times": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                              ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    "a3fr_error_string": ([ctypes.c_int], ctypes.c_char_p),
+    "a3fr_last_error_detail": ([], ctypes.c_char_p),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load libA3FR.so (built by ``paper_2507_04147_gb300.build``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libA3FR.so is not built ({path}); run __graft_entry__.build() "
+                           "or python -m paper_2507_04147_gb300.build -- there is no CPU fallback")
+    lib = ctypes.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def check(code: int, where: str):
+    if code != A3FR_OK:
+        detail = ""
+        if code == -2 and _lib is not None:
+            detail = (_lib.a3fr_last_error_detail() or b"").decode()
+        raise A3FRError(code, where, detail)

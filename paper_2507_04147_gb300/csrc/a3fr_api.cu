@@ -1,0 +1,625 @@
+// a3fr_api.cu -- the C ABI of libA3FR.so (declared in include/a3fr.h): scene objects,
+// library-owned device workspace, the gaze mailbox, and the orchestration of one render:
+//
+//   preprocess -> scan_blocks -> emit_keys -> onesweep sort -> tile_ranges
+//        -> [wait for the gaze event] -> composite (level map + blend + inherit)
+//
+// all enqueued on the caller's stream without a host synchronisation (except the very
+// first render of a scene created with automatic capacity, which measures the instance
+// count once).  Only the composite depends on the gaze, so projection, binning and the
+// sort overlap whatever produces the gaze (Sec. 3.3.3, Sec. 4.3: the preprocessing can
+// start before gaze tracking finishes).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "../../include/a3fr.h"
+#include "common.cuh"
+
+using namespace a3fr;
+
+namespace {
+
+constexpr int kSlots = 8;  // gaze mailbox ring depth
+thread_local std::string g_detail;
+
+int cuda_fail(cudaError_t e, const char *what) {
+  g_detail = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return e == cudaErrorMemoryAllocation ? A3FR_ERR_OOM : A3FR_ERR_CUDA;
+}
+
+#define A3FR_CHECK(call)                          \
+  do {                                            \
+    cudaError_t e_ = (call);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <typename T>
+void dfree(T *&p) {
+  if (p) cudaFree((void *)p);
+  p = nullptr;
+}
+
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+}  // namespace
+
+struct a3fr_scene {
+  a3fr_scene_desc desc{};
+  a3fr_camera cams[kMaxEyes]{};
+  bool cam_set[kMaxEyes]{false, false};
+
+  // per-Gaussian and per-tile workspace, sized for (n_eyes, W, H)
+  int alloc_eyes = 0, W = 0, H = 0, TX = 0, TY = 0, n_tiles = 0, n_blocks = 0;
+  float *rec = nullptr;
+  ushort4 *rect = nullptr;
+  uint32_t *touched = nullptr;
+  uint32_t *block_sums = nullptr;
+  unsigned long long *block_offsets = nullptr;
+  uint2 *ranges = nullptr;
+  uint8_t *levels = nullptr;
+  float *t_final = nullptr;
+  uint32_t *n_contrib = nullptr;
+  // instance workspace
+  size_t capacity = 0;
+  bool auto_capacity = false;
+  uint64_t *keys[2] = {nullptr, nullptr};
+  uint32_t *vals[2] = {nullptr, nullptr};
+  void *sort_ws = nullptr;
+  size_t sort_ws_bytes = 0;
+  bool sorted_in_alt = false;
+  // small device state: counts[4] | status | pad | counters[2]
+  uint32_t *counts = nullptr;
+  uint32_t *status = nullptr;
+  unsigned long long *counters = nullptr;
+  void *small = nullptr;
+  // gaze mailbox ring
+  float *gaze_dev = nullptr;
+  float *gaze_pinned = nullptr;
+  cudaEvent_t gaze_written[kSlots]{};
+  cudaEvent_t gaze_consumed[kSlots]{};
+  bool slot_written[kSlots]{};
+  bool slot_consumed[kSlots]{};
+  int gaze_seq = -1;
+
+  cudaStream_t last_stream = nullptr;
+  int last_eyes = 0;
+  bool keep_aux = false;
+  uint64_t renders = 0;
+  uint64_t launches = 0;
+
+  // stage timing ring: events[slot][A3FR_N_STAGES + 1]
+  int timing_ring = 0;
+  cudaEvent_t *timing_events = nullptr;
+  uint64_t timed_renders = 0;
+};
+
+namespace {
+
+int n_eyes_of(const a3fr_scene *s) { return s->cam_set[1] ? 2 : (s->cam_set[0] ? 1 : 0); }
+
+void free_frame_buffers(a3fr_scene *s) {
+  dfree(s->rec);
+  dfree(s->rect);
+  dfree(s->touched);
+  dfree(s->block_sums);
+  dfree(s->block_offsets);
+  dfree(s->ranges);
+  dfree(s->levels);
+  dfree(s->t_final);
+  dfree(s->n_contrib);
+  s->alloc_eyes = 0;
+}
+
+void free_instance_buffers(a3fr_scene *s) {
+  for (int b = 0; b < 2; ++b) {
+    dfree(s->keys[b]);
+    dfree(s->vals[b]);
+  }
+  dfree(s->sort_ws);
+  s->sort_ws_bytes = 0;
+}
+
+int alloc_instances(a3fr_scene *s, size_t capacity) {
+  free_instance_buffers(s);
+  s->capacity = capacity;
+  if (capacity == 0) return A3FR_OK;
+  for (int b = 0; b < 2; ++b) {
+    A3FR_CHECK(cudaMalloc(&s->keys[b], sizeof(uint64_t) * capacity));
+    A3FR_CHECK(cudaMalloc(&s->vals[b], sizeof(uint32_t) * capacity));
+  }
+  s->sort_ws_bytes = sort_workspace_bytes(capacity);
+  A3FR_CHECK(cudaMalloc(&s->sort_ws, s->sort_ws_bytes));
+  return A3FR_OK;
+}
+
+int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
+  if (s->alloc_eyes == eyes && s->W == W && s->H == H) return A3FR_OK;
+  // a size change: wait for any render still using the old buffers
+  if (s->alloc_eyes) A3FR_CHECK(cudaDeviceSynchronize());
+  free_frame_buffers(s);
+  const int n = s->desc.n;
+  const int tile = s->desc.tile;
+  s->W = W;
+  s->H = H;
+  s->TX = (W + tile - 1) / tile;
+  s->TY = (H + tile - 1) / tile;
+  s->n_tiles = s->TX * s->TY;
+  s->n_blocks = (n + kPreThreads - 1) / kPreThreads;
+  const size_t nn = n > 0 ? (size_t)n : 1;
+  A3FR_CHECK(cudaMalloc(&s->rec, sizeof(float) * kRec * nn * eyes));
+  A3FR_CHECK(cudaMalloc(&s->rect, sizeof(ushort4) * nn * eyes));
+  A3FR_CHECK(cudaMalloc(&s->touched, sizeof(uint32_t) * nn));
+  A3FR_CHECK(cudaMalloc(&s->block_sums, sizeof(uint32_t) * 2 * (s->n_blocks + 1)));
+  A3FR_CHECK(cudaMalloc(&s->block_offsets, sizeof(unsigned long long) * (s->n_blocks + 1)));
+  A3FR_CHECK(cudaMalloc(&s->ranges, sizeof(uint2) * (size_t)s->n_tiles * eyes));
+  A3FR_CHECK(cudaMalloc(&s->levels, (size_t)s->n_tiles * eyes));
+  A3FR_CHECK(cudaMalloc(&s->t_final, sizeof(float) * (size_t)W * H * eyes));
+  A3FR_CHECK(cudaMalloc(&s->n_contrib, sizeof(uint32_t) * (size_t)W * H * eyes));
+  A3FR_CHECK(cudaMemset(s->ranges, 0, sizeof(uint2) * (size_t)s->n_tiles * eyes));
+  A3FR_CHECK(cudaMemset(s->levels, 0, (size_t)s->n_tiles * eyes));
+  s->alloc_eyes = eyes;
+  return A3FR_OK;
+}
+
+CamParams cam_params(const a3fr_camera &c) {
+  CamParams p{};
+  const float *w = c.world_to_cam;
+  for (int r = 0; r < 3; ++r) {
+    for (int k = 0; k < 3; ++k) p.R[3 * r + k] = w[4 * r + k];
+    p.t[r] = w[4 * r + 3];
+  }
+  p.fx = c.fx;
+  p.fy = c.fy;
+  p.cx = c.cx;
+  p.cy = c.cy;
+  p.znear = c.znear;
+  // 1.3 tan(fov / 2), rounded step by step in fp32 (this file is built without contraction)
+  const float half_w = 0.5f * (float)c.width, half_h = 0.5f * (float)c.height;
+  const float tx = half_w / c.fx, ty = half_h / c.fy;
+  p.limx = 1.3f * tx;
+  p.limy = 1.3f * ty;
+  p.width = c.width;
+  p.height = c.height;
+  return p;
+}
+
+ShConsts sh_consts() {
+  const double PI = 3.14159265358979323846;
+  ShConsts k;
+  k.c0 = (float)(0.5 * std::sqrt(1.0 / PI));
+  k.c1 = (float)std::sqrt(3.0 / (4.0 * PI));
+  k.c2a = (float)(0.5 * std::sqrt(15.0 / PI));
+  k.c2b = (float)(0.25 * std::sqrt(5.0 / PI));
+  k.c2c = (float)(0.25 * std::sqrt(15.0 / PI));
+  k.c3a = (float)(0.25 * std::sqrt(35.0 / (2.0 * PI)));
+  k.c3b = (float)(0.5 * std::sqrt(105.0 / PI));
+  k.c3c = (float)(0.25 * std::sqrt(21.0 / (2.0 * PI)));
+  k.c3d = (float)(0.25 * std::sqrt(7.0 / PI));
+  k.c3e = (float)(0.25 * std::sqrt(105.0 / PI));
+  return k;
+}
+
+// Squared radius of layer boundary k (Eq. 1 with rho d = fx): f tan(theta_k + dtheta).
+float layer_radius2(float fx, float theta_deg, float dtheta_deg) {
+  const double PI = 3.14159265358979323846;
+  const float r = (float)((double)fx * std::tan(((double)theta_deg + (double)dtheta_deg) * PI / 180.0));
+  return r * r;
+}
+
+int key_bits_for(int n_ranges) {
+  int bits = 1;
+  while ((1ll << bits) < (long long)n_ranges) ++bits;
+  return 32 + bits;
+}
+
+void free_timing(a3fr_scene *s) {
+  if (s->timing_events) {
+    for (int i = 0; i < s->timing_ring * (A3FR_N_STAGES + 1); ++i)
+      if (s->timing_events[i]) cudaEventDestroy(s->timing_events[i]);
+    delete[] s->timing_events;
+  }
+  s->timing_events = nullptr;
+  s->timing_ring = 0;
+  s->timed_renders = 0;
+}
+
+// Records the boundary event k (0..A3FR_N_STAGES) of the current timed render.
+cudaError_t mark(a3fr_scene *s, int k, cudaStream_t stream) {
+  if (!s->timing_ring) return cudaSuccess;
+  const int slot = (int)(s->timed_renders % (uint64_t)s->timing_ring);
+  return cudaEventRecord(s->timing_events[slot * (A3FR_N_STAGES + 1) + k], stream);
+}
+
+int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream) {
+  const int eyes = n_eyes_of(s);
+  if (eyes == 0 || out == nullptr) return A3FR_ERR_INVALID_ARG;
+  const a3fr_camera &c0 = s->cams[0];
+  if (eyes == 2 && (s->cams[1].width != c0.width || s->cams[1].height != c0.height))
+    return A3FR_ERR_INVALID_ARG;
+  if (fv) {
+    if (fv->n_layers < 1 || fv->n_layers > 4) return A3FR_ERR_INVALID_ARG;
+    for (int k = 0; k < fv->n_layers; ++k)
+      if (fv->level[k] < 1 || fv->level[k] > 4) return A3FR_ERR_INVALID_ARG;
+    if (s->gaze_seq < 0) return A3FR_ERR_NOT_READY;
+  }
+  int rc = ensure_frame_buffers(s, eyes, c0.width, c0.height);
+  if (rc != A3FR_OK) return rc;
+  const int n = s->desc.n;
+
+  PreParams pp{};
+  for (int e = 0; e < eyes; ++e) pp.cam[e] = cam_params(s->cams[e]);
+  pp.shc = sh_consts();
+  pp.n_eyes = eyes;
+  pp.tile = s->desc.tile;
+  pp.tiles_x = s->TX;
+  pp.tiles_y = s->TY;
+
+  uint64_t launches = 0;
+  A3FR_CHECK(mark(s, A3FR_STAGE_PREPROCESS, stream));
+  if (n > 0) {
+    A3FR_CHECK(launch_preprocess(pp, n, s->desc.sh_degree, s->desc.means, s->desc.log_scales,
+                                 s->desc.quats, s->desc.opacity_logits, s->desc.sh, s->rec,
+                                 s->rect, s->touched, s->block_sums, stream));
+    ++launches;
+  }
+  if (s->auto_capacity && s->capacity == 0 && n > 0) {
+    // first render: measure the instance count once
+    A3FR_CHECK(launch_scan_blocks(s->block_sums, s->n_blocks, s->block_offsets, s->counts, 0u,
+                                  s->status, stream));
+    ++launches;
+    uint32_t cnt[4];
+    A3FR_CHECK(cudaMemcpyAsync(cnt, s->counts, sizeof cnt, cudaMemcpyDeviceToHost, stream));
+    A3FR_CHECK(cudaStreamSynchronize(stream));
+    A3FR_CHECK(cudaMemsetAsync(s->status, 0, sizeof(uint32_t), stream));
+    size_t want = 2 * (size_t)cnt[3] + (1u << 16);
+    if (want >= (1u << 30)) want = (1u << 30) - 1;
+    rc = alloc_instances(s, want);
+    if (rc != A3FR_OK) return rc;
+  }
+  A3FR_CHECK(mark(s, A3FR_STAGE_SCAN, stream));
+  if (n > 0) {
+    A3FR_CHECK(launch_scan_blocks(s->block_sums, s->n_blocks, s->block_offsets, s->counts,
+                                  (uint32_t)s->capacity, s->status, stream));
+    ++launches;
+  } else {
+    A3FR_CHECK(cudaMemsetAsync(s->counts, 0, 4 * sizeof(uint32_t), stream));
+  }
+  const int n_ranges = eyes * s->n_tiles;
+  A3FR_CHECK(mark(s, A3FR_STAGE_EMIT, stream));
+  if (n > 0 && s->capacity > 0) {
+    A3FR_CHECK(launch_emit_keys(n, eyes, s->TX, s->n_tiles, s->rec, s->rect, s->touched,
+                                s->block_offsets, (uint32_t)s->capacity, s->keys[0], s->vals[0],
+                                stream));
+    ++launches;
+    A3FR_CHECK(mark(s, A3FR_STAGE_SORT, stream));
+    bool in_alt = false;
+    const int bits = key_bits_for(n_ranges);
+    A3FR_CHECK(launch_sort(s->keys[0], s->vals[0], s->keys[1], s->vals[1], s->counts,
+                           s->capacity, bits, s->sort_ws, s->status, &in_alt, stream));
+    launches += 1 + (bits + 7) / 8;
+    s->sorted_in_alt = in_alt;
+  } else {
+    A3FR_CHECK(mark(s, A3FR_STAGE_SORT, stream));
+    s->sorted_in_alt = false;
+  }
+  const int b = s->sorted_in_alt ? 1 : 0;
+  A3FR_CHECK(mark(s, A3FR_STAGE_RANGES, stream));
+  A3FR_CHECK(launch_tile_ranges(s->keys[b], s->counts, n > 0 ? s->capacity : 0, s->ranges,
+                                n_ranges, stream));
+  if (n > 0 && s->capacity > 0) ++launches;
+
+  CompositeParams cp{};
+  cp.n_eyes = eyes;
+  cp.width = s->W;
+  cp.height = s->H;
+  cp.tile = s->desc.tile;
+  cp.tiles_x = s->TX;
+  cp.tiles_y = s->TY;
+  cp.n_tiles = s->n_tiles;
+  cp.full = fv ? 0 : 1;
+  const float *gaze = nullptr;
+  int slot = -1;
+  if (fv) {
+    cp.n_layers = fv->n_layers;
+    for (int k = 0; k < 4; ++k) cp.level[k] = fv->level[k];
+    for (int e = 0; e < eyes; ++e)
+      for (int k = 0; k < 3; ++k)
+        cp.r2[e][k] = layer_radius2(s->cams[e].fx, fv->theta_deg[k], fv->dtheta_deg);
+    slot = s->gaze_seq % kSlots;
+    A3FR_CHECK(cudaStreamWaitEvent(stream, s->gaze_written[slot], 0));
+    gaze = s->gaze_dev + 4 * slot;
+  } else {
+    cp.n_layers = 1;
+    cp.level[0] = 4;
+    gaze = s->gaze_dev;   // not read when full
+  }
+  A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
+  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, s->vals[b], gaze, out, s->levels,
+                              s->keep_aux ? s->t_final : nullptr,
+                              s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
+  ++launches;
+  A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));
+  if (fv) {
+    A3FR_CHECK(cudaEventRecord(s->gaze_consumed[slot], stream));
+    s->slot_consumed[slot] = true;
+  }
+  s->last_stream = stream;
+  s->last_eyes = eyes;
+  s->renders++;
+  s->launches += launches;
+  if (s->timing_ring) s->timed_renders++;
+  return A3FR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3fr_scene **out) {
+  if (!desc || !out) return A3FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (desc->n < 0 || desc->n >= (1 << 30) || desc->sh_degree < 0 || desc->sh_degree > 3 ||
+      desc->reserved != 0)
+    return A3FR_ERR_INVALID_ARG;
+  const int tile = desc->tile == 0 ? 16 : desc->tile;
+  if (tile != 16) return A3FR_ERR_INVALID_ARG;
+  if (instance_capacity >= (1u << 30)) return A3FR_ERR_INVALID_ARG;
+  if (desc->n > 0) {
+    const void *ptrs[5] = {desc->means, desc->log_scales, desc->quats, desc->opacity_logits,
+                           desc->sh};
+    for (const void *p : ptrs)
+      if (p == nullptr || !aligned16(p)) return A3FR_ERR_INVALID_ARG;
+  }
+  a3fr_scene *s = new (std::nothrow) a3fr_scene();
+  if (!s) return A3FR_ERR_OOM;
+  s->desc = *desc;
+  s->desc.tile = tile;
+  s->auto_capacity = instance_capacity == 0;
+  int rc = A3FR_OK;
+  auto fail = [&](int code) {
+    a3fr_destroy_scene(s);
+    return code;
+  };
+  cudaError_t e = cudaMalloc(&s->small, 256);
+  if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(state)"));
+  unsigned char *sm = static_cast<unsigned char *>(s->small);
+  s->counts = reinterpret_cast<uint32_t *>(sm);
+  s->status = reinterpret_cast<uint32_t *>(sm + 16);
+  s->counters = reinterpret_cast<unsigned long long *>(sm + 32);
+  if ((e = cudaMemset(s->small, 0, 256)) != cudaSuccess) return fail(cuda_fail(e, "cudaMemset"));
+  if ((e = cudaMalloc(&s->gaze_dev, sizeof(float) * 4 * kSlots)) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaMalloc(gaze)"));
+  if ((e = cudaMemset(s->gaze_dev, 0, sizeof(float) * 4 * kSlots)) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaMemset(gaze)"));
+  if ((e = cudaMallocHost(&s->gaze_pinned, sizeof(float) * 4 * kSlots)) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaMallocHost(gaze)"));
+  for (int k = 0; k < kSlots; ++k) {
+    if ((e = cudaEventCreateWithFlags(&s->gaze_written[k], cudaEventDisableTiming)) != cudaSuccess)
+      return fail(cuda_fail(e, "cudaEventCreate"));
+    if ((e = cudaEventCreateWithFlags(&s->gaze_consumed[k], cudaEventDisableTiming)) != cudaSuccess)
+      return fail(cuda_fail(e, "cudaEventCreate"));
+  }
+  if (!s->auto_capacity) {
+    rc = alloc_instances(s, instance_capacity);
+    if (rc != A3FR_OK) return fail(rc);
+  }
+  *out = s;
+  return A3FR_OK;
+}
+
+int a3fr_destroy_scene(a3fr_scene *s) {
+  if (!s) return A3FR_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  free_timing(s);
+  free_frame_buffers(s);
+  free_instance_buffers(s);
+  dfree(s->gaze_dev);
+  if (s->small) cudaFree(s->small);
+  if (s->gaze_pinned) cudaFreeHost(s->gaze_pinned);
+  for (int k = 0; k < kSlots; ++k) {
+    if (s->gaze_written[k]) cudaEventDestroy(s->gaze_written[k]);
+    if (s->gaze_consumed[k]) cudaEventDestroy(s->gaze_consumed[k]);
+  }
+  delete s;
+  return A3FR_OK;
+}
+
+int a3fr_set_camera(a3fr_scene *s, int eye, const a3fr_camera *cam) {
+  if (!s || !cam || eye < 0 || eye >= kMaxEyes) return A3FR_ERR_INVALID_ARG;
+  if (cam->width < 1 || cam->height < 1 || cam->width > 16384 || cam->height > 16384)
+    return A3FR_ERR_INVALID_ARG;
+  if (!(cam->fx > 0.0f) || !(cam->fy > 0.0f) || !(cam->znear > 0.0f)) return A3FR_ERR_INVALID_ARG;
+  s->cams[eye] = *cam;
+  s->cam_set[eye] = true;
+  return A3FR_OK;
+}
+
+int a3fr_set_gaze(a3fr_scene *s, const float *gaze_px, void *side_stream) {
+  if (!s || !gaze_px) return A3FR_ERR_INVALID_ARG;
+  const int eyes = n_eyes_of(s);
+  if (eyes == 0) return A3FR_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(side_stream);
+  const int slot = (s->gaze_seq + 1) % kSlots;
+  // the pinned staging slot is reused only after its previous copy finished
+  if (s->slot_written[slot]) A3FR_CHECK(cudaEventSynchronize(s->gaze_written[slot]));
+  // the device slot is overwritten only after the render that read it
+  if (s->slot_consumed[slot]) A3FR_CHECK(cudaStreamWaitEvent(st, s->gaze_consumed[slot], 0));
+  float *h = s->gaze_pinned + 4 * slot;
+  for (int k = 0; k < 4; ++k) h[k] = k < 2 * eyes ? gaze_px[k] : 0.0f;
+  A3FR_CHECK(cudaMemcpyAsync(s->gaze_dev + 4 * slot, h, sizeof(float) * 4,
+                             cudaMemcpyHostToDevice, st));
+  A3FR_CHECK(cudaEventRecord(s->gaze_written[slot], st));
+  s->slot_written[slot] = true;
+  s->gaze_seq++;
+  return A3FR_OK;
+}
+
+int a3fr_render_foveated(a3fr_scene *s, const a3fr_fovea *fovea, float *out_rgb, void *stream) {
+  if (!s || !fovea) return A3FR_ERR_INVALID_ARG;
+  return render(s, fovea, out_rgb, static_cast<cudaStream_t>(stream));
+}
+
+int a3fr_render_full(a3fr_scene *s, float *out_rgb, void *stream) {
+  if (!s) return A3FR_ERR_INVALID_ARG;
+  return render(s, nullptr, out_rgb, static_cast<cudaStream_t>(stream));
+}
+
+int a3fr_set_keep_aux(a3fr_scene *s, int keep) {
+  if (!s) return A3FR_ERR_INVALID_ARG;
+  s->keep_aux = keep != 0;
+  return A3FR_OK;
+}
+
+int a3fr_get_stats(a3fr_scene *s, a3fr_stats *st, int reset) {
+  if (!s || !st) return A3FR_ERR_INVALID_ARG;
+  A3FR_CHECK(cudaStreamSynchronize(s->last_stream));
+  unsigned char buf[256];
+  A3FR_CHECK(cudaMemcpy(buf, s->small, sizeof buf, cudaMemcpyDeviceToHost));
+  uint32_t counts[4];
+  uint32_t status;
+  unsigned long long ctr[2];
+  std::memcpy(counts, buf, sizeof counts);
+  std::memcpy(&status, buf + 16, sizeof status);
+  std::memcpy(ctr, buf + 32, sizeof ctr);
+  std::memset(st, 0, sizeof *st);
+  st->status = status;
+  st->n_eyes = s->last_eyes;
+  st->instances = counts[0];
+  st->instances_eye[0] = counts[1];
+  st->instances_eye[1] = counts[2];
+  st->capacity = (int64_t)s->capacity;
+  st->evaluations = ctr[0];
+  st->records_staged = ctr[1];
+  st->renders = s->renders;
+  st->kernel_launches = s->launches;
+  if (reset) {
+    A3FR_CHECK(cudaMemset(s->status, 0, sizeof(uint32_t)));
+    A3FR_CHECK(cudaMemset(s->counters, 0, 2 * sizeof(unsigned long long)));
+    s->renders = 0;
+    s->launches = 0;
+  }
+  return A3FR_OK;
+}
+
+int a3fr_set_stage_timing(a3fr_scene *s, int ring) {
+  if (!s || ring < 0 || ring > 65536) return A3FR_ERR_INVALID_ARG;
+  if (s->timing_ring) A3FR_CHECK(cudaStreamSynchronize(s->last_stream));
+  free_timing(s);
+  if (ring == 0) return A3FR_OK;
+  const int count = ring * (A3FR_N_STAGES + 1);
+  s->timing_events = new (std::nothrow) cudaEvent_t[count]();
+  if (!s->timing_events) return A3FR_ERR_OOM;
+  s->timing_ring = ring;
+  for (int i = 0; i < count; ++i) {
+    cudaError_t e = cudaEventCreate(&s->timing_events[i]);
+    if (e != cudaSuccess) {
+      free_timing(s);
+      return cuda_fail(e, "cudaEventCreate(timing)");
+    }
+  }
+  return A3FR_OK;
+}
+
+int a3fr_get_stage_times(a3fr_scene *s, int max_renders, float *ms, int *n_out) {
+  if (!s || !ms || !n_out || max_renders < 0) return A3FR_ERR_INVALID_ARG;
+  *n_out = 0;
+  if (!s->timing_ring) return A3FR_OK;
+  A3FR_CHECK(cudaStreamSynchronize(s->last_stream));
+  uint64_t avail = s->timed_renders < (uint64_t)s->timing_ring ? s->timed_renders
+                                                                 : (uint64_t)s->timing_ring;
+  if (avail > (uint64_t)max_renders) avail = (uint64_t)max_renders;
+  for (uint64_t r = 0; r < avail; ++r) {
+    const uint64_t idx = s->timed_renders - avail + r;
+    const int slot = (int)(idx % (uint64_t)s->timing_ring);
+    cudaEvent_t *ev = s->timing_events + slot * (A3FR_N_STAGES + 1);
+    for (int k = 0; k < A3FR_N_STAGES; ++k) {
+      float t = 0.0f;
+      A3FR_CHECK(cudaEventElapsedTime(&t, ev[k], ev[k + 1]));
+      ms[r * A3FR_N_STAGES + k] = t;
+    }
+  }
+  *n_out = (int)avail;
+  return A3FR_OK;
+}
+
+int a3fr_copy_buffer(a3fr_scene *s, int which, void *dst, size_t bytes, size_t *needed,
+                     void *stream) {
+  if (!s) return A3FR_ERR_INVALID_ARG;
+  const int eyes = s->alloc_eyes;
+  const size_t n = (size_t)s->desc.n;
+  const void *src = nullptr;
+  size_t size = 0;
+  switch (which) {
+    case A3FR_BUF_RECORDS: src = s->rec; size = sizeof(float) * kRec * n * eyes; break;
+    case A3FR_BUF_RECTS: src = s->rect; size = sizeof(ushort4) * n * eyes; break;
+    case A3FR_BUF_KEYS:
+    case A3FR_BUF_VALUES: {
+      A3FR_CHECK(cudaStreamSynchronize(s->last_stream));
+      uint32_t cnt = 0;
+      A3FR_CHECK(cudaMemcpy(&cnt, s->counts, sizeof cnt, cudaMemcpyDeviceToHost));
+      const int b = s->sorted_in_alt ? 1 : 0;
+      if (which == A3FR_BUF_KEYS) { src = s->keys[b]; size = sizeof(uint64_t) * cnt; }
+      else { src = s->vals[b]; size = sizeof(uint32_t) * cnt; }
+      break;
+    }
+    case A3FR_BUF_RANGES: src = s->ranges; size = sizeof(uint2) * (size_t)s->n_tiles * eyes; break;
+    case A3FR_BUF_LEVELS: src = s->levels; size = (size_t)s->n_tiles * eyes; break;
+    case A3FR_BUF_T_FINAL: src = s->t_final; size = sizeof(float) * (size_t)s->W * s->H * eyes; break;
+    case A3FR_BUF_N_CONTRIB: src = s->n_contrib; size = sizeof(uint32_t) * (size_t)s->W * s->H * eyes; break;
+    default: return A3FR_ERR_INVALID_ARG;
+  }
+  if (needed) *needed = size;
+  if (dst == nullptr) return bytes == 0 ? A3FR_OK : A3FR_ERR_INVALID_ARG;
+  if (bytes > size) return A3FR_ERR_INVALID_ARG;
+  if (bytes == 0) return A3FR_OK;
+  A3FR_CHECK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice,
+                             static_cast<cudaStream_t>(stream)));
+  return A3FR_OK;
+}
+
+size_t a3fr_sort_pairs_workspace_bytes(size_t n) { return sort_workspace_bytes(n) + 256; }
+
+int a3fr_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
+                    size_t n, int key_bits, void *workspace, size_t workspace_bytes,
+                    void *stream) {
+  if (n == 0) return A3FR_OK;
+  if (!keys || !vals || !keys_alt || !vals_alt || !workspace) return A3FR_ERR_INVALID_ARG;
+  if (key_bits < 1 || key_bits > 64 || n >= (1u << 30)) return A3FR_ERR_INVALID_ARG;
+  if (workspace_bytes < a3fr_sort_pairs_workspace_bytes(n)) return A3FR_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the first 256 bytes hold the device-resident count and the status word
+  unsigned char *ws = static_cast<unsigned char *>(workspace);
+  uint32_t *d_count = reinterpret_cast<uint32_t *>(ws);
+  uint32_t *status = reinterpret_cast<uint32_t *>(ws + 16);
+  const uint32_t n32 = (uint32_t)n;
+  A3FR_CHECK(cudaMemsetAsync(ws, 0, 256, st));
+  A3FR_CHECK(cudaMemcpyAsync(d_count, &n32, sizeof n32, cudaMemcpyHostToDevice, st));
+  bool in_alt = false;
+  A3FR_CHECK(launch_sort(keys, vals, keys_alt, vals_alt, d_count, n, key_bits, ws + 256, status,
+                         &in_alt, st));
+  if (in_alt) {
+    A3FR_CHECK(cudaMemcpyAsync(keys, keys_alt, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
+    A3FR_CHECK(cudaMemcpyAsync(vals, vals_alt, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
+  }
+  return A3FR_OK;
+}
+
+const char *a3fr_error_string(int code) {
+  switch (code) {
+    case A3FR_OK: return "A3FR_OK";
+    case A3FR_ERR_INVALID_ARG: return "A3FR_ERR_INVALID_ARG: invalid argument";
+    case A3FR_ERR_CUDA: return "A3FR_ERR_CUDA: a CUDA runtime call failed";
+    case A3FR_ERR_OOM: return "A3FR_ERR_OOM: out of memory";
+    case A3FR_ERR_CAPACITY: return "A3FR_ERR_CAPACITY: instance capacity exceeded";
+    case A3FR_ERR_TIMEOUT: return "A3FR_ERR_TIMEOUT: a bounded device wait gave up";
+    case A3FR_ERR_NOT_READY: return "A3FR_ERR_NOT_READY: no gaze has been posted";
+    default: return "unknown A3FR error code";
+  }
+}
+
+const char *a3fr_last_error_detail(void) { return g_detail.c_str(); }
+
+}  // extern "C"

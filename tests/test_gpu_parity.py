@@ -1,0 +1,179 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Bar: per-Gaussian records, tile rectangles, sorted keys, values, tile ranges and tile
+levels bit-exact; pixels within 2e-4 absolute per channel except pixels whose oracle
+threshold margin is below 1e-5 (counted, at most 0.2% of pixels); live pixels of the
+foveated render bit-equal to the full render and inherited pixels equal to their block's
+top-left pixel.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2507_04147_gb300 as a3fr
+from paper_2507_04147_gb300 import synth
+import gpu_helpers as gh
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def check_eye(r, e, scene_np, cam, tile=16, gaze=None, fv=None, full=False, pixels=None):
+    n = scene_np.n
+    rec, rect, touched, keys, vals = gh.oracle_eye(scene_np, cam, tile)
+    assert np.array_equal(r["rec"][e].view(np.uint32), rec.view(np.uint32)), "records differ"
+    assert np.array_equal(r["rect"][e].astype(np.int32), rect), "tile rectangles differ"
+    n_tiles = oracle.tiles(cam.width, tile) * oracle.tiles(cam.height, tile)
+    lo = int(sum(r["stats"]["instances_eye"][:e]))
+    hi = lo + int(r["stats"]["instances_eye"][e])
+    assert hi - lo == len(keys)
+    assert np.array_equal(gh.strip_eye(r["keys"][lo:hi], e, n_tiles), keys), "sorted keys differ"
+    assert np.array_equal(r["vals"][lo:hi], vals), "sorted values differ"
+    ranges = oracle.tile_ranges(keys, n_tiles)
+    gr = r["ranges"][e * n_tiles:(e + 1) * n_tiles].astype(np.int64)
+    nonempty = ranges[:, 1] > ranges[:, 0]
+    assert np.array_equal(gr[nonempty] - lo, ranges[nonempty].astype(np.int64)), "tile ranges differ"
+    assert np.all(gr[~nonempty, 0] == gr[~nonempty, 1])
+    if full:
+        level = None
+        assert np.all(r["levels"][e * n_tiles:(e + 1) * n_tiles] == 4)
+    else:
+        level = oracle.level_map(cam, tile, fv, gaze)
+        assert np.array_equal(r["levels"][e * n_tiles:(e + 1) * n_tiles], level), "levels differ"
+    ref = oracle.render(rec, rect, cam, tile, level=level, pixels=pixels)
+    img = r["img"][e]
+    if pixels is None:
+        got = img.reshape(-1, 3)
+        info = gh.compare_pixels(got, ref)
+        if "t_final" in r:
+            ok = ref.margin >= gh.DELTA
+            tf = r["t_final"][e].reshape(-1)
+            assert np.abs(tf - ref.t_final)[ok].max() <= 2e-4
+            nc = r["n_contrib"][e].reshape(-1)
+            assert np.array_equal(nc[ok], ref.n_contrib[ok])
+    else:
+        got = img[pixels[:, 1], pixels[:, 0]]
+        info = gh.compare_pixels(got, ref)
+    return info
+
+
+def fovea_params():
+    return oracle.fovea((18.0, 36.0), 0.0, (4, 2, 1)), a3fr.Fovea((18.0, 36.0), 0.0, (4, 2, 1))
+
+
+def test_small_single_view_foveated_and_full():
+    w = synth.small_single_view()
+    cam = w.cameras(0)[0]
+    ofv, gfv = fovea_params()
+    r = gh.run(w.scene, [cam], gaze=[w.fixed_gaze_px], fovea=gfv)
+    assert r["stats"]["status"] == 0
+    info = check_eye(r, 0, w.scene, cam, gaze=w.fixed_gaze_px, fv=ofv)
+    print("foveated", info)
+    rf = gh.run(w.scene, [cam], full=True)
+    info = check_eye(rf, 0, w.scene, cam, full=True)
+    print("full", info)
+    # foveated live pixels are bit-equal to the full render; the rest copy their top-left
+    lv = oracle.level_map(cam, 16, ofv, w.fixed_gaze_px)
+    ref = oracle.render(*oracle.preprocess(w.scene, cam, 16)[:2], cam, 16, level=lv)
+    live = ref.rendered.reshape(256, 256).astype(bool)
+    fov, full = r["img"][0], rf["img"][0]
+    assert np.array_equal(fov[live], full[live])
+    tl = np.repeat(np.repeat(full[0::2, 0::2], 2, axis=0), 2, axis=1)
+    assert np.array_equal(fov[~live], tl[~live])
+
+
+def test_stereo_sh3_ragged_image():
+    scene = synth.uniform_scene(6000, 3, seed=3)
+    cams = synth.stereo_cameras(200, 136, yaw_deg=3.0)
+    gaze = np.array([[20.0, 120.0], [25.5, 118.25]], np.float32)
+    ofv, gfv = fovea_params()
+    r = gh.run(scene, cams, gaze=gaze, fovea=gfv)
+    assert r["stats"]["status"] == 0 and r["stats"]["n_eyes"] == 2
+    for e in range(2):
+        print(e, check_eye(r, e, scene, cams[e], gaze=gaze[e], fv=ofv))
+
+
+@pytest.mark.parametrize("levels,theta,dtheta", [((4,), (), 0.0), ((4, 1), (18.0,), 2.1),
+                                                 ((4, 3, 2, 1), (10.0, 20.0, 35.0), 0.0)])
+def test_layer_configurations(levels, theta, dtheta):
+    scene = synth.uniform_scene(4000, 1, seed=5)
+    cam = synth.pinhole_camera(160, 144, 90.0, -2.0)
+    gaze = (101.3, 40.7)
+    ofv = oracle.fovea(theta, dtheta, levels)
+    gfv = a3fr.Fovea(theta, dtheta, levels)
+    r = gh.run(scene, [cam], gaze=[gaze], fovea=gfv)
+    print(check_eye(r, 0, scene, cam, gaze=gaze, fv=ofv))
+
+
+def test_degenerate_scenes():
+    cam = synth.pinhole_camera(64, 48)
+    # no Gaussians
+    empty = synth.uniform_scene(0, 0, seed=1)
+    r = gh.run(empty, [cam], full=True)
+    assert r["stats"]["instances"] == 0 and np.all(r["img"] == 0)
+    # one Gaussian, visible; one behind the camera
+    one = synth.uniform_scene(1, 0, seed=2)
+    r = gh.run(one, [cam], full=True)
+    check_eye(r, 0, one, cam, full=True)
+    behind = synth.uniform_scene(1, 0, seed=2)
+    behind.means[:, 2] = -3.0
+    r = gh.run(behind, [cam], full=True)
+    assert r["stats"]["instances"] == 0 and np.all(r["img"] == 0)
+    # a huge Gaussian covering every tile in front of small ones
+    s = synth.uniform_scene(500, 2, seed=4)
+    s.means[0] = [0.0, 0.0, 2.05]
+    s.log_scales[0] = [0.5, 0.5, 0.5]
+    r = gh.run(s, [cam], gaze=[(0.0, 0.0)], fovea=a3fr.Fovea())
+    check_eye(r, 0, s, cam, gaze=(0.0, 0.0), fv=oracle.fovea())
+    assert r["rect"][0, 0].tolist() == [0, 0, 4, 3]
+
+
+def test_capacity_overflow_sets_status_without_fault():
+    w = synth.small_single_view()
+    cam = w.cameras(0)[0]
+    r = gh.run(w.scene, [cam], full=True, capacity=1000)
+    st = r["stats"]
+    assert st["status"] & a3fr.STATUS_CAPACITY
+    assert st["instances"] == 1000 and st["capacity"] == 1000
+
+
+def test_repeated_renders_are_deterministic_and_counters_accumulate():
+    import torch
+    w = synth.small_single_view()
+    cam = w.cameras(0)[0]
+    s = a3fr.Scene.from_numpy(w.scene)
+    s.set_camera(0, cam)
+    s.set_gaze([w.fixed_gaze_px])
+    a = s.render_foveated().clone()
+    s.stats(reset=True)
+    for _ in range(3):
+        b = s.render_foveated()
+    st = s.stats()
+    torch.cuda.synchronize()
+    assert torch.equal(a, b)
+    assert st["renders"] == 3 and st["evaluations"] > 0 and st["status"] == 0
+
+
+def test_stereo_500k_sh3_sampled_pixels():
+    """The benchmark workload at full size: records and keys in full, pixels sampled."""
+    w = synth.stereo_500k(frames=240)
+    traj = synth.gaze_trajectory(240)
+    frame = 137
+    cams = w.cameras(frame)
+    gaze = w.gaze(frame, traj)
+    ofv, gfv = fovea_params()
+    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False)
+    assert r["stats"]["status"] == 0
+    rng = np.random.default_rng(frame)
+    for e in range(2):
+        pix = np.stack([rng.integers(0, 1280, 1500), rng.integers(0, 1280, 1500)], axis=1)
+        # plus every pixel of the tile row through the gaze (crosses all three layers)
+        gy = int(np.clip(gaze[e][1], 0, 1279)) // 16 * 16
+        band = np.stack(np.meshgrid(np.arange(0, 1280, 3), np.arange(gy, gy + 16, 5)), -1).reshape(-1, 2)
+        pix = np.concatenate([pix, band]).astype(np.int32)
+        print(e, check_eye(r, e, w.scene, cams[e], gaze=gaze[e], fv=ofv, pixels=pix))
