@@ -1,0 +1,521 @@
+#!/usr/bin/env python
+"""Benchmark of the foveated 3DGS forward rasterizer on GB300.
+
+Workload (default): 500k Gaussians, SH degree 3, stereo 1280x1280 per eye (IPD 63 mm,
+fov 90 deg), 16-px tiles, three foveation layers (18 / 36 deg -> levels 4 / 2 / 1), a
+240-frame gaze trajectory of fixations and saccades at 90 Hz and a head yaw drifting
+0.05 deg per frame so no frame reuses the previous projection.  One step = one stereo
+foveated frame: projection, binning, sort, composite of both eyes.
+
+Prints one JSON line: foveated FPS (value), p50/p99 frame ms, the same for the full-
+resolution render, PSNR of foveated vs full, per-stage ms, the roofline of the dominant
+kernel, the end-to-end rate through host buffers, the CPU oracle timed on the host cores,
+and the SM clocks sampled during the timed region.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+    torchrun --nproc-per-node N bench.py --gpus N ...   (frames sharded across ranks)
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "stereo foveated frame ms (p50/p99) & FPS vs full-res on same GB300; PSNR vs full"
+UNIT = "stereo frames/s"
+L2_FLUSH_BYTES = 256 << 20
+STAGES = ("preprocess", "scan", "emit", "sort", "ranges", "composite")
+SMS_GB300 = 152
+FP32_LANES_PER_SM = 128
+
+
+# ----------------------------------------------------------------------------- helpers
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2400)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", choices=["stereo500k", "small", "clustered3m"], default="stereo500k")
+    p.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def frames_for_rank(rank: int, world: int, steps: int, n_frames: int, offset: int = 0):
+    """Frame index of each timed step of a rank: ranks interleave over the trajectory."""
+    return [((s + offset) * world + rank) % n_frames for s in range(steps)]
+
+
+def reduce_max(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int, device=None) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def workload(name: str):
+    from paper_2507_04147_gb300 import synth
+    if name == "small":
+        return synth.small_single_view()
+    if name == "clustered3m":
+        return synth.stereo_3m_clustered()
+    return synth.stereo_500k()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples every 200 ms while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                   "-lms", "200"]
+            if self.gpu_id:
+                cmd += ["-i", self.gpu_id]
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "note": "nvidia-smi unavailable"}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def source_hash(*names) -> str:
+    h = hashlib.sha256()
+    for n in names:
+        with open(os.path.join(ROOT, "paper_2507_04147_gb300", "csrc", n), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if still current."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            entries = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = entries.get(kernel)
+    if not e or e.get("source_hash") != source_hash(*e.get("sources", [])):
+        return None
+    return e.get("dram_bytes_per_launch_full_workload")
+
+
+# ----------------------------------------------------------------------------- oracle
+def oracle_frame(w, frame: int, traj, budget_s: float, pixel_fraction_cap: float = 1.0):
+    """Time the CPU oracle on one foveated stereo frame; pixels are sampled to fit budget_s.
+
+    Returns (estimated frame seconds, description).  The oracle preprocesses every Gaussian,
+    builds and sorts every key in full, and composites a random sample of the rendered
+    (live) pixels of each eye; the composite time is scaled by live pixels / sampled pixels.
+    """
+    import oracle
+    cams = w.cameras(frame)
+    gaze = w.gaze(frame, traj)
+    fv = oracle.fovea(w.theta_deg, 0.0, (4, 2, 1))
+    rng = np.random.default_rng(frame)
+    total = 0.0
+    sampled = 0
+    live_total = 0
+    t_start = time.perf_counter()
+    per_eye_budget = budget_s / len(cams)
+    for e, cam in enumerate(cams):
+        t0 = time.perf_counter()
+        rec, rect, _ = oracle.preprocess(w.scene, cam, w.tile)
+        oracle.sorted_keys(rec, rect, oracle.tiles(cam.width, w.tile))
+        t_fixed = time.perf_counter() - t0
+        lv = oracle.level_map(cam, w.tile, fv, gaze[e])
+        tx = oracle.tiles(cam.width, w.tile)
+        ys, xs = np.mgrid[0:cam.height, 0:cam.width]
+        lab = np.array([[1, 4], [3, 2]])[xs & 1, ys & 1]
+        live = lab <= lv[(ys // w.tile) * tx + xs // w.tile]
+        live_xy = np.stack([xs[live], ys[live]], axis=1).astype(np.int32)
+        n_live = len(live_xy)
+        # calibrate on 256 pixels, then size the sample to the remaining budget
+        probe = live_xy[rng.choice(n_live, size=min(256, n_live), replace=False)]
+        t1 = time.perf_counter()
+        oracle.render(rec, rect, cam, w.tile, level=lv, pixels=probe)
+        t_probe = time.perf_counter() - t1
+        per_px = t_probe / max(len(probe), 1)
+        remaining = max(per_eye_budget - t_fixed - t_probe, 0.0)
+        n_more = int(min(remaining / max(per_px, 1e-9), n_live * pixel_fraction_cap))
+        t_pix, n_pix = t_probe, len(probe)
+        if n_more > 256:
+            more = live_xy[rng.choice(n_live, size=n_more, replace=False)]
+            t2 = time.perf_counter()
+            oracle.render(rec, rect, cam, w.tile, level=lv, pixels=more)
+            t_pix += time.perf_counter() - t2
+            n_pix += n_more
+        total += t_fixed + t_pix * n_live / n_pix
+        sampled += n_pix
+        live_total += n_live
+    wall = time.perf_counter() - t_start
+    desc = (f"frame {frame}: all {w.scene.n} Gaussians preprocessed and all keys sorted per eye; "
+            f"{sampled} of {live_total} rendered pixels composited ({100.0 * sampled / live_total:.2f}%), "
+            f"composite time scaled by pixel count; {wall:.1f} s of CPU work")
+    return total, desc
+
+
+def run_reference(args):
+    """The reference arm: the CPU oracle as it stands, timed on this machine's host cores."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_2507_04147_gb300 import synth
+    oracle.build()
+    w = workload(args.workload)
+    traj = synth.gaze_trajectory(w.frames)
+    per_step = max(150.0 / max(args.steps + args.warmup, 1), 0.05)
+    for s in range(args.warmup):
+        oracle_frame(w, s % w.frames, traj, per_step)
+    est = []
+    descs = []
+    for s in range(args.steps):
+        t, d = oracle_frame(w, (s * max(world, 1)) % w.frames, traj, per_step)
+        est.append(t)
+        descs.append(d)
+    value = len(est) / sum(est)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sum(est) / len(est), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w, world),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": descs[0] + f" (per step, {len(est)} steps)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(w, world: int):
+    c = w.cameras(0)[0]
+    return {"workload": w.name, "gaussians": w.scene.n, "sh_degree": w.scene.sh_degree,
+            "resolution": f"{c.width}x{c.height}", "eyes": w.n_eyes, "tile": w.tile,
+            "layers": {"theta_deg": list(w.theta_deg), "levels": [4, 2, 1]},
+            "trajectory_frames": w.frames, "l2": "flushed between timed frames (256 MiB write)",
+            "parallelism": f"frames sharded over {world} rank(s), no collective on the data path"}
+
+
+# ----------------------------------------------------------------------------- ours
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local_rank = dist_env()
+    torch.cuda.set_device(local_rank)
+    device = torch.device("cuda", local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=device)
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    barrier(world)
+    import paper_2507_04147_gb300 as a3fr
+    from paper_2507_04147_gb300 import synth
+    a3fr._lib.load()
+
+    w = workload(args.workload)
+    traj = synth.gaze_trajectory(w.frames)
+    cams0 = w.cameras(0)
+    eyes, H, W = len(cams0), cams0[0].height, cams0[0].width
+    scene = a3fr.Scene.from_numpy(w.scene)
+    for e, c in enumerate(cams0):
+        scene.set_camera(e, c)
+    fovea = a3fr.Fovea(w.theta_deg, 0.0, (4, 2, 1))
+    render_stream = torch.cuda.Stream()
+    gaze_stream = torch.cuda.Stream()
+    out = torch.empty((eyes, H, W, 3), dtype=torch.float32, device=device)
+    out_full = torch.empty_like(out)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=device)
+
+    def enqueue(f, full, dst, ev0=None, ev1=None, flush_l2=True):
+        cams = w.cameras(f)
+        for e in range(eyes):
+            scene.set_camera(e, cams[e])
+        if not full:
+            scene.set_gaze(w.gaze(f, traj), gaze_stream)
+        with torch.cuda.stream(render_stream):
+            if flush_l2:
+                flush.zero_()
+            if ev0 is not None:
+                ev0.record(render_stream)
+            if full:
+                scene.render_full(out=dst, stream=render_stream)
+            else:
+                scene.render_foveated(fovea, out=dst, stream=render_stream)
+            if ev1 is not None:
+                ev1.record(render_stream)
+
+    # warm-up (also sizes the instance capacity once)
+    for s in range(max(args.warmup, 3)):
+        f = frames_for_rank(rank, world, 1, w.frames, s)[0]
+        enqueue(f, False, out)
+        enqueue(f, True, out_full)
+    torch.cuda.synchronize()
+    frames = frames_for_rank(rank, world, args.steps, w.frames)
+
+    def timed_loop(full):
+        scene.stage_timing(args.steps)
+        scene.stats(reset=True)
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in frames]
+        barrier(world)
+        torch.cuda.synchronize()
+        for f, (a, b) in zip(frames, ev):
+            enqueue(f, full, out_full if full else out, a, b)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms = np.array([a.elapsed_time(b) for a, b in ev])
+        stages = scene.stage_times(args.steps)
+        st = scene.stats()
+        scene.stage_timing(0)
+        return ms, stages, st
+
+    dev_uuid = None
+    try:
+        dev_uuid = str(torch.cuda.get_device_properties(device).uuid)
+        if not dev_uuid.startswith("GPU-"):
+            dev_uuid = "GPU-" + dev_uuid
+    except Exception:
+        dev_uuid = None
+    clocks = ClockSampler(dev_uuid)
+    clocks.start()
+    ms_fov, st_fov, stats_fov = timed_loop(False)
+    clk = clocks.stop()
+    ms_full, st_full, stats_full = timed_loop(True)
+
+    total_fov = reduce_max(float(ms_fov.sum()), world, device)
+    total_full = reduce_max(float(ms_full.sum()), world, device)
+    frames_all = reduce_sum(float(len(frames)), world, device)
+    fps_fov = frames_all / (total_fov / 1000.0)
+    fps_full = frames_all / (total_full / 1000.0)
+
+    # PSNR of foveated vs full on a few frames (foveal = level-4 tiles)
+    psnr = psnr_frames(scene, enqueue, out, out_full, w, [0, 60, 120, 180], a3fr, torch)
+
+    # end to end through host buffers: host gaze/camera in, image back to pinned host memory
+    host_img = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
+    e2e_frames = frames[: min(len(frames), 240)]
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    for f in e2e_frames:
+        enqueue(f, False, out, flush_l2=False)
+        with torch.cuda.stream(render_stream):
+            host_img.copy_(out, non_blocking=True)
+        render_stream.synchronize()
+    e2e_s = reduce_max(time.perf_counter() - t0, world, device)
+    e2e_value = reduce_sum(float(len(e2e_frames)), world, device) / e2e_s
+
+    stage_mean_fov = {k: float(st_fov[:, i].mean()) for i, k in enumerate(STAGES)}
+    stage_mean_full = {k: float(st_full[:, i].mean()) for i, k in enumerate(STAGES)}
+    roof = roofline(w, stats_fov, stage_mean_fov, len(frames), eyes)
+
+    line = {"metric": METRIC, "value": fps_fov, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": total_fov / len(frames), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(w, world),
+            "latency_ms": {"foveated_p50": float(np.percentile(ms_fov, 50)),
+                           "foveated_p99": float(np.percentile(ms_fov, 99)),
+                           "full_p50": float(np.percentile(ms_full, 50)),
+                           "full_p99": float(np.percentile(ms_full, 99))},
+            "fps": {"foveated": fps_fov, "full": fps_full},
+            "speedup_vs_full": fps_fov / fps_full,
+            "psnr_db_vs_full": psnr,
+            "stage_ms": {"foveated": stage_mean_fov, "full": stage_mean_full},
+            "instances_per_frame": stats_fov["instances"],
+            "evaluations_per_frame": stats_fov["evaluations"] / max(len(frames), 1),
+            "roofline": roof,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 16 + eyes * 76,
+                    "d2h_bytes_per_step": int(out.numel() * 4),
+                    "note": "per frame: cameras + gaze from the host, render, image to pinned host memory, synchronise"},
+            "gpu_launches": int(stats_fov["kernel_launches"]),
+            "clocks": clk}
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        t, desc = oracle_frame(w, 0, traj, args.cpu_budget)
+        import oracle
+        line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": oracle.num_threads(),
+                                "kind": "oracle", "sample": desc}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    scene.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def psnr_frames(scene, enqueue, out, out_full, w, frame_ids, a3fr, torch):
+    se = {"foveal": 0.0, "periphery": 0.0, "whole": 0.0}
+    cnt = {"foveal": 0, "periphery": 0, "whole": 0}
+    for f in frame_ids:
+        f = f % w.frames
+        enqueue(f, False, out, flush_l2=False)
+        torch.cuda.synchronize()
+        levels = scene.buffer(a3fr.BUF_LEVELS, torch.uint8)
+        enqueue(f, True, out_full, flush_l2=False)
+        torch.cuda.synchronize()
+        eyes, H, W, _ = out.shape
+        tx = (W + w.tile - 1) // w.tile
+        ty = (H + w.tile - 1) // w.tile
+        lv = levels.reshape(eyes, ty, tx).repeat_interleave(w.tile, 1).repeat_interleave(w.tile, 2)[:, :H, :W]
+        fov = lv == 4
+        d2 = ((out.clamp(0, 1) - out_full.clamp(0, 1)) ** 2).mean(dim=-1).double()
+        for name, mask in (("foveal", fov), ("periphery", ~fov), ("whole", torch.ones_like(fov))):
+            se[name] += float(d2[mask].sum())
+            cnt[name] += int(mask.sum())
+    res = {}
+    for k in se:
+        mse = se[k] / max(cnt[k], 1)
+        res[k] = None if mse == 0 else 10.0 * math.log10(1.0 / mse)
+        res[k + "_mse"] = mse
+    res["note"] = "null dB = identical (MSE 0); foveal = level-4 tiles; images clamped to [0,1]"
+    return res
+
+
+def roofline(w, stats, stage_ms, n_frames, eyes):
+    """Roofline of the kernel with the largest share of the frame (per launch)."""
+    peaks, how = measured_peaks()
+    n = w.scene.n
+    K = (w.scene.sh_degree + 1) ** 2
+    inst = float(stats["instances"])
+    bits = 32 + max(1, math.ceil(math.log2(eyes * ((w.cameras(0)[0].width + 15) // 16) *
+                                           ((w.cameras(0)[0].height + 15) // 16))))
+    passes = (bits + 7) // 8
+    c0 = w.cameras(0)[0]
+    px = eyes * c0.width * c0.height
+    staged = stats["records_staged"] / max(n_frames, 1)
+    evals = stats["evaluations"] / max(n_frames, 1)
+    algo = {
+        # bytes: Gaussian parameters once, records + rects + touched per eye
+        "preprocess": ("hbm", n * (4 * (3 + 3 + 4 + 1 + 3 * K) + 4 + eyes * (48 + 8))),
+        "sort": ("hbm", inst * (8 + 24 * passes)),
+        "emit": ("hbm", n * eyes * (8 + 4) + n * 4 + inst * 12),
+        "ranges": ("hbm", inst * 8),
+        # flops: 14 per (pixel, Gaussian) evaluation (offset, quadratic form, alpha)
+        "composite": ("alu", evals * 14.0),
+    }
+    dom = max(STAGES, key=lambda k: stage_ms.get(k, 0.0) if k in algo else -1)
+    bound, work = algo[dom]
+    t = stage_ms[dom] / 1000.0
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    if bound == "hbm":
+        achieved = work / t / 1e9
+        peak = float(peaks["hbm_gbs"])
+        unit = "GB/s"
+    else:
+        achieved = work / t / 1e12
+        peak = SMS_GB300 * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+        unit = "TFLOP/s"
+    comp_bytes = staged * 52 + px * 12
+    res = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
+           "frac": achieved / peak, "traffic": ncu_traffic(dom),
+           "peak_source": f"{how} MEASURED_PEAKS.json" if bound == "hbm" else
+           f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sm_max_mhz of {how} peaks)",
+           "work_per_launch": work, "launch_ms": stage_ms[dom],
+           "share_of_frame": stage_ms[dom] / max(sum(stage_ms.values()), 1e-9)}
+    # the composite kernel measured in algorithmic bytes as well
+    res["composite_hbm"] = {"bytes_per_launch": comp_bytes,
+                            "achieved_gbs": comp_bytes / (stage_ms["composite"] / 1000.0) / 1e9,
+                            "frac_of_hbm": comp_bytes / (stage_ms["composite"] / 1000.0) / 1e9 / float(peaks["hbm_gbs"])}
+    return res
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()
