@@ -174,6 +174,29 @@ int a3fr_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t
                     size_t n, int key_bits, void *workspace, size_t workspace_bytes,
                     void *stream);
 
+/* Largest n accepted by a3fr_sort_pairs_noalloc. */
+#define A3FR_NOALLOC_MAX_PAIRS 262144
+
+/* The sort of a3fr_sort_pairs for callers that cannot allocate device memory -- for example
+ * a real-time render thread that cannot absorb the device-wide synchronisation cudaMalloc
+ * and cudaFree may cause, or code inside an engine that owns all device memory through its
+ * own allocator.  The paper has no counterpart; this is a library convenience.
+ *
+ * keys/vals (DEVICE uint64/uint32 [n]) hold the input and receive the result, as in
+ * a3fr_sort_pairs; nothing else is passed in.  The scratch (ping-pong buffers, histograms,
+ * look-back words) is one fixed file-scope device array of about 5 MB, which every GPU that
+ * loads the library holds until the process exits.  This call allocates nothing: no
+ * cudaMalloc, no cudaFree, no allocating library routine.
+ *  - n > A3FR_NOALLOC_MAX_PAIRS returns A3FR_ERR_CAPACITY and does no work.
+ *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ *    with that device current; make that first call before any stream capture.
+ *  - Every call shares the one array, so calls whose work overlaps on the GPU (on different
+ *    streams, or from different threads) race and corrupt each other's results; serialise
+ *    them, e.g. on one stream.  The array keeps the last call's contents; each call clears
+ *    what must start at zero. */
+int a3fr_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, size_t n, int key_bits,
+                            void *stream);
+
 /* Human-readable name of an A3FR_* code (static storage). */
 const char *a3fr_error_string(int code);
 

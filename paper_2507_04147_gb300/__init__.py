@@ -22,6 +22,7 @@ from ._lib import A3FRError, BUF_KEYS, BUF_LEVELS, BUF_N_CONTRIB, BUF_RANGES, BU
 __all__ = ["Scene", "Fovea", "A3FRError", "camera_struct", "create_scene", "destroy_scene",
            "set_camera", "set_gaze", "render_foveated", "render_full", "get_stats",
            "set_keep_aux", "set_stage_timing", "get_stage_times", "copy_buffer", "sort_pairs", "sort_pairs_workspace_bytes",
+           "sort_pairs_noalloc",
            "error_string"]
 
 
@@ -150,6 +151,13 @@ def sort_pairs(keys, vals, keys_alt, vals_alt, key_bits: int, workspace, stream=
     _lib.check(_lib.load().a3fr_sort_pairs(_ptr(keys), _ptr(vals), _ptr(keys_alt), _ptr(vals_alt),
                                            n, key_bits, _ptr(workspace), workspace.numel(),
                                            _stream_ptr(stream)), "a3fr_sort_pairs")
+
+
+def sort_pairs_noalloc(keys, vals, key_bits: int, stream=None) -> None:
+    """The same sort for callers that cannot allocate: scratch comes from a fixed device
+    array inside the library (at most NOALLOC_MAX_PAIRS pairs; overlapping calls race)."""
+    _lib.check(_lib.load().a3fr_sort_pairs_noalloc(_ptr(keys), _ptr(vals), keys.numel(), key_bits,
+                                                   _stream_ptr(stream)), "a3fr_sort_pairs_noalloc")
 
 
 def error_string(code: int) -> str:

@@ -16,6 +16,8 @@ ERRORS = {-1: "INVALID_ARG", -2: "CUDA", -3: "OOM", -4: "CAPACITY", -5: "TIMEOUT
 STATUS_CAPACITY = 1
 STATUS_TIMEOUT = 2
 
+NOALLOC_MAX_PAIRS = 262144
+
 STAGES = ("preprocess", "scan", "emit", "sort", "ranges", "composite")
 
 BUF_RECORDS, BUF_RECTS, BUF_KEYS, BUF_VALUES, BUF_RANGES, BUF_LEVELS, BUF_T_FINAL, BUF_N_CONTRIB = range(1, 9)
@@ -74,6 +76,8 @@ _SIGS = {
     "a3fr_sort_pairs": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
                          ctypes.c_size_t, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                          ctypes.c_void_p], ctypes.c_int),
+    "a3fr_sort_pairs_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                 ctypes.c_void_p], ctypes.c_int),
     "a3fr_set_stage_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_get_stage_times": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                               ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
