@@ -52,12 +52,12 @@ struct a3fr_scene {
   bool cam_set[kMaxEyes]{false, false};
 
   // per-Gaussian and per-tile workspace, sized for (n_eyes, W, H)
-  int alloc_eyes = 0, W = 0, H = 0, TX = 0, TY = 0, n_tiles = 0, n_blocks = 0;
+  int alloc_eyes = 0, W = 0, H = 0, TX = 0, TY = 0, n_tiles = 0;
   float *rec = nullptr;
   ushort4 *rect = nullptr;
   uint32_t *touched = nullptr;
-  uint32_t *block_sums = nullptr;
-  unsigned long long *block_offsets = nullptr;
+  uint32_t *dkeys[2] = {nullptr, nullptr};   // depth-sort keys (ping-pong)
+  uint32_t *dvals[2] = {nullptr, nullptr};   // depth-sorted entries e * n + i
   uint2 *ranges = nullptr;
   uint8_t *levels = nullptr;
   float *t_final = nullptr;
@@ -65,13 +65,14 @@ struct a3fr_scene {
   // instance workspace
   size_t capacity = 0;
   bool auto_capacity = false;
-  uint64_t *keys[2] = {nullptr, nullptr};
-  uint32_t *vals[2] = {nullptr, nullptr};
-  void *sort_ws = nullptr;
-  size_t sort_ws_bytes = 0;
+  uint32_t *tkeys[2] = {nullptr, nullptr};   // tile index of each instance (ping-pong)
+  uint32_t *tvals[2] = {nullptr, nullptr};   // Gaussian index of each instance
   bool sorted_in_alt = false;
-  // small device state: counts[4] | status | pad | counters[2]
-  uint32_t *counts = nullptr;
+  // per-frame scratch, zeroed at the start of every render (see frame_layout)
+  void *frame_ws = nullptr;
+  size_t frame_ws_bytes = 0;
+  uint32_t *counts = nullptr;                // [0] kept, [1..2] per eye, [3] total, [4] entries
+  // persistent device state: status | counters[2]
   uint32_t *status = nullptr;
   unsigned long long *counters = nullptr;
   void *small = nullptr;
@@ -100,12 +101,42 @@ namespace {
 
 int n_eyes_of(const a3fr_scene *s) { return s->cam_set[1] ? 2 : (s->cam_set[0] ? 1 : 0); }
 
+constexpr int kDepthPasses = 4;   // 32-bit depth keys, 8-bit digits
+
+int tile_bits_for(int n_ranges) {
+  int bits = 1;
+  while ((1ll << bits) < (long long)n_ranges) ++bits;
+  return bits;
+}
+
+// Byte offsets inside frame_ws; everything in it starts at zero every render.
+struct FrameLayout {
+  size_t counts = 0;                 // 8 x u32: counts[0..4], emit block counter at [6]
+  size_t depth_hist = 64;            // kMaxSortPasses x 256 u32
+  size_t depth_ctr = 64 + 8192;      // kMaxSortPasses u32 (+pad)
+  size_t tile_hist = 64 + 8192 + 64;
+  size_t tile_ctr = 64 + 8192 + 64 + 8192;
+  size_t emit_lb = 64 + 8192 + 64 + 8192 + 64;
+  size_t depth_lb = 0, tile_lb = 0, total = 0;
+};
+
+FrameLayout frame_layout(size_t entries, size_t capacity, int tile_passes) {
+  FrameLayout L;
+  auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+  L.depth_lb = up(L.emit_lb + emit_lookback_bytes((int)entries));
+  L.tile_lb = up(L.depth_lb + onesweep_lookback_bytes(entries, kDepthPasses, false));
+  L.total = up(L.tile_lb + onesweep_lookback_bytes(capacity, tile_passes, false));
+  return L;
+}
+
 void free_frame_buffers(a3fr_scene *s) {
   dfree(s->rec);
   dfree(s->rect);
   dfree(s->touched);
-  dfree(s->block_sums);
-  dfree(s->block_offsets);
+  for (int b = 0; b < 2; ++b) {
+    dfree(s->dkeys[b]);
+    dfree(s->dvals[b]);
+  }
   dfree(s->ranges);
   dfree(s->levels);
   dfree(s->t_final);
@@ -115,23 +146,38 @@ void free_frame_buffers(a3fr_scene *s) {
 
 void free_instance_buffers(a3fr_scene *s) {
   for (int b = 0; b < 2; ++b) {
-    dfree(s->keys[b]);
-    dfree(s->vals[b]);
+    dfree(s->tkeys[b]);
+    dfree(s->tvals[b]);
   }
-  dfree(s->sort_ws);
-  s->sort_ws_bytes = 0;
+}
+
+// (Re)allocate frame_ws for the current entry count and capacity.
+int ensure_frame_ws(a3fr_scene *s) {
+  const size_t entries = (size_t)s->alloc_eyes * (size_t)(s->desc.n > 0 ? s->desc.n : 1);
+  const int tile_passes = sort_plan(tile_bits_for(s->alloc_eyes * s->n_tiles), 8).passes;
+  const FrameLayout L = frame_layout(entries, s->capacity, tile_passes);
+  if (s->frame_ws && s->frame_ws_bytes >= L.total) return A3FR_OK;
+  if (s->frame_ws) {
+    A3FR_CHECK(cudaDeviceSynchronize());
+    dfree(s->frame_ws);
+  }
+  A3FR_CHECK(cudaMalloc(&s->frame_ws, L.total));
+  A3FR_CHECK(cudaMemset(s->frame_ws, 0, L.total));
+  s->frame_ws_bytes = L.total;
+  s->counts = reinterpret_cast<uint32_t *>(static_cast<unsigned char *>(s->frame_ws) + L.counts);
+  return A3FR_OK;
 }
 
 int alloc_instances(a3fr_scene *s, size_t capacity) {
   free_instance_buffers(s);
   s->capacity = capacity;
-  if (capacity == 0) return A3FR_OK;
-  for (int b = 0; b < 2; ++b) {
-    A3FR_CHECK(cudaMalloc(&s->keys[b], sizeof(uint64_t) * capacity));
-    A3FR_CHECK(cudaMalloc(&s->vals[b], sizeof(uint32_t) * capacity));
+  if (capacity > 0) {
+    for (int b = 0; b < 2; ++b) {
+      A3FR_CHECK(cudaMalloc(&s->tkeys[b], sizeof(uint32_t) * capacity));
+      A3FR_CHECK(cudaMalloc(&s->tvals[b], sizeof(uint32_t) * capacity));
+    }
   }
-  s->sort_ws_bytes = sort_workspace_bytes(capacity);
-  A3FR_CHECK(cudaMalloc(&s->sort_ws, s->sort_ws_bytes));
+  if (s->alloc_eyes) return ensure_frame_ws(s);
   return A3FR_OK;
 }
 
@@ -147,13 +193,14 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
   s->TX = (W + tile - 1) / tile;
   s->TY = (H + tile - 1) / tile;
   s->n_tiles = s->TX * s->TY;
-  s->n_blocks = (n + kPreThreads - 1) / kPreThreads;
-  const size_t nn = n > 0 ? (size_t)n : 1;
-  A3FR_CHECK(cudaMalloc(&s->rec, sizeof(float) * kRec * nn * eyes));
-  A3FR_CHECK(cudaMalloc(&s->rect, sizeof(ushort4) * nn * eyes));
+  const size_t nn = (n > 0 ? (size_t)n : 1) * eyes;
+  A3FR_CHECK(cudaMalloc(&s->rec, sizeof(float) * kRec * nn));
+  A3FR_CHECK(cudaMalloc(&s->rect, sizeof(ushort4) * nn));
   A3FR_CHECK(cudaMalloc(&s->touched, sizeof(uint32_t) * nn));
-  A3FR_CHECK(cudaMalloc(&s->block_sums, sizeof(uint32_t) * 2 * (s->n_blocks + 1)));
-  A3FR_CHECK(cudaMalloc(&s->block_offsets, sizeof(unsigned long long) * (s->n_blocks + 1)));
+  for (int b = 0; b < 2; ++b) {
+    A3FR_CHECK(cudaMalloc(&s->dkeys[b], sizeof(uint32_t) * nn));
+    A3FR_CHECK(cudaMalloc(&s->dvals[b], sizeof(uint32_t) * nn));
+  }
   A3FR_CHECK(cudaMalloc(&s->ranges, sizeof(uint2) * (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->levels, (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->t_final, sizeof(float) * (size_t)W * H * eyes));
@@ -161,7 +208,7 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
   A3FR_CHECK(cudaMemset(s->ranges, 0, sizeof(uint2) * (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMemset(s->levels, 0, (size_t)s->n_tiles * eyes));
   s->alloc_eyes = eyes;
-  return A3FR_OK;
+  return ensure_frame_ws(s);
 }
 
 CamParams cam_params(const a3fr_camera &c) {
@@ -209,12 +256,6 @@ float layer_radius2(float fx, float theta_deg, float dtheta_deg) {
   return r * r;
 }
 
-int key_bits_for(int n_ranges) {
-  int bits = 1;
-  while ((1ll << bits) < (long long)n_ranges) ++bits;
-  return 32 + bits;
-}
-
 void free_timing(a3fr_scene *s) {
   if (s->timing_events) {
     for (int i = 0; i < s->timing_ring * (A3FR_N_STAGES + 1); ++i)
@@ -248,6 +289,21 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
   int rc = ensure_frame_buffers(s, eyes, c0.width, c0.height);
   if (rc != A3FR_OK) return rc;
   const int n = s->desc.n;
+  const int n_entries = eyes * n;
+  const int n_ranges = eyes * s->n_tiles;
+  const SortPlan depth_plan = sort_plan(32, 8);
+  const SortPlan tile_plan = sort_plan(tile_bits_for(n_ranges), 8);
+  FrameLayout L = frame_layout((size_t)(n_entries > 0 ? n_entries : eyes), s->capacity,
+                               tile_plan.passes);
+  unsigned char *ws = static_cast<unsigned char *>(s->frame_ws);
+  uint32_t *counts = s->counts;
+  uint32_t *depth_hist = reinterpret_cast<uint32_t *>(ws + L.depth_hist);
+  uint32_t *depth_ctr = reinterpret_cast<uint32_t *>(ws + L.depth_ctr);
+  uint32_t *tile_hist = reinterpret_cast<uint32_t *>(ws + L.tile_hist);
+  uint32_t *tile_ctr = reinterpret_cast<uint32_t *>(ws + L.tile_ctr);
+  unsigned long long *emit_lb = reinterpret_cast<unsigned long long *>(ws + L.emit_lb);
+  uint32_t *depth_lb = reinterpret_cast<uint32_t *>(ws + L.depth_lb);
+  uint32_t *tile_lb = reinterpret_cast<uint32_t *>(ws + L.tile_lb);
 
   PreParams pp{};
   for (int e = 0; e < eyes; ++e) pp.cam[e] = cam_params(s->cams[e]);
@@ -259,55 +315,75 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
 
   uint64_t launches = 0;
   A3FR_CHECK(mark(s, A3FR_STAGE_PREPROCESS, stream));
+  A3FR_CHECK(cudaMemsetAsync(s->frame_ws, 0, L.total, stream));
   if (n > 0) {
     A3FR_CHECK(launch_preprocess(pp, n, s->desc.sh_degree, s->desc.means, s->desc.log_scales,
                                  s->desc.quats, s->desc.opacity_logits, s->desc.sh, s->rec,
-                                 s->rect, s->touched, s->block_sums, stream));
+                                 s->rect, s->touched, s->dkeys[0], counts + 4, stream));
     ++launches;
   }
+  // depth sort of the (eye, Gaussian) entries: 4 passes, result back in dkeys[0]/dvals[0]
+  A3FR_CHECK(mark(s, A3FR_STAGE_SCAN, stream));
+  if (n > 0) {
+    A3FR_CHECK(launch_histogram<uint32_t>(s->dkeys[0], counts + 4, (size_t)n_entries,
+                                          depth_plan, depth_hist, stream));
+    bool in_alt = false;
+    A3FR_CHECK(launch_onesweep<uint32_t>(s->dkeys[0], s->dvals[0], s->dkeys[1], s->dvals[1], true,
+                                         counts + 4, (size_t)n_entries, depth_plan, depth_hist,
+                                         depth_ctr, depth_lb, s->status, &in_alt, stream));
+    launches += 1 + depth_plan.passes;
+  }
+  const uint32_t *entries = s->dvals[depth_plan.passes % 2];
+  EmitParams ep{};
+  ep.n = n;
+  ep.n_entries = n_entries;
+  ep.n_tiles = s->n_tiles;
+  ep.tiles_x = s->TX;
+  ep.tile_plan = tile_plan;
+  uint32_t *emit_ctr = counts + 6;
   if (s->auto_capacity && s->capacity == 0 && n > 0) {
-    // first render: measure the instance count once
-    A3FR_CHECK(launch_scan_blocks(s->block_sums, s->n_blocks, s->block_offsets, s->counts, 0u,
-                                  s->status, stream));
+    // first render: measure the instance count once, then size the instance buffers
+    ep.capacity = 0;
+    A3FR_CHECK(launch_emit(ep, entries, s->touched, s->rect, nullptr, nullptr, emit_lb, emit_ctr,
+                           counts, s->status, tile_hist, stream));
     ++launches;
-    uint32_t cnt[4];
-    A3FR_CHECK(cudaMemcpyAsync(cnt, s->counts, sizeof cnt, cudaMemcpyDeviceToHost, stream));
+    uint32_t cnt[8];
+    A3FR_CHECK(cudaMemcpyAsync(cnt, counts, sizeof cnt, cudaMemcpyDeviceToHost, stream));
     A3FR_CHECK(cudaStreamSynchronize(stream));
     A3FR_CHECK(cudaMemsetAsync(s->status, 0, sizeof(uint32_t), stream));
     size_t want = 2 * (size_t)cnt[3] + (1u << 16);
     if (want >= (1u << 30)) want = (1u << 30) - 1;
     rc = alloc_instances(s, want);
     if (rc != A3FR_OK) return rc;
+    L = frame_layout((size_t)n_entries, s->capacity, tile_plan.passes);
+    ws = static_cast<unsigned char *>(s->frame_ws);
+    counts = s->counts;
+    tile_hist = reinterpret_cast<uint32_t *>(ws + L.tile_hist);
+    tile_ctr = reinterpret_cast<uint32_t *>(ws + L.tile_ctr);
+    emit_lb = reinterpret_cast<unsigned long long *>(ws + L.emit_lb);
+    tile_lb = reinterpret_cast<uint32_t *>(ws + L.tile_lb);
+    emit_ctr = counts + 6;
+    A3FR_CHECK(cudaMemsetAsync(s->frame_ws, 0, L.total, stream));
   }
-  A3FR_CHECK(mark(s, A3FR_STAGE_SCAN, stream));
-  if (n > 0) {
-    A3FR_CHECK(launch_scan_blocks(s->block_sums, s->n_blocks, s->block_offsets, s->counts,
-                                  (uint32_t)s->capacity, s->status, stream));
-    ++launches;
-  } else {
-    A3FR_CHECK(cudaMemsetAsync(s->counts, 0, 4 * sizeof(uint32_t), stream));
-  }
-  const int n_ranges = eyes * s->n_tiles;
   A3FR_CHECK(mark(s, A3FR_STAGE_EMIT, stream));
+  ep.capacity = (uint32_t)s->capacity;
   if (n > 0 && s->capacity > 0) {
-    A3FR_CHECK(launch_emit_keys(n, eyes, s->TX, s->n_tiles, s->rec, s->rect, s->touched,
-                                s->block_offsets, (uint32_t)s->capacity, s->keys[0], s->vals[0],
-                                stream));
+    A3FR_CHECK(launch_emit(ep, entries, s->touched, s->rect, s->tkeys[0], s->tvals[0], emit_lb,
+                           emit_ctr, counts, s->status, tile_hist, stream));
     ++launches;
-    A3FR_CHECK(mark(s, A3FR_STAGE_SORT, stream));
-    bool in_alt = false;
-    const int bits = key_bits_for(n_ranges);
-    A3FR_CHECK(launch_sort(s->keys[0], s->vals[0], s->keys[1], s->vals[1], s->counts,
-                           s->capacity, bits, s->sort_ws, s->status, &in_alt, stream));
-    launches += 1 + (bits + 7) / 8;
-    s->sorted_in_alt = in_alt;
-  } else {
-    A3FR_CHECK(mark(s, A3FR_STAGE_SORT, stream));
-    s->sorted_in_alt = false;
   }
-  const int b = s->sorted_in_alt ? 1 : 0;
+  A3FR_CHECK(mark(s, A3FR_STAGE_SORT, stream));
+  bool in_alt = false;
+  if (n > 0 && s->capacity > 0) {
+    A3FR_CHECK(launch_onesweep<uint32_t>(s->tkeys[0], s->tvals[0], s->tkeys[1], s->tvals[1], false,
+                                         counts, s->capacity, tile_plan, tile_hist, tile_ctr,
+                                         tile_lb, s->status, &in_alt, stream));
+    launches += tile_plan.passes;
+  }
+  s->sorted_in_alt = in_alt;
+  const int b = in_alt ? 1 : 0;
   A3FR_CHECK(mark(s, A3FR_STAGE_RANGES, stream));
-  A3FR_CHECK(launch_tile_ranges(s->keys[b], s->counts, n > 0 ? s->capacity : 0, s->ranges,
+  A3FR_CHECK(launch_tile_ranges(s->tkeys[b], counts, n > 0 ? s->capacity : 0, s->ranges,
                                 n_ranges, stream));
   if (n > 0 && s->capacity > 0) ++launches;
 
@@ -337,7 +413,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
     gaze = s->gaze_dev;   // not read when full
   }
   A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
-  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, s->vals[b], gaze, out, s->levels,
+  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, s->tvals[b], gaze, out, s->levels,
                               s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
   ++launches;
@@ -386,7 +462,6 @@ int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3f
   cudaError_t e = cudaMalloc(&s->small, 256);
   if (e != cudaSuccess) return fail(cuda_fail(e, "cudaMalloc(state)"));
   unsigned char *sm = static_cast<unsigned char *>(s->small);
-  s->counts = reinterpret_cast<uint32_t *>(sm);
   s->status = reinterpret_cast<uint32_t *>(sm + 16);
   s->counters = reinterpret_cast<unsigned long long *>(sm + 32);
   if ((e = cudaMemset(s->small, 0, 256)) != cudaSuccess) return fail(cuda_fail(e, "cudaMemset"));
@@ -416,6 +491,7 @@ int a3fr_destroy_scene(a3fr_scene *s) {
   free_timing(s);
   free_frame_buffers(s);
   free_instance_buffers(s);
+  dfree(s->frame_ws);
   dfree(s->gaze_dev);
   if (s->small) cudaFree(s->small);
   if (s->gaze_pinned) cudaFreeHost(s->gaze_pinned);
@@ -478,10 +554,10 @@ int a3fr_get_stats(a3fr_scene *s, a3fr_stats *st, int reset) {
   A3FR_CHECK(cudaStreamSynchronize(s->last_stream));
   unsigned char buf[256];
   A3FR_CHECK(cudaMemcpy(buf, s->small, sizeof buf, cudaMemcpyDeviceToHost));
-  uint32_t counts[4];
+  uint32_t counts[4] = {0, 0, 0, 0};
+  if (s->counts) A3FR_CHECK(cudaMemcpy(counts, s->counts, sizeof counts, cudaMemcpyDeviceToHost));
   uint32_t status;
   unsigned long long ctr[2];
-  std::memcpy(counts, buf, sizeof counts);
   std::memcpy(&status, buf + 16, sizeof status);
   std::memcpy(ctr, buf + 32, sizeof ctr);
   std::memset(st, 0, sizeof *st);
@@ -552,19 +628,17 @@ int a3fr_copy_buffer(a3fr_scene *s, int which, void *dst, size_t bytes, size_t *
   const size_t n = (size_t)s->desc.n;
   const void *src = nullptr;
   size_t size = 0;
+  uint32_t cnt = 0;
+  const int b = s->sorted_in_alt ? 1 : 0;
+  if (which == A3FR_BUF_KEYS || which == A3FR_BUF_VALUES) {
+    A3FR_CHECK(cudaStreamSynchronize(s->last_stream));
+    if (s->counts) A3FR_CHECK(cudaMemcpy(&cnt, s->counts, sizeof cnt, cudaMemcpyDeviceToHost));
+  }
   switch (which) {
     case A3FR_BUF_RECORDS: src = s->rec; size = sizeof(float) * kRec * n * eyes; break;
     case A3FR_BUF_RECTS: src = s->rect; size = sizeof(ushort4) * n * eyes; break;
-    case A3FR_BUF_KEYS:
-    case A3FR_BUF_VALUES: {
-      A3FR_CHECK(cudaStreamSynchronize(s->last_stream));
-      uint32_t cnt = 0;
-      A3FR_CHECK(cudaMemcpy(&cnt, s->counts, sizeof cnt, cudaMemcpyDeviceToHost));
-      const int b = s->sorted_in_alt ? 1 : 0;
-      if (which == A3FR_BUF_KEYS) { src = s->keys[b]; size = sizeof(uint64_t) * cnt; }
-      else { src = s->vals[b]; size = sizeof(uint32_t) * cnt; }
-      break;
-    }
+    case A3FR_BUF_KEYS: size = sizeof(uint64_t) * cnt; break;   // built on demand below
+    case A3FR_BUF_VALUES: src = s->tvals[b]; size = sizeof(uint32_t) * cnt; break;
     case A3FR_BUF_RANGES: src = s->ranges; size = sizeof(uint2) * (size_t)s->n_tiles * eyes; break;
     case A3FR_BUF_LEVELS: src = s->levels; size = (size_t)s->n_tiles * eyes; break;
     case A3FR_BUF_T_FINAL: src = s->t_final; size = sizeof(float) * (size_t)s->W * s->H * eyes; break;
@@ -575,8 +649,15 @@ int a3fr_copy_buffer(a3fr_scene *s, int which, void *dst, size_t bytes, size_t *
   if (dst == nullptr) return bytes == 0 ? A3FR_OK : A3FR_ERR_INVALID_ARG;
   if (bytes > size) return A3FR_ERR_INVALID_ARG;
   if (bytes == 0) return A3FR_OK;
-  A3FR_CHECK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice,
-                             static_cast<cudaStream_t>(stream)));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (which == A3FR_BUF_KEYS) {
+    // the render sorts tile indices; the 64-bit (tile << 32 | depth bits) keys are rebuilt
+    A3FR_CHECK(launch_materialize_keys(s->tkeys[b], s->tvals[b], s->rec, s->desc.n, s->n_tiles,
+                                       (uint32_t)(bytes / sizeof(uint64_t)),
+                                       static_cast<uint64_t *>(dst), st));
+    return A3FR_OK;
+  }
+  A3FR_CHECK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, st));
   return A3FR_OK;
 }
 

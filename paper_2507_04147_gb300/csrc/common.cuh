@@ -50,30 +50,64 @@ __device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
 // Kernel launchers defined in the .cu files (host side).
 namespace a3fr {
 
+constexpr int kMaxSortPasses = 8;
+
+// Digit plan of a radix sort: `passes` digits of the same width, digit p = (key >> shift[p]) & mask.
+struct SortPlan {
+  int passes;
+  int shift[kMaxSortPasses];
+  uint32_t mask;
+};
+
+// Writes rec/rect per eye, touched[e*n + i], the depth-sort keys dkeys[e*n + i] (depth bits,
+// 0xffffffff when culled) and depth_count[0] = n_eyes * n.
 cudaError_t launch_preprocess(const PreParams &p, int n, int sh_degree, const float *means,
                               const float *log_scales, const float *quats,
                               const float *opacity_logits, const float *sh, float *rec,
-                              ushort4 *rect, uint32_t *touched, uint32_t *block_sums,
-                              cudaStream_t s);
+                              ushort4 *rect, uint32_t *touched, uint32_t *dkeys,
+                              uint32_t *depth_count, cudaStream_t s);
 
-cudaError_t launch_scan_blocks(const uint32_t *block_sums, int n_blocks,
-                               unsigned long long *block_offsets, uint32_t *counts,
-                               uint32_t capacity, uint32_t *status, cudaStream_t s);
+SortPlan sort_plan(int key_bits, int digit_bits_max);
+size_t onesweep_part_size(bool wide_keys);
+size_t onesweep_lookback_bytes(size_t capacity, int passes, bool wide_keys);
+template <typename K>
+cudaError_t launch_histogram(const K *keys, const uint32_t *d_count, size_t capacity,
+                             const SortPlan &plan, uint32_t *hist, cudaStream_t s);
+// Sorts d_count[0] (<= capacity) pairs with `plan`; hist holds the digit counts of every
+// pass, counters and lookback are zeroed scratch.  With implicit_vals the first pass takes
+// each pair's value to be its input position.  *result_in_alt tells where the result is.
+template <typename K>
+cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
+                            bool implicit_vals, const uint32_t *d_count, size_t capacity,
+                            const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
+                            uint32_t *lookback, uint32_t *status, bool *result_in_alt,
+                            cudaStream_t s);
 
-cudaError_t launch_emit_keys(int n, int n_eyes, int tiles_x, int n_tiles, const float *rec,
-                             const ushort4 *rect, const uint32_t *touched,
-                             const unsigned long long *block_offsets, uint32_t capacity,
-                             uint64_t *keys, uint32_t *vals, cudaStream_t s);
-
+// The 64-bit pair sort of the public API: workspace = histograms | counters | look-back.
 size_t sort_workspace_bytes(size_t capacity);
-// Sorts counts[0] pairs (device-resident count, at most capacity); returns in *result_in_alt
-// whether the sorted data ended in the alt buffers.
 cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                         const uint32_t *d_count, size_t capacity, int key_bits, void *workspace,
                         uint32_t *status, bool *result_in_alt, cudaStream_t s);
 
-cudaError_t launch_tile_ranges(const uint64_t *keys, const uint32_t *d_count, size_t capacity,
-                               uint2 *ranges, int n_ranges, cudaStream_t s);
+// Emission of the tile instances of the depth-ordered entries (see binning.cu).
+struct EmitParams {
+  int n, n_entries, n_tiles, tiles_x;
+  uint32_t capacity;
+  SortPlan tile_plan;       // digits of the tile sort (histograms accumulated here)
+};
+size_t emit_lookback_bytes(int n_entries);
+cudaError_t launch_emit(const EmitParams &p, const uint32_t *entries, const uint32_t *touched,
+                        const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
+                        unsigned long long *lookback, uint32_t *block_counter, uint32_t *counts,
+                        uint32_t *status, uint32_t *tile_hist, cudaStream_t s);
+
+cudaError_t launch_tile_ranges(const uint32_t *tile_keys, const uint32_t *d_count,
+                               size_t capacity, uint2 *ranges, int n_ranges, cudaStream_t s);
+
+// keys[j] = tile_keys[j] << 32 | depth bits of the Gaussian vals[j] (for inspection).
+cudaError_t launch_materialize_keys(const uint32_t *tile_keys, const uint32_t *vals,
+                                    const float *rec, int n, int n_tiles, uint32_t count,
+                                    uint64_t *keys, cudaStream_t s);
 
 struct CompositeParams {
   int n_eyes, width, height, tile, tiles_x, tiles_y, n_tiles;

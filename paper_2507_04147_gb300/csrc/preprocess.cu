@@ -13,8 +13,9 @@
 //    rounded fp32 operation in a fixed order (no FMA contraction), with the project's own
 //    Cody-Waite + Taylor exp, so the integer outputs are reproducible bit for bit by any
 //    IEEE fp32 implementation of the same sequence;
-//  * the block's total of touched tiles is reduced here and written to block_sums, the
-//    first half of the reduce-then-scan that assigns instance offsets.
+//  * it also writes the key of the per-frame depth sort of the Gaussians (the depth bits,
+//    all ones when the Gaussian is culled), so that the instances can be emitted in depth
+//    order and then sorted by tile alone.
 #include "common.cuh"
 
 namespace a3fr {
@@ -104,13 +105,13 @@ preprocess_kernel(PreParams p, int n, const float *__restrict__ means,
                   const float *__restrict__ log_scales, const float *__restrict__ quats,
                   const float *__restrict__ opacity_logits, const float *__restrict__ sh,
                   float *__restrict__ rec, ushort4 *__restrict__ rect,
-                  uint32_t *__restrict__ touched, uint32_t *__restrict__ block_sums) {
+                  uint32_t *__restrict__ touched, uint32_t *__restrict__ dkeys,
+                  uint32_t *__restrict__ depth_count) {
   constexpr int SS = sh_stride<K>();
   __shared__ float s_mean[kPreThreads * 3];
   __shared__ float s_scale[kPreThreads * 3];
   __shared__ float4 s_quat[kPreThreads];
   __shared__ float s_sh[kPreThreads * SS];
-  __shared__ uint32_t s_warp[kPreThreads / 32][kMaxEyes];
 
   const int i0 = blockIdx.x * kPreThreads;
   const int cnt = min(kPreThreads, n - i0);
@@ -122,7 +123,7 @@ preprocess_kernel(PreParams p, int n, const float *__restrict__ means,
 
   const int t = threadIdx.x;
   const int i = i0 + t;
-  uint32_t my_touched[kMaxEyes] = {0u, 0u};
+  if (blockIdx.x == 0 && t == 0) depth_count[0] = (uint32_t)(p.n_eyes * n);
   if (i < n) {
     const float mx = s_mean[3 * t], my = s_mean[3 * t + 1], mz = s_mean[3 * t + 2];
     // activation shared by the eyes
@@ -159,6 +160,7 @@ preprocess_kernel(PreParams p, int n, const float *__restrict__ means,
       const CamParams &c = p.cam[e];
       float *o = rec + ((size_t)e * n + i) * kRec;
       ushort4 rc = make_ushort4(0, 0, 0, 0);
+      uint32_t n_touched = 0;
       float4 o0 = make_float4(0.f, 0.f, 0.f, 0.f), o1 = o0, o2 = o0;
       const float tx = fa(fa(fa(fm(c.R[0], mx), fm(c.R[1], my)), fm(c.R[2], mz)), c.t[0]);
       const float ty = fa(fa(fa(fm(c.R[3], mx), fm(c.R[4], my)), fm(c.R[5], mz)), c.t[1]);
@@ -209,7 +211,7 @@ preprocess_kernel(PreParams p, int n, const float *__restrict__ means,
           vis = x0 < x1 && y0 < y1;
           if (vis) {
             rc = make_ushort4(x0, y0, x1, y1);
-            my_touched[e] = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
+            n_touched = static_cast<uint32_t>((x1 - x0) * (y1 - y0));
           }
         }
       }
@@ -236,24 +238,9 @@ preprocess_kernel(PreParams p, int n, const float *__restrict__ means,
       o4[1] = o1;
       o4[2] = o2;
       rect[(size_t)e * n + i] = rc;
+      touched[(size_t)e * n + i] = n_touched;
+      dkeys[(size_t)e * n + i] = vis ? __float_as_uint(tz) : 0xffffffffu;
     }
-    touched[i] = my_touched[0] + my_touched[1];
-  }
-  // block totals per eye (for the offsets of emit_keys and the per-eye statistics)
-  const int lane = t & 31, warp = t >> 5;
-#pragma unroll
-  for (int e = 0; e < kMaxEyes; ++e) {
-    uint32_t v = my_touched[e];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) s_warp[warp][e] = v;
-  }
-  __syncthreads();
-  if (t < kMaxEyes) {
-    uint32_t v = 0;
-#pragma unroll
-    for (int w = 0; w < kPreThreads / 32; ++w) v += s_warp[w][t];
-    block_sums[2 * blockIdx.x + t] = v;
   }
 }
 
@@ -262,30 +249,30 @@ preprocess_kernel(PreParams p, int n, const float *__restrict__ means,
 cudaError_t launch_preprocess(const PreParams &p, int n, int sh_degree, const float *means,
                               const float *log_scales, const float *quats,
                               const float *opacity_logits, const float *sh, float *rec,
-                              ushort4 *rect, uint32_t *touched, uint32_t *block_sums,
-                              cudaStream_t s) {
+                              ushort4 *rect, uint32_t *touched, uint32_t *dkeys,
+                              uint32_t *depth_count, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
   const int blocks = (n + kPreThreads - 1) / kPreThreads;
   switch (sh_degree) {
     case 0:
       preprocess_kernel<1><<<blocks, kPreThreads, 0, s>>>(p, n, means, log_scales, quats,
                                                           opacity_logits, sh, rec, rect, touched,
-                                                          block_sums);
+                                                          dkeys, depth_count);
       break;
     case 1:
       preprocess_kernel<4><<<blocks, kPreThreads, 0, s>>>(p, n, means, log_scales, quats,
                                                           opacity_logits, sh, rec, rect, touched,
-                                                          block_sums);
+                                                          dkeys, depth_count);
       break;
     case 2:
       preprocess_kernel<9><<<blocks, kPreThreads, 0, s>>>(p, n, means, log_scales, quats,
                                                           opacity_logits, sh, rec, rect, touched,
-                                                          block_sums);
+                                                          dkeys, depth_count);
       break;
     default:
       preprocess_kernel<16><<<blocks, kPreThreads, 0, s>>>(p, n, means, log_scales, quats,
                                                            opacity_logits, sh, rec, rect,
-                                                           touched, block_sums);
+                                                           touched, dkeys, depth_count);
       break;
   }
   return cudaGetLastError();

@@ -1,20 +1,23 @@
-// sort.cu -- stable LSD radix sort of (64-bit key, 32-bit value) pairs: the per-tile
-// depth sort of 3DGS (Sec. 2.3, "Sorting"), run on the (tile << 32 | depth bits) keys so
-// that one global sort orders every tile's Gaussians front to back.
+// sort.cu -- stable LSD radix sort of (key, 32-bit value) pairs, the depth sort of 3DGS
+// (Sec. 2.3, "Sorting").  The renderer uses it twice per frame: once on the Gaussians by
+// depth (32-bit keys) and once on the depth-ordered instances by tile index (16-bit or
+// narrower keys); a stable sort by tile of depth-ordered instances is the order of the
+// (tile << 32 | depth) keys.  The public a3fr_sort_pairs sorts 64-bit keys directly.
 //
 // Algorithm: onesweep (Adinets & Merrill, "Onesweep: A Faster Least Significant Digit
-// Radix Sort for GPUs", 2022).  One histogram kernel reads the keys once and counts all
-// 8-bit digits of all passes; then each pass is ONE kernel that
+// Radix Sort for GPUs", 2022).  A histogram kernel (or the producer of the keys) counts
+// the digits of all passes at once; then each pass is ONE kernel that
 //   1. takes a partition index from an atomic counter (so partitions start in order),
 //   2. ranks its keys stably inside the CTA with warp-level multisplit
 //      (__match_any_sync + per-warp digit counters),
 //   3. publishes its per-digit counts and resolves the exclusive prefix of every digit by
 //      decoupled look-back over earlier partitions (flag + 30-bit count in one word),
-//   4. stages the keys in shared memory in digit order and writes them out in runs.
+//   4. stages the pairs in shared memory in digit order and writes them out in runs.
 // Every look-back wait is bounded: after kSpinLimit polls the CTA records
-// kStatusTimeout in the status word and continues, so a scheduling anomaly can corrupt
-// an output but never hang the GPU.  Partitions beyond the device-resident count exit at
-// once, so the grid can be sized for the capacity without a host synchronisation.
+// kStatusTimeout in the status word and carries on (its writes stay in bounds), so a
+// scheduling anomaly can corrupt a result but never hang the GPU.  Partitions beyond the
+// device-resident count exit at once, so grids are sized for a capacity without a host
+// synchronisation.
 #include "common.cuh"
 
 namespace a3fr {
@@ -22,20 +25,15 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-constexpr int kKPT = 12;
-constexpr int kPart = kThreads * kKPT;            // keys per partition
 constexpr int kRadix = 256;
-constexpr int kMaxPasses = 8;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1u;
 constexpr uint32_t kSpinLimit = 1u << 20;
 
-// Workspace: hist[kMaxPasses][256] | counters[kMaxPasses] (+pad) | lookback[passes][parts][256]
-constexpr size_t kHistBytes = sizeof(uint32_t) * kMaxPasses * kRadix;
-constexpr size_t kCounterBytes = 256;
-
-size_t n_parts(size_t n) { return (n + kPart - 1) / kPart; }
+template <typename K> struct Part;
+template <> struct Part<uint64_t> { static constexpr int kKPT = 12; };
+template <> struct Part<uint32_t> { static constexpr int kKPT = 16; };
 
 __device__ __forceinline__ void st_relaxed(uint32_t *p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -64,11 +62,12 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_tmp)
   return before + incl - v;
 }
 
+template <typename K>
 __global__ void __launch_bounds__(kThreads)
-histogram_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__ d_count,
-                 int passes, uint32_t *__restrict__ hist) {
-  __shared__ uint32_t s_hist[kMaxPasses][kRadix];
-  for (int i = threadIdx.x; i < kMaxPasses * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
+histogram_kernel(const K *__restrict__ keys, const uint32_t *__restrict__ d_count, SortPlan plan,
+                 uint32_t *__restrict__ hist) {
+  __shared__ uint32_t s_hist[kMaxSortPasses][kRadix];
+  for (int i = threadIdx.x; i < kMaxSortPasses * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
   const uint32_t n = *d_count;
   const int lane = threadIdx.x & 31;
@@ -76,33 +75,35 @@ histogram_kernel(const uint64_t *__restrict__ keys, const uint32_t *__restrict__
   for (uint32_t base = blockIdx.x * kThreads; base < n; base += stride) {
     const uint32_t i = base + threadIdx.x;
     const bool valid = i < n;
-    const uint64_t k = valid ? keys[i] : 0ull;
+    const K k = valid ? keys[i] : K(0);
     const unsigned active = __ballot_sync(0xffffffffu, valid);
-    for (int p = 0; p < passes; ++p) {
-      const uint32_t d = (uint32_t)(k >> (8 * p)) & 0xffu;
+    for (int p = 0; p < plan.passes; ++p) {
+      const uint32_t d = (uint32_t)(k >> plan.shift[p]) & plan.mask;
       if (valid) {
-        // one shared-memory atomic per distinct digit of the warp
         const unsigned peers = __match_any_sync(active, d);
         if (lane == 31 - __clz(peers)) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
       }
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadix; i += kThreads) {
+  for (int i = threadIdx.x; i < plan.passes * kRadix; i += kThreads) {
     const uint32_t v = (&s_hist[0][0])[i];
     if (v) atomicAdd(hist + i, v);
   }
 }
 
+template <typename K>
 __global__ void __launch_bounds__(kThreads, 3)
-onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                uint64_t *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
+                K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                 const uint32_t *__restrict__ d_count, const uint32_t *__restrict__ hist,
                 uint32_t *__restrict__ part_counter, uint32_t *__restrict__ lookback, int shift,
-                uint32_t *__restrict__ status) {
+                uint32_t mask, uint32_t *__restrict__ status) {
+  constexpr int KPT = Part<K>::kKPT;
+  constexpr int PART = kThreads * KPT;
   extern __shared__ __align__(16) unsigned char s_dyn[];
-  uint64_t *s_keys = reinterpret_cast<uint64_t *>(s_dyn);
-  uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_dyn + sizeof(uint64_t) * kPart);
+  K *s_keys = reinterpret_cast<K *>(s_dyn);
+  uint32_t *s_vals = reinterpret_cast<uint32_t *>(s_dyn + sizeof(K) * PART);
   __shared__ uint32_t s_whist[kWarps][kRadix];
   __shared__ uint32_t s_local_excl[kRadix];
   __shared__ uint32_t s_gbase[kRadix];
@@ -115,30 +116,28 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
   __syncthreads();
   const uint32_t part = s_part;
   const uint32_t n = *d_count;
-  const uint32_t base = part * kPart;
+  const uint32_t base = part * PART;
   if (base >= n) return;
 
-  // load: warp w owns keys [base + w*32*kKPT, ...), item k of lane l at k*32 + l
-  uint64_t key[kKPT];
-  uint32_t val[kKPT];
-  uint32_t dr[kKPT];   // digit (9 bits, 256 = invalid) << 16 | rank in warp
-  const uint32_t wbase = base + warp * 32 * kKPT + lane;
+  // load: warp w owns [base + w*32*KPT, ...), item k of lane l at k*32 + l
+  K key[KPT];
+  uint32_t val[KPT];
+  uint32_t dr[KPT];   // digit (9 bits, 256 = invalid) << 16 | rank in warp
+  const uint32_t wbase = base + warp * 32 * KPT + lane;
 #pragma unroll
-  for (int k = 0; k < kKPT; ++k) {
+  for (int k = 0; k < KPT; ++k) {
     const uint32_t i = wbase + k * 32;
     const bool valid = i < n;
-    key[k] = valid ? keys_in[i] : 0ull;
-    val[k] = valid ? vals_in[i] : 0u;
-    dr[k] = valid ? ((uint32_t)(key[k] >> shift) & 0xffu) : 256u;
+    key[k] = valid ? keys_in[i] : K(0);
+    val[k] = valid ? (vals_in ? vals_in[i] : i) : 0u;
+    dr[k] = valid ? ((uint32_t)(key[k] >> shift) & mask) : 256u;
   }
-  // warp-level multisplit ranking, in original order
   const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
-  for (int k = 0; k < kKPT; ++k) {
+  for (int k = 0; k < KPT; ++k) {
     const uint32_t d = dr[k];
     const unsigned peers = __match_any_sync(0xffffffffu, d);
-    uint32_t rank = 0;
-    uint32_t cnt = 0;
+    uint32_t rank = 0, cnt = 0;
     if (d < 256u) {
       cnt = s_whist[warp][d];
       rank = cnt + __popc(peers & lt_mask);
@@ -150,7 +149,7 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
   }
   __syncthreads();
 
-  // per digit (thread t owns digit t): exclusive offsets across warps, CTA total
+  // thread t owns digit t: exclusive offsets across warps and the CTA total
   const uint32_t d = t;
   uint32_t total = 0;
 #pragma unroll
@@ -187,9 +186,8 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
   s_gbase[d] = global_excl + excl - local_excl;
   __syncthreads();
 
-  // scatter into shared memory in digit order
 #pragma unroll
-  for (int k = 0; k < kKPT; ++k) {
+  for (int k = 0; k < KPT; ++k) {
     const uint32_t dk = dr[k] >> 16;
     if (dk < 256u) {
       const uint32_t pos = s_local_excl[dk] + s_whist[warp][dk] + (dr[k] & 0xffffu);
@@ -198,10 +196,10 @@ onesweep_kernel(const uint64_t *__restrict__ keys_in, const uint32_t *__restrict
     }
   }
   __syncthreads();
-  const uint32_t n_valid = min((uint32_t)kPart, n - base);
+  const uint32_t n_valid = min((uint32_t)PART, n - base);
   for (uint32_t i = t; i < n_valid; i += kThreads) {
-    const uint64_t k = s_keys[i];
-    const uint32_t o = s_gbase[(uint32_t)(k >> shift) & 0xffu] + i;
+    const K k = s_keys[i];
+    const uint32_t o = s_gbase[(uint32_t)(k >> shift) & mask] + i;
     if (o < n) {   // always true unless a look-back wait gave up (status already set)
       keys_out[o] = k;
       vals_out[o] = s_vals[i];
@@ -216,10 +214,96 @@ int sm_count() {
   return sms;
 }
 
+template <typename K>
+cudaError_t set_smem_attr() {
+  // per device: the attribute lives in each device's context
+  constexpr int kMaxDev = 64;
+  static bool done[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 0 && dev < kMaxDev && done[dev]) return cudaSuccess;
+  constexpr int PART = kThreads * Part<K>::kKPT;
+  e = cudaFuncSetAttribute(onesweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)((sizeof(K) + sizeof(uint32_t)) * PART));
+  if (e == cudaSuccess && dev >= 0 && dev < kMaxDev) done[dev] = true;
+  return e;
+}
+
 }  // namespace
 
+SortPlan sort_plan(int key_bits, int digit_bits_max) {
+  SortPlan p{};
+  if (key_bits < 1) key_bits = 1;
+  p.passes = (key_bits + digit_bits_max - 1) / digit_bits_max;
+  const int db = (key_bits + p.passes - 1) / p.passes;
+  p.mask = (1u << db) - 1u;
+  for (int i = 0; i < p.passes; ++i) p.shift[i] = i * db;
+  return p;
+}
+
+size_t onesweep_part_size(bool wide_keys) {
+  return (size_t)kThreads * (wide_keys ? Part<uint64_t>::kKPT : Part<uint32_t>::kKPT);
+}
+
+size_t onesweep_lookback_bytes(size_t capacity, int passes, bool wide_keys) {
+  const size_t part = onesweep_part_size(wide_keys);
+  return sizeof(uint32_t) * kRadix * (size_t)passes * ((capacity + part - 1) / part);
+}
+
+template <typename K>
+cudaError_t launch_histogram(const K *keys, const uint32_t *d_count, size_t capacity,
+                             const SortPlan &plan, uint32_t *hist, cudaStream_t s) {
+  const int sms = sm_count();
+  const size_t hb = (capacity + kThreads * 16 - 1) / (kThreads * 16);
+  const int blocks = (int)(hb < (size_t)sms * 4 ? (hb > 0 ? hb : 1) : (size_t)sms * 4);
+  histogram_kernel<K><<<blocks, kThreads, 0, s>>>(keys, d_count, plan, hist);
+  return cudaGetLastError();
+}
+
+template <typename K>
+cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
+                            bool implicit_vals, const uint32_t *d_count, size_t capacity,
+                            const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
+                            uint32_t *lookback, uint32_t *status, bool *result_in_alt,
+                            cudaStream_t s) {
+  *result_in_alt = false;
+  if (capacity == 0) return cudaSuccess;
+  cudaError_t e = set_smem_attr<K>();
+  if (e != cudaSuccess) return e;
+  constexpr int PART = kThreads * Part<K>::kKPT;
+  const size_t parts = (capacity + PART - 1) / PART;
+  const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * PART;
+  K *kin = keys, *kout = keys_alt;
+  uint32_t *vin = vals, *vout = vals_alt;
+  for (int p = 0; p < plan.passes; ++p) {
+    // the first pass may take the values to be the input positions (vals unread)
+    const uint32_t *vsrc = (p == 0 && implicit_vals) ? nullptr : vin;
+    onesweep_kernel<K><<<(unsigned)parts, kThreads, dyn, s>>>(
+        kin, vsrc, kout, vout, d_count, hist + p * kRadix, counters + p,
+        lookback + (size_t)kRadix * parts * p, plan.shift[p], plan.mask, status);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    K *tk = kin; kin = kout; kout = tk;
+    uint32_t *tv = vin; vin = vout; vout = tv;
+  }
+  *result_in_alt = (plan.passes % 2) == 1;
+  return cudaSuccess;
+}
+
+template cudaError_t launch_histogram<uint32_t>(const uint32_t *, const uint32_t *, size_t,
+                                                const SortPlan &, uint32_t *, cudaStream_t);
+template cudaError_t launch_onesweep<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *,
+                                               bool, const uint32_t *, size_t, const SortPlan &,
+                                               const uint32_t *, uint32_t *, uint32_t *,
+                                               uint32_t *, bool *, cudaStream_t);
+
+// ---- the 64-bit pair sort of the public API (8-bit digits) ----
+constexpr size_t kHistBytes = sizeof(uint32_t) * kMaxSortPasses * kRadix;
+constexpr size_t kCounterBytes = 256;
+
 size_t sort_workspace_bytes(size_t capacity) {
-  return kHistBytes + kCounterBytes + sizeof(uint32_t) * kMaxPasses * kRadix * n_parts(capacity);
+  return kHistBytes + kCounterBytes + onesweep_lookback_bytes(capacity, kMaxSortPasses, true);
 }
 
 cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
@@ -227,45 +311,18 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint
                         uint32_t *status, bool *result_in_alt, cudaStream_t s) {
   *result_in_alt = false;
   if (capacity == 0 || key_bits <= 0) return cudaSuccess;
-  const int passes = (key_bits + 7) / 8;
-  const size_t parts = n_parts(capacity);
+  const SortPlan plan = sort_plan(key_bits, 8);
   unsigned char *ws = static_cast<unsigned char *>(workspace);
   uint32_t *hist = reinterpret_cast<uint32_t *>(ws);
   uint32_t *counters = reinterpret_cast<uint32_t *>(ws + kHistBytes);
   uint32_t *lookback = reinterpret_cast<uint32_t *>(ws + kHistBytes + kCounterBytes);
-  const size_t lb_pass = (size_t)kRadix * parts;
   cudaError_t e = cudaMemsetAsync(
-      ws, 0, kHistBytes + kCounterBytes + sizeof(uint32_t) * lb_pass * passes, s);
+      ws, 0, kHistBytes + kCounterBytes + onesweep_lookback_bytes(capacity, plan.passes, true), s);
   if (e != cudaSuccess) return e;
-
-  static bool attr_set = false;
-  const size_t dyn = (sizeof(uint64_t) + sizeof(uint32_t)) * kPart;
-  if (!attr_set) {
-    e = cudaFuncSetAttribute(onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)dyn);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
-  const int sms = sm_count();
-  const size_t hb = (capacity + kThreads * 16 - 1) / (kThreads * 16);
-  const int hist_blocks = (int)(hb < (size_t)sms * 4 ? hb : (size_t)sms * 4);
-  histogram_kernel<<<hist_blocks > 0 ? hist_blocks : 1, kThreads, 0, s>>>(keys, d_count, passes,
-                                                                         hist);
-  e = cudaGetLastError();
+  e = launch_histogram<uint64_t>(keys, d_count, capacity, plan, hist, s);
   if (e != cudaSuccess) return e;
-  uint64_t *kin = keys, *kout = keys_alt;
-  uint32_t *vin = vals, *vout = vals_alt;
-  for (int p = 0; p < passes; ++p) {
-    onesweep_kernel<<<(unsigned)parts, kThreads, dyn, s>>>(
-        kin, vin, kout, vout, d_count, hist + p * kRadix, counters + p, lookback + lb_pass * p,
-        8 * p, status);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    uint64_t *tk = kin; kin = kout; kout = tk;
-    uint32_t *tv = vin; vin = vout; vout = tv;
-  }
-  *result_in_alt = (passes % 2) == 1;
-  return cudaSuccess;
+  return launch_onesweep<uint64_t>(keys, vals, keys_alt, vals_alt, false, d_count, capacity,
+                                   plan, hist, counters, lookback, status, result_in_alt, s);
 }
 
 }  // namespace a3fr
