@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 METRIC = "stereo foveated frame ms (p50/p99) & FPS vs full-res on same GB300; PSNR vs full"
 UNIT = "stereo frames/s"
 L2_FLUSH_BYTES = 256 << 20
-STAGES = ("preprocess", "scan", "emit", "sort", "ranges", "composite")
+STAGES = ("preprocess", "depth_sort", "tile_scan", "emit", "tile_sort", "composite")
 SMS_GB300 = 152
 FP32_LANES_PER_SM = 128
 
@@ -467,19 +467,22 @@ def roofline(w, stats, stage_ms, n_frames, eyes):
     n = w.scene.n
     K = (w.scene.sh_degree + 1) ** 2
     inst = float(stats["instances"])
-    bits = 32 + max(1, math.ceil(math.log2(eyes * ((w.cameras(0)[0].width + 15) // 16) *
-                                           ((w.cameras(0)[0].height + 15) // 16))))
-    passes = (bits + 7) // 8
     c0 = w.cameras(0)[0]
     px = eyes * c0.width * c0.height
     staged = stats["records_staged"] / max(n_frames, 1)
     evals = stats["evaluations"] / max(n_frames, 1)
+    n_ent = n * eyes
+    tiles = eyes * ((c0.width + 15) // 16) * ((c0.height + 15) // 16)
+    tile_passes = max(1, math.ceil(max(1, math.ceil(math.log2(max(tiles, 2)))) / 8))
     algo = {
-        # bytes: Gaussian parameters once, records + rects + touched per eye
-        "preprocess": ("hbm", n * (4 * (3 + 3 + 4 + 1 + 3 * K) + 4 + eyes * (48 + 8))),
-        "sort": ("hbm", inst * (8 + 24 * passes)),
-        "emit": ("hbm", n * eyes * (8 + 4) + n * 4 + inst * 12),
-        "ranges": ("hbm", inst * 8),
+        # bytes: Gaussian parameters once; records + rects + touched + depth keys per eye
+        "preprocess": ("hbm", n * 4 * (3 + 3 + 4 + 1 + 3 * K) + n_ent * (48 + 8 + 4 + 4)),
+        # 4 passes of (key, value) read + write over the (eye, Gaussian) entries
+        "depth_sort": ("hbm", n_ent * 4 * 16),
+        "tile_scan": ("hbm", tiles * 16),
+        # entries, counts and rectangles read; (tile, index) written per instance
+        "emit": ("hbm", n_ent * 16 + inst * 8),
+        "tile_sort": ("hbm", inst * 16 * tile_passes),
         # flops: 14 per (pixel, Gaussian) evaluation (offset, quadratic form, alpha)
         "composite": ("alu", evals * 14.0),
     }

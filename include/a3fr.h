@@ -127,11 +127,11 @@ int a3fr_get_stats(a3fr_scene *scene, a3fr_stats *stats, int reset);
 int a3fr_set_keep_aux(a3fr_scene *scene, int keep);
 
 /* Stages of a render timed by a3fr_set_stage_timing, in launch order. */
-#define A3FR_STAGE_PREPROCESS 0  /* projection, EWA, SH colour, tile rectangles */
-#define A3FR_STAGE_SCAN 1        /* instance offsets */
-#define A3FR_STAGE_EMIT 2        /* (tile << 32 | depth) keys */
-#define A3FR_STAGE_SORT 3        /* onesweep radix sort */
-#define A3FR_STAGE_RANGES 4      /* per-tile ranges */
+#define A3FR_STAGE_PREPROCESS 0  /* projection, EWA, SH colour, tile rectangles, histograms */
+#define A3FR_STAGE_DEPTH_SORT 1  /* onesweep sort of the (eye, Gaussian) entries by depth */
+#define A3FR_STAGE_TILE_SCAN 2   /* per-tile instance counts -> tile ranges */
+#define A3FR_STAGE_EMIT 3        /* (tile, Gaussian) instances in depth order */
+#define A3FR_STAGE_TILE_SORT 4   /* stable onesweep sort of the instances by tile */
 #define A3FR_STAGE_COMPOSITE 5   /* level map + front-to-back blending + inheritance */
 #define A3FR_N_STAGES 6
 

@@ -59,6 +59,7 @@ struct a3fr_scene {
   uint32_t *dkeys[2] = {nullptr, nullptr};   // depth-sort keys (ping-pong)
   uint32_t *dvals[2] = {nullptr, nullptr};   // depth-sorted entries e * n + i
   uint2 *ranges = nullptr;
+  uint32_t *tile_partials = nullptr;         // per-CTA 2-D difference grids of tile_count
   uint8_t *levels = nullptr;
   float *t_final = nullptr;
   uint32_t *n_contrib = nullptr;
@@ -117,13 +118,15 @@ struct FrameLayout {
   size_t tile_hist = 64 + 8192 + 64;
   size_t tile_ctr = 64 + 8192 + 64 + 8192;
   size_t emit_lb = 64 + 8192 + 64 + 8192 + 64;
-  size_t depth_lb = 0, tile_lb = 0, total = 0;
+  size_t tile_diff = 0, depth_lb = 0, tile_lb = 0, total = 0;
 };
 
-FrameLayout frame_layout(size_t entries, size_t capacity, int tile_passes) {
+FrameLayout frame_layout(size_t entries, size_t capacity, int tile_passes, int eyes, int tiles_x,
+                         int tiles_y) {
   FrameLayout L;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  L.depth_lb = up(L.emit_lb + emit_lookback_bytes((int)entries));
+  L.tile_diff = up(L.emit_lb + emit_lookback_bytes((int)entries));
+  L.depth_lb = up(L.tile_diff + sizeof(uint32_t) * (size_t)eyes * (tiles_x + 1) * (tiles_y + 1));
   L.tile_lb = up(L.depth_lb + onesweep_lookback_bytes(entries, kDepthPasses, false));
   L.total = up(L.tile_lb + onesweep_lookback_bytes(capacity, tile_passes, false));
   return L;
@@ -138,6 +141,7 @@ void free_frame_buffers(a3fr_scene *s) {
     dfree(s->dvals[b]);
   }
   dfree(s->ranges);
+  dfree(s->tile_partials);
   dfree(s->levels);
   dfree(s->t_final);
   dfree(s->n_contrib);
@@ -155,7 +159,7 @@ void free_instance_buffers(a3fr_scene *s) {
 int ensure_frame_ws(a3fr_scene *s) {
   const size_t entries = (size_t)s->alloc_eyes * (size_t)(s->desc.n > 0 ? s->desc.n : 1);
   const int tile_passes = sort_plan(tile_bits_for(s->alloc_eyes * s->n_tiles), 8).passes;
-  const FrameLayout L = frame_layout(entries, s->capacity, tile_passes);
+  const FrameLayout L = frame_layout(entries, s->capacity, tile_passes, s->alloc_eyes, s->TX, s->TY);
   if (s->frame_ws && s->frame_ws_bytes >= L.total) return A3FR_OK;
   if (s->frame_ws) {
     A3FR_CHECK(cudaDeviceSynchronize());
@@ -188,6 +192,13 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
   free_frame_buffers(s);
   const int n = s->desc.n;
   const int tile = s->desc.tile;
+  {
+    int dev = 0, max_optin = 0;
+    A3FR_CHECK(cudaGetDevice(&dev));
+    A3FR_CHECK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
+    if (tile_scan_smem_bytes(eyes, tx, ty) + 9216 > (size_t)max_optin) return A3FR_ERR_INVALID_ARG;
+  }
   s->W = W;
   s->H = H;
   s->TX = (W + tile - 1) / tile;
@@ -202,6 +213,8 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
     A3FR_CHECK(cudaMalloc(&s->dvals[b], sizeof(uint32_t) * nn));
   }
   A3FR_CHECK(cudaMalloc(&s->ranges, sizeof(uint2) * (size_t)s->n_tiles * eyes));
+  A3FR_CHECK(cudaMalloc(&s->tile_partials, sizeof(uint32_t) * (size_t)tile_count_blocks() *
+                                               tile_grid_cells(eyes, s->TX, s->TY)));
   A3FR_CHECK(cudaMalloc(&s->levels, (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->t_final, sizeof(float) * (size_t)W * H * eyes));
   A3FR_CHECK(cudaMalloc(&s->n_contrib, sizeof(uint32_t) * (size_t)W * H * eyes));
@@ -294,7 +307,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
   const SortPlan depth_plan = sort_plan(32, 8);
   const SortPlan tile_plan = sort_plan(tile_bits_for(n_ranges), 8);
   FrameLayout L = frame_layout((size_t)(n_entries > 0 ? n_entries : eyes), s->capacity,
-                               tile_plan.passes);
+                               tile_plan.passes, eyes, s->TX, s->TY);
   unsigned char *ws = static_cast<unsigned char *>(s->frame_ws);
   uint32_t *counts = s->counts;
   uint32_t *depth_hist = reinterpret_cast<uint32_t *>(ws + L.depth_hist);
@@ -302,6 +315,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
   uint32_t *tile_hist = reinterpret_cast<uint32_t *>(ws + L.tile_hist);
   uint32_t *tile_ctr = reinterpret_cast<uint32_t *>(ws + L.tile_ctr);
   unsigned long long *emit_lb = reinterpret_cast<unsigned long long *>(ws + L.emit_lb);
+  uint32_t *tile_diff = reinterpret_cast<uint32_t *>(ws + L.tile_diff);
   uint32_t *depth_lb = reinterpret_cast<uint32_t *>(ws + L.depth_lb);
   uint32_t *tile_lb = reinterpret_cast<uint32_t *>(ws + L.tile_lb);
 
@@ -323,56 +337,78 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
     ++launches;
   }
   // depth sort of the (eye, Gaussian) entries: 4 passes, result back in dkeys[0]/dvals[0]
-  A3FR_CHECK(mark(s, A3FR_STAGE_SCAN, stream));
+  A3FR_CHECK(mark(s, A3FR_STAGE_DEPTH_SORT, stream));
   if (n > 0) {
-    A3FR_CHECK(launch_histogram<uint32_t>(s->dkeys[0], counts + 4, (size_t)n_entries,
-                                          depth_plan, depth_hist, stream));
+    A3FR_CHECK(launch_histogram<uint32_t>(s->dkeys[0], counts + 4, (size_t)n_entries, depth_plan,
+                                          depth_hist, stream));
+    ++launches;
     bool in_alt = false;
     A3FR_CHECK(launch_onesweep<uint32_t>(s->dkeys[0], s->dvals[0], s->dkeys[1], s->dvals[1], true,
                                          counts + 4, (size_t)n_entries, depth_plan, depth_hist,
                                          depth_ctr, depth_lb, s->status, &in_alt, stream));
-    launches += 1 + depth_plan.passes;
+    launches += depth_plan.passes;
   }
   const uint32_t *entries = s->dvals[depth_plan.passes % 2];
-  EmitParams ep{};
-  ep.n = n;
-  ep.n_entries = n_entries;
-  ep.n_tiles = s->n_tiles;
-  ep.tiles_x = s->TX;
-  ep.tile_plan = tile_plan;
-  uint32_t *emit_ctr = counts + 6;
+  // per-tile counts -> ranges, tile-sort histograms, totals
+  A3FR_CHECK(mark(s, A3FR_STAGE_TILE_SCAN, stream));
+  TileScanParams tp{};
+  tp.n_eyes = eyes;
+  tp.n = n;
+  tp.tiles_x = s->TX;
+  tp.tiles_y = s->TY;
+  tp.n_tiles = s->n_tiles;
+  tp.capacity = (uint32_t)s->capacity;
+  tp.tile_plan = tile_plan;
+  if (n > 0) {
+    A3FR_CHECK(launch_tile_count(tp, s->rect, s->tile_partials, tile_diff, stream));
+    launches += 2;
+  }
+  A3FR_CHECK(launch_tile_scan(tp, tile_diff, s->ranges, tile_hist, counts, s->status, stream));
+  ++launches;
   if (s->auto_capacity && s->capacity == 0 && n > 0) {
-    // first render: measure the instance count once, then size the instance buffers
-    ep.capacity = 0;
-    A3FR_CHECK(launch_emit(ep, entries, s->touched, s->rect, nullptr, nullptr, emit_lb, emit_ctr,
-                           counts, s->status, tile_hist, stream));
-    ++launches;
+    // first render: read the instance count once, then size the instance buffers
     uint32_t cnt[8];
     A3FR_CHECK(cudaMemcpyAsync(cnt, counts, sizeof cnt, cudaMemcpyDeviceToHost, stream));
     A3FR_CHECK(cudaStreamSynchronize(stream));
-    A3FR_CHECK(cudaMemsetAsync(s->status, 0, sizeof(uint32_t), stream));
     size_t want = 2 * (size_t)cnt[3] + (1u << 16);
     if (want >= (1u << 30)) want = (1u << 30) - 1;
+    // keep this frame's workspace: the new one must hold the tile look-back of the capacity
+    void *old_ws = s->frame_ws;
+    s->frame_ws = nullptr;
+    s->frame_ws_bytes = 0;
     rc = alloc_instances(s, want);
-    if (rc != A3FR_OK) return rc;
-    L = frame_layout((size_t)n_entries, s->capacity, tile_plan.passes);
+    if (rc != A3FR_OK) {
+      cudaFree(old_ws);
+      return rc;
+    }
+    L = frame_layout((size_t)n_entries, s->capacity, tile_plan.passes, eyes, s->TX, s->TY);
     ws = static_cast<unsigned char *>(s->frame_ws);
+    A3FR_CHECK(cudaMemcpyAsync(ws, old_ws, L.tile_lb, cudaMemcpyDeviceToDevice, stream));
+    A3FR_CHECK(cudaStreamSynchronize(stream));
+    cudaFree(old_ws);
     counts = s->counts;
     tile_hist = reinterpret_cast<uint32_t *>(ws + L.tile_hist);
     tile_ctr = reinterpret_cast<uint32_t *>(ws + L.tile_ctr);
     emit_lb = reinterpret_cast<unsigned long long *>(ws + L.emit_lb);
     tile_lb = reinterpret_cast<uint32_t *>(ws + L.tile_lb);
-    emit_ctr = counts + 6;
-    A3FR_CHECK(cudaMemsetAsync(s->frame_ws, 0, L.total, stream));
+    cnt[0] = cnt[3] < s->capacity ? cnt[3] : (uint32_t)s->capacity;
+    A3FR_CHECK(cudaMemcpyAsync(counts, cnt, sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+    A3FR_CHECK(cudaMemsetAsync(s->status, 0, sizeof(uint32_t), stream));
+    A3FR_CHECK(cudaStreamSynchronize(stream));
   }
   A3FR_CHECK(mark(s, A3FR_STAGE_EMIT, stream));
+  EmitParams ep{};
+  ep.n = n;
+  ep.n_entries = n_entries;
+  ep.n_tiles = s->n_tiles;
+  ep.tiles_x = s->TX;
   ep.capacity = (uint32_t)s->capacity;
   if (n > 0 && s->capacity > 0) {
     A3FR_CHECK(launch_emit(ep, entries, s->touched, s->rect, s->tkeys[0], s->tvals[0], emit_lb,
-                           emit_ctr, counts, s->status, tile_hist, stream));
+                           counts + 6, s->status, stream));
     ++launches;
   }
-  A3FR_CHECK(mark(s, A3FR_STAGE_SORT, stream));
+  A3FR_CHECK(mark(s, A3FR_STAGE_TILE_SORT, stream));
   bool in_alt = false;
   if (n > 0 && s->capacity > 0) {
     A3FR_CHECK(launch_onesweep<uint32_t>(s->tkeys[0], s->tvals[0], s->tkeys[1], s->tvals[1], false,
@@ -382,10 +418,6 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
   }
   s->sorted_in_alt = in_alt;
   const int b = in_alt ? 1 : 0;
-  A3FR_CHECK(mark(s, A3FR_STAGE_RANGES, stream));
-  A3FR_CHECK(launch_tile_ranges(s->tkeys[b], counts, n > 0 ? s->capacity : 0, s->ranges,
-                                n_ranges, stream));
-  if (n > 0 && s->capacity > 0) ++launches;
 
   CompositeParams cp{};
   cp.n_eyes = eyes;
@@ -413,8 +445,8 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
     gaze = s->gaze_dev;   // not read when full
   }
   A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
-  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, s->tvals[b], gaze, out, s->levels,
-                              s->keep_aux ? s->t_final : nullptr,
+  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, counts, s->tvals[b], gaze, out,
+                              s->levels, s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
   ++launches;
   A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));

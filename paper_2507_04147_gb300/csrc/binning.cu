@@ -8,15 +8,18 @@
 // to back with ties in index order -- exactly the order of the (tile << 32 | depth bits)
 // keys sorted stably.
 //
-// emit (one kernel):
-//   * instance offsets by a single-pass scan with decoupled look-back over dynamically
-//     numbered blocks (64-bit flag|value words; bounded waits that set a status bit);
-//   * warp-cooperative expansion: the 32 entries of a warp own a contiguous run of the
-//     output, which the 32 lanes fill together (coalesced stores, no imbalance from large
-//     Gaussians);
-//   * the digit histograms of the tile sort are accumulated on the fly (shared-memory
-//     counters aggregated per warp with __match_any_sync), so that sort needs no
-//     histogram pass.
+// tile_count + tile_scan give every tile's instance count without enumerating instances:
+// each tile rectangle adds +1/-1/-1/+1 at its corners in a 2-D difference grid (per CTA in
+// shared memory, partial grids summed without atomics), whose 2-D prefix sum is the count.
+// The exclusive scan of the counts over tiles is exactly where the stable sort by tile puts
+// each tile's run, i.e. the tile ranges; the digit histograms of that sort follow from the
+// same prefix sums.  So neither a ranges pass nor a histogram pass is needed.
+//
+// emit: instance offsets by a single-pass scan with decoupled look-back over dynamically
+// numbered blocks (64-bit flag|value words; a warp reads 32 predecessors per step; bounded
+// waits that set a status bit).  Each thread then generates its own entry's instances into
+// a shared-memory chunk of the block's contiguous output run, and the block stores the
+// chunk with coalesced writes.
 #include "common.cuh"
 
 namespace a3fr {
@@ -27,7 +30,7 @@ constexpr int kEmitWarps = kEmitThreads / 32;
 constexpr unsigned long long kEFlagAgg = 1ull << 62;
 constexpr unsigned long long kEFlagPrefix = 2ull << 62;
 constexpr unsigned long long kEValMask = (1ull << 62) - 1ull;
-constexpr uint32_t kSpinLimit = 1u << 20;
+constexpr uint32_t kSpinLimit = 1u << 16;   // with back-off: well over a second
 
 __device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v) {
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
@@ -38,145 +41,268 @@ __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long l
   return v;
 }
 
+constexpr int kChunk = 2048;   // instances staged per chunk of the block's run
+
 __global__ void __launch_bounds__(kEmitThreads)
 emit_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
             const ushort4 *__restrict__ rect, uint32_t *__restrict__ tile_keys,
             uint32_t *__restrict__ vals, unsigned long long *__restrict__ lookback,
-            uint32_t *__restrict__ block_counter, uint32_t *__restrict__ counts,
-            uint32_t *__restrict__ status, uint32_t *__restrict__ tile_hist) {
+            uint32_t *__restrict__ block_counter, uint32_t *__restrict__ status) {
   __shared__ uint32_t s_blk;
   __shared__ uint32_t s_warp_total[kEmitWarps];
   __shared__ unsigned long long s_prefix;
-  __shared__ uint32_t s_hist[kMaxSortPasses][256];
-  __shared__ uint32_t s_excl[kEmitThreads];   // exclusive offset within the warp
-  __shared__ uint32_t s_tile0[kEmitThreads];  // first tile index of the rectangle
-  __shared__ uint32_t s_width[kEmitThreads];  // rectangle width in tiles
-  __shared__ uint32_t s_gid[kEmitThreads];    // Gaussian index
+  __shared__ uint32_t s_block_total;
+  __shared__ uint32_t s_tiles[kChunk];
+  __shared__ uint32_t s_gids[kChunk];
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (t == 0) s_blk = atomicAdd(block_counter, 1u);
-  for (int i = t; i < p.tile_plan.passes * 256; i += kEmitThreads) (&s_hist[0][0])[i] = 0;
   __syncthreads();
   const uint32_t blk = s_blk;
   const uint32_t j = blk * kEmitThreads + t;
 
-  uint32_t cnt = 0, eye = 0;
+  uint32_t cnt = 0, tile0 = 0, width = 1, gid = 0;
   if (j < (uint32_t)p.n_entries) {
     const uint32_t v = entries[j];          // e * n + i
     cnt = touched[v];
-    eye = v >= (uint32_t)p.n ? 1u : 0u;
-    const uint32_t gi = v - eye * (uint32_t)p.n;
     if (cnt) {
+      const uint32_t eye = v >= (uint32_t)p.n ? 1u : 0u;
+      gid = v - eye * (uint32_t)p.n;
       const ushort4 rc = rect[v];
-      s_tile0[t] = eye * (uint32_t)p.n_tiles + (uint32_t)rc.y * (uint32_t)p.tiles_x + rc.x;
-      s_width[t] = (uint32_t)(rc.z - rc.x);
-      s_gid[t] = gi;
+      tile0 = eye * (uint32_t)p.n_tiles + (uint32_t)rc.y * (uint32_t)p.tiles_x + rc.x;
+      width = (uint32_t)(rc.z - rc.x);
     }
   }
-  // warp and block scans of the instance counts
+  // block scan of the instance counts
   uint32_t incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
     if (lane >= o) incl += n;
   }
-  s_excl[t] = incl - cnt;
   if (lane == 31) s_warp_total[warp] = incl;
-  // per-eye totals
-  uint32_t e0 = eye ? 0u : cnt, e1 = eye ? cnt : 0u;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    e0 += __shfl_xor_sync(0xffffffffu, e0, o);
-    e1 += __shfl_xor_sync(0xffffffffu, e1, o);
-  }
-  if (lane == 0) {
-    if (e0) atomicAdd(&counts[1], e0);
-    if (e1) atomicAdd(&counts[2], e1);
-  }
   __syncthreads();
+  uint32_t excl = incl - cnt;
+  for (int w = 0; w < warp; ++w) excl += s_warp_total[w];
 
-  // block prefix by decoupled look-back (thread 0)
-  if (t == 0) {
+  // block prefix by decoupled look-back, warp 0: each step reads a window of the 32
+  // nearest unresolved predecessors (one per lane) and sums up to the nearest inclusive
+  // prefix; an unpublished predecessor is polled again after a back-off (bounded)
+  if (warp == 0) {
     uint32_t block_total = 0;
     for (int w = 0; w < kEmitWarps; ++w) block_total += s_warp_total[w];
     unsigned long long *mine = lookback + blk;
-    st_relaxed64(mine, (blk == 0 ? kEFlagPrefix : kEFlagAgg) | block_total);
+    if (lane == 0) st_relaxed64(mine, (blk == 0 ? kEFlagPrefix : kEFlagAgg) | block_total);
     unsigned long long prefix = 0;
     if (blk > 0) {
-      int q = (int)blk - 1;
+      int base = (int)blk - 1;
       uint32_t spins = 0;
       while (true) {
-        const unsigned long long w = ld_relaxed64(lookback + q);
+        const int q = base - lane;
+        const unsigned long long w = q >= 0 ? ld_relaxed64(lookback + q) : kEFlagPrefix;
         const unsigned long long flag = w & ~kEValMask;
-        if (flag == 0ull) {
+        const unsigned not_ready = __ballot_sync(0xffffffffu, flag == 0ull);
+        const unsigned is_prefix = __ballot_sync(0xffffffffu, flag == kEFlagPrefix);
+        const int first_prefix = is_prefix ? __ffs(is_prefix) - 1 : 32;
+        const int first_wait = not_ready ? __ffs(not_ready) - 1 : 32;
+        const int upto = first_wait < first_prefix ? first_wait : first_prefix;   // lanes < upto are AGG
+        const bool take = lane < upto || (lane == first_prefix && first_prefix < first_wait);
+        unsigned long long v = take ? (w & kEValMask) : 0ull;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        prefix += v;
+        if (first_prefix < first_wait) break;          // reached an inclusive prefix
+        base -= upto;
+        if (first_wait < 32) {   // an unpublished predecessor: back off before polling again
           if (++spins > kSpinLimit) {
-            atomicOr(status, kStatusTimeout);
+            if (lane == 0) atomicOr(status, kStatusTimeout);
             break;
           }
-          continue;
+          __nanosleep(spins < 8 ? 32u << spins : 4096u);
         }
-        prefix += w & kEValMask;
-        if (flag == kEFlagPrefix || q == 0) break;
-        --q;
       }
-      st_relaxed64(mine, kEFlagPrefix | ((prefix + block_total) & kEValMask));
+      if (lane == 0) st_relaxed64(mine, kEFlagPrefix | ((prefix + block_total) & kEValMask));
     }
-    s_prefix = prefix;
-    if (blk == gridDim.x - 1) {
-      const unsigned long long total = prefix + block_total;
-      counts[0] = (uint32_t)(total < p.capacity ? total : p.capacity);
-      counts[3] = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
-      if (total > p.capacity) atomicOr(status, kStatusCapacity);
+    if (lane == 0) {
+      s_prefix = prefix;
+      s_block_total = block_total;
     }
   }
   __syncthreads();
 
-  // warp-cooperative expansion of the warp's contiguous run of instances
-  uint32_t warp_before = 0;
-  for (int w = 0; w < warp; ++w) warp_before += s_warp_total[w];
-  const unsigned long long wbase = s_prefix + warp_before;
-  const uint32_t W = s_warp_total[warp];
-  const int wb = warp * 32;
-  for (uint32_t q0 = 0; q0 < W; q0 += 32) {
-    const uint32_t q = q0 + lane;
-    const unsigned long long off = wbase + q;
-    const bool valid = q < W && off < p.capacity;
-    const unsigned m = __ballot_sync(0xffffffffu, valid);
-    if (valid) {
-      int k = 0;
-#pragma unroll
-      for (int step = 16; step > 0; step >>= 1)
-        if (s_excl[wb + k + step] <= q) k += step;
-      const uint32_t r = q - s_excl[wb + k];
-      const uint32_t w = s_width[wb + k];
-      const uint32_t dy = r / w, dx = r - dy * w;
-      const uint32_t tile = s_tile0[wb + k] + dy * (uint32_t)p.tiles_x + dx;
-      tile_keys[off] = tile;
-      vals[off] = s_gid[wb + k];
-      for (int ps = 0; ps < p.tile_plan.passes; ++ps) {
-        const uint32_t d = (tile >> p.tile_plan.shift[ps]) & p.tile_plan.mask;
-        const unsigned peers = __match_any_sync(m, d);
-        if (lane == 31 - __clz(peers)) atomicAdd(&s_hist[ps][d], (uint32_t)__popc(peers));
+  // the block's instances occupy [prefix, prefix + block_total): stage chunks of it in
+  // shared memory (each thread writes its entry's run, row by row), store coalesced
+  const unsigned long long prefix = s_prefix;
+  const uint32_t total = s_block_total;
+  for (uint32_t c0 = 0; c0 < total; c0 += kChunk) {
+    const uint32_t c1 = min(total, c0 + kChunk);
+    if (cnt) {
+      const uint32_t r0 = excl > c0 ? 0u : c0 - excl;            // first local index in chunk
+      const uint32_t r1 = min(cnt, c1 > excl ? c1 - excl : 0u);  // one past the last
+      if (r0 < r1) {
+        uint32_t dy = r0 / width, dx = r0 - dy * width;
+        uint32_t tile = tile0 + dy * (uint32_t)p.tiles_x + dx;
+        for (uint32_t r = r0; r < r1; ++r) {
+          const uint32_t o = excl + r - c0;
+          s_tiles[o] = tile;
+          s_gids[o] = gid;
+          if (++dx == width) {
+            dx = 0;
+            tile += (uint32_t)p.tiles_x - width + 1;
+          } else {
+            ++tile;
+          }
+        }
       }
     }
-  }
-  __syncthreads();
-  for (int i = t; i < p.tile_plan.passes * 256; i += kEmitThreads) {
-    const uint32_t v = (&s_hist[0][0])[i];
-    if (v) atomicAdd(tile_hist + i, v);
+    __syncthreads();
+    for (uint32_t q = c0 + t; q < c1; q += kEmitThreads) {
+      const unsigned long long off = prefix + q;
+      if (off < p.capacity) {
+        tile_keys[off] = s_tiles[q - c0];
+        vals[off] = s_gids[q - c0];
+      }
+    }
+    __syncthreads();
   }
 }
 
-__global__ void tile_ranges_kernel(const uint32_t *__restrict__ tile_keys,
-                                   const uint32_t *__restrict__ d_count, uint2 *__restrict__ ranges,
-                                   uint32_t n_ranges) {
-  const uint32_t count = *d_count;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count;
-       i += gridDim.x * blockDim.x) {
-    const uint32_t tile = tile_keys[i];
-    if (tile >= n_ranges) continue;   // only after a failed sort (status already set)
-    if (i == 0 || tile_keys[i - 1] != tile) ranges[tile].x = i;
-    if (i == count - 1 || tile_keys[i + 1] != tile) ranges[tile].y = i + 1;
+constexpr int kCountThreads = 512;
+
+// Per CTA: the difference grid of a contiguous slice of the (eye, Gaussian) rectangles in
+// shared memory, written to partials[blockIdx.x][cells].
+__global__ void __launch_bounds__(kCountThreads)
+tile_count_kernel(TileScanParams p, const ushort4 *__restrict__ rect,
+                  uint32_t *__restrict__ partials) {
+  extern __shared__ uint32_t s_grid[];
+  const int gw = p.tiles_x + 1, gh = p.tiles_y + 1;
+  const int cells = p.n_eyes * gw * gh;
+  for (int i = threadIdx.x; i < cells; i += kCountThreads) s_grid[i] = 0;
+  __syncthreads();
+  const int entries = p.n_eyes * p.n;
+  const int per = (entries + gridDim.x - 1) / gridDim.x;
+  const int e0 = blockIdx.x * per, e1 = min(entries, e0 + per);
+  for (int v = e0 + threadIdx.x; v < e1; v += kCountThreads) {
+    const ushort4 rc = rect[v];
+    if (rc.x >= rc.z) continue;
+    const int eye = v >= p.n ? 1 : 0;
+    uint32_t *g = s_grid + eye * gw * gh;
+    atomicAdd(g + rc.y * gw + rc.x, 1u);
+    atomicAdd(g + rc.y * gw + rc.z, 0xffffffffu);
+    atomicAdd(g + rc.w * gw + rc.x, 0xffffffffu);
+    atomicAdd(g + rc.w * gw + rc.z, 1u);
+  }
+  __syncthreads();
+  uint32_t *out = partials + (size_t)blockIdx.x * cells;
+  for (int i = threadIdx.x; i < cells; i += kCountThreads) out[i] = s_grid[i];
+}
+
+__global__ void tile_reduce_kernel(const uint32_t *__restrict__ partials, int parts, int cells,
+                                   uint32_t *__restrict__ grid) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += gridDim.x * blockDim.x) {
+    uint32_t acc = 0;
+    for (int b = 0; b < parts; ++b) acc += partials[(size_t)b * cells + i];
+    grid[i] = acc;
+  }
+}
+
+// One CTA: 2-D prefix sums of the summed difference grids in shared memory (rows in
+// parallel, then columns), exclusive scan of the counts over tiles -> ranges; then the
+// digit histograms of the tile sort and the per-eye totals from the scanned ranges.
+__global__ void __launch_bounds__(1024)
+tile_scan_kernel(TileScanParams p, const uint32_t *__restrict__ diff, uint2 *__restrict__ ranges,
+                 uint32_t *__restrict__ tile_hist, uint32_t *__restrict__ counts,
+                 uint32_t *__restrict__ status) {
+  extern __shared__ uint32_t s_grid[];
+  __shared__ unsigned long long s_warp[32];
+  __shared__ unsigned long long s_carry;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int gw = p.tiles_x + 1, gh = p.tiles_y + 1;
+  const int cells = p.n_eyes * gw * gh;
+  if (t == 0) s_carry = 0;
+  for (int i = t; i < cells; i += blockDim.x) s_grid[i] = diff[i];
+  __syncthreads();
+  for (int r = t; r < p.n_eyes * gh; r += blockDim.x) {
+    uint32_t *row = s_grid + r * gw;
+    uint32_t acc = 0;
+    for (int x = 0; x < gw; ++x) { acc += row[x]; row[x] = acc; }
+  }
+  __syncthreads();
+  for (int c = t; c < p.n_eyes * gw; c += blockDim.x) {
+    const int e = c / gw, x = c - e * gw;
+    uint32_t *col = s_grid + e * gw * gh + x;
+    uint32_t acc = 0;
+    for (int y = 0; y < gh; ++y) { acc += col[y * gw]; col[y * gw] = acc; }
+  }
+  __syncthreads();
+  // exclusive scan of the counts over all tiles (eye-major, row-major)
+  const int n_ranges = p.n_eyes * p.n_tiles;
+  for (int base = 0; base < n_ranges; base += blockDim.x) {
+    const int tt = base + t;
+    uint32_t cnt = 0;
+    if (tt < n_ranges) {
+      const int eye = tt / p.n_tiles;
+      const int tile = tt - eye * p.n_tiles;
+      const int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
+      cnt = s_grid[eye * gw * gh + ty * gw + tx];
+    }
+    unsigned long long incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long n = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += n;
+    }
+    if (lane == 31) s_warp[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+      const unsigned long long w = s_warp[lane];
+      unsigned long long wi = w;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long n = __shfl_up_sync(0xffffffffu, wi, o);
+        if (lane >= o) wi += n;
+      }
+      s_warp[lane] = wi - w;
+    }
+    __syncthreads();
+    const unsigned long long excl = s_carry + s_warp[warp] + incl - cnt;
+    if (tt < n_ranges) {
+      // unclamped: the composite clamps every range to the instances the sort kept
+      const unsigned long long lim = 0xffffffffull;
+      ranges[tt] = make_uint2((uint32_t)(excl < lim ? excl : lim),
+                              (uint32_t)(excl + cnt < lim ? excl + cnt : lim));
+    }
+    __syncthreads();
+    if (t == blockDim.x - 1) s_carry = excl + cnt;
+    __syncthreads();
+  }
+  const unsigned long long total = s_carry;
+  // digit histograms: the tiles of digit d in a pass with shift s and b bits form runs of
+  // 2^s consecutive tiles starting at ((k << b) | d) << s; a run's count is a difference
+  // of two scanned range starts
+  const int bits = __popc(p.tile_plan.mask);
+  for (int i = t; i < p.tile_plan.passes * 256; i += blockDim.x) {
+    const int ps = i >> 8, d = i & 255;
+    uint32_t v = 0;
+    if ((uint32_t)d <= p.tile_plan.mask) {
+      const int s = p.tile_plan.shift[ps];
+      for (long long k = 0;; ++k) {
+        const long long a = ((k << bits) | d) << s;
+        if (a >= n_ranges) break;
+        const long long b = min((long long)n_ranges, a + (1ll << s));
+        const uint32_t end = b < n_ranges ? ranges[b].x : (uint32_t)total;
+        v += end - ranges[a].x;
+      }
+    }
+    tile_hist[i] = v;
+  }
+  if (t == 0) {
+    const uint32_t eye0 = p.n_eyes > 1 ? ranges[p.n_tiles].x : (uint32_t)total;
+    counts[0] = (uint32_t)(total < p.capacity ? total : p.capacity);
+    counts[1] = eye0;
+    counts[2] = (uint32_t)total - eye0;
+    counts[3] = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
+    if (total > p.capacity) atomicOr(status, kStatusCapacity);
   }
 }
 
@@ -211,23 +337,54 @@ size_t emit_lookback_bytes(int n_entries) {
 
 cudaError_t launch_emit(const EmitParams &p, const uint32_t *entries, const uint32_t *touched,
                         const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
-                        unsigned long long *lookback, uint32_t *block_counter, uint32_t *counts,
-                        uint32_t *status, uint32_t *tile_hist, cudaStream_t s) {
+                        unsigned long long *lookback, uint32_t *block_counter, uint32_t *status,
+                        cudaStream_t s) {
   if (p.n_entries <= 0) return cudaSuccess;
   const int blocks = (p.n_entries + kEmitThreads - 1) / kEmitThreads;
   emit_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, rect, tile_keys, vals,
-                                              lookback, block_counter, counts, status,
-                                              tile_hist);
+                                              lookback, block_counter, status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_ranges(const uint32_t *tile_keys, const uint32_t *d_count,
-                               size_t capacity, uint2 *ranges, int n_ranges, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(ranges, 0, sizeof(uint2) * (size_t)n_ranges, s);
+size_t tile_grid_cells(int n_eyes, int tiles_x, int tiles_y) {
+  return (size_t)n_eyes * (tiles_x + 1) * (tiles_y + 1);
+}
+
+size_t tile_scan_smem_bytes(int n_eyes, int tiles_x, int tiles_y) {
+  return sizeof(uint32_t) * tile_grid_cells(n_eyes, tiles_x, tiles_y);
+}
+
+int tile_count_blocks() {
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms;
+}
+
+cudaError_t launch_tile_count(const TileScanParams &p, const ushort4 *rect, uint32_t *partials,
+                              uint32_t *grid, cudaStream_t s) {
+  const size_t cells = tile_grid_cells(p.n_eyes, p.tiles_x, p.tiles_y);
+  const size_t smem = sizeof(uint32_t) * cells;
+  cudaError_t e = cudaFuncSetAttribute(tile_count_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (capacity == 0) return cudaSuccess;
-  tile_ranges_kernel<<<grid_for(capacity, 256), 256, 0, s>>>(tile_keys, d_count, ranges,
-                                                              (uint32_t)n_ranges);
+  const int parts = tile_count_blocks();
+  tile_count_kernel<<<parts, kCountThreads, smem, s>>>(p, rect, partials);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int rb = (int)((cells + 255) / 256);
+  tile_reduce_kernel<<<rb, 256, 0, s>>>(partials, parts, (int)cells, grid);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_scan(const TileScanParams &p, const uint32_t *grid, uint2 *ranges,
+                             uint32_t *tile_hist, uint32_t *counts, uint32_t *status,
+                             cudaStream_t s) {
+  const size_t smem = tile_scan_smem_bytes(p.n_eyes, p.tiles_x, p.tiles_y);
+  cudaError_t e = cudaFuncSetAttribute(tile_scan_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  tile_scan_kernel<<<1, 1024, smem, s>>>(p, grid, ranges, tile_hist, counts, status);
   return cudaGetLastError();
 }
 

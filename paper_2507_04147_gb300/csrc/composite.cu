@@ -14,7 +14,9 @@
 // depth-sorted list (indices from the sorted values) into shared memory; the live
 // threads then blend them front to back with the 1/255 skip, the 0.99 clamp and the 1e-4
 // transmittance stop.  A CTA-wide vote ends the tile as soon as every pixel is done.  The
-// exp of the Gaussian falloff uses the MUFU ex2 unit with log2(e) folded into the conic.
+// exp of the Gaussian falloff uses the MUFU ex2 unit with log2(e) folded into the conic,
+// and the 1/255 test is made on the exponent first (log2 threshold per Gaussian), so
+// pixels outside a Gaussian's support never reach the exp.
 // Results are assembled in shared memory (label-1 threads also write the inherited
 // pixels of their block) and stored row by row.
 #include "common.cuh"
@@ -32,17 +34,23 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 
 template <bool kAux>
 __global__ void __launch_bounds__(kThreads)
 composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
-                 const uint2 *__restrict__ ranges, const uint32_t *__restrict__ vals,
+                 const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
+                 const uint32_t *__restrict__ vals,
                  const float *__restrict__ gaze, float *__restrict__ out,
                  uint8_t *__restrict__ levels, float *__restrict__ t_final,
                  uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ counters) {
-  __shared__ float2 s_xy[kBatch];
-  __shared__ float4 s_co[kBatch];     // conic * (-0.5 log2 e) terms and opacity
-  __shared__ float4 s_rgb[kBatch];
+  __shared__ float4 s_geo[kBatch];    // u, v, -0.5 log2e a, -log2e b
+  __shared__ float4 s_co[kBatch];     // -0.5 log2e c, log2 threshold, unused, unused
+  __shared__ float4 s_rgb[kBatch];    // r, g, b, opacity
   __shared__ float s_out[kTile][kTile][3];
   __shared__ unsigned long long s_eval;
 
@@ -83,7 +91,10 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
   const bool live = (g < level) && inside;
   const float fpx = (float)px, fpy = (float)py;
 
-  const uint2 range = ranges[gtile];
+  uint2 range = ranges[gtile];
+  const uint32_t n_kept = *kept;   // fewer than the instances only after a capacity overflow
+  range.x = min(range.x, n_kept);
+  range.y = min(range.y, n_kept);
   const float *rec_eye = rec + (size_t)eye * n * kRec;
   float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
   uint32_t contrib = 0, evals = 0;
@@ -98,29 +109,32 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
       const uint32_t gidx = min(vals[idx], (uint32_t)(n - 1));   // in range unless a sort failed
       const float4 *r4 = reinterpret_cast<const float4 *>(rec_eye + (size_t)gidx * kRec);
       const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
-      s_xy[t] = make_float2(a.x, a.y);
-      s_co[t] = make_float4(-0.5f * kLog2e * a.z, -kLog2e * a.w, -0.5f * kLog2e * b.x, b.y);
-      s_rgb[t] = make_float4(b.z, b.w, c.x, 0.0f);
+      // alpha >= 1/255  <=>  power * log2e >= log2(1 / (255 opacity)) = thr
+      const float op = b.y;
+      const float thr = -lg2_approx(255.0f * op);
+      s_geo[t] = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
+      s_co[t] = make_float4(-0.5f * kLog2e * b.x, thr, 0.0f, 0.0f);
+      s_rgb[t] = make_float4(b.z, b.w, c.x, op);
     }
     __syncthreads();
     const int cnt = (int)min((uint32_t)kBatch, range.y - start);
     if (!done) {
       for (int k = 0; k < cnt; ++k) {
-        const float2 xy = s_xy[k];
+        const float4 geo = s_geo[k];
         const float4 co = s_co[k];
-        const float dx = xy.x - fpx, dy = xy.y - fpy;
         ++evals;
+        const float dx = geo.x - fpx, dy = geo.y - fpy;
         // power * log2(e) = -0.5 log2e (a dx^2 + c dy^2) - log2e b dx dy
-        const float pw = co.x * dx * dx + co.z * dy * dy + co.y * dx * dy;
-        if (pw > 0.0f) continue;
-        const float alpha = fminf(0.99f, co.w * ex2_approx(pw));
+        const float pw = geo.z * dx * dx + co.x * dy * dy + geo.w * dx * dy;
+        if (pw > 0.0f || pw < co.y) continue;
+        const float4 rgb = s_rgb[k];
+        const float alpha = fminf(0.99f, rgb.w * ex2_approx(pw));
         if (alpha < 1.0f / 255.0f) continue;
         const float test_t = T * (1.0f - alpha);
         if (test_t < 0.0001f) {
           done = true;
           break;
         }
-        const float4 rgb = s_rgb[k];
         const float w = alpha * T;
         C0 += rgb.x * w;
         C1 += rgb.y * w;
@@ -188,16 +202,17 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
 }  // namespace
 
 cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
-                             const uint2 *ranges, const uint32_t *vals, const float *gaze,
+                             const uint2 *ranges, const uint32_t *kept, const uint32_t *vals,
+                             const float *gaze,
                              float *out, uint8_t *levels, float *t_final, uint32_t *n_contrib,
                              unsigned long long *counters, cudaStream_t s) {
   const int blocks = p.n_eyes * p.n_tiles;
   if (blocks <= 0) return cudaSuccess;
   if (t_final != nullptr)
-    composite_kernel<true><<<blocks, kThreads, 0, s>>>(p, rec, n, ranges, vals, gaze, out,
+    composite_kernel<true><<<blocks, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, gaze, out,
                                                        levels, t_final, n_contrib, counters);
   else
-    composite_kernel<false><<<blocks, kThreads, 0, s>>>(p, rec, n, ranges, vals, gaze, out,
+    composite_kernel<false><<<blocks, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, gaze, out,
                                                         levels, t_final, n_contrib, counters);
   return cudaGetLastError();
 }

@@ -12,6 +12,8 @@
 //      (__match_any_sync + per-warp digit counters),
 //   3. publishes its per-digit counts and resolves the exclusive prefix of every digit by
 //      decoupled look-back over earlier partitions (flag + 30-bit count in one word),
+//      reading a window of 8 predecessors per step so a single wave of partitions does
+//      not serialise on one L2 round trip per predecessor,
 //   4. stages the pairs in shared memory in digit order and writes them out in runs.
 // Every look-back wait is bounded: after kSpinLimit polls the CTA records
 // kStatusTimeout in the status word and carries on (its writes stay in bounds), so a
@@ -29,7 +31,8 @@ constexpr int kRadix = 256;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1u;
-constexpr uint32_t kSpinLimit = 1u << 20;
+constexpr uint32_t kSpinLimit = 1u << 16;   // with back-off: well over a second
+constexpr int kWin = 8;   // look-back window (predecessor partitions read at once)
 
 template <typename K> struct Part;
 template <> struct Part<uint64_t> { static constexpr int kKPT = 12; };
@@ -62,33 +65,57 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_tmp)
   return before + incl - v;
 }
 
+// Digit histograms of every pass in one read of the keys.  Each thread walks a contiguous
+// run of keys and, per pass, adds to shared memory only when the digit changes (so the
+// few-valued high digits of depths cost one atomic per run instead of one per key); each
+// warp owns a private copy of the counters, summed at the end.
+constexpr int kHistKeysPerThread = 8;
+
 template <typename K>
 __global__ void __launch_bounds__(kThreads)
 histogram_kernel(const K *__restrict__ keys, const uint32_t *__restrict__ d_count, SortPlan plan,
                  uint32_t *__restrict__ hist) {
-  __shared__ uint32_t s_hist[kMaxSortPasses][kRadix];
-  for (int i = threadIdx.x; i < kMaxSortPasses * kRadix; i += kThreads) (&s_hist[0][0])[i] = 0;
-  __syncthreads();
+  __shared__ uint32_t s_hist[kWarps][4][kRadix];   // per warp, up to 4 passes per launch
+  const int t = threadIdx.x, warp = t >> 5;
   const uint32_t n = *d_count;
-  const int lane = threadIdx.x & 31;
-  const uint32_t stride = gridDim.x * kThreads;
-  for (uint32_t base = blockIdx.x * kThreads; base < n; base += stride) {
-    const uint32_t i = base + threadIdx.x;
-    const bool valid = i < n;
-    const K k = valid ? keys[i] : K(0);
-    const unsigned active = __ballot_sync(0xffffffffu, valid);
-    for (int p = 0; p < plan.passes; ++p) {
-      const uint32_t d = (uint32_t)(k >> plan.shift[p]) & plan.mask;
-      if (valid) {
-        const unsigned peers = __match_any_sync(active, d);
-        if (lane == 31 - __clz(peers)) atomicAdd(&s_hist[p][d], (uint32_t)__popc(peers));
+  for (int p0 = 0; p0 < plan.passes; p0 += 4) {
+    const int np = min(4, plan.passes - p0);
+    for (int i = t; i < kWarps * 4 * kRadix; i += kThreads) (&s_hist[0][0][0])[i] = 0;
+    __syncthreads();
+    const uint32_t per_block = kThreads * kHistKeysPerThread;
+    for (uint32_t base = blockIdx.x * per_block; base < n; base += gridDim.x * per_block) {
+      const uint32_t i0 = base + t * kHistKeysPerThread;
+      const uint32_t i1 = min(n, i0 + kHistKeysPerThread);
+      uint32_t cur[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
+      uint32_t run[4] = {0u, 0u, 0u, 0u};
+      for (uint32_t i = i0; i < i1; ++i) {
+        const K k = keys[i];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (q < np) {
+            const uint32_t d = (uint32_t)(k >> plan.shift[p0 + q]) & plan.mask;
+            if (d != cur[q]) {
+              if (run[q]) atomicAdd(&s_hist[warp][q][cur[q]], run[q]);
+              cur[q] = d;
+              run[q] = 0;
+            }
+            ++run[q];
+          }
+        }
       }
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (q < np && run[q]) atomicAdd(&s_hist[warp][q][cur[q]], run[q]);
     }
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < plan.passes * kRadix; i += kThreads) {
-    const uint32_t v = (&s_hist[0][0])[i];
-    if (v) atomicAdd(hist + i, v);
+    __syncthreads();
+    for (int i = t; i < np * kRadix; i += kThreads) {
+      const int q = i / kRadix, d = i - q * kRadix;
+      uint32_t v = 0;
+#pragma unroll
+      for (int w = 0; w < kWarps; ++w) v += s_hist[w][q][d];
+      if (v) atomicAdd(hist + (p0 + q) * kRadix + d, v);
+    }
+    __syncthreads();
   }
 }
 
@@ -164,21 +191,35 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
   const uint32_t global_excl = block_excl_scan(hist[d], s_tmp);
   uint32_t excl = 0;
   if (part > 0) {
+    // windowed look-back: kWin predecessors are read at once (independent loads), summed
+    // nearest first up to the first inclusive prefix; an unpublished one is polled again
     int j = (int)part - 1;
     uint32_t spins = 0;
     while (true) {
-      const uint32_t v = ld_relaxed(lookback + (size_t)j * kRadix + d);
-      const uint32_t flag = v & ~kValMask;
-      if (flag == 0u) {
+      uint32_t w[kWin];
+#pragma unroll
+      for (int k = 0; k < kWin; ++k)
+        w[k] = (j - k >= 0) ? ld_relaxed(lookback + (size_t)(j - k) * kRadix + d) : kFlagPrefix;
+      bool done = false;
+      int k = 0;
+      for (; k < kWin; ++k) {
+        const uint32_t flag = w[k] & ~kValMask;
+        if (flag == 0u) break;
+        excl += w[k] & kValMask;
+        if (flag == kFlagPrefix) {
+          done = true;
+          break;
+        }
+      }
+      if (done) break;
+      j -= k;
+      if (k < kWin) {   // an unpublished predecessor: back off before polling it again
         if (++spins > kSpinLimit) {
           atomicOr(status, kStatusTimeout);
           break;
         }
-        continue;
+        __nanosleep(spins < 8 ? 32u << spins : 4096u);
       }
-      excl += v & kValMask;
-      if (flag == kFlagPrefix || j == 0) break;
-      --j;
     }
     st_relaxed(my_lb, kFlagPrefix | ((excl + total) & kValMask));
   }
@@ -255,8 +296,9 @@ template <typename K>
 cudaError_t launch_histogram(const K *keys, const uint32_t *d_count, size_t capacity,
                              const SortPlan &plan, uint32_t *hist, cudaStream_t s) {
   const int sms = sm_count();
-  const size_t hb = (capacity + kThreads * 16 - 1) / (kThreads * 16);
-  const int blocks = (int)(hb < (size_t)sms * 4 ? (hb > 0 ? hb : 1) : (size_t)sms * 4);
+  const size_t per_block = (size_t)kThreads * kHistKeysPerThread;
+  const size_t hb = (capacity + per_block - 1) / per_block;
+  const int blocks = (int)(hb < (size_t)sms * 8 ? (hb > 0 ? hb : 1) : (size_t)sms * 8);
   histogram_kernel<K><<<blocks, kThreads, 0, s>>>(keys, d_count, plan, hist);
   return cudaGetLastError();
 }
