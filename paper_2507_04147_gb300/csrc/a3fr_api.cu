@@ -60,6 +60,7 @@ struct a3fr_scene {
   uint32_t *dvals[2] = {nullptr, nullptr};   // depth-sorted entries e * n + i
   uint2 *ranges = nullptr;
   uint32_t *tile_partials = nullptr;         // per-CTA 2-D difference grids of tile_count
+  uint32_t *plan = nullptr;                  // tiles bucketed by level (foveated composite)
   uint8_t *levels = nullptr;
   float *t_final = nullptr;
   uint32_t *n_contrib = nullptr;
@@ -142,6 +143,7 @@ void free_frame_buffers(a3fr_scene *s) {
   }
   dfree(s->ranges);
   dfree(s->tile_partials);
+  dfree(s->plan);
   dfree(s->levels);
   dfree(s->t_final);
   dfree(s->n_contrib);
@@ -215,6 +217,7 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
   A3FR_CHECK(cudaMalloc(&s->ranges, sizeof(uint2) * (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->tile_partials, sizeof(uint32_t) * (size_t)tile_count_blocks() *
                                                tile_grid_cells(eyes, s->TX, s->TY)));
+  A3FR_CHECK(cudaMalloc(&s->plan, plan_bytes(s->n_tiles * eyes)));
   A3FR_CHECK(cudaMalloc(&s->levels, (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->t_final, sizeof(float) * (size_t)W * H * eyes));
   A3FR_CHECK(cudaMalloc(&s->n_contrib, sizeof(uint32_t) * (size_t)W * H * eyes));
@@ -445,10 +448,10 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
     gaze = s->gaze_dev;   // not read when full
   }
   A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
-  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, counts, s->tvals[b], gaze, out,
+  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, counts, s->tvals[b], gaze, s->plan, out,
                               s->levels, s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
-  ++launches;
+  launches += fv ? 2 : 1;
   A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));
   if (fv) {
     A3FR_CHECK(cudaEventRecord(s->gaze_consumed[slot], stream));

@@ -134,11 +134,15 @@ struct CompositeParams {
   float r2[kMaxEyes][3];    // squared layer radii per eye
 };
 
-// ranges are clamped to kept[0] (the instances the sort kept).
+// Bytes of the level plan of launch_composite for n_ranges = n_eyes * n_tiles.
+size_t plan_bytes(int n_ranges);
+// Foveated: computes the tile levels from the gaze, buckets the tiles by level into `plan`,
+// then composites; full (p.full): every tile at level 4, plan unused.  Ranges are clamped to
+// kept[0] (the instances the sort kept).
 cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
                              const uint2 *ranges, const uint32_t *kept, const uint32_t *vals,
-                             const float *gaze,
-                             float *out, uint8_t *levels, float *t_final, uint32_t *n_contrib,
-                             unsigned long long *counters, cudaStream_t s);
+                             const float *gaze, uint32_t *plan, float *out, uint8_t *levels,
+                             float *t_final, uint32_t *n_contrib, unsigned long long *counters,
+                             cudaStream_t s);
 
 }  // namespace a3fr

@@ -1,32 +1,33 @@
-// composite.cu -- foveated front-to-back compositing of every tile of every eye in one
-// launch (Sec. 2.3 "Rasterization"; Sec. 3.4 AMR; Sec. 3.5 implementation details).
+// composite.cu -- foveated front-to-back compositing of every tile of every eye (Sec. 2.3
+// "Rasterization"; Sec. 3.4 AMR; Sec. 3.5 implementation details).
 //
-// One CTA renders one 16x16 tile.  Its level (Eq. 1: distance from the gaze in the
-// device mailbox to the tile's nearest pixel centre against r_k = f tan(theta_k)) is
-// computed by the CTA itself, so the level map costs no launch.  The 256 threads form the
-// paper's four groups of 64, one per 2x2-block label (TL 1, BR 2, TR 3, BL 4): group g
-// renders label g+1 of each of the tile's 8x8 blocks, and a level-k tile runs groups
-// 0..k-1 while the other warps only help stage Gaussians (they never touch the FP32 or
-// MUFU pipes).  Pixels are compacted by label, so every warp that works holds 32 live
-// pixels.
+// Work is split the way the paper splits a tile: one group per 2x2-block label (TL 1,
+// BR 2, TR 3, BL 4), and a level-k tile runs only the groups of labels 1..k.  Here a group
+// is two warps: a 16x16 tile has 64 pixels per label, one per lane.
 //
-// Each round, all 256 threads gather the records of the next 256 Gaussians of the tile's
-// depth-sorted list (indices from the sorted values) into shared memory; the live
-// threads then blend them front to back with the 1/255 skip, the 0.99 clamp and the 1e-4
-// transmittance stop.  A CTA-wide vote ends the tile as soon as every pixel is done.  The
-// exp of the Gaussian falloff uses the MUFU ex2 unit with log2(e) folded into the conic,
-// and the 1/255 test is made on the exponent first (log2 threshold per Gaussian), so
-// pixels outside a Gaussian's support never reach the exp.
-// Results are assembled in shared memory (label-1 threads also write the inherited
-// pixels of their block) and stored row by row.
+// fovea_plan computes every tile's level from the gaze in the device mailbox (Eq. 1: the
+// distance from the gaze to the tile's nearest pixel centre against r_k = f tan(theta_k))
+// and buckets the tiles by level.  composite then packs 8-warp CTAs so that no warp idles:
+//   level 4: one tile per CTA, the CTA stages each batch of Gaussians together;
+//   level 3: one tile per CTA, the last two warps only help staging;
+//   level 2: two tiles per CTA, each half stages its own tile (named barrier);
+//   level 1: four tiles per CTA, each warp pair stages its own tile (named barrier).
+// A full-resolution render skips the plan: every tile is a level-4 CTA.
+//
+// Per batch, the staging threads gather the tile's next Gaussians (indices from the
+// sorted values) into shared memory; each warp then blends them front to back with the
+// 1/255 skip, the 0.99 clamp and the 1e-4 transmittance stop; the staging group stops when
+// all its pixels are done.  The exp of the falloff
+// uses the MUFU ex2 unit with log2(e) folded into the conic, and the 1/255 test is made on
+// the exponent first, so pixels outside a Gaussian's support never reach the exp.  Label-1
+// warps also write the inherited pixels of their blocks.
 #include "common.cuh"
 
 namespace a3fr {
 namespace {
 
 constexpr int kTile = 16;
-constexpr int kThreads = 256;
-constexpr int kBatch = 256;
+constexpr int kThreads = 256;          // 8 warps
 constexpr float kLog2e = 1.4426950408889634f;
 
 __device__ __forceinline__ float ex2_approx(float x) {
@@ -40,55 +41,144 @@ __device__ __forceinline__ float lg2_approx(float x) {
   return y;
 }
 
-template <bool kAux>
-__global__ void __launch_bounds__(kThreads)
+// Level of tile `tile` of eye `eye` (exactly rounded; the same decision as the definition).
+__device__ __forceinline__ int tile_level(const CompositeParams &p, int eye, int tile,
+                                          const float *gaze) {
+  const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+  const float gx = gaze[2 * eye], gy = gaze[2 * eye + 1];
+  const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
+  const float x1 = (float)(min((tx + 1) * kTile, p.width) - 1);
+  const float y1 = (float)(min((ty + 1) * kTile, p.height) - 1);
+  const float dx = fmaxf(fmaxf(fs(x0, gx), fs(gx, x1)), 0.0f);
+  const float dy = fmaxf(fmaxf(fs(y0, gy), fs(gy, y1)), 0.0f);
+  const float d2 = fa(fm(dx, dx), fm(dy, dy));
+  int layer = p.n_layers - 1;
+  for (int k = p.n_layers - 2; k >= 0; --k)
+    if (d2 <= p.r2[eye][k]) layer = k;
+  return p.level[layer];
+}
+
+// Buckets the tiles by level: plan[(level - 1) * n_ranges + slot], counts[level - 1].
+__global__ void __launch_bounds__(256)
+fovea_plan_kernel(CompositeParams p, const float *__restrict__ gaze, uint8_t *__restrict__ levels,
+                  uint32_t *__restrict__ plan, uint32_t *__restrict__ plan_counts) {
+  const int n_ranges = p.n_eyes * p.n_tiles;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  int level = 0;
+  if (gt < n_ranges) {
+    const int eye = gt / p.n_tiles;
+    level = tile_level(p, eye, gt - eye * p.n_tiles, gaze);
+    levels[gt] = (uint8_t)level;
+  }
+  for (int L = 1; L <= 4; ++L) {
+    const unsigned m = __ballot_sync(0xffffffffu, level == L);
+    if (!m) continue;
+    const int leader = __ffs(m) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(plan_counts + (L - 1), (uint32_t)__popc(m));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (level == L)
+      plan[(size_t)(L - 1) * n_ranges + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)gt;
+  }
+}
+
+// Barrier of a staging group of `size` threads (64, 128 or 256) with barrier id `bar`
+// (1..4).  The ids are literals so the kernel reserves 5 hardware barriers, not 16 (the
+// per-SM barrier budget would otherwise cap residency at 4 CTAs).
+__device__ __forceinline__ void group_sync(int size, int bar) {
+  switch (bar) {
+    case 1: asm volatile("bar.sync 1, %0;" ::"r"(size) : "memory"); break;
+    case 2: asm volatile("bar.sync 2, %0;" ::"r"(size) : "memory"); break;
+    case 3: asm volatile("bar.sync 3, %0;" ::"r"(size) : "memory"); break;
+    default: asm volatile("bar.sync 4, %0;" ::"r"(size) : "memory"); break;
+  }
+}
+
+// Front-to-back blend of one Gaussian into one pixel; returns true when the pixel is done.
+__device__ __forceinline__ void blend(float pw, const float4 &rgb, uint32_t pos, float &T,
+                                      float &C0, float &C1, float &C2, uint32_t &last,
+                                      uint32_t &stop, bool &done) {
+  const float alpha = fminf(0.99f, rgb.w * ex2_approx(pw));
+  if (alpha < 1.0f / 255.0f) return;
+  const float tt = T * (1.0f - alpha);
+  if (tt < 0.0001f) {
+    done = true;
+    stop = pos;
+    return;
+  }
+  const float w = alpha * T;
+  C0 += rgb.x * w;
+  C1 += rgb.y * w;
+  C2 += rgb.z * w;
+  T = tt;
+  last = pos;
+}
+
+template <bool kAux, bool kFull>
+__global__ void __launch_bounds__(kThreads, 6)
 composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
-                 const uint32_t *__restrict__ vals,
-                 const float *__restrict__ gaze, float *__restrict__ out,
+                 const uint32_t *__restrict__ vals, const uint32_t *__restrict__ plan,
+                 const uint32_t *__restrict__ plan_counts, float *__restrict__ out,
                  uint8_t *__restrict__ levels, float *__restrict__ t_final,
                  uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ counters) {
-  __shared__ float4 s_geo[kBatch];    // u, v, -0.5 log2e a, -log2e b
-  __shared__ float4 s_co[kBatch];     // -0.5 log2e c, log2 threshold, unused, unused
-  __shared__ float4 s_rgb[kBatch];    // r, g, b, opacity
-  __shared__ float s_out[kTile][kTile][3];
-  __shared__ unsigned long long s_eval;
+  __shared__ float4 s_geo[kThreads];   // u, v, -0.5 log2e a, -log2e b
+  __shared__ float4 s_co[kThreads];    // -0.5 log2e c, log2 threshold, -, -
+  __shared__ float4 s_rgb[kThreads];   // r, g, b, opacity
+  __shared__ int s_done[kThreads / 32];
+  __shared__ float s_out[4][kTile][kTile * 3];   // the tiles of the CTA, assembled for stores
 
-  const int gtile = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int n_ranges = p.n_eyes * p.n_tiles;
+
+  // ---- which tile, which label group (two warps each), which staging group
+  int gtile = -1, group = warp >> 1, level = 4, gsize = kThreads, gbar = 1, gfirst = 0;
+  if (kFull) {
+    gtile = blockIdx.x;
+    if (threadIdx.x == 0) levels[gtile] = 4;
+  } else {
+    const int c = blockIdx.x;
+    const int n4 = plan_counts[3], n3 = plan_counts[2], n2 = plan_counts[1], n1 = plan_counts[0];
+    const int c3 = n4 + n3, c2 = c3 + (n2 + 1) / 2, c1 = c2 + (n1 + 3) / 4;
+    if (c < n4) {
+      gtile = plan[3 * (size_t)n_ranges + c];
+    } else if (c < c3) {
+      gtile = plan[2 * (size_t)n_ranges + (c - n4)];
+      level = 3;
+    } else if (c < c2) {
+      const int half = warp >> 2;
+      const int slot = 2 * (c - c3) + half;
+      level = 2;
+      group = (warp >> 1) & 1;
+      gsize = 128;
+      gbar = 1 + half;
+      gfirst = half * 128;
+      gtile = slot < n2 ? (int)plan[(size_t)n_ranges + slot] : -1;
+    } else if (c < c1) {
+      const int quarter = warp >> 1;
+      const int slot = 4 * (c - c2) + quarter;
+      level = 1;
+      group = 0;
+      gsize = 64;
+      gbar = 1 + quarter;
+      gfirst = quarter * 64;
+      gtile = slot < n1 ? (int)plan[slot] : -1;
+    } else {
+      return;
+    }
+    if (gtile < 0) return;   // a partly filled pair or quad: these warps have no tile
+  }
   const int eye = gtile / p.n_tiles;
   const int tile = gtile - eye * p.n_tiles;
   const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
-  const int t = threadIdx.x;
 
-  // tile level from the gaze (exactly rounded, same decision as the definition)
-  int level = 4;
-  if (!p.full) {
-    const float gx = gaze[2 * eye], gy = gaze[2 * eye + 1];
-    const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
-    const float x1 = (float)(min((tx + 1) * kTile, p.width) - 1);
-    const float y1 = (float)(min((ty + 1) * kTile, p.height) - 1);
-    const float dx = fmaxf(fmaxf(fs(x0, gx), fs(gx, x1)), 0.0f);
-    const float dy = fmaxf(fmaxf(fs(y0, gy), fs(gy, y1)), 0.0f);
-    const float d2 = fa(fm(dx, dx), fm(dy, dy));
-    int layer = p.n_layers - 1;
-    for (int k = p.n_layers - 2; k >= 0; --k)
-      if (d2 <= p.r2[eye][k]) layer = k;
-    level = p.level[layer];
-  }
-  if (t == 0) {
-    levels[gtile] = (uint8_t)level;
-    s_eval = 0ull;
-  }
-
-  // compacted pixel of this thread: group g = label g+1, block (bx, by) of the 8x8
-  const int g = t >> 6, j = t & 63;
-  const int bx = j & 7, by = j >> 3;
-  const int ox = (g == 1 || g == 2) ? 1 : 0;     // BR, TR
-  const int oy = (g == 1 || g == 3) ? 1 : 0;     // BR, BL
-  const int lx = 2 * bx + ox, ly = 2 * by + oy;
-  const int px = tx * kTile + lx, py = ty * kTile + ly;
-  const bool inside = px < p.width && py < p.height;
-  const bool live = (g < level) && inside;
+  // ---- this lane's pixel: label `group` of block (bx, by) of the tile's 8x8 blocks
+  const int ox = (group == 1 || group == 2) ? 1 : 0;   // BR, TR
+  const int oy = (group == 1 || group == 3) ? 1 : 0;   // BR, BL
+  const int bx = lane & 7, by = (warp & 1) * 4 + (lane >> 3);
+  const int px = tx * kTile + 2 * bx + ox, py = ty * kTile + 2 * by + oy;
+  const bool inside = group < level && px < p.width && py < p.height;
   const float fpx = (float)px, fpy = (float)py;
 
   uint2 range = ranges[gtile];
@@ -96,124 +186,164 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
   range.x = min(range.x, n_kept);
   range.y = min(range.y, n_kept);
   const float *rec_eye = rec + (size_t)eye * n * kRec;
-  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
-  uint32_t contrib = 0, evals = 0;
-  bool done = !live;
-  uint32_t staged = 0;
 
-  for (uint32_t start = range.x; start < range.y; start += kBatch) {
-    if (__syncthreads_count(done) == kThreads) break;
-    staged += min((uint32_t)kBatch, range.y - start);
-    const uint32_t idx = start + t;
-    if (idx < range.y) {
-      const uint32_t gidx = min(vals[idx], (uint32_t)(n - 1));   // in range unless a sort failed
+  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+  uint32_t last = 0;                   // 1-based position of the last contributor
+  uint32_t stop = 0;                   // Gaussians evaluated when the pixel stopped
+  bool done = !inside;
+  uint32_t staged = 0;
+  if (kFull) {   // compile-time layout: one level-4 tile, the whole CTA stages together
+    group = warp >> 1;
+    level = 4;
+    gsize = kThreads;
+    gbar = 1;
+    gfirst = 0;
+  }
+  const int gt = threadIdx.x - gfirst;   // thread index inside the staging group
+
+  for (uint32_t start = range.x; start < range.y; start += gsize) {
+    // stop when every pixel of the staging group is done
+    const bool wdone = __all_sync(0xffffffffu, done);
+    if (lane == 0) s_done[warp] = wdone;
+    group_sync(gsize, gbar);
+    bool all = true;
+    for (int w = gfirst >> 5; w < (gfirst + gsize) >> 5; ++w) all = all && s_done[w];
+    if (all) break;
+    const uint32_t cnt = min((uint32_t)gsize, range.y - start);
+    staged += cnt;
+    if ((uint32_t)gt < cnt) {
+      const uint32_t gidx = min(vals[start + gt], (uint32_t)(n - 1));   // in range unless a sort failed
       const float4 *r4 = reinterpret_cast<const float4 *>(rec_eye + (size_t)gidx * kRec);
       const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
       // alpha >= 1/255  <=>  power * log2e >= log2(1 / (255 opacity)) = thr
-      const float op = b.y;
-      const float thr = -lg2_approx(255.0f * op);
-      s_geo[t] = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
-      s_co[t] = make_float4(-0.5f * kLog2e * b.x, thr, 0.0f, 0.0f);
-      s_rgb[t] = make_float4(b.z, b.w, c.x, op);
+      const float thr = -lg2_approx(255.0f * b.y);
+      s_geo[threadIdx.x] = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
+      s_co[threadIdx.x] = make_float4(-0.5f * kLog2e * b.x, thr, 0.0f, 0.0f);
+      s_rgb[threadIdx.x] = make_float4(b.z, b.w, c.x, b.y);
     }
-    __syncthreads();
-    const int cnt = (int)min((uint32_t)kBatch, range.y - start);
+    group_sync(gsize, gbar);
     if (!done) {
-      for (int k = 0; k < cnt; ++k) {
-        const float4 geo = s_geo[k];
-        const float4 co = s_co[k];
-        ++evals;
+      for (uint32_t k = 0; k < cnt; ++k) {
+        const float4 geo = s_geo[gfirst + k];
+        const float4 co = s_co[gfirst + k];
         const float dx = geo.x - fpx, dy = geo.y - fpy;
         // power * log2(e) = -0.5 log2e (a dx^2 + c dy^2) - log2e b dx dy
-        const float pw = geo.z * dx * dx + co.x * dy * dy + geo.w * dx * dy;
-        if (pw > 0.0f || pw < co.y) continue;
-        const float4 rgb = s_rgb[k];
-        const float alpha = fminf(0.99f, rgb.w * ex2_approx(pw));
-        if (alpha < 1.0f / 255.0f) continue;
-        const float test_t = T * (1.0f - alpha);
-        if (test_t < 0.0001f) {
-          done = true;
-          break;
+        const float pw = (geo.z * dx + geo.w * dy) * dx + co.x * dy * dy;
+        if (pw <= 0.0f && pw >= co.y) {
+          blend(pw, s_rgb[gfirst + k], start - range.x + k + 1, T, C0, C1, C2, last, stop, done);
+          if (done) break;
         }
-        const float w = alpha * T;
-        C0 += rgb.x * w;
-        C1 += rgb.y * w;
-        C2 += rgb.z * w;
-        T = test_t;
-        contrib = evals;
+      }
+    }
+    group_sync(gsize, gbar);   // the next batch overwrites the staged Gaussians
+  }
+  if (inside && !done) stop = range.y - range.x;
+
+  // ---- outputs: the pixel, and for label 1 the inherited pixels of its block, are
+  // assembled in shared memory; the staging group then stores its tile row by row
+  const int slot = gfirst >> 6 >> (gsize == 256 ? 2 : (gsize == 128 ? 1 : 0));   // tile slot
+  const int lx = 2 * bx + ox, ly = 2 * by + oy;
+  if (inside) {
+    float *o = &s_out[slot][ly][3 * lx];
+    o[0] = C0;
+    o[1] = C1;
+    o[2] = C2;
+    if (kAux) {
+      const size_t pix = ((size_t)eye * p.height + py) * p.width + px;
+      t_final[pix] = T;
+      n_contrib[pix] = last;
+    }
+    if (group == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        // inherited pixels of the block: BR (label 2), TR (label 3), BL (label 4)
+        const int dx = k < 2 ? 1 : 0, dy = k == 1 ? 0 : 1;
+        if (level < k + 2 && px + dx < p.width && py + dy < p.height) {
+          float *f = &s_out[slot][ly + dy][3 * (lx + dx)];
+          f[0] = C0;
+          f[1] = C1;
+          f[2] = C2;
+          if (kAux) {
+            const size_t pix = ((size_t)eye * p.height + py + dy) * p.width + px + dx;
+            t_final[pix] = T;
+            n_contrib[pix] = last;
+          }
+        }
       }
     }
   }
+  group_sync(gsize, gbar);
+  {
+    const int w_tile = min(kTile, p.width - tx * kTile);
+    const int h_tile = min(kTile, p.height - ty * kTile);
+    const size_t row = (size_t)p.width * 3;
+    float *dst = out + ((size_t)eye * p.height + ty * kTile) * row + (size_t)tx * kTile * 3;
+    for (int f = gt; f < kTile * kTile * 3; f += gsize) {
+      const int r = f / (3 * kTile), c = f - r * (3 * kTile);
+      if (r < h_tile && c < 3 * w_tile) dst[(size_t)r * row + c] = s_out[slot][r][c];
+    }
+  }
 
-  // statistics: evaluations and staged records of the tile
-  unsigned long long ev = evals;
+  // ---- statistics: evaluations of this warp, records staged by this staging group
+  unsigned long long ev = stop;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
-  if ((t & 31) == 0 && ev) atomicAdd(&s_eval, ev);
-
-  // assemble the tile: live pixels, then label-1 threads fill the inherited ones
-  if (live) {
-    s_out[ly][lx][0] = C0;
-    s_out[ly][lx][1] = C1;
-    s_out[ly][lx][2] = C2;
-    if (g == 0) {
-      if (level < 2) { s_out[ly + 1][lx + 1][0] = C0; s_out[ly + 1][lx + 1][1] = C1; s_out[ly + 1][lx + 1][2] = C2; }
-      if (level < 3) { s_out[ly][lx + 1][0] = C0; s_out[ly][lx + 1][1] = C1; s_out[ly][lx + 1][2] = C2; }
-      if (level < 4) { s_out[ly + 1][lx][0] = C0; s_out[ly + 1][lx][1] = C1; s_out[ly + 1][lx][2] = C2; }
-    }
-  }
-  if (kAux && inside) {
-    // aux buffers describe the shaded pixel; inherited pixels repeat their top-left
-    const size_t pix = ((size_t)eye * p.height + py) * p.width + px;
-    if (live) {
-      t_final[pix] = T;
-      n_contrib[pix] = contrib;
-    }
-  }
-  __syncthreads();
-  if (kAux && g == 0 && inside) {
-    // inherited pixels of this block take the top-left pixel's aux values
-    const int sx[3] = {1, 1, 0}, sy[3] = {1, 0, 1}, need[3] = {2, 3, 4};
-    for (int q = 0; q < 3; ++q) {
-      const int qx = px + sx[q], qy = py + sy[q];
-      if (level < need[q] && qx < p.width && qy < p.height) {
-        const size_t pix = ((size_t)eye * p.height + qy) * p.width + qx;
-        t_final[pix] = T;
-        n_contrib[pix] = contrib;
-      }
-    }
-  }
-  const int w_tile = min(kTile, p.width - tx * kTile);
-  const int h_tile = min(kTile, p.height - ty * kTile);
-  const int row_floats = 3 * w_tile;
-  for (int f = t; f < kTile * 3 * kTile; f += kThreads) {
-    const int r = f / (3 * kTile), c = f - r * (3 * kTile);
-    if (r < h_tile && c < row_floats) {
-      const size_t o = (((size_t)eye * p.height + ty * kTile + r) * p.width + tx * kTile) * 3 + c;
-      out[o] = (&s_out[r][0][0])[c];
-    }
-  }
-  if (t == 0) {
-    atomicAdd(counters, s_eval);
-    atomicAdd(counters + 1, (unsigned long long)staged);
+  if (lane == 0) {
+    if (ev) atomicAdd(counters, ev);
+    if (gt == 0 && staged) atomicAdd(counters + 1, (unsigned long long)staged);
   }
 }
 
 }  // namespace
 
+size_t plan_bytes(int n_ranges) { return sizeof(uint32_t) * (4 * (size_t)n_ranges + 4); }
+
 cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
                              const uint2 *ranges, const uint32_t *kept, const uint32_t *vals,
-                             const float *gaze,
-                             float *out, uint8_t *levels, float *t_final, uint32_t *n_contrib,
-                             unsigned long long *counters, cudaStream_t s) {
-  const int blocks = p.n_eyes * p.n_tiles;
-  if (blocks <= 0) return cudaSuccess;
-  if (t_final != nullptr)
-    composite_kernel<true><<<blocks, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, gaze, out,
-                                                       levels, t_final, n_contrib, counters);
-  else
-    composite_kernel<false><<<blocks, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, gaze, out,
-                                                        levels, t_final, n_contrib, counters);
+                             const float *gaze, uint32_t *plan, float *out, uint8_t *levels,
+                             float *t_final, uint32_t *n_contrib, unsigned long long *counters,
+                             cudaStream_t s) {
+  const int n_ranges = p.n_eyes * p.n_tiles;
+  if (n_ranges <= 0) return cudaSuccess;
+  uint32_t *plan_counts = plan + 4 * (size_t)n_ranges;
+  if (!p.full) {
+    cudaError_t e = cudaMemsetAsync(plan_counts, 0, 4 * sizeof(uint32_t), s);
+    if (e != cudaSuccess) return e;
+    fovea_plan_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p, gaze, levels, plan, plan_counts);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  static bool carveout_set[64] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !carveout_set[dev]) {
+    // prefer shared memory so that the register limit, not the carveout, sets residency
+    const int c = cudaSharedmemCarveoutMaxShared;
+    cudaFuncSetAttribute(composite_kernel<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(composite_kernel<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(composite_kernel<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    cudaFuncSetAttribute(composite_kernel<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
+    carveout_set[dev] = true;
+  }
+  const uint32_t *pc = plan_counts;
+  if (t_final != nullptr) {
+    if (p.full)
+      composite_kernel<true, true><<<n_ranges, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, plan,
+                                                                 pc, out, levels, t_final, n_contrib,
+                                                                 counters);
+    else
+      composite_kernel<true, false><<<n_ranges, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, plan,
+                                                                  pc, out, levels, t_final, n_contrib,
+                                                                  counters);
+  } else {
+    if (p.full)
+      composite_kernel<false, true><<<n_ranges, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, plan,
+                                                                  pc, out, levels, t_final, n_contrib,
+                                                                  counters);
+    else
+      composite_kernel<false, false><<<n_ranges, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals,
+                                                                   plan, pc, out, levels, t_final,
+                                                                   n_contrib, counters);
+  }
   return cudaGetLastError();
 }
 
