@@ -122,6 +122,51 @@ int a3fr_render_full(a3fr_scene *scene, float *out_rgb, void *stream);
 /* Synchronise the scene's last stream and report counters; reset != 0 clears them. */
 int a3fr_get_stats(a3fr_scene *scene, a3fr_stats *stats, int reset);
 
+/* ---- incremental rendering rounds (Sec. 3.3, Algorithm 1) ----
+ * A frame is rendered in rounds while the gaze tracker refines its prediction: the first
+ * round does the buffered precompute (projection, sorts, tile ranges; Sec. 3.5) and renders
+ * every tile at the peripheral level; each later round reads the latest prediction u_i from a
+ * mailbox in mapped host memory when it runs on the GPU and renders only the pixels its
+ * region adds (labels above each tile's current level), never a pixel twice. */
+#define A3FR_MAX_EXITS 8
+
+typedef struct {
+  int32_t n_exits;                 /* N, the number of tracker exits, 1..A3FR_MAX_EXITS */
+  int32_t sir;                     /* 1: speculative rounds when no new prediction arrived */
+  float expected_dist_px[A3FR_MAX_EXITS]; /* E[dist(u_i, u_N)] in pixels, exit i at [i-1];
+                                      the last one should be 0 */
+  float sir_step_px;               /* growth of the radii per speculative round, pixels */
+} a3fr_rounds;
+
+typedef struct {
+  int32_t exit_consumed;           /* exit of the prediction the last round used, 0 = none */
+  int32_t complete;                /* 1 once the final exit's region has been rendered */
+  int32_t rounds;                  /* rounds that rendered something, this frame */
+  float radius_px[3];              /* layer radii of eye 0 in the last round */
+} a3fr_round_status;
+
+/* Round 1 of a frame: the full precompute for the current cameras and every tile rendered at
+ * the peripheral level (fovea->level[n_layers - 1]) into out_rgb (DEVICE [eyes][H][W][3],
+ * which later rounds keep refining).  Clears the mailbox and the round state.  The final
+ * layer radii are those of `fovea` (Eq. 1). */
+int a3fr_begin_frame(a3fr_scene *scene, const a3fr_fovea *fovea, const a3fr_rounds *rounds,
+                     float *out_rgb, void *stream);
+
+/* Post prediction u_i (exit_index i in 1..N, HOST float[eyes][2] pixels) into the mailbox.
+ * Callable from any host thread at any time, without a CUDA call (sequence-locked write into
+ * mapped pinned memory). */
+int a3fr_post_prediction(a3fr_scene *scene, int exit_index, const float *gaze_px);
+
+/* One later round on `stream` (after a3fr_begin_frame, same out_rgb).  When it runs, a new
+ * prediction u_i renders the region of radii max(0, r_{k,N} - E_i) around u_i (Eq. 3'); with
+ * no new prediction and SIR on, the region around the last prediction u_j grows by
+ * sir_step_px up to r_{k,N} + E_j (Eq. 4); otherwise nothing is rendered.  Returns
+ * A3FR_ERR_NOT_READY without a begun frame. */
+int a3fr_render_round(a3fr_scene *scene, float *out_rgb, void *stream);
+
+/* Status of the last completed round, read from mapped host memory (no synchronisation). */
+int a3fr_get_round_status(a3fr_scene *scene, a3fr_round_status *status);
+
 /* Keep per-pixel transmittance and contributor counts of the next renders (aux buffers,
  * see a3fr_copy_buffer); off by default because they cost 8 bytes per pixel. */
 int a3fr_set_keep_aux(a3fr_scene *scene, int keep);

@@ -22,7 +22,8 @@ from ._lib import A3FRError, BUF_KEYS, BUF_LEVELS, BUF_N_CONTRIB, BUF_RANGES, BU
 __all__ = ["Scene", "Fovea", "A3FRError", "camera_struct", "create_scene", "destroy_scene",
            "set_camera", "set_gaze", "render_foveated", "render_full", "get_stats",
            "set_keep_aux", "set_stage_timing", "get_stage_times", "copy_buffer", "sort_pairs", "sort_pairs_workspace_bytes",
-           "sort_pairs_noalloc",
+           "sort_pairs_noalloc", "Rounds", "begin_frame", "post_prediction", "render_round",
+           "get_round_status",
            "error_string"]
 
 
@@ -160,6 +161,40 @@ def sort_pairs_noalloc(keys, vals, key_bits: int, stream=None) -> None:
                                                    _stream_ptr(stream)), "a3fr_sort_pairs_noalloc")
 
 
+def Rounds(expected_dist_px, sir: bool = True, sir_step_px: float = 8.0) -> _lib.Rounds:
+    """Round schedule: E[dist(u_i, u_N)] per exit (pixels, last = 0), SIR on/off and step."""
+    r = _lib.Rounds()
+    r.n_exits = len(expected_dist_px)
+    r.sir = int(bool(sir))
+    for i, e in enumerate(expected_dist_px):
+        r.expected_dist_px[i] = float(e)
+    r.sir_step_px = float(sir_step_px)
+    return r
+
+
+def begin_frame(handle: int, fovea: _lib.Fovea, rounds: _lib.Rounds, out_rgb, stream=None) -> None:
+    _lib.check(_lib.load().a3fr_begin_frame(handle, ctypes.byref(fovea), ctypes.byref(rounds),
+                                            _ptr(out_rgb), _stream_ptr(stream)), "a3fr_begin_frame")
+
+
+def post_prediction(handle: int, exit_index: int, gaze_px) -> None:
+    g = np.ascontiguousarray(np.asarray(gaze_px, dtype=np.float32).reshape(-1))
+    _lib.check(_lib.load().a3fr_post_prediction(handle, exit_index, g.ctypes.data),
+               "a3fr_post_prediction")
+
+
+def render_round(handle: int, out_rgb, stream=None) -> None:
+    _lib.check(_lib.load().a3fr_render_round(handle, _ptr(out_rgb), _stream_ptr(stream)),
+               "a3fr_render_round")
+
+
+def get_round_status(handle: int) -> dict:
+    st = _lib.RoundStatus()
+    _lib.check(_lib.load().a3fr_get_round_status(handle, ctypes.byref(st)), "a3fr_get_round_status")
+    return {"exit_consumed": st.exit_consumed, "complete": st.complete, "rounds": st.rounds,
+            "radius_px": [st.radius_px[0], st.radius_px[1], st.radius_px[2]]}
+
+
 def error_string(code: int) -> str:
     return _lib.load().a3fr_error_string(code).decode()
 
@@ -232,6 +267,21 @@ class Scene:
         out = self._out(out)
         render_full(self.handle, out, stream)
         return out
+
+    def begin_frame(self, fovea, rounds, out=None, stream=None):
+        out = self._out(out)
+        begin_frame(self.handle, fovea, rounds, out, stream)
+        return out
+
+    def post_prediction(self, exit_index: int, gaze_px):
+        post_prediction(self.handle, exit_index, gaze_px)
+
+    def render_round(self, out, stream=None):
+        render_round(self.handle, out, stream)
+        return out
+
+    def round_status(self) -> dict:
+        return get_round_status(self.handle)
 
     def stats(self, reset: bool = False) -> dict:
         return get_stats(self.handle, reset)

@@ -49,6 +49,19 @@ class Stats(ctypes.Structure):
                 ("kernel_launches", ctypes.c_uint64)]
 
 
+MAX_EXITS = 8
+
+
+class Rounds(ctypes.Structure):
+    _fields_ = [("n_exits", ctypes.c_int32), ("sir", ctypes.c_int32),
+                ("expected_dist_px", ctypes.c_float * MAX_EXITS), ("sir_step_px", ctypes.c_float)]
+
+
+class RoundStatus(ctypes.Structure):
+    _fields_ = [("exit_consumed", ctypes.c_int32), ("complete", ctypes.c_int32),
+                ("rounds", ctypes.c_int32), ("radius_px", ctypes.c_float * 3)]
+
+
 class A3FRError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str = ""):
         self.code = code
@@ -78,6 +91,11 @@ _SIGS = {
                          ctypes.c_void_p], ctypes.c_int),
     "a3fr_sort_pairs_noalloc": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
                                  ctypes.c_void_p], ctypes.c_int),
+    "a3fr_begin_frame": ([ctypes.c_void_p, ctypes.POINTER(Fovea), ctypes.POINTER(Rounds),
+                          ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "a3fr_post_prediction": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "a3fr_render_round": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "a3fr_get_round_status": ([ctypes.c_void_p, ctypes.POINTER(RoundStatus)], ctypes.c_int),
     "a3fr_set_stage_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_get_stage_times": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                               ctypes.POINTER(ctypes.c_int)], ctypes.c_int),

@@ -9,9 +9,11 @@
 // count once).  Only the composite depends on the gaze, so projection, binning and the
 // sort overlap whatever produces the gaze (Sec. 3.3.3, Sec. 4.3: the preprocessing can
 // start before gaze tracking finishes).
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 
@@ -97,6 +99,20 @@ struct a3fr_scene {
   int timing_ring = 0;
   cudaEvent_t *timing_events = nullptr;
   uint64_t timed_renders = 0;
+
+  // incremental rounds (Sec. 3.3): the frame's precompute is kept between rounds
+  bool round_ready = false;
+  a3fr_fovea round_fovea{};
+  RoundConfig round_cfg{};
+  uint8_t *cur_level = nullptr;              // [eye * tiles] levels rendered so far
+  RoundState *round_state = nullptr;         // device
+  RoundPlan *round_plan = nullptr;           // device
+  Mailbox *mbox_host = nullptr;              // mapped pinned host memory
+  Mailbox *mbox_dev = nullptr;
+  RoundStatus *status_host = nullptr;        // mapped pinned host memory
+  RoundStatus *status_dev = nullptr;
+  std::mutex mbox_mutex;
+  float *out_round = nullptr;                // the canvas of the frame's rounds
 };
 
 namespace {
@@ -144,6 +160,8 @@ void free_frame_buffers(a3fr_scene *s) {
   dfree(s->ranges);
   dfree(s->tile_partials);
   dfree(s->plan);
+  dfree(s->cur_level);
+  s->round_ready = false;
   dfree(s->levels);
   dfree(s->t_final);
   dfree(s->n_contrib);
@@ -218,6 +236,7 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
   A3FR_CHECK(cudaMalloc(&s->tile_partials, sizeof(uint32_t) * (size_t)tile_count_blocks() *
                                                tile_grid_cells(eyes, s->TX, s->TY)));
   A3FR_CHECK(cudaMalloc(&s->plan, plan_bytes(s->n_tiles * eyes)));
+  A3FR_CHECK(cudaMalloc(&s->cur_level, (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->levels, (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->t_final, sizeof(float) * (size_t)W * H * eyes));
   A3FR_CHECK(cudaMalloc(&s->n_contrib, sizeof(uint32_t) * (size_t)W * H * eyes));
@@ -290,7 +309,49 @@ cudaError_t mark(a3fr_scene *s, int k, cudaStream_t stream) {
   return cudaEventRecord(s->timing_events[slot * (A3FR_N_STAGES + 1) + k], stream);
 }
 
-int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream) {
+CompositeParams composite_params(const a3fr_scene *s, int eyes, const a3fr_fovea *fv) {
+  CompositeParams cp{};
+  cp.n_eyes = eyes;
+  cp.width = s->W;
+  cp.height = s->H;
+  cp.tile = s->desc.tile;
+  cp.tiles_x = s->TX;
+  cp.tiles_y = s->TY;
+  cp.n_tiles = s->n_tiles;
+  cp.full = fv ? 0 : 1;
+  if (fv) {
+    cp.n_layers = fv->n_layers;
+    for (int k = 0; k < 4; ++k) cp.level[k] = fv->level[k];
+    for (int e = 0; e < eyes; ++e)
+      for (int k = 0; k < 3; ++k)
+        cp.r2[e][k] = layer_radius2(s->cams[e].fx, fv->theta_deg[k], fv->dtheta_deg);
+  } else {
+    cp.n_layers = 1;
+    cp.level[0] = 4;
+  }
+  return cp;
+}
+
+enum class Mode { kFull, kFoveated, kFirstRound };
+
+// Writes the mailbox under its sequence lock (any host thread).
+void post_mailbox(a3fr_scene *s, int exit, const float *gaze, int eyes) {
+  std::lock_guard<std::mutex> lock(s->mbox_mutex);
+  Mailbox *m = s->mbox_host;
+  const unsigned int seq = __atomic_load_n(&m->seq, __ATOMIC_RELAXED);
+  __atomic_store_n(&m->seq, seq + 1u, __ATOMIC_RELAXED);
+  std::atomic_thread_fence(std::memory_order_release);
+  __atomic_store_n(&m->exit, exit, __ATOMIC_RELAXED);
+  for (int q = 0; q < kMaxEyes; ++q)
+    for (int k = 0; k < 2; ++k) {
+      const float v = (gaze && q < eyes) ? gaze[2 * q + k] : 0.0f;
+      __atomic_store(&m->gaze[q][k], &v, __ATOMIC_RELAXED);
+    }
+  __atomic_store_n(&m->seq, seq + 2u, __ATOMIC_RELEASE);
+}
+
+int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream, Mode mode) {
+  s->round_ready = false;   // any render replaces the precompute that rounds build on
   const int eyes = n_eyes_of(s);
   if (eyes == 0 || out == nullptr) return A3FR_ERR_INVALID_ARG;
   const a3fr_camera &c0 = s->cams[0];
@@ -300,7 +361,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
     if (fv->n_layers < 1 || fv->n_layers > 4) return A3FR_ERR_INVALID_ARG;
     for (int k = 0; k < fv->n_layers; ++k)
       if (fv->level[k] < 1 || fv->level[k] > 4) return A3FR_ERR_INVALID_ARG;
-    if (s->gaze_seq < 0) return A3FR_ERR_NOT_READY;
+    if (mode == Mode::kFoveated && s->gaze_seq < 0) return A3FR_ERR_NOT_READY;
   }
   int rc = ensure_frame_buffers(s, eyes, c0.width, c0.height);
   if (rc != A3FR_OK) return rc;
@@ -422,38 +483,30 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
   s->sorted_in_alt = in_alt;
   const int b = in_alt ? 1 : 0;
 
-  CompositeParams cp{};
-  cp.n_eyes = eyes;
-  cp.width = s->W;
-  cp.height = s->H;
-  cp.tile = s->desc.tile;
-  cp.tiles_x = s->TX;
-  cp.tiles_y = s->TY;
-  cp.n_tiles = s->n_tiles;
-  cp.full = fv ? 0 : 1;
-  const float *gaze = nullptr;
+  CompositeParams cp = composite_params(s, eyes, mode == Mode::kFull ? nullptr : fv);
+  const float *gaze = s->gaze_dev;   // not read by full renders and first rounds
   int slot = -1;
-  if (fv) {
-    cp.n_layers = fv->n_layers;
-    for (int k = 0; k < 4; ++k) cp.level[k] = fv->level[k];
-    for (int e = 0; e < eyes; ++e)
-      for (int k = 0; k < 3; ++k)
-        cp.r2[e][k] = layer_radius2(s->cams[e].fx, fv->theta_deg[k], fv->dtheta_deg);
+  int uniform = 0;
+  uint8_t *cur = nullptr;
+  if (mode == Mode::kFoveated) {
     slot = s->gaze_seq % kSlots;
     A3FR_CHECK(cudaStreamWaitEvent(stream, s->gaze_written[slot], 0));
     gaze = s->gaze_dev + 4 * slot;
-  } else {
-    cp.n_layers = 1;
-    cp.level[0] = 4;
-    gaze = s->gaze_dev;   // not read when full
+  } else if (mode == Mode::kFirstRound) {
+    // round 1 renders every tile at the peripheral level (Fig. 6: rendering starts at
+    // peripheral resolution) and starts the frame's round state afresh
+    uniform = fv->level[fv->n_layers - 1];
+    cur = s->cur_level;
+    A3FR_CHECK(cudaMemsetAsync(s->round_state, 0, sizeof(RoundState), stream));
+    post_mailbox(s, 0, nullptr, eyes);
   }
   A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
-  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, counts, s->tvals[b], gaze, s->plan, out,
-                              s->levels, s->keep_aux ? s->t_final : nullptr,
+  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, counts, s->tvals[b], gaze, nullptr, uniform,
+                              cur, s->plan, out, s->levels, s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
-  launches += fv ? 2 : 1;
+  launches += mode == Mode::kFull ? 1 : 2;
   A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));
-  if (fv) {
+  if (mode == Mode::kFoveated) {
     A3FR_CHECK(cudaEventRecord(s->gaze_consumed[slot], stream));
     s->slot_consumed[slot] = true;
   }
@@ -462,6 +515,27 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream)
   s->renders++;
   s->launches += launches;
   if (s->timing_ring) s->timed_renders++;
+  if (mode == Mode::kFirstRound) {
+    s->round_ready = true;
+    s->out_round = out;
+  }
+  return A3FR_OK;
+}
+
+// One later round: round_begin (mailbox, Eq. 3' / Eq. 4) + plan + composite of new labels.
+int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
+  if (!s->round_ready || out == nullptr) return A3FR_ERR_NOT_READY;
+  const int eyes = s->last_eyes;
+  CompositeParams cp = composite_params(s, eyes, &s->round_fovea);
+  A3FR_CHECK(launch_round_begin(s->round_cfg, s->mbox_dev, s->round_state, s->round_plan,
+                                s->status_dev, s->status, stream));
+  const int b = s->sorted_in_alt ? 1 : 0;
+  A3FR_CHECK(launch_composite(cp, s->rec, s->desc.n, s->ranges, s->counts, s->tvals[b], s->gaze_dev,
+                              s->round_plan, 0, s->cur_level, s->plan, out, s->levels,
+                              s->keep_aux ? s->t_final : nullptr,
+                              s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
+  s->launches += 3;
+  s->last_stream = stream;
   return A3FR_OK;
 }
 
@@ -512,6 +586,19 @@ int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3f
     if ((e = cudaEventCreateWithFlags(&s->gaze_consumed[k], cudaEventDisableTiming)) != cudaSuccess)
       return fail(cuda_fail(e, "cudaEventCreate"));
   }
+  if ((e = cudaMalloc(&s->round_state, sizeof(RoundState))) != cudaSuccess ||
+      (e = cudaMalloc(&s->round_plan, sizeof(RoundPlan))) != cudaSuccess ||
+      (e = cudaMemset(s->round_state, 0, sizeof(RoundState))) != cudaSuccess ||
+      (e = cudaMemset(s->round_plan, 0, sizeof(RoundPlan))) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaMalloc(round state)"));
+  if ((e = cudaHostAlloc(&s->mbox_host, sizeof(Mailbox), cudaHostAllocMapped)) != cudaSuccess ||
+      (e = cudaHostAlloc(&s->status_host, sizeof(RoundStatus), cudaHostAllocMapped)) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaHostAlloc(mailbox)"));
+  std::memset(s->mbox_host, 0, sizeof(Mailbox));
+  std::memset(s->status_host, 0, sizeof(RoundStatus));
+  if ((e = cudaHostGetDevicePointer(&s->mbox_dev, s->mbox_host, 0)) != cudaSuccess ||
+      (e = cudaHostGetDevicePointer(&s->status_dev, s->status_host, 0)) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaHostGetDevicePointer(mailbox)"));
   if (!s->auto_capacity) {
     rc = alloc_instances(s, instance_capacity);
     if (rc != A3FR_OK) return fail(rc);
@@ -528,6 +615,10 @@ int a3fr_destroy_scene(a3fr_scene *s) {
   free_instance_buffers(s);
   dfree(s->frame_ws);
   dfree(s->gaze_dev);
+  dfree(s->round_state);
+  dfree(s->round_plan);
+  if (s->mbox_host) cudaFreeHost(s->mbox_host);
+  if (s->status_host) cudaFreeHost(s->status_host);
   if (s->small) cudaFree(s->small);
   if (s->gaze_pinned) cudaFreeHost(s->gaze_pinned);
   for (int k = 0; k < kSlots; ++k) {
@@ -570,12 +661,63 @@ int a3fr_set_gaze(a3fr_scene *s, const float *gaze_px, void *side_stream) {
 
 int a3fr_render_foveated(a3fr_scene *s, const a3fr_fovea *fovea, float *out_rgb, void *stream) {
   if (!s || !fovea) return A3FR_ERR_INVALID_ARG;
-  return render(s, fovea, out_rgb, static_cast<cudaStream_t>(stream));
+  return render(s, fovea, out_rgb, static_cast<cudaStream_t>(stream), Mode::kFoveated);
 }
 
 int a3fr_render_full(a3fr_scene *s, float *out_rgb, void *stream) {
   if (!s) return A3FR_ERR_INVALID_ARG;
-  return render(s, nullptr, out_rgb, static_cast<cudaStream_t>(stream));
+  return render(s, nullptr, out_rgb, static_cast<cudaStream_t>(stream), Mode::kFull);
+}
+
+int a3fr_begin_frame(a3fr_scene *s, const a3fr_fovea *fovea, const a3fr_rounds *rounds,
+                     float *out_rgb, void *stream) {
+  if (!s || !fovea || !rounds || !out_rgb) return A3FR_ERR_INVALID_ARG;
+  if (rounds->n_exits < 1 || rounds->n_exits > A3FR_MAX_EXITS || !(rounds->sir_step_px >= 0.0f))
+    return A3FR_ERR_INVALID_ARG;
+  for (int i = 0; i < rounds->n_exits; ++i)
+    if (!(rounds->expected_dist_px[i] >= 0.0f)) return A3FR_ERR_INVALID_ARG;
+  const int eyes = n_eyes_of(s);
+  if (eyes == 0) return A3FR_ERR_INVALID_ARG;
+  RoundConfig c{};
+  c.n_eyes = eyes;
+  c.n_exits = rounds->n_exits;
+  c.sir = rounds->sir != 0;
+  c.step = rounds->sir_step_px;
+  c.n_layers = fovea->n_layers;
+  for (int i = 0; i < rounds->n_exits; ++i) c.expected[i] = rounds->expected_dist_px[i];
+  for (int e = 0; e < eyes; ++e)
+    for (int k = 0; k < 3; ++k) c.rf[e][k] = std::sqrt(layer_radius2(s->cams[e].fx,
+                                                                        fovea->theta_deg[k],
+                                                                        fovea->dtheta_deg));
+  s->round_ready = false;
+  const int rc = render(s, fovea, out_rgb, static_cast<cudaStream_t>(stream), Mode::kFirstRound);
+  if (rc != A3FR_OK) return rc;
+  s->round_fovea = *fovea;
+  s->round_cfg = c;
+  return A3FR_OK;
+}
+
+int a3fr_post_prediction(a3fr_scene *s, int exit_index, const float *gaze_px) {
+  if (!s || !gaze_px || exit_index < 1 || exit_index > A3FR_MAX_EXITS) return A3FR_ERR_INVALID_ARG;
+  const int eyes = n_eyes_of(s);
+  if (eyes == 0) return A3FR_ERR_INVALID_ARG;
+  post_mailbox(s, exit_index, gaze_px, eyes);
+  return A3FR_OK;
+}
+
+int a3fr_render_round(a3fr_scene *s, float *out_rgb, void *stream) {
+  if (!s) return A3FR_ERR_INVALID_ARG;
+  return render_round(s, out_rgb, static_cast<cudaStream_t>(stream));
+}
+
+int a3fr_get_round_status(a3fr_scene *s, a3fr_round_status *out) {
+  if (!s || !out) return A3FR_ERR_INVALID_ARG;
+  const volatile RoundStatus *v = s->status_host;
+  out->exit_consumed = v->exit_consumed;
+  out->complete = v->complete;
+  out->rounds = v->rounds;
+  for (int k = 0; k < 3; ++k) out->radius_px[k] = v->radius[k];
+  return A3FR_OK;
 }
 
 int a3fr_set_keep_aux(a3fr_scene *s, int keep) {

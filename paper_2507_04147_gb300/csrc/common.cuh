@@ -134,15 +134,59 @@ struct CompositeParams {
   float r2[kMaxEyes][3];    // squared layer radii per eye
 };
 
-// Bytes of the level plan of launch_composite for n_ranges = n_eyes * n_tiles.
+// Per-round parameters of an incremental round, written on the device by round_begin.
+struct RoundPlan {
+  float r2[kMaxEyes][3];    // squared layer radii of this round, per eye
+  float gaze[kMaxEyes][2];  // gaze of this round, per eye
+  int active;               // 0: nothing to render this round
+  int pad[3];
+};
+
+// Bytes of the work plan of launch_composite for n_ranges = n_eyes * n_tiles.
 size_t plan_bytes(int n_ranges);
-// Foveated: computes the tile levels from the gaze, buckets the tiles by level into `plan`,
-// then composites; full (p.full): every tile at level 4, plan unused.  Ranges are clamped to
-// kept[0] (the instances the sort kept).
+// One composite launch (plan kernel + composite).  p.full: every tile at level 4, no plan.
+// Otherwise the plan gives each tile labels (lo, hi]: a normal foveated render uses the gaze
+// (round == nullptr, uniform == 0); the first round of a frame renders every tile at level
+// `uniform` from label 0 and sets cur; a later round (round != nullptr) renders from cur up
+// to the level of its gaze and radii, stores only those pixels, and raises cur.  Ranges are
+// clamped to kept[0] (the instances the sort kept).
 cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
                              const uint2 *ranges, const uint32_t *kept, const uint32_t *vals,
-                             const float *gaze, uint32_t *plan, float *out, uint8_t *levels,
+                             const float *gaze, const RoundPlan *round, int uniform,
+                             uint8_t *cur, uint32_t *plan, float *out, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, unsigned long long *counters,
                              cudaStream_t s);
+
+// Incremental rounds (Sec. 3.3, Alg. 1): state on the device, mailbox in mapped host memory.
+struct RoundConfig {
+  int n_eyes, n_exits, sir;
+  float rf[kMaxEyes][3];     // final layer radii r_{f,N} per eye (pixels)
+  float expected[8];         // E[dist(u_i, u_N)] per exit i = 1..N (pixels), index i - 1
+  float step;                // SIR growth per speculative round (pixels)
+  int n_layers;
+};
+struct RoundState {
+  int last_exit;             // exit index of the last prediction consumed (0 = none)
+  int rounds;
+  int complete;
+  int pad;
+  float gaze[kMaxEyes][2];
+  float r[kMaxEyes][3];      // current layer radii
+};
+// Mapped mailbox written by the host: seq is odd while a write is in progress.
+struct Mailbox {
+  unsigned int seq;
+  int exit;
+  float gaze[kMaxEyes][2];
+};
+// Status mirrored to mapped host memory after each round (read without a sync).
+struct RoundStatus {
+  int exit_consumed, complete, rounds, pad;
+  float radius[3];
+  float pad2;
+};
+cudaError_t launch_round_begin(const RoundConfig &c, const Mailbox *mbox, RoundState *state,
+                               RoundPlan *plan, RoundStatus *status, uint32_t *error_status,
+                               cudaStream_t s);
 
 }  // namespace a3fr

@@ -58,28 +58,52 @@ __device__ __forceinline__ int tile_level(const CompositeParams &p, int eye, int
   return p.level[layer];
 }
 
-// Buckets the tiles by level: plan[(level - 1) * n_ranges + slot], counts[level - 1].
+// Work plan of one composite launch.  Each tile gets a label interval (lo, hi] to render;
+// entries (tile << 2 | lo) are bucketed by hi - lo in plan[(hi - lo - 1) * n_ranges + slot]
+// with the bucket sizes in plan_counts[0..3].  Three uses:
+//   * a normal foveated render: lo = 0, hi = the tile's level from the gaze mailbox;
+//   * the first round of a frame (uniform > 0): lo = 0, hi = uniform for every tile;
+//   * a later round (round != nullptr): hi = the level from the round's gaze and radii, lo =
+//     the level already rendered (cur); tiles with hi <= lo get no entry; cur becomes hi.
 __global__ void __launch_bounds__(256)
-fovea_plan_kernel(CompositeParams p, const float *__restrict__ gaze, uint8_t *__restrict__ levels,
-                  uint32_t *__restrict__ plan, uint32_t *__restrict__ plan_counts) {
+plan_kernel(CompositeParams p, const float *__restrict__ gaze, const RoundPlan *__restrict__ round,
+            int uniform, uint8_t *__restrict__ cur, uint8_t *__restrict__ levels,
+            uint32_t *__restrict__ plan, uint32_t *__restrict__ plan_counts) {
   const int n_ranges = p.n_eyes * p.n_tiles;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  int level = 0;
+  int lo = 0, count = 0;
   if (gt < n_ranges) {
     const int eye = gt / p.n_tiles;
-    level = tile_level(p, eye, gt - eye * p.n_tiles, gaze);
-    levels[gt] = (uint8_t)level;
+    const int tile = gt - eye * p.n_tiles;
+    int hi;
+    if (uniform > 0) {
+      hi = uniform;
+    } else if (round != nullptr) {
+      hi = 0;
+      if (round->active) {
+        CompositeParams q = p;
+        for (int k = 0; k < 3; ++k) q.r2[eye][k] = round->r2[eye][k];
+        hi = tile_level(q, eye, tile, &round->gaze[0][0]);
+      }
+      lo = cur[gt];
+    } else {
+      hi = tile_level(p, eye, tile, gaze);
+    }
+    count = hi > lo ? hi - lo : 0;
+    if (cur != nullptr && hi > lo) cur[gt] = (uint8_t)hi;
+    levels[gt] = (uint8_t)(hi > lo ? hi : lo);
   }
-  for (int L = 1; L <= 4; ++L) {
-    const unsigned m = __ballot_sync(0xffffffffu, level == L);
+  for (int c = 1; c <= 4; ++c) {
+    const unsigned m = __ballot_sync(0xffffffffu, count == c);
     if (!m) continue;
     const int leader = __ffs(m) - 1;
     uint32_t base = 0;
-    if (lane == leader) base = atomicAdd(plan_counts + (L - 1), (uint32_t)__popc(m));
+    if (lane == leader) base = atomicAdd(plan_counts + (c - 1), (uint32_t)__popc(m));
     base = __shfl_sync(0xffffffffu, base, leader);
-    if (level == L)
-      plan[(size_t)(L - 1) * n_ranges + base + __popc(m & ((1u << lane) - 1u))] = (uint32_t)gt;
+    if (count == c)
+      plan[(size_t)(c - 1) * n_ranges + base + __popc(m & ((1u << lane) - 1u))] =
+          ((uint32_t)gt << 2) | (uint32_t)lo;
   }
 }
 
@@ -120,9 +144,10 @@ __global__ void __launch_bounds__(kThreads, 6)
 composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
                  const uint32_t *__restrict__ vals, const uint32_t *__restrict__ plan,
-                 const uint32_t *__restrict__ plan_counts, float *__restrict__ out,
-                 uint8_t *__restrict__ levels, float *__restrict__ t_final,
-                 uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ counters) {
+                 const uint32_t *__restrict__ plan_counts, int incremental,
+                 float *__restrict__ out, uint8_t *__restrict__ levels,
+                 float *__restrict__ t_final, uint32_t *__restrict__ n_contrib,
+                 unsigned long long *__restrict__ counters) {
   __shared__ float4 s_geo[kThreads];   // u, v, -0.5 log2e a, -log2e b
   __shared__ float4 s_co[kThreads];    // -0.5 log2e c, log2 threshold, -, -
   __shared__ float4 s_rgb[kThreads];   // r, g, b, opacity
@@ -132,8 +157,9 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n_ranges = p.n_eyes * p.n_tiles;
 
-  // ---- which tile, which label group (two warps each), which staging group
-  int gtile = -1, group = warp >> 1, level = 4, gsize = kThreads, gbar = 1, gfirst = 0;
+  // ---- which tile, which labels (lo, level], which staging group; a label group is
+  // two warps, and group = the label index (0 = top-left) this warp pair renders
+  int gtile = -1, group = warp >> 1, level = 4, lo = 0, gsize = kThreads, gbar = 1, gfirst = 0;
   if (kFull) {
     gtile = blockIdx.x;
     if (threadIdx.x == 0) levels[gtile] = 4;
@@ -141,33 +167,39 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
     const int c = blockIdx.x;
     const int n4 = plan_counts[3], n3 = plan_counts[2], n2 = plan_counts[1], n1 = plan_counts[0];
     const int c3 = n4 + n3, c2 = c3 + (n2 + 1) / 2, c1 = c2 + (n1 + 3) / 4;
+    uint32_t entry = 0xffffffffu;
+    int count = 4;
     if (c < n4) {
-      gtile = plan[3 * (size_t)n_ranges + c];
+      entry = plan[3 * (size_t)n_ranges + c];
     } else if (c < c3) {
-      gtile = plan[2 * (size_t)n_ranges + (c - n4)];
-      level = 3;
+      entry = plan[2 * (size_t)n_ranges + (c - n4)];
+      count = 3;
     } else if (c < c2) {
       const int half = warp >> 2;
       const int slot = 2 * (c - c3) + half;
-      level = 2;
+      count = 2;
       group = (warp >> 1) & 1;
       gsize = 128;
       gbar = 1 + half;
       gfirst = half * 128;
-      gtile = slot < n2 ? (int)plan[(size_t)n_ranges + slot] : -1;
+      if (slot < n2) entry = plan[(size_t)n_ranges + slot];
     } else if (c < c1) {
       const int quarter = warp >> 1;
       const int slot = 4 * (c - c2) + quarter;
-      level = 1;
+      count = 1;
       group = 0;
       gsize = 64;
       gbar = 1 + quarter;
       gfirst = quarter * 64;
-      gtile = slot < n1 ? (int)plan[slot] : -1;
+      if (slot < n1) entry = plan[slot];
     } else {
       return;
     }
-    if (gtile < 0) return;   // a partly filled pair or quad: these warps have no tile
+    if (entry == 0xffffffffu) return;   // a partly filled pair or quad: these warps have no tile
+    gtile = (int)(entry >> 2);
+    lo = (int)(entry & 3u);
+    level = lo + count;
+    group += lo;
   }
   const int eye = gtile / p.n_tiles;
   const int tile = gtile - eye * p.n_tiles;
@@ -178,7 +210,7 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
   const int oy = (group == 1 || group == 3) ? 1 : 0;   // BR, BL
   const int bx = lane & 7, by = (warp & 1) * 4 + (lane >> 3);
   const int px = tx * kTile + 2 * bx + ox, py = ty * kTile + 2 * by + oy;
-  const bool inside = group < level && px < p.width && py < p.height;
+  const bool inside = group >= lo && group < level && px < p.width && py < p.height;
   const float fpx = (float)px, fpy = (float)py;
 
   uint2 range = ranges[gtile];
@@ -195,6 +227,7 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
   if (kFull) {   // compile-time layout: one level-4 tile, the whole CTA stages together
     group = warp >> 1;
     level = 4;
+    lo = 0;
     gsize = kThreads;
     gbar = 1;
     gfirst = 0;
@@ -239,41 +272,54 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
   }
   if (inside && !done) stop = range.y - range.x;
 
-  // ---- outputs: the pixel, and for label 1 the inherited pixels of its block, are
-  // assembled in shared memory; the staging group then stores its tile row by row
-  const int slot = gfirst >> 6 >> (gsize == 256 ? 2 : (gsize == 128 ? 1 : 0));   // tile slot
-  const int lx = 2 * bx + ox, ly = 2 * by + oy;
-  if (inside) {
-    float *o = &s_out[slot][ly][3 * lx];
-    o[0] = C0;
-    o[1] = C1;
-    o[2] = C2;
-    if (kAux) {
-      const size_t pix = ((size_t)eye * p.height + py) * p.width + px;
-      t_final[pix] = T;
-      n_contrib[pix] = last;
+  // ---- outputs.  A tile rendered from label 0 is assembled in shared memory (its pixel,
+  // and for label 1 the inherited pixels of its block) and stored row by row; a later
+  // round (lo > 0) stores only the pixels it rendered, keeping the others.
+  if (!kFull && incremental) {
+    if (inside) {
+      float *o = out + (((size_t)eye * p.height + py) * p.width + px) * 3;
+      o[0] = C0;
+      o[1] = C1;
+      o[2] = C2;
+      if (kAux) {
+        const size_t pix = ((size_t)eye * p.height + py) * p.width + px;
+        t_final[pix] = T;
+        n_contrib[pix] = last;
+      }
     }
-    if (group == 0) {
+  } else {
+    const int slot = gfirst >> 6 >> (gsize == 256 ? 2 : (gsize == 128 ? 1 : 0));   // tile slot
+    const int lx = 2 * bx + ox, ly = 2 * by + oy;
+    if (inside) {
+      float *o = &s_out[slot][ly][3 * lx];
+      o[0] = C0;
+      o[1] = C1;
+      o[2] = C2;
+      if (kAux) {
+        const size_t pix = ((size_t)eye * p.height + py) * p.width + px;
+        t_final[pix] = T;
+        n_contrib[pix] = last;
+      }
+      if (group == 0) {
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        // inherited pixels of the block: BR (label 2), TR (label 3), BL (label 4)
-        const int dx = k < 2 ? 1 : 0, dy = k == 1 ? 0 : 1;
-        if (level < k + 2 && px + dx < p.width && py + dy < p.height) {
-          float *f = &s_out[slot][ly + dy][3 * (lx + dx)];
-          f[0] = C0;
-          f[1] = C1;
-          f[2] = C2;
-          if (kAux) {
-            const size_t pix = ((size_t)eye * p.height + py + dy) * p.width + px + dx;
-            t_final[pix] = T;
-            n_contrib[pix] = last;
+        for (int k = 0; k < 3; ++k) {
+          // inherited pixels of the block: BR (label 2), TR (label 3), BL (label 4)
+          const int dx = k < 2 ? 1 : 0, dy = k == 1 ? 0 : 1;
+          if (level < k + 2 && px + dx < p.width && py + dy < p.height) {
+            float *f = &s_out[slot][ly + dy][3 * (lx + dx)];
+            f[0] = C0;
+            f[1] = C1;
+            f[2] = C2;
+            if (kAux) {
+              const size_t pix = ((size_t)eye * p.height + py + dy) * p.width + px + dx;
+              t_final[pix] = T;
+              n_contrib[pix] = last;
+            }
           }
         }
       }
     }
-  }
-  group_sync(gsize, gbar);
-  {
+    group_sync(gsize, gbar);
     const int w_tile = min(kTile, p.width - tx * kTile);
     const int h_tile = min(kTile, p.height - ty * kTile);
     const size_t row = (size_t)p.width * 3;
@@ -300,16 +346,18 @@ size_t plan_bytes(int n_ranges) { return sizeof(uint32_t) * (4 * (size_t)n_range
 
 cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
                              const uint2 *ranges, const uint32_t *kept, const uint32_t *vals,
-                             const float *gaze, uint32_t *plan, float *out, uint8_t *levels,
+                             const float *gaze, const RoundPlan *round, int uniform,
+                             uint8_t *cur, uint32_t *plan, float *out, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, unsigned long long *counters,
                              cudaStream_t s) {
   const int n_ranges = p.n_eyes * p.n_tiles;
   if (n_ranges <= 0) return cudaSuccess;
-  uint32_t *plan_counts = plan + 4 * (size_t)n_ranges;
+  uint32_t *pc = plan + 4 * (size_t)n_ranges;
   if (!p.full) {
-    cudaError_t e = cudaMemsetAsync(plan_counts, 0, 4 * sizeof(uint32_t), s);
+    cudaError_t e = cudaMemsetAsync(pc, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    fovea_plan_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p, gaze, levels, plan, plan_counts);
+    plan_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p, gaze, round, uniform, cur, levels, plan,
+                                                       pc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -324,25 +372,21 @@ cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
     cudaFuncSetAttribute(composite_kernel<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
     carveout_set[dev] = true;
   }
-  const uint32_t *pc = plan_counts;
+  const int inc = round != nullptr ? 1 : 0;
   if (t_final != nullptr) {
     if (p.full)
-      composite_kernel<true, true><<<n_ranges, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, plan,
-                                                                 pc, out, levels, t_final, n_contrib,
-                                                                 counters);
+      composite_kernel<true, true><<<n_ranges, kThreads, 0, s>>>(
+          p, rec, n, ranges, kept, vals, plan, pc, 0, out, levels, t_final, n_contrib, counters);
     else
-      composite_kernel<true, false><<<n_ranges, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, plan,
-                                                                  pc, out, levels, t_final, n_contrib,
-                                                                  counters);
+      composite_kernel<true, false><<<n_ranges, kThreads, 0, s>>>(
+          p, rec, n, ranges, kept, vals, plan, pc, inc, out, levels, t_final, n_contrib, counters);
   } else {
     if (p.full)
-      composite_kernel<false, true><<<n_ranges, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals, plan,
-                                                                  pc, out, levels, t_final, n_contrib,
-                                                                  counters);
+      composite_kernel<false, true><<<n_ranges, kThreads, 0, s>>>(
+          p, rec, n, ranges, kept, vals, plan, pc, 0, out, levels, t_final, n_contrib, counters);
     else
-      composite_kernel<false, false><<<n_ranges, kThreads, 0, s>>>(p, rec, n, ranges, kept, vals,
-                                                                   plan, pc, out, levels, t_final,
-                                                                   n_contrib, counters);
+      composite_kernel<false, false><<<n_ranges, kThreads, 0, s>>>(
+          p, rec, n, ranges, kept, vals, plan, pc, inc, out, levels, t_final, n_contrib, counters);
   }
   return cudaGetLastError();
 }
