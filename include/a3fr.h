@@ -167,6 +167,40 @@ int a3fr_render_round(a3fr_scene *scene, float *out_rgb, void *stream);
 /* Status of the last completed round, read from mapped host memory (no synchronisation). */
 int a3fr_get_round_status(a3fr_scene *scene, a3fr_round_status *status);
 
+/* ---- one frame of Algorithm 1, natively timed ---- */
+#define A3FR_DRIVE_A3FR 0  /* rounds overlapped with tracking (SIR per rounds->sir) */
+#define A3FR_DRIVE_SFR 1   /* sequential: wait for the final prediction, then render foveated */
+#define A3FR_DRIVE_FRR 2   /* full resolution, no tracking */
+
+typedef struct {
+  int32_t mode;                    /* A3FR_DRIVE_* */
+  int32_t n_exits;                 /* must equal rounds->n_exits */
+  const float *predictions;        /* HOST [n_exits][eyes][2]: u_1..u_N in pixels */
+  const double *exit_time_us;      /* HOST [n_exits]: time each prediction is ready, unloaded */
+  double load_period_us;           /* > 0: tracker intervals in every odd period are stretched */
+  double load_factor;              /*   by this factor (alternating CPU load, Sec. 4.5) */
+  int32_t max_rounds;              /* bound on the rounds launched after the first */
+} a3fr_frame_driver;
+
+typedef struct {
+  double latency_us;               /* frame start -> completion of its last needed GPU work */
+  double tracker_end_us;           /* when the tracker thread posted its last prediction */
+  int32_t rounds;                  /* rounds launched after the first (1 for SFR/FRR) */
+  int32_t exit_per_round[16];      /* exit consumed by each of the first 16 rounds */
+  double round_end_us[16];         /* completion time of each of the first 16 rounds */
+} a3fr_frame_result;
+
+/* Render one frame the way Algorithm 1 runs its two processes: a host thread posts
+ * drv->predictions at drv->exit_time_us (process 1) while this thread begins the frame and
+ * launches rounds until the final prediction's region is rendered (process 2); a round
+ * without a new prediction speculates (Eq. 4) when rounds->sir is set and the region can
+ * still grow, otherwise this thread waits for the next prediction.  SFR and FRR modes run the
+ * sequential and full-resolution baselines with the same clock.  Synchronous; the cameras
+ * must be set. */
+int a3fr_run_frame(a3fr_scene *scene, const a3fr_fovea *fovea, const a3fr_rounds *rounds,
+                   const a3fr_frame_driver *driver, float *out_rgb, void *stream,
+                   a3fr_frame_result *result);
+
 /* Keep per-pixel transmittance and contributor counts of the next renders (aux buffers,
  * see a3fr_copy_buffer); off by default because they cost 8 bytes per pixel. */
 int a3fr_set_keep_aux(a3fr_scene *scene, int keep);

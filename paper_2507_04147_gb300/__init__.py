@@ -23,7 +23,7 @@ __all__ = ["Scene", "Fovea", "A3FRError", "camera_struct", "create_scene", "dest
            "set_camera", "set_gaze", "render_foveated", "render_full", "get_stats",
            "set_keep_aux", "set_stage_timing", "get_stage_times", "copy_buffer", "sort_pairs", "sort_pairs_workspace_bytes",
            "sort_pairs_noalloc", "Rounds", "begin_frame", "post_prediction", "render_round",
-           "get_round_status",
+           "get_round_status", "run_frame",
            "error_string"]
 
 
@@ -193,6 +193,25 @@ def get_round_status(handle: int) -> dict:
     _lib.check(_lib.load().a3fr_get_round_status(handle, ctypes.byref(st)), "a3fr_get_round_status")
     return {"exit_consumed": st.exit_consumed, "complete": st.complete, "rounds": st.rounds,
             "radius_px": [st.radius_px[0], st.radius_px[1], st.radius_px[2]]}
+
+
+def run_frame(handle: int, fovea, rounds, predictions, exit_time_us, out_rgb, mode: int = 0,
+              load_period_us: float = 0.0, load_factor: float = 1.0, max_rounds: int = 64,
+              stream=None) -> dict:
+    """One frame of Algorithm 1 in native code (see a3fr_run_frame)."""
+    pred = np.ascontiguousarray(np.asarray(predictions, dtype=np.float32))
+    times = np.ascontiguousarray(np.asarray(exit_time_us, dtype=np.float64))
+    d = _lib.FrameDriver()
+    d.mode, d.n_exits = int(mode), int(len(times))
+    d.predictions, d.exit_time_us = pred.ctypes.data, times.ctypes.data
+    d.load_period_us, d.load_factor, d.max_rounds = float(load_period_us), float(load_factor), int(max_rounds)
+    r = _lib.FrameResult()
+    _lib.check(_lib.load().a3fr_run_frame(handle, ctypes.byref(fovea), ctypes.byref(rounds),
+                                          ctypes.byref(d), _ptr(out_rgb), _stream_ptr(stream),
+                                          ctypes.byref(r)), "a3fr_run_frame")
+    k = min(r.rounds, 16)
+    return {"latency_us": r.latency_us, "tracker_end_us": r.tracker_end_us, "rounds": r.rounds,
+            "exits": list(r.exit_per_round[:k]), "round_end_us": list(r.round_end_us[:k])}
 
 
 def error_string(code: int) -> str:

@@ -62,6 +62,22 @@ class RoundStatus(ctypes.Structure):
                 ("rounds", ctypes.c_int32), ("radius_px", ctypes.c_float * 3)]
 
 
+DRIVE_A3FR, DRIVE_SFR, DRIVE_FRR = 0, 1, 2
+
+
+class FrameDriver(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("n_exits", ctypes.c_int32),
+                ("predictions", ctypes.c_void_p), ("exit_time_us", ctypes.c_void_p),
+                ("load_period_us", ctypes.c_double), ("load_factor", ctypes.c_double),
+                ("max_rounds", ctypes.c_int32)]
+
+
+class FrameResult(ctypes.Structure):
+    _fields_ = [("latency_us", ctypes.c_double), ("tracker_end_us", ctypes.c_double),
+                ("rounds", ctypes.c_int32), ("exit_per_round", ctypes.c_int32 * 16),
+                ("round_end_us", ctypes.c_double * 16)]
+
+
 class A3FRError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str = ""):
         self.code = code
@@ -96,6 +112,9 @@ _SIGS = {
     "a3fr_post_prediction": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "a3fr_render_round": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "a3fr_get_round_status": ([ctypes.c_void_p, ctypes.POINTER(RoundStatus)], ctypes.c_int),
+    "a3fr_run_frame": ([ctypes.c_void_p, ctypes.POINTER(Fovea), ctypes.POINTER(Rounds),
+                        ctypes.POINTER(FrameDriver), ctypes.c_void_p, ctypes.c_void_p,
+                        ctypes.POINTER(FrameResult)], ctypes.c_int),
     "a3fr_set_stage_timing": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_get_stage_times": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                               ctypes.POINTER(ctypes.c_int)], ctypes.c_int),

@@ -541,6 +541,8 @@ int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
 
 }  // namespace
 
+int a3fr::scene_eyes(const a3fr_scene *s) { return n_eyes_of(s); }
+
 extern "C" {
 
 int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3fr_scene **out) {

@@ -185,6 +185,13 @@ struct RoundStatus {
   float radius[3];
   float pad2;
 };
+}  // namespace a3fr
+
+struct a3fr_scene;
+namespace a3fr {
+// Eyes rendered by a scene (eyes with a camera).
+int scene_eyes(const a3fr_scene *s);
+
 cudaError_t launch_round_begin(const RoundConfig &c, const Mailbox *mbox, RoundState *state,
                                RoundPlan *plan, RoundStatus *status, uint32_t *error_status,
                                cudaStream_t s);

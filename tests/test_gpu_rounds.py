@@ -114,3 +114,30 @@ def test_round_before_begin_frame_is_not_ready():
     s.render_foveated()                         # a normal render does not begin a frame
     with pytest.raises(a3fr.A3FRError, match="NOT_READY"):
         s.render_round(out)
+
+
+def test_native_frame_driver_modes():
+    import torch
+    scene_np, cams, s, out = _setup(n=20000, w=256, h=256, stereo=True)
+    from paper_2507_04147_gb300 import rounds as prounds
+    gfv = a3fr.Fovea()
+    f = cams[0].fx
+    expected = prounds.profile_expected_distances(f_px=f, samples=20000)
+    preds = prounds.synthetic_predictions([[128.0, 128.0], [128.0, 128.0]], f_px=f, seed=1)
+    times = np.array(prounds.TABLE2_CUM_LATENCY_MS) * 50.0      # microseconds, scaled
+    st = torch.cuda.current_stream()
+    res = {}
+    for mode, sir in ((0, True), (0, False), (1, True), (2, True)):
+        out.zero_()
+        res[(mode, sir)] = a3fr.run_frame(s.handle, gfv, a3fr.Rounds(expected, sir=sir), preds, times,
+                                          out, mode=mode, stream=st)
+    a = res[(0, True)]
+    assert a["latency_us"] > 0 and a["exits"][-1] == 6 and a["rounds"] >= 1
+    assert res[(0, False)]["exits"][-1] == 6
+    # without speculation every round uses a new prediction
+    ex = res[(0, False)]["exits"]
+    assert all(x < y for x, y in zip(ex, ex[1:]))
+    assert res[(1, True)]["latency_us"] >= times[-1]         # SFR waits for the final prediction
+    assert res[(2, True)]["latency_us"] > 0                  # FRR does not wait
+    # the A3FR frame ends no earlier than the final prediction
+    assert a["latency_us"] >= times[-1]
