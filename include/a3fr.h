@@ -201,6 +201,15 @@ int a3fr_run_frame(a3fr_scene *scene, const a3fr_fovea *fovea, const a3fr_rounds
                    const a3fr_frame_driver *driver, float *out_rgb, void *stream,
                    a3fr_frame_result *result);
 
+/* Graph mode (default off): renders replay two captured CUDA graphs -- the precompute and
+ * the composite (foveated or full) -- instead of launching ~20 operations each; the gaze wait
+ * sits between them, so the precompute still overlaps the tracker.  Per-render parameters
+ * (cameras, layer radii, gaze slot, output pointer) live in device memory and one copy per
+ * render updates them.  Graphs are captured at the first render that can use them and again
+ * whenever a workspace buffer moves; renders with stage timing on, the first render of an
+ * automatic-capacity scene and the rounds API launch directly. */
+int a3fr_set_graph_mode(a3fr_scene *scene, int on);
+
 /* Keep per-pixel transmittance and contributor counts of the next renders (aux buffers,
  * see a3fr_copy_buffer); off by default because they cost 8 bytes per pixel. */
 int a3fr_set_keep_aux(a3fr_scene *scene, int keep);

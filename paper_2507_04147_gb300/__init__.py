@@ -21,7 +21,7 @@ from ._lib import A3FRError, BUF_KEYS, BUF_LEVELS, BUF_N_CONTRIB, BUF_RANGES, BU
 
 __all__ = ["Scene", "Fovea", "A3FRError", "camera_struct", "create_scene", "destroy_scene",
            "set_camera", "set_gaze", "render_foveated", "render_full", "get_stats",
-           "set_keep_aux", "set_stage_timing", "get_stage_times", "copy_buffer", "sort_pairs", "sort_pairs_workspace_bytes",
+           "set_keep_aux", "set_graph_mode", "set_stage_timing", "get_stage_times", "copy_buffer", "sort_pairs", "sort_pairs_workspace_bytes",
            "sort_pairs_noalloc", "Rounds", "begin_frame", "post_prediction", "render_round",
            "get_round_status", "run_frame",
            "error_string"]
@@ -122,6 +122,10 @@ def get_stage_times(handle: int, max_renders: int) -> np.ndarray:
     _lib.check(_lib.load().a3fr_get_stage_times(handle, max_renders, ms.ctypes.data,
                                                 ctypes.byref(k)), "a3fr_get_stage_times")
     return ms[:k.value]
+
+
+def set_graph_mode(handle: int, on: bool) -> None:
+    _lib.check(_lib.load().a3fr_set_graph_mode(handle, int(on)), "a3fr_set_graph_mode")
 
 
 def set_keep_aux(handle: int, keep: bool) -> None:
@@ -310,6 +314,9 @@ class Scene:
 
     def stage_times(self, max_renders: int) -> np.ndarray:
         return get_stage_times(self.handle, max_renders)
+
+    def graph_mode(self, on: bool = True):
+        set_graph_mode(self.handle, on)
 
     def keep_aux(self, keep: bool = True):
         set_keep_aux(self.handle, keep)

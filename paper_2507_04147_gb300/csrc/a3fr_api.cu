@@ -113,6 +113,23 @@ struct a3fr_scene {
   RoundStatus *status_dev = nullptr;
   std::mutex mbox_mutex;
   float *out_round = nullptr;                // the canvas of the frame's rounds
+
+  // per-render parameters: device copy, pinned staging ring, completion of the last render
+  DevParams *params_dev = nullptr;
+  DevParams *params_pinned = nullptr;        // [kSlots]
+  cudaEvent_t params_copied[kSlots]{};
+  bool params_used[kSlots]{};
+  uint64_t params_seq = 0;
+  cudaEvent_t render_done = nullptr;
+  bool render_done_recorded = false;
+
+  // CUDA graphs of the precompute and of the composite (foveated / full)
+  bool graph_mode = false;
+  uint64_t alloc_gen = 1;                    // bumped whenever a workspace buffer moves
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t g_pre = nullptr, g_fov = nullptr, g_full = nullptr;
+  uint64_t g_pre_key = 0, g_fov_key = 0, g_full_key = 0;
+  uint64_t g_pre_launches = 0;               // kernels in the precompute graph
 };
 
 namespace {
@@ -185,6 +202,7 @@ int ensure_frame_ws(a3fr_scene *s) {
     A3FR_CHECK(cudaDeviceSynchronize());
     dfree(s->frame_ws);
   }
+  s->alloc_gen++;
   A3FR_CHECK(cudaMalloc(&s->frame_ws, L.total));
   A3FR_CHECK(cudaMemset(s->frame_ws, 0, L.total));
   s->frame_ws_bytes = L.total;
@@ -193,6 +211,7 @@ int ensure_frame_ws(a3fr_scene *s) {
 }
 
 int alloc_instances(a3fr_scene *s, size_t capacity) {
+  s->alloc_gen++;
   free_instance_buffers(s);
   s->capacity = capacity;
   if (capacity > 0) {
@@ -210,6 +229,7 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
   // a size change: wait for any render still using the old buffers
   if (s->alloc_eyes) A3FR_CHECK(cudaDeviceSynchronize());
   free_frame_buffers(s);
+  s->alloc_gen++;
   const int n = s->desc.n;
   const int tile = s->desc.tile;
   {
@@ -350,21 +370,42 @@ void post_mailbox(a3fr_scene *s, int exit, const float *gaze, int eyes) {
   __atomic_store_n(&m->seq, seq + 2u, __ATOMIC_RELEASE);
 }
 
-int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream, Mode mode) {
-  s->round_ready = false;   // any render replaces the precompute that rounds build on
-  const int eyes = n_eyes_of(s);
-  if (eyes == 0 || out == nullptr) return A3FR_ERR_INVALID_ARG;
-  const a3fr_camera &c0 = s->cams[0];
-  if (eyes == 2 && (s->cams[1].width != c0.width || s->cams[1].height != c0.height))
-    return A3FR_ERR_INVALID_ARG;
-  if (fv) {
-    if (fv->n_layers < 1 || fv->n_layers > 4) return A3FR_ERR_INVALID_ARG;
-    for (int k = 0; k < fv->n_layers; ++k)
-      if (fv->level[k] < 1 || fv->level[k] > 4) return A3FR_ERR_INVALID_ARG;
-    if (mode == Mode::kFoveated && s->gaze_seq < 0) return A3FR_ERR_NOT_READY;
-  }
-  int rc = ensure_frame_buffers(s, eyes, c0.width, c0.height);
-  if (rc != A3FR_OK) return rc;
+// Copies the per-render parameters to the device (pinned staging ring), after the previous
+// render of the scene is done with them.
+int upload_params(a3fr_scene *s, const DevParams &hp, cudaStream_t stream) {
+  const int slot = (int)(s->params_seq++ % kSlots);
+  if (s->params_used[slot]) A3FR_CHECK(cudaEventSynchronize(s->params_copied[slot]));
+  s->params_pinned[slot] = hp;
+  if (s->render_done_recorded) A3FR_CHECK(cudaStreamWaitEvent(stream, s->render_done, 0));
+  A3FR_CHECK(cudaMemcpyAsync(s->params_dev, s->params_pinned + slot, sizeof(DevParams),
+                             cudaMemcpyHostToDevice, stream));
+  A3FR_CHECK(cudaEventRecord(s->params_copied[slot], stream));
+  s->params_used[slot] = true;
+  return A3FR_OK;
+}
+
+int finish_render(a3fr_scene *s, cudaStream_t stream) {
+  A3FR_CHECK(cudaEventRecord(s->render_done, stream));
+  s->render_done_recorded = true;
+  return A3FR_OK;
+}
+
+PreParams pre_params(const a3fr_scene *s, int eyes) {
+  PreParams pp{};
+  for (int e = 0; e < eyes; ++e) pp.cam[e] = cam_params(s->cams[e]);
+  pp.shc = sh_consts();
+  pp.n_eyes = eyes;
+  pp.tile = s->desc.tile;
+  pp.tiles_x = s->TX;
+  pp.tiles_y = s->TY;
+  return pp;
+}
+
+// The precompute of a render: projection, depth sort, tile counts and ranges, emission and the
+// tile sort.  allow_resize: the first render of an automatic-capacity scene measures the
+// instance count (one host synchronisation) and sizes the instance buffers.
+int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
+                uint64_t *launches) {
   const int n = s->desc.n;
   const int n_entries = eyes * n;
   const int n_ranges = eyes * s->n_tiles;
@@ -383,34 +424,25 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
   uint32_t *depth_lb = reinterpret_cast<uint32_t *>(ws + L.depth_lb);
   uint32_t *tile_lb = reinterpret_cast<uint32_t *>(ws + L.tile_lb);
 
-  PreParams pp{};
-  for (int e = 0; e < eyes; ++e) pp.cam[e] = cam_params(s->cams[e]);
-  pp.shc = sh_consts();
-  pp.n_eyes = eyes;
-  pp.tile = s->desc.tile;
-  pp.tiles_x = s->TX;
-  pp.tiles_y = s->TY;
-
-  uint64_t launches = 0;
   A3FR_CHECK(mark(s, A3FR_STAGE_PREPROCESS, stream));
   A3FR_CHECK(cudaMemsetAsync(s->frame_ws, 0, L.total, stream));
   if (n > 0) {
-    A3FR_CHECK(launch_preprocess(pp, n, s->desc.sh_degree, s->desc.means, s->desc.log_scales,
-                                 s->desc.quats, s->desc.opacity_logits, s->desc.sh, s->rec,
-                                 s->rect, s->touched, s->dkeys[0], counts + 4, stream));
-    ++launches;
+    A3FR_CHECK(launch_preprocess(&s->params_dev->pre, n, s->desc.sh_degree, s->desc.means,
+                                 s->desc.log_scales, s->desc.quats, s->desc.opacity_logits,
+                                 s->desc.sh, s->rec, s->rect, s->touched, s->dkeys[0], counts + 4,
+                                 stream));
+    ++*launches;
   }
   // depth sort of the (eye, Gaussian) entries: 4 passes, result back in dkeys[0]/dvals[0]
   A3FR_CHECK(mark(s, A3FR_STAGE_DEPTH_SORT, stream));
   if (n > 0) {
     A3FR_CHECK(launch_histogram<uint32_t>(s->dkeys[0], counts + 4, (size_t)n_entries, depth_plan,
                                           depth_hist, stream));
-    ++launches;
     bool in_alt = false;
     A3FR_CHECK(launch_onesweep<uint32_t>(s->dkeys[0], s->dvals[0], s->dkeys[1], s->dvals[1], true,
                                          counts + 4, (size_t)n_entries, depth_plan, depth_hist,
                                          depth_ctr, depth_lb, s->status, &in_alt, stream));
-    launches += depth_plan.passes;
+    *launches += 1 + depth_plan.passes;
   }
   const uint32_t *entries = s->dvals[depth_plan.passes % 2];
   // per-tile counts -> ranges, tile-sort histograms, totals
@@ -425,11 +457,11 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
   tp.tile_plan = tile_plan;
   if (n > 0) {
     A3FR_CHECK(launch_tile_count(tp, s->rect, s->tile_partials, tile_diff, stream));
-    launches += 2;
+    *launches += 2;
   }
   A3FR_CHECK(launch_tile_scan(tp, tile_diff, s->ranges, tile_hist, counts, s->status, stream));
-  ++launches;
-  if (s->auto_capacity && s->capacity == 0 && n > 0) {
+  ++*launches;
+  if (allow_resize && s->auto_capacity && s->capacity == 0 && n > 0) {
     // first render: read the instance count once, then size the instance buffers
     uint32_t cnt[8];
     A3FR_CHECK(cudaMemcpyAsync(cnt, counts, sizeof cnt, cudaMemcpyDeviceToHost, stream));
@@ -440,7 +472,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
     void *old_ws = s->frame_ws;
     s->frame_ws = nullptr;
     s->frame_ws_bytes = 0;
-    rc = alloc_instances(s, want);
+    const int rc = alloc_instances(s, want);
     if (rc != A3FR_OK) {
       cudaFree(old_ws);
       return rc;
@@ -470,7 +502,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
   if (n > 0 && s->capacity > 0) {
     A3FR_CHECK(launch_emit(ep, entries, s->touched, s->rect, s->tkeys[0], s->tvals[0], emit_lb,
                            counts + 6, s->status, stream));
-    ++launches;
+    ++*launches;
   }
   A3FR_CHECK(mark(s, A3FR_STAGE_TILE_SORT, stream));
   bool in_alt = false;
@@ -478,20 +510,100 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
     A3FR_CHECK(launch_onesweep<uint32_t>(s->tkeys[0], s->tvals[0], s->tkeys[1], s->tvals[1], false,
                                          counts, s->capacity, tile_plan, tile_hist, tile_ctr,
                                          tile_lb, s->status, &in_alt, stream));
-    launches += tile_plan.passes;
+    *launches += tile_plan.passes;
   }
   s->sorted_in_alt = in_alt;
-  const int b = in_alt ? 1 : 0;
+  return A3FR_OK;
+}
 
-  CompositeParams cp = composite_params(s, eyes, mode == Mode::kFull ? nullptr : fv);
-  const float *gaze = s->gaze_dev;   // not read by full renders and first rounds
+// The composite of a render (plan + composite, or composite alone for full resolution).
+int enqueue_comp(a3fr_scene *s, const CompositeParams &cp, int uniform, uint8_t *cur,
+                 cudaStream_t stream, uint64_t *launches) {
+  const int b = s->sorted_in_alt ? 1 : 0;
+  A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
+  A3FR_CHECK(launch_composite(cp, &s->params_dev->comp, s->rec, s->desc.n, s->ranges, s->counts,
+                              s->tvals[b], s->gaze_dev, nullptr, uniform, cur, s->plan, s->levels,
+                              s->keep_aux ? s->t_final : nullptr,
+                              s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
+  *launches += cp.full ? 1 : 2;
+  A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));
+  return A3FR_OK;
+}
+
+// Captures `fn` (enqueuing on a stream) into an executable graph.
+template <typename F>
+int capture(a3fr_scene *s, cudaGraphExec_t *exec, uint64_t *kernels, F fn) {
+  if (*exec) {
+    cudaGraphExecDestroy(*exec);
+    *exec = nullptr;
+  }
+  A3FR_CHECK(cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeRelaxed));
+  *kernels = 0;
+  const int rc = fn(s->capture_stream, kernels);
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(s->capture_stream, &g);
+  if (rc != A3FR_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+  const cudaError_t ei = cudaGraphInstantiate(exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) return cuda_fail(ei, "cudaGraphInstantiate");
+  return A3FR_OK;
+}
+
+int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream, Mode mode) {
+  s->round_ready = false;   // any render replaces the precompute that rounds build on
+  const int eyes = n_eyes_of(s);
+  if (eyes == 0 || out == nullptr) return A3FR_ERR_INVALID_ARG;
+  const a3fr_camera &c0 = s->cams[0];
+  if (eyes == 2 && (s->cams[1].width != c0.width || s->cams[1].height != c0.height))
+    return A3FR_ERR_INVALID_ARG;
+  if (fv) {
+    if (fv->n_layers < 1 || fv->n_layers > 4) return A3FR_ERR_INVALID_ARG;
+    for (int k = 0; k < fv->n_layers; ++k)
+      if (fv->level[k] < 1 || fv->level[k] > 4) return A3FR_ERR_INVALID_ARG;
+    if (mode == Mode::kFoveated && s->gaze_seq < 0) return A3FR_ERR_NOT_READY;
+  }
+  int rc = ensure_frame_buffers(s, eyes, c0.width, c0.height);
+  if (rc != A3FR_OK) return rc;
+
+  DevParams hp{};
+  hp.pre = pre_params(s, eyes);
+  hp.comp = composite_params(s, eyes, mode == Mode::kFull ? nullptr : fv);
+  hp.comp.out = out;
   int slot = -1;
+  if (mode == Mode::kFoveated) {
+    slot = s->gaze_seq % kSlots;
+    hp.comp.gaze_slot = slot;
+  }
+  rc = upload_params(s, hp, stream);
+  if (rc != A3FR_OK) return rc;
+
+  uint64_t launches = 0;
+  const bool graphs = s->graph_mode && s->timing_ring == 0 && s->capacity > 0 &&
+                      mode != Mode::kFirstRound && s->desc.n > 0;
+  if (graphs) {
+    const uint64_t key = s->alloc_gen * 4 + (s->keep_aux ? 2 : 0) + (uint64_t)eyes;
+    if (!s->g_pre || s->g_pre_key != key) {
+      rc = capture(s, &s->g_pre, &s->g_pre_launches, [&](cudaStream_t cs, uint64_t *l) {
+        return enqueue_pre(s, eyes, cs, false, l);
+      });
+      if (rc != A3FR_OK) return rc;
+      s->g_pre_key = key;
+    }
+    A3FR_CHECK(cudaGraphLaunch(s->g_pre, stream));
+    launches += s->g_pre_launches;
+  } else {
+    rc = enqueue_pre(s, eyes, stream, true, &launches);
+    if (rc != A3FR_OK) return rc;
+  }
+
   int uniform = 0;
   uint8_t *cur = nullptr;
   if (mode == Mode::kFoveated) {
-    slot = s->gaze_seq % kSlots;
     A3FR_CHECK(cudaStreamWaitEvent(stream, s->gaze_written[slot], 0));
-    gaze = s->gaze_dev + 4 * slot;
   } else if (mode == Mode::kFirstRound) {
     // round 1 renders every tile at the peripheral level (Fig. 6: rendering starts at
     // peripheral resolution) and starts the frame's round state afresh
@@ -500,16 +612,30 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
     A3FR_CHECK(cudaMemsetAsync(s->round_state, 0, sizeof(RoundState), stream));
     post_mailbox(s, 0, nullptr, eyes);
   }
-  A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
-  A3FR_CHECK(launch_composite(cp, s->rec, n, s->ranges, counts, s->tvals[b], gaze, nullptr, uniform,
-                              cur, s->plan, out, s->levels, s->keep_aux ? s->t_final : nullptr,
-                              s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
-  launches += mode == Mode::kFull ? 1 : 2;
-  A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));
+  if (graphs) {
+    const uint64_t key = s->alloc_gen * 4 + (s->keep_aux ? 2 : 0) + (uint64_t)eyes;
+    cudaGraphExec_t *g = mode == Mode::kFull ? &s->g_full : &s->g_fov;
+    uint64_t *gk = mode == Mode::kFull ? &s->g_full_key : &s->g_fov_key;
+    if (!*g || *gk != key) {
+      uint64_t k = 0;
+      rc = capture(s, g, &k, [&](cudaStream_t cs, uint64_t *l) {
+        return enqueue_comp(s, hp.comp, 0, nullptr, cs, l);
+      });
+      if (rc != A3FR_OK) return rc;
+      *gk = key;
+    }
+    A3FR_CHECK(cudaGraphLaunch(*g, stream));
+    launches += mode == Mode::kFull ? 1 : 2;
+  } else {
+    rc = enqueue_comp(s, hp.comp, uniform, cur, stream, &launches);
+    if (rc != A3FR_OK) return rc;
+  }
   if (mode == Mode::kFoveated) {
     A3FR_CHECK(cudaEventRecord(s->gaze_consumed[slot], stream));
     s->slot_consumed[slot] = true;
   }
+  rc = finish_render(s, stream);
+  if (rc != A3FR_OK) return rc;
   s->last_stream = stream;
   s->last_eyes = eyes;
   s->renders++;
@@ -526,14 +652,21 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
 int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
   if (!s->round_ready || out == nullptr) return A3FR_ERR_NOT_READY;
   const int eyes = s->last_eyes;
-  CompositeParams cp = composite_params(s, eyes, &s->round_fovea);
+  DevParams hp{};
+  hp.pre = pre_params(s, eyes);
+  hp.comp = composite_params(s, eyes, &s->round_fovea);
+  hp.comp.out = out;
+  int rc = upload_params(s, hp, stream);
+  if (rc != A3FR_OK) return rc;
   A3FR_CHECK(launch_round_begin(s->round_cfg, s->mbox_dev, s->round_state, s->round_plan,
                                 s->status_dev, s->status, stream));
   const int b = s->sorted_in_alt ? 1 : 0;
-  A3FR_CHECK(launch_composite(cp, s->rec, s->desc.n, s->ranges, s->counts, s->tvals[b], s->gaze_dev,
-                              s->round_plan, 0, s->cur_level, s->plan, out, s->levels,
-                              s->keep_aux ? s->t_final : nullptr,
+  A3FR_CHECK(launch_composite(hp.comp, &s->params_dev->comp, s->rec, s->desc.n, s->ranges,
+                              s->counts, s->tvals[b], s->gaze_dev, s->round_plan, 0, s->cur_level,
+                              s->plan, s->levels, s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
+  rc = finish_render(s, stream);
+  if (rc != A3FR_OK) return rc;
   s->launches += 3;
   s->last_stream = stream;
   return A3FR_OK;
@@ -588,6 +721,14 @@ int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3f
     if ((e = cudaEventCreateWithFlags(&s->gaze_consumed[k], cudaEventDisableTiming)) != cudaSuccess)
       return fail(cuda_fail(e, "cudaEventCreate"));
   }
+  if ((e = cudaMalloc(&s->params_dev, sizeof(DevParams))) != cudaSuccess ||
+      (e = cudaMallocHost(&s->params_pinned, sizeof(DevParams) * kSlots)) != cudaSuccess ||
+      (e = cudaEventCreateWithFlags(&s->render_done, cudaEventDisableTiming)) != cudaSuccess ||
+      (e = cudaStreamCreateWithFlags(&s->capture_stream, cudaStreamNonBlocking)) != cudaSuccess)
+    return fail(cuda_fail(e, "cudaMalloc(params)"));
+  for (int k = 0; k < kSlots; ++k)
+    if ((e = cudaEventCreateWithFlags(&s->params_copied[k], cudaEventDisableTiming)) != cudaSuccess)
+      return fail(cuda_fail(e, "cudaEventCreate(params)"));
   if ((e = cudaMalloc(&s->round_state, sizeof(RoundState))) != cudaSuccess ||
       (e = cudaMalloc(&s->round_plan, sizeof(RoundPlan))) != cudaSuccess ||
       (e = cudaMemset(s->round_state, 0, sizeof(RoundState))) != cudaSuccess ||
@@ -619,6 +760,15 @@ int a3fr_destroy_scene(a3fr_scene *s) {
   dfree(s->gaze_dev);
   dfree(s->round_state);
   dfree(s->round_plan);
+  dfree(s->params_dev);
+  if (s->params_pinned) cudaFreeHost(s->params_pinned);
+  for (int k = 0; k < kSlots; ++k)
+    if (s->params_copied[k]) cudaEventDestroy(s->params_copied[k]);
+  if (s->render_done) cudaEventDestroy(s->render_done);
+  if (s->g_pre) cudaGraphExecDestroy(s->g_pre);
+  if (s->g_fov) cudaGraphExecDestroy(s->g_fov);
+  if (s->g_full) cudaGraphExecDestroy(s->g_full);
+  if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
   if (s->mbox_host) cudaFreeHost(s->mbox_host);
   if (s->status_host) cudaFreeHost(s->status_host);
   if (s->small) cudaFree(s->small);
@@ -719,6 +869,12 @@ int a3fr_get_round_status(a3fr_scene *s, a3fr_round_status *out) {
   out->complete = v->complete;
   out->rounds = v->rounds;
   for (int k = 0; k < 3; ++k) out->radius_px[k] = v->radius[k];
+  return A3FR_OK;
+}
+
+int a3fr_set_graph_mode(a3fr_scene *s, int on) {
+  if (!s) return A3FR_ERR_INVALID_ARG;
+  s->graph_mode = on != 0;
   return A3FR_OK;
 }
 

@@ -61,7 +61,7 @@ struct SortPlan {
 
 // Writes rec/rect per eye, touched[e*n + i], the depth-sort keys dkeys[e*n + i] (depth bits,
 // 0xffffffff when culled) and depth_count[0] = n_eyes * n.
-cudaError_t launch_preprocess(const PreParams &p, int n, int sh_degree, const float *means,
+cudaError_t launch_preprocess(const PreParams *p_dev, int n, int sh_degree, const float *means,
                               const float *log_scales, const float *quats,
                               const float *opacity_logits, const float *sh, float *rec,
                               ushort4 *rect, uint32_t *touched, uint32_t *dkeys,
@@ -132,6 +132,15 @@ struct CompositeParams {
   int n_layers;
   int level[4];
   float r2[kMaxEyes][3];    // squared layer radii per eye
+  int gaze_slot;            // mailbox-ring slot of the gaze (foveated renders)
+  float *out;               // output image [eyes][H][W][3]
+};
+
+// Per-render parameters, resident in device memory so that captured graphs stay valid: one
+// host-to-device copy per render updates them.
+struct DevParams {
+  PreParams pre;
+  CompositeParams comp;
 };
 
 // Per-round parameters of an incremental round, written on the device by round_begin.
@@ -150,10 +159,11 @@ size_t plan_bytes(int n_ranges);
 // `uniform` from label 0 and sets cur; a later round (round != nullptr) renders from cur up
 // to the level of its gaze and radii, stores only those pixels, and raises cur.  Ranges are
 // clamped to kept[0] (the instances the sort kept).
-cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
-                             const uint2 *ranges, const uint32_t *kept, const uint32_t *vals,
-                             const float *gaze, const RoundPlan *round, int uniform,
-                             uint8_t *cur, uint32_t *plan, float *out, uint8_t *levels,
+// p (host copy) decides the launch shape; the kernels read p_dev (the same values).
+cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_dev,
+                             const float *rec, int n, const uint2 *ranges, const uint32_t *kept,
+                             const uint32_t *vals, const float *gaze, const RoundPlan *round,
+                             int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, unsigned long long *counters,
                              cudaStream_t s);
 

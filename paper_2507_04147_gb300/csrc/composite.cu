@@ -66,9 +66,12 @@ __device__ __forceinline__ int tile_level(const CompositeParams &p, int eye, int
 //   * a later round (round != nullptr): hi = the level from the round's gaze and radii, lo =
 //     the level already rendered (cur); tiles with hi <= lo get no entry; cur becomes hi.
 __global__ void __launch_bounds__(256)
-plan_kernel(CompositeParams p, const float *__restrict__ gaze, const RoundPlan *__restrict__ round,
-            int uniform, uint8_t *__restrict__ cur, uint8_t *__restrict__ levels,
-            uint32_t *__restrict__ plan, uint32_t *__restrict__ plan_counts) {
+plan_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ gaze_ring,
+            const RoundPlan *__restrict__ round, int uniform, uint8_t *__restrict__ cur,
+            uint8_t *__restrict__ levels, uint32_t *__restrict__ plan,
+            uint32_t *__restrict__ plan_counts) {
+  const CompositeParams &p = *pp;
+  const float *gaze = gaze_ring + 4 * p.gaze_slot;
   const int n_ranges = p.n_eyes * p.n_tiles;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -141,13 +144,14 @@ __device__ __forceinline__ void blend(float pw, const float4 &rgb, uint32_t pos,
 
 template <bool kAux, bool kFull>
 __global__ void __launch_bounds__(kThreads, 6)
-composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
+composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
                  const uint32_t *__restrict__ vals, const uint32_t *__restrict__ plan,
                  const uint32_t *__restrict__ plan_counts, int incremental,
-                 float *__restrict__ out, uint8_t *__restrict__ levels,
-                 float *__restrict__ t_final, uint32_t *__restrict__ n_contrib,
-                 unsigned long long *__restrict__ counters) {
+                 uint8_t *__restrict__ levels, float *__restrict__ t_final,
+                 uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ counters) {
+  const CompositeParams &p = *pp;   // per-render parameters in device memory
+  float *out = p.out;
   __shared__ float4 s_geo[kThreads];   // u, v, -0.5 log2e a, -log2e b
   __shared__ float4 s_co[kThreads];    // -0.5 log2e c, log2 threshold, -, -
   __shared__ float4 s_rgb[kThreads];   // r, g, b, opacity
@@ -344,10 +348,10 @@ composite_kernel(CompositeParams p, const float *__restrict__ rec, int n,
 
 size_t plan_bytes(int n_ranges) { return sizeof(uint32_t) * (4 * (size_t)n_ranges + 4); }
 
-cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
-                             const uint2 *ranges, const uint32_t *kept, const uint32_t *vals,
-                             const float *gaze, const RoundPlan *round, int uniform,
-                             uint8_t *cur, uint32_t *plan, float *out, uint8_t *levels,
+cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_dev,
+                             const float *rec, int n, const uint2 *ranges, const uint32_t *kept,
+                             const uint32_t *vals, const float *gaze, const RoundPlan *round,
+                             int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, unsigned long long *counters,
                              cudaStream_t s) {
   const int n_ranges = p.n_eyes * p.n_tiles;
@@ -356,8 +360,8 @@ cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
   if (!p.full) {
     cudaError_t e = cudaMemsetAsync(pc, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    plan_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p, gaze, round, uniform, cur, levels, plan,
-                                                       pc);
+    plan_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p_dev, gaze, round, uniform, cur, levels,
+                                                       plan, pc);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -376,17 +380,17 @@ cudaError_t launch_composite(const CompositeParams &p, const float *rec, int n,
   if (t_final != nullptr) {
     if (p.full)
       composite_kernel<true, true><<<n_ranges, kThreads, 0, s>>>(
-          p, rec, n, ranges, kept, vals, plan, pc, 0, out, levels, t_final, n_contrib, counters);
+          p_dev, rec, n, ranges, kept, vals, plan, pc, 0, levels, t_final, n_contrib, counters);
     else
       composite_kernel<true, false><<<n_ranges, kThreads, 0, s>>>(
-          p, rec, n, ranges, kept, vals, plan, pc, inc, out, levels, t_final, n_contrib, counters);
+          p_dev, rec, n, ranges, kept, vals, plan, pc, inc, levels, t_final, n_contrib, counters);
   } else {
     if (p.full)
       composite_kernel<false, true><<<n_ranges, kThreads, 0, s>>>(
-          p, rec, n, ranges, kept, vals, plan, pc, 0, out, levels, t_final, n_contrib, counters);
+          p_dev, rec, n, ranges, kept, vals, plan, pc, 0, levels, t_final, n_contrib, counters);
     else
       composite_kernel<false, false><<<n_ranges, kThreads, 0, s>>>(
-          p, rec, n, ranges, kept, vals, plan, pc, inc, out, levels, t_final, n_contrib, counters);
+          p_dev, rec, n, ranges, kept, vals, plan, pc, inc, levels, t_final, n_contrib, counters);
   }
   return cudaGetLastError();
 }

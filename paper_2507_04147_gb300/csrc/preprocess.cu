@@ -101,13 +101,14 @@ __device__ __forceinline__ void stage(float *dst, const float *__restrict__ src,
 
 template <int K>
 __global__ void __launch_bounds__(kPreThreads)
-preprocess_kernel(PreParams p, int n, const float *__restrict__ means,
+preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restrict__ means,
                   const float *__restrict__ log_scales, const float *__restrict__ quats,
                   const float *__restrict__ opacity_logits, const float *__restrict__ sh,
                   float *__restrict__ rec, ushort4 *__restrict__ rect,
                   uint32_t *__restrict__ touched, uint32_t *__restrict__ dkeys,
                   uint32_t *__restrict__ depth_count) {
   constexpr int SS = sh_stride<K>();
+  const PreParams &p = *pp;   // per-render parameters in device memory
   __shared__ float s_mean[kPreThreads * 3];
   __shared__ float s_scale[kPreThreads * 3];
   __shared__ float4 s_quat[kPreThreads];
@@ -246,7 +247,7 @@ preprocess_kernel(PreParams p, int n, const float *__restrict__ means,
 
 }  // namespace
 
-cudaError_t launch_preprocess(const PreParams &p, int n, int sh_degree, const float *means,
+cudaError_t launch_preprocess(const PreParams *p, int n, int sh_degree, const float *means,
                               const float *log_scales, const float *quats,
                               const float *opacity_logits, const float *sh, float *rec,
                               ushort4 *rect, uint32_t *touched, uint32_t *dkeys,
