@@ -53,6 +53,9 @@ def parse_args(argv=None):
     p.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--skip-3m", action="store_true", help="skip the 3M-Gaussian clustered section")
+    p.add_argument("--quick", action="store_true",
+                   help="timed loops and stage breakdown only (no PSNR, e2e, rounds, 3M, CPU legs); "
+                        "the short command the profiler captures")
     return p.parse_args(argv)
 
 
@@ -394,11 +397,12 @@ def run_ours(args):
     fps_full = frames_all / (total_full / 1000.0)
 
     # PSNR of foveated vs full on a few frames (foveal = level-4 tiles)
-    psnr = psnr_frames(scene, enqueue, out, out_full, w, [0, 60, 120, 180], a3fr, torch)
+    psnr = None if args.quick else psnr_frames(scene, enqueue, out, out_full, w,
+                                               [0, 60, 120, 180], a3fr, torch)
 
     # end to end through host buffers: host gaze/camera in, image back to pinned host memory
     host_img = torch.empty(out.shape, dtype=torch.float32, pin_memory=True)
-    e2e_frames = frames[: min(len(frames), 240)]
+    e2e_frames = [] if args.quick else frames[: min(len(frames), 240)]
     scene.graph_mode(True)
     torch.cuda.synchronize()
     barrier(world)
@@ -410,10 +414,10 @@ def run_ours(args):
         render_stream.synchronize()
     e2e_s = reduce_max(time.perf_counter() - t0, world, device)
     scene.graph_mode(False)
-    e2e_value = reduce_sum(float(len(e2e_frames)), world, device) / e2e_s
+    e2e_value = reduce_sum(float(len(e2e_frames)), world, device) / e2e_s if e2e_frames else None
 
-    incremental = incremental_latency(a3fr, scene, w, traj, out, render_stream,
-                                      float(np.percentile(ms_full, 50)))
+    incremental = None if args.quick else incremental_latency(
+        a3fr, scene, w, traj, out, render_stream, float(np.percentile(ms_full, 50)))
 
     stage_mean_fov = {k: float(st_fov[:, i].mean()) for i, k in enumerate(STAGES)}
     stage_mean_full = {k: float(st_full[:, i].mean()) for i, k in enumerate(STAGES)}
@@ -445,11 +449,11 @@ def run_ours(args):
                     "note": "per frame: cameras + gaze from the host, render, image to pinned host memory, synchronise"},
             "gpu_launches": int(stats_fov["kernel_launches"]),
             "clocks": clk}
-    if rank == 0 and not args.skip_3m and args.workload == "stereo500k":
+    if rank == 0 and not (args.skip_3m or args.quick) and args.workload == "stereo500k":
         scene.close()
         line["clustered_3m"] = clustered_3m_section(a3fr, torch, device, render_stream, gaze_stream,
                                                     flush, max(args.warmup, 3))
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.quick):
         t, desc = oracle_frame(w, 0, traj, args.cpu_budget)
         import oracle
         line["cpu_baseline"] = {"value": 1.0 / t, "unit": UNIT, "cores": oracle.num_threads(),

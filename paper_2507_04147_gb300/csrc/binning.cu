@@ -197,106 +197,161 @@ tile_count_kernel(TileScanParams p, const ushort4 *__restrict__ rect,
   for (int i = threadIdx.x; i < cells; i += kCountThreads) out[i] = s_grid[i];
 }
 
-__global__ void tile_reduce_kernel(const uint32_t *__restrict__ partials, int parts, int cells,
-                                   uint32_t *__restrict__ grid) {
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < cells; i += gridDim.x * blockDim.x) {
-    uint32_t acc = 0;
-    for (int b = 0; b < parts; ++b) acc += partials[(size_t)b * cells + i];
-    grid[i] = acc;
-  }
+// Sum of the per-CTA difference grids: blockIdx.y takes a group of kReduceParts partial
+// grids, each thread one cell; the group sums are added into the zeroed grid (integer adds,
+// so the result does not depend on their order).
+constexpr int kReduceParts = 19;
+
+__global__ void __launch_bounds__(256)
+tile_reduce_kernel(const uint32_t *__restrict__ partials, int parts, int cells,
+                   uint32_t *__restrict__ grid) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= cells) return;
+  const int b0 = blockIdx.y * kReduceParts, b1 = min(parts, b0 + kReduceParts);
+  uint32_t acc = 0;
+#pragma unroll 4
+  for (int b = b0; b < b1; ++b) acc += partials[(size_t)b * cells + i];
+  if (acc) atomicAdd(grid + i, acc);
 }
 
-// One CTA: 2-D prefix sums of the summed difference grids in shared memory (rows in
-// parallel, then columns), exclusive scan of the counts over tiles -> ranges; then the
-// digit histograms of the tile sort and the per-eye totals from the scanned ranges.
+// Inclusive scan of one value per lane across the warp.
+template <typename T>
+__device__ __forceinline__ T warp_incl_scan(T v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const T n = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += n;
+  }
+  return v;
+}
+
+// One CTA: 2-D prefix sums of the summed difference grids in shared memory (a warp per row,
+// then a warp per column, 32 cells per step), then the exclusive scan of the counts over
+// tiles (eye-major, row-major) -> ranges: each thread owns a contiguous run of tiles, so
+// one block-wide scan of the run totals suffices.  The digit histograms of the tile sort
+// are accumulated from the same counts (one shared atomic per run of equal digits), and
+// the per-eye totals are read from the scanned ranges.
 __global__ void __launch_bounds__(1024)
 tile_scan_kernel(TileScanParams p, const uint32_t *__restrict__ diff, uint2 *__restrict__ ranges,
                  uint32_t *__restrict__ tile_hist, uint32_t *__restrict__ counts,
                  uint32_t *__restrict__ status) {
   extern __shared__ uint32_t s_grid[];
   __shared__ unsigned long long s_warp[32];
-  __shared__ unsigned long long s_carry;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  __shared__ uint32_t s_hist[kMaxSortPasses][256];
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, n_warps = blockDim.x >> 5;
   const int gw = p.tiles_x + 1, gh = p.tiles_y + 1;
   const int cells = p.n_eyes * gw * gh;
-  if (t == 0) s_carry = 0;
-  for (int i = t; i < cells; i += blockDim.x) s_grid[i] = diff[i];
-  __syncthreads();
-  for (int r = t; r < p.n_eyes * gh; r += blockDim.x) {
-    uint32_t *row = s_grid + r * gw;
-    uint32_t acc = 0;
-    for (int x = 0; x < gw; ++x) { acc += row[x]; row[x] = acc; }
+  for (int i = t; i < kMaxSortPasses * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0;
+  // bulk copy, four independent loads in flight per thread
+  for (int i0 = t; i0 < cells; i0 += 4 * blockDim.x) {
+    uint32_t v[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k * blockDim.x;
+      v[k] = i < cells ? diff[i] : 0u;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int i = i0 + k * blockDim.x;
+      if (i < cells) s_grid[i] = v[k];
+    }
   }
   __syncthreads();
-  for (int c = t; c < p.n_eyes * gw; c += blockDim.x) {
+  // rows
+  for (int r = warp; r < p.n_eyes * gh; r += n_warps) {
+    uint32_t *row = s_grid + r * gw;
+    uint32_t carry = 0;
+    for (int x0 = 0; x0 < gw; x0 += 32) {
+      const int x = x0 + lane;
+      uint32_t v = x < gw ? row[x] : 0u;
+      v = warp_incl_scan(v, lane) + carry;
+      if (x < gw) row[x] = v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+  }
+  __syncthreads();
+  // columns
+  for (int c = warp; c < p.n_eyes * gw; c += n_warps) {
     const int e = c / gw, x = c - e * gw;
     uint32_t *col = s_grid + e * gw * gh + x;
-    uint32_t acc = 0;
-    for (int y = 0; y < gh; ++y) { acc += col[y * gw]; col[y * gw] = acc; }
+    uint32_t carry = 0;
+    for (int y0 = 0; y0 < gh; y0 += 32) {
+      const int y = y0 + lane;
+      uint32_t v = y < gh ? col[y * gw] : 0u;
+      v = warp_incl_scan(v, lane) + carry;
+      if (y < gh) col[y * gw] = v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
+    }
   }
   __syncthreads();
-  // exclusive scan of the counts over all tiles (eye-major, row-major)
+  // this thread's run of tiles [r0, r1) and its total
   const int n_ranges = p.n_eyes * p.n_tiles;
-  for (int base = 0; base < n_ranges; base += blockDim.x) {
-    const int tt = base + t;
-    uint32_t cnt = 0;
-    if (tt < n_ranges) {
-      const int eye = tt / p.n_tiles;
-      const int tile = tt - eye * p.n_tiles;
-      const int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
-      cnt = s_grid[eye * gw * gh + ty * gw + tx];
-    }
-    unsigned long long incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long n = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += n;
-    }
-    if (lane == 31) s_warp[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-      const unsigned long long w = s_warp[lane];
-      unsigned long long wi = w;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned long long n = __shfl_up_sync(0xffffffffu, wi, o);
-        if (lane >= o) wi += n;
+  const int per = (n_ranges + (int)blockDim.x - 1) / (int)blockDim.x;
+  const int r0 = min(n_ranges, t * per), r1 = min(n_ranges, r0 + per);
+  unsigned long long sum = 0;
+  if (r0 < r1) {
+    int eye = r0 / p.n_tiles, tile = r0 - eye * p.n_tiles;
+    int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
+    for (int r = r0; r < r1; ++r) {
+      sum += s_grid[eye * gw * gh + ty * gw + tx];
+      if (++tx == p.tiles_x) {
+        tx = 0;
+        if (++ty == p.tiles_y) { ty = 0; ++eye; }
       }
-      s_warp[lane] = wi - w;
     }
-    __syncthreads();
-    const unsigned long long excl = s_carry + s_warp[warp] + incl - cnt;
-    if (tt < n_ranges) {
+  }
+  // block-wide exclusive scan of the run totals
+  const unsigned long long incl = warp_incl_scan(sum, lane);
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const unsigned long long w = lane < n_warps ? s_warp[lane] : 0ull;
+    s_warp[lane] = warp_incl_scan(w, lane) - w;
+  }
+  __syncthreads();
+  unsigned long long excl = s_warp[warp] + incl - sum;
+  if (r0 < r1) {
+    int eye = r0 / p.n_tiles, tile = r0 - eye * p.n_tiles;
+    int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
+    uint32_t run_d[kMaxSortPasses], run_v[kMaxSortPasses];
+#pragma unroll
+    for (int ps = 0; ps < kMaxSortPasses; ++ps) {
+      run_d[ps] = 0xffffffffu;
+      run_v[ps] = 0;
+    }
+    const unsigned long long lim = 0xffffffffull;
+    for (int r = r0; r < r1; ++r) {
+      const uint32_t cnt = s_grid[eye * gw * gh + ty * gw + tx];
       // unclamped: the composite clamps every range to the instances the sort kept
-      const unsigned long long lim = 0xffffffffull;
-      ranges[tt] = make_uint2((uint32_t)(excl < lim ? excl : lim),
-                              (uint32_t)(excl + cnt < lim ? excl + cnt : lim));
-    }
-    __syncthreads();
-    if (t == blockDim.x - 1) s_carry = excl + cnt;
-    __syncthreads();
-  }
-  const unsigned long long total = s_carry;
-  // digit histograms: the tiles of digit d in a pass with shift s and b bits form runs of
-  // 2^s consecutive tiles starting at ((k << b) | d) << s; a run's count is a difference
-  // of two scanned range starts
-  const int bits = __popc(p.tile_plan.mask);
-  for (int i = t; i < p.tile_plan.passes * 256; i += blockDim.x) {
-    const int ps = i >> 8, d = i & 255;
-    uint32_t v = 0;
-    if ((uint32_t)d <= p.tile_plan.mask) {
-      const int s = p.tile_plan.shift[ps];
-      for (long long k = 0;; ++k) {
-        const long long a = ((k << bits) | d) << s;
-        if (a >= n_ranges) break;
-        const long long b = min((long long)n_ranges, a + (1ll << s));
-        const uint32_t end = b < n_ranges ? ranges[b].x : (uint32_t)total;
-        v += end - ranges[a].x;
+      ranges[r] = make_uint2((uint32_t)(excl < lim ? excl : lim),
+                             (uint32_t)(excl + cnt < lim ? excl + cnt : lim));
+      excl += cnt;
+#pragma unroll
+      for (int ps = 0; ps < kMaxSortPasses; ++ps) {
+        if (ps < p.tile_plan.passes) {
+          const uint32_t d = ((uint32_t)r >> p.tile_plan.shift[ps]) & p.tile_plan.mask;
+          if (d != run_d[ps]) {
+            if (run_v[ps]) atomicAdd(&s_hist[ps][run_d[ps]], run_v[ps]);
+            run_d[ps] = d;
+            run_v[ps] = 0;
+          }
+          run_v[ps] += cnt;
+        }
+      }
+      if (++tx == p.tiles_x) {
+        tx = 0;
+        if (++ty == p.tiles_y) { ty = 0; ++eye; }
       }
     }
-    tile_hist[i] = v;
+#pragma unroll
+    for (int ps = 0; ps < kMaxSortPasses; ++ps)
+      if (ps < p.tile_plan.passes && run_v[ps]) atomicAdd(&s_hist[ps][run_d[ps]], run_v[ps]);
   }
-  if (t == 0) {
+  __syncthreads();
+  for (int i = t; i < p.tile_plan.passes * 256; i += blockDim.x) tile_hist[i] = (&s_hist[0][0])[i];
+  if (t == blockDim.x - 1) {
+    // the last thread's running offset is the total (threads past the tiles carry it too)
+    const unsigned long long total = excl;
     const uint32_t eye0 = p.n_eyes > 1 ? ranges[p.n_tiles].x : (uint32_t)total;
     counts[0] = (uint32_t)(total < p.capacity ? total : p.capacity);
     counts[1] = eye0;
@@ -372,7 +427,9 @@ cudaError_t launch_tile_count(const TileScanParams &p, const ushort4 *rect, uint
   tile_count_kernel<<<parts, kCountThreads, smem, s>>>(p, rect, partials);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int rb = (int)((cells + 255) / 256);
+  e = cudaMemsetAsync(grid, 0, sizeof(uint32_t) * cells, s);
+  if (e != cudaSuccess) return e;
+  const dim3 rb((unsigned)((cells + 255) / 256), (unsigned)((parts + kReduceParts - 1) / kReduceParts));
   tile_reduce_kernel<<<rb, 256, 0, s>>>(partials, parts, (int)cells, grid);
   return cudaGetLastError();
 }

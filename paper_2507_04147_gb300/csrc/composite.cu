@@ -17,10 +17,10 @@
 // Per batch, the staging threads gather the tile's next Gaussians (indices from the
 // sorted values) into shared memory; each warp then blends them front to back with the
 // 1/255 skip, the 0.99 clamp and the 1e-4 transmittance stop; the staging group stops when
-// all its pixels are done.  The exp of the falloff
-// uses the MUFU ex2 unit with log2(e) folded into the conic, and the 1/255 test is made on
-// the exponent first, so pixels outside a Gaussian's support never reach the exp.  Label-1
-// warps also write the inherited pixels of their blocks.
+// all its pixels are done.  The exp of the falloff uses the MUFU ex2 unit with log2(e)
+// folded into the conic.  The blend is branch-free (predicated updates), so a warp whose
+// lanes disagree on the accept test does not run both sides.  Label-1 warps also write the
+// inherited pixels of their blocks.
 #include "common.cuh"
 
 namespace a3fr {
@@ -33,11 +33,6 @@ constexpr float kLog2e = 1.4426950408889634f;
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-__device__ __forceinline__ float lg2_approx(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
 }
 
@@ -122,26 +117,6 @@ __device__ __forceinline__ void group_sync(int size, int bar) {
   }
 }
 
-// Front-to-back blend of one Gaussian into one pixel; returns true when the pixel is done.
-__device__ __forceinline__ void blend(float pw, const float4 &rgb, uint32_t pos, float &T,
-                                      float &C0, float &C1, float &C2, uint32_t &last,
-                                      uint32_t &stop, bool &done) {
-  const float alpha = fminf(0.99f, rgb.w * ex2_approx(pw));
-  if (alpha < 1.0f / 255.0f) return;
-  const float tt = T * (1.0f - alpha);
-  if (tt < 0.0001f) {
-    done = true;
-    stop = pos;
-    return;
-  }
-  const float w = alpha * T;
-  C0 += rgb.x * w;
-  C1 += rgb.y * w;
-  C2 += rgb.z * w;
-  T = tt;
-  last = pos;
-}
-
 template <bool kAux, bool kFull>
 __global__ void __launch_bounds__(kThreads, 6)
 composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
@@ -153,7 +128,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
   const CompositeParams &p = *pp;   // per-render parameters in device memory
   float *out = p.out;
   __shared__ float4 s_geo[kThreads];   // u, v, -0.5 log2e a, -log2e b
-  __shared__ float4 s_co[kThreads];    // -0.5 log2e c, log2 threshold, -, -
+  __shared__ float s_c[kThreads];      // -0.5 log2e c
   __shared__ float4 s_rgb[kThreads];   // r, g, b, opacity
   __shared__ int s_done[kThreads / 32];
   __shared__ float s_out[4][kTile][kTile * 3];   // the tiles of the CTA, assembled for stores
@@ -252,24 +227,48 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
       const uint32_t gidx = min(vals[start + gt], (uint32_t)(n - 1));   // in range unless a sort failed
       const float4 *r4 = reinterpret_cast<const float4 *>(rec_eye + (size_t)gidx * kRec);
       const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
-      // alpha >= 1/255  <=>  power * log2e >= log2(1 / (255 opacity)) = thr
-      const float thr = -lg2_approx(255.0f * b.y);
       s_geo[threadIdx.x] = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
-      s_co[threadIdx.x] = make_float4(-0.5f * kLog2e * b.x, thr, 0.0f, 0.0f);
+      s_c[threadIdx.x] = -0.5f * kLog2e * b.x;
       s_rgb[threadIdx.x] = make_float4(b.z, b.w, c.x, b.y);
+    } else if ((uint32_t)gt < ((cnt + 3u) & ~3u)) {
+      // padding up to a multiple of 4: zero opacity never passes the 1/255 test
+      s_geo[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      s_c[threadIdx.x] = 0.0f;
+      s_rgb[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     group_sync(gsize, gbar);
-    if (!done) {
-      for (uint32_t k = 0; k < cnt; ++k) {
-        const float4 geo = s_geo[gfirst + k];
-        const float4 co = s_co[gfirst + k];
-        const float dx = geo.x - fpx, dy = geo.y - fpy;
-        // power * log2(e) = -0.5 log2e (a dx^2 + c dy^2) - log2e b dx dy
-        const float pw = (geo.z * dx + geo.w * dy) * dx + co.x * dy * dy;
-        if (pw <= 0.0f && pw >= co.y) {
-          blend(pw, s_rgb[gfirst + k], start - range.x + k + 1, T, C0, C1, C2, last, stop, done);
-          if (done) break;
+    if (!__all_sync(0xffffffffu, done)) {
+      // Branch-free blending: every lane evaluates every Gaussian of the batch and the
+      // update is predicated (a lane that is done, or outside the Gaussian's support or
+      // below 1/255, keeps its state), so the warp never splits on the accept test.
+      const uint32_t cnt4 = (cnt + 3u) & ~3u;
+      const uint32_t pos0 = start - range.x + 1;
+      for (uint32_t k = 0; k < cnt4; k += 4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int e = gfirst + (int)k + j;
+          const float4 geo = s_geo[e];
+          const float cc = s_c[e];
+          const float4 rgb = s_rgb[e];
+          const float dx = geo.x - fpx, dy = geo.y - fpy;
+          // power * log2(e) = -0.5 log2e (a dx^2 + c dy^2) - log2e b dx dy
+          const float pw = (geo.z * dx + geo.w * dy) * dx + cc * dy * dy;
+          const float alpha = fminf(0.99f, rgb.w * ex2_approx(pw));
+          const float tt = T * (1.0f - alpha);
+          const bool ok = !done && pw <= 0.0f && alpha >= 1.0f / 255.0f;
+          const bool fin = ok && tt < 0.0001f;    // this Gaussian would end the pixel: stop
+          const bool upd = ok && !fin;
+          const uint32_t pos = pos0 + k + (uint32_t)j;
+          const float w = upd ? alpha * T : 0.0f;
+          C0 += rgb.x * w;
+          C1 += rgb.y * w;
+          C2 += rgb.z * w;
+          T = upd ? tt : T;
+          last = upd ? pos : last;
+          stop = fin ? pos : stop;
+          done = done || fin;
         }
+        if (__all_sync(0xffffffffu, done)) break;
       }
     }
     group_sync(gsize, gbar);   // the next batch overwrites the staged Gaussians

@@ -108,7 +108,13 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
                   uint32_t *__restrict__ touched, uint32_t *__restrict__ dkeys,
                   uint32_t *__restrict__ depth_count) {
   constexpr int SS = sh_stride<K>();
-  const PreParams &p = *pp;   // per-render parameters in device memory
+  // per-render parameters: device memory (so a captured graph sees each render's cameras),
+  // copied once per block into shared memory
+  __shared__ PreParams s_p;
+  static_assert(sizeof(PreParams) % 4 == 0 && sizeof(PreParams) / 4 <= kPreThreads, "PreParams copy");
+  if (threadIdx.x < sizeof(PreParams) / 4)
+    reinterpret_cast<uint32_t *>(&s_p)[threadIdx.x] = reinterpret_cast<const uint32_t *>(pp)[threadIdx.x];
+  const PreParams &p = s_p;
   __shared__ float s_mean[kPreThreads * 3];
   __shared__ float s_scale[kPreThreads * 3];
   __shared__ float4 s_quat[kPreThreads];
