@@ -210,6 +210,32 @@ int a3fr_run_frame(a3fr_scene *scene, const a3fr_fovea *fovea, const a3fr_rounds
  * automatic-capacity scene and the rounds API launch directly. */
 int a3fr_set_graph_mode(a3fr_scene *scene, int on);
 
+/* ---------------------------------------------------------------- backward rasterizer
+ * Gradients of L = sum(dl_drgb * image) with respect to the scene parameters, for the last
+ * render of this scene (3DGS training, Sec. 4.1 "Training": the rasterizer's forward pass
+ * differentiated through compositing, projection and SH colour of Sec. 2.3).
+ *
+ * grads: DEVICE pointers, caller-owned, same layouts and sizes as the scene description
+ *   (means [n][3], log_scales [n][3], quats [n][4], opacity_logits [n], sh [n][(deg+1)^2][3]);
+ *   every element is overwritten (culled Gaussians get zeros).  With two eyes the
+ *   gradients of both eyes' images are summed.
+ * dl_drgb: DEVICE fp32 [n_eyes][height][width][3], the gradient of L with respect to the
+ *   image the last render wrote.  For a foveated render, an inherited pixel's gradient is
+ *   passed to the top-left pixel of its block (the pixel it copies).
+ * Preconditions: the last render of the scene was a3fr_render_full or a3fr_render_foveated
+ *   with keep_aux on (its final transmittance and last contributor per pixel are what the
+ *   backward walks from; per-pixel transmittance is recomputed back to front, not stored),
+ *   no round has run since, the scene's parameter arrays are unchanged since that render,
+ *   and `stream` is ordered after it.  Otherwise A3FR_ERR_NOT_READY.
+ * Asynchronous on `stream`; per-Gaussian partial sums are accumulated with float atomics,
+ *   so the last bits of a gradient may differ from run to run.  Allocates a workspace of
+ *   36 bytes per eye and Gaussian on first use. */
+typedef struct {
+  float *means, *log_scales, *quats, *opacity_logits, *sh;
+} a3fr_grads;
+
+int a3fr_backward(a3fr_scene *scene, const float *dl_drgb, const a3fr_grads *grads, void *stream);
+
 /* Keep per-pixel transmittance and contributor counts of the next renders (aux buffers,
  * see a3fr_copy_buffer); off by default because they cost 8 bytes per pixel. */
 int a3fr_set_keep_aux(a3fr_scene *scene, int keep);

@@ -131,11 +131,18 @@ def composite(proj: dict, vis: Visibility, pixels: np.ndarray, chunk: int = 4096
               keep_mask: bool = False):
     """Step 5 for the pixels [P,2] (x, y).  Returns (C [P,3] differentiable, info dict);
     with keep_mask, info["contrib"] is the [P, G] mask of contributing Gaussians."""
-    g = torch.as_tensor(vis.order, dtype=torch.long)
+    # only Gaussians whose rectangle meets the bounding box of the pixels' tiles can reach
+    # them (the others fail the membership test for every pixel): drop them up front
+    order = vis.order
+    tx0, tx1 = pixels[:, 0].min() // vis.tile, pixels[:, 0].max() // vis.tile
+    ty0, ty1 = pixels[:, 1].min() // vis.tile, pixels[:, 1].max() // vis.tile
+    r = vis.rect[order]
+    order = order[(r[:, 0] <= tx1) & (r[:, 2] > tx0) & (r[:, 1] <= ty1) & (r[:, 3] > ty0)]
+    g = torch.as_tensor(order, dtype=torch.long)
     u, v = proj["u"][g], proj["v"][g]
     ca, cb, cc = proj["ca"][g], proj["cb"][g], proj["cc"][g]
     op, rgb = proj["opacity"][g], proj["rgb"][g]
-    rect = vis.rect[vis.order]
+    rect = vis.rect[order]
     outs, t_final, n_contrib, margins, masks = [], [], [], [], []
     for p0 in range(0, len(pixels), chunk):
         pix = pixels[p0:p0 + chunk]

@@ -101,6 +101,17 @@ def render_full(handle: int, out_rgb, stream=None) -> None:
                "a3fr_render_full")
 
 
+def backward(handle: int, dl_drgb, d_means, d_log_scales, d_quats, d_opacity_logits, d_sh,
+             stream=None) -> None:
+    """Gradients of sum(dl_drgb * image) of the last render (keep_aux on) into the d_* CUDA
+    tensors (overwritten; layouts of the scene arrays)."""
+    g = _lib.Grads()
+    g.means, g.log_scales, g.quats = _ptr(d_means), _ptr(d_log_scales), _ptr(d_quats)
+    g.opacity_logits, g.sh = _ptr(d_opacity_logits), _ptr(d_sh)
+    _lib.check(_lib.load().a3fr_backward(handle, _ptr(dl_drgb), ctypes.byref(g), _stream_ptr(stream)),
+               "a3fr_backward")
+
+
 def get_stats(handle: int, reset: bool = False) -> dict:
     st = _lib.Stats()
     _lib.check(_lib.load().a3fr_get_stats(handle, ctypes.byref(st), int(reset)), "a3fr_get_stats")
@@ -317,6 +328,17 @@ class Scene:
 
     def graph_mode(self, on: bool = True):
         set_graph_mode(self.handle, on)
+
+    def backward(self, dl_drgb, stream=None) -> dict:
+        """Gradients of sum(dl_drgb * image) of the last render (needs keep_aux) as new
+        CUDA tensors shaped like the scene arrays."""
+        torch = _torch()
+        if not (dl_drgb.is_cuda and dl_drgb.dtype == torch.float32 and dl_drgb.is_contiguous()):
+            raise ValueError("dl_drgb must be a contiguous CUDA float32 tensor")
+        names = ("means", "log_scales", "quats", "opacity_logits", "sh")
+        grads = {k: torch.empty_like(t) for k, t in zip(names, self._tensors)}
+        backward(self.handle, dl_drgb, *[grads[k] for k in names], stream=stream)
+        return grads
 
     def keep_aux(self, keep: bool = True):
         set_keep_aux(self.handle, keep)

@@ -78,6 +78,12 @@ class FrameResult(ctypes.Structure):
                 ("round_end_us", ctypes.c_double * 16)]
 
 
+class Grads(ctypes.Structure):
+    _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
+                ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
+                ("sh", ctypes.c_void_p)]
+
+
 class A3FRError(RuntimeError):
     def __init__(self, code: int, where: str, detail: str = ""):
         self.code = code
@@ -100,6 +106,8 @@ _SIGS = {
     "a3fr_get_stats": ([ctypes.c_void_p, ctypes.POINTER(Stats), ctypes.c_int], ctypes.c_int),
     "a3fr_set_keep_aux": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_set_graph_mode": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "a3fr_backward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Grads), ctypes.c_void_p],
+                      ctypes.c_int),
     "a3fr_copy_buffer": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
                           ctypes.POINTER(ctypes.c_size_t), ctypes.c_void_p], ctypes.c_int),
     "a3fr_sort_pairs_workspace_bytes": ([ctypes.c_size_t], ctypes.c_size_t),

@@ -130,6 +130,11 @@ struct a3fr_scene {
   cudaGraphExec_t g_pre = nullptr, g_fov = nullptr, g_full = nullptr;
   uint64_t g_pre_key = 0, g_fov_key = 0, g_full_key = 0;
   uint64_t g_pre_launches = 0;               // kernels in the precompute graph
+
+  // backward: what the last render leaves for it (0 none, 1 full, 2 foveated; keep_aux only)
+  int bw_mode = 0;
+  float *g2d = nullptr;                      // [eye][n][9] per-Gaussian image-space gradients
+  size_t g2d_floats = 0;
 };
 
 namespace {
@@ -645,6 +650,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
     s->round_ready = true;
     s->out_round = out;
   }
+  s->bw_mode = !s->keep_aux ? 0 : (mode == Mode::kFull ? 1 : (mode == Mode::kFoveated ? 2 : 0));
   return A3FR_OK;
 }
 
@@ -669,6 +675,7 @@ int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
   if (rc != A3FR_OK) return rc;
   s->launches += 3;
   s->last_stream = stream;
+  s->bw_mode = 0;
   return A3FR_OK;
 }
 
@@ -757,6 +764,7 @@ int a3fr_destroy_scene(a3fr_scene *s) {
   free_frame_buffers(s);
   free_instance_buffers(s);
   dfree(s->frame_ws);
+  dfree(s->g2d);
   dfree(s->gaze_dev);
   dfree(s->round_state);
   dfree(s->round_plan);
@@ -1037,5 +1045,44 @@ const char *a3fr_error_string(int code) {
 }
 
 const char *a3fr_last_error_detail(void) { return g_detail.c_str(); }
+
+
+int a3fr_backward(a3fr_scene *s, const float *dl_drgb, const a3fr_grads *g, void *stream) {
+  if (!s || !dl_drgb || !g) return A3FR_ERR_INVALID_ARG;
+  const int n = s->desc.n;
+  if (n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
+    return A3FR_ERR_INVALID_ARG;
+  if (s->bw_mode == 0 || s->last_eyes == 0) return A3FR_ERR_NOT_READY;
+  if (n == 0) return A3FR_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int eyes = s->last_eyes;
+  const size_t need = backward_g2d_floats(eyes, n);
+  if (s->g2d_floats < need) {
+    dfree(s->g2d);
+    s->g2d_floats = 0;
+    cudaError_t e = cudaMalloc(&s->g2d, sizeof(float) * need);
+    if (e != cudaSuccess) {
+      s->g2d = nullptr;
+      return cuda_fail(e, "cudaMalloc(backward workspace)");
+    }
+    s->g2d_floats = need;
+  }
+  BackwardParams bp{};
+  bp.n_eyes = eyes;
+  bp.n = n;
+  bp.width = s->cams[0].width;
+  bp.height = s->cams[0].height;
+  bp.tiles_x = s->TX;
+  bp.n_tiles = s->n_tiles;
+  const int b = s->sorted_in_alt ? 1 : 0;
+  A3FR_CHECK(launch_backward(bp, &s->params_dev->pre, s->desc.sh_degree, s->desc.means,
+                             s->desc.log_scales, s->desc.quats, s->desc.opacity_logits, s->desc.sh,
+                             s->rec, s->ranges, s->counts, s->tvals[b],
+                             s->bw_mode == 2 ? s->levels : nullptr, s->t_final, s->n_contrib,
+                             dl_drgb, s->g2d, g->means, g->log_scales, g->quats, g->opacity_logits,
+                             g->sh, st));
+  s->launches += 2;
+  return A3FR_OK;
+}
 
 }  // extern "C"

@@ -45,6 +45,24 @@ __device__ __forceinline__ float fs(float a, float b) { return __fsub_rn(a, b); 
 __device__ __forceinline__ float fdv(float a, float b) { return __fdiv_rn(a, b); }
 __device__ __forceinline__ float fsq(float a) { return __fsqrt_rn(a); }
 
+// The falloff of the compositing step in base 2: with A = -0.5 log2(e) a, B = -log2(e) b,
+// C = -0.5 log2(e) c for the conic (a, b, c), (A dx + B dy) dx + C dy^2 = power * log2(e),
+// power = -0.5 (a dx^2 + c dy^2) - b dx dy.  Explicitly rounded, so the forward composite
+// and its backward evaluate the same value bit for bit.
+constexpr float kLog2e = 1.4426950408889634f;
+__device__ __forceinline__ float falloff_log2(float A, float B, float C, float dx, float dy) {
+  return __fmaf_rn(__fmaf_rn(A, dx, __fmul_rn(B, dy)), dx, __fmul_rn(__fmul_rn(C, dy), dy));
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+// alpha = min(0.99, opacity * 2^pw)
+__device__ __forceinline__ float blend_alpha(float opacity, float pw) {
+  return fminf(0.99f, __fmul_rn(opacity, ex2_approx(pw)));
+}
+
 }  // namespace a3fr
 
 // Kernel launchers defined in the .cu files (host side).
@@ -201,6 +219,19 @@ struct a3fr_scene;
 namespace a3fr {
 // Eyes rendered by a scene (eyes with a camera).
 int scene_eyes(const a3fr_scene *s);
+
+// Backward rasterizer (backward.cu).
+struct BackwardParams {
+  int n_eyes, n, width, height, tiles_x, n_tiles;
+};
+size_t backward_g2d_floats(int n_eyes, int n);
+cudaError_t launch_backward(const BackwardParams &bp, const PreParams *pre_dev, int sh_degree,
+                            const float *means, const float *log_scales, const float *quats,
+                            const float *opacity_logits, const float *sh, const float *rec,
+                            const uint2 *ranges, const uint32_t *kept, const uint32_t *vals,
+                            const uint8_t *levels, const float *t_final, const uint32_t *n_contrib,
+                            const float *dl_drgb, float *g2d, float *d_means, float *d_log_scales,
+                            float *d_quats, float *d_logits, float *d_sh, cudaStream_t s);
 
 cudaError_t launch_round_begin(const RoundConfig &c, const Mailbox *mbox, RoundState *state,
                                RoundPlan *plan, RoundStatus *status, uint32_t *error_status,

@@ -28,14 +28,6 @@ namespace {
 
 constexpr int kTile = 16;
 constexpr int kThreads = 256;          // 8 warps
-constexpr float kLog2e = 1.4426950408889634f;
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // Level of tile `tile` of eye `eye` (exactly rounded; the same decision as the definition).
 __device__ __forceinline__ int tile_level(const CompositeParams &p, int eye, int tile,
                                           const float *gaze) {
@@ -227,8 +219,8 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
       const uint32_t gidx = min(vals[start + gt], (uint32_t)(n - 1));   // in range unless a sort failed
       const float4 *r4 = reinterpret_cast<const float4 *>(rec_eye + (size_t)gidx * kRec);
       const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
-      s_geo[threadIdx.x] = make_float4(a.x, a.y, -0.5f * kLog2e * a.z, -kLog2e * a.w);
-      s_c[threadIdx.x] = -0.5f * kLog2e * b.x;
+      s_geo[threadIdx.x] = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
+      s_c[threadIdx.x] = __fmul_rn(-0.5f * kLog2e, b.x);
       s_rgb[threadIdx.x] = make_float4(b.z, b.w, c.x, b.y);
     } else if ((uint32_t)gt < ((cnt + 3u) & ~3u)) {
       // padding up to a multiple of 4: zero opacity never passes the 1/255 test
@@ -250,11 +242,11 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
           const float4 geo = s_geo[e];
           const float cc = s_c[e];
           const float4 rgb = s_rgb[e];
-          const float dx = geo.x - fpx, dy = geo.y - fpy;
+          const float dx = __fsub_rn(geo.x, fpx), dy = __fsub_rn(geo.y, fpy);
           // power * log2(e) = -0.5 log2e (a dx^2 + c dy^2) - log2e b dx dy
-          const float pw = (geo.z * dx + geo.w * dy) * dx + cc * dy * dy;
-          const float alpha = fminf(0.99f, rgb.w * ex2_approx(pw));
-          const float tt = T * (1.0f - alpha);
+          const float pw = falloff_log2(geo.z, geo.w, cc, dx, dy);
+          const float alpha = blend_alpha(rgb.w, pw);
+          const float tt = __fmul_rn(T, __fsub_rn(1.0f, alpha));
           const bool ok = !done && pw <= 0.0f && alpha >= 1.0f / 255.0f;
           const bool fin = ok && tt < 0.0001f;    // this Gaussian would end the pixel: stop
           const bool upd = ok && !fin;
