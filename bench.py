@@ -453,6 +453,9 @@ def run_ours(args):
         scene.close()
         line["clustered_3m"] = clustered_3m_section(a3fr, torch, device, render_stream, gaze_stream,
                                                     flush, max(args.warmup, 3))
+    if rank == 0 and not (args.skip_3m or args.quick) and args.workload == "stereo500k":
+        line["backward_1m_1024"] = backward_section(a3fr, torch, device, render_stream, flush,
+                                                    max(args.warmup, 3))
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.quick):
         t, desc = oracle_frame(w, 0, traj, args.cpu_budget)
         import oracle
@@ -525,6 +528,53 @@ def clustered_3m_section(a3fr, torch, device, render_stream, gaze_stream, flush,
     res["workload"] = w.name
     scene.close()
     return res
+
+
+def backward_section(a3fr, torch, device, render_stream, flush, warmup, steps: int = 60):
+    """Training step of the rasterizer: 1M Gaussians, SH3, one 1024x1024 view; forward
+    (full render keeping T_final / last contributor) and backward (a3fr_backward), ms each."""
+    from paper_2507_04147_gb300 import synth
+    sc = synth.uniform_scene(1_000_000, 3, seed=5)
+    cam = synth.pinhole_camera(1024, 1024)
+    scene = a3fr.Scene.from_numpy(sc)
+    scene.set_camera(0, cam)
+    scene.keep_aux(True)
+    out = torch.empty((1, 1024, 1024, 3), dtype=torch.float32, device=device)
+    gen = torch.Generator(device=device).manual_seed(0)
+    dl = torch.randn((1, 1024, 1024, 3), dtype=torch.float32, device=device, generator=gen)
+    names = ("means", "log_scales", "quats", "opacity_logits", "sh")
+    grads = [torch.empty_like(t) for t in scene._tensors]
+    yaws = np.linspace(0.0, 3.0, 16)
+
+    def step(k, ev=None):
+        scene.set_camera(0, synth.pinhole_camera(1024, 1024, yaw_deg=float(yaws[k % len(yaws)])))
+        with torch.cuda.stream(render_stream):
+            flush.zero_()
+            if ev:
+                ev[0].record(render_stream)
+            scene.render_full(out=out, stream=render_stream)
+            if ev:
+                ev[1].record(render_stream)
+            a3fr.backward(scene.handle, dl, *grads, stream=render_stream)
+            if ev:
+                ev[2].record(render_stream)
+
+    for k in range(warmup):
+        step(k)
+    torch.cuda.synchronize()
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for k in range(steps):
+        step(k, evs[k])
+    torch.cuda.synchronize()
+    fwd = np.array([a.elapsed_time(b) for a, b, _ in evs])
+    bwd = np.array([b.elapsed_time(c) for _, b, c in evs])
+    st = scene.stats()
+    scene.close()
+    return {"workload": "1M-G SH3 single view 1024x1024, full render + backward to all parameters",
+            "forward_ms_p50": float(np.percentile(fwd, 50)), "backward_ms_p50": float(np.percentile(bwd, 50)),
+            "step_ms_p50": float(np.percentile(fwd + bwd, 50)),
+            "steps_per_s": 1000.0 / float((fwd + bwd).mean()), "instances": st["instances"],
+            "gradients": list(names), "l2": "flushed before every step"}
 
 
 def incremental_latency(a3fr, scene, w, traj, out, stream, full_ms: float, frames: int = 40):
