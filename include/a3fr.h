@@ -236,6 +236,17 @@ typedef struct {
 
 int a3fr_backward(a3fr_scene *scene, const float *dl_drgb, const a3fr_grads *grads, void *stream);
 
+/* ------------------------------------------------------------ tensor-core building block
+ * No counterpart in the paper: the single-tile BF16 GEMM on the fifth-generation tensor
+ * cores (tcgen05) that the learned-periphery kernels are built from, exported so that its
+ * operand encodings can be checked on their own.  D[128][n] = A[128][k] * B[n][k]^T with
+ * A, B bf16 (uint16 bit patterns) and D fp32, all DEVICE, row-major, caller-owned;
+ * n in {16, 32}, k in {16, 32, 48, 64}; variant 0 is the descriptor layout the library uses,
+ * variant 1 swaps its two stride fields (a wrong layout gives wrong numbers, never an
+ * out-of-bounds access).  Synchronous; A3FR_ERR_TIMEOUT if the MMA never completed. */
+int a3fr_tc_tile_gemm(const uint16_t *A, const uint16_t *B, float *D, int n, int k, int variant,
+                      void *stream);
+
 /* Keep per-pixel transmittance and contributor counts of the next renders (aux buffers,
  * see a3fr_copy_buffer); off by default because they cost 8 bytes per pixel. */
 int a3fr_set_keep_aux(a3fr_scene *scene, int keep);

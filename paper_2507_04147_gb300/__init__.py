@@ -112,6 +112,13 @@ def backward(handle: int, dl_drgb, d_means, d_log_scales, d_quats, d_opacity_log
                "a3fr_backward")
 
 
+def tc_tile_gemm(a_bf16, b_bf16, d, variant: int = 0, stream=None) -> None:
+    """D[128][n] = A[128][k] B[n][k]^T on the tensor cores (bf16 tensors in, fp32 out)."""
+    _lib.check(_lib.load().a3fr_tc_tile_gemm(_ptr(a_bf16), _ptr(b_bf16), _ptr(d), b_bf16.shape[0],
+                                             a_bf16.shape[1], variant, _stream_ptr(stream)),
+               "a3fr_tc_tile_gemm")
+
+
 def get_stats(handle: int, reset: bool = False) -> dict:
     st = _lib.Stats()
     _lib.check(_lib.load().a3fr_get_stats(handle, ctypes.byref(st), int(reset)), "a3fr_get_stats")

@@ -106,6 +106,8 @@ _SIGS = {
     "a3fr_get_stats": ([ctypes.c_void_p, ctypes.POINTER(Stats), ctypes.c_int], ctypes.c_int),
     "a3fr_set_keep_aux": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_set_graph_mode": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "a3fr_tc_tile_gemm": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                           ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "a3fr_backward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Grads), ctypes.c_void_p],
                       ctypes.c_int),
     "a3fr_copy_buffer": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,
