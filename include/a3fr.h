@@ -277,6 +277,7 @@ int a3fr_get_stage_times(a3fr_scene *scene, int max_renders, float *ms, int *n_o
 #define A3FR_BUF_LEVELS 6     /* uint8 [n_eyes*tiles]: pixel-density level of each tile */
 #define A3FR_BUF_T_FINAL 7    /* fp32 [n_eyes][height][width] (keep_aux only) */
 #define A3FR_BUF_N_CONTRIB 8  /* uint32 [n_eyes][height][width] (keep_aux only) */
+#define A3FR_BUF_DEPTH 9      /* fp32 [n_eyes][height][width]: expected depth sum(alpha T z) (keep_aux only) */
 
 /* Copy `bytes` bytes of internal buffer `which` (A3FR_BUF_*) of the last render into the
  * DEVICE buffer dst, asynchronously on `stream`.  *needed (HOST, may be NULL) receives the

@@ -79,7 +79,7 @@ def lib():
         L.or_tile_ranges.argtypes = [i64, vp, i32, vp]
         L.or_layer_radii2.argtypes = [vp, vp, vp]
         L.or_level_map.argtypes = [vp, i32, vp, vp, vp]
-        L.or_render.argtypes = [i32, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp]
+        L.or_render.argtypes = [i32, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
         L.or_render_eye.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, i32,
                                     vp, vp, vp, vp, vp, vp]
         L.or_num_threads.restype = i32
@@ -182,6 +182,7 @@ class Image:
         self.n_eval = np.zeros(count, dtype=np.int32)
         self.margin = np.zeros(count, dtype=np.float32)
         self.rendered = np.zeros(count, dtype=np.uint8)
+        self.depth = np.zeros(count, dtype=np.float32)   # expected depth sum(alpha T z)
 
 
 def render(rec, rect, cam, tile: int, level=None, pixels=None) -> Image:
@@ -198,7 +199,7 @@ def render(rec, rect, cam, tile: int, level=None, pixels=None) -> Image:
     lib().or_render(n, _p(np.ascontiguousarray(rec)), _p(np.ascontiguousarray(rect)),
                     ctypes.byref(c), tile, _p(lv), _p(pix), count if pix is not None else 0,
                     _p(img.rgb), _p(img.t_final), _p(img.n_contrib), _p(img.n_eval),
-                    _p(img.margin), _p(img.rendered))
+                    _p(img.margin), _p(img.rendered), _p(img.depth))
     return img
 
 

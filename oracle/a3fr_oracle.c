@@ -358,9 +358,10 @@ static int or_cmp_order(const void *pa, const void *pb) {
 /* Front-to-back volume rendering of one pixel over the global depth-sorted list. */
 static void or_shade(int x, int y, int tile, const float *rec, const int32_t *rect,
                      const or_order *list, int n_vis, float out[3], float *t_final,
-                     int32_t *n_contrib, int32_t *n_eval, float *margin) {
+                     int32_t *n_contrib, int32_t *n_eval, float *margin, float *depth) {
   const int ptx = x / tile, pty = y / tile;
   float T = 1.0f, C[3] = {0.0f, 0.0f, 0.0f};
+  float Z = 0.0f;   /* expected depth: the blend weights applied to camera-space depth */
   int32_t contrib = 0, evals = 0;
   float m = INFINITY;
   for (int j = 0; j < n_vis; ++j) {
@@ -382,6 +383,7 @@ static void or_shade(int x, int y, int tile, const float *rec, const int32_t *re
     if (mt < m) m = mt;
     if (testT < 0.0001f) break;
     for (int ch = 0; ch < 3; ++ch) C[ch] += o[6 + ch] * alpha * T;
+    Z += o[9] * alpha * T;
     T = testT;
     contrib = evals;
   }
@@ -390,6 +392,7 @@ static void or_shade(int x, int y, int tile, const float *rec, const int32_t *re
   *n_contrib = contrib;
   *n_eval = evals;
   *margin = m;
+  if (depth) *depth = Z;
 }
 
 static or_order *or_global_list(int n, const float *rec, int *n_vis) {
@@ -412,11 +415,12 @@ static or_order *or_global_list(int n, const float *rec, int *n_vis) {
  * row-major order; otherwise the n_pix (x, y) pairs listed.  Per output pixel:
  * rgb[3], T_final, n_contrib, n_eval and the threshold margin of the pixel that was
  * actually shaded (the top-left one for inherited pixels); rendered[] is 1 when the
- * pixel itself was shaded. */
+ * pixel itself was shaded; depth (optional) is the expected depth sum(alpha T z) of the
+ * blended Gaussians, the usual 3DGS depth render. */
 void or_render(int n, const float *rec, const int32_t *rect, const or_camera *cam, int tile,
                const uint8_t *level, const int32_t *pix, int n_pix, float *rgb,
                float *t_final, int32_t *n_contrib, int32_t *n_eval, float *margin,
-               uint8_t *rendered) {
+               uint8_t *rendered, float *depth) {
   int n_vis = 0;
   or_order *list = or_global_list(n, rec, &n_vis);
   const int W = cam->width, H = cam->height;
@@ -435,7 +439,7 @@ void or_render(int n, const float *rec, const int32_t *rect, const or_camera *ca
       if (!live) { sx = x & ~1; sy = y & ~1; }
     }
     or_shade(sx, sy, tile, rec, rect, list, n_vis, rgb + 3 * p, t_final + p, n_contrib + p,
-             n_eval + p, margin + p);
+             n_eval + p, margin + p, depth ? depth + p : NULL);
     if (rendered) rendered[p] = (uint8_t)live;
   }
   free(list);
@@ -459,7 +463,7 @@ void or_render_eye(int n, int degree, const float *means, const float *log_scale
     or_level_map(cam, tile, fv, gaze, level);
   }
   or_render(n, rec, rect, cam, tile, level, pix, n_pix, rgb, t_final, n_contrib, n_eval,
-            margin, rendered);
+            margin, rendered, NULL);
   free(level);
   free(touched);
   free(rect);

@@ -16,7 +16,7 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import A3FRError, BUF_KEYS, BUF_LEVELS, BUF_N_CONTRIB, BUF_RANGES, BUF_RECORDS, \
+from ._lib import A3FRError, BUF_DEPTH, BUF_KEYS, BUF_LEVELS, BUF_N_CONTRIB, BUF_RANGES, BUF_RECORDS, \
     BUF_RECTS, BUF_T_FINAL, BUF_VALUES, STATUS_CAPACITY, STATUS_TIMEOUT
 
 __all__ = ["Scene", "Fovea", "A3FRError", "camera_struct", "create_scene", "destroy_scene",

@@ -20,7 +20,7 @@ NOALLOC_MAX_PAIRS = 262144
 
 STAGES = ("preprocess", "depth_sort", "tile_scan", "emit", "tile_sort", "composite")
 
-BUF_RECORDS, BUF_RECTS, BUF_KEYS, BUF_VALUES, BUF_RANGES, BUF_LEVELS, BUF_T_FINAL, BUF_N_CONTRIB = range(1, 9)
+BUF_RECORDS, BUF_RECTS, BUF_KEYS, BUF_VALUES, BUF_RANGES, BUF_LEVELS, BUF_T_FINAL, BUF_N_CONTRIB, BUF_DEPTH = range(1, 10)
 
 
 class SceneDesc(ctypes.Structure):

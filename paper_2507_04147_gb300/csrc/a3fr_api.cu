@@ -66,6 +66,7 @@ struct a3fr_scene {
   uint8_t *levels = nullptr;
   float *t_final = nullptr;
   uint32_t *n_contrib = nullptr;
+  float *depth = nullptr;                    // expected depth per pixel (keep_aux only)
   // instance workspace
   size_t capacity = 0;
   bool auto_capacity = false;
@@ -186,6 +187,7 @@ void free_frame_buffers(a3fr_scene *s) {
   s->round_ready = false;
   dfree(s->levels);
   dfree(s->t_final);
+  dfree(s->depth);
   dfree(s->n_contrib);
   s->alloc_eyes = 0;
 }
@@ -265,6 +267,7 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
   A3FR_CHECK(cudaMalloc(&s->levels, (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->t_final, sizeof(float) * (size_t)W * H * eyes));
   A3FR_CHECK(cudaMalloc(&s->n_contrib, sizeof(uint32_t) * (size_t)W * H * eyes));
+  A3FR_CHECK(cudaMalloc(&s->depth, sizeof(float) * (size_t)W * H * eyes));
   A3FR_CHECK(cudaMemset(s->ranges, 0, sizeof(uint2) * (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMemset(s->levels, 0, (size_t)s->n_tiles * eyes));
   s->alloc_eyes = eyes;
@@ -529,7 +532,8 @@ int enqueue_comp(a3fr_scene *s, const CompositeParams &cp, int uniform, uint8_t 
   A3FR_CHECK(launch_composite(cp, &s->params_dev->comp, s->rec, s->desc.n, s->ranges, s->counts,
                               s->tvals[b], s->gaze_dev, nullptr, uniform, cur, s->plan, s->levels,
                               s->keep_aux ? s->t_final : nullptr,
-                              s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
+                              s->keep_aux ? s->n_contrib : nullptr,
+                              s->keep_aux ? s->depth : nullptr, s->counters, stream));
   *launches += cp.full ? 1 : 2;
   A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));
   return A3FR_OK;
@@ -670,7 +674,8 @@ int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
   A3FR_CHECK(launch_composite(hp.comp, &s->params_dev->comp, s->rec, s->desc.n, s->ranges,
                               s->counts, s->tvals[b], s->gaze_dev, s->round_plan, 0, s->cur_level,
                               s->plan, s->levels, s->keep_aux ? s->t_final : nullptr,
-                              s->keep_aux ? s->n_contrib : nullptr, s->counters, stream));
+                              s->keep_aux ? s->n_contrib : nullptr,
+                              s->keep_aux ? s->depth : nullptr, s->counters, stream));
   rc = finish_render(s, stream);
   if (rc != A3FR_OK) return rc;
   s->launches += 3;
@@ -986,6 +991,7 @@ int a3fr_copy_buffer(a3fr_scene *s, int which, void *dst, size_t bytes, size_t *
     case A3FR_BUF_LEVELS: src = s->levels; size = (size_t)s->n_tiles * eyes; break;
     case A3FR_BUF_T_FINAL: src = s->t_final; size = sizeof(float) * (size_t)s->W * s->H * eyes; break;
     case A3FR_BUF_N_CONTRIB: src = s->n_contrib; size = sizeof(uint32_t) * (size_t)s->W * s->H * eyes; break;
+    case A3FR_BUF_DEPTH: src = s->depth; size = sizeof(float) * (size_t)s->W * s->H * eyes; break;
     default: return A3FR_ERR_INVALID_ARG;
   }
   if (needed) *needed = size;

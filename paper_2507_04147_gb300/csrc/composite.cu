@@ -116,11 +116,12 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
                  const uint32_t *__restrict__ vals, const uint32_t *__restrict__ plan,
                  const uint32_t *__restrict__ plan_counts, int incremental,
                  uint8_t *__restrict__ levels, float *__restrict__ t_final,
-                 uint32_t *__restrict__ n_contrib, unsigned long long *__restrict__ counters) {
+                 uint32_t *__restrict__ n_contrib, float *__restrict__ depth,
+                 unsigned long long *__restrict__ counters) {
   const CompositeParams &p = *pp;   // per-render parameters in device memory
   float *out = p.out;
   __shared__ float4 s_geo[kThreads];   // u, v, -0.5 log2e a, -log2e b
-  __shared__ float s_c[kThreads];      // -0.5 log2e c
+  __shared__ float2 s_cz[kThreads];    // -0.5 log2e c, camera-space depth
   __shared__ float4 s_rgb[kThreads];   // r, g, b, opacity
   __shared__ int s_done[kThreads / 32];
   __shared__ float s_out[4][kTile][kTile * 3];   // the tiles of the CTA, assembled for stores
@@ -191,6 +192,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
   const float *rec_eye = rec + (size_t)eye * n * kRec;
 
   float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f;
+  float Z = 0.0f;                      // expected depth (auxiliary output)
   uint32_t last = 0;                   // 1-based position of the last contributor
   uint32_t stop = 0;                   // Gaussians evaluated when the pixel stopped
   bool done = !inside;
@@ -220,12 +222,12 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
       const float4 *r4 = reinterpret_cast<const float4 *>(rec_eye + (size_t)gidx * kRec);
       const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
       s_geo[threadIdx.x] = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
-      s_c[threadIdx.x] = __fmul_rn(-0.5f * kLog2e, b.x);
+      s_cz[threadIdx.x] = make_float2(__fmul_rn(-0.5f * kLog2e, b.x), c.y);
       s_rgb[threadIdx.x] = make_float4(b.z, b.w, c.x, b.y);
     } else if ((uint32_t)gt < ((cnt + 3u) & ~3u)) {
       // padding up to a multiple of 4: zero opacity never passes the 1/255 test
       s_geo[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      s_c[threadIdx.x] = 0.0f;
+      s_cz[threadIdx.x] = make_float2(0.0f, 0.0f);
       s_rgb[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
     }
     group_sync(gsize, gbar);
@@ -240,7 +242,8 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
         for (int j = 0; j < 4; ++j) {
           const int e = gfirst + (int)k + j;
           const float4 geo = s_geo[e];
-          const float cc = s_c[e];
+          const float2 cz = s_cz[e];
+          const float cc = cz.x;
           const float4 rgb = s_rgb[e];
           const float dx = __fsub_rn(geo.x, fpx), dy = __fsub_rn(geo.y, fpy);
           // power * log2(e) = -0.5 log2e (a dx^2 + c dy^2) - log2e b dx dy
@@ -255,6 +258,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
           C0 += rgb.x * w;
           C1 += rgb.y * w;
           C2 += rgb.z * w;
+          if (kAux) Z += cz.y * w;
           T = upd ? tt : T;
           last = upd ? pos : last;
           stop = fin ? pos : stop;
@@ -280,6 +284,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
         const size_t pix = ((size_t)eye * p.height + py) * p.width + px;
         t_final[pix] = T;
         n_contrib[pix] = last;
+        depth[pix] = Z;
       }
     }
   } else {
@@ -294,6 +299,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
         const size_t pix = ((size_t)eye * p.height + py) * p.width + px;
         t_final[pix] = T;
         n_contrib[pix] = last;
+        depth[pix] = Z;
       }
       if (group == 0) {
 #pragma unroll
@@ -309,6 +315,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
               const size_t pix = ((size_t)eye * p.height + py + dy) * p.width + px + dx;
               t_final[pix] = T;
               n_contrib[pix] = last;
+        depth[pix] = Z;
             }
           }
         }
@@ -343,8 +350,8 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
                              const float *rec, int n, const uint2 *ranges, const uint32_t *kept,
                              const uint32_t *vals, const float *gaze, const RoundPlan *round,
                              int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
-                             float *t_final, uint32_t *n_contrib, unsigned long long *counters,
-                             cudaStream_t s) {
+                             float *t_final, uint32_t *n_contrib, float *depth,
+                             unsigned long long *counters, cudaStream_t s) {
   const int n_ranges = p.n_eyes * p.n_tiles;
   if (n_ranges <= 0) return cudaSuccess;
   uint32_t *pc = plan + 4 * (size_t)n_ranges;
@@ -371,17 +378,17 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
   if (t_final != nullptr) {
     if (p.full)
       composite_kernel<true, true><<<n_ranges, kThreads, 0, s>>>(
-          p_dev, rec, n, ranges, kept, vals, plan, pc, 0, levels, t_final, n_contrib, counters);
+          p_dev, rec, n, ranges, kept, vals, plan, pc, 0, levels, t_final, n_contrib, depth, counters);
     else
       composite_kernel<true, false><<<n_ranges, kThreads, 0, s>>>(
-          p_dev, rec, n, ranges, kept, vals, plan, pc, inc, levels, t_final, n_contrib, counters);
+          p_dev, rec, n, ranges, kept, vals, plan, pc, inc, levels, t_final, n_contrib, depth, counters);
   } else {
     if (p.full)
       composite_kernel<false, true><<<n_ranges, kThreads, 0, s>>>(
-          p_dev, rec, n, ranges, kept, vals, plan, pc, 0, levels, t_final, n_contrib, counters);
+          p_dev, rec, n, ranges, kept, vals, plan, pc, 0, levels, t_final, n_contrib, depth, counters);
     else
       composite_kernel<false, false><<<n_ranges, kThreads, 0, s>>>(
-          p_dev, rec, n, ranges, kept, vals, plan, pc, inc, levels, t_final, n_contrib, counters);
+          p_dev, rec, n, ranges, kept, vals, plan, pc, inc, levels, t_final, n_contrib, depth, counters);
   }
   return cudaGetLastError();
 }

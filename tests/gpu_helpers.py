@@ -41,6 +41,7 @@ def run(scene_np, cams, gaze=None, fovea=None, full=False, capacity=0, keep_aux=
     if keep_aux:
         r["t_final"] = s.buffer(a3fr.BUF_T_FINAL, torch.float32).cpu().numpy().reshape(eyes, H, W)
         r["n_contrib"] = s.buffer(a3fr.BUF_N_CONTRIB, torch.int32).cpu().numpy().reshape(eyes, H, W)
+        r["depth"] = s.buffer(a3fr.BUF_DEPTH, torch.float32).cpu().numpy().reshape(eyes, H, W)
     r["stats"] = s.stats()
     return r
 

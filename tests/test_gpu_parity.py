@@ -56,6 +56,9 @@ def check_eye(r, e, scene_np, cam, tile=16, gaze=None, fv=None, full=False, pixe
             assert np.abs(tf - ref.t_final)[ok].max() <= 2e-4
             nc = r["n_contrib"][e].reshape(-1)
             assert np.array_equal(nc[ok], ref.n_contrib[ok])
+            # expected depth: the blend weights (2e-4 each) times depths of a few units
+            dz = r["depth"][e].reshape(-1)
+            assert np.abs(dz - ref.depth)[ok].max() <= 2e-3
     else:
         got = img[pixels[:, 1], pixels[:, 0]]
         info = gh.compare_pixels(got, ref)

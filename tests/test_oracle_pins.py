@@ -237,6 +237,19 @@ def test_stack_front_to_back_and_early_stop_closed_form():
     np.testing.assert_allclose(img.rgb[p], ref, rtol=1e-5)
     np.testing.assert_allclose(img.t_final[p], 0.05 ** 3, rtol=1e-4)
     assert img.n_contrib[p] == 3 and img.n_eval[p] == 4
+    # expected depth: the same blend weights applied to the three depths
+    np.testing.assert_allclose(img.depth[p], sum(depths[k] * 0.95 * 0.05 ** k for k in range(3)),
+                               rtol=1e-5)
+
+
+def test_depth_of_uniform_depth_scene_is_coverage_times_depth():
+    """All Gaussians at one depth z: the expected depth is z (1 - T_final) at every pixel."""
+    scene = synth.uniform_scene(2000, 0, seed=6)
+    scene.means[:, 2] = 3.25
+    cam = _cam(64, 48)
+    rec, rect, _ = oracle.preprocess(scene, cam, 16)
+    img = oracle.render(rec, rect, cam, 16)
+    np.testing.assert_allclose(img.depth, 3.25 * (1.0 - img.t_final), atol=2e-5)
 
 
 def test_weight_sum_and_white_colour_invariant():
