@@ -1,0 +1,80 @@
+"""Pins of the learned-periphery reference network (oracle/cnn.py) -- CPU only."""
+import numpy as np
+import torch
+import torch.nn.functional as F
+
+from oracle import cnn
+
+
+def test_library_conv_equals_loop_definition():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(7, 9, 5))
+    w = rng.normal(size=(4, 5, 3, 3))
+    b = rng.normal(size=4)
+    ref = cnn.conv3x3_loops(x, w, b)
+    got = F.conv2d(torch.tensor(x).permute(2, 0, 1)[None], torch.tensor(w), torch.tensor(b),
+                   padding=1)[0].permute(1, 2, 0).numpy()
+    np.testing.assert_allclose(got, ref, rtol=1e-12, atol=1e-12)
+
+
+def test_shuffle_places_each_subpixel():
+    B, H2, W2 = 1, 2, 3
+    r = torch.arange(B * H2 * W2 * 16, dtype=torch.float64).reshape(B, H2, W2, 16)
+    tl = torch.full((B, H2, W2, 3), 1000.0, dtype=torch.float64)
+    out = cnn.shuffle(r, tl, 4, 5)                 # ragged: the last column is cut
+    assert out.shape == (1, 4, 5, 3)
+    for y in range(4):
+        for x in range(5):
+            for c in range(3):
+                k = c * 4 + 2 * (y % 2) + (x % 2)
+                assert out[0, y, x, c] == 1000.0 + r[0, y // 2, x // 2, k]
+
+
+def test_gradients_equal_central_differences():
+    cnn.QUANTIZE = False
+    try:
+        rng = np.random.default_rng(1)
+        ws, bs = cnn.init_params(3)
+        ws = [w + rng.normal(0, 0.05, w.shape).astype(np.float32) for w in ws]
+        bs = [b + rng.normal(0, 0.05, b.shape).astype(np.float32) for b in bs]
+        img = rng.uniform(size=(1, 10, 12, 3))
+        depth = rng.uniform(2, 6, size=(1, 10, 12))
+        x0, tl = cnn.make_input(img, depth)
+        target = img + rng.normal(0, 0.05, img.shape)
+        loss, gw, gb, _ = cnn.loss_and_grads(x0, tl, target, ws, bs)
+
+        def L(ws_, bs_):
+            r = cnn.forward(torch.tensor(x0, dtype=torch.float64),
+                            [torch.tensor(np.asarray(w, np.float64)) for w in ws_],
+                            [torch.tensor(np.asarray(b, np.float64)) for b in bs_])
+            pred = cnn.shuffle(r, torch.tensor(tl, dtype=torch.float64), 10, 12)
+            return float(((pred - torch.tensor(target)) ** 2).mean())
+
+        h = 1e-6
+        for li, idx in [(0, (3, 1, 0, 2)), (4, (7, 30, 1, 1)), (9, (5, 12, 2, 0)), (9, (11, 0, 1, 1))]:
+            wp = [np.asarray(w, np.float64).copy() for w in ws]
+            wm = [np.asarray(w, np.float64).copy() for w in ws]
+            wp[li][idx] += h
+            wm[li][idx] -= h
+            fd = (L(wp, bs) - L(wm, bs)) / (2 * h)
+            assert abs(fd - gw[li][idx]) <= 1e-6 * max(1.0, abs(fd)), (li, idx, fd, gw[li][idx])
+        for li, k in [(2, 5), (9, 7)]:
+            bp = [np.asarray(b, np.float64).copy() for b in bs]
+            bm = [np.asarray(b, np.float64).copy() for b in bs]
+            bp[li][k] += h
+            bm[li][k] -= h
+            fd = (L(ws, bp) - L(ws, bm)) / (2 * h)
+            assert abs(fd - gb[li][k]) <= 1e-6 * max(1.0, abs(fd))
+    finally:
+        cnn.QUANTIZE = True
+
+
+def test_initial_network_is_near_the_inherit_fill():
+    rng = np.random.default_rng(2)
+    ws, bs = cnn.init_params(0)
+    img = rng.uniform(size=(1, 32, 32, 3))
+    x0, tl = cnn.make_input(img, rng.uniform(2, 6, size=(1, 32, 32)))
+    r = cnn.forward(torch.tensor(x0, dtype=torch.float64), [torch.tensor(np.asarray(w, np.float64)) for w in ws],
+                    [torch.tensor(np.asarray(b, np.float64)) for b in bs])
+    assert r[..., 12:].abs().max() == 0.0          # the padding outputs are exactly zero
+    assert r[..., :12].abs().mean() < 0.5
