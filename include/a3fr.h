@@ -247,6 +247,46 @@ int a3fr_backward(a3fr_scene *scene, const float *dl_drgb, const a3fr_grads *gra
 int a3fr_tc_tile_gemm(const uint16_t *A, const uint16_t *B, float *D, int n, int k, int variant,
                       void *stream);
 
+/* ------------------------------------------------------------------- learned periphery
+ * Not in the paper (its un-rendered pixels "inherit or interpolate", Sec. 3.4): a small
+ * residual CNN that predicts the pixels a foveated render skipped from the quarter-density
+ * layer (the top-left pixel of every 2x2 block, which every level renders) and its expected
+ * depth.  Network: 3x3 conv 16->32 + ReLU; four residual blocks (3x3 conv 32->32 + ReLU,
+ * 3x3 conv 32->32, skip); 3x3 conv 32->16 whose channel c*4 + 2*dy + dx is the correction
+ * of colour c at sub-pixel (dx, dy) of the block, added to the block's top-left colour.
+ * BF16 weights and activations, FP32 accumulation, all convolutions on the tensor cores
+ * (tcgen05); inputs (r, g, b, depth/8) per block.  Parameters: fp32, layer by layer the
+ * weights [out][in][3][3] (layer 0's input channels 4..15 unused), then the biases; the
+ * library keeps Adam state for training.  The object owns its device memory; one object per
+ * host thread. */
+typedef struct a3fr_cnn a3fr_cnn;
+
+size_t a3fr_cnn_param_count(void);
+int a3fr_cnn_create(a3fr_cnn **out);                    /* zero parameters */
+int a3fr_cnn_destroy(a3fr_cnn *net);
+/* host fp32 [a3fr_cnn_param_count()]; set resets the Adam state; both synchronous */
+int a3fr_cnn_set_params(a3fr_cnn *net, const float *host, size_t count);
+int a3fr_cnn_get_params(a3fr_cnn *net, float *host, size_t count);
+/* img: DEVICE fp32 [b][h][w][3], depth: DEVICE fp32 [b][h][w] (expected depth).  Runs the
+ * network on the top-left pixels; residual_out (optional, DEVICE fp32 [b][(h+1)/2][(w+1)/2][16])
+ * receives the per-block corrections.  Asynchronous on stream. */
+int a3fr_cnn_forward(a3fr_cnn *net, const float *img, const float *depth, int b, int h, int w,
+                     float *residual_out, void *stream);
+/* Mean squared error of the prediction (top-left colour + correction at every pixel) against
+ * target (DEVICE fp32 [b][h][w][3]) and its gradient with respect to every parameter, into
+ * host_grads (host fp32 [a3fr_cnn_param_count()]) and *loss; synchronous. */
+int a3fr_cnn_grads(a3fr_cnn *net, const float *img, const float *depth, const float *target, int b,
+                   int h, int w, float *host_grads, float *loss, void *stream);
+/* One Adam step (beta 0.9 / 0.999) on the same loss; *loss (optional) makes it synchronous.
+ * A3FR_ERR_TIMEOUT if a tensor-core wait gave up (the step's numbers are then unreliable). */
+int a3fr_cnn_train_step(a3fr_cnn *net, const float *img, const float *depth, const float *target,
+                        int b, int h, int w, float lr, float *loss, void *stream);
+/* Learned fill of the scene's last render, which must be a3fr_render_foveated with keep_aux
+ * on (for its depth) writing out_rgb: rendered pixels are kept, every skipped pixel becomes its
+ * block's top-left colour plus the network's correction.  A3FR_ERR_NOT_READY otherwise.
+ * Asynchronous on stream (ordered after the render). */
+int a3fr_cnn_fill(a3fr_cnn *net, a3fr_scene *scene, float *out_rgb, void *stream);
+
 /* Keep per-pixel transmittance and contributor counts of the next renders (aux buffers,
  * see a3fr_copy_buffer); off by default because they cost 8 bytes per pixel. */
 int a3fr_set_keep_aux(a3fr_scene *scene, int keep);

@@ -108,6 +108,20 @@ _SIGS = {
     "a3fr_set_graph_mode": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_tc_tile_gemm": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                            ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
+    "a3fr_cnn_param_count": ([], ctypes.c_size_t),
+    "a3fr_cnn_create": ([ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "a3fr_cnn_destroy": ([ctypes.c_void_p], ctypes.c_int),
+    "a3fr_cnn_set_params": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "a3fr_cnn_get_params": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
+    "a3fr_cnn_forward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                          ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "a3fr_cnn_grads": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                        ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.POINTER(ctypes.c_float),
+                        ctypes.c_void_p], ctypes.c_int),
+    "a3fr_cnn_train_step": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int,
+                             ctypes.c_int, ctypes.c_int, ctypes.c_float, ctypes.POINTER(ctypes.c_float),
+                             ctypes.c_void_p], ctypes.c_int),
+    "a3fr_cnn_fill": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "a3fr_backward": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(Grads), ctypes.c_void_p],
                       ctypes.c_int),
     "a3fr_copy_buffer": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_size_t,

@@ -688,6 +688,19 @@ int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
 
 int a3fr::scene_eyes(const a3fr_scene *s) { return n_eyes_of(s); }
 
+bool a3fr::scene_fill_view(a3fr_scene *s, FillView *v) {
+  if (!s || !v || s->bw_mode != 2 || s->last_eyes == 0) return false;
+  v->depth = s->depth;
+  v->levels = s->levels;
+  v->eyes = s->last_eyes;
+  v->width = s->cams[0].width;
+  v->height = s->cams[0].height;
+  v->tile = s->desc.tile;
+  v->tiles_x = s->TX;
+  v->n_tiles = s->n_tiles;
+  return true;
+}
+
 extern "C" {
 
 int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3fr_scene **out) {

@@ -7,6 +7,11 @@
 // convolution kernels use them.
 #include "../../include/a3fr.h"
 #include "common.cuh"
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <new>
+
 #include "tc.cuh"
 
 namespace a3fr {
@@ -71,6 +76,568 @@ tc_tile_gemm_kernel(const uint16_t *__restrict__ A, const uint16_t *__restrict__
   if (warp == 0) tc::tmem_dealloc(tmem, 256);
 }
 
+
+// ---------------------------------------------------------------- convolution kernels
+// Activations are NHWC BF16 with 16 or 32 channels (32 or 64 bytes per pixel); a 3x3 "same"
+// convolution is an implicit GEMM  D[pixel][cout] = sum over (tap, cin) of X[pixel + tap][cin]
+// W[cout][cin][tap].  The A operand is never expanded: the tile's input halo sits in shared
+// memory as [channel group of 8][row][column][8 channels], which is exactly the K-major core-
+// matrix layout (8 pixels x 16 bytes) with the column direction inside a core matrix, so the
+// operand of tap (ky, kx) is the same halo seen from a start address shifted by ky rows and kx
+// columns.  Weights come pre-packed as [tap][cin group][cout][8 cin].
+
+constexpr int kConvTW = 8;    // output tile width (pixels)
+constexpr int kConvTH = 16;   // output tile height: 128 pixels = the MMA's M
+
+struct ConvDims {
+  int B, H, W;
+};
+
+enum : int { kEpiBias = 1, kEpiRelu = 2, kEpiResid = 4, kEpiMask = 8, kEpiF32 = 16 };
+
+// Halo rows x cols of 8-channel groups around the tile whose top-left output pixel is (y0, x0).
+template <int CG>
+__device__ __forceinline__ void load_halo(uint8_t *hs, const __nv_bfloat16 *__restrict__ X, int b,
+                                          int y0, int x0, int rows, int cols, int H, int W) {
+  const int total = rows * cols * CG;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int cg = i % CG, rc = i / CG;
+    const int c = rc % cols, r = rc / cols;
+    const int y = y0 - 1 + r, x = x0 - 1 + c;
+    uint4 v = make_uint4(0, 0, 0, 0);
+    if (y >= 0 && y < H && x >= 0 && x < W)
+      v = __ldg(reinterpret_cast<const uint4 *>(X + (((size_t)b * H + y) * W + x) * (CG * 8)) + cg);
+    *reinterpret_cast<uint4 *>(hs + ((size_t)(cg * rows + r) * cols + c) * 16) = v;
+  }
+}
+
+template <int CIN, int COUT>
+constexpr int conv_smem_bytes() {
+  return (CIN / 8) * (kConvTH + 2) * (kConvTW + 2) * 16 + 9 * (CIN / 8) * COUT * 16;
+}
+
+// One 8 x 16 output tile per CTA (128 threads = one thread per output pixel in the epilogue).
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128)
+conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *__restrict__ Wpk,
+                  const float *__restrict__ bias, const __nv_bfloat16 *__restrict__ R,
+                  const __nv_bfloat16 *__restrict__ Mk, void *__restrict__ Y, int flags,
+                  uint32_t *__restrict__ status) {
+  constexpr int CG = CIN / 8, HR = kConvTH + 2, HC = kConvTW + 2;
+  constexpr int HALO = CG * HR * HC * 16, WBYTES = 9 * CG * COUT * 16;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t *hs = smem, *ws = smem + HALO;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int x0 = blockIdx.x * kConvTW, y0 = blockIdx.y * kConvTH, b = blockIdx.z;
+  if (warp == 0) tc::tmem_alloc(&s_tmem, 32);
+  for (int i = t; i < WBYTES / 16; i += 128) reinterpret_cast<uint4 *>(ws)[i] = __ldg(Wpk + i);
+  load_halo<CG>(hs, X, b, y0, x0, HR, HC, d.H, d.W);
+  tc::fence_proxy_async();
+  if (t == 0) tc::mbar_init(&s_bar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  if (t == 0) {
+    const uint32_t h0 = tc::smem_u32(hs), w0 = tc::smem_u32(ws);
+    const uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+    int k = 0;
+#pragma unroll 1
+    for (int tap = 0; tap < 9; ++tap) {
+      const int ky = tap / 3, kx = tap - 3 * ky;
+#pragma unroll
+      for (int cb = 0; cb < CIN / 16; ++cb) {
+        const uint64_t a = tc::smem_desc(h0 + (2 * cb) * (HR * HC * 16) + ky * (HC * 16) + kx * 16,
+                                         HR * HC * 16, HC * 16);
+        const uint64_t w = tc::smem_desc(w0 + tap * (CG * COUT * 16) + (2 * cb) * (COUT * 16), COUT * 16, 128);
+        tc::mma_bf16(tmem, a, w, idesc, k > 0);
+        ++k;
+      }
+    }
+    tc::mma_commit(&s_bar);
+  }
+  if (!tc::mbar_wait(&s_bar, 0) && lane == 0) atomicOr(status, kStatusTimeout);
+  tc::fence_after_sync();
+  float v[32];
+  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  if (COUT == 32) tc::tmem_ld32(taddr, v);
+  else tc::tmem_ld16(taddr, v);
+  const int m = warp * 32 + lane;
+  const int y = y0 + m / kConvTW, x = x0 + (m % kConvTW);
+  if (y < d.H && x < d.W) {
+    const size_t pix = ((size_t)b * d.H + y) * d.W + x;
+#pragma unroll
+    for (int g = 0; g < COUT / 8; ++g) {
+      float o[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        o[c] = v[g * 8 + c];
+        if (flags & kEpiBias) o[c] += bias[g * 8 + c];
+        if (flags & kEpiRelu) o[c] = fmaxf(o[c], 0.0f);
+      }
+      if (flags & kEpiResid) {
+        const uint4 rv = __ldg(reinterpret_cast<const uint4 *>(R + pix * COUT) + g);
+        const __nv_bfloat16 *rb = reinterpret_cast<const __nv_bfloat16 *>(&rv);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) o[c] += __bfloat162float(rb[c]);
+      }
+      if (flags & kEpiMask) {
+        const uint4 mv = __ldg(reinterpret_cast<const uint4 *>(Mk + pix * COUT) + g);
+        const __nv_bfloat16 *mb = reinterpret_cast<const __nv_bfloat16 *>(&mv);
+#pragma unroll
+        for (int c = 0; c < 8; ++c) o[c] = __bfloat162float(mb[c]) > 0.0f ? o[c] : 0.0f;
+      }
+      if (flags & kEpiF32) {
+        float4 *yo = reinterpret_cast<float4 *>(static_cast<float *>(Y) + pix * COUT + g * 8);
+        yo[0] = make_float4(o[0], o[1], o[2], o[3]);
+        yo[1] = make_float4(o[4], o[5], o[6], o[7]);
+      } else {
+        uint4 pk;
+        __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p2[c] = __floats2bfloat162_rn(o[2 * c], o[2 * c + 1]);
+        reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(Y) + pix * COUT)[g] = pk;
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 32);
+}
+
+// Weight gradient  dW[cout][cin][tap] += sum over pixels of X[pixel + tap][cin] dY[pixel][cout]
+// as D[(tap, cin)][cout] = A[(tap, cin)][pixel] B[cout][pixel]^T with K = pixels: per 8 x 8
+// pixel tile the CTA transposes the halo into A (K-major, one M-tile per 128 (tap, cin) rows)
+// and dY into B, and accumulates in tensor memory over the tiles it owns; the bias gradient
+// is summed alongside.  Partial results are added to the fp32 outputs with atomics.
+constexpr int kWgTile = 8;   // 8 x 8 pixel tiles, K = 64 per tile
+
+template <int CIN, int COUT>
+constexpr int wgrad_mtiles() { return (9 * CIN + 127) / 128; }
+
+template <int CIN, int COUT>
+constexpr int wgrad_smem_bytes() {
+  return wgrad_mtiles<CIN, COUT>() * 16384 + (COUT / 8) * 1024 + (CIN / 8) * (kWgTile + 2) * (kWgTile + 2) * 16;
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128)
+conv3x3_wgrad_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X,
+                        const __nv_bfloat16 *__restrict__ dY, float *__restrict__ dW,
+                        float *__restrict__ db, int tiles_per_cta, uint32_t *__restrict__ status) {
+  constexpr int CG = CIN / 8, MT = wgrad_mtiles<CIN, COUT>(), HR = kWgTile + 2, HC = kWgTile + 2;
+  constexpr int ABYTES = MT * 16384, BBYTES = (COUT / 8) * 1024;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t *as = smem, *bs = smem + ABYTES, *hs = smem + ABYTES + BBYTES;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int tx_n = (d.W + kWgTile - 1) / kWgTile, ty_n = (d.H + kWgTile - 1) / kWgTile;
+  const int n_tiles = d.B * tx_n * ty_n;
+  if (warp == 0) tc::tmem_alloc(&s_tmem, 128);
+  if (t == 0) tc::mbar_init(&s_bar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  constexpr int BG = COUT / 8;           // 8-channel groups of dY
+  const int my_g = t % BG;               // every (pixel, group) entry of this thread has group my_g
+  float dbl[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  int issued = 0;
+  for (int q = 0; q < tiles_per_cta; ++q) {
+    const int tt = blockIdx.x * tiles_per_cta + q;
+    if (tt >= n_tiles) break;
+    const int b = tt / (tx_n * ty_n), rem = tt - b * (tx_n * ty_n);
+    const int y0 = (rem / tx_n) * kWgTile, x0 = (rem % tx_n) * kWgTile;
+    if (issued > 0) {   // the previous tile's MMAs still read A and B
+      if (!tc::mbar_wait(&s_bar, (issued - 1) & 1) && lane == 0) atomicOr(status, kStatusTimeout);
+      tc::fence_after_sync();
+    }
+    load_halo<CG>(hs, X, b, y0, x0, HR, HC, d.H, d.W);
+    // B[cout][pixel]: entry e = (pixel, group of 8 couts)
+    for (int e = t; e < 64 * BG; e += 128) {
+      const int p = e / BG, g = e - (e / BG) * BG;
+      const int y = y0 + p / kWgTile, x = x0 + (p % kWgTile);
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (y < d.H && x < d.W) v = __ldg(reinterpret_cast<const uint4 *>(dY + (((size_t)b * d.H + y) * d.W + x) * COUT) + g);
+      const __nv_bfloat16 *vb = reinterpret_cast<const __nv_bfloat16 *>(&v);
+      uint8_t *dst = bs + g * 1024 + (p >> 3) * 128 + (p & 7) * 2;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        *reinterpret_cast<__nv_bfloat16 *>(dst + c * 16) = vb[c];
+        dbl[c] += __bfloat162float(vb[c]);
+      }
+    }
+    __syncthreads();   // halo complete
+    // A[(tap, cin)][pixel]: entry e = (pixel, tap, channel group)
+    for (int e = t; e < 64 * 9 * CG; e += 128) {
+      const int cg = e % CG, pt = e / CG;
+      const int tap = pt % 9, p = pt / 9;
+      const int ky = tap / 3, kx = tap - 3 * ky;
+      const int oy = p / kWgTile, ox = p % kWgTile;
+      const uint4 v = *reinterpret_cast<const uint4 *>(hs + ((size_t)(cg * HR + oy + ky) * HC + ox + kx) * 16);
+      const __nv_bfloat16 *vb = reinterpret_cast<const __nv_bfloat16 *>(&v);
+      const int row = tap * CIN + cg * 8;    // 8 consecutive rows: one core matrix's rows
+      const int mt = row >> 7, i = row & 127;
+      uint8_t *dst = as + mt * 16384 + (i >> 3) * 1024 + (p >> 3) * 128 + (p & 7) * 2;
+#pragma unroll
+      for (int c = 0; c < 8; ++c) *reinterpret_cast<__nv_bfloat16 *>(dst + c * 16) = vb[c];
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (t == 0) {
+      const uint32_t a0 = tc::smem_u32(as), b0 = tc::smem_u32(bs);
+      const uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+#pragma unroll
+      for (int mt = 0; mt < MT; ++mt)
+#pragma unroll
+        for (int kc = 0; kc < 4; ++kc)
+          tc::mma_bf16(tmem + mt * COUT, tc::smem_desc(a0 + mt * 16384 + kc * 256, 128, 1024),
+                       tc::smem_desc(b0 + kc * 256, 128, 1024), idesc, issued > 0 || kc > 0);
+      tc::mma_commit(&s_bar);
+    }
+    ++issued;
+  }
+  // bias gradient: lanes with the same channel group are BG apart within the warp
+#pragma unroll
+  for (int c = 0; c < 8; ++c)
+    for (int o = BG; o < 32; o <<= 1) dbl[c] += __shfl_xor_sync(0xffffffffu, dbl[c], o);
+  if (lane < BG)
+#pragma unroll
+    for (int c = 0; c < 8; ++c) atomicAdd(db + my_g * 8 + c, dbl[c]);
+  if (issued > 0) {
+    if (!tc::mbar_wait(&s_bar, (issued - 1) & 1) && lane == 0) atomicOr(status, kStatusTimeout);
+    tc::fence_after_sync();
+#pragma unroll 1
+    for (int mt = 0; mt < MT; ++mt) {
+      float v[32];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + mt * COUT;
+      if (COUT == 32) tc::tmem_ld32(taddr, v);
+      else tc::tmem_ld16(taddr, v);
+      const int row = mt * 128 + warp * 32 + lane;
+      if (row < 9 * CIN) {
+        const int tap = row / CIN, ci = row - tap * CIN;
+#pragma unroll
+        for (int co = 0; co < COUT; ++co) atomicAdd(dW + ((size_t)co * CIN + ci) * 9 + tap, v[co]);
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, 128);
+}
+
+// ------------------------------------------------------- CUDA-core helpers of the network
+// x0[b][y2][x2] = (r, g, b, depth / 8, 0 ...) of the top-left pixel of each 2x2 block.
+__global__ void gather_input_kernel(const float *__restrict__ img, const float *__restrict__ depth, int B,
+                                    int H, int W, __nv_bfloat16 *__restrict__ x0) {
+  const int H2 = (H + 1) / 2, W2 = (W + 1) / 2;
+  const size_t n = (size_t)B * H2 * W2;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x2 = (int)(i % W2);
+    const size_t r = i / W2;
+    const int y2 = (int)(r % H2), b = (int)(r / H2);
+    const size_t src = ((size_t)b * H + 2 * y2) * W + 2 * x2;
+    uint4 lo, hi = make_uint4(0, 0, 0, 0);
+    __nv_bfloat162 *l2 = reinterpret_cast<__nv_bfloat162 *>(&lo);
+    l2[0] = __floats2bfloat162_rn(img[3 * src], img[3 * src + 1]);
+    l2[1] = __floats2bfloat162_rn(img[3 * src + 2], depth[src] * 0.125f);
+    l2[2] = __floats2bfloat162_rn(0.0f, 0.0f);
+    l2[3] = l2[2];
+    uint4 *dst = reinterpret_cast<uint4 *>(x0 + i * 16);
+    dst[0] = lo;
+    dst[1] = hi;
+  }
+}
+
+// Prediction = top-left value + residual of the sub-pixel; loss = mean squared error against
+// the target; g_r = dL/dr (BF16, channels 12..15 zero).  loss_acc accumulates the sum of
+// squared errors.
+__global__ void loss_kernel(const float *__restrict__ r, const float *__restrict__ img,
+                            const float *__restrict__ target, int B, int H, int W, float inv_count,
+                            __nv_bfloat16 *__restrict__ g_r, float *__restrict__ loss_acc) {
+  const int H2 = (H + 1) / 2, W2 = (W + 1) / 2;
+  const size_t n = (size_t)B * H2 * W2;
+  float acc = 0.0f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x2 = (int)(i % W2);
+    const size_t rr = i / W2;
+    const int y2 = (int)(rr % H2), b = (int)(rr / H2);
+    const size_t tl = ((size_t)b * H + 2 * y2) * W + 2 * x2;
+    float g[16];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) g[k] = 0.0f;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int dy = s >> 1, dx = s & 1;
+      const int y = 2 * y2 + dy, x = 2 * x2 + dx;
+      if (y >= H || x >= W) continue;
+      const size_t q = ((size_t)b * H + y) * W + x;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float e = img[3 * tl + c] + r[i * 16 + c * 4 + s] - target[3 * q + c];
+        acc += e * e;
+        g[c * 4 + s] = 2.0f * e * inv_count;
+      }
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(g_r + i * 16);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      uint4 pk;
+      __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) p2[c] = __floats2bfloat162_rn(g[h * 8 + 2 * c], g[h * 8 + 2 * c + 1]);
+      dst[h] = pk;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, acc);
+}
+
+// Final image of a foveated render: rendered pixels kept, the others = top-left + residual.
+__global__ void compose_kernel(const float *__restrict__ r, float *__restrict__ img,
+                               const uint8_t *__restrict__ levels, int B, int H, int W, int tile,
+                               int tiles_x, int n_tiles) {
+  const size_t n = (size_t)B * H * W;
+  const int H2 = (H + 1) / 2, W2 = (W + 1) / 2;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % W);
+    const size_t rr = i / W;
+    const int y = (int)(rr % H), b = (int)(rr / H);
+    const int bx = x & 1, by = y & 1;
+    const int lab = bx == by ? (bx ? 1 : 0) : (bx ? 2 : 3);
+    const int lv = levels[b * n_tiles + (y / tile) * tiles_x + x / tile];
+    if (lab < lv) continue;   // rendered
+    const size_t tl = ((size_t)b * H + (y & ~1)) * W + (x & ~1);
+    const size_t ri = (((size_t)b * H2 + y / 2) * W2 + x / 2) * 16 + 2 * by + bx;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) img[3 * i + c] = img[3 * tl + c] + r[ri + 4 * c];
+  }
+}
+
+// Adam on the fp32 master parameters.
+__global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                            float *__restrict__ v, int n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+  }
+}
+
+// BF16 packs of one layer's weights W[cout][cin][9]: forward [tap][cin/8][cout][8 cin] and the
+// data-gradient conv's [tap'][cout/8][cin][8 cout] with W'[cin][cout][tap'] = W[cout][cin][8 - tap'].
+__global__ void pack_kernel(const float *__restrict__ w, int cin, int cout, __nv_bfloat16 *__restrict__ fwd,
+                            __nv_bfloat16 *__restrict__ bwd) {
+  const int n = cin * cout * 9;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int tap = i % 9, rest = i / 9;
+    const int ci = rest % cin, co = rest / cin;
+    const __nv_bfloat16 v = __float2bfloat16_rn(w[i]);
+    fwd[((size_t)(tap * (cin / 8) + ci / 8) * cout + co) * 8 + (ci & 7)] = v;
+    if (bwd) bwd[((size_t)((8 - tap) * (cout / 8) + co / 8) * cin + ci) * 8 + (co & 7)] = v;
+  }
+}
+
+
+constexpr int kLayers = 10;
+__host__ __device__ constexpr int layer_in(int l) { return l == 0 ? 16 : 32; }
+__host__ __device__ constexpr int layer_out(int l) { return l == kLayers - 1 ? 16 : 32; }
+
+size_t weight_offset(int l) {
+  size_t o = 0;
+  for (int k = 0; k < l; ++k) o += (size_t)layer_in(k) * layer_out(k) * 9;
+  return o;
+}
+size_t n_weights() { return weight_offset(kLayers); }
+size_t bias_offset(int l) {
+  size_t o = n_weights();
+  for (int k = 0; k < l; ++k) o += layer_out(k);
+  return o;
+}
+size_t n_params() { return bias_offset(kLayers); }
+
+int grid_1d(size_t n) {
+  const size_t b = (n + 255) / 256;
+  return (int)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+}  // namespace
+}  // namespace a3fr
+
+struct a3fr_cnn {
+  float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  __nv_bfloat16 *wf[a3fr::kLayers] = {}, *wb[a3fr::kLayers] = {};
+  size_t cap_px = 0;
+  __nv_bfloat16 *x0 = nullptr, *h[5] = {}, *t[4] = {}, *g_r = nullptr, *gA = nullptr, *gB = nullptr, *gT = nullptr;
+  float *r = nullptr;
+  float *loss_acc = nullptr;
+  uint32_t *status = nullptr;
+  int step = 0;
+};
+
+namespace a3fr {
+namespace {
+
+template <typename T>
+void dfree2(T *&p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+void free_acts(a3fr_cnn *n) {
+  dfree2(n->x0);
+  for (auto &p : n->h) dfree2(p);
+  for (auto &p : n->t) dfree2(p);
+  dfree2(n->g_r);
+  dfree2(n->gA);
+  dfree2(n->gB);
+  dfree2(n->gT);
+  dfree2(n->r);
+  n->cap_px = 0;
+}
+
+int ensure_acts(a3fr_cnn *n, size_t px) {
+  if (px <= n->cap_px) return A3FR_OK;
+  free_acts(n);
+  const size_t b16 = sizeof(__nv_bfloat16);
+  bool ok = cudaMalloc(&n->x0, px * 16 * b16) == cudaSuccess &&
+            cudaMalloc(&n->g_r, px * 16 * b16) == cudaSuccess &&
+            cudaMalloc(&n->gA, px * 32 * b16) == cudaSuccess &&
+            cudaMalloc(&n->gB, px * 32 * b16) == cudaSuccess &&
+            cudaMalloc(&n->gT, px * 32 * b16) == cudaSuccess &&
+            cudaMalloc(&n->r, px * 16 * sizeof(float)) == cudaSuccess;
+  for (auto &p : n->h) ok = ok && cudaMalloc(&p, px * 32 * b16) == cudaSuccess;
+  for (auto &p : n->t) ok = ok && cudaMalloc(&p, px * 32 * b16) == cudaSuccess;
+  if (!ok) {
+    free_acts(n);
+    return A3FR_ERR_OOM;
+  }
+  n->cap_px = px;
+  return A3FR_OK;
+}
+
+template <int CIN, int COUT>
+cudaError_t conv(const ConvDims &d, const __nv_bfloat16 *X, const __nv_bfloat16 *W, const float *bias,
+                 const __nv_bfloat16 *R, const __nv_bfloat16 *M, void *Y, int flags, uint32_t *status,
+                 cudaStream_t s) {
+  constexpr int smem = conv_smem_bytes<CIN, COUT>();
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, COUT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  const dim3 grid((d.W + kConvTW - 1) / kConvTW, (d.H + kConvTH - 1) / kConvTH, d.B);
+  conv3x3_tc_kernel<CIN, COUT><<<grid, 128, smem, s>>>(d, X, reinterpret_cast<const uint4 *>(W), bias, R,
+                                                       M, Y, flags, status);
+  return cudaGetLastError();
+}
+
+template <int CIN, int COUT>
+cudaError_t wgrad(const ConvDims &d, const __nv_bfloat16 *X, const __nv_bfloat16 *dY, float *dW, float *db,
+                  uint32_t *status, cudaStream_t s) {
+  constexpr int smem = wgrad_smem_bytes<CIN, COUT>();
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_wgrad_tc_kernel<CIN, COUT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  const int tiles = d.B * ((d.H + kWgTile - 1) / kWgTile) * ((d.W + kWgTile - 1) / kWgTile);
+  const int ctas = tiles < 152 * 3 ? tiles : 152 * 3;
+  const int per = (tiles + ctas - 1) / ctas;
+  conv3x3_wgrad_tc_kernel<CIN, COUT><<<ctas, 128, smem, s>>>(d, X, dY, dW, db, per, status);
+  return cudaGetLastError();
+}
+
+#define CNN_CHECK(call)                                  \
+  do {                                                   \
+    cudaError_t e_ = (call);                             \
+    if (e_ != cudaSuccess) return A3FR_ERR_CUDA;         \
+  } while (0)
+
+int pack_all(a3fr_cnn *n, cudaStream_t s) {
+  for (int l = 0; l < kLayers; ++l) {
+    const int cin = layer_in(l), cout = layer_out(l);
+    pack_kernel<<<grid_1d((size_t)cin * cout * 9), 256, 0, s>>>(n->params + weight_offset(l), cin, cout,
+                                                               n->wf[l], l > 0 ? n->wb[l] : nullptr);
+    CNN_CHECK(cudaGetLastError());
+  }
+  return A3FR_OK;
+}
+
+int forward(a3fr_cnn *n, const float *img, const float *depth, int B, int H, int W, cudaStream_t s) {
+  const ConvDims d{B, (H + 1) / 2, (W + 1) / 2};
+  const size_t px = (size_t)d.B * d.H * d.W;
+  const int rc = ensure_acts(n, px);
+  if (rc != A3FR_OK) return rc;
+  gather_input_kernel<<<grid_1d(px), 256, 0, s>>>(img, depth, B, H, W, n->x0);
+  CNN_CHECK(cudaGetLastError());
+  const float *P = n->params;
+  CNN_CHECK((conv<16, 32>(d, n->x0, n->wf[0], P + bias_offset(0), nullptr, nullptr, n->h[0],
+                          kEpiBias | kEpiRelu, n->status, s)));
+  for (int b = 0; b < 4; ++b) {
+    CNN_CHECK((conv<32, 32>(d, n->h[b], n->wf[1 + 2 * b], P + bias_offset(1 + 2 * b), nullptr, nullptr,
+                            n->t[b], kEpiBias | kEpiRelu, n->status, s)));
+    CNN_CHECK((conv<32, 32>(d, n->t[b], n->wf[2 + 2 * b], P + bias_offset(2 + 2 * b), n->h[b], nullptr,
+                            n->h[b + 1], kEpiBias | kEpiResid, n->status, s)));
+  }
+  CNN_CHECK((conv<32, 16>(d, n->h[4], n->wf[9], P + bias_offset(9), nullptr, nullptr, n->r,
+                          kEpiBias | kEpiF32, n->status, s)));
+  return A3FR_OK;
+}
+
+// Gradients of the mean squared error of the prediction against target into n->grads.
+int backward(a3fr_cnn *n, const float *img, const float *target, int B, int H, int W, cudaStream_t s) {
+  const ConvDims d{B, (H + 1) / 2, (W + 1) / 2};
+  const size_t px = (size_t)d.B * d.H * d.W;
+  float *G = n->grads;
+  CNN_CHECK(cudaMemsetAsync(G, 0, sizeof(float) * n_params(), s));
+  CNN_CHECK(cudaMemsetAsync(n->loss_acc, 0, sizeof(float), s));
+  loss_kernel<<<grid_1d(px), 256, 0, s>>>(n->r, img, target, B, H, W, 1.0f / (3.0f * B * H * W), n->g_r,
+                                          n->loss_acc);
+  CNN_CHECK(cudaGetLastError());
+  CNN_CHECK((wgrad<32, 16>(d, n->h[4], n->g_r, G + weight_offset(9), G + bias_offset(9), n->status, s)));
+  CNN_CHECK((conv<16, 32>(d, n->g_r, n->wb[9], nullptr, nullptr, nullptr, n->gA, 0, n->status, s)));
+  __nv_bfloat16 *cur = n->gA, *nxt = n->gB;
+  for (int b = 3; b >= 0; --b) {
+    const int l2 = 2 + 2 * b, l1 = 1 + 2 * b;
+    CNN_CHECK((wgrad<32, 32>(d, n->t[b], cur, G + weight_offset(l2), G + bias_offset(l2), n->status, s)));
+    CNN_CHECK((conv<32, 32>(d, cur, n->wb[l2], nullptr, nullptr, n->t[b], n->gT, kEpiMask, n->status, s)));
+    CNN_CHECK((wgrad<32, 32>(d, n->h[b], n->gT, G + weight_offset(l1), G + bias_offset(l1), n->status, s)));
+    CNN_CHECK((conv<32, 32>(d, n->gT, n->wb[l1], nullptr, cur, b == 0 ? n->h[0] : nullptr, nxt,
+                            kEpiResid | (b == 0 ? kEpiMask : 0), n->status, s)));
+    __nv_bfloat16 *tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  CNN_CHECK((wgrad<16, 32>(d, n->x0, cur, G + weight_offset(0), G + bias_offset(0), n->status, s)));
+  return A3FR_OK;
+}
+
+int read_status(a3fr_cnn *n, cudaStream_t s) {
+  uint32_t h = 0;
+  CNN_CHECK(cudaMemcpyAsync(&h, n->status, sizeof h, cudaMemcpyDeviceToHost, s));
+  CNN_CHECK(cudaStreamSynchronize(s));
+  return h ? A3FR_ERR_TIMEOUT : A3FR_OK;
+}
+
 }  // namespace
 }  // namespace a3fr
 
@@ -98,3 +665,142 @@ extern "C" int a3fr_tc_tile_gemm(const uint16_t *A, const uint16_t *B, float *D,
   if (e != cudaSuccess) return A3FR_ERR_CUDA;
   return h ? A3FR_ERR_TIMEOUT : A3FR_OK;
 }
+
+extern "C" {
+
+size_t a3fr_cnn_param_count(void) { return n_params(); }
+
+int a3fr_cnn_create(a3fr_cnn **out) {
+  if (!out) return A3FR_ERR_INVALID_ARG;
+  *out = nullptr;
+  a3fr_cnn *n = new (std::nothrow) a3fr_cnn();
+  if (!n) return A3FR_ERR_OOM;
+  const size_t np = n_params();
+  bool ok = cudaMalloc(&n->params, np * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&n->grads, np * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&n->adam_m, np * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&n->adam_v, np * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&n->loss_acc, sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&n->status, sizeof(uint32_t)) == cudaSuccess;
+  for (int l = 0; l < kLayers && ok; ++l) {
+    const size_t w = (size_t)layer_in(l) * layer_out(l) * 9 * sizeof(__nv_bfloat16);
+    ok = cudaMalloc(&n->wf[l], w) == cudaSuccess && cudaMalloc(&n->wb[l], w) == cudaSuccess;
+  }
+  if (ok) ok = cudaMemset(n->params, 0, np * sizeof(float)) == cudaSuccess &&
+               cudaMemset(n->adam_m, 0, np * sizeof(float)) == cudaSuccess &&
+               cudaMemset(n->adam_v, 0, np * sizeof(float)) == cudaSuccess &&
+               cudaMemset(n->status, 0, sizeof(uint32_t)) == cudaSuccess;
+  if (ok) ok = pack_all(n, nullptr) == A3FR_OK && cudaDeviceSynchronize() == cudaSuccess;
+  if (!ok) {
+    a3fr_cnn_destroy(n);
+    return A3FR_ERR_OOM;
+  }
+  *out = n;
+  return A3FR_OK;
+}
+
+int a3fr_cnn_destroy(a3fr_cnn *n) {
+  if (!n) return A3FR_ERR_INVALID_ARG;
+  cudaDeviceSynchronize();
+  free_acts(n);
+  dfree2(n->params);
+  dfree2(n->grads);
+  dfree2(n->adam_m);
+  dfree2(n->adam_v);
+  dfree2(n->loss_acc);
+  dfree2(n->status);
+  for (int l = 0; l < kLayers; ++l) {
+    dfree2(n->wf[l]);
+    dfree2(n->wb[l]);
+  }
+  delete n;
+  return A3FR_OK;
+}
+
+int a3fr_cnn_set_params(a3fr_cnn *n, const float *host, size_t count) {
+  if (!n || !host || count != n_params()) return A3FR_ERR_INVALID_ARG;
+  CNN_CHECK(cudaMemcpy(n->params, host, count * sizeof(float), cudaMemcpyHostToDevice));
+  CNN_CHECK(cudaMemset(n->adam_m, 0, count * sizeof(float)));
+  CNN_CHECK(cudaMemset(n->adam_v, 0, count * sizeof(float)));
+  n->step = 0;
+  const int rc = pack_all(n, nullptr);
+  if (rc != A3FR_OK) return rc;
+  CNN_CHECK(cudaDeviceSynchronize());
+  return A3FR_OK;
+}
+
+int a3fr_cnn_get_params(a3fr_cnn *n, float *host, size_t count) {
+  if (!n || !host || count != n_params()) return A3FR_ERR_INVALID_ARG;
+  CNN_CHECK(cudaDeviceSynchronize());
+  CNN_CHECK(cudaMemcpy(host, n->params, count * sizeof(float), cudaMemcpyDeviceToHost));
+  return A3FR_OK;
+}
+
+int a3fr_cnn_forward(a3fr_cnn *n, const float *img, const float *depth, int b, int h, int w,
+                     float *residual_out, void *stream) {
+  if (!n || !img || !depth || b < 1 || h < 2 || w < 2) return A3FR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = forward(n, img, depth, b, h, w, s);
+  if (rc != A3FR_OK) return rc;
+  if (residual_out) {
+    const size_t px = (size_t)b * ((h + 1) / 2) * ((w + 1) / 2);
+    CNN_CHECK(cudaMemcpyAsync(residual_out, n->r, px * 16 * sizeof(float), cudaMemcpyDeviceToDevice, s));
+  }
+  return A3FR_OK;
+}
+
+int a3fr_cnn_grads(a3fr_cnn *n, const float *img, const float *depth, const float *target, int b, int h,
+                   int w, float *host_grads, float *loss, void *stream) {
+  if (!n || !img || !depth || !target || !host_grads || b < 1 || h < 2 || w < 2) return A3FR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = forward(n, img, depth, b, h, w, s);
+  if (rc == A3FR_OK) rc = backward(n, img, target, b, h, w, s);
+  if (rc != A3FR_OK) return rc;
+  CNN_CHECK(cudaMemcpyAsync(host_grads, n->grads, n_params() * sizeof(float), cudaMemcpyDeviceToHost, s));
+  float acc = 0.0f;
+  CNN_CHECK(cudaMemcpyAsync(&acc, n->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, s));
+  rc = read_status(n, s);
+  if (loss) *loss = acc / (3.0f * b * h * w);
+  return rc;
+}
+
+int a3fr_cnn_train_step(a3fr_cnn *n, const float *img, const float *depth, const float *target, int b, int h,
+                        int w, float lr, float *loss, void *stream) {
+  if (!n || !img || !depth || !target || b < 1 || h < 2 || w < 2 || !(lr > 0.0f)) return A3FR_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = forward(n, img, depth, b, h, w, s);
+  if (rc == A3FR_OK) rc = backward(n, img, target, b, h, w, s);
+  if (rc != A3FR_OK) return rc;
+  n->step++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.0f / (1.0f - powf(b1, (float)n->step)), c2 = 1.0f / (1.0f - powf(b2, (float)n->step));
+  adam_kernel<<<grid_1d(n_params()), 256, 0, s>>>(n->params, n->grads, n->adam_m, n->adam_v, (int)n_params(),
+                                                  lr, b1, b2, 1e-8f, c1, c2);
+  CNN_CHECK(cudaGetLastError());
+  rc = pack_all(n, s);
+  if (rc != A3FR_OK) return rc;
+  if (loss) {
+    float acc = 0.0f;
+    CNN_CHECK(cudaMemcpyAsync(&acc, n->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, s));
+    rc = read_status(n, s);
+    *loss = acc / (3.0f * b * h * w);
+    return rc;
+  }
+  return A3FR_OK;
+}
+
+int a3fr_cnn_fill(a3fr_cnn *n, a3fr_scene *scene, float *out_rgb, void *stream) {
+  if (!n || !scene || !out_rgb) return A3FR_ERR_INVALID_ARG;
+  FillView v{};
+  if (!scene_fill_view(scene, &v)) return A3FR_ERR_NOT_READY;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int rc = forward(n, out_rgb, v.depth, v.eyes, v.height, v.width, s);
+  if (rc != A3FR_OK) return rc;
+  const size_t total = (size_t)v.eyes * v.height * v.width;
+  compose_kernel<<<grid_1d(total), 256, 0, s>>>(n->r, out_rgb, v.levels, v.eyes, v.height, v.width, v.tile,
+                                                v.tiles_x, v.n_tiles);
+  CNN_CHECK(cudaGetLastError());
+  return A3FR_OK;
+}
+
+}  // extern "C"

@@ -220,6 +220,15 @@ namespace a3fr {
 // Eyes rendered by a scene (eyes with a camera).
 int scene_eyes(const a3fr_scene *s);
 
+// What the learned periphery needs from a scene's last foveated render (keep_aux on):
+// its expected depth and tile levels; false when there is no such render.
+struct FillView {
+  const float *depth;
+  const uint8_t *levels;
+  int eyes, width, height, tile, tiles_x, n_tiles;
+};
+bool scene_fill_view(a3fr_scene *s, FillView *v);
+
 // Backward rasterizer (backward.cu).
 struct BackwardParams {
   int n_eyes, n, width, height, tiles_x, n_tiles;

@@ -25,3 +25,109 @@ def test_tensor_core_tile_gemm(n, k):
     ref = A.double() @ B.double().T
     err = (D.cpu().double() - ref).abs().max().item()
     assert err < 1e-4 * max(1.0, ref.abs().max().item()), err
+
+
+# ------------------------------------------------------------------ the network
+import torch as _t                                            # noqa: E402
+
+from oracle import cnn as ocnn                                # noqa: E402
+from paper_2507_04147_gb300 import periphery, synth           # noqa: E402
+
+
+def random_params(seed):
+    rng = np.random.default_rng(seed)
+    flat = periphery.init_params(seed)
+    ws, bs = periphery.unpack(flat.copy())
+    for li, w in enumerate(ws):
+        w += rng.normal(0, 0.02, w.shape).astype(np.float32)
+        if li == 0:
+            w[:, 4:] = 0.0
+    for b in bs:
+        b += rng.normal(0, 0.05, b.shape).astype(np.float32)
+    return periphery.pack(ws, bs)
+
+
+def random_images(seed, b=2, h=40, w=56):
+    rng = np.random.default_rng(seed)
+    img = rng.uniform(0, 1, size=(b, h, w, 3)).astype(np.float32)
+    depth = rng.uniform(0, 6, size=(b, h, w)).astype(np.float32)
+    return img, depth
+
+
+def test_network_forward_matches_reference():
+    flat = random_params(1)
+    img, depth = random_images(2)
+    net = periphery.Periphery(flat)
+    r = net.forward(_t.from_numpy(img).cuda(), _t.from_numpy(depth).cuda()).cpu().numpy()
+    net.close()
+    ws, bs = periphery.unpack(flat)
+    x0, _ = ocnn.make_input(img, depth)
+    ref = ocnn.forward(_t.tensor(x0, dtype=_t.float64), [_t.tensor(w, dtype=_t.float64) for w in ws],
+                       [_t.tensor(b, dtype=_t.float64) for b in bs]).numpy()
+    scale = np.abs(ref).max()
+    err = np.abs(r - ref)
+    print("forward max", err.max() / scale, "mean", err.mean() / scale)
+    assert err.max() <= 3e-2 * scale and err.mean() <= 2e-3 * scale
+
+
+def test_network_gradients_match_reference():
+    flat = random_params(3)
+    img, depth = random_images(4)
+    rng = np.random.default_rng(5)
+    target = np.clip(img + rng.normal(0, 0.1, img.shape), 0, 1).astype(np.float32)
+    net = periphery.Periphery(flat)
+    g, loss = net.grads(_t.from_numpy(img).cuda(), _t.from_numpy(depth).cuda(), _t.from_numpy(target).cuda())
+    net.close()
+    ws, bs = periphery.unpack(flat)
+    x0, tl = ocnn.make_input(img, depth)
+    ref_loss, gw, gb, _ = ocnn.loss_and_grads(x0, tl, target, ws, bs)
+    assert loss == pytest.approx(ref_loss, rel=2e-3)
+    gws, gbs = periphery.unpack(g)
+    for li in range(len(gw)):
+        for got, ref, kind in ((gws[li], gw[li], "w"), (gbs[li], gb[li], "b")):
+            rel = np.linalg.norm(got - ref) / max(np.linalg.norm(ref), 1e-12)
+            print(li, kind, rel)
+            assert rel <= 5e-2, (li, kind, rel)
+
+
+def test_learned_fill_beats_inherit_fill():
+    """Trained on the rasterizer's own renders, the network's fill of a foveated render is
+    closer to the full-resolution render than the inherit fill, on views it never saw."""
+    import paper_2507_04147_gb300 as a3fr
+    scene_np = synth.uniform_scene(200_000, 1, seed=3, log_scale_mean=-3.6)
+    scene = a3fr.Scene.from_numpy(scene_np)
+    scene.keep_aux(True)
+    rng = np.random.default_rng(0)
+    train_cams = [synth.pinhole_camera(384, 384, yaw_deg=float(y)) for y in rng.uniform(-20, 20, 24)]
+    imgs, deps = periphery.render_crops(scene, train_cams, 96, 8, rng)
+    net = periphery.Periphery(seed=0)
+    first = last = None
+    for step in range(300):
+        idx = _t.from_numpy(rng.choice(len(imgs), 16, replace=False)).cuda()
+        loss = net.train_step(imgs[idx].contiguous(), deps[idx].contiguous(), imgs[idx].contiguous(), 2e-3,
+                              sync=(step % 50 == 0 or step == 299))
+        if loss is not None:
+            first = loss if first is None else first
+            last = loss
+    assert last < first
+    fv = a3fr.Fovea((18.0, 36.0), 0.0, (4, 2, 1))
+    gains = []
+    for yaw in (27.0, -27.0, 33.0):
+        cam = synth.pinhole_camera(384, 384, yaw_deg=yaw)
+        scene.set_camera(0, cam)
+        full = scene.render_full().clone()
+        scene.set_gaze([[40.0, 40.0]])
+        inh = scene.render_foveated(fv).clone()
+        lv = scene.buffer(a3fr.BUF_LEVELS, _t.uint8).reshape(24, 24)
+        learned = inh.clone()
+        scene.render_foveated(fv, out=learned)
+        net.fill(scene, learned)
+        _t.cuda.synchronize()
+        per = (lv == 1).repeat_interleave(16, 0).repeat_interleave(16, 1)[None]
+        p_inh = periphery.psnr(inh, full, per)
+        p_cnn = periphery.psnr(learned, full, per)
+        print(yaw, "periphery PSNR inherit", p_inh, "learned", p_cnn)
+        gains.append(p_cnn - p_inh)
+    net.close()
+    scene.close()
+    assert min(gains) > 0.2, gains
