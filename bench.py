@@ -456,6 +456,8 @@ def run_ours(args):
     if rank == 0 and not (args.skip_3m or args.quick) and args.workload == "stereo500k":
         line["backward_1m_1024"] = backward_section(a3fr, torch, device, render_stream, flush,
                                                     max(args.warmup, 3))
+        line["learned_periphery"] = learned_periphery_section(a3fr, torch, device, render_stream,
+                                                              gaze_stream)
     if rank == 0 and world == 1 and not (args.no_cpu_baseline or args.quick):
         t, desc = oracle_frame(w, 0, traj, args.cpu_budget)
         import oracle
@@ -575,6 +577,94 @@ def backward_section(a3fr, torch, device, render_stream, flush, warmup, steps: i
             "step_ms_p50": float(np.percentile(fwd + bwd, 50)),
             "steps_per_s": 1000.0 / float((fwd + bwd).mean()), "instances": st["instances"],
             "gradients": list(names), "l2": "flushed before every step"}
+
+
+def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, steps: int = 1250,
+                              batch: int = 16, crop: int = 256, eval_frames: int = 8):
+    """Train the periphery network on 20k 256x256 crop pairs the rasterizer renders from
+    seeded 1M-Gaussian scenes, then fill the foveated frames of the held-out 3M clustered
+    stereo 2064x2208 workload and compare with the inherit fill against the full render."""
+    from paper_2507_04147_gb300 import periphery, synth
+    rng = np.random.default_rng(0)
+    scenes = []
+    for k, make in enumerate((synth.uniform_scene, synth.clustered_scene,
+                              synth.uniform_scene, synth.clustered_scene)):
+        sc = a3fr.Scene.from_numpy(make(1_000_000, 3, seed=40 + k))
+        sc.keep_aux(True)
+        scenes.append(sc)
+    net = periphery.Periphery(seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = []
+    with torch.cuda.stream(render_stream):
+        for step in range(steps):
+            sc = scenes[step % len(scenes)]
+            cam = synth.pinhole_camera(1024, 1024, yaw_deg=float(rng.uniform(-30.0, 30.0)))
+            imgs, deps = periphery.render_crops(sc, [cam], crop, batch, rng, stream=render_stream)
+            lr = 2e-3 * (0.1 + 0.9 * 0.5 * (1.0 + math.cos(math.pi * step / steps)))
+            loss = net.train_step(imgs, deps, imgs, lr, sync=(step % 250 == 0 or step == steps - 1),
+                                  stream=render_stream)
+            if loss is not None:
+                losses.append(loss)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    for sc in scenes:
+        sc.close()
+    # held-out evaluation at 2064x2208 stereo
+    w = synth.stereo_3m_clustered(frames=240)
+    traj = synth.gaze_trajectory(240)
+    scene = a3fr.Scene.from_numpy(w.scene)
+    scene.keep_aux(True)
+    fv = a3fr.Fovea(w.theta_deg, 0.0, (4, 2, 1))
+    cams0 = w.cameras(0)
+    eyes, H, W = len(cams0), cams0[0].height, cams0[0].width
+    out = torch.empty((eyes, H, W, 3), device=device)
+    stats = {"inherit": [], "learned": []}
+    t_render, t_fill, t_full = [], [], []
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for k, f in enumerate(np.linspace(0, 239, eval_frames).astype(int)):
+        for e, c in enumerate(w.cameras(f)):
+            scene.set_camera(e, c)
+        scene.set_gaze(w.gaze(f, traj), gaze_stream)
+        with torch.cuda.stream(render_stream):
+            a, b, c_ = ev(), ev(), ev()
+            a.record(render_stream)
+            scene.render_foveated(fv, out=out, stream=render_stream)
+            b.record(render_stream)
+            inherit = out.clone()
+            b2 = ev()
+            b2.record(render_stream)
+            net.fill(scene, out, stream=render_stream)
+            c_.record(render_stream)
+            levels = scene.buffer(a3fr.BUF_LEVELS, torch.uint8, stream=render_stream)
+            f0, f1 = ev(), ev()
+            f0.record(render_stream)
+            full = scene.render_full(stream=render_stream)
+            f1.record(render_stream)
+        torch.cuda.synchronize()
+        if k > 0:   # the first frame warms up
+            t_render.append(a.elapsed_time(b))
+            t_fill.append(b2.elapsed_time(c_))
+            t_full.append(f0.elapsed_time(f1))
+        ty, tx = (H + 15) // 16, (W + 15) // 16
+        per = (levels.reshape(eyes, ty, tx) == 1).repeat_interleave(16, 1).repeat_interleave(16, 2)[:, :H, :W]
+        for name, img in (("inherit", inherit), ("learned", out)):
+            stats[name].append((periphery.psnr(img, full, per), periphery.psnr(img, full),
+                                periphery.ssim(img, full)))
+    scene.close()
+    net.close()
+    res = {"workload": "train: %d steps x %d crops %dx%d from four seeded 1M-G SH3 scenes; eval: %s, %d frames"
+                       % (steps, batch, crop, crop, w.name, eval_frames),
+           "train_s": train_s, "train_loss_first_last": [losses[0], losses[-1]],
+           "crops": steps * batch}
+    for name in ("inherit", "learned"):
+        arr = np.array(stats[name])
+        res[name] = {"psnr_periphery_db": float(arr[:, 0].mean()), "psnr_whole_db": float(arr[:, 1].mean()),
+                     "ssim_whole": float(arr[:, 2].mean())}
+    res["latency_ms"] = {"foveated_render_aux_p50": float(np.percentile(t_render, 50)),
+                         "learned_fill_p50": float(np.percentile(t_fill, 50)),
+                         "full_render_p50": float(np.percentile(t_full, 50))}
+    return res
 
 
 def incremental_latency(a3fr, scene, w, traj, out, stream, full_ms: float, frames: int = 40):
