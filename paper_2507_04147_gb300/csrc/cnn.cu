@@ -111,12 +111,38 @@ __device__ __forceinline__ void load_halo(uint8_t *hs, const __nv_bfloat16 *__re
   }
 }
 
+// The same halo with asynchronous 16-byte copies (zero-filled outside the image); the caller
+// waits with cp_async_wait_all() before the data is used.
+template <int CG>
+__device__ __forceinline__ void load_halo_async(uint8_t *hs, const __nv_bfloat16 *__restrict__ X, int b,
+                                                int y0, int x0, int rows, int cols, int H, int W) {
+  const int total = rows * cols * CG;
+  for (int i = threadIdx.x; i < total; i += blockDim.x) {
+    const int cg = i % CG, rc = i / CG;
+    const int c = rc % cols, r = rc / cols;
+    const int y = y0 - 1 + r, x = x0 - 1 + c;
+    const bool in = y >= 0 && y < H && x >= 0 && x < W;
+    const __nv_bfloat16 *src = in ? X + (((size_t)b * H + y) * W + x) * (CG * 8) + cg * 8 : X;
+    const uint32_t dst = tc::smem_u32(hs + ((size_t)(cg * rows + r) * cols + c) * 16);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src), "r"(in ? 16 : 0)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int CIN, int COUT>
 constexpr int conv_smem_bytes() {
-  return (CIN / 8) * (kConvTH + 2) * (kConvTW + 2) * 16 + 9 * (CIN / 8) * COUT * 16;
+  return 2 * (CIN / 8) * (kConvTH + 2) * (kConvTW + 2) * 16 + 9 * (CIN / 8) * COUT * 16;
 }
 
-// One 8 x 16 output tile per CTA (128 threads = one thread per output pixel in the epilogue).
+// Persistent over 8 x 16 output tiles (128 threads: one per output pixel in the epilogue).  A
+// CTA loads the layer's packed weights once, then walks tiles blockIdx.x, + gridDim.x, ...
+// with a two-deep pipeline: two halo buffers in shared memory and two 32-column accumulators
+// in tensor memory, so the halo of tile k+1 loads while tile k's MMAs run, and tile k's
+// epilogue (tensor-memory read, bias, ReLU, residual, mask, store) runs while tile k+1's MMAs
+// do.  One thread issues the 9 x (CIN/16) MMAs of a tile and commits them to the mbarrier;
+// tile k completes phase k.
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(128)
 conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *__restrict__ Wpk,
@@ -126,24 +152,41 @@ conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *
   constexpr int CG = CIN / 8, HR = kConvTH + 2, HC = kConvTW + 2;
   constexpr int HALO = CG * HR * HC * 16, WBYTES = 9 * CG * COUT * 16;
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t *hs = smem, *ws = smem + HALO;
+  uint8_t *const ws = smem + 2 * HALO;
   __shared__ uint32_t s_tmem;
   __shared__ __align__(8) uint64_t s_bar;
+  __shared__ float s_bias[32];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int x0 = blockIdx.x * kConvTW, y0 = blockIdx.y * kConvTH, b = blockIdx.z;
-  if (warp == 0) tc::tmem_alloc(&s_tmem, 32);
+  if (t < COUT) s_bias[t] = (flags & kEpiBias) ? bias[t] : 0.0f;
+  const int tiles_x = (d.W + kConvTW - 1) / kConvTW, tiles_y = (d.H + kConvTH - 1) / kConvTH;
+  const int n_tiles = d.B * tiles_x * tiles_y;
+  const int my_n = (int)blockIdx.x < n_tiles ? (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  auto origin = [&](int k, int &b, int &y0, int &x0) {
+    const int tt = (int)blockIdx.x + k * (int)gridDim.x;
+    x0 = (tt % tiles_x) * kConvTW;
+    const int r = tt / tiles_x;
+    y0 = (r % tiles_y) * kConvTH;
+    b = r / tiles_y;
+  };
+  if (warp == 0) tc::tmem_alloc(&s_tmem, 64);
   for (int i = t; i < WBYTES / 16; i += 128) reinterpret_cast<uint4 *>(ws)[i] = __ldg(Wpk + i);
-  load_halo<CG>(hs, X, b, y0, x0, HR, HC, d.H, d.W);
+  if (my_n > 0) {
+    int b, y0, x0;
+    origin(0, b, y0, x0);
+    load_halo_async<CG>(smem, X, b, y0, x0, HR, HC, d.H, d.W);
+  }
+  cp_async_wait_all();
   tc::fence_proxy_async();
   if (t == 0) tc::mbar_init(&s_bar, 1);
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tmem = s_tmem;
-  if (t == 0) {
-    const uint32_t h0 = tc::smem_u32(hs), w0 = tc::smem_u32(ws);
-    const uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
-    int k = 0;
+  const uint32_t idesc = tc::idesc_bf16_f32(128, COUT);
+  auto issue = [&](int k) {   // MMAs of tile k: halo buffer k & 1, accumulator columns 32 (k & 1)
+    const uint32_t h0 = tc::smem_u32(smem + (k & 1) * HALO), w0 = tc::smem_u32(ws);
+    const uint32_t dt = tmem + (uint32_t)((k & 1) * 32);
+    int n = 0;
 #pragma unroll 1
     for (int tap = 0; tap < 9; ++tap) {
       const int ky = tap / 3, kx = tap - 3 * ky;
@@ -152,59 +195,80 @@ conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *
         const uint64_t a = tc::smem_desc(h0 + (2 * cb) * (HR * HC * 16) + ky * (HC * 16) + kx * 16,
                                          HR * HC * 16, HC * 16);
         const uint64_t w = tc::smem_desc(w0 + tap * (CG * COUT * 16) + (2 * cb) * (COUT * 16), COUT * 16, 128);
-        tc::mma_bf16(tmem, a, w, idesc, k > 0);
-        ++k;
+        tc::mma_bf16(dt, a, w, idesc, n > 0);
+        ++n;
       }
     }
     tc::mma_commit(&s_bar);
+  };
+  if (t == 0 && my_n > 0) issue(0);
+  if (my_n > 1) {   // buffer 1 is free: start tile 1's halo
+    int b, y0, x0;
+    origin(1, b, y0, x0);
+    load_halo_async<CG>(smem + HALO, X, b, y0, x0, HR, HC, d.H, d.W);
   }
-  if (!tc::mbar_wait(&s_bar, 0) && lane == 0) atomicOr(status, kStatusTimeout);
-  tc::fence_after_sync();
-  float v[32];
-  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-  if (COUT == 32) tc::tmem_ld32(taddr, v);
-  else tc::tmem_ld16(taddr, v);
-  const int m = warp * 32 + lane;
-  const int y = y0 + m / kConvTW, x = x0 + (m % kConvTW);
-  if (y < d.H && x < d.W) {
-    const size_t pix = ((size_t)b * d.H + y) * d.W + x;
+  for (int k = 0; k < my_n; ++k) {
+    int b, y0, x0;
+    origin(k, b, y0, x0);
+    const int m = warp * 32 + lane;
+    const int y = y0 + m / kConvTW, x = x0 + (m % kConvTW);
+    const bool inside = y < d.H && x < d.W;
+    const size_t pix = inside ? ((size_t)b * d.H + y) * d.W + x : 0;
+    if (!tc::mbar_wait(&s_bar, (uint32_t)(k & 1)) && lane == 0) atomicOr(status, kStatusTimeout);
+    cp_async_wait_all();   // halo k + 1 has landed
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();   // halo k + 1 complete everywhere; every thread saw tile k complete
+    tc::fence_after_sync();
+    if (t == 0 && k + 1 < my_n) issue(k + 1);
+    if (k + 2 < my_n) {   // buffer k & 1 was read by tile k, which completed
+      int b, y0, x0;
+      origin(k + 2, b, y0, x0);
+      load_halo_async<CG>(smem + (k & 1) * HALO, X, b, y0, x0, HR, HC, d.H, d.W);
+    }
+    // epilogue of tile k
+    float v[32];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((k & 1) * 32);
+    if (COUT == 32) tc::tmem_ld32(taddr, v);
+    else tc::tmem_ld16(taddr, v);
+    if (inside) {
 #pragma unroll
-    for (int g = 0; g < COUT / 8; ++g) {
-      float o[8];
+      for (int g = 0; g < COUT / 8; ++g) {
+        float o[8];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
-        o[c] = v[g * 8 + c];
-        if (flags & kEpiBias) o[c] += bias[g * 8 + c];
-        if (flags & kEpiRelu) o[c] = fmaxf(o[c], 0.0f);
-      }
-      if (flags & kEpiResid) {
-        const uint4 rv = __ldg(reinterpret_cast<const uint4 *>(R + pix * COUT) + g);
-        const __nv_bfloat16 *rb = reinterpret_cast<const __nv_bfloat16 *>(&rv);
+        for (int c = 0; c < 8; ++c) {
+          o[c] = v[g * 8 + c] + s_bias[g * 8 + c];
+          if (flags & kEpiRelu) o[c] = fmaxf(o[c], 0.0f);
+        }
+        if (flags & kEpiResid) {
+          const uint4 rv = __ldg(reinterpret_cast<const uint4 *>(R + pix * COUT) + g);
+          const __nv_bfloat16 *rb = reinterpret_cast<const __nv_bfloat16 *>(&rv);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) o[c] += __bfloat162float(rb[c]);
-      }
-      if (flags & kEpiMask) {
-        const uint4 mv = __ldg(reinterpret_cast<const uint4 *>(Mk + pix * COUT) + g);
-        const __nv_bfloat16 *mb = reinterpret_cast<const __nv_bfloat16 *>(&mv);
+          for (int c = 0; c < 8; ++c) o[c] += __bfloat162float(rb[c]);
+        }
+        if (flags & kEpiMask) {
+          const uint4 mv = __ldg(reinterpret_cast<const uint4 *>(Mk + pix * COUT) + g);
+          const __nv_bfloat16 *mb = reinterpret_cast<const __nv_bfloat16 *>(&mv);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) o[c] = __bfloat162float(mb[c]) > 0.0f ? o[c] : 0.0f;
-      }
-      if (flags & kEpiF32) {
-        float4 *yo = reinterpret_cast<float4 *>(static_cast<float *>(Y) + pix * COUT + g * 8);
-        yo[0] = make_float4(o[0], o[1], o[2], o[3]);
-        yo[1] = make_float4(o[4], o[5], o[6], o[7]);
-      } else {
-        uint4 pk;
-        __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
+          for (int c = 0; c < 8; ++c) o[c] = __bfloat162float(mb[c]) > 0.0f ? o[c] : 0.0f;
+        }
+        if (flags & kEpiF32) {
+          float4 *yo = reinterpret_cast<float4 *>(static_cast<float *>(Y) + pix * COUT + g * 8);
+          yo[0] = make_float4(o[0], o[1], o[2], o[3]);
+          yo[1] = make_float4(o[4], o[5], o[6], o[7]);
+        } else {
+          uint4 pk;
+          __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
 #pragma unroll
-        for (int c = 0; c < 4; ++c) p2[c] = __floats2bfloat162_rn(o[2 * c], o[2 * c + 1]);
-        reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(Y) + pix * COUT)[g] = pk;
+          for (int c = 0; c < 4; ++c) p2[c] = __floats2bfloat162_rn(o[2 * c], o[2 * c + 1]);
+          reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(Y) + pix * COUT)[g] = pk;
+        }
       }
     }
   }
   tc::fence_before_sync();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tmem, 32);
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
 // Weight gradient  dW[cout][cin][tap] += sum over pixels of X[pixel + tap][cin] dY[pixel][cout]
@@ -540,7 +604,8 @@ cudaError_t conv(const ConvDims &d, const __nv_bfloat16 *X, const __nv_bfloat16 
     if (e != cudaSuccess) return e;
     attr[dev] = true;
   }
-  const dim3 grid((d.W + kConvTW - 1) / kConvTW, (d.H + kConvTH - 1) / kConvTH, d.B);
+  const int tiles = d.B * ((d.W + kConvTW - 1) / kConvTW) * ((d.H + kConvTH - 1) / kConvTH);
+  const int grid = tiles < 152 * 5 ? tiles : 152 * 5;
   conv3x3_tc_kernel<CIN, COUT><<<grid, 128, smem, s>>>(d, X, reinterpret_cast<const uint4 *>(W), bias, R,
                                                        M, Y, flags, status);
   return cudaGetLastError();
