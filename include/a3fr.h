@@ -53,7 +53,7 @@ typedef struct a3fr_scene a3fr_scene; /* opaque, library-owned */
 typedef struct {
   int32_t n;                    /* number of Gaussians, 0 <= n < 2^30 */
   int32_t sh_degree;            /* 0..3 */
-  int32_t tile;                 /* tile edge in pixels: 16 (0 selects 16) */
+  int32_t tile;                 /* tile edge in pixels: 16 or 32 (0 selects 16) */
   int32_t reserved;             /* must be 0 */
   const float *means;           /* [n][3] world position */
   const float *log_scales;      /* [n][3] log standard deviation per axis */
@@ -209,6 +209,28 @@ int a3fr_run_frame(a3fr_scene *scene, const a3fr_fovea *fovea, const a3fr_rounds
  * whenever a workspace buffer moves; renders with stage timing on, the first render of an
  * automatic-capacity scene and the rounds API launch directly. */
 int a3fr_set_graph_mode(a3fr_scene *scene, int on);
+
+/* ------------------------------------------------------------------ tiling and tuning
+ * Tile size (16 or 32 pixels; the paper tiles 32 x 32, Sec. 3.5): with 32, every label of a
+ * tile is its own 256-thread CTA and only the labels a tile's level needs are launched.  The
+ * per-thread staging batch (1 or 2 Gaussians per thread per shared-memory batch) trades
+ * barrier count for shared memory.  Changing either invalidates the scene's buffers and
+ * captured graphs (the next render reallocates); synchronous.  The backward rasterizer
+ * needs tile 16. */
+int a3fr_set_tile(a3fr_scene *scene, int tile);
+int a3fr_set_batch(a3fr_scene *scene, int batch_mult);
+
+typedef struct {
+  int32_t tile, batch_mult;   /* the configuration chosen (and left set on the scene) */
+  float ms[2][2];             /* mean foveated render time per (tile 16|32, batch 1|2) */
+} a3fr_tune_result;
+
+/* Autotuner (not in the paper, which fixes its tiling by hand): renders the scene foveated
+ * with the current cameras and gaze under every (tile, batch) configuration -- 2 warm-up
+ * and timed_renders timed renders each, CUDA events on `stream` -- and keeps the fastest.
+ * out_rgb as for a3fr_render_foveated; synchronous. */
+int a3fr_autotune(a3fr_scene *scene, const a3fr_fovea *fovea, float *out_rgb, int timed_renders,
+                  void *stream, a3fr_tune_result *result);
 
 /* ---------------------------------------------------------------- backward rasterizer
  * Gradients of L = sum(dl_drgb * image) with respect to the scene parameters, for the last

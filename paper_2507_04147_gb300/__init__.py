@@ -336,6 +336,22 @@ class Scene:
     def graph_mode(self, on: bool = True):
         set_graph_mode(self.handle, on)
 
+    def set_tile(self, tile: int):
+        _lib.check(_lib.load().a3fr_set_tile(self.handle, int(tile)), "a3fr_set_tile")
+
+    def set_batch(self, batch_mult: int):
+        _lib.check(_lib.load().a3fr_set_batch(self.handle, int(batch_mult)), "a3fr_set_batch")
+
+    def autotune(self, fovea=None, out=None, timed_renders: int = 5, stream=None) -> dict:
+        """Times every (tile, batch) configuration on the current view and keeps the fastest."""
+        out = self._out(out)
+        r = _lib.TuneResult()
+        _lib.check(_lib.load().a3fr_autotune(self.handle, ctypes.byref(fovea if fovea is not None else Fovea()),
+                                             _ptr(out), int(timed_renders), _stream_ptr(stream),
+                                             ctypes.byref(r)), "a3fr_autotune")
+        return {"tile": r.tile, "batch_mult": r.batch_mult,
+                "ms": {(t, m): r.ms[i][j] for i, t in enumerate((16, 32)) for j, m in enumerate((1, 2))}}
+
     def backward(self, dl_drgb, stream=None) -> dict:
         """Gradients of sum(dl_drgb * image) of the last render (needs keep_aux) as new
         CUDA tensors shaped like the scene arrays."""

@@ -78,6 +78,10 @@ class FrameResult(ctypes.Structure):
                 ("round_end_us", ctypes.c_double * 16)]
 
 
+class TuneResult(ctypes.Structure):
+    _fields_ = [("tile", ctypes.c_int32), ("batch_mult", ctypes.c_int32), ("ms", (ctypes.c_float * 2) * 2)]
+
+
 class Grads(ctypes.Structure):
     _fields_ = [("means", ctypes.c_void_p), ("log_scales", ctypes.c_void_p),
                 ("quats", ctypes.c_void_p), ("opacity_logits", ctypes.c_void_p),
@@ -106,6 +110,10 @@ _SIGS = {
     "a3fr_get_stats": ([ctypes.c_void_p, ctypes.POINTER(Stats), ctypes.c_int], ctypes.c_int),
     "a3fr_set_keep_aux": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_set_graph_mode": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "a3fr_set_tile": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "a3fr_set_batch": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "a3fr_autotune": ([ctypes.c_void_p, ctypes.POINTER(Fovea), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
+                       ctypes.POINTER(TuneResult)], ctypes.c_int),
     "a3fr_tc_tile_gemm": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                            ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "a3fr_cnn_param_count": ([], ctypes.c_size_t),

@@ -132,6 +132,8 @@ struct a3fr_scene {
   uint64_t g_pre_key = 0, g_fov_key = 0, g_full_key = 0;
   uint64_t g_pre_launches = 0;               // kernels in the precompute graph
 
+  int batch_mult = 1;                        // Gaussians staged per thread per composite batch
+
   // backward: what the last render leaves for it (0 none, 1 full, 2 foveated; keep_aux only)
   int bw_mode = 0;
   float *g2d = nullptr;                      // [eye][n][9] per-Gaussian image-space gradients
@@ -533,7 +535,7 @@ int enqueue_comp(a3fr_scene *s, const CompositeParams &cp, int uniform, uint8_t 
                               s->tvals[b], s->gaze_dev, nullptr, uniform, cur, s->plan, s->levels,
                               s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr,
-                              s->keep_aux ? s->depth : nullptr, s->counters, stream));
+                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, stream));
   *launches += cp.full ? 1 : 2;
   A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));
   return A3FR_OK;
@@ -675,7 +677,7 @@ int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
                               s->counts, s->tvals[b], s->gaze_dev, s->round_plan, 0, s->cur_level,
                               s->plan, s->levels, s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr,
-                              s->keep_aux ? s->depth : nullptr, s->counters, stream));
+                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, stream));
   rc = finish_render(s, stream);
   if (rc != A3FR_OK) return rc;
   s->launches += 3;
@@ -710,7 +712,7 @@ int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3f
       desc->reserved != 0)
     return A3FR_ERR_INVALID_ARG;
   const int tile = desc->tile == 0 ? 16 : desc->tile;
-  if (tile != 16) return A3FR_ERR_INVALID_ARG;
+  if (tile != 16 && tile != 32) return A3FR_ERR_INVALID_ARG;
   if (instance_capacity >= (1u << 30)) return A3FR_ERR_INVALID_ARG;
   if (desc->n > 0) {
     const void *ptrs[5] = {desc->means, desc->log_scales, desc->quats, desc->opacity_logits,
@@ -1072,6 +1074,7 @@ int a3fr_backward(a3fr_scene *s, const float *dl_drgb, const a3fr_grads *g, void
   if (n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
     return A3FR_ERR_INVALID_ARG;
   if (s->bw_mode == 0 || s->last_eyes == 0) return A3FR_ERR_NOT_READY;
+  if (s->desc.tile != 16) return A3FR_ERR_INVALID_ARG;   // the backward walks 16-pixel tiles
   if (n == 0) return A3FR_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int eyes = s->last_eyes;
@@ -1102,6 +1105,73 @@ int a3fr_backward(a3fr_scene *s, const float *dl_drgb, const a3fr_grads *g, void
                              g->sh, st));
   s->launches += 2;
   return A3FR_OK;
+}
+
+
+int a3fr_set_tile(a3fr_scene *s, int tile) {
+  if (!s || (tile != 16 && tile != 32)) return A3FR_ERR_INVALID_ARG;
+  if (s->desc.tile == tile) return A3FR_OK;
+  A3FR_CHECK(cudaDeviceSynchronize());
+  free_frame_buffers(s);
+  s->desc.tile = tile;
+  s->alloc_gen++;
+  s->bw_mode = 0;
+  return A3FR_OK;
+}
+
+int a3fr_set_batch(a3fr_scene *s, int batch_mult) {
+  if (!s || (batch_mult != 1 && batch_mult != 2)) return A3FR_ERR_INVALID_ARG;
+  if (s->batch_mult != batch_mult) {
+    s->batch_mult = batch_mult;
+    s->alloc_gen++;   // captured composite graphs hold the kernel choice
+  }
+  return A3FR_OK;
+}
+
+int a3fr_autotune(a3fr_scene *s, const a3fr_fovea *fovea, float *out_rgb, int timed_renders,
+                  void *stream, a3fr_tune_result *result) {
+  if (!s || !fovea || !out_rgb || !result || timed_renders < 1) return A3FR_ERR_INVALID_ARG;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  *result = a3fr_tune_result{};
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess) return A3FR_ERR_CUDA;
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return A3FR_ERR_CUDA;
+  }
+  const int tiles[2] = {16, 32}, mults[2] = {1, 2};
+  float best = 1e30f;
+  int rc = A3FR_OK;
+  for (int ti = 0; ti < 2 && rc == A3FR_OK; ++ti) {
+    for (int mi = 0; mi < 2 && rc == A3FR_OK; ++mi) {
+      rc = a3fr_set_tile(s, tiles[ti]);
+      if (rc == A3FR_OK) rc = a3fr_set_batch(s, mults[mi]);
+      for (int w = 0; w < 2 && rc == A3FR_OK; ++w) rc = a3fr_render_foveated(s, fovea, out_rgb, stream);
+      if (rc != A3FR_OK) break;
+      if (cudaEventRecord(e0, st) != cudaSuccess) { rc = A3FR_ERR_CUDA; break; }
+      for (int r = 0; r < timed_renders && rc == A3FR_OK; ++r) rc = a3fr_render_foveated(s, fovea, out_rgb, stream);
+      if (rc != A3FR_OK) break;
+      float ms = 0.0f;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        rc = A3FR_ERR_CUDA;
+        break;
+      }
+      ms /= (float)timed_renders;
+      result->ms[ti][mi] = ms;
+      if (ms < best) {
+        best = ms;
+        result->tile = tiles[ti];
+        result->batch_mult = mults[mi];
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != A3FR_OK) return rc;
+  rc = a3fr_set_tile(s, result->tile);
+  if (rc == A3FR_OK) rc = a3fr_set_batch(s, result->batch_mult);
+  return rc;
 }
 
 }  // extern "C"

@@ -183,7 +183,7 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
                              const uint32_t *vals, const float *gaze, const RoundPlan *round,
                              int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, float *depth,
-                             unsigned long long *counters, cudaStream_t s);
+                             unsigned long long *counters, int batch_mult, cudaStream_t s);
 
 // Incremental rounds (Sec. 3.3, Alg. 1): state on the device, mailbox in mapped host memory.
 struct RoundConfig {

@@ -33,9 +33,9 @@ __device__ __forceinline__ int tile_level(const CompositeParams &p, int eye, int
                                           const float *gaze) {
   const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
   const float gx = gaze[2 * eye], gy = gaze[2 * eye + 1];
-  const float x0 = (float)(tx * kTile), y0 = (float)(ty * kTile);
-  const float x1 = (float)(min((tx + 1) * kTile, p.width) - 1);
-  const float y1 = (float)(min((ty + 1) * kTile, p.height) - 1);
+  const float x0 = (float)(tx * p.tile), y0 = (float)(ty * p.tile);
+  const float x1 = (float)(min((tx + 1) * p.tile, p.width) - 1);
+  const float y1 = (float)(min((ty + 1) * p.tile, p.height) - 1);
   const float dx = fmaxf(fmaxf(fs(x0, gx), fs(gx, x1)), 0.0f);
   const float dy = fmaxf(fmaxf(fs(y0, gy), fs(gy, y1)), 0.0f);
   const float d2 = fa(fm(dx, dx), fm(dy, dy));
@@ -109,7 +109,7 @@ __device__ __forceinline__ void group_sync(int size, int bar) {
   }
 }
 
-template <bool kAux, bool kFull>
+template <bool kAux, bool kFull, int kMult>
 __global__ void __launch_bounds__(kThreads, 6)
 composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
                  const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
@@ -120,9 +120,9 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
                  unsigned long long *__restrict__ counters) {
   const CompositeParams &p = *pp;   // per-render parameters in device memory
   float *out = p.out;
-  __shared__ float4 s_geo[kThreads];   // u, v, -0.5 log2e a, -log2e b
-  __shared__ float2 s_cz[kThreads];    // -0.5 log2e c, camera-space depth
-  __shared__ float4 s_rgb[kThreads];   // r, g, b, opacity
+  __shared__ float4 s_geo[kThreads * kMult];   // u, v, -0.5 log2e a, -log2e b
+  __shared__ float2 s_cz[kThreads * kMult];    // -0.5 log2e c, camera-space depth
+  __shared__ float4 s_rgb[kThreads * kMult];   // r, g, b, opacity
   __shared__ int s_done[kThreads / 32];
   __shared__ float s_out[4][kTile][kTile * 3];   // the tiles of the CTA, assembled for stores
 
@@ -206,8 +206,10 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
     gfirst = 0;
   }
   const int gt = threadIdx.x - gfirst;   // thread index inside the staging group
+  const int sbase = gfirst * kMult;      // the group's staging slots
+  const uint32_t bsz = (uint32_t)(gsize * kMult);   // Gaussians per batch
 
-  for (uint32_t start = range.x; start < range.y; start += gsize) {
+  for (uint32_t start = range.x; start < range.y; start += bsz) {
     // stop when every pixel of the staging group is done
     const bool wdone = __all_sync(0xffffffffu, done);
     if (lane == 0) s_done[warp] = wdone;
@@ -215,20 +217,24 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
     bool all = true;
     for (int w = gfirst >> 5; w < (gfirst + gsize) >> 5; ++w) all = all && s_done[w];
     if (all) break;
-    const uint32_t cnt = min((uint32_t)gsize, range.y - start);
+    const uint32_t cnt = min(bsz, range.y - start);
     staged += cnt;
-    if ((uint32_t)gt < cnt) {
-      const uint32_t gidx = min(vals[start + gt], (uint32_t)(n - 1));   // in range unless a sort failed
-      const float4 *r4 = reinterpret_cast<const float4 *>(rec_eye + (size_t)gidx * kRec);
-      const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
-      s_geo[threadIdx.x] = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
-      s_cz[threadIdx.x] = make_float2(__fmul_rn(-0.5f * kLog2e, b.x), c.y);
-      s_rgb[threadIdx.x] = make_float4(b.z, b.w, c.x, b.y);
-    } else if ((uint32_t)gt < ((cnt + 3u) & ~3u)) {
-      // padding up to a multiple of 4: zero opacity never passes the 1/255 test
-      s_geo[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-      s_cz[threadIdx.x] = make_float2(0.0f, 0.0f);
-      s_rgb[threadIdx.x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+#pragma unroll
+    for (int j = 0; j < kMult; ++j) {
+      const uint32_t slot = (uint32_t)(gt + j * gsize);
+      if (slot < cnt) {
+        const uint32_t gidx = min(vals[start + slot], (uint32_t)(n - 1));   // in range unless a sort failed
+        const float4 *r4 = reinterpret_cast<const float4 *>(rec_eye + (size_t)gidx * kRec);
+        const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
+        s_geo[sbase + slot] = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
+        s_cz[sbase + slot] = make_float2(__fmul_rn(-0.5f * kLog2e, b.x), c.y);
+        s_rgb[sbase + slot] = make_float4(b.z, b.w, c.x, b.y);
+      } else if (slot < ((cnt + 3u) & ~3u)) {
+        // padding up to a multiple of 4: zero opacity never passes the 1/255 test
+        s_geo[sbase + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s_cz[sbase + slot] = make_float2(0.0f, 0.0f);
+        s_rgb[sbase + slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
     }
     group_sync(gsize, gbar);
     if (!__all_sync(0xffffffffu, done)) {
@@ -240,7 +246,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
       for (uint32_t k = 0; k < cnt4; k += 4) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int e = gfirst + (int)k + j;
+          const int e = sbase + (int)k + j;
           const float4 geo = s_geo[e];
           const float2 cz = s_cz[e];
           const float cc = cz.x;
@@ -342,6 +348,180 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
   }
 }
 
+
+// 32 x 32 tiles (the paper's tiling, Sec. 3.5): a tile is 16 x 16 blocks of 2 x 2 pixels and
+// each of its four labels is one 256-thread group; a level-k tile runs the groups of its
+// labels (lo, lo + k] and no other.  Here each (tile, label) pair is one CTA, taken from the
+// same level buckets as the 16-pixel kernel (a bucket-c entry spawns c CTAs), so only the
+// groups that render are ever launched.  The label-1 CTA of a tile rendered from label 0
+// also writes the inherited pixels of its blocks.
+template <bool kAux, bool kFull, int kMult>
+__global__ void __launch_bounds__(kThreads, 6)
+composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
+                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
+                   const uint32_t *__restrict__ vals, const uint32_t *__restrict__ plan,
+                   const uint32_t *__restrict__ plan_counts, int incremental,
+                   uint8_t *__restrict__ levels, float *__restrict__ t_final,
+                   uint32_t *__restrict__ n_contrib, float *__restrict__ depth,
+                   unsigned long long *__restrict__ counters) {
+  constexpr int T32 = 32;
+  constexpr int NB = kThreads * kMult;
+  const CompositeParams &p = *pp;
+  float *out = p.out;
+  __shared__ float4 s_geo[NB];
+  __shared__ float2 s_cz[NB];
+  __shared__ float4 s_rgb[NB];
+  __shared__ int s_done[kThreads / 32];
+  const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+  const int n_ranges = p.n_eyes * p.n_tiles;
+  int gtile, label, level = 4, lo = 0;
+  if (kFull) {
+    gtile = blockIdx.x >> 2;
+    label = blockIdx.x & 3;
+    if (label == 0 && t == 0) levels[gtile] = 4;
+  } else {
+    const int c = blockIdx.x;
+    const int n4 = plan_counts[3], n3 = plan_counts[2], n2 = plan_counts[1], n1 = plan_counts[0];
+    const int c3 = 4 * n4, c2 = c3 + 3 * n3, c1 = c2 + 2 * n2, c0 = c1 + n1;
+    uint32_t entry;
+    int count, sub;
+    if (c < c3) {
+      entry = plan[3 * (size_t)n_ranges + c / 4];
+      count = 4;
+      sub = c & 3;
+    } else if (c < c2) {
+      entry = plan[2 * (size_t)n_ranges + (c - c3) / 3];
+      count = 3;
+      sub = (c - c3) % 3;
+    } else if (c < c1) {
+      entry = plan[(size_t)n_ranges + (c - c2) / 2];
+      count = 2;
+      sub = (c - c2) & 1;
+    } else if (c < c0) {
+      entry = plan[c - c1];
+      count = 1;
+      sub = 0;
+    } else {
+      return;
+    }
+    gtile = (int)(entry >> 2);
+    lo = (int)(entry & 3u);
+    level = lo + count;
+    label = lo + sub;
+  }
+  const int eye = gtile / p.n_tiles;
+  const int tile = gtile - eye * p.n_tiles;
+  const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+  const int ox = (label == 1 || label == 2) ? 1 : 0;   // BR, TR
+  const int oy = (label == 1 || label == 3) ? 1 : 0;   // BR, BL
+  const int bx = t & 15, by = t >> 4;
+  const int px = tx * T32 + 2 * bx + ox, py = ty * T32 + 2 * by + oy;
+  const bool inside = px < p.width && py < p.height;
+  const float fpx = (float)px, fpy = (float)py;
+
+  uint2 range = ranges[gtile];
+  const uint32_t n_kept = *kept;
+  range.x = min(range.x, n_kept);
+  range.y = min(range.y, n_kept);
+  const float *rec_eye = rec + (size_t)eye * n * kRec;
+
+  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Z = 0.0f;
+  uint32_t last = 0, stop = 0, staged = 0;
+  bool done = !inside;
+  for (uint32_t start = range.x; start < range.y; start += NB) {
+    const bool wdone = __all_sync(0xffffffffu, done);
+    if (lane == 0) s_done[warp] = wdone;
+    __syncthreads();
+    bool all = true;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) all = all && s_done[w];
+    if (all) break;
+    const uint32_t cnt = min((uint32_t)NB, range.y - start);
+    staged += cnt;
+#pragma unroll
+    for (int j = 0; j < kMult; ++j) {
+      const uint32_t slot = (uint32_t)(t + j * kThreads);
+      if (slot < cnt) {
+        const uint32_t gidx = min(vals[start + slot], (uint32_t)(n - 1));
+        const float4 *r4 = reinterpret_cast<const float4 *>(rec_eye + (size_t)gidx * kRec);
+        const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
+        s_geo[slot] = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
+        s_cz[slot] = make_float2(__fmul_rn(-0.5f * kLog2e, b.x), c.y);
+        s_rgb[slot] = make_float4(b.z, b.w, c.x, b.y);
+      } else if (slot < ((cnt + 3u) & ~3u)) {
+        s_geo[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s_cz[slot] = make_float2(0.0f, 0.0f);
+        s_rgb[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      }
+    }
+    __syncthreads();
+    if (!__all_sync(0xffffffffu, done)) {
+      const uint32_t cnt4 = (cnt + 3u) & ~3u;
+      const uint32_t pos0 = start - range.x + 1;
+      for (uint32_t k = 0; k < cnt4; k += 4) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int e = (int)k + j;
+          const float4 geo = s_geo[e];
+          const float2 cz = s_cz[e];
+          const float4 rgb = s_rgb[e];
+          const float dx = __fsub_rn(geo.x, fpx), dy = __fsub_rn(geo.y, fpy);
+          const float pw = falloff_log2(geo.z, geo.w, cz.x, dx, dy);
+          const float alpha = blend_alpha(rgb.w, pw);
+          const float tt = __fmul_rn(T, __fsub_rn(1.0f, alpha));
+          const bool ok = !done && pw <= 0.0f && alpha >= 1.0f / 255.0f;
+          const bool fin = ok && tt < 0.0001f;
+          const bool upd = ok && !fin;
+          const uint32_t pos = pos0 + k + (uint32_t)j;
+          const float w = upd ? alpha * T : 0.0f;
+          C0 += rgb.x * w;
+          C1 += rgb.y * w;
+          C2 += rgb.z * w;
+          if (kAux) Z += cz.y * w;
+          T = upd ? tt : T;
+          last = upd ? pos : last;
+          stop = fin ? pos : stop;
+          done = done || fin;
+        }
+        if (__all_sync(0xffffffffu, done)) break;
+      }
+    }
+    __syncthreads();
+  }
+  if (inside && !done) stop = range.y - range.x;
+
+  if (inside) {
+    // this label's pixel, and for label 1 of a tile rendered from label 0 the inherited
+    // pixels of its block (BR for level < 2, TR for level < 3, BL for level < 4)
+#pragma unroll
+    for (int k = -1; k < 3; ++k) {
+      int dx = 0, dy = 0;
+      if (k >= 0) {
+        if (kFull || incremental || label != 0 || level >= k + 2) continue;
+        dx = k < 2 ? 1 : 0;
+        dy = k == 1 ? 0 : 1;
+        if (px + dx >= p.width || py + dy >= p.height) continue;
+      }
+      const size_t pix = ((size_t)eye * p.height + py + dy) * p.width + px + dx;
+      out[3 * pix] = C0;
+      out[3 * pix + 1] = C1;
+      out[3 * pix + 2] = C2;
+      if (kAux) {
+        t_final[pix] = T;
+        n_contrib[pix] = last;
+        depth[pix] = Z;
+      }
+    }
+  }
+  unsigned long long ev = stop;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+  if (lane == 0) {
+    if (ev) atomicAdd(counters, ev);
+    if (t == 0 && staged) atomicAdd(counters + 1, (unsigned long long)staged);
+  }
+}
+
 }  // namespace
 
 size_t plan_bytes(int n_ranges) { return sizeof(uint32_t) * (4 * (size_t)n_ranges + 4); }
@@ -351,7 +531,7 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
                              const uint32_t *vals, const float *gaze, const RoundPlan *round,
                              int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, float *depth,
-                             unsigned long long *counters, cudaStream_t s) {
+                             unsigned long long *counters, int batch_mult, cudaStream_t s) {
   const int n_ranges = p.n_eyes * p.n_tiles;
   if (n_ranges <= 0) return cudaSuccess;
   uint32_t *pc = plan + 4 * (size_t)n_ranges;
@@ -363,34 +543,39 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  static bool carveout_set[64] = {};
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && !carveout_set[dev]) {
-    // prefer shared memory so that the register limit, not the carveout, sets residency
-    const int c = cudaSharedmemCarveoutMaxShared;
-    cudaFuncSetAttribute(composite_kernel<true, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-    cudaFuncSetAttribute(composite_kernel<true, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-    cudaFuncSetAttribute(composite_kernel<false, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-    cudaFuncSetAttribute(composite_kernel<false, false>, cudaFuncAttributePreferredSharedMemoryCarveout, c);
-    carveout_set[dev] = true;
-  }
   const int inc = round != nullptr ? 1 : 0;
-  if (t_final != nullptr) {
-    if (p.full)
-      composite_kernel<true, true><<<n_ranges, kThreads, 0, s>>>(
-          p_dev, rec, n, ranges, kept, vals, plan, pc, 0, levels, t_final, n_contrib, depth, counters);
-    else
-      composite_kernel<true, false><<<n_ranges, kThreads, 0, s>>>(
-          p_dev, rec, n, ranges, kept, vals, plan, pc, inc, levels, t_final, n_contrib, depth, counters);
-  } else {
-    if (p.full)
-      composite_kernel<false, true><<<n_ranges, kThreads, 0, s>>>(
-          p_dev, rec, n, ranges, kept, vals, plan, pc, 0, levels, t_final, n_contrib, depth, counters);
-    else
-      composite_kernel<false, false><<<n_ranges, kThreads, 0, s>>>(
-          p_dev, rec, n, ranges, kept, vals, plan, pc, inc, levels, t_final, n_contrib, depth, counters);
+  const bool aux = t_final != nullptr;
+  const int mult = batch_mult == 2 ? 2 : 1;
+  // one composite kernel per (tile, aux, full, batch) combination; shared memory preferred so
+  // that registers, not the carveout, set residency
+  auto launch = [&](auto kern, int grid) -> cudaError_t {
+    static bool carve[64][64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
+      const int slot = (p.tile == 32 ? 32 : 0) + (aux ? 16 : 0) + (p.full ? 8 : 0) + mult;
+      if (!carve[dev][slot]) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+        carve[dev][slot] = true;
+      }
+    }
+    kern<<<grid, kThreads, 0, s>>>(p_dev, rec, n, ranges, kept, vals, plan, pc, p.full ? 0 : inc, levels,
+                                   t_final, n_contrib, depth, counters);
+    return cudaGetLastError();
+  };
+  const int g16 = n_ranges, g32 = 4 * n_ranges;
+#define A3FR_COMPOSITE_CASE(K, GRID)                                                        \
+  if (aux) {                                                                               \
+    if (p.full) return mult == 2 ? launch(K<true, true, 2>, GRID) : launch(K<true, true, 1>, GRID); \
+    return mult == 2 ? launch(K<true, false, 2>, GRID) : launch(K<true, false, 1>, GRID);    \
+  }                                                                                        \
+  if (p.full) return mult == 2 ? launch(K<false, true, 2>, GRID) : launch(K<false, true, 1>, GRID); \
+  return mult == 2 ? launch(K<false, false, 2>, GRID) : launch(K<false, false, 1>, GRID);
+  if (p.tile == 32) {
+    A3FR_COMPOSITE_CASE(composite32_kernel, g32)
   }
-  return cudaGetLastError();
+  A3FR_COMPOSITE_CASE(composite_kernel, g16)
+#undef A3FR_COMPOSITE_CASE
 }
 
 }  // namespace a3fr

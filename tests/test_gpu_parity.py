@@ -210,3 +210,53 @@ def test_graph_mode_matches_direct_launches_bitwise():
         assert torch.equal(a, b)
     st = graph.stats()
     assert st["status"] == 0
+
+
+@pytest.mark.parametrize("batch_mult", [1, 2])
+def test_tile32_foveated_and_full(batch_mult):
+    """32-pixel tiles (one CTA per tile label) against the oracle run with 32-pixel tiles."""
+    scene = synth.uniform_scene(8000, 3, seed=13)
+    cams = synth.stereo_cameras(200, 136, yaw_deg=2.0)
+    gaze = np.array([[70.0, 60.0], [66.0, 61.0]], np.float32)
+    ofv, gfv = fovea_params()
+    r = gh.run(scene, cams, gaze=gaze, fovea=gfv, tile=32, batch_mult=batch_mult)
+    assert r["stats"]["status"] == 0
+    for e in range(2):
+        print(e, check_eye(r, e, scene, cams[e], tile=32, gaze=gaze[e], fv=ofv))
+    rf = gh.run(scene, cams, full=True, tile=32, batch_mult=batch_mult)
+    for e in range(2):
+        check_eye(rf, e, scene, cams[e], tile=32, full=True)
+
+
+def test_batch_multiplier_renders_bitwise_equal():
+    """Staging two Gaussians per thread changes only the batching, not any pixel's sequence."""
+    w = synth.small_single_view()
+    cam = w.cameras(0)[0]
+    for tile in (16, 32):
+        a = gh.run(w.scene, [cam], gaze=[w.fixed_gaze_px], fovea=a3fr.Fovea(), tile=tile, batch_mult=1)
+        b = gh.run(w.scene, [cam], gaze=[w.fixed_gaze_px], fovea=a3fr.Fovea(), tile=tile, batch_mult=2)
+        assert np.array_equal(a["img"], b["img"])
+
+
+def test_autotune_picks_a_configuration_and_renders_it():
+    import torch
+    w = synth.stereo_500k(frames=240)
+    scene_np = w.scene.subset(np.arange(100000))
+    cams = synth.stereo_cameras(640, 640, yaw_deg=1.0)
+    s = a3fr.Scene.from_numpy(scene_np)
+    for e, c in enumerate(cams):
+        s.set_camera(e, c)
+    s.set_gaze([[300.0, 330.0], [290.0, 330.0]])
+    res = s.autotune(a3fr.Fovea(), timed_renders=3)
+    print(res)
+    assert res["tile"] in (16, 32) and res["batch_mult"] in (1, 2)
+    assert all(v > 0 for v in res["ms"].values())
+    assert res["ms"][(res["tile"], res["batch_mult"])] == min(res["ms"].values())
+    img = s.render_foveated(a3fr.Fovea()).clone()
+    s.set_tile(16)
+    s.set_batch(1)
+    ref = s.render_foveated(a3fr.Fovea())
+    torch.cuda.synchronize()
+    if res["tile"] == 16:
+        assert torch.equal(img, ref)
+    s.close()
