@@ -272,7 +272,8 @@ def run_reference(args):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * sum(est) / len(est), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(w, world),
+            "config": dict(workload_config(w, world), tile=scene.tile,
+                           tile_choice="autotuned over tile 16/32 x staging batch 1/2"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(),
                              "kind": "oracle", "sample": descs[0] + f" (per step, {len(est)} steps)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -429,13 +430,14 @@ def run_ours(args):
 
     stage_mean_fov = {k: float(st_fov[:, i].mean()) for i, k in enumerate(STAGES)}
     stage_mean_full = {k: float(st_full[:, i].mean()) for i, k in enumerate(STAGES)}
-    roof = roofline(w, stats_fov_direct, stage_mean_fov, len(sframes), eyes)
+    roof = roofline(w, stats_fov_direct, stage_mean_fov, len(sframes), eyes, scene.tile)
 
     line = {"metric": METRIC, "value": fps_fov, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": total_fov / len(frames), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": workload_config(w, world),
+            "config": dict(workload_config(w, world), tile=scene.tile,
+                           tile_choice="autotuned over tile 16/32 x staging batch 1/2"),
             "latency_ms": {"foveated_p50": float(np.percentile(ms_fov, 50)),
                            "foveated_p99": float(np.percentile(ms_fov, 99)),
                            "full_p50": float(np.percentile(ms_full, 50)),
@@ -740,9 +742,10 @@ def psnr_frames(scene, enqueue, out, out_full, w, frame_ids, a3fr, torch):
         enqueue(f, True, out_full, flush_l2=False)
         torch.cuda.synchronize()
         eyes, H, W, _ = out.shape
-        tx = (W + w.tile - 1) // w.tile
-        ty = (H + w.tile - 1) // w.tile
-        lv = levels.reshape(eyes, ty, tx).repeat_interleave(w.tile, 1).repeat_interleave(w.tile, 2)[:, :H, :W]
+        tile = scene.tile
+        tx = (W + tile - 1) // tile
+        ty = (H + tile - 1) // tile
+        lv = levels.reshape(eyes, ty, tx).repeat_interleave(tile, 1).repeat_interleave(tile, 2)[:, :H, :W]
         fov = lv == 4
         d2 = ((out.clamp(0, 1) - out_full.clamp(0, 1)) ** 2).mean(dim=-1).double()
         for name, mask in (("foveal", fov), ("periphery", ~fov), ("whole", torch.ones_like(fov))):
@@ -757,7 +760,7 @@ def psnr_frames(scene, enqueue, out, out_full, w, frame_ids, a3fr, torch):
     return res
 
 
-def roofline(w, stats, stage_ms, n_frames, eyes):
+def roofline(w, stats, stage_ms, n_frames, eyes, tile=16):
     """Roofline of the kernel with the largest share of the frame (per launch)."""
     peaks, how = measured_peaks()
     n = w.scene.n
@@ -768,7 +771,7 @@ def roofline(w, stats, stage_ms, n_frames, eyes):
     staged = stats["records_staged"] / max(n_frames, 1)
     evals = stats["evaluations"] / max(n_frames, 1)
     n_ent = n * eyes
-    tiles = eyes * ((c0.width + 15) // 16) * ((c0.height + 15) // 16)
+    tiles = eyes * ((c0.width + tile - 1) // tile) * ((c0.height + tile - 1) // tile)
     tile_passes = max(1, math.ceil(max(1, math.ceil(math.log2(max(tiles, 2)))) / 8))
     algo = {
         # bytes: Gaussian parameters once; records + rects + touched + depth keys per eye

@@ -262,6 +262,7 @@ class Scene:
         d.opacity_logits, d.sh = _ptr(opacity_logits), _ptr(sh)
         self.handle = create_scene(d, instance_capacity)
         self.cams = {}
+        self.tile = tile
 
     @classmethod
     def from_numpy(cls, scene, device="cuda", **kw) -> "Scene":
@@ -338,6 +339,7 @@ class Scene:
 
     def set_tile(self, tile: int):
         _lib.check(_lib.load().a3fr_set_tile(self.handle, int(tile)), "a3fr_set_tile")
+        self.tile = int(tile)
 
     def set_batch(self, batch_mult: int):
         _lib.check(_lib.load().a3fr_set_batch(self.handle, int(batch_mult)), "a3fr_set_batch")
@@ -349,6 +351,7 @@ class Scene:
         _lib.check(_lib.load().a3fr_autotune(self.handle, ctypes.byref(fovea if fovea is not None else Fovea()),
                                              _ptr(out), int(timed_renders), _stream_ptr(stream),
                                              ctypes.byref(r)), "a3fr_autotune")
+        self.tile = int(r.tile)
         return {"tile": r.tile, "batch_mult": r.batch_mult,
                 "ms": {(t, m): r.ms[i][j] for i, t in enumerate((16, 32)) for j, m in enumerate((1, 2))}}
 

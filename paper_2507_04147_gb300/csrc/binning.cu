@@ -17,9 +17,10 @@
 //
 // emit: instance offsets by a single-pass scan with decoupled look-back over dynamically
 // numbered blocks (64-bit flag|value words; a warp reads 32 predecessors per step; bounded
-// waits that set a status bit).  Each thread then generates its own entry's instances into
-// a shared-memory chunk of the block's contiguous output run, and the block stores the
-// chunk with coalesced writes.
+// waits that set a status bit).  The block's instances are then expanded load-balanced: each
+// output slot of the block's contiguous run is one thread's work (its entry found by binary
+// search over the block's exclusive offsets), so a Gaussian covering hundreds of tiles does
+// not hold its warp, and consecutive threads store consecutive slots.
 #include "common.cuh"
 
 namespace a3fr {
@@ -41,8 +42,6 @@ __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long l
   return v;
 }
 
-constexpr int kChunk = 2048;   // instances staged per chunk of the block's run
-
 __global__ void __launch_bounds__(kEmitThreads)
 emit_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
             const ushort4 *__restrict__ rect, uint32_t *__restrict__ tile_keys,
@@ -51,9 +50,8 @@ emit_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *
   __shared__ uint32_t s_blk;
   __shared__ uint32_t s_warp_total[kEmitWarps];
   __shared__ unsigned long long s_prefix;
-  __shared__ uint32_t s_block_total;
-  __shared__ uint32_t s_tiles[kChunk];
-  __shared__ uint32_t s_gids[kChunk];
+  __shared__ uint32_t s_excl[kEmitThreads + 1];   // exclusive instance offsets of the entries
+  __shared__ uint32_t s_tile0[kEmitThreads], s_width[kEmitThreads], s_gid[kEmitThreads];
 
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (t == 0) s_blk = atomicAdd(block_counter, 1u);
@@ -84,6 +82,10 @@ emit_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *
   __syncthreads();
   uint32_t excl = incl - cnt;
   for (int w = 0; w < warp; ++w) excl += s_warp_total[w];
+  s_excl[t] = excl;
+  s_tile0[t] = tile0;
+  s_width[t] = width;
+  s_gid[t] = gid;
 
   // block prefix by decoupled look-back, warp 0: each step reads a window of the 32
   // nearest unresolved predecessors (one per lane) and sums up to the nearest inclusive
@@ -125,45 +127,32 @@ emit_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *
     }
     if (lane == 0) {
       s_prefix = prefix;
-      s_block_total = block_total;
+      s_excl[kEmitThreads] = block_total;
     }
   }
   __syncthreads();
 
-  // the block's instances occupy [prefix, prefix + block_total): stage chunks of it in
-  // shared memory (each thread writes its entry's run, row by row), store coalesced
+  // the block's instances occupy [prefix, prefix + total): one output slot per thread at a
+  // time (consecutive threads, consecutive slots: coalesced stores); a slot's entry is the
+  // last one whose exclusive offset is <= the slot (binary search over the block's offsets)
   const unsigned long long prefix = s_prefix;
-  const uint32_t total = s_block_total;
-  for (uint32_t c0 = 0; c0 < total; c0 += kChunk) {
-    const uint32_t c1 = min(total, c0 + kChunk);
-    if (cnt) {
-      const uint32_t r0 = excl > c0 ? 0u : c0 - excl;            // first local index in chunk
-      const uint32_t r1 = min(cnt, c1 > excl ? c1 - excl : 0u);  // one past the last
-      if (r0 < r1) {
-        uint32_t dy = r0 / width, dx = r0 - dy * width;
-        uint32_t tile = tile0 + dy * (uint32_t)p.tiles_x + dx;
-        for (uint32_t r = r0; r < r1; ++r) {
-          const uint32_t o = excl + r - c0;
-          s_tiles[o] = tile;
-          s_gids[o] = gid;
-          if (++dx == width) {
-            dx = 0;
-            tile += (uint32_t)p.tiles_x - width + 1;
-          } else {
-            ++tile;
-          }
-        }
-      }
+  const uint32_t total = s_excl[kEmitThreads];
+  for (uint32_t q = t; q < total; q += kEmitThreads) {
+    int lo = 0, hi = kEmitThreads;   // s_excl[lo] <= q < s_excl[hi]
+#pragma unroll
+    for (int step = 0; step < 8; ++step) {
+      const int mid = (lo + hi) >> 1;
+      if (s_excl[mid] <= q) lo = mid;
+      else hi = mid;
     }
-    __syncthreads();
-    for (uint32_t q = c0 + t; q < c1; q += kEmitThreads) {
-      const unsigned long long off = prefix + q;
-      if (off < p.capacity) {
-        tile_keys[off] = s_tiles[q - c0];
-        vals[off] = s_gids[q - c0];
-      }
+    const uint32_t r = q - s_excl[lo];
+    const uint32_t w = s_width[lo];
+    const uint32_t dy = r / w, dx = r - dy * w;
+    const unsigned long long off = prefix + q;
+    if (off < p.capacity) {
+      tile_keys[off] = s_tile0[lo] + dy * (uint32_t)p.tiles_x + dx;
+      vals[off] = s_gid[lo];
     }
-    __syncthreads();
   }
 }
 
