@@ -97,6 +97,19 @@ plan_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ ga
   }
 }
 
+// Conservative box of the pixels where a Gaussian can reach alpha >= 1/255: the ellipse
+// d^T conic d <= 2 ln(255 opacity) has half-extents k sqrt(cov_xx), k sqrt(cov_yy) with cov
+// the inverse of the conic; one pixel of margin absorbs rounding.  Empty (never hit) when
+// opacity < 1/255.  (x0, x1, y0, y1).
+__device__ __forceinline__ float4 support_box(float u, float v, float ca, float cb, float cc, float op) {
+  const float k2 = 2.0f * __logf(255.0f * op);
+  if (!(k2 > 0.0f)) return make_float4(1e30f, -1e30f, 1e30f, -1e30f);
+  const float det = ca * cc - cb * cb;
+  const float ex = sqrtf(k2 * cc / det) + 1.0f, ey = sqrtf(k2 * ca / det) + 1.0f;
+  if (!(ex < 1e6f) || !(ey < 1e6f)) return make_float4(-1e30f, 1e30f, -1e30f, 1e30f);
+  return make_float4(u - ex, u + ex, v - ey, v + ey);
+}
+
 // Barrier of a staging group of `size` threads (64, 128 or 256) with barrier id `bar`
 // (1..4).  The ids are literals so the kernel reserves 5 hardware barriers, not 16 (the
 // per-SM barrier budget would otherwise cap residency at 4 CTAs).
@@ -351,7 +364,10 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
 
 // 32 x 32 tiles (the paper's tiling, Sec. 3.5): a tile is 16 x 16 blocks of 2 x 2 pixels and
 // each of its four labels is one 256-thread group; a level-k tile runs the groups of its
-// labels (lo, lo + k] and no other.  Here each (tile, label) pair is one CTA, taken from the
+// labels (lo, lo + k] and no other.  A warp's pixels are a 4-row band of the tile, which many
+// of the tile's Gaussians cannot reach: each staged Gaussian carries the box where its alpha
+// can reach 1/255, and a warp skips (uniformly) the Gaussians whose box misses its band --
+// those would fail the 1/255 test at every pixel of the band, so the image is unchanged.  Here each (tile, label) pair is one CTA, taken from the
 // same level buckets as the 16-pixel kernel (a bucket-c entry spawns c CTAs), so only the
 // groups that render are ever launched.  The label-1 CTA of a tile rendered from label 0
 // also writes the inherited pixels of its blocks.
@@ -371,6 +387,7 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
   __shared__ float4 s_geo[NB];
   __shared__ float2 s_cz[NB];
   __shared__ float4 s_rgb[NB];
+  __shared__ float4 s_box[NB];
   __shared__ int s_done[kThreads / 32];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int n_ranges = p.n_eyes * p.n_tiles;
@@ -418,6 +435,9 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
   const int px = tx * T32 + 2 * bx + ox, py = ty * T32 + 2 * by + oy;
   const bool inside = px < p.width && py < p.height;
   const float fpx = (float)px, fpy = (float)py;
+  // the warp's pixels: one label of a 16 x 2 block strip (x every other pixel, 4 rows)
+  const float wx0 = (float)(tx * T32 + ox), wx1 = wx0 + 30.0f;
+  const float wy0 = (float)(ty * T32 + 4 * warp + oy), wy1 = wy0 + 2.0f;
 
   uint2 range = ranges[gtile];
   const uint32_t n_kept = *kept;
@@ -448,10 +468,12 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
         s_geo[slot] = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
         s_cz[slot] = make_float2(__fmul_rn(-0.5f * kLog2e, b.x), c.y);
         s_rgb[slot] = make_float4(b.z, b.w, c.x, b.y);
+        s_box[slot] = support_box(a.x, a.y, a.z, a.w, b.x, b.y);
       } else if (slot < ((cnt + 3u) & ~3u)) {
         s_geo[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         s_cz[slot] = make_float2(0.0f, 0.0f);
         s_rgb[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        s_box[slot] = make_float4(1e30f, -1e30f, 1e30f, -1e30f);
       }
     }
     __syncthreads();
@@ -462,6 +484,8 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           const int e = (int)k + j;
+          const float4 box = s_box[e];
+          if (box.y < wx0 || box.x > wx1 || box.w < wy0 || box.z > wy1) continue;   // misses the warp
           const float4 geo = s_geo[e];
           const float2 cz = s_cz[e];
           const float4 rgb = s_rgb[e];
