@@ -1,7 +1,7 @@
 // a3fr_api.cu -- the C ABI of libA3FR.so (declared in include/a3fr.h): scene objects,
 // library-owned device workspace, the gaze mailbox, and the orchestration of one render:
 //
-//   preprocess -> scan_blocks -> emit_keys -> onesweep sort -> tile_ranges
+//   preprocess -> depth sort -> tile counts / ranges -> emit -> tile sort -> plan + composite
 //        -> [wait for the gaze event] -> composite (level map + blend + inherit)
 //
 // all enqueued on the caller's stream without a host synchronisation (except the very
@@ -169,8 +169,8 @@ FrameLayout frame_layout(size_t entries, size_t capacity, int tile_passes, int e
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
   L.tile_diff = up(L.emit_lb + emit_lookback_bytes((int)entries));
   L.depth_lb = up(L.tile_diff + sizeof(uint32_t) * (size_t)eyes * (tiles_x + 1) * (tiles_y + 1));
-  L.tile_lb = up(L.depth_lb + onesweep_lookback_bytes(entries, kDepthPasses, false));
-  L.total = up(L.tile_lb + onesweep_lookback_bytes(capacity, tile_passes, false));
+  L.tile_lb = up(L.depth_lb + onesweep_lookback_bytes(entries, kDepthPasses, false, false));
+  L.total = up(L.tile_lb + onesweep_lookback_bytes(capacity, tile_passes, false, false));
   return L;
 }
 
@@ -451,7 +451,7 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
     bool in_alt = false;
     A3FR_CHECK(launch_onesweep<uint32_t>(s->dkeys[0], s->dvals[0], s->dkeys[1], s->dvals[1], true,
                                          counts + 4, (size_t)n_entries, depth_plan, depth_hist,
-                                         depth_ctr, depth_lb, s->status, &in_alt, stream));
+                                         depth_ctr, depth_lb, s->status, &in_alt, stream, false));
     *launches += 1 + depth_plan.passes;
   }
   const uint32_t *entries = s->dvals[depth_plan.passes % 2];

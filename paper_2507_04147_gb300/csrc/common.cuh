@@ -86,8 +86,9 @@ cudaError_t launch_preprocess(const PreParams *p_dev, int n, int sh_degree, cons
                               uint32_t *depth_count, cudaStream_t s);
 
 SortPlan sort_plan(int key_bits, int digit_bits_max);
-size_t onesweep_part_size(bool wide_keys);
-size_t onesweep_lookback_bytes(size_t capacity, int passes, bool wide_keys);
+// small_parts: 2048-key partitions for 32-bit keys (more CTAs for short inputs), else 4096.
+size_t onesweep_part_size(bool wide_keys, bool small_parts);
+size_t onesweep_lookback_bytes(size_t capacity, int passes, bool wide_keys, bool small_parts);
 template <typename K>
 cudaError_t launch_histogram(const K *keys, const uint32_t *d_count, size_t capacity,
                              const SortPlan &plan, uint32_t *hist, cudaStream_t s);
@@ -99,7 +100,7 @@ cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
                             bool implicit_vals, const uint32_t *d_count, size_t capacity,
                             const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
                             uint32_t *lookback, uint32_t *status, bool *result_in_alt,
-                            cudaStream_t s);
+                            cudaStream_t s, bool small_parts = false);
 
 // The 64-bit pair sort of the public API: workspace = histograms | counters | look-back.
 size_t sort_workspace_bytes(size_t capacity);

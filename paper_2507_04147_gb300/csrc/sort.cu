@@ -119,14 +119,13 @@ histogram_kernel(const K *__restrict__ keys, const uint32_t *__restrict__ d_coun
   }
 }
 
-template <typename K>
+template <typename K, int KPT>
 __global__ void __launch_bounds__(kThreads, 3)
 onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
                 K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                 const uint32_t *__restrict__ d_count, const uint32_t *__restrict__ hist,
                 uint32_t *__restrict__ part_counter, uint32_t *__restrict__ lookback, int shift,
                 uint32_t mask, uint32_t *__restrict__ status) {
-  constexpr int KPT = Part<K>::kKPT;
   constexpr int PART = kThreads * KPT;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   K *s_keys = reinterpret_cast<K *>(s_dyn);
@@ -255,7 +254,7 @@ int sm_count() {
   return sms;
 }
 
-template <typename K>
+template <typename K, int KPT>
 cudaError_t set_smem_attr() {
   // per device: the attribute lives in each device's context
   constexpr int kMaxDev = 64;
@@ -264,8 +263,8 @@ cudaError_t set_smem_attr() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < kMaxDev && done[dev]) return cudaSuccess;
-  constexpr int PART = kThreads * Part<K>::kKPT;
-  e = cudaFuncSetAttribute(onesweep_kernel<K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  constexpr int PART = kThreads * KPT;
+  e = cudaFuncSetAttribute(onesweep_kernel<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            (int)((sizeof(K) + sizeof(uint32_t)) * PART));
   if (e == cudaSuccess && dev >= 0 && dev < kMaxDev) done[dev] = true;
   return e;
@@ -283,12 +282,12 @@ SortPlan sort_plan(int key_bits, int digit_bits_max) {
   return p;
 }
 
-size_t onesweep_part_size(bool wide_keys) {
-  return (size_t)kThreads * (wide_keys ? Part<uint64_t>::kKPT : Part<uint32_t>::kKPT);
+size_t onesweep_part_size(bool wide_keys, bool small_parts) {
+  return (size_t)kThreads * (wide_keys ? Part<uint64_t>::kKPT : (small_parts ? 8 : Part<uint32_t>::kKPT));
 }
 
-size_t onesweep_lookback_bytes(size_t capacity, int passes, bool wide_keys) {
-  const size_t part = onesweep_part_size(wide_keys);
+size_t onesweep_lookback_bytes(size_t capacity, int passes, bool wide_keys, bool small_parts) {
+  const size_t part = onesweep_part_size(wide_keys, small_parts);
   return sizeof(uint32_t) * kRadix * (size_t)passes * ((capacity + part - 1) / part);
 }
 
@@ -303,17 +302,17 @@ cudaError_t launch_histogram(const K *keys, const uint32_t *d_count, size_t capa
   return cudaGetLastError();
 }
 
-template <typename K>
-cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
-                            bool implicit_vals, const uint32_t *d_count, size_t capacity,
-                            const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
-                            uint32_t *lookback, uint32_t *status, bool *result_in_alt,
-                            cudaStream_t s) {
+template <typename K, int KPT>
+cudaError_t launch_onesweep_kpt(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
+                                bool implicit_vals, const uint32_t *d_count, size_t capacity,
+                                const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
+                                uint32_t *lookback, uint32_t *status, bool *result_in_alt,
+                                cudaStream_t s) {
   *result_in_alt = false;
   if (capacity == 0) return cudaSuccess;
-  cudaError_t e = set_smem_attr<K>();
+  cudaError_t e = set_smem_attr<K, KPT>();
   if (e != cudaSuccess) return e;
-  constexpr int PART = kThreads * Part<K>::kKPT;
+  constexpr int PART = kThreads * KPT;
   const size_t parts = (capacity + PART - 1) / PART;
   const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * PART;
   K *kin = keys, *kout = keys_alt;
@@ -321,7 +320,7 @@ cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
   for (int p = 0; p < plan.passes; ++p) {
     // the first pass may take the values to be the input positions (vals unread)
     const uint32_t *vsrc = (p == 0 && implicit_vals) ? nullptr : vin;
-    onesweep_kernel<K><<<(unsigned)parts, kThreads, dyn, s>>>(
+    onesweep_kernel<K, KPT><<<(unsigned)parts, kThreads, dyn, s>>>(
         kin, vsrc, kout, vout, d_count, hist + p * kRadix, counters + p,
         lookback + (size_t)kRadix * parts * p, plan.shift[p], plan.mask, status);
     e = cudaGetLastError();
@@ -333,19 +332,33 @@ cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
   return cudaSuccess;
 }
 
+template <typename K>
+cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
+                            bool implicit_vals, const uint32_t *d_count, size_t capacity,
+                            const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
+                            uint32_t *lookback, uint32_t *status, bool *result_in_alt,
+                            cudaStream_t s, bool small_parts) {
+  if (sizeof(K) == 4 && small_parts)
+    return launch_onesweep_kpt<K, 8>(keys, vals, keys_alt, vals_alt, implicit_vals, d_count, capacity,
+                                     plan, hist, counters, lookback, status, result_in_alt, s);
+  return launch_onesweep_kpt<K, Part<K>::kKPT>(keys, vals, keys_alt, vals_alt, implicit_vals, d_count,
+                                               capacity, plan, hist, counters, lookback, status,
+                                               result_in_alt, s);
+}
+
 template cudaError_t launch_histogram<uint32_t>(const uint32_t *, const uint32_t *, size_t,
                                                 const SortPlan &, uint32_t *, cudaStream_t);
 template cudaError_t launch_onesweep<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *,
                                                bool, const uint32_t *, size_t, const SortPlan &,
                                                const uint32_t *, uint32_t *, uint32_t *,
-                                               uint32_t *, bool *, cudaStream_t);
+                                               uint32_t *, bool *, cudaStream_t, bool);
 
 // ---- the 64-bit pair sort of the public API (8-bit digits) ----
 constexpr size_t kHistBytes = sizeof(uint32_t) * kMaxSortPasses * kRadix;
 constexpr size_t kCounterBytes = 256;
 
 size_t sort_workspace_bytes(size_t capacity) {
-  return kHistBytes + kCounterBytes + onesweep_lookback_bytes(capacity, kMaxSortPasses, true);
+  return kHistBytes + kCounterBytes + onesweep_lookback_bytes(capacity, kMaxSortPasses, true, false);
 }
 
 cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
@@ -359,12 +372,12 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint
   uint32_t *counters = reinterpret_cast<uint32_t *>(ws + kHistBytes);
   uint32_t *lookback = reinterpret_cast<uint32_t *>(ws + kHistBytes + kCounterBytes);
   cudaError_t e = cudaMemsetAsync(
-      ws, 0, kHistBytes + kCounterBytes + onesweep_lookback_bytes(capacity, plan.passes, true), s);
+      ws, 0, kHistBytes + kCounterBytes + onesweep_lookback_bytes(capacity, plan.passes, true, false), s);
   if (e != cudaSuccess) return e;
   e = launch_histogram<uint64_t>(keys, d_count, capacity, plan, hist, s);
   if (e != cudaSuccess) return e;
   return launch_onesweep<uint64_t>(keys, vals, keys_alt, vals_alt, false, d_count, capacity,
-                                   plan, hist, counters, lookback, status, result_in_alt, s);
+                                   plan, hist, counters, lookback, status, result_in_alt, s, false);
 }
 
 }  // namespace a3fr
