@@ -53,6 +53,8 @@ def parse_args(argv=None):
     p.add_argument("--cpu-budget", type=float, default=15.0, help="seconds of oracle work for cpu_baseline")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--skip-3m", action="store_true", help="skip the 3M-Gaussian clustered section")
+    p.add_argument("--tune", default="auto", choices=["auto", "16x1", "16x2", "32x1", "32x2"],
+                   help="tile x staging batch: autotuned, or fixed (profiler runs need a fixed one)")
     p.add_argument("--quick", action="store_true",
                    help="timed loops and stage breakdown only (no PSNR, e2e, rounds, 3M, CPU legs); "
                         "the short command the profiler captures")
@@ -376,8 +378,14 @@ def run_ours(args):
     except Exception:
         dev_uuid = None
     # autotuner: tile size and staging batch picked on this workload's first frame
-    with torch.cuda.stream(render_stream):
-        tuned = scene.autotune(fovea, out=out, timed_renders=5, stream=render_stream)
+    if args.tune == "auto":
+        with torch.cuda.stream(render_stream):
+            tuned = scene.autotune(fovea, out=out, timed_renders=5, stream=render_stream)
+    else:
+        t_, m_ = (int(v) for v in args.tune.split("x"))
+        scene.set_tile(t_)
+        scene.set_batch(m_)
+        tuned = {"tile": t_, "batch_mult": m_, "ms": {}}
     torch.cuda.synchronize()
     for s_ in range(3):
         enqueue(frames[0], False, out)
