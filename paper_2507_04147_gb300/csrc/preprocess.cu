@@ -86,13 +86,25 @@ __device__ __forceinline__ void stage(float *dst, const float *__restrict__ src,
                                       int row, int stride) {
   const int n4 = count >> 2;
   const float4 *src4 = reinterpret_cast<const float4 *>(src);
-  for (int i = threadIdx.x; i < n4; i += blockDim.x) {
-    const float4 v = __ldg(src4 + i);
-    const float e[4] = {v.x, v.y, v.z, v.w};
+  // four independent 16-byte loads in flight per thread before the shared-memory stores
+  for (int i0 = threadIdx.x; i0 < n4; i0 += 4 * blockDim.x) {
+    float4 v[4];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int f = 4 * i + j;
-      dst[(f / row) * stride + (f % row)] = e[j];
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      v[u] = i < n4 ? __ldg(src4 + i) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int i = i0 + u * blockDim.x;
+      if (i < n4) {
+        const float e[4] = {v[u].x, v[u].y, v[u].z, v[u].w};
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int f = 4 * i + j;
+          dst[(f / row) * stride + (f % row)] = e[j];
+        }
+      }
     }
   }
   for (int f = 4 * n4 + threadIdx.x; f < count; f += blockDim.x)
