@@ -511,8 +511,8 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
   ep.capacity = (uint32_t)s->capacity;
   if (n > 0 && s->capacity > 0) {
     A3FR_CHECK(launch_emit(ep, entries, s->touched, s->rect, s->tkeys[0], s->tvals[0], emit_lb,
-                           counts + 6, s->status, stream));
-    ++*launches;
+                           counts + 6, stream));
+    *launches += 2;
   }
   A3FR_CHECK(mark(s, A3FR_STAGE_TILE_SORT, stream));
   bool in_alt = false;

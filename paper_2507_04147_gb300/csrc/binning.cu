@@ -15,12 +15,12 @@
 // each tile's run, i.e. the tile ranges; the digit histograms of that sort follow from the
 // same prefix sums.  So neither a ranges pass nor a histogram pass is needed.
 //
-// emit: instance offsets by a single-pass scan with decoupled look-back over dynamically
-// numbered blocks (64-bit flag|value words; a warp reads 32 predecessors per step; bounded
-// waits that set a status bit).  The block's instances are then expanded load-balanced: each
-// output slot of the block's contiguous run is one thread's work (its entry found by binary
-// search over the block's exclusive offsets), so a Gaussian covering hundreds of tiles does
-// not hold its warp, and consecutive threads store consecutive slots.
+// emit: instance offsets by reduce-then-scan over blocks of 1024 depth-ordered entries (a
+// count kernel whose last block scans the block sums; no block ever waits on another), then
+// each block expands its instances load-balanced: each output slot of its contiguous run is
+// one thread's work (its entry found by binary search over the block's exclusive offsets), so
+// a Gaussian covering hundreds of tiles does not hold its warp, and consecutive threads store
+// consecutive slots.
 #include "common.cuh"
 
 namespace a3fr {
@@ -28,51 +28,98 @@ namespace {
 
 constexpr int kEmitThreads = 256;
 constexpr int kEmitWarps = kEmitThreads / 32;
-constexpr unsigned long long kEFlagAgg = 1ull << 62;
-constexpr unsigned long long kEFlagPrefix = 2ull << 62;
-constexpr unsigned long long kEValMask = (1ull << 62) - 1ull;
-constexpr uint32_t kSpinLimit = 1u << 16;   // with back-off: well over a second
-
-__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+constexpr int kEmitPer = 4;                                // entries per thread
+constexpr int kEmitEntries = kEmitThreads * kEmitPer;      // entries per block
+// Instance count of every block of kEmitEntries depth-ordered entries; the last block to
+// finish (fence + counter: the blocks never wait on one another) turns the sums into
+// exclusive prefixes in place, with the total after the last block.
+__global__ void __launch_bounds__(kEmitThreads)
+emit_count_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
+                  unsigned long long *__restrict__ blk, uint32_t *__restrict__ done_counter) {
+  __shared__ unsigned long long s_w[kEmitWarps];
+  __shared__ unsigned long long s_carry;
+  __shared__ bool s_last;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < kEmitPer; ++k) {
+    const uint32_t j = blockIdx.x * kEmitEntries + t * kEmitPer + k;
+    if (j < (uint32_t)p.n_entries) sum += touched[entries[j]];
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) s_w[warp] = sum;
+  __syncthreads();
+  if (t == 0) {
+    unsigned long long total = 0;
+    for (int w = 0; w < kEmitWarps; ++w) total += s_w[w];
+    blk[blockIdx.x] = total;
+    __threadfence();
+    s_last = atomicAdd(done_counter, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (t == 0) s_carry = 0;
+  __syncthreads();
+  const int nb = gridDim.x;
+  for (int base = 0; base < nb; base += kEmitThreads) {
+    const int i = base + t;
+    const unsigned long long v = i < nb ? __ldcg(blk + i) : 0ull;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long n = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += n;
+    }
+    if (lane == 31) s_w[warp] = incl;
+    __syncthreads();
+    unsigned long long before = s_carry;
+    for (int w = 0; w < warp; ++w) before += s_w[w];
+    if (i < nb) blk[i] = before + incl - v;
+    __syncthreads();
+    if (t == kEmitThreads - 1) s_carry = before + incl;
+    __syncthreads();
+  }
+  if (t == 0) blk[nb] = s_carry;
 }
-__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
-  return v;
-}
 
+// Instances of block blockIdx.x's entries at [blk[blockIdx.x], +count): each thread reads
+// kEmitPer consecutive entries, the block scans them, and the block's run is expanded
+// load-balanced: one output slot per thread at a time (consecutive threads, consecutive
+// slots), its entry found by binary search over the block's exclusive offsets.
 __global__ void __launch_bounds__(kEmitThreads)
 emit_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
             const ushort4 *__restrict__ rect, uint32_t *__restrict__ tile_keys,
-            uint32_t *__restrict__ vals, unsigned long long *__restrict__ lookback,
-            uint32_t *__restrict__ block_counter, uint32_t *__restrict__ status) {
-  __shared__ uint32_t s_blk;
+            uint32_t *__restrict__ vals, const unsigned long long *__restrict__ blk) {
   __shared__ uint32_t s_warp_total[kEmitWarps];
-  __shared__ unsigned long long s_prefix;
-  __shared__ uint32_t s_excl[kEmitThreads + 1];   // exclusive instance offsets of the entries
-  __shared__ uint32_t s_tile0[kEmitThreads], s_width[kEmitThreads], s_gid[kEmitThreads];
-
+  __shared__ uint32_t s_excl[kEmitEntries + 1];   // exclusive instance offsets of the entries
+  __shared__ uint32_t s_tile0[kEmitEntries], s_width[kEmitEntries], s_gid[kEmitEntries];
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  if (t == 0) s_blk = atomicAdd(block_counter, 1u);
-  __syncthreads();
-  const uint32_t blk = s_blk;
-  const uint32_t j = blk * kEmitThreads + t;
-
-  uint32_t cnt = 0, tile0 = 0, width = 1, gid = 0;
-  if (j < (uint32_t)p.n_entries) {
-    const uint32_t v = entries[j];          // e * n + i
-    cnt = touched[v];
-    if (cnt) {
-      const uint32_t eye = v >= (uint32_t)p.n ? 1u : 0u;
-      gid = v - eye * (uint32_t)p.n;
-      const ushort4 rc = rect[v];
-      tile0 = eye * (uint32_t)p.n_tiles + (uint32_t)rc.y * (uint32_t)p.tiles_x + rc.x;
-      width = (uint32_t)(rc.z - rc.x);
+  uint32_t cnt[kEmitPer], mine = 0;
+#pragma unroll
+  for (int k = 0; k < kEmitPer; ++k) {
+    const int le = t * kEmitPer + k;
+    const uint32_t j = blockIdx.x * kEmitEntries + le;
+    uint32_t c = 0, tile0 = 0, width = 1, gid = 0;
+    if (j < (uint32_t)p.n_entries) {
+      const uint32_t v = entries[j];          // e * n + i
+      c = touched[v];
+      if (c) {
+        const uint32_t eye = v >= (uint32_t)p.n ? 1u : 0u;
+        gid = v - eye * (uint32_t)p.n;
+        const ushort4 rc = rect[v];
+        tile0 = eye * (uint32_t)p.n_tiles + (uint32_t)rc.y * (uint32_t)p.tiles_x + rc.x;
+        width = (uint32_t)(rc.z - rc.x);
+      }
     }
+    cnt[k] = c;
+    mine += c;
+    s_tile0[le] = tile0;
+    s_width[le] = width;
+    s_gid[le] = gid;
   }
-  // block scan of the instance counts
-  uint32_t incl = cnt;
+  uint32_t incl = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
@@ -80,67 +127,21 @@ emit_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *
   }
   if (lane == 31) s_warp_total[warp] = incl;
   __syncthreads();
-  uint32_t excl = incl - cnt;
+  uint32_t excl = incl - mine;
   for (int w = 0; w < warp; ++w) excl += s_warp_total[w];
-  s_excl[t] = excl;
-  s_tile0[t] = tile0;
-  s_width[t] = width;
-  s_gid[t] = gid;
-
-  // block prefix by decoupled look-back, warp 0: each step reads a window of the 32
-  // nearest unresolved predecessors (one per lane) and sums up to the nearest inclusive
-  // prefix; an unpublished predecessor is polled again after a back-off (bounded)
-  if (warp == 0) {
-    uint32_t block_total = 0;
-    for (int w = 0; w < kEmitWarps; ++w) block_total += s_warp_total[w];
-    unsigned long long *mine = lookback + blk;
-    if (lane == 0) st_relaxed64(mine, (blk == 0 ? kEFlagPrefix : kEFlagAgg) | block_total);
-    unsigned long long prefix = 0;
-    if (blk > 0) {
-      int base = (int)blk - 1;
-      uint32_t spins = 0;
-      while (true) {
-        const int q = base - lane;
-        const unsigned long long w = q >= 0 ? ld_relaxed64(lookback + q) : kEFlagPrefix;
-        const unsigned long long flag = w & ~kEValMask;
-        const unsigned not_ready = __ballot_sync(0xffffffffu, flag == 0ull);
-        const unsigned is_prefix = __ballot_sync(0xffffffffu, flag == kEFlagPrefix);
-        const int first_prefix = is_prefix ? __ffs(is_prefix) - 1 : 32;
-        const int first_wait = not_ready ? __ffs(not_ready) - 1 : 32;
-        const int upto = first_wait < first_prefix ? first_wait : first_prefix;   // lanes < upto are AGG
-        const bool take = lane < upto || (lane == first_prefix && first_prefix < first_wait);
-        unsigned long long v = take ? (w & kEValMask) : 0ull;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-        prefix += v;
-        if (first_prefix < first_wait) break;          // reached an inclusive prefix
-        base -= upto;
-        if (first_wait < 32) {   // an unpublished predecessor: back off before polling again
-          if (++spins > kSpinLimit) {
-            if (lane == 0) atomicOr(status, kStatusTimeout);
-            break;
-          }
-          __nanosleep(spins < 8 ? 32u << spins : 4096u);
-        }
-      }
-      if (lane == 0) st_relaxed64(mine, kEFlagPrefix | ((prefix + block_total) & kEValMask));
-    }
-    if (lane == 0) {
-      s_prefix = prefix;
-      s_excl[kEmitThreads] = block_total;
-    }
+  for (int k = 0; k < kEmitPer; ++k) {
+    s_excl[t * kEmitPer + k] = excl;
+    excl += cnt[k];
   }
+  if (t == kEmitThreads - 1) s_excl[kEmitEntries] = excl;
   __syncthreads();
-
-  // the block's instances occupy [prefix, prefix + total): one output slot per thread at a
-  // time (consecutive threads, consecutive slots: coalesced stores); a slot's entry is the
-  // last one whose exclusive offset is <= the slot (binary search over the block's offsets)
-  const unsigned long long prefix = s_prefix;
-  const uint32_t total = s_excl[kEmitThreads];
+  const unsigned long long prefix = blk[blockIdx.x];
+  const uint32_t total = s_excl[kEmitEntries];
   for (uint32_t q = t; q < total; q += kEmitThreads) {
-    int lo = 0, hi = kEmitThreads;   // s_excl[lo] <= q < s_excl[hi]
+    int lo = 0, hi = kEmitEntries;   // s_excl[lo] <= q < s_excl[hi]
 #pragma unroll
-    for (int step = 0; step < 8; ++step) {
+    for (int step = 0; step < 10; ++step) {
       const int mid = (lo + hi) >> 1;
       if (s_excl[mid] <= q) lo = mid;
       else hi = mid;
@@ -376,17 +377,18 @@ int grid_for(size_t work, int per_block) {
 }  // namespace
 
 size_t emit_lookback_bytes(int n_entries) {
-  return sizeof(unsigned long long) * (size_t)((n_entries + kEmitThreads - 1) / kEmitThreads + 1);
+  return sizeof(unsigned long long) * (size_t)((n_entries + kEmitEntries - 1) / kEmitEntries + 1);
 }
 
 cudaError_t launch_emit(const EmitParams &p, const uint32_t *entries, const uint32_t *touched,
                         const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
-                        unsigned long long *lookback, uint32_t *block_counter, uint32_t *status,
-                        cudaStream_t s) {
+                        unsigned long long *blk, uint32_t *done_counter, cudaStream_t s) {
   if (p.n_entries <= 0) return cudaSuccess;
-  const int blocks = (p.n_entries + kEmitThreads - 1) / kEmitThreads;
-  emit_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, rect, tile_keys, vals,
-                                              lookback, block_counter, status);
+  const int blocks = (p.n_entries + kEmitEntries - 1) / kEmitEntries;
+  emit_count_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, blk, done_counter);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  emit_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, rect, tile_keys, vals, blk);
   return cudaGetLastError();
 }
 

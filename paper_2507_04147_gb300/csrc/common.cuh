@@ -116,8 +116,7 @@ struct EmitParams {
 size_t emit_lookback_bytes(int n_entries);
 cudaError_t launch_emit(const EmitParams &p, const uint32_t *entries, const uint32_t *touched,
                         const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
-                        unsigned long long *lookback, uint32_t *block_counter, uint32_t *status,
-                        cudaStream_t s);
+                        unsigned long long *blk, uint32_t *done_counter, cudaStream_t s);
 
 // Per-tile instance counts without enumerating instances: every tile rectangle adds
 // +1/-1/-1/+1 at its four corners in a per-eye 2-D difference grid (tiles_y+1 rows of
