@@ -364,10 +364,11 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
 
 // 32 x 32 tiles (the paper's tiling, Sec. 3.5): a tile is 16 x 16 blocks of 2 x 2 pixels and
 // each of its four labels is one 256-thread group; a level-k tile runs the groups of its
-// labels (lo, lo + k] and no other.  A warp's pixels are a 4-row band of the tile, which many
-// of the tile's Gaussians cannot reach: each staged Gaussian carries the box where its alpha
-// can reach 1/255, and a warp skips (uniformly) the Gaussians whose box misses its band --
-// those would fail the 1/255 test at every pixel of the band, so the image is unchanged.  Here each (tile, label) pair is one CTA, taken from the
+// labels (lo, lo + k] and no other.  A warp's pixels are one label of an 8 x 4 patch of blocks
+// (a 16 x 8 pixel area), which many of the tile's Gaussians cannot reach: each staged Gaussian
+// carries the box where its alpha can reach 1/255, and a warp skips (uniformly) the Gaussians
+// whose box misses its patch -- those would fail the 1/255 test at every pixel of the patch,
+// so the image is unchanged.  Here each (tile, label) pair is one CTA, taken from the
 // same level buckets as the 16-pixel kernel (a bucket-c entry spawns c CTAs), so only the
 // groups that render are ever launched.  The label-1 CTA of a tile rendered from label 0
 // also writes the inherited pixels of its blocks.
@@ -431,13 +432,15 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
   const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
   const int ox = (label == 1 || label == 2) ? 1 : 0;   // BR, TR
   const int oy = (label == 1 || label == 3) ? 1 : 0;   // BR, BL
-  const int bx = t & 15, by = t >> 4;
+  // warp w covers an 8 x 4 patch of blocks (column half w & 1, row quarter w >> 1): a squarer
+  // footprint than a strip, so fewer Gaussian boxes reach it
+  const int bx = (lane & 7) + 8 * (warp & 1), by = (lane >> 3) + 4 * (warp >> 1);
   const int px = tx * T32 + 2 * bx + ox, py = ty * T32 + 2 * by + oy;
   const bool inside = px < p.width && py < p.height;
   const float fpx = (float)px, fpy = (float)py;
-  // the warp's pixels: one label of a 16 x 2 block strip (x every other pixel, 4 rows)
-  const float wx0 = (float)(tx * T32 + ox), wx1 = wx0 + 30.0f;
-  const float wy0 = (float)(ty * T32 + 4 * warp + oy), wy1 = wy0 + 2.0f;
+  // the warp's pixels: one label of its 8 x 4 block patch (every other pixel)
+  const float wx0 = (float)(tx * T32 + 16 * (warp & 1) + ox), wx1 = wx0 + 14.0f;
+  const float wy0 = (float)(ty * T32 + 8 * (warp >> 1) + oy), wy1 = wy0 + 6.0f;
 
   uint2 range = ranges[gtile];
   const uint32_t n_kept = *kept;
