@@ -389,6 +389,7 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
   __shared__ float2 s_cz[NB];
   __shared__ float4 s_rgb[NB];
   __shared__ float4 s_box[NB];
+  __shared__ uint16_t s_hits[kThreads / 32][NB];   // per warp: batch slots whose box meets its patch
   __shared__ int s_done[kThreads / 32];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int n_ranges = p.n_eyes * p.n_tiles;
@@ -481,14 +482,26 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
     }
     __syncthreads();
     if (!__all_sync(0xffffffffu, done)) {
-      const uint32_t cnt4 = (cnt + 3u) & ~3u;
+      // the warp's hit list: 32 boxes tested per step, slots kept in list order
+      int n_hit = 0;
+      for (uint32_t base = 0; base < cnt; base += 32) {
+        const uint32_t k = base + (uint32_t)lane;
+        bool hit = false;
+        if (k < cnt) {
+          const float4 box = s_box[k];
+          hit = !(box.y < wx0 || box.x > wx1 || box.w < wy0 || box.z > wy1);
+        }
+        const unsigned m = __ballot_sync(0xffffffffu, hit);
+        if (hit) s_hits[warp][n_hit + __popc(m & ((1u << lane) - 1u))] = (uint16_t)k;
+        n_hit += __popc(m);
+      }
+      __syncwarp();
       const uint32_t pos0 = start - range.x + 1;
-      for (uint32_t k = 0; k < cnt4; k += 4) {
+      for (int i = 0; i < n_hit; i += 4) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          const int e = (int)k + j;
-          const float4 box = s_box[e];
-          if (box.y < wx0 || box.x > wx1 || box.w < wy0 || box.z > wy1) continue;   // misses the warp
+          if (i + j >= n_hit) break;
+          const int e = s_hits[warp][i + j];
           const float4 geo = s_geo[e];
           const float2 cz = s_cz[e];
           const float4 rgb = s_rgb[e];
@@ -499,7 +512,7 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
           const bool ok = !done && pw <= 0.0f && alpha >= 1.0f / 255.0f;
           const bool fin = ok && tt < 0.0001f;
           const bool upd = ok && !fin;
-          const uint32_t pos = pos0 + k + (uint32_t)j;
+          const uint32_t pos = pos0 + (uint32_t)e;
           const float w = upd ? alpha * T : 0.0f;
           C0 += rgb.x * w;
           C1 += rgb.y * w;
