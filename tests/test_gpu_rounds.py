@@ -23,11 +23,11 @@ def _built():
     __graft_entry__.build()
 
 
-def _setup(n=5000, w=200, h=168, stereo=True, seed=11):
+def _setup(n=5000, w=200, h=168, stereo=True, seed=11, tile=16):
     import torch
     scene_np = synth.uniform_scene(n, 1, seed=seed)
     cams = synth.stereo_cameras(w, h, 2.0) if stereo else [synth.pinhole_camera(w, h)]
-    s = a3fr.Scene.from_numpy(scene_np)
+    s = a3fr.Scene.from_numpy(scene_np, tile=tile)
     for e, c in enumerate(cams):
         s.set_camera(e, c)
     out = torch.zeros((len(cams), h, w, 3), dtype=torch.float32, device="cuda")
@@ -39,17 +39,18 @@ def _levels(s, eyes, n_tiles):
     return s.buffer(a3fr.BUF_LEVELS, torch.uint8).cpu().numpy().reshape(eyes, n_tiles)
 
 
-def test_rounds_follow_the_schedule_and_match_the_oracle():
+@pytest.mark.parametrize("tile", [16, 32])
+def test_rounds_follow_the_schedule_and_match_the_oracle(tile):
     import torch
-    scene_np, cams, s, out = _setup()
+    scene_np, cams, s, out = _setup(tile=tile)
     eyes = len(cams)
-    n_tiles = oracle.tiles(200, 16) * oracle.tiles(168, 16)
+    n_tiles = oracle.tiles(200, tile) * oracle.tiles(168, tile)
     expected = [30.0, 12.0, 0.0]
     ofv = oracle.fovea((18.0, 36.0), 0.0, (4, 2, 1))
     gfv = a3fr.Fovea((18.0, 36.0), 0.0, (4, 2, 1))
     st = torch.cuda.current_stream()
     s.begin_frame(gfv, a3fr.Rounds(expected, sir=True, sir_step_px=6.0), out=out, stream=st)
-    fr = [orounds.FrameRounds(cams[e], 16, ofv, expected, True, 6.0) for e in range(eyes)]
+    fr = [orounds.FrameRounds(cams[e], tile, ofv, expected, True, 6.0) for e in range(eyes)]
     torch.cuda.synchronize()
     assert np.array_equal(_levels(s, eyes, n_tiles), np.stack([f.level for f in fr]))
     # a prediction, two speculative rounds, a better prediction, the final prediction
@@ -71,8 +72,8 @@ def test_rounds_follow_the_schedule_and_match_the_oracle():
     img = out.cpu().numpy()
     full = s.render_full().cpu().numpy()
     for e in range(eyes):
-        rec, rect, _ = oracle.preprocess(scene_np, cams[e], 16)
-        ref = oracle.render(rec, rect, cams[e], 16, level=fr[e].level)
+        rec, rect, _ = oracle.preprocess(scene_np, cams[e], tile)
+        ref = oracle.render(rec, rect, cams[e], tile, level=fr[e].level)
         print(e, gh.compare_pixels(img[e].reshape(-1, 3), ref))
         live = ref.rendered.reshape(168, 200).astype(bool)
         assert np.array_equal(img[e][live], full[e][live])
