@@ -446,8 +446,8 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
   // depth sort of the (eye, Gaussian) entries: 4 passes, result back in dkeys[0]/dvals[0]
   A3FR_CHECK(mark(s, A3FR_STAGE_DEPTH_SORT, stream));
   if (n > 0) {
-    A3FR_CHECK(launch_histogram<uint32_t>(s->dkeys[0], counts + 4, (size_t)n_entries, depth_plan,
-                                          depth_hist, stream));
+    A3FR_CHECK(launch_depth_histogram(s->dkeys[0], counts + 4, counts + 5, (size_t)n_entries,
+                                      depth_plan, depth_hist, stream));
     bool in_alt = false;
     A3FR_CHECK(launch_onesweep<uint32_t>(s->dkeys[0], s->dvals[0], s->dkeys[1], s->dvals[1], true,
                                          counts + 4, (size_t)n_entries, depth_plan, depth_hist,

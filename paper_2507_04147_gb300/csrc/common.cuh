@@ -78,7 +78,8 @@ struct SortPlan {
 };
 
 // Writes rec/rect per eye, touched[e*n + i], the depth-sort keys dkeys[e*n + i] (depth bits,
-// 0xffffffff when culled) and depth_count[0] = n_eyes * n.
+// 0xffffffff when culled), depth_count[0] = n_eyes * n and the visible key range
+// (depth_count[1] = ~min, depth_count[3] = max, accumulated with atomics on zeroed counters).
 cudaError_t launch_preprocess(const PreParams *p_dev, int n, int sh_degree, const float *means,
                               const float *log_scales, const float *quats,
                               const float *opacity_logits, const float *sh, float *rec,
@@ -92,6 +93,13 @@ size_t onesweep_lookback_bytes(size_t capacity, int passes, bool wide_keys, bool
 template <typename K>
 cudaError_t launch_histogram(const K *keys, const uint32_t *d_count, size_t capacity,
                              const SortPlan &plan, uint32_t *hist, cudaStream_t s);
+// The depth keys' histogram, which first rebases them in place when the visible range fits in
+// 24 bits (visible: key - min, culled: 0xffffff; the order of the visible keys is unchanged and
+// culled entries emit nothing), so that the top digit is 0 everywhere and the last pass is a
+// copy.  range = {~min, -, max} as preprocess leaves it.
+cudaError_t launch_depth_histogram(uint32_t *keys, const uint32_t *d_count, const uint32_t *range,
+                                   size_t capacity, const SortPlan &plan, uint32_t *hist,
+                                   cudaStream_t s);
 // Sorts d_count[0] (<= capacity) pairs with `plan`; hist holds the digit counts of every
 // pass, counters and lookback are zeroed scratch.  With implicit_vals the first pass takes
 // each pair's value to be its input position.  *result_in_alt tells where the result is.

@@ -112,7 +112,7 @@ __device__ __forceinline__ void stage(float *dst, const float *__restrict__ src,
 }
 
 template <int K>
-__global__ void __launch_bounds__(kPreThreads)
+__global__ void __launch_bounds__(kPreThreads, 6)
 preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restrict__ means,
                   const float *__restrict__ log_scales, const float *__restrict__ quats,
                   const float *__restrict__ opacity_logits, const float *__restrict__ sh,
@@ -143,6 +143,7 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
   const int t = threadIdx.x;
   const int i = i0 + t;
   if (blockIdx.x == 0 && t == 0) depth_count[0] = (uint32_t)(p.n_eyes * n);
+  uint32_t kmin = 0xffffffffu, kmax = 0u;   // depth-key range of this thread's visible entries
   if (i < n) {
     const float mx = s_mean[3 * t], my = s_mean[3 * t + 1], mz = s_mean[3 * t + 2];
     // activation shared by the eyes
@@ -259,7 +260,33 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
       rect[(size_t)e * n + i] = rc;
       touched[(size_t)e * n + i] = n_touched;
       dkeys[(size_t)e * n + i] = vis ? __float_as_uint(tz) : 0xffffffffu;
+      if (vis) {
+        kmin = min(kmin, __float_as_uint(tz));
+        kmax = max(kmax, __float_as_uint(tz));
+      }
     }
+  }
+  // range of the visible depth keys: depth_count[1] = ~min, depth_count[3] = max (the counters
+  // start at zero every render, so the minimum is kept as the maximum of the complement)
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+  }
+  __shared__ uint32_t s_range[2];
+  if (t == 0) {
+    s_range[0] = 0u;
+    s_range[1] = 0u;
+  }
+  __syncthreads();
+  if ((t & 31) == 0 && kmax != 0u) {
+    atomicMax(&s_range[0], ~kmin);
+    atomicMax(&s_range[1], kmax);
+  }
+  __syncthreads();
+  if (t == 0 && s_range[1] != 0u) {
+    atomicMax(depth_count + 1, s_range[0]);
+    atomicMax(depth_count + 3, s_range[1]);
   }
 }
 

@@ -71,10 +71,10 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *s_tmp)
 // warp owns a private copy of the counters, summed at the end.
 constexpr int kHistKeysPerThread = 8;
 
-template <typename K>
+template <typename K, bool kRebase>
 __global__ void __launch_bounds__(kThreads)
-histogram_kernel(const K *__restrict__ keys, const uint32_t *__restrict__ d_count, SortPlan plan,
-                 uint32_t *__restrict__ hist) {
+histogram_kernel(K *__restrict__ keys, const uint32_t *__restrict__ d_count, SortPlan plan,
+                 uint32_t *__restrict__ hist, const uint32_t *__restrict__ range) {
   __shared__ uint32_t s_hist[kWarps][4][kRadix];   // per warp, up to 4 passes per launch
   const int t = threadIdx.x, warp = t >> 5;
   const uint32_t n = *d_count;
@@ -89,7 +89,15 @@ histogram_kernel(const K *__restrict__ keys, const uint32_t *__restrict__ d_coun
       uint32_t cur[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
       uint32_t run[4] = {0u, 0u, 0u, 0u};
       for (uint32_t i = i0; i < i1; ++i) {
-        const K k = keys[i];
+        K k = keys[i];
+        if (kRebase && p0 == 0) {
+          // visible keys are <= max; a range under 2^24 leaves the top digit zero
+          const uint32_t kmin = ~range[0], kmax = range[2];
+          if (kmax >= kmin && kmax - kmin < (1u << 24)) {
+            k = (K)((uint32_t)k <= kmax ? (uint32_t)k - kmin : 0xffffffu);
+            keys[i] = k;
+          }
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
           if (q < np) {
@@ -139,11 +147,21 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
   if (t == 0) s_part = atomicAdd(part_counter, 1u);
   for (int i = t; i < kWarps * kRadix; i += kThreads) (&s_whist[0][0])[i] = 0;
-  __syncthreads();
-  const uint32_t part = s_part;
   const uint32_t n = *d_count;
+  // a pass whose digit is the same for every key is the identity permutation (the sort is
+  // stable): each partition just copies itself
+  const bool trivial = __syncthreads_or(n > 0 && hist[t] == n) != 0;
+  const uint32_t part = s_part;
   const uint32_t base = part * PART;
   if (base >= n) return;
+  if (trivial) {
+    const uint32_t end = min(n, base + (uint32_t)PART);
+    for (uint32_t i = base + t; i < end; i += kThreads) {
+      keys_out[i] = keys_in[i];
+      vals_out[i] = vals_in ? vals_in[i] : i;
+    }
+    return;
+  }
 
   // load: warp w owns [base + w*32*KPT, ...), item k of lane l at k*32 + l
   K key[KPT];
@@ -291,14 +309,26 @@ size_t onesweep_lookback_bytes(size_t capacity, int passes, bool wide_keys, bool
   return sizeof(uint32_t) * kRadix * (size_t)passes * ((capacity + part - 1) / part);
 }
 
-template <typename K>
-cudaError_t launch_histogram(const K *keys, const uint32_t *d_count, size_t capacity,
-                             const SortPlan &plan, uint32_t *hist, cudaStream_t s) {
+int histogram_blocks(size_t capacity) {
   const int sms = sm_count();
   const size_t per_block = (size_t)kThreads * kHistKeysPerThread;
   const size_t hb = (capacity + per_block - 1) / per_block;
-  const int blocks = (int)(hb < (size_t)sms * 8 ? (hb > 0 ? hb : 1) : (size_t)sms * 8);
-  histogram_kernel<K><<<blocks, kThreads, 0, s>>>(keys, d_count, plan, hist);
+  return (int)(hb < (size_t)sms * 8 ? (hb > 0 ? hb : 1) : (size_t)sms * 8);
+}
+
+template <typename K>
+cudaError_t launch_histogram(const K *keys, const uint32_t *d_count, size_t capacity,
+                             const SortPlan &plan, uint32_t *hist, cudaStream_t s) {
+  histogram_kernel<K, false><<<histogram_blocks(capacity), kThreads, 0, s>>>(
+      const_cast<K *>(keys), d_count, plan, hist, nullptr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_depth_histogram(uint32_t *keys, const uint32_t *d_count, const uint32_t *range,
+                                   size_t capacity, const SortPlan &plan, uint32_t *hist,
+                                   cudaStream_t s) {
+  histogram_kernel<uint32_t, true><<<histogram_blocks(capacity), kThreads, 0, s>>>(
+      keys, d_count, plan, hist, range);
   return cudaGetLastError();
 }
 
