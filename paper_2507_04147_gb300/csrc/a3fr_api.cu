@@ -1113,6 +1113,10 @@ int a3fr_set_tile(a3fr_scene *s, int tile) {
   if (s->desc.tile == tile) return A3FR_OK;
   A3FR_CHECK(cudaDeviceSynchronize());
   free_frame_buffers(s);
+  if (s->auto_capacity) {   // the instance count changes with the tile: measure it again
+    free_instance_buffers(s);
+    s->capacity = 0;
+  }
   s->desc.tile = tile;
   s->alloc_gen++;
   s->bw_mode = 0;

@@ -203,11 +203,14 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
     total += c;
   }
   uint32_t *my_lb = lookback + (size_t)part * kRadix + d;
-  st_relaxed(my_lb, (part == 0 ? kFlagPrefix : kFlagAgg) | total);
+  // a digit with no key anywhere (narrow digits leave most of the 256 empty) needs no
+  // look-back: every partition skips it alike, so nobody reads its entries either
+  const bool used = hist[d] != 0u;
+  if (used) st_relaxed(my_lb, (part == 0 ? kFlagPrefix : kFlagAgg) | total);
   const uint32_t local_excl = block_excl_scan(total, s_tmp);
   const uint32_t global_excl = block_excl_scan(hist[d], s_tmp);
   uint32_t excl = 0;
-  if (part > 0) {
+  if (part > 0 && used) {
     // windowed look-back: kWin predecessors are read at once (independent loads), summed
     // nearest first up to the first inclusive prefix; an unpublished one is polled again
     int j = (int)part - 1;
