@@ -215,8 +215,7 @@ int a3fr_set_graph_mode(a3fr_scene *scene, int on);
  * tile is its own 256-thread CTA and only the labels a tile's level needs are launched.  The
  * per-thread staging batch (1 or 2 Gaussians per thread per shared-memory batch) trades
  * barrier count for shared memory.  Changing either invalidates the scene's buffers and
- * captured graphs (the next render reallocates); synchronous.  The backward rasterizer
- * needs tile 16. */
+ * captured graphs (the next render reallocates); synchronous. */
 int a3fr_set_tile(a3fr_scene *scene, int tile);
 int a3fr_set_batch(a3fr_scene *scene, int batch_mult);
 

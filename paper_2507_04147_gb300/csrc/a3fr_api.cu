@@ -1074,7 +1074,6 @@ int a3fr_backward(a3fr_scene *s, const float *dl_drgb, const a3fr_grads *g, void
   if (n > 0 && (!g->means || !g->log_scales || !g->quats || !g->opacity_logits || !g->sh))
     return A3FR_ERR_INVALID_ARG;
   if (s->bw_mode == 0 || s->last_eyes == 0) return A3FR_ERR_NOT_READY;
-  if (s->desc.tile != 16) return A3FR_ERR_INVALID_ARG;   // the backward walks 16-pixel tiles
   if (n == 0) return A3FR_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int eyes = s->last_eyes;
@@ -1094,6 +1093,7 @@ int a3fr_backward(a3fr_scene *s, const float *dl_drgb, const a3fr_grads *g, void
   bp.n = n;
   bp.width = s->cams[0].width;
   bp.height = s->cams[0].height;
+  bp.tile = s->desc.tile;
   bp.tiles_x = s->TX;
   bp.n_tiles = s->n_tiles;
   const int b = s->sorted_in_alt ? 1 : 0;

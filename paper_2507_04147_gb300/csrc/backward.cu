@@ -2,7 +2,7 @@
 // with respect to the scene parameters, for a loss whose gradient with respect to the
 // rendered image is given (L = sum(dl_drgb * image)).
 //
-// composite_backward: one CTA per (eye, tile), one pixel per thread.  A pixel walks its
+// composite_backward: one CTA per 16 x 16 quadrant of an (eye, tile), one pixel per thread.  A pixel walks its
 // tile's Gaussians back to front from its last contributor (n_contrib), recovering the
 // transmittance before each contributor from the stored final one (T_before = T_after /
 // (1 - alpha)) instead of storing it per Gaussian.  The colour accumulated behind a
@@ -39,12 +39,17 @@ composite_backward_kernel(BackwardParams p, const float *__restrict__ rec, const
   __shared__ uint32_t s_gid[kThreads];
   __shared__ uint32_t s_max[kThreads / 32];
 
-  const int gtile = blockIdx.x;
+  // one CTA per 16 x 16 quadrant of a tile (a 16-pixel tile is one quadrant, a 32-pixel tile
+  // four, each walking the tile's whole list for its own pixels)
+  const int qn = p.tile / kTile;
+  const int gtile = blockIdx.x / (qn * qn);
+  const int quad = blockIdx.x - gtile * qn * qn;
   const int eye = gtile / p.n_tiles;
   const int tile = gtile - eye * p.n_tiles;
   const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  const int px = tx * kTile + (t & 15), py = ty * kTile + (t >> 4);
+  const int px = tx * p.tile + (quad % qn) * kTile + (t & 15);
+  const int py = ty * p.tile + (quad / qn) * kTile + (t >> 4);
   const bool inside = px < p.width && py < p.height;
   // labels of the 2x2 block: top-left 0, bottom-right 1, top-right 2, bottom-left 3
   const int bx = px & 1, by = py & 1;
@@ -482,7 +487,8 @@ cudaError_t launch_backward(const BackwardParams &bp, const PreParams *pre_dev, 
   if (bp.n <= 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(g2d, 0, sizeof(float) * backward_g2d_floats(bp.n_eyes, bp.n), s);
   if (e != cudaSuccess) return e;
-  composite_backward_kernel<<<bp.n_eyes * bp.n_tiles, kThreads, 0, s>>>(
+  const int quads = (bp.tile / kTile) * (bp.tile / kTile);
+  composite_backward_kernel<<<bp.n_eyes * bp.n_tiles * quads, kThreads, 0, s>>>(
       bp, rec, ranges, kept, vals, levels, t_final, n_contrib, dl_drgb, g2d);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -239,7 +239,7 @@ bool scene_fill_view(a3fr_scene *s, FillView *v);
 
 // Backward rasterizer (backward.cu).
 struct BackwardParams {
-  int n_eyes, n, width, height, tiles_x, n_tiles;
+  int n_eyes, n, width, height, tile, tiles_x, n_tiles;
 };
 size_t backward_g2d_floats(int n_eyes, int n);
 cudaError_t launch_backward(const BackwardParams &bp, const PreParams *pre_dev, int sh_degree,

@@ -29,9 +29,9 @@ def _built():
     __graft_entry__.build()
 
 
-def gpu_grads(scene_np, cams, dl, fovea=None, gaze=None):
+def gpu_grads(scene_np, cams, dl, fovea=None, gaze=None, tile=16):
     import torch
-    s = a3fr.Scene.from_numpy(scene_np)
+    s = a3fr.Scene.from_numpy(scene_np, tile=tile)
     for e, c in enumerate(cams):
         s.set_camera(e, c)
     s.keep_aux(True)
@@ -66,11 +66,11 @@ def small_scene(n=64, seed=7):
     return synth.uniform_scene(n, 3, seed=seed, log_scale_mean=-1.8, log_scale_std=0.3)
 
 
-def masked_weights(scene_np, cam, seed, pixels=None):
+def masked_weights(scene_np, cam, seed, pixels=None, tile=16):
     rng = np.random.default_rng(seed)
     npx = cam.width * cam.height if pixels is None else len(pixels)
     w = rng.normal(size=(npx, 3))
-    _, _, info = og.loss(og.params_f64(scene_np), scene_np, cam, 16, np.zeros((npx, 3)), pixels=pixels)
+    _, _, info = og.loss(og.params_f64(scene_np), scene_np, cam, tile, np.zeros((npx, 3)), pixels=pixels)
     w[info["margin"] < 1e-4] = 0.0
     return w
 
@@ -82,6 +82,17 @@ def test_small_scene_matches_oracle_gradient():
     ref = og.gradient(s, cam, 16, w)
     gpu = gpu_grads(s, [cam], w.reshape(1, 32, 32, 3))
     print(compare(gpu, ref))
+
+
+def test_tile32_stereo_foveated_matches_oracle_gradient():
+    """32-pixel tiles: each quadrant of a tile walks the tile's list for its own pixels."""
+    s = synth.uniform_scene(500, 3, seed=23, log_scale_mean=-2.5, log_scale_std=0.4)
+    cams = synth.stereo_cameras(72, 56, yaw_deg=1.0)
+    ws = [masked_weights(s, c, 30 + e, tile=32) for e, c in enumerate(cams)]
+    ref = [og.gradient(s, c, 32, w) for c, w in zip(cams, ws)]
+    tot = {k: ref[0][k] + ref[1][k] for k in NAMES}
+    gpu = gpu_grads(s, cams, np.stack(ws).reshape(2, 56, 72, 3), tile=32)
+    print(compare(gpu, tot))
 
 
 def test_small_scene_matches_central_differences():
