@@ -80,6 +80,11 @@ typedef struct {
   float theta_deg[3];           /* increasing eccentricity boundaries, degrees */
   float dtheta_deg;             /* gaze-tracking error margin of Eq. 1, degrees */
   int32_t level[4];             /* e.g. {4, 2, 1} for three layers */
+  int32_t fill;                 /* skipped pixels (Sec. 3.4 "inherit or interpolate"): 0 inherit the
+                                   block's top-left pixel; 1 interpolate: the mean of the pixel's
+                                   rendered 4-neighbours (up, down, left, right), else of its rendered
+                                   diagonal neighbours, else the top-left pixel (a3fr_render_foveated
+                                   only; rounds inherit) */
 } a3fr_fovea;
 
 typedef struct {

@@ -221,5 +221,31 @@ def render_eye(scene, cam, tile: int, fv: Fovea | None, gaze=None, pixels=None) 
     return img
 
 
+def fill_interpolate(img: np.ndarray, rendered: np.ndarray) -> np.ndarray:
+    """Interpolating fill of a foveated image (Sec. 3.4: skipped pixels "inherit or
+    interpolate"), the reading taken: a skipped pixel becomes the mean of its rendered
+    4-neighbours (summed in the order up, down, left, right), else of its rendered diagonal
+    neighbours (up-left, up-right, down-left, down-right), else keeps the inherited top-left
+    value.  fp32 throughout.  img [H, W, 3] float32, rendered [H, W] bool."""
+    H, W, _ = img.shape
+    out = img.astype(np.float32).copy()
+    for y in range(H):
+        for x in range(W):
+            if rendered[y, x]:
+                continue
+            for nbrs in (((0, -1), (0, 1), (-1, 0), (1, 0)), ((-1, -1), (1, -1), (-1, 1), (1, 1))):
+                acc = np.zeros(3, dtype=np.float32)
+                cnt = 0
+                for dx, dy in nbrs:
+                    xx, yy = x + dx, y + dy
+                    if 0 <= xx < W and 0 <= yy < H and rendered[yy, xx]:
+                        acc = (acc + img[yy, xx]).astype(np.float32)
+                        cnt += 1
+                if cnt:
+                    out[y, x] = (acc / np.float32(cnt)).astype(np.float32)
+                    break
+    return out
+
+
 def num_threads() -> int:
     return int(lib().or_num_threads())

@@ -44,8 +44,12 @@ def _ptr(t) -> int:
     return t.data_ptr()
 
 
-def Fovea(theta_deg=(18.0, 36.0), dtheta_deg: float = 0.0, levels=(4, 2, 1)) -> _lib.Fovea:
-    """Foveation layers (Eq. 1 radii from eccentricity angles; Sec. 3.4 levels)."""
+FILL_INHERIT, FILL_INTERPOLATE = 0, 1
+
+
+def Fovea(theta_deg=(18.0, 36.0), dtheta_deg: float = 0.0, levels=(4, 2, 1),
+          fill: int = FILL_INHERIT) -> _lib.Fovea:
+    """Foveation layers (Eq. 1 radii from eccentricity angles; Sec. 3.4 levels and fill)."""
     f = _lib.Fovea()
     f.n_layers = len(levels)
     for k, t in enumerate(theta_deg):
@@ -53,6 +57,7 @@ def Fovea(theta_deg=(18.0, 36.0), dtheta_deg: float = 0.0, levels=(4, 2, 1)) -> 
     f.dtheta_deg = float(dtheta_deg)
     for k, lv in enumerate(levels):
         f.level[k] = int(lv)
+    f.fill = int(fill)
     return f
 
 

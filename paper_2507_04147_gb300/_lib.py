@@ -38,7 +38,7 @@ class Camera(ctypes.Structure):
 
 class Fovea(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int32), ("theta_deg", ctypes.c_float * 3),
-                ("dtheta_deg", ctypes.c_float), ("level", ctypes.c_int32 * 4)]
+                ("dtheta_deg", ctypes.c_float), ("level", ctypes.c_int32 * 4), ("fill", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -527,7 +527,7 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
 }
 
 // The composite of a render (plan + composite, or composite alone for full resolution).
-int enqueue_comp(a3fr_scene *s, const CompositeParams &cp, int uniform, uint8_t *cur,
+int enqueue_comp(a3fr_scene *s, const CompositeParams &cp, int uniform, uint8_t *cur, bool fill,
                  cudaStream_t stream, uint64_t *launches) {
   const int b = s->sorted_in_alt ? 1 : 0;
   A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
@@ -537,6 +537,10 @@ int enqueue_comp(a3fr_scene *s, const CompositeParams &cp, int uniform, uint8_t 
                               s->keep_aux ? s->n_contrib : nullptr,
                               s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, stream));
   *launches += cp.full ? 1 : 2;
+  if (fill) {
+    A3FR_CHECK(launch_fill(cp, &s->params_dev->comp, s->levels, stream));
+    ++*launches;
+  }
   A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));
   return A3FR_OK;
 }
@@ -575,6 +579,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
     if (fv->n_layers < 1 || fv->n_layers > 4) return A3FR_ERR_INVALID_ARG;
     for (int k = 0; k < fv->n_layers; ++k)
       if (fv->level[k] < 1 || fv->level[k] > 4) return A3FR_ERR_INVALID_ARG;
+    if (fv->fill != 0 && fv->fill != 1) return A3FR_ERR_INVALID_ARG;
     if (mode == Mode::kFoveated && s->gaze_seq < 0) return A3FR_ERR_NOT_READY;
   }
   int rc = ensure_frame_buffers(s, eyes, c0.width, c0.height);
@@ -623,22 +628,23 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
     A3FR_CHECK(cudaMemsetAsync(s->round_state, 0, sizeof(RoundState), stream));
     post_mailbox(s, 0, nullptr, eyes);
   }
+  const bool fill = mode == Mode::kFoveated && fv->fill == 1;
   if (graphs) {
-    const uint64_t key = s->alloc_gen * 4 + (s->keep_aux ? 2 : 0) + (uint64_t)eyes;
+    const uint64_t key = s->alloc_gen * 8 + (fill ? 4 : 0) + (s->keep_aux ? 2 : 0) + (uint64_t)eyes;
     cudaGraphExec_t *g = mode == Mode::kFull ? &s->g_full : &s->g_fov;
     uint64_t *gk = mode == Mode::kFull ? &s->g_full_key : &s->g_fov_key;
     if (!*g || *gk != key) {
       uint64_t k = 0;
       rc = capture(s, g, &k, [&](cudaStream_t cs, uint64_t *l) {
-        return enqueue_comp(s, hp.comp, 0, nullptr, cs, l);
+        return enqueue_comp(s, hp.comp, 0, nullptr, fill, cs, l);
       });
       if (rc != A3FR_OK) return rc;
       *gk = key;
     }
     A3FR_CHECK(cudaGraphLaunch(*g, stream));
-    launches += mode == Mode::kFull ? 1 : 2;
+    launches += (mode == Mode::kFull ? 1 : 2) + (fill ? 1 : 0);
   } else {
-    rc = enqueue_comp(s, hp.comp, uniform, cur, stream, &launches);
+    rc = enqueue_comp(s, hp.comp, uniform, cur, fill, stream, &launches);
     if (rc != A3FR_OK) return rc;
   }
   if (mode == Mode::kFoveated) {

@@ -177,6 +177,10 @@ struct RoundPlan {
   int pad[3];
 };
 
+// Interpolating fill of the skipped pixels of a foveated render (after the composite).
+cudaError_t launch_fill(const CompositeParams &p, const CompositeParams *p_dev, const uint8_t *levels,
+                        cudaStream_t s);
+
 // Bytes of the work plan of launch_composite for n_ranges = n_eyes * n_tiles.
 size_t plan_bytes(int n_ranges);
 // One composite launch (plan kernel + composite).  p.full: every tile at level 4, no plan.

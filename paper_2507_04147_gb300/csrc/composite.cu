@@ -562,9 +562,67 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
   }
 }
 
+
+// Interpolating fill of a foveated render (Sec. 3.4, "inherit or interpolate"): every pixel its
+// tile's level skipped becomes the mean of its rendered 4-neighbours (summed up, down, left,
+// right), else of its rendered diagonal neighbours (up-left, up-right, down-left, down-right),
+// else keeps the inherited top-left value.  Reads only rendered pixels and writes only skipped
+// ones, so the pixels of one launch never race.
+__device__ __forceinline__ bool rendered_px(const CompositeParams &p, const uint8_t *levels, int e, int x,
+                                            int y) {
+  if (x < 0 || y < 0 || x >= p.width || y >= p.height) return false;
+  const int bx = x & 1, by = y & 1;
+  const int lab = bx == by ? (bx ? 1 : 0) : (bx ? 2 : 3);
+  return lab < levels[e * p.n_tiles + (y / p.tile) * p.tiles_x + x / p.tile];
+}
+
+__global__ void __launch_bounds__(256)
+fill_kernel(const CompositeParams *__restrict__ pp, const uint8_t *__restrict__ levels) {
+  const CompositeParams &p = *pp;
+  float *out = p.out;
+  const size_t total = (size_t)p.n_eyes * p.height * p.width;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % p.width);
+    const size_t r = i / p.width;
+    const int y = (int)(r % p.height), e = (int)(r / p.height);
+    if (rendered_px(p, levels, e, x, y)) continue;
+    const int nb[2][4][2] = {{{0, -1}, {0, 1}, {-1, 0}, {1, 0}}, {{-1, -1}, {1, -1}, {-1, 1}, {1, 1}}};
+    for (int ring = 0; ring < 2; ++ring) {
+      float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+      int cnt = 0;
+      for (int k = 0; k < 4; ++k) {
+        const int xx = x + nb[ring][k][0], yy = y + nb[ring][k][1];
+        if (!rendered_px(p, levels, e, xx, yy)) continue;
+        const float *q = out + (((size_t)e * p.height + yy) * p.width + xx) * 3;
+        a0 = __fadd_rn(a0, q[0]);
+        a1 = __fadd_rn(a1, q[1]);
+        a2 = __fadd_rn(a2, q[2]);
+        ++cnt;
+      }
+      if (cnt) {
+        const float c = (float)cnt;
+        out[3 * i] = __fdiv_rn(a0, c);
+        out[3 * i + 1] = __fdiv_rn(a1, c);
+        out[3 * i + 2] = __fdiv_rn(a2, c);
+        break;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 size_t plan_bytes(int n_ranges) { return sizeof(uint32_t) * (4 * (size_t)n_ranges + 4); }
+
+cudaError_t launch_fill(const CompositeParams &p, const CompositeParams *p_dev, const uint8_t *levels,
+                        cudaStream_t s) {
+  const size_t total = (size_t)p.n_eyes * p.height * p.width;
+  if (total == 0) return cudaSuccess;
+  const size_t want = (total + 255) / 256;
+  const int grid = (int)(want < 152 * 16 ? want : 152 * 16);
+  fill_kernel<<<grid, 256, 0, s>>>(p_dev, levels);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_dev,
                              const float *rec, int n, const uint2 *ranges, const uint32_t *kept,

@@ -260,3 +260,32 @@ def test_autotune_picks_a_configuration_and_renders_it():
     if res["tile"] == 16:
         assert torch.equal(img, ref)
     s.close()
+
+
+@pytest.mark.parametrize("tile", [16, 32])
+def test_interpolating_fill(tile):
+    """Skipped pixels interpolated from rendered neighbours: bit-equal to the oracle's rule
+    applied to the GPU's rendered pixels, rendered pixels unchanged, and within the pixel
+    tolerance of the oracle's own filled image."""
+    scene = synth.uniform_scene(6000, 3, seed=3)
+    cams = synth.stereo_cameras(200, 136, yaw_deg=3.0)
+    gaze = np.array([[60.0, 70.0], [58.5, 70.0]], np.float32)
+    ofv = oracle.fovea((18.0, 36.0), 0.0, (4, 2, 1))
+    inh = gh.run(scene, cams, gaze=gaze, fovea=a3fr.Fovea((18.0, 36.0), 0.0, (4, 2, 1)), tile=tile)
+    itp = gh.run(scene, cams, gaze=gaze, tile=tile,
+                 fovea=a3fr.Fovea((18.0, 36.0), 0.0, (4, 2, 1), fill=a3fr.FILL_INTERPOLATE))
+    for e in range(2):
+        lv = oracle.level_map(cams[e], tile, ofv, gaze[e])
+        ref = oracle.render(*oracle.preprocess(scene, cams[e], tile)[:2], cams[e], tile, level=lv)
+        live = ref.rendered.reshape(136, 200).astype(bool)
+        assert np.array_equal(itp["img"][e][live], inh["img"][e][live])
+        exact = oracle.fill_interpolate(inh["img"][e], live)
+        assert np.array_equal(itp["img"][e], exact)
+        filled_ref = oracle.fill_interpolate(ref.rgb.reshape(136, 200, 3), live)
+        ok = np.ones((136, 200), bool)
+        bad = (ref.margin < gh.DELTA).reshape(136, 200)
+        # a filled pixel inherits the exemption of any neighbour it averages
+        ok &= ~(bad | np.roll(bad, 1, 0) | np.roll(bad, -1, 0) | np.roll(bad, 1, 1) | np.roll(bad, -1, 1)
+                | np.roll(np.roll(bad, 1, 0), 1, 1) | np.roll(np.roll(bad, 1, 0), -1, 1)
+                | np.roll(np.roll(bad, -1, 0), 1, 1) | np.roll(np.roll(bad, -1, 0), -1, 1))
+        assert np.abs(itp["img"][e] - filled_ref).max(axis=-1)[ok].max() <= gh.TOL

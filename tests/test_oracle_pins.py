@@ -440,3 +440,38 @@ def test_pixel_list_mode_matches_full_image():
     flat = pix[:, 1] * 256 + pix[:, 0]
     assert np.array_equal(part.rgb, full.rgb[flat])
     assert np.array_equal(part.rendered, full.rendered[flat])
+
+
+def test_interpolating_fill_reproduces_a_linear_ramp():
+    """A linear image sampled on the rendered pixels is reproduced exactly (up to fp32
+    rounding) at interior skipped pixels: the mean of two or four symmetric neighbours of a
+    linear function is its value at the centre."""
+    H, W = 12, 16
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float32)
+    ramp = np.stack([0.01 * xs + 0.02 * ys, 0.5 - 0.01 * xs, 0.03 * ys], -1).astype(np.float32)
+    lab = np.where((xs % 2) == (ys % 2), np.where(xs % 2 == 0, 1, 2), np.where(xs % 2 == 1, 3, 4))
+    for level in (1, 2, 3):
+        rendered = lab <= level
+        img = ramp.copy()
+        img[~rendered] = 0.0                      # whatever the skipped pixels held
+        out = oracle.fill_interpolate(img, rendered)
+        assert np.array_equal(out[rendered], ramp[rendered])
+        interior = ~rendered
+        interior[0, :] = interior[-1, :] = False
+        interior[:, 0] = interior[:, -1] = False
+        np.testing.assert_allclose(out[interior], ramp[interior], atol=2e-6)
+
+
+def test_interpolating_fill_edge_rules():
+    """Neighbours outside the image or skipped do not count; a pixel without rendered
+    4-neighbours uses its rendered diagonals; with none, it keeps its value."""
+    img = np.zeros((3, 3, 3), np.float32)
+    rendered = np.zeros((3, 3), bool)
+    img[0, 0] = 1.0
+    img[2, 2] = 3.0
+    rendered[0, 0] = rendered[2, 2] = True
+    out = oracle.fill_interpolate(img, rendered)
+    np.testing.assert_array_equal(out[1, 1], np.float32(2.0))     # diagonals (0,0) and (2,2)
+    np.testing.assert_array_equal(out[0, 1], np.float32(1.0))     # left neighbour only
+    img2 = np.full((1, 1, 3), 7.0, np.float32)
+    np.testing.assert_array_equal(oracle.fill_interpolate(img2, np.zeros((1, 1), bool)), img2)
