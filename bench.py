@@ -643,8 +643,10 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
     cams0 = w.cameras(0)
     eyes, H, W = len(cams0), cams0[0].height, cams0[0].width
     out = torch.empty((eyes, H, W, 3), device=device)
-    stats = {"inherit": [], "learned": []}
-    t_render, t_fill, t_full = [], [], []
+    fv_itp = a3fr.Fovea(w.theta_deg, 0.0, (4, 2, 1), fill=a3fr.FILL_INTERPOLATE)
+    itp_out = torch.empty_like(out)
+    stats = {"inherit": [], "interpolate": [], "learned": []}
+    t_render, t_fill, t_full, t_itp = [], [], [], []
     ev = lambda: torch.cuda.Event(enable_timing=True)
     for k, f in enumerate(np.linspace(0, 239, eval_frames).astype(int)):
         for e, c in enumerate(w.cameras(f)):
@@ -661,6 +663,10 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
             net.fill(scene, out, stream=render_stream)
             c_.record(render_stream)
             levels = scene.buffer(a3fr.BUF_LEVELS, torch.uint8, stream=render_stream)
+            i0, i1 = ev(), ev()
+            i0.record(render_stream)
+            scene.render_foveated(fv_itp, out=itp_out, stream=render_stream)
+            i1.record(render_stream)
             f0, f1 = ev(), ev()
             f0.record(render_stream)
             full = scene.render_full(stream=render_stream)
@@ -670,9 +676,10 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
             t_render.append(a.elapsed_time(b))
             t_fill.append(b2.elapsed_time(c_))
             t_full.append(f0.elapsed_time(f1))
+            t_itp.append(i0.elapsed_time(i1))
         ty, tx = (H + 15) // 16, (W + 15) // 16
         per = (levels.reshape(eyes, ty, tx) == 1).repeat_interleave(16, 1).repeat_interleave(16, 2)[:, :H, :W]
-        for name, img in (("inherit", inherit), ("learned", out)):
+        for name, img in (("inherit", inherit), ("interpolate", itp_out), ("learned", out)):
             stats[name].append((periphery.psnr(img, full, per), periphery.psnr(img, full),
                                 periphery.ssim(img, full)))
     scene.close()
@@ -681,11 +688,12 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
                        % (steps, batch, crop, crop, w.name, eval_frames),
            "train_s": train_s, "train_loss_first_last": [losses[0], losses[-1]],
            "crops": steps * batch}
-    for name in ("inherit", "learned"):
+    for name in ("inherit", "interpolate", "learned"):
         arr = np.array(stats[name])
         res[name] = {"psnr_periphery_db": float(arr[:, 0].mean()), "psnr_whole_db": float(arr[:, 1].mean()),
                      "ssim_whole": float(arr[:, 2].mean())}
     res["latency_ms"] = {"foveated_render_aux_p50": float(np.percentile(t_render, 50)),
+                         "foveated_render_interpolate_p50": float(np.percentile(t_itp, 50)),
                          "learned_fill_p50": float(np.percentile(t_fill, 50)),
                          "full_render_p50": float(np.percentile(t_full, 50))}
     return res

@@ -85,6 +85,12 @@ typedef struct {
                                    rendered 4-neighbours (up, down, left, right), else of its rendered
                                    diagonal neighbours, else the top-left pixel (a3fr_render_foveated
                                    only; rounds inherit) */
+  float count_frac;             /* tile levels by Gaussian count (Sec. 3.6, 4.6: tiles sorted by their
+                                   number of Gaussians, resolution adjusted): per eye, the
+                                   floor(count_frac * tiles) tiles with the most instances (every tile
+                                   whose count is >= the k-th largest) drop one level if their level is
+                                   2 or 3; 0 = off; in [0, 1].  a3fr_render_foveated only
+                                   (the rounds API ignores it). */
 } a3fr_fovea;
 
 typedef struct {

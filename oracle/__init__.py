@@ -19,6 +19,8 @@ Parity status of each part (pins are the ``-m "not gpu"`` tests in ``tests/``):
     form, weight-sum and white-colour invariants, input-order invariance, fp64 brute force)
   * foveation level map, live mask, fill             -- pinned (brute-force geometry,
     closed-form disc count)
+  * count-based tile levels                          -- pinned (hand-counted cases, ties,
+    the k = 0 and k = tiles limits)
   * absolute agreement with the paper's own renderer and its second-layer angle
                                                      -- parity unpinned (the paper prints
     no rendered values and names no second-layer angle)
@@ -170,6 +172,24 @@ def level_map(cam, tile: int, fv: Fovea, gaze):
     out = np.zeros(tiles(cam.width, tile) * tiles(cam.height, tile), dtype=np.uint8)
     lib().or_level_map(ctypes.byref(c), tile, ctypes.byref(fv), _p(g), _p(out))
     return out
+
+
+def count_levels(level, ranges, count_frac: float):
+    """Tile levels by Gaussian count (Sec. 3.6 and 4.6: tiles ordered by how many Gaussians
+    they hold, the resolution of the heaviest lowered), the reading taken: with k =
+    floor(count_frac * tiles) computed in fp32, tau is the k-th largest instance count of
+    the eye's tiles; a tile whose level is 2 or 3 and whose count c satisfies c > 0 and
+    c >= tau renders one level lower.  Foveal tiles (level 4) and level 1 keep their level.
+    level [tiles] uint8 (one eye), ranges [tiles, 2] uint32; returns a new level array."""
+    level = np.array(level, dtype=np.uint8)
+    counts = ranges[:, 1].astype(np.int64) - ranges[:, 0].astype(np.int64)
+    k = int(np.floor(np.float32(count_frac) * np.float32(len(counts))))
+    if k < 1:
+        return level
+    tau = np.sort(counts)[::-1][min(k, len(counts)) - 1]
+    heavy = (counts > 0) & (counts >= tau) & ((level == 2) | (level == 3))
+    level[heavy] -= 1
+    return level
 
 
 class Image:

@@ -48,8 +48,9 @@ FILL_INHERIT, FILL_INTERPOLATE = 0, 1
 
 
 def Fovea(theta_deg=(18.0, 36.0), dtheta_deg: float = 0.0, levels=(4, 2, 1),
-          fill: int = FILL_INHERIT) -> _lib.Fovea:
-    """Foveation layers (Eq. 1 radii from eccentricity angles; Sec. 3.4 levels and fill)."""
+          fill: int = FILL_INHERIT, count_frac: float = 0.0) -> _lib.Fovea:
+    """Foveation layers (Eq. 1 radii from eccentricity angles; Sec. 3.4 levels and fill;
+    Sec. 3.6 count-based tile levels when count_frac > 0)."""
     f = _lib.Fovea()
     f.n_layers = len(levels)
     for k, t in enumerate(theta_deg):
@@ -58,6 +59,7 @@ def Fovea(theta_deg=(18.0, 36.0), dtheta_deg: float = 0.0, levels=(4, 2, 1),
     for k, lv in enumerate(levels):
         f.level[k] = int(lv)
     f.fill = int(fill)
+    f.count_frac = float(count_frac)
     return f
 
 

@@ -38,7 +38,8 @@ class Camera(ctypes.Structure):
 
 class Fovea(ctypes.Structure):
     _fields_ = [("n_layers", ctypes.c_int32), ("theta_deg", ctypes.c_float * 3),
-                ("dtheta_deg", ctypes.c_float), ("level", ctypes.c_int32 * 4), ("fill", ctypes.c_int32)]
+                ("dtheta_deg", ctypes.c_float), ("level", ctypes.c_int32 * 4), ("fill", ctypes.c_int32),
+                ("count_frac", ctypes.c_float)]
 
 
 class Stats(ctypes.Structure):

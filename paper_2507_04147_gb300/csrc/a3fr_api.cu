@@ -77,9 +77,10 @@ struct a3fr_scene {
   void *frame_ws = nullptr;
   size_t frame_ws_bytes = 0;
   uint32_t *counts = nullptr;                // [0] kept, [1..2] per eye, [3] total, [4] entries
-  // persistent device state: status | counters[2]
+  // persistent device state: status | counters[2] | thresholds[2]
   uint32_t *status = nullptr;
   unsigned long long *counters = nullptr;
+  uint32_t *thresholds = nullptr;            // per-eye heavy-tile count thresholds
   void *small = nullptr;
   // gaze mailbox ring
   float *gaze_dev = nullptr;
@@ -352,6 +353,7 @@ CompositeParams composite_params(const a3fr_scene *s, int eyes, const a3fr_fovea
   if (fv) {
     cp.n_layers = fv->n_layers;
     for (int k = 0; k < 4; ++k) cp.level[k] = fv->level[k];
+    cp.count_frac = fv->count_frac;
     for (int e = 0; e < eyes; ++e)
       for (int k = 0; k < 3; ++k)
         cp.r2[e][k] = layer_radius2(s->cams[e].fx, fv->theta_deg[k], fv->dtheta_deg);
@@ -535,7 +537,7 @@ int enqueue_comp(a3fr_scene *s, const CompositeParams &cp, int uniform, uint8_t 
                               s->tvals[b], s->gaze_dev, nullptr, uniform, cur, s->plan, s->levels,
                               s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr,
-                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, stream));
+                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, s->thresholds, stream));
   *launches += cp.full ? 1 : 2;
   if (fill) {
     A3FR_CHECK(launch_fill(cp, &s->params_dev->comp, s->levels, stream));
@@ -580,6 +582,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
     for (int k = 0; k < fv->n_layers; ++k)
       if (fv->level[k] < 1 || fv->level[k] > 4) return A3FR_ERR_INVALID_ARG;
     if (fv->fill != 0 && fv->fill != 1) return A3FR_ERR_INVALID_ARG;
+    if (!(fv->count_frac >= 0.0f && fv->count_frac <= 1.0f)) return A3FR_ERR_INVALID_ARG;
     if (mode == Mode::kFoveated && s->gaze_seq < 0) return A3FR_ERR_NOT_READY;
   }
   int rc = ensure_frame_buffers(s, eyes, c0.width, c0.height);
@@ -630,7 +633,9 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
   }
   const bool fill = mode == Mode::kFoveated && fv->fill == 1;
   if (graphs) {
-    const uint64_t key = s->alloc_gen * 8 + (fill ? 4 : 0) + (s->keep_aux ? 2 : 0) + (uint64_t)eyes;
+    const bool by_count = mode == Mode::kFoveated && fv->count_frac > 0.0f;
+    const uint64_t key = s->alloc_gen * 16 + (by_count ? 8 : 0) + (fill ? 4 : 0) + (s->keep_aux ? 2 : 0) +
+                         (uint64_t)eyes;
     cudaGraphExec_t *g = mode == Mode::kFull ? &s->g_full : &s->g_fov;
     uint64_t *gk = mode == Mode::kFull ? &s->g_full_key : &s->g_fov_key;
     if (!*g || *gk != key) {
@@ -683,7 +688,7 @@ int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
                               s->counts, s->tvals[b], s->gaze_dev, s->round_plan, 0, s->cur_level,
                               s->plan, s->levels, s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr,
-                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, stream));
+                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, s->thresholds, stream));
   rc = finish_render(s, stream);
   if (rc != A3FR_OK) return rc;
   s->launches += 3;
@@ -741,6 +746,7 @@ int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3f
   unsigned char *sm = static_cast<unsigned char *>(s->small);
   s->status = reinterpret_cast<uint32_t *>(sm + 16);
   s->counters = reinterpret_cast<unsigned long long *>(sm + 32);
+  s->thresholds = reinterpret_cast<uint32_t *>(sm + 64);
   if ((e = cudaMemset(s->small, 0, 256)) != cudaSuccess) return fail(cuda_fail(e, "cudaMemset"));
   if ((e = cudaMalloc(&s->gaze_dev, sizeof(float) * 4 * kSlots)) != cudaSuccess)
     return fail(cuda_fail(e, "cudaMalloc(gaze)"));

@@ -160,6 +160,7 @@ struct CompositeParams {
   float r2[kMaxEyes][3];    // squared layer radii per eye
   int gaze_slot;            // mailbox-ring slot of the gaze (foveated renders)
   float *out;               // output image [eyes][H][W][3]
+  float count_frac;         // count-based tile levels: fraction of heavy tiles per eye (0 = off)
 };
 
 // Per-render parameters, resident in device memory so that captured graphs stay valid: one
@@ -195,7 +196,8 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
                              const uint32_t *vals, const float *gaze, const RoundPlan *round,
                              int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, float *depth,
-                             unsigned long long *counters, int batch_mult, cudaStream_t s);
+                             unsigned long long *counters, int batch_mult, uint32_t *thresholds,
+                             cudaStream_t s);
 
 // Incremental rounds (Sec. 3.3, Alg. 1): state on the device, mailbox in mapped host memory.
 struct RoundConfig {

@@ -45,6 +45,56 @@ __device__ __forceinline__ int tile_level(const CompositeParams &p, int eye, int
   return p.level[layer];
 }
 
+// Count-based tile levels (Sec. 3.6, 4.6): per eye, the instance count tau of the k-th
+// heaviest tile, k = floor(count_frac * tiles), by an exact radix select (four 8-bit digits,
+// most significant first) over the tiles' range lengths in one CTA; tau = UINT32_MAX when
+// k < 1 (no tile is heavy).
+__global__ void __launch_bounds__(1024)
+tile_threshold_kernel(const CompositeParams *__restrict__ pp, const uint2 *__restrict__ ranges,
+                      uint32_t *__restrict__ thresholds) {
+  const CompositeParams &p = *pp;
+  __shared__ uint32_t s_hist[256];
+  __shared__ uint32_t s_prefix, s_k;
+  const int t = threadIdx.x;
+  for (int e = 0; e < p.n_eyes; ++e) {
+    const uint32_t k0 = (uint32_t)floorf(p.count_frac * (float)p.n_tiles);
+    if (k0 < 1u) {
+      if (t == 0) thresholds[e] = 0xffffffffu;
+      continue;
+    }
+    if (t == 0) {
+      s_prefix = 0u;
+      s_k = min(k0, (uint32_t)p.n_tiles);
+    }
+    __syncthreads();
+    for (int shift = 24; shift >= 0; shift -= 8) {
+      for (int i = t; i < 256; i += blockDim.x) s_hist[i] = 0u;
+      __syncthreads();
+      const uint32_t prefix = s_prefix;
+      for (int i = t; i < p.n_tiles; i += blockDim.x) {
+        const uint2 r = ranges[e * p.n_tiles + i];
+        const uint32_t c = r.y - r.x;
+        const bool match = shift == 24 || (c >> (shift + 8)) == prefix;
+        if (match) atomicAdd(&s_hist[(c >> shift) & 255u], 1u);
+      }
+      __syncthreads();
+      if (t == 0) {
+        uint32_t k = s_k;
+        int d = 255;
+        for (; d > 0; --d) {
+          if (s_hist[d] >= k) break;
+          k -= s_hist[d];
+        }
+        s_k = k;
+        s_prefix = (prefix << 8) | (uint32_t)d;
+      }
+      __syncthreads();
+    }
+    if (t == 0) thresholds[e] = s_prefix;
+    __syncthreads();
+  }
+}
+
 // Work plan of one composite launch.  Each tile gets a label interval (lo, hi] to render;
 // entries (tile << 2 | lo) are bucketed by hi - lo in plan[(hi - lo - 1) * n_ranges + slot]
 // with the bucket sizes in plan_counts[0..3].  Three uses:
@@ -56,7 +106,8 @@ __global__ void __launch_bounds__(256)
 plan_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ gaze_ring,
             const RoundPlan *__restrict__ round, int uniform, uint8_t *__restrict__ cur,
             uint8_t *__restrict__ levels, uint32_t *__restrict__ plan,
-            uint32_t *__restrict__ plan_counts) {
+            uint32_t *__restrict__ plan_counts, const uint2 *__restrict__ ranges,
+            const uint32_t *__restrict__ thresholds) {
   const CompositeParams &p = *pp;
   const float *gaze = gaze_ring + 4 * p.gaze_slot;
   const int n_ranges = p.n_eyes * p.n_tiles;
@@ -79,6 +130,12 @@ plan_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ ga
       lo = cur[gt];
     } else {
       hi = tile_level(p, eye, tile, gaze);
+      if (p.count_frac > 0.0f && (hi == 2 || hi == 3)) {
+        // a heavy tile (count >= the k-th largest count of its eye) drops one level
+        const uint2 r = ranges[gt];
+        const uint32_t c = r.y - r.x;
+        if (c > 0u && c >= thresholds[eye]) hi -= 1;
+      }
     }
     count = hi > lo ? hi - lo : 0;
     if (cur != nullptr && hi > lo) cur[gt] = (uint8_t)hi;
@@ -629,15 +686,22 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
                              const uint32_t *vals, const float *gaze, const RoundPlan *round,
                              int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, float *depth,
-                             unsigned long long *counters, int batch_mult, cudaStream_t s) {
+                             unsigned long long *counters, int batch_mult, uint32_t *thresholds,
+                             cudaStream_t s) {
   const int n_ranges = p.n_eyes * p.n_tiles;
   if (n_ranges <= 0) return cudaSuccess;
   uint32_t *pc = plan + 4 * (size_t)n_ranges;
   if (!p.full) {
     cudaError_t e = cudaMemsetAsync(pc, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
+    const bool by_count = p.count_frac > 0.0f && round == nullptr && uniform == 0;
+    if (by_count) {
+      tile_threshold_kernel<<<1, 1024, 0, s>>>(p_dev, ranges, thresholds);
+      e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+    }
     plan_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p_dev, gaze, round, uniform, cur, levels,
-                                                       plan, pc);
+                                                       plan, pc, ranges, thresholds);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -23,7 +23,8 @@ def _built():
     __graft_entry__.build()
 
 
-def check_eye(r, e, scene_np, cam, tile=16, gaze=None, fv=None, full=False, pixels=None):
+def check_eye(r, e, scene_np, cam, tile=16, gaze=None, fv=None, full=False, pixels=None,
+              count_frac=0.0):
     n = scene_np.n
     rec, rect, touched, keys, vals = gh.oracle_eye(scene_np, cam, tile)
     assert np.array_equal(r["rec"][e].view(np.uint32), rec.view(np.uint32)), "records differ"
@@ -43,7 +44,7 @@ def check_eye(r, e, scene_np, cam, tile=16, gaze=None, fv=None, full=False, pixe
         level = None
         assert np.all(r["levels"][e * n_tiles:(e + 1) * n_tiles] == 4)
     else:
-        level = oracle.level_map(cam, tile, fv, gaze)
+        level = oracle.count_levels(oracle.level_map(cam, tile, fv, gaze), ranges, count_frac)
         assert np.array_equal(r["levels"][e * n_tiles:(e + 1) * n_tiles], level), "levels differ"
     ref = oracle.render(rec, rect, cam, tile, level=level, pixels=pixels)
     img = r["img"][e]
@@ -289,3 +290,33 @@ def test_interpolating_fill(tile):
                 | np.roll(np.roll(bad, 1, 0), 1, 1) | np.roll(np.roll(bad, 1, 0), -1, 1)
                 | np.roll(np.roll(bad, -1, 0), 1, 1) | np.roll(np.roll(bad, -1, 0), -1, 1))
         assert np.abs(itp["img"][e] - filled_ref).max(axis=-1)[ok].max() <= gh.TOL
+
+
+@pytest.mark.parametrize("tile", [16, 32])
+@pytest.mark.parametrize("count_frac", [0.2, 1.0])
+def test_count_based_tile_levels(tile, count_frac):
+    """Tile levels by Gaussian count: levels bit-equal to the oracle's rule over the oracle's
+    own tile ranges, pixels within the parity bar; the rule changes some tiles, and the
+    scene's cached graphs keep count-based and plain renders apart."""
+    import torch
+    scene = synth.uniform_scene(6000, 3, seed=3)
+    cams = synth.stereo_cameras(200, 136, yaw_deg=3.0)
+    gaze = np.array([[60.0, 70.0], [58.5, 70.0]], np.float32)
+    ofv = oracle.fovea((18.0, 36.0), 0.0, (4, 3, 2))
+    gfv = a3fr.Fovea((18.0, 36.0), 0.0, (4, 3, 2), count_frac=count_frac)
+    r = gh.run(scene, cams, gaze=gaze, fovea=gfv, tile=tile)
+    assert r["stats"]["status"] == 0
+    n_tiles = oracle.tiles(200, tile) * oracle.tiles(136, tile)
+    changed = 0
+    for e in range(2):
+        print(e, check_eye(r, e, scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv, count_frac=count_frac))
+        plain = oracle.level_map(cams[e], tile, ofv, gaze[e])
+        changed += int((r["levels"][e * n_tiles:(e + 1) * n_tiles] != plain).sum())
+    assert changed > 0
+    s = r["scene"]
+    for frac in (0.0, count_frac, 0.0):
+        s.render_foveated(a3fr.Fovea((18.0, 36.0), 0.0, (4, 3, 2), count_frac=frac))
+        torch.cuda.synchronize()
+        lv = s.buffer(a3fr.BUF_LEVELS, torch.uint8).cpu().numpy()
+        assert np.array_equal(lv, r["levels"]) == (frac == count_frac)
+    s.close()

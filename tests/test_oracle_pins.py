@@ -475,3 +475,40 @@ def test_interpolating_fill_edge_rules():
     np.testing.assert_array_equal(out[0, 1], np.float32(1.0))     # left neighbour only
     img2 = np.full((1, 1, 3), 7.0, np.float32)
     np.testing.assert_array_equal(oracle.fill_interpolate(img2, np.zeros((1, 1), bool)), img2)
+
+
+def _ranges_of(counts):
+    ends = np.cumsum(counts).astype(np.uint32)
+    return np.stack([ends - np.asarray(counts, np.uint32), ends], axis=1)
+
+
+def test_count_levels_hand_counted():
+    """Count-based tile levels (Sec. 3.6 / 4.6 reading): the k = floor(frac * tiles) heaviest
+    tiles at level 2 or 3 drop one level; hand-counted expectations."""
+    counts = [5, 0, 9, 9, 3, 7, 1, 0]
+    level = np.array([2, 2, 3, 2, 4, 1, 3, 2], np.uint8)
+    r = _ranges_of(counts)
+    cases = {
+        0.0: [2, 2, 3, 2, 4, 1, 3, 2],     # off
+        0.1: [2, 2, 3, 2, 4, 1, 3, 2],     # k = 0
+        0.25: [2, 2, 2, 1, 4, 1, 3, 2],    # k = 2: tau = 9, both 9s drop
+        0.375: [2, 2, 2, 1, 4, 1, 3, 2],   # k = 3: tau = 7 hits a level-1 tile (kept)
+        0.5: [1, 2, 2, 1, 4, 1, 3, 2],     # k = 4: tau = 5
+        1.0: [1, 2, 2, 1, 4, 1, 2, 2],     # k = tiles: every non-empty tile, empty ones kept
+    }
+    for frac, want in cases.items():
+        got = oracle.count_levels(level, r, frac)
+        assert got.tolist() == want, (frac, got)
+    assert level.tolist() == [2, 2, 3, 2, 4, 1, 3, 2]      # input untouched
+
+
+def test_count_levels_ties_and_fp32_k():
+    """Ties at tau are all heavy (more than k tiles may drop); k is taken in fp32 like the
+    kernel: 0.7f * 10 rounds to 7.0f, where the same fp32 fraction multiplied in fp64 gives
+    6.9999999 and k = 6."""
+    r = _ranges_of([4, 4, 4, 1])
+    assert oracle.count_levels(np.full(4, 3, np.uint8), r, 0.25).tolist() == [2, 2, 2, 3]
+    counts = list(range(10, 0, -1))                      # 10, 9, ..., 1
+    got = oracle.count_levels(np.full(10, 2, np.uint8), _ranges_of(counts), 0.7)
+    assert got.tolist() == [1] * 7 + [2] * 3
+    assert int(np.floor(float(np.float32(0.7)) * 10)) == 6   # the fp64 product would keep 6
