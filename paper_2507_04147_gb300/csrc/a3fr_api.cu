@@ -61,7 +61,7 @@ struct a3fr_scene {
   uint32_t *dkeys[2] = {nullptr, nullptr};   // depth-sort keys (ping-pong)
   uint32_t *dvals[2] = {nullptr, nullptr};   // depth-sorted entries e * n + i
   uint2 *ranges = nullptr;
-  uint32_t *tile_partials = nullptr;         // per-CTA 2-D difference grids of tile_count
+  uint32_t *bin_h = nullptr;                 // per-chunk tile counts, then starts (binning.cu)
   uint32_t *plan = nullptr;                  // tiles bucketed by level (foveated composite)
   uint8_t *levels = nullptr;
   float *t_final = nullptr;
@@ -70,9 +70,7 @@ struct a3fr_scene {
   // instance workspace
   size_t capacity = 0;
   bool auto_capacity = false;
-  uint32_t *tkeys[2] = {nullptr, nullptr};   // tile index of each instance (ping-pong)
-  uint32_t *tvals[2] = {nullptr, nullptr};   // Gaussian index of each instance
-  bool sorted_in_alt = false;
+  uint32_t *vals = nullptr;                  // Gaussian index of each instance, by tile
   // per-frame scratch, zeroed at the start of every render (see frame_layout)
   void *frame_ws = nullptr;
   size_t frame_ws_bytes = 0;
@@ -147,31 +145,23 @@ int n_eyes_of(const a3fr_scene *s) { return s->cam_set[1] ? 2 : (s->cam_set[0] ?
 
 constexpr int kDepthPasses = 4;   // 32-bit depth keys, 8-bit digits
 
-int tile_bits_for(int n_ranges) {
-  int bits = 1;
-  while ((1ll << bits) < (long long)n_ranges) ++bits;
-  return bits;
-}
 
 // Byte offsets inside frame_ws; everything in it starts at zero every render.
 struct FrameLayout {
-  size_t counts = 0;                 // 8 x u32: counts[0..4], emit block counter at [6]
+  size_t counts = 0;                 // counts[0..7] u32, [8..9] the u64 instance total
   size_t depth_hist = 64;            // kMaxSortPasses x 256 u32
   size_t depth_ctr = 64 + 8192;      // kMaxSortPasses u32 (+pad)
-  size_t tile_hist = 64 + 8192 + 64;
-  size_t tile_ctr = 64 + 8192 + 64 + 8192;
-  size_t emit_lb = 64 + 8192 + 64 + 8192 + 64;
-  size_t tile_diff = 0, depth_lb = 0, tile_lb = 0, total = 0;
+  size_t depth_lb = 0, bin_lb = 0, plan_lb = 0, bounds = 0, total = 0;
 };
 
-FrameLayout frame_layout(size_t entries, size_t capacity, int tile_passes, int eyes, int tiles_x,
-                         int tiles_y) {
+FrameLayout frame_layout(size_t entries, int eyes, int n_tiles) {
   FrameLayout L;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  L.tile_diff = up(L.emit_lb + emit_lookback_bytes((int)entries));
-  L.depth_lb = up(L.tile_diff + sizeof(uint32_t) * (size_t)eyes * (tiles_x + 1) * (tiles_y + 1));
-  L.tile_lb = up(L.depth_lb + onesweep_lookback_bytes(entries, kDepthPasses, false, false));
-  L.total = up(L.tile_lb + onesweep_lookback_bytes(capacity, tile_passes, false, false));
+  L.depth_lb = up(L.depth_ctr + 64);
+  L.bin_lb = up(L.depth_lb + onesweep_lookback_bytes(entries, kDepthPasses, false, false));
+  L.plan_lb = up(L.bin_lb + bin_lookback_bytes(eyes, n_tiles));
+  L.bounds = up(L.plan_lb + bin_plan_lookback_bytes((int)entries));
+  L.total = up(L.bounds + sizeof(uint32_t) * (kBinMaxChunks + 1));
   return L;
 }
 
@@ -184,7 +174,7 @@ void free_frame_buffers(a3fr_scene *s) {
     dfree(s->dvals[b]);
   }
   dfree(s->ranges);
-  dfree(s->tile_partials);
+  dfree(s->bin_h);
   dfree(s->plan);
   dfree(s->cur_level);
   s->round_ready = false;
@@ -196,17 +186,13 @@ void free_frame_buffers(a3fr_scene *s) {
 }
 
 void free_instance_buffers(a3fr_scene *s) {
-  for (int b = 0; b < 2; ++b) {
-    dfree(s->tkeys[b]);
-    dfree(s->tvals[b]);
-  }
+  dfree(s->vals);
 }
 
 // (Re)allocate frame_ws for the current entry count and capacity.
 int ensure_frame_ws(a3fr_scene *s) {
   const size_t entries = (size_t)s->alloc_eyes * (size_t)(s->desc.n > 0 ? s->desc.n : 1);
-  const int tile_passes = sort_plan(tile_bits_for(s->alloc_eyes * s->n_tiles), 8).passes;
-  const FrameLayout L = frame_layout(entries, s->capacity, tile_passes, s->alloc_eyes, s->TX, s->TY);
+  const FrameLayout L = frame_layout(entries, s->alloc_eyes, s->n_tiles);
   if (s->frame_ws && s->frame_ws_bytes >= L.total) return A3FR_OK;
   if (s->frame_ws) {
     A3FR_CHECK(cudaDeviceSynchronize());
@@ -224,12 +210,7 @@ int alloc_instances(a3fr_scene *s, size_t capacity) {
   s->alloc_gen++;
   free_instance_buffers(s);
   s->capacity = capacity;
-  if (capacity > 0) {
-    for (int b = 0; b < 2; ++b) {
-      A3FR_CHECK(cudaMalloc(&s->tkeys[b], sizeof(uint32_t) * capacity));
-      A3FR_CHECK(cudaMalloc(&s->tvals[b], sizeof(uint32_t) * capacity));
-    }
-  }
+  if (capacity > 0) A3FR_CHECK(cudaMalloc(&s->vals, sizeof(uint32_t) * capacity));
   if (s->alloc_eyes) return ensure_frame_ws(s);
   return A3FR_OK;
 }
@@ -247,7 +228,7 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
     A3FR_CHECK(cudaGetDevice(&dev));
     A3FR_CHECK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
-    if (tile_scan_smem_bytes(eyes, tx, ty) + 9216 > (size_t)max_optin) return A3FR_ERR_INVALID_ARG;
+    if (bin_smem_bytes(eyes, tx, ty) > (size_t)max_optin) return A3FR_ERR_INVALID_ARG;
   }
   s->W = W;
   s->H = H;
@@ -263,8 +244,8 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
     A3FR_CHECK(cudaMalloc(&s->dvals[b], sizeof(uint32_t) * nn));
   }
   A3FR_CHECK(cudaMalloc(&s->ranges, sizeof(uint2) * (size_t)s->n_tiles * eyes));
-  A3FR_CHECK(cudaMalloc(&s->tile_partials, sizeof(uint32_t) * (size_t)tile_count_blocks() *
-                                               tile_grid_cells(eyes, s->TX, s->TY)));
+  A3FR_CHECK(cudaMalloc(&s->bin_h, sizeof(uint32_t) *
+                                       bin_chunk_cells(bin_params(eyes, n > 0 ? n : 1, s->TX, s->TY, 0))));
   A3FR_CHECK(cudaMalloc(&s->plan, plan_bytes(s->n_tiles * eyes)));
   A3FR_CHECK(cudaMalloc(&s->cur_level, (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->levels, (size_t)s->n_tiles * eyes));
@@ -420,21 +401,17 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
                 uint64_t *launches) {
   const int n = s->desc.n;
   const int n_entries = eyes * n;
-  const int n_ranges = eyes * s->n_tiles;
   const SortPlan depth_plan = sort_plan(32, 8);
-  const SortPlan tile_plan = sort_plan(tile_bits_for(n_ranges), 8);
-  FrameLayout L = frame_layout((size_t)(n_entries > 0 ? n_entries : eyes), s->capacity,
-                               tile_plan.passes, eyes, s->TX, s->TY);
+  const FrameLayout L = frame_layout((size_t)(n_entries > 0 ? n_entries : eyes), eyes, s->n_tiles);
   unsigned char *ws = static_cast<unsigned char *>(s->frame_ws);
   uint32_t *counts = s->counts;
   uint32_t *depth_hist = reinterpret_cast<uint32_t *>(ws + L.depth_hist);
   uint32_t *depth_ctr = reinterpret_cast<uint32_t *>(ws + L.depth_ctr);
-  uint32_t *tile_hist = reinterpret_cast<uint32_t *>(ws + L.tile_hist);
-  uint32_t *tile_ctr = reinterpret_cast<uint32_t *>(ws + L.tile_ctr);
-  unsigned long long *emit_lb = reinterpret_cast<unsigned long long *>(ws + L.emit_lb);
-  uint32_t *tile_diff = reinterpret_cast<uint32_t *>(ws + L.tile_diff);
   uint32_t *depth_lb = reinterpret_cast<uint32_t *>(ws + L.depth_lb);
-  uint32_t *tile_lb = reinterpret_cast<uint32_t *>(ws + L.tile_lb);
+  unsigned long long *bin_lb = reinterpret_cast<unsigned long long *>(ws + L.bin_lb);
+  unsigned long long *plan_lb = reinterpret_cast<unsigned long long *>(ws + L.plan_lb);
+  uint32_t *bounds = reinterpret_cast<uint32_t *>(ws + L.bounds);
+  const unsigned long long *inst_total = reinterpret_cast<const unsigned long long *>(counts + 8);
 
   A3FR_CHECK(mark(s, A3FR_STAGE_PREPROCESS, stream));
   A3FR_CHECK(cudaMemsetAsync(s->frame_ws, 0, L.total, stream));
@@ -457,84 +434,46 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
     *launches += 1 + depth_plan.passes;
   }
   const uint32_t *entries = s->dvals[depth_plan.passes % 2];
-  // per-tile counts -> ranges, tile-sort histograms, totals
+  // per-chunk tile counts -> tile ranges, per-chunk starts, totals
   A3FR_CHECK(mark(s, A3FR_STAGE_TILE_SCAN, stream));
-  TileScanParams tp{};
-  tp.n_eyes = eyes;
-  tp.n = n;
-  tp.tiles_x = s->TX;
-  tp.tiles_y = s->TY;
-  tp.n_tiles = s->n_tiles;
-  tp.capacity = (uint32_t)s->capacity;
-  tp.tile_plan = tile_plan;
-  if (n > 0) {
-    A3FR_CHECK(launch_tile_count(tp, s->rect, s->tile_partials, tile_diff, stream));
-    *launches += 2;
-  }
-  A3FR_CHECK(launch_tile_scan(tp, tile_diff, s->ranges, tile_hist, counts, s->status, stream));
-  ++*launches;
+  BinParams bp = bin_params(eyes, n, s->TX, s->TY, (uint32_t)s->capacity);
+  A3FR_CHECK(launch_bin_plan(bp, entries, s->touched, inst_total, plan_lb, bounds, s->status, stream));
+  A3FR_CHECK(launch_bin_count(bp, entries, s->rect, bounds, s->bin_h, stream));
+  A3FR_CHECK(launch_bin_offsets(bp, s->bin_h, bin_lb, s->ranges, counts, s->status, stream));
+  *launches += 3;
   if (allow_resize && s->auto_capacity && s->capacity == 0 && n > 0) {
-    // first render: read the instance count once, then size the instance buffers
+    // first render: read the instance count once, then size the instance buffer (the
+    // starts in bin_h do not depend on the capacity)
     uint32_t cnt[8];
     A3FR_CHECK(cudaMemcpyAsync(cnt, counts, sizeof cnt, cudaMemcpyDeviceToHost, stream));
     A3FR_CHECK(cudaStreamSynchronize(stream));
     size_t want = 2 * (size_t)cnt[3] + (1u << 16);
     if (want >= (1u << 30)) want = (1u << 30) - 1;
-    // keep this frame's workspace: the new one must hold the tile look-back of the capacity
-    void *old_ws = s->frame_ws;
-    s->frame_ws = nullptr;
-    s->frame_ws_bytes = 0;
     const int rc = alloc_instances(s, want);
-    if (rc != A3FR_OK) {
-      cudaFree(old_ws);
-      return rc;
-    }
-    L = frame_layout((size_t)n_entries, s->capacity, tile_plan.passes, eyes, s->TX, s->TY);
-    ws = static_cast<unsigned char *>(s->frame_ws);
-    A3FR_CHECK(cudaMemcpyAsync(ws, old_ws, L.tile_lb, cudaMemcpyDeviceToDevice, stream));
-    A3FR_CHECK(cudaStreamSynchronize(stream));
-    cudaFree(old_ws);
-    counts = s->counts;
-    tile_hist = reinterpret_cast<uint32_t *>(ws + L.tile_hist);
-    tile_ctr = reinterpret_cast<uint32_t *>(ws + L.tile_ctr);
-    emit_lb = reinterpret_cast<unsigned long long *>(ws + L.emit_lb);
-    tile_lb = reinterpret_cast<uint32_t *>(ws + L.tile_lb);
+    if (rc != A3FR_OK) return rc;
+    bp.capacity = (uint32_t)s->capacity;
     cnt[0] = cnt[3] < s->capacity ? cnt[3] : (uint32_t)s->capacity;
     A3FR_CHECK(cudaMemcpyAsync(counts, cnt, sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
     A3FR_CHECK(cudaMemsetAsync(s->status, 0, sizeof(uint32_t), stream));
     A3FR_CHECK(cudaStreamSynchronize(stream));
   }
+  // every instance straight to its slot, each tile's run in depth order
   A3FR_CHECK(mark(s, A3FR_STAGE_EMIT, stream));
-  EmitParams ep{};
-  ep.n = n;
-  ep.n_entries = n_entries;
-  ep.n_tiles = s->n_tiles;
-  ep.tiles_x = s->TX;
-  ep.capacity = (uint32_t)s->capacity;
   if (n > 0 && s->capacity > 0) {
-    A3FR_CHECK(launch_emit(ep, entries, s->touched, s->rect, s->tkeys[0], s->tvals[0], emit_lb,
-                           counts + 6, stream));
-    *launches += 2;
+    A3FR_CHECK(launch_bin_emit(bp, entries, s->rect, bounds, s->bin_h, s->vals, stream));
+    ++*launches;
   }
+  // the instances are already in tile order: the tile-sort stage is empty
   A3FR_CHECK(mark(s, A3FR_STAGE_TILE_SORT, stream));
-  bool in_alt = false;
-  if (n > 0 && s->capacity > 0) {
-    A3FR_CHECK(launch_onesweep<uint32_t>(s->tkeys[0], s->tvals[0], s->tkeys[1], s->tvals[1], false,
-                                         counts, s->capacity, tile_plan, tile_hist, tile_ctr,
-                                         tile_lb, s->status, &in_alt, stream));
-    *launches += tile_plan.passes;
-  }
-  s->sorted_in_alt = in_alt;
   return A3FR_OK;
 }
 
 // The composite of a render (plan + composite, or composite alone for full resolution).
 int enqueue_comp(a3fr_scene *s, const CompositeParams &cp, int uniform, uint8_t *cur, bool fill,
                  cudaStream_t stream, uint64_t *launches) {
-  const int b = s->sorted_in_alt ? 1 : 0;
   A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
   A3FR_CHECK(launch_composite(cp, &s->params_dev->comp, s->rec, s->desc.n, s->ranges, s->counts,
-                              s->tvals[b], s->gaze_dev, nullptr, uniform, cur, s->plan, s->levels,
+                              s->vals, s->gaze_dev, nullptr, uniform, cur, s->plan, s->levels,
                               s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr,
                               s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, s->thresholds, stream));
@@ -683,9 +622,8 @@ int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
   if (rc != A3FR_OK) return rc;
   A3FR_CHECK(launch_round_begin(s->round_cfg, s->mbox_dev, s->round_state, s->round_plan,
                                 s->status_dev, s->status, stream));
-  const int b = s->sorted_in_alt ? 1 : 0;
   A3FR_CHECK(launch_composite(hp.comp, &s->params_dev->comp, s->rec, s->desc.n, s->ranges,
-                              s->counts, s->tvals[b], s->gaze_dev, s->round_plan, 0, s->cur_level,
+                              s->counts, s->vals, s->gaze_dev, s->round_plan, 0, s->cur_level,
                               s->plan, s->levels, s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr,
                               s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, s->thresholds, stream));
@@ -940,7 +878,7 @@ int a3fr_get_stats(a3fr_scene *s, a3fr_stats *st, int reset) {
   st->n_eyes = s->last_eyes;
   st->instances = counts[0];
   st->instances_eye[0] = counts[1];
-  st->instances_eye[1] = counts[2];
+  st->instances_eye[1] = s->last_eyes > 1 ? counts[3] - counts[1] : 0;
   st->capacity = (int64_t)s->capacity;
   st->evaluations = ctr[0];
   st->records_staged = ctr[1];
@@ -1004,7 +942,6 @@ int a3fr_copy_buffer(a3fr_scene *s, int which, void *dst, size_t bytes, size_t *
   const void *src = nullptr;
   size_t size = 0;
   uint32_t cnt = 0;
-  const int b = s->sorted_in_alt ? 1 : 0;
   if (which == A3FR_BUF_KEYS || which == A3FR_BUF_VALUES) {
     A3FR_CHECK(cudaStreamSynchronize(s->last_stream));
     if (s->counts) A3FR_CHECK(cudaMemcpy(&cnt, s->counts, sizeof cnt, cudaMemcpyDeviceToHost));
@@ -1013,7 +950,7 @@ int a3fr_copy_buffer(a3fr_scene *s, int which, void *dst, size_t bytes, size_t *
     case A3FR_BUF_RECORDS: src = s->rec; size = sizeof(float) * kRec * n * eyes; break;
     case A3FR_BUF_RECTS: src = s->rect; size = sizeof(ushort4) * n * eyes; break;
     case A3FR_BUF_KEYS: size = sizeof(uint64_t) * cnt; break;   // built on demand below
-    case A3FR_BUF_VALUES: src = s->tvals[b]; size = sizeof(uint32_t) * cnt; break;
+    case A3FR_BUF_VALUES: src = s->vals; size = sizeof(uint32_t) * cnt; break;
     case A3FR_BUF_RANGES: src = s->ranges; size = sizeof(uint2) * (size_t)s->n_tiles * eyes; break;
     case A3FR_BUF_LEVELS: src = s->levels; size = (size_t)s->n_tiles * eyes; break;
     case A3FR_BUF_T_FINAL: src = s->t_final; size = sizeof(float) * (size_t)s->W * s->H * eyes; break;
@@ -1028,7 +965,8 @@ int a3fr_copy_buffer(a3fr_scene *s, int which, void *dst, size_t bytes, size_t *
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (which == A3FR_BUF_KEYS) {
     // the render sorts tile indices; the 64-bit (tile << 32 | depth bits) keys are rebuilt
-    A3FR_CHECK(launch_materialize_keys(s->tkeys[b], s->tvals[b], s->rec, s->desc.n, s->n_tiles,
+    A3FR_CHECK(launch_materialize_keys(s->ranges, eyes * s->n_tiles, s->vals, s->rec, s->desc.n,
+                                       s->n_tiles,
                                        (uint32_t)(bytes / sizeof(uint64_t)),
                                        static_cast<uint64_t *>(dst), st));
     return A3FR_OK;
@@ -1108,10 +1046,9 @@ int a3fr_backward(a3fr_scene *s, const float *dl_drgb, const a3fr_grads *g, void
   bp.tile = s->desc.tile;
   bp.tiles_x = s->TX;
   bp.n_tiles = s->n_tiles;
-  const int b = s->sorted_in_alt ? 1 : 0;
   A3FR_CHECK(launch_backward(bp, &s->params_dev->pre, s->desc.sh_degree, s->desc.means,
                              s->desc.log_scales, s->desc.quats, s->desc.opacity_logits, s->desc.sh,
-                             s->rec, s->ranges, s->counts, s->tvals[b],
+                             s->rec, s->ranges, s->counts, s->vals,
                              s->bw_mode == 2 ? s->levels : nullptr, s->t_final, s->n_contrib,
                              dl_drgb, s->g2d, g->means, g->log_scales, g->quats, g->opacity_logits,
                              g->sh, st));

@@ -2,207 +2,46 @@
 // ellipses intersect with a given pixel tile") and the per-tile ranges of the sorted
 // instances ("subsets of Gaussian points on each tile", Sec. 3.5).
 //
-// The Gaussians of all eyes have already been sorted by depth (sort.cu).  emit walks them
-// in that order and writes one (tile index, Gaussian index) instance per overlapped tile,
-// so a STABLE sort of the instances by tile index alone gives every tile's Gaussians front
-// to back with ties in index order -- exactly the order of the (tile << 32 | depth bits)
-// keys sorted stably.
+// The Gaussians of all eyes have already been sorted by depth (sort.cu).  A tile's list is
+// the depth-ordered entries whose tile rectangle covers the tile, in that order -- exactly
+// the order of the (tile << 32 | depth bits) keys sorted stably.  Binning writes every
+// (tile, Gaussian) instance straight to its final slot; there is no sort by tile:
 //
-// tile_count + tile_scan give every tile's instance count without enumerating instances:
-// each tile rectangle adds +1/-1/-1/+1 at its corners in a 2-D difference grid (per CTA in
-// shared memory, partial grids summed without atomics), whose 2-D prefix sum is the count.
-// The exclusive scan of the counts over tiles is exactly where the stable sort by tile puts
-// each tile's run, i.e. the tile ranges; the digit histograms of that sort follow from the
-// same prefix sums.  So neither a ranges pass nor a histogram pass is needed.
+//  bin_plan     The entries are cut into C chunks of consecutive entries holding about
+//               equal numbers of instances (a look-back prefix of the entries' counts).
+//  bin_count    Per chunk
+//               (one CTA), shared-memory atomics over the tile rectangles give the
+//               chunk's instance count of every tile, h[c][r].
+//  bin_offsets  With T[r] = sum over chunks of h[c][r], tile r's run starts at R[r] = sum
+//               of T over the tiles before it (these are the tile ranges), and chunk c's
+//               instances of tile r at R[r] + sum over the earlier chunks of h[c'][r]; the
+//               start overwrites h.  One CTA per 32 tiles; the CTAs chain their sums by a
+//               decoupled look-back (bounded waits, like the sort's).
+//  bin_emit     One warp per chunk walks the chunk's instances in entry order, 32 at a
+//               time (lane = instance).  A lane's slot is the tile's cursor plus the number
+//               of lower lanes with the same tile; the highest of them advances the cursor.
+//               Every tile's instances land in entry (= depth) order, the same on every run.
 //
-// emit: instance offsets by reduce-then-scan over blocks of 1024 depth-ordered entries (a
-// count kernel whose last block scans the block sums; no block ever waits on another), then
-// each block expands its instances load-balanced: each output slot of its contiguous run is
-// one thread's work (its entry found by binary search over the block's exclusive offsets), so
-// a Gaussian covering hundreds of tiles does not hold its warp, and consecutive threads store
-// consecutive slots.
+// Instances whose slot is at or past the capacity are dropped (the render raises the
+// capacity status and the composite clamps ranges to the instances kept).
 #include "common.cuh"
 
 namespace a3fr {
 namespace {
 
-constexpr int kEmitThreads = 256;
-constexpr int kEmitWarps = kEmitThreads / 32;
-constexpr int kEmitPer = 4;                                // entries per thread
-constexpr int kEmitEntries = kEmitThreads * kEmitPer;      // entries per block
-// Instance count of every block of kEmitEntries depth-ordered entries; the last block to
-// finish (fence + counter: the blocks never wait on one another) turns the sums into
-// exclusive prefixes in place, with the total after the last block.
-__global__ void __launch_bounds__(kEmitThreads)
-emit_count_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
-                  unsigned long long *__restrict__ blk, uint32_t *__restrict__ done_counter) {
-  __shared__ unsigned long long s_w[kEmitWarps];
-  __shared__ unsigned long long s_carry;
-  __shared__ bool s_last;
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  unsigned long long sum = 0;
-#pragma unroll
-  for (int k = 0; k < kEmitPer; ++k) {
-    const uint32_t j = blockIdx.x * kEmitEntries + t * kEmitPer + k;
-    if (j < (uint32_t)p.n_entries) sum += touched[entries[j]];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if (lane == 0) s_w[warp] = sum;
-  __syncthreads();
-  if (t == 0) {
-    unsigned long long total = 0;
-    for (int w = 0; w < kEmitWarps; ++w) total += s_w[w];
-    blk[blockIdx.x] = total;
-    __threadfence();
-    s_last = atomicAdd(done_counter, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (t == 0) s_carry = 0;
-  __syncthreads();
-  const int nb = gridDim.x;
-  for (int base = 0; base < nb; base += kEmitThreads) {
-    const int i = base + t;
-    const unsigned long long v = i < nb ? __ldcg(blk + i) : 0ull;
-    unsigned long long incl = v;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long n = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += n;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    unsigned long long before = s_carry;
-    for (int w = 0; w < warp; ++w) before += s_w[w];
-    if (i < nb) blk[i] = before + incl - v;
-    __syncthreads();
-    if (t == kEmitThreads - 1) s_carry = before + incl;
-    __syncthreads();
-  }
-  if (t == 0) blk[nb] = s_carry;
-}
-
-// Instances of block blockIdx.x's entries at [blk[blockIdx.x], +count): each thread reads
-// kEmitPer consecutive entries, the block scans them, and the block's run is expanded
-// load-balanced: one output slot per thread at a time (consecutive threads, consecutive
-// slots), its entry found by binary search over the block's exclusive offsets.
-__global__ void __launch_bounds__(kEmitThreads)
-emit_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
-            const ushort4 *__restrict__ rect, uint32_t *__restrict__ tile_keys,
-            uint32_t *__restrict__ vals, const unsigned long long *__restrict__ blk) {
-  __shared__ uint32_t s_warp_total[kEmitWarps];
-  __shared__ uint32_t s_excl[kEmitEntries + 1];   // exclusive instance offsets of the entries
-  __shared__ uint32_t s_tile0[kEmitEntries], s_width[kEmitEntries], s_gid[kEmitEntries];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint32_t cnt[kEmitPer], mine = 0;
-#pragma unroll
-  for (int k = 0; k < kEmitPer; ++k) {
-    const int le = t * kEmitPer + k;
-    const uint32_t j = blockIdx.x * kEmitEntries + le;
-    uint32_t c = 0, tile0 = 0, width = 1, gid = 0;
-    if (j < (uint32_t)p.n_entries) {
-      const uint32_t v = entries[j];          // e * n + i
-      c = touched[v];
-      if (c) {
-        const uint32_t eye = v >= (uint32_t)p.n ? 1u : 0u;
-        gid = v - eye * (uint32_t)p.n;
-        const ushort4 rc = rect[v];
-        tile0 = eye * (uint32_t)p.n_tiles + (uint32_t)rc.y * (uint32_t)p.tiles_x + rc.x;
-        width = (uint32_t)(rc.z - rc.x);
-      }
-    }
-    cnt[k] = c;
-    mine += c;
-    s_tile0[le] = tile0;
-    s_width[le] = width;
-    s_gid[le] = gid;
-  }
-  uint32_t incl = mine;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += n;
-  }
-  if (lane == 31) s_warp_total[warp] = incl;
-  __syncthreads();
-  uint32_t excl = incl - mine;
-  for (int w = 0; w < warp; ++w) excl += s_warp_total[w];
-#pragma unroll
-  for (int k = 0; k < kEmitPer; ++k) {
-    s_excl[t * kEmitPer + k] = excl;
-    excl += cnt[k];
-  }
-  if (t == kEmitThreads - 1) s_excl[kEmitEntries] = excl;
-  __syncthreads();
-  const unsigned long long prefix = blk[blockIdx.x];
-  const uint32_t total = s_excl[kEmitEntries];
-  for (uint32_t q = t; q < total; q += kEmitThreads) {
-    int lo = 0, hi = kEmitEntries;   // s_excl[lo] <= q < s_excl[hi]
-#pragma unroll
-    for (int step = 0; step < 10; ++step) {
-      const int mid = (lo + hi) >> 1;
-      if (s_excl[mid] <= q) lo = mid;
-      else hi = mid;
-    }
-    const uint32_t r = q - s_excl[lo];
-    const uint32_t w = s_width[lo];
-    const uint32_t dy = r / w, dx = r - dy * w;
-    const unsigned long long off = prefix + q;
-    if (off < p.capacity) {
-      tile_keys[off] = s_tile0[lo] + dy * (uint32_t)p.tiles_x + dx;
-      vals[off] = s_gid[lo];
-    }
-  }
-}
-
-constexpr int kCountThreads = 512;
-
-// Per CTA: the difference grid of a contiguous slice of the (eye, Gaussian) rectangles in
-// shared memory, written to partials[blockIdx.x][cells].
-__global__ void __launch_bounds__(kCountThreads)
-tile_count_kernel(TileScanParams p, const ushort4 *__restrict__ rect,
-                  uint32_t *__restrict__ partials) {
-  extern __shared__ uint32_t s_grid[];
-  const int gw = p.tiles_x + 1, gh = p.tiles_y + 1;
-  const int cells = p.n_eyes * gw * gh;
-  for (int i = threadIdx.x; i < cells; i += kCountThreads) s_grid[i] = 0;
-  __syncthreads();
-  const int entries = p.n_eyes * p.n;
-  const int per = (entries + gridDim.x - 1) / gridDim.x;
-  const int e0 = blockIdx.x * per, e1 = min(entries, e0 + per);
-  for (int v = e0 + threadIdx.x; v < e1; v += kCountThreads) {
-    const ushort4 rc = rect[v];
-    if (rc.x >= rc.z) continue;
-    const int eye = v >= p.n ? 1 : 0;
-    uint32_t *g = s_grid + eye * gw * gh;
-    atomicAdd(g + rc.y * gw + rc.x, 1u);
-    atomicAdd(g + rc.y * gw + rc.z, 0xffffffffu);
-    atomicAdd(g + rc.w * gw + rc.x, 0xffffffffu);
-    atomicAdd(g + rc.w * gw + rc.z, 1u);
-  }
-  __syncthreads();
-  uint32_t *out = partials + (size_t)blockIdx.x * cells;
-  for (int i = threadIdx.x; i < cells; i += kCountThreads) out[i] = s_grid[i];
-}
-
-// Sum of the per-CTA difference grids: blockIdx.y takes a group of kReduceParts partial
-// grids, each thread one cell; the group sums are added into the zeroed grid (integer adds,
-// so the result does not depend on their order).
-constexpr int kReduceParts = 19;
-
-__global__ void __launch_bounds__(256)
-tile_reduce_kernel(const uint32_t *__restrict__ partials, int parts, int cells,
-                   uint32_t *__restrict__ grid) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= cells) return;
-  const int b0 = blockIdx.y * kReduceParts, b1 = min(parts, b0 + kReduceParts);
-  uint32_t acc = 0;
-#pragma unroll 4
-  for (int b = b0; b < b1; ++b) acc += partials[(size_t)b * cells + i];
-  if (acc) atomicAdd(grid + i, acc);
-}
+constexpr int kCountThreads = 256;
+constexpr int kPlanThreads = 256;
+constexpr int kPlanPer = 8;                  // entries per thread of bin_plan
+constexpr int kPlanEntries = kPlanThreads * kPlanPer;
+constexpr int kOffsetThreads = 1024;
+constexpr int kMaxChunks = kBinMaxChunks;
+constexpr int kSegUnroll = 16;              // bin_offsets loads in flight per thread
+constexpr unsigned long long kAggFlag = 1ull << 62, kPrefixFlag = 2ull << 62;
+constexpr unsigned long long kVal62 = (1ull << 62) - 1ull;
+constexpr uint32_t kSpinLimit = 1u << 16;   // with back-off: well over a second
+constexpr int kMap = 256;                   // instances a bin_emit warp expands per window
+constexpr int kMapPad = kMap + kMap / 32;   // one pad word per 32 (fewer bank conflicts)
+constexpr long long kMaxChunkCells = 24ll << 20;   // bound on C * tiles (u32 cells of h)
 
 // Inclusive scan of one value per lane across the warp.
 template <typename T>
@@ -215,153 +54,340 @@ __device__ __forceinline__ T warp_incl_scan(T v, int lane) {
   return v;
 }
 
-// One CTA: 2-D prefix sums of the summed difference grids in shared memory (a warp per row,
-// then a warp per column, 32 cells per step), then the exclusive scan of the counts over
-// tiles (eye-major, row-major) -> ranges: each thread owns a contiguous run of tiles, so
-// one block-wide scan of the run totals suffices.  The digit histograms of the tile sort
-// are accumulated from the same counts (one shared atomic per run of equal digits), and
-// the per-eye totals are read from the scanned ranges.
-__global__ void __launch_bounds__(1024)
-tile_scan_kernel(TileScanParams p, const uint32_t *__restrict__ diff, uint2 *__restrict__ ranges,
-                 uint32_t *__restrict__ tile_hist, uint32_t *__restrict__ counts,
-                 uint32_t *__restrict__ status) {
-  extern __shared__ uint32_t s_grid[];
-  __shared__ unsigned long long s_warp[32];
-  __shared__ uint32_t s_hist[kMaxSortPasses][256];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5, n_warps = blockDim.x >> 5;
-  const int gw = p.tiles_x + 1, gh = p.tiles_y + 1;
-  const int cells = p.n_eyes * gw * gh;
-  for (int i = t; i < kMaxSortPasses * 256; i += blockDim.x) (&s_hist[0][0])[i] = 0;
-  // bulk copy, four independent loads in flight per thread
-  for (int i0 = t; i0 < cells; i0 += 4 * blockDim.x) {
-    uint32_t v[4];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int i = i0 + k * blockDim.x;
-      v[k] = i < cells ? diff[i] : 0u;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int i = i0 + k * blockDim.x;
-      if (i < cells) s_grid[i] = v[k];
-    }
-  }
-  __syncthreads();
-  // rows
-  for (int r = warp; r < p.n_eyes * gh; r += n_warps) {
-    uint32_t *row = s_grid + r * gw;
-    uint32_t carry = 0;
-    for (int x0 = 0; x0 < gw; x0 += 32) {
-      const int x = x0 + lane;
-      uint32_t v = x < gw ? row[x] : 0u;
-      v = warp_incl_scan(v, lane) + carry;
-      if (x < gw) row[x] = v;
-      carry = __shfl_sync(0xffffffffu, v, 31);
-    }
-  }
-  __syncthreads();
-  // columns
-  for (int c = warp; c < p.n_eyes * gw; c += n_warps) {
-    const int e = c / gw, x = c - e * gw;
-    uint32_t *col = s_grid + e * gw * gh + x;
-    uint32_t carry = 0;
-    for (int y0 = 0; y0 < gh; y0 += 32) {
-      const int y = y0 + lane;
-      uint32_t v = y < gh ? col[y * gw] : 0u;
-      v = warp_incl_scan(v, lane) + carry;
-      if (y < gh) col[y * gw] = v;
-      carry = __shfl_sync(0xffffffffu, v, 31);
-    }
-  }
-  __syncthreads();
-  // this thread's run of tiles [r0, r1) and its total
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Per chunk: the instance count of every tile by shared-memory atomics over the chunk's
+// tile rectangles (each thread walks the rectangles of its entries), written as h[c][r].
+__global__ void __launch_bounds__(kCountThreads)
+bin_count_kernel(BinParams p, const uint32_t *__restrict__ entries, const ushort4 *__restrict__ rect,
+                 const uint32_t *__restrict__ bounds, uint32_t *__restrict__ h) {
+  extern __shared__ uint32_t s_hist[];
+  const int t = threadIdx.x;
   const int n_ranges = p.n_eyes * p.n_tiles;
-  const int per = (n_ranges + (int)blockDim.x - 1) / (int)blockDim.x;
-  const int r0 = min(n_ranges, t * per), r1 = min(n_ranges, r0 + per);
-  unsigned long long sum = 0;
-  if (r0 < r1) {
-    int eye = r0 / p.n_tiles, tile = r0 - eye * p.n_tiles;
-    int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
-    for (int r = r0; r < r1; ++r) {
-      sum += s_grid[eye * gw * gh + ty * gw + tx];
-      if (++tx == p.tiles_x) {
-        tx = 0;
-        if (++ty == p.tiles_y) { ty = 0; ++eye; }
-      }
+  for (int i = t; i < n_ranges; i += kCountThreads) s_hist[i] = 0u;
+  __syncthreads();
+  const int j0 = (int)bounds[blockIdx.x], j1 = (int)bounds[blockIdx.x + 1];
+  for (int j = j0 + t; j < j1; j += kCountThreads) {
+    const uint32_t v = entries[j];
+    const ushort4 rc = rect[v];
+    if (rc.x >= rc.z) continue;
+    const int row0 = (v >= (uint32_t)p.n ? p.tiles_y : 0) + (int)rc.y;
+    const int rows = (int)rc.w - (int)rc.y;
+    for (int y = 0; y < rows; ++y) {
+      uint32_t *hr = s_hist + (row0 + y) * p.tiles_x;
+      for (int x = rc.x; x < (int)rc.z; ++x) atomicAdd(hr + x, 1u);
     }
   }
-  // block-wide exclusive scan of the run totals
-  const unsigned long long incl = warp_incl_scan(sum, lane);
+  __syncthreads();
+  uint32_t *out = h + (size_t)blockIdx.x * p.row;
+  for (int r = t; r < n_ranges; r += kCountThreads) out[r] = s_hist[r];
+}
+
+// Exclusive prefix of block b's aggregate over the blocks before it, by warp 0: windows of
+// 32 predecessors (lane k reads block b-1-k) summed nearest first up to the first
+// inclusive prefix; an unpublished predecessor is polled again after a back-off.
+__device__ unsigned long long block_lookback(unsigned long long *lookback, int b, uint32_t *status) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long excl = 0;
+  int j = b - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    const unsigned long long w = j - lane >= 0 ? ld_relaxed64(lookback + (j - lane)) : kPrefixFlag;
+    const unsigned long long flag = w & ~kVal62;
+    const unsigned ready = __ballot_sync(0xffffffffu, flag != 0ull);
+    const unsigned pref = __ballot_sync(0xffffffffu, flag == kPrefixFlag);
+    // lanes up to the nearest inclusive prefix, if every one of them is published
+    const int lim = pref ? __ffs(pref) - 1 : 31;
+    const unsigned need = lim == 31 ? 0xffffffffu : ((2u << lim) - 1u);
+    if ((ready & need) != need) {
+      if (++spins > kSpinLimit) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        break;
+      }
+      __nanosleep(spins < 8 ? 32u << spins : 4096u);
+      continue;
+    }
+    unsigned long long v = lane <= lim ? (w & kVal62) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (pref) break;
+    j -= 32;
+  }
+  return excl;
+}
+
+// Chunk plan: bounds[c] = the first entry j whose preceding instances P_j (prefix of the
+// entries' tile counts in depth order) reach c T / C, T the render's instance total, so
+// every chunk holds about T / C instances (near Gaussians, first in depth order, cover
+// many tiles: equal entry counts would load the first chunks with twice the mean).  An
+// entry j writes bounds[c] = j + 1 for the c with floor(P_j C / T) < c <= floor(P_{j+1} C / T).
+// The blocks chain their sums by the same look-back as bin_offsets.
+__global__ void __launch_bounds__(kPlanThreads)
+bin_plan_kernel(BinParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
+                const unsigned long long *__restrict__ inst_total,
+                unsigned long long *__restrict__ lookback, uint32_t *__restrict__ bounds,
+                uint32_t *__restrict__ status) {
+  __shared__ unsigned long long s_warp[kPlanThreads / 32];
+  __shared__ unsigned long long s_before;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const unsigned long long T = *inst_total;
+  const unsigned long long C = (unsigned long long)p.n_chunks;
+  if (blockIdx.x == 0 && t == 0) {
+    bounds[0] = 0u;
+    bounds[p.n_chunks] = (uint32_t)p.n_entries;
+  }
+  if (T == 0ull) {
+    // no instances: any split will do
+    for (int c = 1 + blockIdx.x * kPlanThreads + t; c < p.n_chunks; c += gridDim.x * kPlanThreads)
+      bounds[c] = (uint32_t)((unsigned long long)p.n_entries * (unsigned long long)c / C);
+    return;
+  }
+  const int jb = blockIdx.x * kPlanEntries + t * kPlanPer;
+  uint32_t cnt[kPlanPer];
+  unsigned long long sum = 0;
+#pragma unroll
+  for (int k = 0; k < kPlanPer; ++k) {
+    const int j = jb + k;
+    cnt[k] = j < p.n_entries ? touched[entries[j]] : 0u;
+    sum += cnt[k];
+  }
+  const unsigned long long incl = warp_incl_scan<unsigned long long>(sum, lane);
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();
+  unsigned long long wbefore = 0, agg = 0;
+  for (int w = 0; w < kPlanThreads / 32; ++w) {
+    if (w < warp) wbefore += s_warp[w];
+    agg += s_warp[w];
+  }
   if (warp == 0) {
-    const unsigned long long w = lane < n_warps ? s_warp[lane] : 0ull;
-    s_warp[lane] = warp_incl_scan(w, lane) - w;
+    unsigned long long before = 0;
+    if (blockIdx.x == 0) {
+      if (lane == 0) st_relaxed64(lookback, kPrefixFlag | (agg & kVal62));
+    } else {
+      if (lane == 0) st_relaxed64(lookback + blockIdx.x, kAggFlag | (agg & kVal62));
+      before = block_lookback(lookback, blockIdx.x, status);
+      if (lane == 0) st_relaxed64(lookback + blockIdx.x, kPrefixFlag | ((before + agg) & kVal62));
+    }
+    if (lane == 0) s_before = before;
   }
   __syncthreads();
-  unsigned long long excl = s_warp[warp] + incl - sum;
-  if (r0 < r1) {
-    int eye = r0 / p.n_tiles, tile = r0 - eye * p.n_tiles;
-    int ty = tile / p.tiles_x, tx = tile - ty * p.tiles_x;
-    uint32_t run_d[kMaxSortPasses], run_v[kMaxSortPasses];
+  unsigned long long P = s_before + wbefore + incl - sum;
+  unsigned long long c_lo = P * C / T;
 #pragma unroll
-    for (int ps = 0; ps < kMaxSortPasses; ++ps) {
-      run_d[ps] = 0xffffffffu;
-      run_v[ps] = 0;
+  for (int k = 0; k < kPlanPer; ++k) {
+    const unsigned long long P1 = P + cnt[k];
+    const unsigned long long c_hi = P1 * C / T;
+    for (unsigned long long c = c_lo + 1; c <= c_hi && c < C; ++c) bounds[c] = (uint32_t)(jb + k + 1);
+    P = P1;
+    c_lo = c_hi;
+  }
+}
+
+// Block b owns tiles [32 b, 32 b + 32) (lane = tile) and warp w the chunk segment
+// [C w / 32, C (w + 1) / 32), staged in shared memory (s_seg[k][thread]).  Starts are stored clamped to 2^31 - 1,
+// so the cursors of bin_emit cannot wrap; bin_emit drops every slot at or past the
+// capacity.  counts[1] (the first eye's instances) comes from the block holding the first
+// tile of the second eye, counts[0] and [3] from the last block.
+__global__ void __launch_bounds__(kOffsetThreads)
+bin_offsets_kernel(BinParams p, uint32_t *__restrict__ h, unsigned long long *__restrict__ lookback,
+                   uint2 *__restrict__ ranges, uint32_t *__restrict__ counts,
+                   uint32_t *__restrict__ status) {
+  extern __shared__ uint32_t s_seg[];
+  __shared__ uint32_t s_part[32][33];
+  __shared__ unsigned long long s_before;
+  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+  const int n_ranges = p.n_eyes * p.n_tiles;
+  const int r = blockIdx.x * 32 + lane;
+  const int c0 = (int)((long long)p.n_chunks * warp / 32);
+  const int c1 = (int)((long long)p.n_chunks * (warp + 1) / 32);
+  const int n_seg = r < n_ranges ? c1 - c0 : 0;
+  uint32_t *col = h + (size_t)c0 * p.row + (r < n_ranges ? r : 0);
+  uint32_t part = 0;
+  for (int k0 = 0; k0 < n_seg; k0 += kSegUnroll) {
+    uint32_t v[kSegUnroll];
+#pragma unroll
+    for (int u = 0; u < kSegUnroll; ++u)
+      v[u] = k0 + u < n_seg ? col[(size_t)(k0 + u) * p.row] : 0u;
+#pragma unroll
+    for (int u = 0; u < kSegUnroll; ++u) {
+      if (k0 + u < n_seg) s_seg[(k0 + u) * kOffsetThreads + t] = v[u];
+      part += v[u];
     }
-    const unsigned long long lim = 0xffffffffull;
-    for (int r = r0; r < r1; ++r) {
-      const uint32_t cnt = s_grid[eye * gw * gh + ty * gw + tx];
-      // unclamped: the composite clamps every range to the instances the sort kept
-      ranges[r] = make_uint2((uint32_t)(excl < lim ? excl : lim),
-                             (uint32_t)(excl + cnt < lim ? excl + cnt : lim));
-      excl += cnt;
+  }
+  s_part[warp][lane] = part;
+  __syncthreads();
+  unsigned long long tot = 0, earlier = 0;
+  for (int w = 0; w < 32; ++w) {
+    const uint32_t v = s_part[w][lane];
+    tot += v;
+    if (w < warp) earlier += v;
+  }
+  unsigned long long agg = tot;
 #pragma unroll
-      for (int ps = 0; ps < kMaxSortPasses; ++ps) {
-        if (ps < p.tile_plan.passes) {
-          const uint32_t d = ((uint32_t)r >> p.tile_plan.shift[ps]) & p.tile_plan.mask;
-          if (d != run_d[ps]) {
-            if (run_v[ps]) atomicAdd(&s_hist[ps][run_d[ps]], run_v[ps]);
-            run_d[ps] = d;
-            run_v[ps] = 0;
-          }
-          run_v[ps] += cnt;
-        }
-      }
-      if (++tx == p.tiles_x) {
-        tx = 0;
-        if (++ty == p.tiles_y) { ty = 0; ++eye; }
-      }
+  for (int o = 16; o > 0; o >>= 1) agg += __shfl_xor_sync(0xffffffffu, agg, o);
+  if (warp == 0) {
+    unsigned long long before = 0;
+    if (blockIdx.x == 0) {
+      if (lane == 0) st_relaxed64(lookback, kPrefixFlag | (agg & kVal62));
+    } else {
+      if (lane == 0) st_relaxed64(lookback + blockIdx.x, kAggFlag | (agg & kVal62));
+      before = block_lookback(lookback, blockIdx.x, status);
+      if (lane == 0) st_relaxed64(lookback + blockIdx.x, kPrefixFlag | ((before + agg) & kVal62));
     }
-#pragma unroll
-    for (int ps = 0; ps < kMaxSortPasses; ++ps)
-      if (ps < p.tile_plan.passes && run_v[ps]) atomicAdd(&s_hist[ps][run_d[ps]], run_v[ps]);
+    if (lane == 0) s_before = before;
   }
   __syncthreads();
-  for (int i = t; i < p.tile_plan.passes * 256; i += blockDim.x) tile_hist[i] = (&s_hist[0][0])[i];
-  if (t == blockDim.x - 1) {
-    // the last thread's running offset is the total (threads past the tiles carry it too)
-    const unsigned long long total = excl;
-    const uint32_t eye0 = p.n_eyes > 1 ? ranges[p.n_tiles].x : (uint32_t)total;
+  const unsigned long long before = s_before;
+  const unsigned long long start = before + warp_incl_scan<unsigned long long>(tot, lane) - tot;
+  unsigned long long run = start + earlier;
+  const unsigned long long lim = 0xffffffffull, clamp = 0x7fffffffull;
+  for (int k = 0; k < n_seg; ++k) {
+    *col = (uint32_t)(run < clamp ? run : clamp);
+    run += s_seg[k * kOffsetThreads + t];
+    col += p.row;
+  }
+  if (warp == 0 && r < n_ranges) {
+    // unclamped: the composite clamps every range to the instances kept
+    ranges[r] = make_uint2((uint32_t)(start < lim ? start : lim),
+                           (uint32_t)(start + tot < lim ? start + tot : lim));
+    if (p.n_eyes > 1 && r == p.n_tiles) counts[1] = (uint32_t)(start < lim ? start : lim);
+  }
+  if (warp == 0 && lane == 0 && blockIdx.x == gridDim.x - 1) {
+    const unsigned long long total = before + agg;
     counts[0] = (uint32_t)(total < p.capacity ? total : p.capacity);
-    counts[1] = eye0;
-    counts[2] = (uint32_t)total - eye0;
-    counts[3] = (uint32_t)(total < 0xffffffffull ? total : 0xffffffffull);
+    if (p.n_eyes < 2) counts[1] = (uint32_t)(total < lim ? total : lim);
+    counts[3] = (uint32_t)(total < lim ? total : lim);
     if (total > p.capacity) atomicOr(status, kStatusCapacity);
   }
 }
 
-__global__ void materialize_keys_kernel(const uint32_t *__restrict__ tile_keys,
+// floor(r / w) for r < 2^24, 1 <= w < 2^16: a float estimate, then corrected to the exact
+// integer quotient (so the estimate's rounding never matters).
+__device__ __forceinline__ uint32_t div_small(uint32_t r, uint32_t w) {
+  uint32_t d = (uint32_t)((float)r * __frcp_rn((float)w));
+  if (d * w > r) --d;
+  else if ((d + 1u) * w <= r) ++d;
+  return d;
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// One warp (CTA) per chunk walks the chunk's instances in entry order.  Per round of 32
+// entries (lane = entry) the warp scans the entries' instance counts and expands the
+// instances into its map (tile, Gaussian) in windows of kMap, then takes the map 32
+// instances at a time (lane = instance: full warps whatever the rectangle sizes).  A lane's
+// rank among the step's instances of its tile is the number of lower lanes with the same
+// tile (__match_any_sync); the highest of them advances the tile's cursor.  Shared memory:
+// cursor[row] (the chunk's starts, copied in by cp.async) and the map.  Entry values are
+// loaded two rounds ahead, rectangles one round ahead.
+__global__ void __launch_bounds__(32)
+bin_emit_kernel(BinParams p, const uint32_t *__restrict__ entries, const ushort4 *__restrict__ rect,
+                const uint32_t *__restrict__ bounds, const uint32_t *__restrict__ h,
+                uint32_t *__restrict__ vals) {
+  extern __shared__ __align__(16) uint32_t s_dyn[];
+  __shared__ uint32_t s_map_tile[kMapPad];
+  __shared__ uint32_t s_map_gid[kMapPad];
+  const int lane = threadIdx.x;
+  uint32_t *s_cur = s_dyn;
+  {
+    const uint32_t *hb = h + (size_t)blockIdx.x * p.row;
+    for (int i = lane * 4; i < p.row; i += 128) cp_async16(s_cur + i, hb + i);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  }
+  const unsigned below = (1u << lane) - 1u;
+  const int j0 = (int)bounds[blockIdx.x], j1 = (int)bounds[blockIdx.x + 1];
+  const ushort4 none = make_ushort4(0, 0, 0, 0);
+  uint32_t v_cur = j0 + lane < j1 ? entries[j0 + lane] : 0u;
+  uint32_t v_next = j0 + 32 + lane < j1 ? entries[j0 + 32 + lane] : 0u;
+  ushort4 r_cur = j0 + lane < j1 ? rect[v_cur] : none;
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncwarp();
+  for (int b = j0; b < j1; b += 32) {
+    const uint32_t v = v_cur;
+    const ushort4 rc = r_cur;
+    {
+      const int jn = b + 32 + lane, jnn = jn + 32;
+      r_cur = jn < j1 ? rect[v_next] : none;
+      v_cur = v_next;
+      v_next = jnn < j1 ? entries[jnn] : 0u;
+    }
+    const uint32_t w = rc.z > rc.x ? (uint32_t)(rc.z - rc.x) : 0u;
+    const uint32_t cnt = (b + lane < j1 && rc.w > rc.y) ? w * (uint32_t)(rc.w - rc.y) : 0u;
+    const uint32_t incl = warp_incl_scan(cnt, lane);
+    const uint32_t first = incl - cnt;
+    const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+    const int eye = v >= (uint32_t)p.n ? 1 : 0;
+    const uint32_t gid = v - (uint32_t)eye * (uint32_t)p.n;
+    const int row0 = eye * p.tiles_y + (int)rc.y;
+    for (uint32_t base = 0; base < total; base += kMap) {
+      const uint32_t wend = min(total, base + kMap);
+      // this lane's instances in [base, wend) into the map
+      const uint32_t lo = max(first, base), hi = min(incl, wend);
+      if (lo < hi) {
+        const uint32_t off = lo - first;
+        const uint32_t dy = off ? div_small(off, w) : 0u;
+        int x = (int)rc.x + (int)(off - dy * w);
+        int tile = (row0 + (int)dy) * p.tiles_x + x;
+        for (uint32_t j = lo; j < hi; ++j) {
+          const uint32_t mj = j - base;
+          s_map_tile[mj + (mj >> 5)] = (uint32_t)tile;
+          s_map_gid[mj + (mj >> 5)] = gid;
+          ++tile;
+          if (++x == (int)rc.z) {
+            x = rc.x;
+            tile += p.tiles_x - (int)w;
+          }
+        }
+      }
+      __syncwarp();
+      for (uint32_t q0 = base; q0 < wend; q0 += 32) {
+        const uint32_t mj = q0 - base + lane;
+        const bool valid = q0 + lane < wend;
+        const uint32_t tile = valid ? s_map_tile[mj + (mj >> 5)] : (0x80000000u | lane);
+        const unsigned m = __match_any_sync(0xffffffffu, tile);
+        uint32_t cur = 0u;
+        if (valid) {
+          cur = s_cur[tile];
+          const uint32_t pos = cur + (uint32_t)__popc(m & below);
+          if (pos < p.capacity) vals[pos] = s_map_gid[mj + (mj >> 5)];
+        }
+        __syncwarp();
+        if (valid && (m >> lane) == 1u) s_cur[tile] = cur + (uint32_t)__popc(m);
+        __syncwarp();
+      }
+    }
+  }
+}
+
+// keys[i] = (tile << 32) | depth bits of the Gaussian vals[i]: the tile is the last range
+// starting at or before i (ranges are contiguous, so that range holds i).
+__global__ void materialize_keys_kernel(const uint2 *__restrict__ ranges, int n_ranges,
                                         const uint32_t *__restrict__ vals,
                                         const float *__restrict__ rec, int n, int n_tiles,
                                         uint32_t count, uint64_t *__restrict__ keys) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += gridDim.x * blockDim.x) {
-    const uint32_t tile = tile_keys[i];
-    const uint32_t eye = tile / (uint32_t)n_tiles;
+    int lo = 0, hi = n_ranges;   // ranges[lo].x <= i < ranges[hi].x (hi = n_ranges: none)
+    while (hi - lo > 1) {
+      const int mid = (lo + hi) >> 1;
+      if (ranges[mid].x <= i) lo = mid;
+      else hi = mid;
+    }
+    const uint32_t eye = (uint32_t)lo / (uint32_t)n_tiles;
     const uint32_t g = min(vals[i], (uint32_t)(n - 1));
     const float depth = rec[((size_t)eye * n + g) * kRec + 9];
-    keys[i] = ((uint64_t)tile << 32) | __float_as_uint(depth);
+    keys[i] = ((uint64_t)lo << 32) | __float_as_uint(depth);
   }
 }
 
@@ -376,71 +402,115 @@ int grid_for(size_t work, int per_block) {
 
 }  // namespace
 
-size_t emit_lookback_bytes(int n_entries) {
-  return sizeof(unsigned long long) * (size_t)((n_entries + kEmitEntries - 1) / kEmitEntries + 1);
-}
-
-cudaError_t launch_emit(const EmitParams &p, const uint32_t *entries, const uint32_t *touched,
-                        const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
-                        unsigned long long *blk, uint32_t *done_counter, cudaStream_t s) {
-  if (p.n_entries <= 0) return cudaSuccess;
-  const int blocks = (p.n_entries + kEmitEntries - 1) / kEmitEntries;
-  emit_count_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, blk, done_counter);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  emit_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, rect, tile_keys, vals, blk);
-  return cudaGetLastError();
-}
-
-size_t tile_grid_cells(int n_eyes, int tiles_x, int tiles_y) {
-  return (size_t)n_eyes * (tiles_x + 1) * (tiles_y + 1);
-}
-
-size_t tile_scan_smem_bytes(int n_eyes, int tiles_x, int tiles_y) {
-  return sizeof(uint32_t) * tile_grid_cells(n_eyes, tiles_x, tiles_y);
-}
-
-int tile_count_blocks() {
+BinParams bin_params(int n_eyes, int n, int tiles_x, int tiles_y, uint32_t capacity) {
+  BinParams p{};
+  p.n_eyes = n_eyes;
+  p.n = n;
+  p.n_entries = n_eyes * n;
+  p.tiles_x = tiles_x;
+  p.tiles_y = tiles_y;
+  p.n_tiles = tiles_x * tiles_y;
+  p.capacity = capacity;
+  const long long n_ranges = (long long)n_eyes * p.n_tiles;
+  p.row = (int)((n_ranges + 3) / 4 * 4);
+  // one bin_emit warp per chunk: as many chunks as warps fit on the device at once (their
+  // shared memory), at least 256 entries each, at most kMaxChunks and kMaxChunkCells cells
   int dev = 0, sms = 152;
-  if (cudaGetDevice(&dev) == cudaSuccess)
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  return sms;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const long long per_warp = (long long)bin_emit_smem_bytes(n_eyes, tiles_x, tiles_y) +
+                             2 * sizeof(uint32_t) * kMapPad + 1024;
+  long long warps_per_sm = (228ll * 1024) / per_warp;
+  if (warps_per_sm > 32) warps_per_sm = 32;
+  if (warps_per_sm < 1) warps_per_sm = 1;
+  long long max_chunks = kMaxChunkCells / (p.row > 0 ? p.row : 1);
+  if (max_chunks > kMaxChunks) max_chunks = kMaxChunks;
+  if (max_chunks > warps_per_sm * sms) max_chunks = warps_per_sm * sms;
+  if (max_chunks < 1) max_chunks = 1;
+  long long chunks = ((long long)p.n_entries + 255) / 256;
+  if (chunks > max_chunks) chunks = max_chunks;
+  if (chunks < 1) chunks = 1;
+  long long L = ((long long)p.n_entries + chunks - 1) / chunks;
+  L = (L + 31) / 32 * 32;
+  if (L < 32) L = 32;
+  p.chunk = (int)L;
+  p.n_chunks = (int)(((long long)p.n_entries + L - 1) / L);
+  if (p.n_chunks < 1) p.n_chunks = 1;
+  return p;
 }
 
-cudaError_t launch_tile_count(const TileScanParams &p, const ushort4 *rect, uint32_t *partials,
-                              uint32_t *grid, cudaStream_t s) {
-  const size_t cells = tile_grid_cells(p.n_eyes, p.tiles_x, p.tiles_y);
-  const size_t smem = sizeof(uint32_t) * cells;
-  cudaError_t e = cudaFuncSetAttribute(tile_count_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const int parts = tile_count_blocks();
-  tile_count_kernel<<<parts, kCountThreads, smem, s>>>(p, rect, partials);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(grid, 0, sizeof(uint32_t) * cells, s);
-  if (e != cudaSuccess) return e;
-  const dim3 rb((unsigned)((cells + 255) / 256), (unsigned)((parts + kReduceParts - 1) / kReduceParts));
-  tile_reduce_kernel<<<rb, 256, 0, s>>>(partials, parts, (int)cells, grid);
+size_t bin_chunk_cells(const BinParams &p) { return (size_t)p.n_chunks * (size_t)p.row; }
+
+size_t bin_emit_smem_bytes(int n_eyes, int tiles_x, int tiles_y) {
+  return sizeof(uint32_t) * (((size_t)n_eyes * tiles_x * tiles_y + 3) / 4 * 4);
+}
+
+size_t bin_smem_bytes(int n_eyes, int tiles_x, int tiles_y) {
+  const size_t a = bin_count_smem_bytes(n_eyes, tiles_x, tiles_y);
+  const size_t b = bin_emit_smem_bytes(n_eyes, tiles_x, tiles_y) + 2 * sizeof(uint32_t) * kMapPad;
+  return a > b ? a : b;
+}
+
+size_t bin_count_smem_bytes(int n_eyes, int tiles_x, int tiles_y) {
+  return sizeof(uint32_t) * (size_t)n_eyes * tiles_x * tiles_y;
+}
+
+size_t bin_plan_lookback_bytes(int n_entries) {
+  return sizeof(unsigned long long) * (size_t)((n_entries + kPlanEntries - 1) / kPlanEntries + 1);
+}
+
+cudaError_t launch_bin_plan(const BinParams &p, const uint32_t *entries, const uint32_t *touched,
+                            const unsigned long long *inst_total, unsigned long long *lookback,
+                            uint32_t *bounds, uint32_t *status, cudaStream_t s) {
+  const int blocks = p.n_entries > 0 ? (p.n_entries + kPlanEntries - 1) / kPlanEntries : 1;
+  bin_plan_kernel<<<blocks, kPlanThreads, 0, s>>>(p, entries, touched, inst_total, lookback, bounds,
+                                                  status);
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_scan(const TileScanParams &p, const uint32_t *grid, uint2 *ranges,
-                             uint32_t *tile_hist, uint32_t *counts, uint32_t *status,
-                             cudaStream_t s) {
-  const size_t smem = tile_scan_smem_bytes(p.n_eyes, p.tiles_x, p.tiles_y);
-  cudaError_t e = cudaFuncSetAttribute(tile_scan_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+cudaError_t launch_bin_count(const BinParams &p, const uint32_t *entries, const ushort4 *rect,
+                             const uint32_t *bounds, uint32_t *h, cudaStream_t s) {
+  const size_t smem = bin_count_smem_bytes(p.n_eyes, p.tiles_x, p.tiles_y);
+  cudaError_t e = cudaFuncSetAttribute(bin_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
   if (e != cudaSuccess) return e;
-  tile_scan_kernel<<<1, 1024, smem, s>>>(p, grid, ranges, tile_hist, counts, status);
+  bin_count_kernel<<<p.n_chunks, kCountThreads, smem, s>>>(p, entries, rect, bounds, h);
   return cudaGetLastError();
 }
 
-cudaError_t launch_materialize_keys(const uint32_t *tile_keys, const uint32_t *vals,
+size_t bin_lookback_bytes(int n_eyes, int n_tiles) {
+  return sizeof(unsigned long long) * (size_t)((n_eyes * n_tiles + 31) / 32 + 1);
+}
+
+cudaError_t launch_bin_offsets(const BinParams &p, uint32_t *h, unsigned long long *lookback,
+                               uint2 *ranges, uint32_t *counts, uint32_t *status, cudaStream_t s) {
+  const int n_ranges = p.n_eyes * p.n_tiles;
+  const int blocks = (n_ranges + 31) / 32;
+  const size_t smem = sizeof(uint32_t) * kOffsetThreads * (size_t)((p.n_chunks + 31) / 32);
+  cudaError_t e = cudaFuncSetAttribute(bin_offsets_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  bin_offsets_kernel<<<blocks > 0 ? blocks : 1, kOffsetThreads, smem, s>>>(p, h, lookback, ranges,
+                                                                           counts, status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_bin_emit(const BinParams &p, const uint32_t *entries, const ushort4 *rect,
+                            const uint32_t *bounds, const uint32_t *h, uint32_t *vals,
+                            cudaStream_t s) {
+  if (p.n_entries <= 0 || p.capacity == 0) return cudaSuccess;
+  const size_t smem = bin_emit_smem_bytes(p.n_eyes, p.tiles_x, p.tiles_y);
+  cudaError_t e = cudaFuncSetAttribute(bin_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  bin_emit_kernel<<<p.n_chunks, 32, smem, s>>>(p, entries, rect, bounds, h, vals);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_materialize_keys(const uint2 *ranges, int n_ranges, const uint32_t *vals,
                                     const float *rec, int n, int n_tiles, uint32_t count,
                                     uint64_t *keys, cudaStream_t s) {
-  if (count == 0 || n <= 0) return cudaSuccess;
-  materialize_keys_kernel<<<grid_for(count, 256), 256, 0, s>>>(tile_keys, vals, rec, n, n_tiles,
+  if (count == 0 || n <= 0 || n_ranges <= 0) return cudaSuccess;
+  materialize_keys_kernel<<<grid_for(count, 256), 256, 0, s>>>(ranges, n_ranges, vals, rec, n, n_tiles,
                                                                count, keys);
   return cudaGetLastError();
 }

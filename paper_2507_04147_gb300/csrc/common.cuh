@@ -116,39 +116,48 @@ cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint
                         const uint32_t *d_count, size_t capacity, int key_bits, void *workspace,
                         uint32_t *status, bool *result_in_alt, cudaStream_t s);
 
-// Emission of the tile instances of the depth-ordered entries (see binning.cu).
-struct EmitParams {
-  int n, n_entries, n_tiles, tiles_x;
+// Tile binning of the depth-ordered entries (see binning.cu): per-chunk tile counts
+// (bin_count), tile ranges and per-chunk starts (bin_offsets), and the ordered placement of
+// every instance at its final slot (bin_emit).
+constexpr int kBinMaxChunks = 1536;   // bin_offsets stages chunks x 128 bytes per CTA
+struct BinParams {
+  int n_eyes, n, n_entries, tiles_x, tiles_y, n_tiles;
+  int chunk;                // mean entries per chunk (sizing; bin_plan sets the bounds)
+  int n_chunks;
+  int row;                  // u32 cells per chunk row of h: tiles rounded up to 4 (16 bytes)
   uint32_t capacity;
 };
-size_t emit_lookback_bytes(int n_entries);
-cudaError_t launch_emit(const EmitParams &p, const uint32_t *entries, const uint32_t *touched,
-                        const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
-                        unsigned long long *blk, uint32_t *done_counter, cudaStream_t s);
+BinParams bin_params(int n_eyes, int n, int tiles_x, int tiles_y, uint32_t capacity);
+size_t bin_chunk_cells(const BinParams &p);          // u32 cells of h: chunks x row
+// Shared memory of bin_count (the difference grids) and of bin_emit (the cursors); the
+// larger of the two, with bin_emit's static part, is checked against the device up front.
+size_t bin_count_smem_bytes(int n_eyes, int tiles_x, int tiles_y);
+size_t bin_emit_smem_bytes(int n_eyes, int tiles_x, int tiles_y);
+size_t bin_smem_bytes(int n_eyes, int tiles_x, int tiles_y);
+// bounds[0..n_chunks] <- chunk c = entries [bounds[c], bounds[c + 1]), about equal
+// instance counts; inst_total is the render's instance total (preprocess), lookback
+// (bin_plan_lookback_bytes, zeroed by the caller) chains the CTAs' sums.
+size_t bin_plan_lookback_bytes(int n_entries);
+cudaError_t launch_bin_plan(const BinParams &p, const uint32_t *entries, const uint32_t *touched,
+                            const unsigned long long *inst_total, unsigned long long *lookback,
+                            uint32_t *bounds, uint32_t *status, cudaStream_t s);
+// h[c][r] <- chunk c's instances of tile r.
+cudaError_t launch_bin_count(const BinParams &p, const uint32_t *entries, const ushort4 *rect,
+                             const uint32_t *bounds, uint32_t *h, cudaStream_t s);
+// ranges, h[c][r] <- start slot of chunk c's instances of tile r, counts[0] kept, [1] first
+// eye, [3] total; the capacity status when the total exceeds the capacity.  lookback
+// (bin_lookback_bytes, zeroed by the caller) chains the CTAs' sums.
+size_t bin_lookback_bytes(int n_eyes, int n_tiles);
+cudaError_t launch_bin_offsets(const BinParams &p, uint32_t *h, unsigned long long *lookback,
+                               uint2 *ranges, uint32_t *counts, uint32_t *status, cudaStream_t s);
+// vals[slot] <- Gaussian index of every instance, each tile's run in entry order.
+cudaError_t launch_bin_emit(const BinParams &p, const uint32_t *entries, const ushort4 *rect,
+                            const uint32_t *bounds, const uint32_t *h, uint32_t *vals,
+                            cudaStream_t s);
 
-// Per-tile instance counts without enumerating instances: every tile rectangle adds
-// +1/-1/-1/+1 at its four corners in a per-eye 2-D difference grid (tiles_y+1 rows of
-// tiles_x+1), accumulated per CTA in shared memory and written out as partial grids
-// (no global atomics), then summed by a reduction; the 2-D prefix sum is the count.
-struct TileScanParams {
-  int n_eyes, n, tiles_x, tiles_y, n_tiles;
-  uint32_t capacity;
-  SortPlan tile_plan;
-};
-int tile_count_blocks();
-size_t tile_grid_cells(int n_eyes, int tiles_x, int tiles_y);
-cudaError_t launch_tile_count(const TileScanParams &p, const ushort4 *rect, uint32_t *partials,
-                              uint32_t *grid, cudaStream_t s);
-// One CTA: counts -> ranges (exclusive scan over tiles, eye-major), tile-sort histograms and
-// totals (counts[0] kept, [1..2] per eye, [3] total).  Grids that do not fit in shared
-// memory are rejected by the caller up front.
-size_t tile_scan_smem_bytes(int n_eyes, int tiles_x, int tiles_y);
-cudaError_t launch_tile_scan(const TileScanParams &p, const uint32_t *grid, uint2 *ranges,
-                             uint32_t *tile_hist, uint32_t *counts, uint32_t *status,
-                             cudaStream_t s);
-
-// keys[j] = tile_keys[j] << 32 | depth bits of the Gaussian vals[j] (for inspection).
-cudaError_t launch_materialize_keys(const uint32_t *tile_keys, const uint32_t *vals,
+// keys[j] = tile << 32 | depth bits of the Gaussian vals[j] (for inspection), the tile of
+// slot j found in the ranges.
+cudaError_t launch_materialize_keys(const uint2 *ranges, int n_ranges, const uint32_t *vals,
                                     const float *rec, int n, int n_tiles, uint32_t count,
                                     uint64_t *keys, cudaStream_t s);
 

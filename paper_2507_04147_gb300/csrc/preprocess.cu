@@ -144,6 +144,7 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
   const int i = i0 + t;
   if (blockIdx.x == 0 && t == 0) depth_count[0] = (uint32_t)(p.n_eyes * n);
   uint32_t kmin = 0xffffffffu, kmax = 0u;   // depth-key range of this thread's visible entries
+  uint32_t inst = 0u;                        // tile instances of this thread's entries
   if (i < n) {
     const float mx = s_mean[3 * t], my = s_mean[3 * t + 1], mz = s_mean[3 * t + 2];
     // activation shared by the eyes
@@ -259,6 +260,7 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
       o4[2] = o2;
       rect[(size_t)e * n + i] = rc;
       touched[(size_t)e * n + i] = n_touched;
+      inst += n_touched;
       dkeys[(size_t)e * n + i] = vis ? __float_as_uint(tz) : 0xffffffffu;
       if (vis) {
         kmin = min(kmin, __float_as_uint(tz));
@@ -268,26 +270,34 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
   }
   // range of the visible depth keys: depth_count[1] = ~min, depth_count[3] = max (the counters
   // start at zero every render, so the minimum is kept as the maximum of the complement)
+  // and the render's instance total: depth_count[4..5] as one 64-bit counter
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
     kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+    inst += __shfl_xor_sync(0xffffffffu, inst, o);
   }
   __shared__ uint32_t s_range[2];
+  __shared__ unsigned long long s_inst;
   if (t == 0) {
     s_range[0] = 0u;
     s_range[1] = 0u;
+    s_inst = 0ull;
   }
   __syncthreads();
-  if ((t & 31) == 0 && kmax != 0u) {
-    atomicMax(&s_range[0], ~kmin);
-    atomicMax(&s_range[1], kmax);
+  if ((t & 31) == 0) {
+    if (kmax != 0u) {
+      atomicMax(&s_range[0], ~kmin);
+      atomicMax(&s_range[1], kmax);
+    }
+    if (inst) atomicAdd(&s_inst, (unsigned long long)inst);
   }
   __syncthreads();
   if (t == 0 && s_range[1] != 0u) {
     atomicMax(depth_count + 1, s_range[0]);
     atomicMax(depth_count + 3, s_range[1]);
   }
+  if (t == 0 && s_inst) atomicAdd(reinterpret_cast<unsigned long long *>(depth_count + 4), s_inst);
 }
 
 }  // namespace
