@@ -37,7 +37,7 @@ if ROOT not in sys.path:
 METRIC = "stereo foveated frame ms (p50/p99) & FPS vs full-res on same GB300; PSNR vs full"
 UNIT = "stereo frames/s"
 L2_FLUSH_BYTES = 256 << 20
-STAGES = ("preprocess", "depth_sort", "tile_scan", "emit", "tile_sort", "composite")
+STAGES = ("preprocess", "depth_sort", "bin", "emit", "composite")
 SMS_GB300 = 152
 FP32_LANES_PER_SM = 128
 
@@ -787,16 +787,16 @@ def roofline(w, stats, stage_ms, n_frames, eyes, tile=16):
     evals = stats["evaluations"] / max(n_frames, 1)
     n_ent = n * eyes
     tiles = eyes * ((c0.width + tile - 1) // tile) * ((c0.height + tile - 1) // tile)
-    tile_passes = max(1, math.ceil(max(1, math.ceil(math.log2(max(tiles, 2)))) / 8))
     algo = {
         # bytes: Gaussian parameters once; records + rects + touched + depth keys per eye
         "preprocess": ("hbm", n * 4 * (3 + 3 + 4 + 1 + 3 * K) + n_ent * (48 + 8 + 4 + 4)),
         # 4 passes of (key, value) read + write over the (eye, Gaussian) entries
         "depth_sort": ("hbm", n_ent * 4 * 16),
-        "tile_scan": ("hbm", tiles * 16),
-        # entries, counts and rectangles read; (tile, index) written per instance
-        "emit": ("hbm", n_ent * 16 + inst * 8),
-        "tile_sort": ("hbm", inst * 16 * tile_passes),
+        # entries and tile counts read (plan), entries and rectangles read (counts), ranges
+        # written
+        "bin": ("hbm", n_ent * 20 + tiles * 8),
+        # entries and rectangles read; the Gaussian index of every instance written
+        "emit": ("hbm", n_ent * 12 + inst * 4),
         # flops: 14 per (pixel, Gaussian) evaluation (offset, quadratic form, alpha)
         "composite": ("alu", evals * 14.0),
     }

@@ -326,11 +326,10 @@ int a3fr_set_keep_aux(a3fr_scene *scene, int keep);
 /* Stages of a render timed by a3fr_set_stage_timing, in launch order. */
 #define A3FR_STAGE_PREPROCESS 0  /* projection, EWA, SH colour, tile rectangles, histograms */
 #define A3FR_STAGE_DEPTH_SORT 1  /* onesweep sort of the (eye, Gaussian) entries by depth */
-#define A3FR_STAGE_TILE_SCAN 2   /* per-tile instance counts -> tile ranges */
-#define A3FR_STAGE_EMIT 3        /* (tile, Gaussian) instances in depth order */
-#define A3FR_STAGE_TILE_SORT 4   /* stable onesweep sort of the instances by tile */
-#define A3FR_STAGE_COMPOSITE 5   /* level map + front-to-back blending + inheritance */
-#define A3FR_N_STAGES 6
+#define A3FR_STAGE_BIN 2         /* chunk plan, per-chunk tile counts, tile ranges, chunk starts */
+#define A3FR_STAGE_EMIT 3        /* every (tile, Gaussian) instance to its slot, depth order */
+#define A3FR_STAGE_COMPOSITE 4   /* level map + front-to-back blending + inheritance */
+#define A3FR_N_STAGES 5
 
 /* Record CUDA events around every stage of the next renders on their stream, keeping the
  * last `ring` renders (0 turns timing off and frees the events). */

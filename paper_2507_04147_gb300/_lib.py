@@ -18,7 +18,7 @@ STATUS_TIMEOUT = 2
 
 NOALLOC_MAX_PAIRS = 262144
 
-STAGES = ("preprocess", "depth_sort", "tile_scan", "emit", "tile_sort", "composite")
+STAGES = ("preprocess", "depth_sort", "bin", "emit", "composite")
 
 BUF_RECORDS, BUF_RECTS, BUF_KEYS, BUF_VALUES, BUF_RANGES, BUF_LEVELS, BUF_T_FINAL, BUF_N_CONTRIB, BUF_DEPTH = range(1, 10)
 

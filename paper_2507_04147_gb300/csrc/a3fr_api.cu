@@ -435,7 +435,7 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
   }
   const uint32_t *entries = s->dvals[depth_plan.passes % 2];
   // per-chunk tile counts -> tile ranges, per-chunk starts, totals
-  A3FR_CHECK(mark(s, A3FR_STAGE_TILE_SCAN, stream));
+  A3FR_CHECK(mark(s, A3FR_STAGE_BIN, stream));
   BinParams bp = bin_params(eyes, n, s->TX, s->TY, (uint32_t)s->capacity);
   A3FR_CHECK(launch_bin_plan(bp, entries, s->touched, inst_total, plan_lb, bounds, s->status, stream));
   A3FR_CHECK(launch_bin_count(bp, entries, s->rect, bounds, s->bin_h, stream));
@@ -463,8 +463,6 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
     A3FR_CHECK(launch_bin_emit(bp, entries, s->rect, bounds, s->bin_h, s->vals, stream));
     ++*launches;
   }
-  // the instances are already in tile order: the tile-sort stage is empty
-  A3FR_CHECK(mark(s, A3FR_STAGE_TILE_SORT, stream));
   return A3FR_OK;
 }
 

@@ -167,6 +167,34 @@ __device__ __forceinline__ float4 support_box(float u, float v, float ca, float 
   return make_float4(u - ex, u + ex, v - ey, v + ey);
 }
 
+// A support box rounded outward to whole pixels in 16 bits (clamped to +-kBoxFar, which no
+// pixel reaches): a superset of the float box, so the integer test rejects no more.
+constexpr short kBoxFar = 30000;
+__device__ __forceinline__ short4 int_box(float4 b) {
+  auto lo = [](float v) { return (short)fminf(fmaxf(floorf(v), -(float)kBoxFar), (float)kBoxFar); };
+  auto hi = [](float v) { return (short)fminf(fmaxf(ceilf(v), -(float)kBoxFar), (float)kBoxFar); };
+  return make_short4(lo(b.x), hi(b.y), lo(b.z), hi(b.w));
+}
+
+// Whether a Gaussian can reach alpha >= 1/255 at some point of the rectangle [x0, x1] x
+// [y0, y1] (pixel coordinates relative to its centre): the log2 falloff f = A x^2 + B x y +
+// C y^2 (A, C < 0: concave) is largest at the centre if the rectangle holds it, else on an
+// edge, where the best point along the edge is the clamped stationary point.  thr is the
+// falloff alpha = 1/255 needs, lowered by a margin (0.01 in log2) far above the rounding
+// of f, of the stationary points and of the kernel's own alpha, so a Gaussian it rejects
+// has alpha < 1/255 at every pixel of the rectangle: rejecting it changes no output bit.
+__device__ __forceinline__ bool falloff_reaches(float A, float B, float C, float thr, float x0, float x1,
+                                                float y0, float y1) {
+  if (!(A < 0.0f) || !(C < 0.0f) || !(4.0f * A * C > 1.0001f * B * B)) return true;   // not concave
+  if (x0 <= 0.0f && x1 >= 0.0f && y0 <= 0.0f && y1 >= 0.0f) return thr <= 0.0f;
+  const float ky = __fdividef(-B, 2.0f * C), kx = __fdividef(-B, 2.0f * A);
+  auto f = [&](float x, float y) { return (A * x + B * y) * x + C * y * y; };
+  const float ya = fminf(fmaxf(ky * x0, y0), y1), yb = fminf(fmaxf(ky * x1, y0), y1);
+  const float xa = fminf(fmaxf(kx * y0, x0), x1), xb = fminf(fmaxf(kx * y1, x0), x1);
+  const float best = fmaxf(fmaxf(f(x0, ya), f(x1, yb)), fmaxf(f(xa, y0), f(xb, y1)));
+  return best >= thr;
+}
+
 // Barrier of a staging group of `size` threads (64, 128 or 256) with barrier id `bar`
 // (1..4).  The ids are literals so the kernel reserves 5 hardware barriers, not 16 (the
 // per-SM barrier budget would otherwise cap residency at 4 CTAs).
@@ -445,8 +473,9 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
   __shared__ float4 s_geo[NB];
   __shared__ float2 s_cz[NB];
   __shared__ float4 s_rgb[NB];
-  __shared__ float4 s_box[NB];
-  __shared__ uint16_t s_hits[kThreads / 32][NB];   // per warp: batch slots whose box meets its patch
+  __shared__ short4 s_box[NB];                     // support box, outward-rounded pixels
+  __shared__ float s_thr[NB];                      // log2 falloff needed for alpha = 1/255
+  __shared__ uint16_t s_hits[kThreads / 32][NB];   // per warp: batch slots that reach its patch
   __shared__ int s_done[kThreads / 32];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int n_ranges = p.n_eyes * p.n_tiles;
@@ -529,24 +558,32 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
         s_geo[slot] = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
         s_cz[slot] = make_float2(__fmul_rn(-0.5f * kLog2e, b.x), c.y);
         s_rgb[slot] = make_float4(b.z, b.w, c.x, b.y);
-        s_box[slot] = support_box(a.x, a.y, a.z, a.w, b.x, b.y);
+        s_box[slot] = int_box(support_box(a.x, a.y, a.z, a.w, b.x, b.y));
+        s_thr[slot] = -__log2f(255.0f * b.y) - 0.01f;
       } else if (slot < ((cnt + 3u) & ~3u)) {
         s_geo[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
         s_cz[slot] = make_float2(0.0f, 0.0f);
         s_rgb[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        s_box[slot] = make_float4(1e30f, -1e30f, 1e30f, -1e30f);
+        s_box[slot] = make_short4(kBoxFar, -kBoxFar, kBoxFar, -kBoxFar);
+        s_thr[slot] = 1.0f;
       }
     }
     __syncthreads();
     if (!__all_sync(0xffffffffu, done)) {
-      // the warp's hit list: 32 boxes tested per step, slots kept in list order
+      // the warp's hit list: 32 Gaussians tested per step (support box, then the falloff
+      // over the patch), slots kept in list order
       int n_hit = 0;
       for (uint32_t base = 0; base < cnt; base += 32) {
         const uint32_t k = base + (uint32_t)lane;
         bool hit = false;
         if (k < cnt) {
-          const float4 box = s_box[k];
-          hit = !(box.y < wx0 || box.x > wx1 || box.w < wy0 || box.z > wy1);
+          const short4 box = s_box[k];
+          hit = !((float)box.y < wx0 || (float)box.x > wx1 || (float)box.w < wy0 || (float)box.z > wy1);
+          if (hit) {
+            const float4 geo = s_geo[k];
+            hit = falloff_reaches(geo.z, geo.w, s_cz[k].x, s_thr[k], wx0 - geo.x, wx1 - geo.x,
+                                  wy0 - geo.y, wy1 - geo.y);
+          }
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) s_hits[warp][n_hit + __popc(m & ((1u << lane) - 1u))] = (uint16_t)k;
