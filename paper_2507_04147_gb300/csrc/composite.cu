@@ -579,15 +579,32 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
         if (k < cnt) {
           const short4 box = s_box[k];
           hit = !((float)box.y < wx0 || (float)box.x > wx1 || (float)box.w < wy0 || (float)box.z > wy1);
-          if (hit) {
-            const float4 geo = s_geo[k];
-            hit = falloff_reaches(geo.z, geo.w, s_cz[k].x, s_thr[k], wx0 - geo.x, wx1 - geo.x,
-                                  wy0 - geo.y, wy1 - geo.y);
-          }
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
         if (hit) s_hits[warp][n_hit + __popc(m & ((1u << lane) - 1u))] = (uint16_t)k;
         n_hit += __popc(m);
+      }
+      __syncwarp();
+      // second pass over the box hits, 32 at a time with full warps: keep those whose
+      // falloff reaches the threshold on the patch (compacted in place, list order kept)
+      {
+        int n_keep = 0;
+        for (int base = 0; base < n_hit; base += 32) {
+          const int i = base + lane;
+          int k = 0;
+          bool keep = false;
+          if (i < n_hit) {
+            k = s_hits[warp][i];
+            const float4 geo = s_geo[k];
+            keep = falloff_reaches(geo.z, geo.w, s_cz[k].x, s_thr[k], wx0 - geo.x, wx1 - geo.x,
+                                   wy0 - geo.y, wy1 - geo.y);
+          }
+          __syncwarp();
+          const unsigned m = __ballot_sync(0xffffffffu, keep);
+          if (keep) s_hits[warp][n_keep + __popc(m & ((1u << lane) - 1u))] = (uint16_t)k;
+          n_keep += __popc(m);
+        }
+        n_hit = n_keep;
       }
       __syncwarp();
       const uint32_t pos0 = start - range.x + 1;
