@@ -221,12 +221,14 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
           radius = ceilf(fm(3.0f, fsq(lam)));
           u = fa(fm(c.fx, txz), c.cx);
           v = fa(fm(c.fy, tyz), c.cy);
-          const float fb = static_cast<float>(p.tile);
+          // x / tile as x * (1 / tile): the tile (16 or 32) is a power of two, so both are the
+          // exact quotient
+          const float rb = 1.0f / static_cast<float>(p.tile);
           const float ftx = static_cast<float>(p.tiles_x), fty = static_cast<float>(p.tiles_y);
-          const float fx0 = fminf(ftx, fmaxf(0.0f, floorf(fdv(fs(u, radius), fb))));
-          const float fx1 = fminf(ftx, fmaxf(0.0f, fa(floorf(fdv(fa(u, radius), fb)), 1.0f)));
-          const float fy0 = fminf(fty, fmaxf(0.0f, floorf(fdv(fs(v, radius), fb))));
-          const float fy1 = fminf(fty, fmaxf(0.0f, fa(floorf(fdv(fa(v, radius), fb)), 1.0f)));
+          const float fx0 = fminf(ftx, fmaxf(0.0f, floorf(fm(fs(u, radius), rb))));
+          const float fx1 = fminf(ftx, fmaxf(0.0f, fa(floorf(fm(fa(u, radius), rb)), 1.0f)));
+          const float fy0 = fminf(fty, fmaxf(0.0f, floorf(fm(fs(v, radius), rb))));
+          const float fy1 = fminf(fty, fmaxf(0.0f, fa(floorf(fm(fa(v, radius), rb)), 1.0f)));
           const int x0 = static_cast<int>(fx0), x1 = static_cast<int>(fx1);
           const int y0 = static_cast<int>(fy0), y1 = static_cast<int>(fy1);
           vis = x0 < x1 && y0 < y1;
