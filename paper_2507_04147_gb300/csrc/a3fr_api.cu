@@ -62,6 +62,14 @@ struct a3fr_scene {
   uint32_t *dvals[2] = {nullptr, nullptr};   // depth-sorted entries e * n + i
   uint2 *ranges = nullptr;
   uint32_t *bin_h = nullptr;                 // per-chunk tile counts, then starts (binning.cu)
+  // the sort-based binning (binning_sorted.cu), for renders with more than
+  // kBinDirectMaxTiles tiles: difference grids, instance tile keys, the sort's second buffers
+  bool sorted_bin = false;
+  uint32_t *tile_partials = nullptr;
+  uint32_t *tkeys[2] = {nullptr, nullptr};
+  uint32_t *vals_alt = nullptr;
+  uint32_t *tile_lb = nullptr;               // the tile sort's look-back (capacity-sized)
+  size_t tile_lb_bytes = 0;
   uint32_t *plan = nullptr;                  // tiles bucketed by level (foveated composite)
   uint8_t *levels = nullptr;
   float *t_final = nullptr;
@@ -144,24 +152,37 @@ namespace {
 int n_eyes_of(const a3fr_scene *s) { return s->cam_set[1] ? 2 : (s->cam_set[0] ? 1 : 0); }
 
 constexpr int kDepthPasses = 4;   // 32-bit depth keys, 8-bit digits
+// Above this many tiles (all eyes) bin_emit's per-warp cursor table (4 B per tile) leaves
+// fewer than ~8 warps per SM, and the sort-based binning is faster.
+constexpr int kBinDirectMaxTiles = 6144;
+
+int tile_bits_for(int n_ranges) {
+  int bits = 1;
+  while ((1ll << bits) < (long long)n_ranges) ++bits;
+  return bits;
+}
 
 
 // Byte offsets inside frame_ws; everything in it starts at zero every render.
 struct FrameLayout {
-  size_t counts = 0;                 // counts[0..7] u32, [8..9] the u64 instance total
+  size_t counts = 0;                 // counts[0..7] u32 ([6]: emit's block counter), [8..9] the u64 instance total
   size_t depth_hist = 64;            // kMaxSortPasses x 256 u32
   size_t depth_ctr = 64 + 8192;      // kMaxSortPasses u32 (+pad)
-  size_t depth_lb = 0, bin_lb = 0, plan_lb = 0, bounds = 0, total = 0;
+  size_t tile_hist = 64 + 8192 + 64; // sort-based binning: the tile sort's histograms, counters
+  size_t tile_ctr = 64 + 8192 + 64 + 8192;
+  size_t depth_lb = 0, bin_lb = 0, plan_lb = 0, bounds = 0, emit_lb = 0, tile_diff = 0, total = 0;
 };
 
-FrameLayout frame_layout(size_t entries, int eyes, int n_tiles) {
+FrameLayout frame_layout(size_t entries, int eyes, int tiles_x, int tiles_y) {
   FrameLayout L;
   auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
-  L.depth_lb = up(L.depth_ctr + 64);
+  L.depth_lb = up(L.tile_ctr + 64);
   L.bin_lb = up(L.depth_lb + onesweep_lookback_bytes(entries, kDepthPasses, false, false));
-  L.plan_lb = up(L.bin_lb + bin_lookback_bytes(eyes, n_tiles));
+  L.plan_lb = up(L.bin_lb + bin_lookback_bytes(eyes, tiles_x * tiles_y));
   L.bounds = up(L.plan_lb + bin_plan_lookback_bytes((int)entries));
-  L.total = up(L.bounds + sizeof(uint32_t) * (kBinMaxChunks + 1));
+  L.emit_lb = up(L.bounds + sizeof(uint32_t) * (kBinMaxChunks + 1));
+  L.tile_diff = up(L.emit_lb + emit_lookback_bytes((int)entries));
+  L.total = up(L.tile_diff + sizeof(uint32_t) * tile_grid_cells(eyes, tiles_x, tiles_y));
   return L;
 }
 
@@ -175,6 +196,7 @@ void free_frame_buffers(a3fr_scene *s) {
   }
   dfree(s->ranges);
   dfree(s->bin_h);
+  dfree(s->tile_partials);
   dfree(s->plan);
   dfree(s->cur_level);
   s->round_ready = false;
@@ -185,14 +207,38 @@ void free_frame_buffers(a3fr_scene *s) {
   s->alloc_eyes = 0;
 }
 
+void free_sort_buffers(a3fr_scene *s) {
+  for (int b = 0; b < 2; ++b) dfree(s->tkeys[b]);
+  dfree(s->vals_alt);
+  dfree(s->tile_lb);
+  s->tile_lb_bytes = 0;
+}
+
 void free_instance_buffers(a3fr_scene *s) {
   dfree(s->vals);
+  free_sort_buffers(s);
+}
+
+// The sort-based binning's instance buffers: tile keys (ping-pong), the second value buffer
+// and the tile sort's look-back, all sized by the capacity.
+int ensure_sort_buffers(a3fr_scene *s) {
+  if (!s->sorted_bin || s->capacity == 0) {
+    free_sort_buffers(s);
+    return A3FR_OK;
+  }
+  if (s->vals_alt) return A3FR_OK;
+  const int passes = sort_plan(tile_bits_for(s->alloc_eyes * s->n_tiles), 8).passes;
+  for (int b = 0; b < 2; ++b) A3FR_CHECK(cudaMalloc(&s->tkeys[b], sizeof(uint32_t) * s->capacity));
+  A3FR_CHECK(cudaMalloc(&s->vals_alt, sizeof(uint32_t) * s->capacity));
+  s->tile_lb_bytes = onesweep_lookback_bytes(s->capacity, passes, false, false);
+  A3FR_CHECK(cudaMalloc(&s->tile_lb, s->tile_lb_bytes));
+  return A3FR_OK;
 }
 
 // (Re)allocate frame_ws for the current entry count and capacity.
 int ensure_frame_ws(a3fr_scene *s) {
   const size_t entries = (size_t)s->alloc_eyes * (size_t)(s->desc.n > 0 ? s->desc.n : 1);
-  const FrameLayout L = frame_layout(entries, s->alloc_eyes, s->n_tiles);
+  const FrameLayout L = frame_layout(entries, s->alloc_eyes, s->TX, s->TY);
   if (s->frame_ws && s->frame_ws_bytes >= L.total) return A3FR_OK;
   if (s->frame_ws) {
     A3FR_CHECK(cudaDeviceSynchronize());
@@ -211,7 +257,11 @@ int alloc_instances(a3fr_scene *s, size_t capacity) {
   free_instance_buffers(s);
   s->capacity = capacity;
   if (capacity > 0) A3FR_CHECK(cudaMalloc(&s->vals, sizeof(uint32_t) * capacity));
-  if (s->alloc_eyes) return ensure_frame_ws(s);
+  if (s->alloc_eyes) {
+    const int rc = ensure_sort_buffers(s);
+    if (rc != A3FR_OK) return rc;
+    return ensure_frame_ws(s);
+  }
   return A3FR_OK;
 }
 
@@ -228,7 +278,9 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
     A3FR_CHECK(cudaGetDevice(&dev));
     A3FR_CHECK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
-    if (bin_smem_bytes(eyes, tx, ty) > (size_t)max_optin) return A3FR_ERR_INVALID_ARG;
+    s->sorted_bin = (long long)eyes * tx * ty > kBinDirectMaxTiles;
+    const size_t need = s->sorted_bin ? tile_scan_smem_bytes(eyes, tx, ty) + 9216 : bin_smem_bytes(eyes, tx, ty);
+    if (need > (size_t)max_optin) return A3FR_ERR_INVALID_ARG;
   }
   s->W = W;
   s->H = H;
@@ -244,8 +296,12 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
     A3FR_CHECK(cudaMalloc(&s->dvals[b], sizeof(uint32_t) * nn));
   }
   A3FR_CHECK(cudaMalloc(&s->ranges, sizeof(uint2) * (size_t)s->n_tiles * eyes));
-  A3FR_CHECK(cudaMalloc(&s->bin_h, sizeof(uint32_t) *
-                                       bin_chunk_cells(bin_params(eyes, n > 0 ? n : 1, s->TX, s->TY, 0))));
+  if (s->sorted_bin)
+    A3FR_CHECK(cudaMalloc(&s->tile_partials, sizeof(uint32_t) * (size_t)tile_count_blocks() *
+                                                 tile_grid_cells(eyes, s->TX, s->TY)));
+  else
+    A3FR_CHECK(cudaMalloc(&s->bin_h, sizeof(uint32_t) *
+                                         bin_chunk_cells(bin_params(eyes, n > 0 ? n : 1, s->TX, s->TY, 0))));
   A3FR_CHECK(cudaMalloc(&s->plan, plan_bytes(s->n_tiles * eyes)));
   A3FR_CHECK(cudaMalloc(&s->cur_level, (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMalloc(&s->levels, (size_t)s->n_tiles * eyes));
@@ -255,6 +311,8 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
   A3FR_CHECK(cudaMemset(s->ranges, 0, sizeof(uint2) * (size_t)s->n_tiles * eyes));
   A3FR_CHECK(cudaMemset(s->levels, 0, (size_t)s->n_tiles * eyes));
   s->alloc_eyes = eyes;
+  const int rc = ensure_sort_buffers(s);
+  if (rc != A3FR_OK) return rc;
   return ensure_frame_ws(s);
 }
 
@@ -397,12 +455,83 @@ PreParams pre_params(const a3fr_scene *s, int eyes) {
 // The precompute of a render: projection, depth sort, tile counts and ranges, emission and the
 // tile sort.  allow_resize: the first render of an automatic-capacity scene measures the
 // instance count (one host synchronisation) and sizes the instance buffers.
+// First render of an automatic-capacity scene: read the instance count once, size the
+// instance buffers for twice that, and fix the kept count and the status of this render.
+int size_instances(a3fr_scene *s, cudaStream_t stream) {
+  uint32_t cnt[8];
+  A3FR_CHECK(cudaMemcpyAsync(cnt, s->counts, sizeof cnt, cudaMemcpyDeviceToHost, stream));
+  A3FR_CHECK(cudaStreamSynchronize(stream));
+  size_t want = 2 * (size_t)cnt[3] + (1u << 16);
+  if (want >= (1u << 30)) want = (1u << 30) - 1;
+  const int rc = alloc_instances(s, want);
+  if (rc != A3FR_OK) return rc;
+  cnt[0] = cnt[3] < s->capacity ? cnt[3] : (uint32_t)s->capacity;
+  A3FR_CHECK(cudaMemcpyAsync(s->counts, cnt, sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
+  A3FR_CHECK(cudaMemsetAsync(s->status, 0, sizeof(uint32_t), stream));
+  A3FR_CHECK(cudaStreamSynchronize(stream));
+  return A3FR_OK;
+}
+
+// The sort-based binning (renders with more than kBinDirectMaxTiles tiles): tile counts ->
+// ranges and the tile sort's histograms, emit of the depth-ordered instances, stable
+// onesweep by tile index.  The sort's result lands in s->vals.
+int enqueue_bin_sorted(a3fr_scene *s, int eyes, const uint32_t *entries, const FrameLayout &L,
+                       cudaStream_t stream, bool allow_resize, uint64_t *launches) {
+  const int n = s->desc.n;
+  const SortPlan tile_plan = sort_plan(tile_bits_for(eyes * s->n_tiles), 8);
+  unsigned char *ws = static_cast<unsigned char *>(s->frame_ws);
+  uint32_t *counts = s->counts;
+  uint32_t *tile_hist = reinterpret_cast<uint32_t *>(ws + L.tile_hist);
+  uint32_t *tile_ctr = reinterpret_cast<uint32_t *>(ws + L.tile_ctr);
+  unsigned long long *emit_lb = reinterpret_cast<unsigned long long *>(ws + L.emit_lb);
+  uint32_t *tile_diff = reinterpret_cast<uint32_t *>(ws + L.tile_diff);
+  TileScanParams tp{};
+  tp.n_eyes = eyes;
+  tp.n = n;
+  tp.tiles_x = s->TX;
+  tp.tiles_y = s->TY;
+  tp.n_tiles = s->n_tiles;
+  tp.capacity = (uint32_t)s->capacity;
+  tp.tile_plan = tile_plan;
+  if (n > 0) {
+    A3FR_CHECK(launch_tile_count(tp, s->rect, s->tile_partials, tile_diff, stream));
+    *launches += 2;
+  }
+  A3FR_CHECK(launch_tile_scan(tp, tile_diff, s->ranges, tile_hist, counts, s->status, stream));
+  ++*launches;
+  if (allow_resize && s->auto_capacity && s->capacity == 0 && n > 0) {
+    const int rc = size_instances(s, stream);
+    if (rc != A3FR_OK) return rc;
+  }
+  A3FR_CHECK(mark(s, A3FR_STAGE_EMIT, stream));
+  if (n > 0 && s->capacity > 0) {
+    EmitParams ep{};
+    ep.n = n;
+    ep.n_entries = eyes * n;
+    ep.n_tiles = s->n_tiles;
+    ep.tiles_x = s->TX;
+    ep.capacity = (uint32_t)s->capacity;
+    // an odd number of passes ends in the second buffers: start there so it ends in vals
+    uint32_t *v0 = tile_plan.passes % 2 ? s->vals_alt : s->vals;
+    uint32_t *v1 = tile_plan.passes % 2 ? s->vals : s->vals_alt;
+    A3FR_CHECK(cudaMemsetAsync(s->tile_lb, 0, s->tile_lb_bytes, stream));
+    A3FR_CHECK(launch_emit(ep, entries, s->touched, s->rect, s->tkeys[0], v0, emit_lb, counts + 6,
+                           stream));
+    bool in_alt = false;
+    A3FR_CHECK(launch_onesweep<uint32_t>(s->tkeys[0], v0, s->tkeys[1], v1, false, counts, s->capacity,
+                                         tile_plan, tile_hist, tile_ctr, s->tile_lb, s->status,
+                                         &in_alt, stream));
+    *launches += 2 + tile_plan.passes;
+  }
+  return A3FR_OK;
+}
+
 int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
                 uint64_t *launches) {
   const int n = s->desc.n;
   const int n_entries = eyes * n;
   const SortPlan depth_plan = sort_plan(32, 8);
-  const FrameLayout L = frame_layout((size_t)(n_entries > 0 ? n_entries : eyes), eyes, s->n_tiles);
+  const FrameLayout L = frame_layout((size_t)(n_entries > 0 ? n_entries : eyes), eyes, s->TX, s->TY);
   unsigned char *ws = static_cast<unsigned char *>(s->frame_ws);
   uint32_t *counts = s->counts;
   uint32_t *depth_hist = reinterpret_cast<uint32_t *>(ws + L.depth_hist);
@@ -434,8 +563,9 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
     *launches += 1 + depth_plan.passes;
   }
   const uint32_t *entries = s->dvals[depth_plan.passes % 2];
-  // per-chunk tile counts -> tile ranges, per-chunk starts, totals
   A3FR_CHECK(mark(s, A3FR_STAGE_BIN, stream));
+  if (s->sorted_bin) return enqueue_bin_sorted(s, eyes, entries, L, stream, allow_resize, launches);
+  // per-chunk tile counts -> tile ranges, per-chunk starts, totals
   BinParams bp = bin_params(eyes, n, s->TX, s->TY, (uint32_t)s->capacity);
   A3FR_CHECK(launch_bin_plan(bp, entries, s->touched, inst_total, plan_lb, bounds, s->status, stream));
   A3FR_CHECK(launch_bin_count(bp, entries, s->rect, bounds, s->bin_h, stream));
@@ -444,18 +574,9 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
   if (allow_resize && s->auto_capacity && s->capacity == 0 && n > 0) {
     // first render: read the instance count once, then size the instance buffer (the
     // starts in bin_h do not depend on the capacity)
-    uint32_t cnt[8];
-    A3FR_CHECK(cudaMemcpyAsync(cnt, counts, sizeof cnt, cudaMemcpyDeviceToHost, stream));
-    A3FR_CHECK(cudaStreamSynchronize(stream));
-    size_t want = 2 * (size_t)cnt[3] + (1u << 16);
-    if (want >= (1u << 30)) want = (1u << 30) - 1;
-    const int rc = alloc_instances(s, want);
+    const int rc = size_instances(s, stream);
     if (rc != A3FR_OK) return rc;
     bp.capacity = (uint32_t)s->capacity;
-    cnt[0] = cnt[3] < s->capacity ? cnt[3] : (uint32_t)s->capacity;
-    A3FR_CHECK(cudaMemcpyAsync(counts, cnt, sizeof(uint32_t), cudaMemcpyHostToDevice, stream));
-    A3FR_CHECK(cudaMemsetAsync(s->status, 0, sizeof(uint32_t), stream));
-    A3FR_CHECK(cudaStreamSynchronize(stream));
   }
   // every instance straight to its slot, each tile's run in depth order
   A3FR_CHECK(mark(s, A3FR_STAGE_EMIT, stream));

@@ -155,6 +155,39 @@ cudaError_t launch_bin_emit(const BinParams &p, const uint32_t *entries, const u
                             const uint32_t *bounds, const uint32_t *h, uint32_t *vals,
                             cudaStream_t s);
 
+// The sort-based binning for renders with many tiles (binning_sorted.cu): per-tile counts
+// -> ranges, emit of the depth-ordered instances, then a stable onesweep sort by tile.
+// Emission of the tile instances of the depth-ordered entries (see binning_sorted.cu).
+struct EmitParams {
+  int n, n_entries, n_tiles, tiles_x;
+  uint32_t capacity;
+};
+size_t emit_lookback_bytes(int n_entries);
+cudaError_t launch_emit(const EmitParams &p, const uint32_t *entries, const uint32_t *touched,
+                        const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
+                        unsigned long long *blk, uint32_t *done_counter, cudaStream_t s);
+
+// Per-tile instance counts without enumerating instances: every tile rectangle adds
+// +1/-1/-1/+1 at its four corners in a per-eye 2-D difference grid (tiles_y+1 rows of
+// tiles_x+1), accumulated per CTA in shared memory and written out as partial grids
+// (no global atomics), then summed by a reduction; the 2-D prefix sum is the count.
+struct TileScanParams {
+  int n_eyes, n, tiles_x, tiles_y, n_tiles;
+  uint32_t capacity;
+  SortPlan tile_plan;
+};
+int tile_count_blocks();
+size_t tile_grid_cells(int n_eyes, int tiles_x, int tiles_y);
+cudaError_t launch_tile_count(const TileScanParams &p, const ushort4 *rect, uint32_t *partials,
+                              uint32_t *grid, cudaStream_t s);
+// One CTA: counts -> ranges (exclusive scan over tiles, eye-major), tile-sort histograms and
+// totals (counts[0] kept, [1..2] per eye, [3] total).  Grids that do not fit in shared
+// memory are rejected by the caller up front.
+size_t tile_scan_smem_bytes(int n_eyes, int tiles_x, int tiles_y);
+cudaError_t launch_tile_scan(const TileScanParams &p, const uint32_t *grid, uint2 *ranges,
+                             uint32_t *tile_hist, uint32_t *counts, uint32_t *status,
+                             cudaStream_t s);
+
 // keys[j] = tile << 32 | depth bits of the Gaussian vals[j] (for inspection), the tile of
 // slot j found in the ranges.
 cudaError_t launch_materialize_keys(const uint2 *ranges, int n_ranges, const uint32_t *vals,

@@ -163,24 +163,27 @@ def test_repeated_renders_are_deterministic_and_counters_accumulate():
     assert st["renders"] == 3 and st["evaluations"] > 0 and st["status"] == 0
 
 
-def test_stereo_500k_sh3_sampled_pixels():
-    """The benchmark workload at full size: records and keys in full, pixels sampled."""
+@pytest.mark.parametrize("tile", [16, 32])
+def test_stereo_500k_sh3_sampled_pixels(tile):
+    """The benchmark workload at full size: records and keys in full, pixels sampled.  Its
+    12,800 16-pixel tiles take the sort-based binning, its 3,200 32-pixel tiles the direct
+    one."""
     w = synth.stereo_500k(frames=240)
     traj = synth.gaze_trajectory(240)
     frame = 137
     cams = w.cameras(frame)
     gaze = w.gaze(frame, traj)
     ofv, gfv = fovea_params()
-    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False)
+    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False, tile=tile)
     assert r["stats"]["status"] == 0
     rng = np.random.default_rng(frame)
     for e in range(2):
         pix = np.stack([rng.integers(0, 1280, 1500), rng.integers(0, 1280, 1500)], axis=1)
         # plus every pixel of the tile row through the gaze (crosses all three layers)
-        gy = int(np.clip(gaze[e][1], 0, 1279)) // 16 * 16
-        band = np.stack(np.meshgrid(np.arange(0, 1280, 3), np.arange(gy, gy + 16, 5)), -1).reshape(-1, 2)
+        gy = int(np.clip(gaze[e][1], 0, 1279)) // tile * tile
+        band = np.stack(np.meshgrid(np.arange(0, 1280, 3), np.arange(gy, gy + tile, 5)), -1).reshape(-1, 2)
         pix = np.concatenate([pix, band]).astype(np.int32)
-        print(e, check_eye(r, e, w.scene, cams[e], gaze=gaze[e], fv=ofv, pixels=pix))
+        print(e, check_eye(r, e, w.scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv, pixels=pix))
 
 
 def test_graph_mode_matches_direct_launches_bitwise():
