@@ -230,6 +230,17 @@ int a3fr_set_graph_mode(a3fr_scene *scene, int on);
 int a3fr_set_tile(a3fr_scene *scene, int tile);
 int a3fr_set_batch(a3fr_scene *scene, int batch_mult);
 
+/* Binning path (Sec. 2.3 tile binning; both give the same tile lists bit for bit).  DIRECT:
+ * the depth-ordered entries cut into chunks, per-chunk tile counts and start slots, every
+ * instance placed at its slot by ordered ranks (no sort over the instances).  SORTED: tile
+ * counts, emit of the depth-ordered instances, a stable radix sort by tile.  AUTO (default):
+ * DIRECT up to 6,144 tiles over all eyes, SORTED above (where it is faster).  Changing it invalidates the scene's buffers (the next render reallocates);
+ * synchronous.  Invalid mode: A3FR_ERR_INVALID_ARG. */
+#define A3FR_BINNING_AUTO 0
+#define A3FR_BINNING_DIRECT 1
+#define A3FR_BINNING_SORTED 2
+int a3fr_set_binning(a3fr_scene *scene, int mode);
+
 typedef struct {
   int32_t tile, batch_mult;   /* the configuration chosen (and left set on the scene) */
   float ms[2][2];             /* mean foveated render time per (tile 16|32, batch 1|2) */

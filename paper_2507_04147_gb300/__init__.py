@@ -45,6 +45,7 @@ def _ptr(t) -> int:
 
 
 FILL_INHERIT, FILL_INTERPOLATE = 0, 1
+BINNING_AUTO, BINNING_DIRECT, BINNING_SORTED = 0, 1, 2
 
 
 def Fovea(theta_deg=(18.0, 36.0), dtheta_deg: float = 0.0, levels=(4, 2, 1),
@@ -350,6 +351,10 @@ class Scene:
 
     def set_batch(self, batch_mult: int):
         _lib.check(_lib.load().a3fr_set_batch(self.handle, int(batch_mult)), "a3fr_set_batch")
+
+    def set_binning(self, mode: int):
+        """BINNING_AUTO, BINNING_DIRECT or BINNING_SORTED (the same tile lists either way)."""
+        _lib.check(_lib.load().a3fr_set_binning(self.handle, int(mode)), "a3fr_set_binning")
 
     def autotune(self, fovea=None, out=None, timed_renders: int = 5, stream=None) -> dict:
         """Times every (tile, batch) configuration on the current view and keeps the fastest."""

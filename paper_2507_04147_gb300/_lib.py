@@ -113,6 +113,7 @@ _SIGS = {
     "a3fr_set_graph_mode": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_set_tile": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_set_batch": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
+    "a3fr_set_binning": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_autotune": ([ctypes.c_void_p, ctypes.POINTER(Fovea), ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                        ctypes.POINTER(TuneResult)], ctypes.c_int),
     "a3fr_tc_tile_gemm": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int, ctypes.c_int,

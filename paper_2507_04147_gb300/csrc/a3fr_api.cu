@@ -64,6 +64,7 @@ struct a3fr_scene {
   uint32_t *bin_h = nullptr;                 // per-chunk tile counts, then starts (binning.cu)
   // the sort-based binning (binning_sorted.cu), for renders with more than
   // kBinDirectMaxTiles tiles: difference grids, instance tile keys, the sort's second buffers
+  int binning = A3FR_BINNING_AUTO;
   bool sorted_bin = false;
   uint32_t *tile_partials = nullptr;
   uint32_t *tkeys[2] = {nullptr, nullptr};
@@ -152,8 +153,11 @@ namespace {
 int n_eyes_of(const a3fr_scene *s) { return s->cam_set[1] ? 2 : (s->cam_set[0] ? 1 : 0); }
 
 constexpr int kDepthPasses = 4;   // 32-bit depth keys, 8-bit digits
-// Above this many tiles (all eyes) bin_emit's per-warp cursor table (4 B per tile) leaves
-// fewer than ~8 warps per SM, and the sort-based binning is faster.
+
+// AUTO binning: direct placement up to this many tiles (all eyes), the sort-based binning
+// above.  Each direct-binning warp walks one chunk of entries serially; with many tiles the
+// chunk table (chunks x tiles) caps the chunk count, the chains grow and the stable radix
+// sort by tile is faster (3M clustered stereo 2064x2208, 8,970 tiles: 0.54 vs 0.80 ms).
 constexpr int kBinDirectMaxTiles = 6144;
 
 int tile_bits_for(int n_ranges) {
@@ -278,7 +282,8 @@ int ensure_frame_buffers(a3fr_scene *s, int eyes, int W, int H) {
     A3FR_CHECK(cudaGetDevice(&dev));
     A3FR_CHECK(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
     const int tx = (W + tile - 1) / tile, ty = (H + tile - 1) / tile;
-    s->sorted_bin = (long long)eyes * tx * ty > kBinDirectMaxTiles;
+    s->sorted_bin = s->binning == A3FR_BINNING_SORTED ||
+                    (s->binning == A3FR_BINNING_AUTO && (long long)eyes * tx * ty > kBinDirectMaxTiles);
     const size_t need = s->sorted_bin ? tile_scan_smem_bytes(eyes, tx, ty) + 9216 : bin_smem_bytes(eyes, tx, ty);
     if (need > (size_t)max_optin) return A3FR_ERR_INVALID_ARG;
   }
@@ -1186,6 +1191,18 @@ int a3fr_set_tile(a3fr_scene *s, int tile) {
     s->capacity = 0;
   }
   s->desc.tile = tile;
+  s->alloc_gen++;
+  s->bw_mode = 0;
+  return A3FR_OK;
+}
+
+int a3fr_set_binning(a3fr_scene *s, int mode) {
+  if (!s || mode < A3FR_BINNING_AUTO || mode > A3FR_BINNING_SORTED) return A3FR_ERR_INVALID_ARG;
+  if (s->binning == mode) return A3FR_OK;
+  A3FR_CHECK(cudaDeviceSynchronize());
+  free_frame_buffers(s);
+  free_sort_buffers(s);
+  s->binning = mode;
   s->alloc_gen++;
   s->bw_mode = 0;
   return A3FR_OK;

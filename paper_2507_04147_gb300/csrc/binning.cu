@@ -17,8 +17,8 @@
 //               instances of tile r at R[r] + sum over the earlier chunks of h[c'][r]; the
 //               start overwrites h.  One CTA per 32 tiles; the CTAs chain their sums by a
 //               decoupled look-back (bounded waits, like the sort's).
-//  bin_emit     One warp per chunk walks the chunk's instances in entry order, 32 at a
-//               time (lane = instance).  A lane's slot is the tile's cursor plus the number
+//  bin_emit     One warp per (chunk, band of tile rows) walks the chunk's instances in its
+//               band in entry order, 32 at a time (lane = instance).  A lane's slot is the tile's cursor plus the number
 //               of lower lanes with the same tile; the highest of them advances the cursor.
 //               Every tile's instances land in entry (= depth) order, the same on every run.
 //
@@ -40,6 +40,7 @@ constexpr unsigned long long kAggFlag = 1ull << 62, kPrefixFlag = 2ull << 62;
 constexpr unsigned long long kVal62 = (1ull << 62) - 1ull;
 constexpr uint32_t kSpinLimit = 1u << 16;   // with back-off: well over a second
 constexpr int kMap = 256;                   // instances a bin_emit warp expands per window
+constexpr int kBandTiles = 3200;            // tiles per bin_emit band (12.8 KB of cursors)
 constexpr int kMapPad = kMap + kMap / 32;   // one pad word per 32 (fewer bank conflicts)
 constexpr long long kMaxChunkCells = 24ll << 20;   // bound on C * tiles (u32 cells of h)
 
@@ -283,14 +284,16 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
 }
 
-// One warp (CTA) per chunk walks the chunk's instances in entry order.  Per round of 32
-// entries (lane = entry) the warp scans the entries' instance counts and expands the
-// instances into its map (tile, Gaussian) in windows of kMap, then takes the map 32
-// instances at a time (lane = instance: full warps whatever the rectangle sizes).  A lane's
-// rank among the step's instances of its tile is the number of lower lanes with the same
-// tile (__match_any_sync); the highest of them advances the tile's cursor.  Shared memory:
-// cursor[row] (the chunk's starts, copied in by cp.async) and the map.  Entry values are
-// loaded two rounds ahead, rectangles one round ahead.
+// One warp (CTA) per (chunk, band): blockIdx.x = chunk * n_bands + band, the band being the
+// tile rows [R0, R1) (row index eye * tiles_y + y), i.e. the contiguous tiles [R0 tiles_x,
+// R1 tiles_x).  The warp walks the chunk's entries 32 at a time (lane = entry), scans their
+// instance counts inside the band and expands those instances into its map (band tile,
+// Gaussian) in windows of kMap, then takes the map 32 instances at a time (lane = instance:
+// full warps whatever the rectangle sizes).  A lane's rank among the step's instances of its
+// tile is the number of lower lanes with the same tile (__match_any_sync); the highest of
+// them advances the tile's cursor.  Shared memory: the band's cursors (from the chunk's row
+// of h, copied in by cp.async) and the map.  Entry values are loaded two rounds ahead,
+// rectangles one round ahead.
 __global__ void __launch_bounds__(32)
 bin_emit_kernel(BinParams p, const uint32_t *__restrict__ entries, const ushort4 *__restrict__ rect,
                 const uint32_t *__restrict__ bounds, const uint32_t *__restrict__ h,
@@ -299,14 +302,19 @@ bin_emit_kernel(BinParams p, const uint32_t *__restrict__ entries, const ushort4
   __shared__ uint32_t s_map_tile[kMapPad];
   __shared__ uint32_t s_map_gid[kMapPad];
   const int lane = threadIdx.x;
-  uint32_t *s_cur = s_dyn;
+  const int chunk = blockIdx.x / p.n_bands, band = blockIdx.x - chunk * p.n_bands;
+  const int R0 = band * p.band_rows, R1 = min(p.n_eyes * p.tiles_y, R0 + p.band_rows);
+  // the band's tiles [R0 tiles_x, R1 tiles_x) of the chunk's row of h, copied from the
+  // 16-byte boundary at or below its start; s_cur[t] is the cursor of band tile t
+  const int t0 = R0 * p.tiles_x, a0 = t0 & ~3, a1 = min(p.row, (R1 * p.tiles_x + 3) & ~3);
+  uint32_t *s_cur = s_dyn + (t0 - a0);
   {
-    const uint32_t *hb = h + (size_t)blockIdx.x * p.row;
-    for (int i = lane * 4; i < p.row; i += 128) cp_async16(s_cur + i, hb + i);
+    const uint32_t *hb = h + (size_t)chunk * p.row;
+    for (int i = a0 + lane * 4; i < a1; i += 128) cp_async16(s_dyn + (i - a0), hb + i);
     asm volatile("cp.async.commit_group;" ::: "memory");
   }
   const unsigned below = (1u << lane) - 1u;
-  const int j0 = (int)bounds[blockIdx.x], j1 = (int)bounds[blockIdx.x + 1];
+  const int j0 = (int)bounds[chunk], j1 = (int)bounds[chunk + 1];
   const ushort4 none = make_ushort4(0, 0, 0, 0);
   uint32_t v_cur = j0 + lane < j1 ? entries[j0 + lane] : 0u;
   uint32_t v_next = j0 + 32 + lane < j1 ? entries[j0 + 32 + lane] : 0u;
@@ -323,13 +331,15 @@ bin_emit_kernel(BinParams p, const uint32_t *__restrict__ entries, const ushort4
       v_next = jnn < j1 ? entries[jnn] : 0u;
     }
     const uint32_t w = rc.z > rc.x ? (uint32_t)(rc.z - rc.x) : 0u;
-    const uint32_t cnt = (b + lane < j1 && rc.w > rc.y) ? w * (uint32_t)(rc.w - rc.y) : 0u;
+    const int eye = v >= (uint32_t)p.n ? 1 : 0;
+    const uint32_t gid = v - (uint32_t)eye * (uint32_t)p.n;
+    // the rectangle's rows inside the band
+    const int row0 = max(R0, eye * p.tiles_y + (int)rc.y);
+    const int row1 = min(R1, eye * p.tiles_y + (int)rc.w);
+    const uint32_t cnt = (b + lane < j1 && row1 > row0) ? w * (uint32_t)(row1 - row0) : 0u;
     const uint32_t incl = warp_incl_scan(cnt, lane);
     const uint32_t first = incl - cnt;
     const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-    const int eye = v >= (uint32_t)p.n ? 1 : 0;
-    const uint32_t gid = v - (uint32_t)eye * (uint32_t)p.n;
-    const int row0 = eye * p.tiles_y + (int)rc.y;
     for (uint32_t base = 0; base < total; base += kMap) {
       const uint32_t wend = min(total, base + kMap);
       // this lane's instances in [base, wend) into the map
@@ -338,7 +348,7 @@ bin_emit_kernel(BinParams p, const uint32_t *__restrict__ entries, const ushort4
         const uint32_t off = lo - first;
         const uint32_t dy = off ? div_small(off, w) : 0u;
         int x = (int)rc.x + (int)(off - dy * w);
-        int tile = (row0 + (int)dy) * p.tiles_x + x;
+        int tile = (row0 - R0 + (int)dy) * p.tiles_x + x;   // band tile index
         for (uint32_t j = lo; j < hi; ++j) {
           const uint32_t mj = j - base;
           s_map_tile[mj + (mj >> 5)] = (uint32_t)tile;
@@ -413,18 +423,27 @@ BinParams bin_params(int n_eyes, int n, int tiles_x, int tiles_y, uint32_t capac
   p.capacity = capacity;
   const long long n_ranges = (long long)n_eyes * p.n_tiles;
   p.row = (int)((n_ranges + 3) / 4 * 4);
-  // one bin_emit warp per chunk: as many chunks as warps fit on the device at once (their
-  // shared memory), at least 256 entries each, at most kMaxChunks and kMaxChunkCells cells
+  // bin_emit: one warp per (chunk, band of tile rows); a band holds at most kBandTiles tiles
+  // (whole rows, at least one), so a warp's cursor table stays small however many tiles the
+  // render has and many warps fit on an SM
+  const int rows = n_eyes * tiles_y;
+  p.band_rows = kBandTiles / (tiles_x > 0 ? tiles_x : 1);
+  if (p.band_rows < 1) p.band_rows = 1;
+  if (p.band_rows > rows) p.band_rows = rows > 0 ? rows : 1;
+  p.n_bands = rows > 0 ? (rows + p.band_rows - 1) / p.band_rows : 1;
+  // chunks: enough (chunk, band) warps to fill the device (as many as fit at once), at
+  // least 256 entries each, at most kMaxChunks and kMaxChunkCells cells of h
   int dev = 0, sms = 152;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const long long per_warp = (long long)bin_emit_smem_bytes(n_eyes, tiles_x, tiles_y) +
+  const long long per_warp = (long long)sizeof(uint32_t) * ((long long)p.band_rows * tiles_x + 8) +
                              2 * sizeof(uint32_t) * kMapPad + 1024;
   long long warps_per_sm = (228ll * 1024) / per_warp;
   if (warps_per_sm > 32) warps_per_sm = 32;
   if (warps_per_sm < 1) warps_per_sm = 1;
   long long max_chunks = kMaxChunkCells / (p.row > 0 ? p.row : 1);
   if (max_chunks > kMaxChunks) max_chunks = kMaxChunks;
-  if (max_chunks > warps_per_sm * sms) max_chunks = warps_per_sm * sms;
+  const long long fill = (warps_per_sm * sms + p.n_bands - 1) / p.n_bands;
+  if (max_chunks > fill) max_chunks = fill;
   if (max_chunks < 1) max_chunks = 1;
   long long chunks = ((long long)p.n_entries + 255) / 256;
   if (chunks > max_chunks) chunks = max_chunks;
@@ -440,13 +459,15 @@ BinParams bin_params(int n_eyes, int n, int tiles_x, int tiles_y, uint32_t capac
 
 size_t bin_chunk_cells(const BinParams &p) { return (size_t)p.n_chunks * (size_t)p.row; }
 
-size_t bin_emit_smem_bytes(int n_eyes, int tiles_x, int tiles_y) {
-  return sizeof(uint32_t) * (((size_t)n_eyes * tiles_x * tiles_y + 3) / 4 * 4);
+size_t bin_emit_smem_bytes(const BinParams &p) {
+  // one band's cursors and up to 3 words either side of its 16-byte-aligned copy
+  return sizeof(uint32_t) * ((size_t)p.band_rows * p.tiles_x + 8);
 }
 
 size_t bin_smem_bytes(int n_eyes, int tiles_x, int tiles_y) {
   const size_t a = bin_count_smem_bytes(n_eyes, tiles_x, tiles_y);
-  const size_t b = bin_emit_smem_bytes(n_eyes, tiles_x, tiles_y) + 2 * sizeof(uint32_t) * kMapPad;
+  const size_t b = bin_emit_smem_bytes(bin_params(n_eyes, 1, tiles_x, tiles_y, 0)) +
+                   2 * sizeof(uint32_t) * kMapPad;
   return a > b ? a : b;
 }
 
@@ -498,11 +519,11 @@ cudaError_t launch_bin_emit(const BinParams &p, const uint32_t *entries, const u
                             const uint32_t *bounds, const uint32_t *h, uint32_t *vals,
                             cudaStream_t s) {
   if (p.n_entries <= 0 || p.capacity == 0) return cudaSuccess;
-  const size_t smem = bin_emit_smem_bytes(p.n_eyes, p.tiles_x, p.tiles_y);
+  const size_t smem = bin_emit_smem_bytes(p);
   cudaError_t e = cudaFuncSetAttribute(bin_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  bin_emit_kernel<<<p.n_chunks, 32, smem, s>>>(p, entries, rect, bounds, h, vals);
+  bin_emit_kernel<<<p.n_chunks * p.n_bands, 32, smem, s>>>(p, entries, rect, bounds, h, vals);
   return cudaGetLastError();
 }
 

@@ -125,6 +125,8 @@ struct BinParams {
   int chunk;                // mean entries per chunk (sizing; bin_plan sets the bounds)
   int n_chunks;
   int row;                  // u32 cells per chunk row of h: tiles rounded up to 4 (16 bytes)
+  int band_rows;            // tile rows (eye * tiles_y + y) per bin_emit band
+  int n_bands;
   uint32_t capacity;
 };
 BinParams bin_params(int n_eyes, int n, int tiles_x, int tiles_y, uint32_t capacity);
@@ -132,7 +134,7 @@ size_t bin_chunk_cells(const BinParams &p);          // u32 cells of h: chunks x
 // Shared memory of bin_count (the difference grids) and of bin_emit (the cursors); the
 // larger of the two, with bin_emit's static part, is checked against the device up front.
 size_t bin_count_smem_bytes(int n_eyes, int tiles_x, int tiles_y);
-size_t bin_emit_smem_bytes(int n_eyes, int tiles_x, int tiles_y);
+size_t bin_emit_smem_bytes(const BinParams &p);
 size_t bin_smem_bytes(int n_eyes, int tiles_x, int tiles_y);
 // bounds[0..n_chunks] <- chunk c = entries [bounds[c], bounds[c + 1]), about equal
 // instance counts; inst_total is the render's instance total (preprocess), lookback

@@ -17,10 +17,11 @@ MAX_EXEMPT_FRACTION = 2e-3
 
 
 def run(scene_np, cams, gaze=None, fovea=None, full=False, capacity=0, keep_aux=True,
-        out=None, tile=16, batch_mult=1):
+        out=None, tile=16, batch_mult=1, binning=a3fr.BINNING_AUTO):
     import torch
     s = a3fr.Scene.from_numpy(scene_np, instance_capacity=capacity, tile=tile)
     s.set_batch(batch_mult)
+    s.set_binning(binning)
     for e, c in enumerate(cams):
         s.set_camera(e, c)
     s.keep_aux(keep_aux)

@@ -91,12 +91,13 @@ def test_small_single_view_foveated_and_full():
     assert np.array_equal(fov[~live], tl[~live])
 
 
-def test_stereo_sh3_ragged_image():
+@pytest.mark.parametrize("binning", [a3fr.BINNING_DIRECT, a3fr.BINNING_SORTED])
+def test_stereo_sh3_ragged_image(binning):
     scene = synth.uniform_scene(6000, 3, seed=3)
     cams = synth.stereo_cameras(200, 136, yaw_deg=3.0)
     gaze = np.array([[20.0, 120.0], [25.5, 118.25]], np.float32)
     ofv, gfv = fovea_params()
-    r = gh.run(scene, cams, gaze=gaze, fovea=gfv)
+    r = gh.run(scene, cams, gaze=gaze, fovea=gfv, binning=binning)
     assert r["stats"]["status"] == 0 and r["stats"]["n_eyes"] == 2
     for e in range(2):
         print(e, check_eye(r, e, scene, cams[e], gaze=gaze[e], fv=ofv))
@@ -137,10 +138,11 @@ def test_degenerate_scenes():
     assert r["rect"][0, 0].tolist() == [0, 0, 4, 3]
 
 
-def test_capacity_overflow_sets_status_without_fault():
+@pytest.mark.parametrize("binning", [a3fr.BINNING_DIRECT, a3fr.BINNING_SORTED])
+def test_capacity_overflow_sets_status_without_fault(binning):
     w = synth.small_single_view()
     cam = w.cameras(0)[0]
-    r = gh.run(w.scene, [cam], full=True, capacity=1000)
+    r = gh.run(w.scene, [cam], full=True, capacity=1000, binning=binning)
     st = r["stats"]
     assert st["status"] & a3fr.STATUS_CAPACITY
     assert st["instances"] == 1000 and st["capacity"] == 1000
@@ -163,18 +165,18 @@ def test_repeated_renders_are_deterministic_and_counters_accumulate():
     assert st["renders"] == 3 and st["evaluations"] > 0 and st["status"] == 0
 
 
-@pytest.mark.parametrize("tile", [16, 32])
-def test_stereo_500k_sh3_sampled_pixels(tile):
-    """The benchmark workload at full size: records and keys in full, pixels sampled.  Its
-    12,800 16-pixel tiles take the sort-based binning, its 3,200 32-pixel tiles the direct
-    one."""
+@pytest.mark.parametrize("tile,binning", [(16, a3fr.BINNING_SORTED), (32, a3fr.BINNING_DIRECT),
+                                         (16, a3fr.BINNING_DIRECT)])
+def test_stereo_500k_sh3_sampled_pixels(tile, binning):
+    """The benchmark workload at full size: records and keys in full, pixels sampled, under
+    both binning paths (16-pixel tiles: 12,800 tiles, 4 bands per chunk in the direct path)."""
     w = synth.stereo_500k(frames=240)
     traj = synth.gaze_trajectory(240)
     frame = 137
     cams = w.cameras(frame)
     gaze = w.gaze(frame, traj)
     ofv, gfv = fovea_params()
-    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False, tile=tile)
+    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False, tile=tile, binning=binning)
     assert r["stats"]["status"] == 0
     rng = np.random.default_rng(frame)
     for e in range(2):
