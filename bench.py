@@ -625,7 +625,7 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
             sc = scenes[step % len(scenes)]
             cam = synth.pinhole_camera(1024, 1024, yaw_deg=float(rng.uniform(-30.0, 30.0)))
             imgs, deps = periphery.render_crops(sc, [cam], crop, batch, rng, stream=render_stream)
-            lr = 2e-3 * (0.1 + 0.9 * 0.5 * (1.0 + math.cos(math.pi * step / steps)))
+            lr = 3e-5 * (0.1 + 0.9 * 0.5 * (1.0 + math.cos(math.pi * step / steps)))
             loss = net.train_step(imgs, deps, imgs, lr, sync=(step % 250 == 0 or step == steps - 1),
                                   stream=render_stream)
             if loss is not None:

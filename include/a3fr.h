@@ -296,7 +296,11 @@ int a3fr_tc_tile_gemm(const uint16_t *A, const uint16_t *B, float *D, int n, int
  * layer (the top-left pixel of every 2x2 block, which every level renders) and its expected
  * depth.  Network: 3x3 conv 16->32 + ReLU; four residual blocks (3x3 conv 32->32 + ReLU,
  * 3x3 conv 32->32, skip); 3x3 conv 32->16 whose channel c*4 + 2*dy + dx is the correction
- * of colour c at sub-pixel (dx, dy) of the block, added to the block's top-left colour.
+ * of colour c at sub-pixel (dx, dy) of the block, added to the base: the bilinear
+ * interpolation of the top-left pixels (the block's a, its right neighbour's, the one below,
+ * the diagonal one; the last block repeated past the edge) -- a at (0, 0), (a + right) / 2,
+ * (a + down) / 2, (((a + right) + down) + diag) / 4 -- i.e. the interpolating fill where
+ * only top-left pixels are rendered.
  * BF16 weights and activations, FP32 accumulation, all convolutions on the tensor cores
  * (tcgen05); inputs (r, g, b, depth/8) per block.  Parameters: fp32, layer by layer the
  * weights [out][in][3][3] (layer 0's input channels 4..15 unused), then the biases; the
@@ -315,7 +319,7 @@ int a3fr_cnn_get_params(a3fr_cnn *net, float *host, size_t count);
  * receives the per-block corrections.  Asynchronous on stream. */
 int a3fr_cnn_forward(a3fr_cnn *net, const float *img, const float *depth, int b, int h, int w,
                      float *residual_out, void *stream);
-/* Mean squared error of the prediction (top-left colour + correction at every pixel) against
+/* Mean squared error of the prediction (base + correction at every pixel) against
  * target (DEVICE fp32 [b][h][w][3]) and its gradient with respect to every parameter, into
  * host_grads (host fp32 [a3fr_cnn_param_count()]) and *loss; synchronous. */
 int a3fr_cnn_grads(a3fr_cnn *net, const float *img, const float *depth, const float *target, int b,
@@ -326,7 +330,7 @@ int a3fr_cnn_train_step(a3fr_cnn *net, const float *img, const float *depth, con
                         int b, int h, int w, float lr, float *loss, void *stream);
 /* Learned fill of the scene's last render, which must be a3fr_render_foveated with keep_aux
  * on (for its depth) writing out_rgb: rendered pixels are kept, every skipped pixel becomes its
- * block's top-left colour plus the network's correction.  A3FR_ERR_NOT_READY otherwise.
+ * base plus the network's correction.  A3FR_ERR_NOT_READY otherwise.
  * Asynchronous on stream (ordered after the render). */
 int a3fr_cnn_fill(a3fr_cnn *net, a3fr_scene *scene, float *out_rgb, void *stream);
 

@@ -10,8 +10,13 @@ the tensor-core kernels implement, as plain PyTorch CPU operations in float64 (a
 * four residual blocks: t = ReLU(conv(h) + b) (BF16); h = h + conv(t) + b (BF16);
 * conv9: 3x3, 32 -> 16, bias -> r (FP32); channel c * 4 + 2 dy + dx is the residual of colour
   c at sub-pixel (dx, dy) of the block;
-* full-resolution prediction: the block's top-left pixel (FP32, as rendered) + r (2x pixel
-  shuffle), i.e. the inherit fill of Sec. 3.4 plus a learned correction.
+* full-resolution prediction: a base from the quarter-density layer + r (2x pixel shuffle).
+  The base of sub-pixel (dx, dy) of block (x2, y2) is the bilinear interpolation of the
+  top-left pixels a = tl[y2][x2], right = tl[y2][x2 + 1], down = tl[y2 + 1][x2], diag =
+  tl[y2 + 1][x2 + 1] (an index past the last block repeats the last block): a at (0, 0),
+  (a + right) / 2 at (1, 0), (a + down) / 2 at (0, 1), (((a + right) + down) + diag) / 4 at
+  (1, 1) -- where only top-left pixels are rendered this is the interpolating fill of
+  Sec. 3.4 ("inherit or interpolate"), so the network learns a correction to it.
 
 Convolutions use zero padding of one pixel; weights are [out, in, 3, 3] and rounded to BF16.
 Gradients are float64 autograd of the same operations with the roundings passed straight
@@ -54,8 +59,7 @@ def init_params(seed: int = 0):
         if li == 0:
             w[:, 4:] = 0.0                      # padding channels of the input
         if li == N_CONV - 1:
-            w *= 0.1                            # start near the inherit fill
-            w[12:] = 0.0
+            w[:] = 0.0                          # start at the bilinear base exactly
         ws.append(w)
         bs.append(np.zeros(cout, dtype=np.float32))
     return ws, bs
@@ -73,13 +77,25 @@ def forward(x0: torch.Tensor, ws, bs) -> torch.Tensor:
     return r.permute(0, 2, 3, 1)
 
 
+def base(tl_rgb: torch.Tensor) -> torch.Tensor:
+    """Bilinear base [B, H2, W2, 4, 3] of the quarter-density layer tl [B, H2, W2, 3]: entry
+    2 dy + dx is the base of sub-pixel (dx, dy) (the last block repeated past the edge)."""
+    a = tl_rgb
+    right = torch.cat([a[:, :, 1:], a[:, :, -1:]], dim=2)
+    down = torch.cat([a[:, 1:], a[:, -1:]], dim=1)
+    diag = torch.cat([down[:, :, 1:], down[:, :, -1:]], dim=2)
+    return torch.stack([a, (a + right) * 0.5, (a + down) * 0.5, (((a + right) + down) + diag) * 0.25],
+                       dim=3)
+
+
 def shuffle(r: torch.Tensor, tl_rgb: torch.Tensor, H: int, W: int) -> torch.Tensor:
-    """Full-resolution prediction [B, H, W, 3]: top-left value + residual of the sub-pixel."""
+    """Full-resolution prediction [B, H, W, 3]: bilinear base + residual of the sub-pixel."""
     B, H2, W2, _ = r.shape
+    bs = base(tl_rgb.to(r.dtype))
     out = torch.empty((B, 2 * H2, 2 * W2, 3), dtype=r.dtype)
     for dy in range(2):
         for dx in range(2):
-            out[:, dy::2, dx::2, :] = tl_rgb + r[..., [c * 4 + 2 * dy + dx for c in range(3)]]
+            out[:, dy::2, dx::2, :] = bs[:, :, :, 2 * dy + dx] + r[..., [c * 4 + 2 * dy + dx for c in range(3)]]
     return out[:, :H, :W]
 
 

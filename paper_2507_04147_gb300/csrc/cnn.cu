@@ -418,7 +418,24 @@ __global__ void gather_input_kernel(const float *__restrict__ img, const float *
   }
 }
 
-// Prediction = top-left value + residual of the sub-pixel; loss = mean squared error against
+// Base of sub-pixel (dx, dy) of block (x2, y2), colour c: the bilinear interpolation of the
+// blocks' top-left pixels of img [B][H][W][3] -- a, right = (x2 + 1), down = (y2 + 1), diag --
+// with the last block repeated past the edge: a; (a + right) / 2; (a + down) / 2;
+// (((a + right) + down) + diag) / 4.  Where only top-left pixels are rendered it is the
+// interpolating fill (Sec. 3.4 "inherit or interpolate").
+__device__ __forceinline__ float base_px(const float *__restrict__ img, int b, int H, int W, int y2,
+                                         int x2, int dy, int dx, int c) {
+  const int H2 = (H + 1) / 2, W2 = (W + 1) / 2;
+  const int xr = min(x2 + 1, W2 - 1), yd = min(y2 + 1, H2 - 1);
+  auto tl = [&](int yy, int xx) { return img[3 * (((size_t)b * H + 2 * yy) * W + 2 * xx) + c]; };
+  const float a = tl(y2, x2);
+  if (dx == 0 && dy == 0) return a;
+  if (dy == 0) return __fmul_rn(__fadd_rn(a, tl(y2, xr)), 0.5f);
+  if (dx == 0) return __fmul_rn(__fadd_rn(a, tl(yd, x2)), 0.5f);
+  return __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(a, tl(y2, xr)), tl(yd, x2)), tl(yd, xr)), 0.25f);
+}
+
+// Prediction = bilinear base + residual of the sub-pixel; loss = mean squared error against
 // the target; g_r = dL/dr (BF16, channels 12..15 zero).  loss_acc accumulates the sum of
 // squared errors.
 __global__ void loss_kernel(const float *__restrict__ r, const float *__restrict__ img,
@@ -431,7 +448,6 @@ __global__ void loss_kernel(const float *__restrict__ r, const float *__restrict
     const int x2 = (int)(i % W2);
     const size_t rr = i / W2;
     const int y2 = (int)(rr % H2), b = (int)(rr / H2);
-    const size_t tl = ((size_t)b * H + 2 * y2) * W + 2 * x2;
     float g[16];
 #pragma unroll
     for (int k = 0; k < 16; ++k) g[k] = 0.0f;
@@ -443,7 +459,7 @@ __global__ void loss_kernel(const float *__restrict__ r, const float *__restrict
       const size_t q = ((size_t)b * H + y) * W + x;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float e = img[3 * tl + c] + r[i * 16 + c * 4 + s] - target[3 * q + c];
+        const float e = base_px(img, b, H, W, y2, x2, dy, dx, c) + r[i * 16 + c * 4 + s] - target[3 * q + c];
         acc += e * e;
         g[c * 4 + s] = 2.0f * e * inv_count;
       }
@@ -463,7 +479,9 @@ __global__ void loss_kernel(const float *__restrict__ r, const float *__restrict
   if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, acc);
 }
 
-// Final image of a foveated render: rendered pixels kept, the others = top-left + residual.
+// Final image of a foveated render: rendered pixels kept, the others = bilinear base +
+// residual (the base reads only top-left pixels, which every level renders, so the pixels
+// this kernel writes are never read by it).
 __global__ void compose_kernel(const float *__restrict__ r, float *__restrict__ img,
                                const uint8_t *__restrict__ levels, int B, int H, int W, int tile,
                                int tiles_x, int n_tiles) {
@@ -477,10 +495,9 @@ __global__ void compose_kernel(const float *__restrict__ r, float *__restrict__ 
     const int lab = bx == by ? (bx ? 1 : 0) : (bx ? 2 : 3);
     const int lv = levels[b * n_tiles + (y / tile) * tiles_x + x / tile];
     if (lab < lv) continue;   // rendered
-    const size_t tl = ((size_t)b * H + (y & ~1)) * W + (x & ~1);
     const size_t ri = (((size_t)b * H2 + y / 2) * W2 + x / 2) * 16 + 2 * by + bx;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) img[3 * i + c] = img[3 * tl + c] + r[ri + 4 * c];
+    for (int c = 0; c < 3; ++c) img[3 * i + c] = base_px(img, b, H, W, y / 2, x / 2, by, bx, c) + r[ri + 4 * c];
   }
 }
 

@@ -17,9 +17,9 @@ LAYERS = [(16, 32)] + [(32, 32)] * 8 + [(32, 16)]   # (in, out) channels of the 
 
 
 def init_params(seed: int = 0) -> np.ndarray:
-    """He-initialised parameters (flat fp32): input channels 4..15 of layer 0 and output
-    channels 12..15 of the last layer are zero; the last layer starts small, so the initial
-    prediction is close to the inherit fill."""
+    """He-initialised parameters (flat fp32): input channels 4..15 of layer 0 are zero and the
+    last layer is zero, so the initial prediction is its bilinear base exactly (the
+    interpolating fill of the periphery) and training only refines it."""
     rng = np.random.default_rng(seed)
     ws, bs = [], []
     for li, (cin, cout) in enumerate(LAYERS):
@@ -28,8 +28,7 @@ def init_params(seed: int = 0) -> np.ndarray:
         if li == 0:
             w[:, 4:] = 0.0
         if li == len(LAYERS) - 1:
-            w *= 0.1
-            w[12:] = 0.0
+            w[:] = 0.0
         ws.append(w)
         bs.append(np.zeros(cout, dtype=np.float32))
     return pack(ws, bs)

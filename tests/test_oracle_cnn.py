@@ -69,12 +69,29 @@ def test_gradients_equal_central_differences():
         cnn.QUANTIZE = True
 
 
-def test_initial_network_is_near_the_inherit_fill():
+def test_base_is_bilinear_on_a_ramp_and_repeats_at_the_edge():
+    """The base reproduces a linear ramp exactly inside the layer (bilinear interpolation at
+    the sub-pixel positions) and repeats the last block past the right and bottom edges."""
+    H2, W2 = 4, 5
+    yy, xx = np.meshgrid(np.arange(H2), np.arange(W2), indexing="ij")
+    ramp = lambda y, x: 0.25 + 0.5 * x - 0.125 * y        # value at pixel (2x2 + x, 2y2 + y) / 2
+    tl = np.stack([ramp(yy, xx)] * 3, -1)[None]
+    b = cnn.base(torch.tensor(tl, dtype=torch.float64)).numpy()[0]
+    for dy in range(2):
+        for dx in range(2):
+            want = ramp(yy + 0.5 * dy, xx + 0.5 * dx)
+            inner = (xx + dx < W2) & (yy + dy < H2)
+            np.testing.assert_allclose(b[..., 2 * dy + dx, 0][inner], want[inner], rtol=0, atol=1e-15)
+    # past the right edge the (1, 0) base is the last block itself
+    np.testing.assert_array_equal(b[:, -1, 1, 0], tl[0, :, -1, 0])
+    np.testing.assert_array_equal(b[-1, :, 2, 0], tl[0, -1, :, 0])
+
+
+def test_initial_network_is_near_the_base():
     rng = np.random.default_rng(2)
     ws, bs = cnn.init_params(0)
     img = rng.uniform(size=(1, 32, 32, 3))
     x0, tl = cnn.make_input(img, rng.uniform(2, 6, size=(1, 32, 32)))
     r = cnn.forward(torch.tensor(x0, dtype=torch.float64), [torch.tensor(np.asarray(w, np.float64)) for w in ws],
                     [torch.tensor(np.asarray(b, np.float64)) for b in bs])
-    assert r[..., 12:].abs().max() == 0.0          # the padding outputs are exactly zero
-    assert r[..., :12].abs().mean() < 0.5
+    assert r.abs().max() == 0.0                    # zero last layer: the prediction is the base
