@@ -8,7 +8,7 @@
  *   volume rendering of each pixel (Sec. 2.3, "Rasterization"), with the tiles
  *   labelled by eccentricity from the gaze (Eq. 1, Sec. 3.4) so that a level-k tile
  *   renders k of the 4 pixels of every 2x2 block and the other pixels inherit the
- *   block's top-left pixel (Sec. 3.4, Sec. 3.5).  All foveation layers of all eyes
+ *   block's top-left pixel or are interpolated (Sec. 3.4, Sec. 3.5).  All foveation layers of all eyes
  *   form one canvas, written in one pass.
  *
  * Conventions shared by every entry point:
@@ -43,7 +43,7 @@ extern "C" {
 
 /* bits of a3fr_stats.status */
 #define A3FR_STATUS_CAPACITY 1u   /* some instances were dropped: the image is incomplete */
-#define A3FR_STATUS_TIMEOUT 2u    /* a look-back wait of the radix sort gave up */
+#define A3FR_STATUS_TIMEOUT 2u    /* a look-back wait (radix sort, binning) gave up */
 
 typedef struct a3fr_scene a3fr_scene; /* opaque, library-owned */
 

@@ -1,8 +1,10 @@
 // a3fr_api.cu -- the C ABI of libA3FR.so (declared in include/a3fr.h): scene objects,
 // library-owned device workspace, the gaze mailbox, and the orchestration of one render:
 //
-//   preprocess -> depth sort -> tile counts / ranges -> emit -> tile sort -> plan + composite
-//        -> [wait for the gaze event] -> composite (level map + blend + inherit)
+//   preprocess -> depth sort -> binning (direct: chunk plan, per-chunk tile counts, ranges
+//   and chunk starts, every instance to its slot; or sort-based: tile counts / ranges, emit,
+//   stable sort by tile) -> [wait for the gaze event] -> plan + composite (level map, blend,
+//   inherit or interpolate)
 //
 // all enqueued on the caller's stream without a host synchronisation (except the very
 // first render of a scene created with automatic capacity, which measures the instance
@@ -457,9 +459,6 @@ PreParams pre_params(const a3fr_scene *s, int eyes) {
   return pp;
 }
 
-// The precompute of a render: projection, depth sort, tile counts and ranges, emission and the
-// tile sort.  allow_resize: the first render of an automatic-capacity scene measures the
-// instance count (one host synchronisation) and sizes the instance buffers.
 // First render of an automatic-capacity scene: read the instance count once, size the
 // instance buffers for twice that, and fix the kept count and the status of this render.
 int size_instances(a3fr_scene *s, cudaStream_t stream) {
@@ -531,6 +530,9 @@ int enqueue_bin_sorted(a3fr_scene *s, int eyes, const uint32_t *entries, const F
   return A3FR_OK;
 }
 
+// The precompute of a render: projection, depth sort and binning (tile ranges and the
+// instances in tile order).  allow_resize: the first render of an automatic-capacity scene
+// measures the instance count (one host synchronisation) and sizes the instance buffers.
 int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
                 uint64_t *launches) {
   const int n = s->desc.n;
