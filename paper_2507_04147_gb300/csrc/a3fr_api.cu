@@ -524,7 +524,7 @@ int enqueue_bin_sorted(a3fr_scene *s, int eyes, const uint32_t *entries, const F
     bool in_alt = false;
     A3FR_CHECK(launch_onesweep<uint32_t>(s->tkeys[0], v0, s->tkeys[1], v1, false, counts, s->capacity,
                                          tile_plan, tile_hist, tile_ctr, s->tile_lb, s->status,
-                                         &in_alt, stream));
+                                         &in_alt, stream, false, /*drop_final_keys=*/true));
     *launches += 2 + tile_plan.passes;
   }
   return A3FR_OK;
@@ -566,7 +566,8 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
     bool in_alt = false;
     A3FR_CHECK(launch_onesweep<uint32_t>(s->dkeys[0], s->dvals[0], s->dkeys[1], s->dvals[1], true,
                                          counts + 4, (size_t)n_entries, depth_plan, depth_hist,
-                                         depth_ctr, depth_lb, s->status, &in_alt, stream, false));
+                                         depth_ctr, depth_lb, s->status, &in_alt, stream, false,
+                                         /*drop_final_keys=*/true));
     *launches += 1 + depth_plan.passes;
   }
   const uint32_t *entries = s->dvals[depth_plan.passes % 2];

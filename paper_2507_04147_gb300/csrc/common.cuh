@@ -103,12 +103,14 @@ cudaError_t launch_depth_histogram(uint32_t *keys, const uint32_t *d_count, cons
 // Sorts d_count[0] (<= capacity) pairs with `plan`; hist holds the digit counts of every
 // pass, counters and lookback are zeroed scratch.  With implicit_vals the first pass takes
 // each pair's value to be its input position.  *result_in_alt tells where the result is.
+// drop_final_keys: the last pass writes only the values (the caller never reads the sorted
+// keys), so the result buffer's keys are left as they were.
 template <typename K>
 cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
                             bool implicit_vals, const uint32_t *d_count, size_t capacity,
                             const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
                             uint32_t *lookback, uint32_t *status, bool *result_in_alt,
-                            cudaStream_t s, bool small_parts = false);
+                            cudaStream_t s, bool small_parts = false, bool drop_final_keys = false);
 
 // The 64-bit pair sort of the public API: workspace = histograms | counters | look-back.
 size_t sort_workspace_bytes(size_t capacity);

@@ -157,7 +157,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
   if (trivial) {
     const uint32_t end = min(n, base + (uint32_t)PART);
     for (uint32_t i = base + t; i < end; i += kThreads) {
-      keys_out[i] = keys_in[i];
+      if (keys_out) keys_out[i] = keys_in[i];
       vals_out[i] = vals_in ? vals_in[i] : i;
     }
     return;
@@ -262,7 +262,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
     const K k = s_keys[i];
     const uint32_t o = s_gbase[(uint32_t)(k >> shift) & mask] + i;
     if (o < n) {   // always true unless a look-back wait gave up (status already set)
-      keys_out[o] = k;
+      if (keys_out) keys_out[o] = k;   // null: the caller reads only the values
       vals_out[o] = s_vals[i];
     }
   }
@@ -340,7 +340,7 @@ cudaError_t launch_onesweep_kpt(K *keys, uint32_t *vals, K *keys_alt, uint32_t *
                                 bool implicit_vals, const uint32_t *d_count, size_t capacity,
                                 const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
                                 uint32_t *lookback, uint32_t *status, bool *result_in_alt,
-                                cudaStream_t s) {
+                                cudaStream_t s, bool drop_final_keys) {
   *result_in_alt = false;
   if (capacity == 0) return cudaSuccess;
   cudaError_t e = set_smem_attr<K, KPT>();
@@ -353,8 +353,9 @@ cudaError_t launch_onesweep_kpt(K *keys, uint32_t *vals, K *keys_alt, uint32_t *
   for (int p = 0; p < plan.passes; ++p) {
     // the first pass may take the values to be the input positions (vals unread)
     const uint32_t *vsrc = (p == 0 && implicit_vals) ? nullptr : vin;
+    K *kdst = (drop_final_keys && p == plan.passes - 1) ? nullptr : kout;
     onesweep_kernel<K, KPT><<<(unsigned)parts, kThreads, dyn, s>>>(
-        kin, vsrc, kout, vout, d_count, hist + p * kRadix, counters + p,
+        kin, vsrc, kdst, vout, d_count, hist + p * kRadix, counters + p,
         lookback + (size_t)kRadix * parts * p, plan.shift[p], plan.mask, status);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -370,13 +371,14 @@ cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
                             bool implicit_vals, const uint32_t *d_count, size_t capacity,
                             const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
                             uint32_t *lookback, uint32_t *status, bool *result_in_alt,
-                            cudaStream_t s, bool small_parts) {
+                            cudaStream_t s, bool small_parts, bool drop_final_keys) {
   if (sizeof(K) == 4 && small_parts)
     return launch_onesweep_kpt<K, 8>(keys, vals, keys_alt, vals_alt, implicit_vals, d_count, capacity,
-                                     plan, hist, counters, lookback, status, result_in_alt, s);
+                                     plan, hist, counters, lookback, status, result_in_alt, s,
+                                     drop_final_keys);
   return launch_onesweep_kpt<K, Part<K>::kKPT>(keys, vals, keys_alt, vals_alt, implicit_vals, d_count,
                                                capacity, plan, hist, counters, lookback, status,
-                                               result_in_alt, s);
+                                               result_in_alt, s, drop_final_keys);
 }
 
 template cudaError_t launch_histogram<uint32_t>(const uint32_t *, const uint32_t *, size_t,
@@ -384,7 +386,7 @@ template cudaError_t launch_histogram<uint32_t>(const uint32_t *, const uint32_t
 template cudaError_t launch_onesweep<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *,
                                                bool, const uint32_t *, size_t, const SortPlan &,
                                                const uint32_t *, uint32_t *, uint32_t *,
-                                               uint32_t *, bool *, cudaStream_t, bool);
+                                               uint32_t *, bool *, cudaStream_t, bool, bool);
 
 // ---- the 64-bit pair sort of the public API (8-bit digits) ----
 constexpr size_t kHistBytes = sizeof(uint32_t) * kMaxSortPasses * kRadix;
