@@ -236,14 +236,20 @@ size_t plan_bytes(int n_ranges);
 // `uniform` from label 0 and sets cur; a later round (round != nullptr) renders from cur up
 // to the level of its gaze and radii, stores only those pixels, and raises cur.  Ranges are
 // clamped to kept[0] (the instances the sort kept).
-// p (host copy) decides the launch shape; the kernels read p_dev (the same values).
+// p (host copy) decides the launch shape; the kernels read p_dev (the same values).  With
+// fork (optional), the 32-pixel foveated composite's launches (one per label count) run
+// concurrently on fork->aux, joined back into s.
+struct ForkStreams {
+  cudaStream_t aux[3];
+  cudaEvent_t fork, join[3];
+};
 cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_dev,
                              const float *rec, int n, const uint2 *ranges, const uint32_t *kept,
                              const uint32_t *vals, const float *gaze, const RoundPlan *round,
                              int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, float *depth,
                              unsigned long long *counters, int batch_mult, uint32_t *thresholds,
-                             cudaStream_t s);
+                             cudaStream_t s, const ForkStreams *fork = nullptr);
 
 // Incremental rounds (Sec. 3.3, Alg. 1): state on the device, mailbox in mapped host memory.
 struct RoundConfig {

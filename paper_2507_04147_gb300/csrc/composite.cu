@@ -448,17 +448,19 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
 
 
 // 32 x 32 tiles (the paper's tiling, Sec. 3.5): a tile is 16 x 16 blocks of 2 x 2 pixels and
-// each of its four labels is one 256-thread group; a level-k tile runs the groups of its
-// labels (lo, lo + k] and no other.  A warp's pixels are one label of an 8 x 4 patch of blocks
-// (a 16 x 8 pixel area), which many of the tile's Gaussians cannot reach: each staged Gaussian
-// carries the box where its alpha can reach 1/255, and a warp skips (uniformly) the Gaussians
-// whose box misses its patch -- those would fail the 1/255 test at every pixel of the patch,
-// so the image is unchanged.  Here each (tile, label) pair is one CTA, taken from the
-// same level buckets as the 16-pixel kernel (a bucket-c entry spawns c CTAs), so only the
-// groups that render are ever launched.  The label-1 CTA of a tile rendered from label 0
-// also writes the inherited pixels of its blocks.
-template <bool kAux, bool kFull, int kMult>
-__global__ void __launch_bounds__(kThreads, 6)
+// a level-k tile renders the k labels (lo, lo + k] of every block and no others.  One
+// 256-thread CTA renders all the labels a tile needs: launch P (1..4) takes the plan's bucket
+// of tiles with P labels to render, and each lane renders those P pixels of its block, so a
+// tile's Gaussian list is staged once whatever its level and each staged Gaussian is set up
+// once for the lane's P pixels (the per-pixel arithmetic is the same as with one pixel).  A
+// warp covers an 8 x 4 patch of blocks (a 16 x 8 pixel area), which many of the tile's
+// Gaussians cannot reach: each staged Gaussian carries the box where its alpha can reach
+// 1/255, and after staging every warp builds its hit list (box test, then the exact falloff
+// over the patch) -- a Gaussian left out fails the 1/255 test at every pixel of the patch, so
+// the image is unchanged.  A tile rendered from label 0 also writes the inherited pixels of
+// its blocks (the labels above its level take the top-left value).
+template <bool kAux, bool kFull, int kMult, int P>
+__global__ void __launch_bounds__(kThreads, (P == 1 ? 6 : (P == 2 ? 5 : 4)))
 composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
                    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
                    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ plan,
@@ -479,55 +481,44 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
   __shared__ int s_done[kThreads / 32];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
   const int n_ranges = p.n_eyes * p.n_tiles;
-  int gtile, label, level = 4, lo = 0;
+  int gtile, lo = 0, level = 4;
   if (kFull) {
-    gtile = blockIdx.x >> 2;
-    label = blockIdx.x & 3;
-    if (label == 0 && t == 0) levels[gtile] = 4;
+    gtile = blockIdx.x;
+    if (gtile >= n_ranges) return;
+    if (t == 0) levels[gtile] = 4;
   } else {
-    const int c = blockIdx.x;
-    const int n4 = plan_counts[3], n3 = plan_counts[2], n2 = plan_counts[1], n1 = plan_counts[0];
-    const int c3 = 4 * n4, c2 = c3 + 3 * n3, c1 = c2 + 2 * n2, c0 = c1 + n1;
-    uint32_t entry;
-    int count, sub;
-    if (c < c3) {
-      entry = plan[3 * (size_t)n_ranges + c / 4];
-      count = 4;
-      sub = c & 3;
-    } else if (c < c2) {
-      entry = plan[2 * (size_t)n_ranges + (c - c3) / 3];
-      count = 3;
-      sub = (c - c3) % 3;
-    } else if (c < c1) {
-      entry = plan[(size_t)n_ranges + (c - c2) / 2];
-      count = 2;
-      sub = (c - c2) & 1;
-    } else if (c < c0) {
-      entry = plan[c - c1];
-      count = 1;
-      sub = 0;
-    } else {
-      return;
-    }
+    if (blockIdx.x >= plan_counts[P - 1]) return;
+    const uint32_t entry = plan[(size_t)(P - 1) * n_ranges + blockIdx.x];
     gtile = (int)(entry >> 2);
     lo = (int)(entry & 3u);
-    level = lo + count;
-    label = lo + sub;
+    level = lo + P;
   }
   const int eye = gtile / p.n_tiles;
   const int tile = gtile - eye * p.n_tiles;
   const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
-  const int ox = (label == 1 || label == 2) ? 1 : 0;   // BR, TR
-  const int oy = (label == 1 || label == 3) ? 1 : 0;   // BR, BL
   // warp w covers an 8 x 4 patch of blocks (column half w & 1, row quarter w >> 1): a squarer
   // footprint than a strip, so fewer Gaussian boxes reach it
   const int bx = (lane & 7) + 8 * (warp & 1), by = (lane >> 3) + 4 * (warp >> 1);
-  const int px = tx * T32 + 2 * bx + ox, py = ty * T32 + 2 * by + oy;
-  const bool inside = px < p.width && py < p.height;
-  const float fpx = (float)px, fpy = (float)py;
-  // the warp's pixels: one label of its 8 x 4 block patch (every other pixel)
-  const float wx0 = (float)(tx * T32 + 16 * (warp & 1) + ox), wx1 = wx0 + 14.0f;
-  const float wy0 = (float)(ty * T32 + 8 * (warp >> 1) + oy), wy1 = wy0 + 6.0f;
+  const int px0 = tx * T32 + 2 * bx, py0 = ty * T32 + 2 * by;   // the block's top-left pixel
+  // the lane's pixels: labels lo .. lo + P - 1 of its block (TL, BR, TR, BL)
+  float fpx[P], fpy[P];
+  bool inside[P];
+  int any_ox = 0, all_ox = 1, any_oy = 0, all_oy = 1;
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    const int L = lo + k;
+    const int ox = (L == 1 || L == 2) ? 1 : 0, oy = (L == 1 || L == 3) ? 1 : 0;
+    any_ox |= ox;
+    all_ox &= ox;
+    any_oy |= oy;
+    all_oy &= oy;
+    inside[k] = px0 + ox < p.width && py0 + oy < p.height;
+    fpx[k] = (float)(px0 + ox);
+    fpy[k] = (float)(py0 + oy);
+  }
+  // the warp's patch: the span of its pixels (one label: every other pixel of 16 x 8)
+  const float wx0 = (float)(tx * T32 + 16 * (warp & 1) + all_ox), wx1 = (float)(tx * T32 + 16 * (warp & 1) + 14 + any_ox);
+  const float wy0 = (float)(ty * T32 + 8 * (warp >> 1) + all_oy), wy1 = (float)(ty * T32 + 8 * (warp >> 1) + 6 + any_oy);
 
   uint2 range = ranges[gtile];
   const uint32_t n_kept = *kept;
@@ -535,11 +526,25 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
   range.y = min(range.y, n_kept);
   const float *rec_eye = rec + (size_t)eye * n * kRec;
 
-  float T = 1.0f, C0 = 0.0f, C1 = 0.0f, C2 = 0.0f, Z = 0.0f;
-  uint32_t last = 0, stop = 0, staged = 0;
-  bool done = !inside;
+  float T[P], C0[P], C1[P], C2[P], Z[P];
+  uint32_t last[P], stop[P];
+  bool done[P];
+#pragma unroll
+  for (int k = 0; k < P; ++k) {
+    T[k] = 1.0f;
+    C0[k] = C1[k] = C2[k] = Z[k] = 0.0f;
+    last[k] = stop[k] = 0u;
+    done[k] = !inside[k];
+  }
+  auto all_done = [&]() {
+    bool a = true;
+#pragma unroll
+    for (int k = 0; k < P; ++k) a = a && done[k];
+    return a;
+  };
+  uint32_t staged = 0;
   for (uint32_t start = range.x; start < range.y; start += NB) {
-    const bool wdone = __all_sync(0xffffffffu, done);
+    const bool wdone = __all_sync(0xffffffffu, all_done());
     if (lane == 0) s_done[warp] = wdone;
     __syncthreads();
     bool all = true;
@@ -569,7 +574,7 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
       }
     }
     __syncthreads();
-    if (!__all_sync(0xffffffffu, done)) {
+    if (!__all_sync(0xffffffffu, all_done())) {
       // the warp's hit list: 32 Gaussians tested per step (support box, then the falloff
       // over the patch), slots kept in list order
       int n_hit = 0;
@@ -616,55 +621,66 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
           const float4 geo = s_geo[e];
           const float2 cz = s_cz[e];
           const float4 rgb = s_rgb[e];
-          const float dx = __fsub_rn(geo.x, fpx), dy = __fsub_rn(geo.y, fpy);
-          const float pw = falloff_log2(geo.z, geo.w, cz.x, dx, dy);
-          const float alpha = blend_alpha(rgb.w, pw);
-          const float tt = __fmul_rn(T, __fsub_rn(1.0f, alpha));
-          const bool ok = !done && pw <= 0.0f && alpha >= 1.0f / 255.0f;
-          const bool fin = ok && tt < 0.0001f;
-          const bool upd = ok && !fin;
           const uint32_t pos = pos0 + (uint32_t)e;
-          const float w = upd ? alpha * T : 0.0f;
-          C0 += rgb.x * w;
-          C1 += rgb.y * w;
-          C2 += rgb.z * w;
-          if (kAux) Z += cz.y * w;
-          T = upd ? tt : T;
-          last = upd ? pos : last;
-          stop = fin ? pos : stop;
-          done = done || fin;
+#pragma unroll
+          for (int k = 0; k < P; ++k) {
+            const float dx = __fsub_rn(geo.x, fpx[k]), dy = __fsub_rn(geo.y, fpy[k]);
+            const float pw = falloff_log2(geo.z, geo.w, cz.x, dx, dy);
+            const float alpha = blend_alpha(rgb.w, pw);
+            const float tt = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
+            const bool ok = !done[k] && pw <= 0.0f && alpha >= 1.0f / 255.0f;
+            const bool fin = ok && tt < 0.0001f;
+            const bool upd = ok && !fin;
+            const float w = upd ? alpha * T[k] : 0.0f;
+            C0[k] += rgb.x * w;
+            C1[k] += rgb.y * w;
+            C2[k] += rgb.z * w;
+            if (kAux) Z[k] += cz.y * w;
+            T[k] = upd ? tt : T[k];
+            last[k] = upd ? pos : last[k];
+            stop[k] = fin ? pos : stop[k];
+            done[k] = done[k] || fin;
+          }
         }
-        if (__all_sync(0xffffffffu, done)) break;
+        if (__all_sync(0xffffffffu, all_done())) break;
       }
     }
     __syncthreads();
   }
-  if (inside && !done) stop = range.y - range.x;
-
-  if (inside) {
-    // this label's pixel, and for label 1 of a tile rendered from label 0 the inherited
-    // pixels of its block (BR for level < 2, TR for level < 3, BL for level < 4)
+  unsigned long long ev = 0;
 #pragma unroll
-    for (int k = -1; k < 3; ++k) {
-      int dx = 0, dy = 0;
-      if (k >= 0) {
-        if (kFull || incremental || label != 0 || level >= k + 2) continue;
-        dx = k < 2 ? 1 : 0;
-        dy = k == 1 ? 0 : 1;
-        if (px + dx >= p.width || py + dy >= p.height) continue;
-      }
-      const size_t pix = ((size_t)eye * p.height + py + dy) * p.width + px + dx;
-      out[3 * pix] = C0;
-      out[3 * pix + 1] = C1;
-      out[3 * pix + 2] = C2;
+  for (int k = 0; k < P; ++k) {
+    if (inside[k] && !done[k]) stop[k] = range.y - range.x;
+    if (!inside[k]) continue;
+    ev += stop[k];
+    const size_t pix = ((size_t)eye * p.height + (size_t)fpy[k]) * p.width + (size_t)fpx[k];
+    out[3 * pix] = C0[k];
+    out[3 * pix + 1] = C1[k];
+    out[3 * pix + 2] = C2[k];
+    if (kAux) {
+      t_final[pix] = T[k];
+      n_contrib[pix] = last[k];
+      depth[pix] = Z[k];
+    }
+  }
+  if (!kFull && !incremental && lo == 0 && level < 4 && inside[0]) {
+    // the inherited pixels of the block: the labels above the level take the top-left value
+#pragma unroll
+    for (int L = 1; L < 4; ++L) {
+      if (L < level) continue;
+      const int dx = (L == 1 || L == 2) ? 1 : 0, dy = (L == 1 || L == 3) ? 1 : 0;
+      if (px0 + dx >= p.width || py0 + dy >= p.height) continue;
+      const size_t pix = ((size_t)eye * p.height + py0 + dy) * p.width + px0 + dx;
+      out[3 * pix] = C0[0];
+      out[3 * pix + 1] = C1[0];
+      out[3 * pix + 2] = C2[0];
       if (kAux) {
-        t_final[pix] = T;
-        n_contrib[pix] = last;
-        depth[pix] = Z;
+        t_final[pix] = T[0];
+        n_contrib[pix] = last[0];
+        depth[pix] = Z[0];
       }
     }
   }
-  unsigned long long ev = stop;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
   if (lane == 0) {
@@ -741,7 +757,7 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
                              int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, float *depth,
                              unsigned long long *counters, int batch_mult, uint32_t *thresholds,
-                             cudaStream_t s) {
+                             cudaStream_t s, const ForkStreams *fork) {
   const int n_ranges = p.n_eyes * p.n_tiles;
   if (n_ranges <= 0) return cudaSuccess;
   uint32_t *pc = plan + 4 * (size_t)n_ranges;
@@ -762,36 +778,68 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
   const int inc = round != nullptr ? 1 : 0;
   const bool aux = t_final != nullptr;
   const int mult = batch_mult == 2 ? 2 : 1;
-  // one composite kernel per (tile, aux, full, batch) combination; shared memory preferred so
-  // that registers, not the carveout, set residency
-  auto launch = [&](auto kern, int grid) -> cudaError_t {
-    static bool carve[64][64] = {};
+  // one composite kernel per (tile, aux, full, batch[, labels]) combination; shared memory
+  // preferred so that registers, not the carveout, set residency
+  auto launch_on = [&](cudaStream_t st, auto kern, int grid, int variant) -> cudaError_t {
+    static bool carve[64][128] = {};
     int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64) {
-      const int slot = (p.tile == 32 ? 32 : 0) + (aux ? 16 : 0) + (p.full ? 8 : 0) + mult;
-      if (!carve[dev][slot]) {
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && variant >= 0 && variant < 128) {
+      if (!carve[dev][variant]) {
         cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                              cudaSharedmemCarveoutMaxShared);
-        carve[dev][slot] = true;
+        carve[dev][variant] = true;
       }
     }
-    kern<<<grid, kThreads, 0, s>>>(p_dev, rec, n, ranges, kept, vals, plan, pc, p.full ? 0 : inc, levels,
-                                   t_final, n_contrib, depth, counters);
+    kern<<<grid, kThreads, 0, st>>>(p_dev, rec, n, ranges, kept, vals, plan, pc, p.full ? 0 : inc, levels,
+                                    t_final, n_contrib, depth, counters);
     return cudaGetLastError();
   };
-  const int g16 = n_ranges, g32 = 4 * n_ranges;
-#define A3FR_COMPOSITE_CASE(K, GRID)                                                        \
-  if (aux) {                                                                               \
-    if (p.full) return mult == 2 ? launch(K<true, true, 2>, GRID) : launch(K<true, true, 1>, GRID); \
-    return mult == 2 ? launch(K<true, false, 2>, GRID) : launch(K<true, false, 1>, GRID);    \
-  }                                                                                        \
-  if (p.full) return mult == 2 ? launch(K<false, true, 2>, GRID) : launch(K<false, true, 1>, GRID); \
-  return mult == 2 ? launch(K<false, false, 2>, GRID) : launch(K<false, false, 1>, GRID);
+  auto launch = [&](auto kern, int grid, int variant) { return launch_on(s, kern, grid, variant); };
+  const int var = (aux ? 64 : 0) + (p.full ? 32 : 0) + (mult == 2 ? 16 : 0);
   if (p.tile == 32) {
-    A3FR_COMPOSITE_CASE(composite32_kernel, g32)
+    // one launch per label count (the full render: every tile renders all four labels)
+#define A3FR_C32(AUX, FULL, MULT, P) launch(composite32_kernel<AUX, FULL, MULT, P>, n_ranges, var + 4 + P)
+#define A3FR_C32_ON(ST, AUX, MULT, P) \
+  launch_on(ST, composite32_kernel<AUX, false, MULT, P>, n_ranges, var + 4 + P)
+#define A3FR_C32_FOV(AUX, MULT)                                                  \
+  {                                                                              \
+    cudaError_t e2 = cudaSuccess;                                                \
+    if (fork) {                                                                  \
+      e2 = cudaEventRecord(fork->fork, s);                                       \
+      for (int f = 0; f < 3 && e2 == cudaSuccess; ++f)                           \
+        e2 = cudaStreamWaitEvent(fork->aux[f], fork->fork, 0);                   \
+    }                                                                            \
+    if (e2 == cudaSuccess) e2 = A3FR_C32_ON(s, AUX, MULT, 4);                    \
+    if (e2 == cudaSuccess) e2 = A3FR_C32_ON(fork ? fork->aux[0] : s, AUX, MULT, 2); \
+    if (e2 == cudaSuccess) e2 = A3FR_C32_ON(fork ? fork->aux[1] : s, AUX, MULT, 1); \
+    if (e2 == cudaSuccess) e2 = A3FR_C32_ON(fork ? fork->aux[2] : s, AUX, MULT, 3); \
+    if (fork) {                                                                  \
+      for (int f = 0; f < 3 && e2 == cudaSuccess; ++f) {                         \
+        e2 = cudaEventRecord(fork->join[f], fork->aux[f]);                       \
+        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, fork->join[f], 0);    \
+      }                                                                          \
+    }                                                                            \
+    return e2;                                                                   \
   }
-  A3FR_COMPOSITE_CASE(composite_kernel, g16)
-#undef A3FR_COMPOSITE_CASE
+    if (p.full) {
+      if (aux) return mult == 2 ? A3FR_C32(true, true, 2, 4) : A3FR_C32(true, true, 1, 4);
+      return mult == 2 ? A3FR_C32(false, true, 2, 4) : A3FR_C32(false, true, 1, 4);
+    }
+    if (aux) {
+      if (mult == 2) A3FR_C32_FOV(true, 2) else A3FR_C32_FOV(true, 1)
+    }
+    if (mult == 2) A3FR_C32_FOV(false, 2) else A3FR_C32_FOV(false, 1)
+#undef A3FR_C32_FOV
+#undef A3FR_C32_ON
+#undef A3FR_C32
+  }
+  const int g16 = n_ranges;
+  if (aux) {
+    if (p.full) return mult == 2 ? launch(composite_kernel<true, true, 2>, g16, var) : launch(composite_kernel<true, true, 1>, g16, var);
+    return mult == 2 ? launch(composite_kernel<true, false, 2>, g16, var) : launch(composite_kernel<true, false, 1>, g16, var);
+  }
+  if (p.full) return mult == 2 ? launch(composite_kernel<false, true, 2>, g16, var) : launch(composite_kernel<false, true, 1>, g16, var);
+  return mult == 2 ? launch(composite_kernel<false, false, 2>, g16, var) : launch(composite_kernel<false, false, 1>, g16, var);
 }
 
 }  // namespace a3fr
