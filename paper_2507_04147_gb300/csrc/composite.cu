@@ -460,7 +460,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
 // the image is unchanged.  A tile rendered from label 0 also writes the inherited pixels of
 // its blocks (the labels above its level take the top-left value).
 template <bool kAux, bool kFull, int kMult, int P>
-__global__ void __launch_bounds__(kThreads, (P == 1 ? 6 : (P == 2 ? 5 : 4)))
+__global__ void __launch_bounds__(kThreads, (P == 1 ? 6 : (P == 2 ? 5 : (P == 3 ? 4 : 3))))
 composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
                    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
                    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ plan,
