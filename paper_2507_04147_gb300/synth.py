@@ -217,18 +217,18 @@ class Workload:
 
 def small_single_view(seed: int = 0) -> Workload:
     """20k Gaussians, SH degree 0, one 256x256 view, 16x16 tiles, gaze at the centre."""
-    return Workload("20k-G SH0 256x256 mono, 16px tiles, centre gaze",
+    return Workload("20k-G SH0 256x256 mono, centre gaze",
                     uniform_scene(20000, 0, seed), 256, 256, 1, 16, 1, 0.0, (18.0, 36.0),
                     fixed_gaze_px=(127.5, 127.5))
 
 
 def stereo_500k(seed: int = 0, frames: int = 240) -> Workload:
     """500k Gaussians, SH degree 3, stereo 1280x1280, 240 frames of gaze at 90 Hz."""
-    return Workload("500k-G SH3 stereo 1280x1280, 16px tiles, 240-frame gaze trajectory",
+    return Workload("500k-G SH3 stereo 1280x1280, 240-frame gaze trajectory",
                     uniform_scene(500000, 3, seed), 1280, 1280, 2, 16, frames, 0.05, (18.0, 36.0))
 
 
 def stereo_3m_clustered(seed: int = 0, frames: int = 240) -> Workload:
     """3M clustered Gaussians, SH degree 3, stereo 2064x2208, 240 frames at 90 Hz."""
-    return Workload("3M-G clustered SH3 stereo 2064x2208, 16px tiles, 240-frame gaze trajectory",
+    return Workload("3M-G clustered SH3 stereo 2064x2208, 240-frame gaze trajectory",
                     clustered_scene(3000000, 3, seed), 2064, 2208, 2, 16, frames, 0.05, (18.0, 36.0))
