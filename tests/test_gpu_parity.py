@@ -188,15 +188,17 @@ def test_stereo_500k_sh3_sampled_pixels(tile, binning):
         print(e, check_eye(r, e, w.scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv, pixels=pix))
 
 
-def test_graph_mode_matches_direct_launches_bitwise():
+@pytest.mark.parametrize("tile", [16, 32])
+def test_graph_mode_matches_direct_launches_bitwise(tile):
     """Replayed CUDA graphs see each render's cameras, gaze and output through device-resident
-    parameters, so they must reproduce the directly launched renders exactly."""
+    parameters, so they must reproduce the directly launched renders exactly (with 32-pixel
+    tiles the foveated composite's launches are parallel branches of the graph)."""
     import torch
     w = synth.stereo_500k(frames=240)
     scene_np = w.scene.subset(np.arange(60000))
     traj = synth.gaze_trajectory(240)
-    direct = a3fr.Scene.from_numpy(scene_np)
-    graph = a3fr.Scene.from_numpy(scene_np)
+    direct = a3fr.Scene.from_numpy(scene_np, tile=tile)
+    graph = a3fr.Scene.from_numpy(scene_np, tile=tile)
     graph.graph_mode(True)
     for s in (direct, graph):
         for e, c in enumerate(w.cameras(0)):
@@ -220,7 +222,8 @@ def test_graph_mode_matches_direct_launches_bitwise():
 
 @pytest.mark.parametrize("batch_mult", [1, 2])
 def test_tile32_foveated_and_full(batch_mult):
-    """32-pixel tiles (one CTA per tile label) against the oracle run with 32-pixel tiles."""
+    """32-pixel tiles (one CTA per tile rendering all its labels) against the oracle run with
+    32-pixel tiles."""
     scene = synth.uniform_scene(8000, 3, seed=13)
     cams = synth.stereo_cameras(200, 136, yaw_deg=2.0)
     gaze = np.array([[70.0, 60.0], [66.0, 61.0]], np.float32)
