@@ -172,7 +172,7 @@ int tile_bits_for(int n_ranges) {
 
 // Byte offsets inside frame_ws; everything in it starts at zero every render.
 struct FrameLayout {
-  size_t counts = 0;                 // counts[0..7] u32 ([6]: emit's block counter), [8..9] the u64 instance total
+  size_t counts = 0;                 // counts[0..7] u32 ([6]: emit's block counter), [8..9] the u64 instance total, [10] the depth sort's skipped last pass
   size_t depth_hist = 64;            // kMaxSortPasses x 256 u32
   size_t depth_ctr = 64 + 8192;      // kMaxSortPasses u32 (+pad)
   size_t tile_hist = 64 + 8192 + 64; // sort-based binning: the tile sort's histograms, counters
@@ -480,7 +480,7 @@ int size_instances(a3fr_scene *s, cudaStream_t stream) {
 // The sort-based binning (renders with more than kBinDirectMaxTiles tiles): tile counts ->
 // ranges and the tile sort's histograms, emit of the depth-ordered instances, stable
 // onesweep by tile index.  The sort's result lands in s->vals.
-int enqueue_bin_sorted(a3fr_scene *s, int eyes, const uint32_t *entries, const FrameLayout &L,
+int enqueue_bin_sorted(a3fr_scene *s, int eyes, Entries entries, const FrameLayout &L,
                        cudaStream_t stream, bool allow_resize, uint64_t *launches) {
   const int n = s->desc.n;
   const SortPlan tile_plan = sort_plan(tile_bits_for(eyes * s->n_tiles), 8);
@@ -568,10 +568,13 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
     A3FR_CHECK(launch_onesweep<uint32_t>(s->dkeys[0], s->dvals[0], s->dkeys[1], s->dvals[1], true,
                                          counts + 4, (size_t)n_entries, depth_plan, depth_hist,
                                          depth_ctr, depth_lb, s->status, &in_alt, stream, false,
-                                         /*drop_final_keys=*/true));
+                                         /*drop_final_keys=*/true, /*final_skip=*/counts + 10));
     *launches += 1 + depth_plan.passes;
   }
-  const uint32_t *entries = s->dvals[depth_plan.passes % 2];
+  // the last pass's digit (the top 8 bits of the rebased depth) is often one bucket: that pass
+  // then writes nothing and sets counts[10], and the kernels below read its input instead
+  const Entries entries{{s->dvals[depth_plan.passes % 2], s->dvals[(depth_plan.passes + 1) % 2]},
+                        counts + 10};
   A3FR_CHECK(mark(s, A3FR_STAGE_BIN, stream));
   if (s->sorted_bin) return enqueue_bin_sorted(s, eyes, entries, L, stream, allow_resize, launches);
   // per-chunk tile counts -> tile ranges, per-chunk starts, totals

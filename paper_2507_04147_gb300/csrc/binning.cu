@@ -67,8 +67,9 @@ __device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long l
 // Per chunk: the instance count of every tile by shared-memory atomics over the chunk's
 // tile rectangles (each thread walks the rectangles of its entries), written as h[c][r].
 __global__ void __launch_bounds__(kCountThreads)
-bin_count_kernel(BinParams p, const uint32_t *__restrict__ entries, const ushort4 *__restrict__ rect,
+bin_count_kernel(BinParams p, Entries ents, const ushort4 *__restrict__ rect,
                  const uint32_t *__restrict__ bounds, uint32_t *__restrict__ h) {
+  const uint32_t *__restrict__ entries = ents.get();
   extern __shared__ uint32_t s_hist[];
   const int t = threadIdx.x;
   const int n_ranges = p.n_eyes * p.n_tiles;
@@ -132,10 +133,11 @@ __device__ unsigned long long block_lookback(unsigned long long *lookback, int b
 // entry j writes bounds[c] = j + 1 for the c with floor(P_j C / T) < c <= floor(P_{j+1} C / T).
 // The blocks chain their sums by the same look-back as bin_offsets.
 __global__ void __launch_bounds__(kPlanThreads)
-bin_plan_kernel(BinParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
+bin_plan_kernel(BinParams p, Entries ents, const uint32_t *__restrict__ touched,
                 const unsigned long long *__restrict__ inst_total,
                 unsigned long long *__restrict__ lookback, uint32_t *__restrict__ bounds,
                 uint32_t *__restrict__ status) {
+  const uint32_t *__restrict__ entries = ents.get();
   __shared__ unsigned long long s_warp[kPlanThreads / 32];
   __shared__ unsigned long long s_before;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -295,9 +297,10 @@ __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
 // of h, copied in by cp.async) and the map.  Entry values are loaded two rounds ahead,
 // rectangles one round ahead.
 __global__ void __launch_bounds__(32)
-bin_emit_kernel(BinParams p, const uint32_t *__restrict__ entries, const ushort4 *__restrict__ rect,
+bin_emit_kernel(BinParams p, Entries ents, const ushort4 *__restrict__ rect,
                 const uint32_t *__restrict__ bounds, const uint32_t *__restrict__ h,
                 uint32_t *__restrict__ vals) {
+  const uint32_t *__restrict__ entries = ents.get();
   extern __shared__ __align__(16) uint32_t s_dyn[];
   __shared__ uint32_t s_map_tile[kMapPad];
   __shared__ uint32_t s_map_gid[kMapPad];
@@ -479,7 +482,7 @@ size_t bin_plan_lookback_bytes(int n_entries) {
   return sizeof(unsigned long long) * (size_t)((n_entries + kPlanEntries - 1) / kPlanEntries + 1);
 }
 
-cudaError_t launch_bin_plan(const BinParams &p, const uint32_t *entries, const uint32_t *touched,
+cudaError_t launch_bin_plan(const BinParams &p, Entries entries, const uint32_t *touched,
                             const unsigned long long *inst_total, unsigned long long *lookback,
                             uint32_t *bounds, uint32_t *status, cudaStream_t s) {
   const int blocks = p.n_entries > 0 ? (p.n_entries + kPlanEntries - 1) / kPlanEntries : 1;
@@ -488,7 +491,7 @@ cudaError_t launch_bin_plan(const BinParams &p, const uint32_t *entries, const u
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin_count(const BinParams &p, const uint32_t *entries, const ushort4 *rect,
+cudaError_t launch_bin_count(const BinParams &p, Entries entries, const ushort4 *rect,
                              const uint32_t *bounds, uint32_t *h, cudaStream_t s) {
   const size_t smem = bin_count_smem_bytes(p.n_eyes, p.tiles_x, p.tiles_y);
   cudaError_t e = cudaFuncSetAttribute(bin_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -515,7 +518,7 @@ cudaError_t launch_bin_offsets(const BinParams &p, uint32_t *h, unsigned long lo
   return cudaGetLastError();
 }
 
-cudaError_t launch_bin_emit(const BinParams &p, const uint32_t *entries, const ushort4 *rect,
+cudaError_t launch_bin_emit(const BinParams &p, Entries entries, const ushort4 *rect,
                             const uint32_t *bounds, const uint32_t *h, uint32_t *vals,
                             cudaStream_t s) {
   if (p.n_entries <= 0 || p.capacity == 0) return cudaSuccess;

@@ -34,8 +34,9 @@ constexpr int kEmitEntries = kEmitThreads * kEmitPer;      // entries per block
 // finish (fence + counter: the blocks never wait on one another) turns the sums into
 // exclusive prefixes in place, with the total after the last block.
 __global__ void __launch_bounds__(kEmitThreads)
-emit_count_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
+emit_count_kernel(EmitParams p, Entries ents, const uint32_t *__restrict__ touched,
                   unsigned long long *__restrict__ blk, uint32_t *__restrict__ done_counter) {
+  const uint32_t *__restrict__ entries = ents.get();
   __shared__ unsigned long long s_w[kEmitWarps];
   __shared__ unsigned long long s_carry;
   __shared__ bool s_last;
@@ -89,9 +90,10 @@ emit_count_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint
 // load-balanced: one output slot per thread at a time (consecutive threads, consecutive
 // slots), its entry found by binary search over the block's exclusive offsets.
 __global__ void __launch_bounds__(kEmitThreads)
-emit_kernel(EmitParams p, const uint32_t *__restrict__ entries, const uint32_t *__restrict__ touched,
+emit_kernel(EmitParams p, Entries ents, const uint32_t *__restrict__ touched,
             const ushort4 *__restrict__ rect, uint32_t *__restrict__ tile_keys,
             uint32_t *__restrict__ vals, const unsigned long long *__restrict__ blk) {
+  const uint32_t *__restrict__ entries = ents.get();
   __shared__ uint32_t s_warp_total[kEmitWarps];
   __shared__ uint32_t s_excl[kEmitEntries + 1];   // exclusive instance offsets of the entries
   __shared__ uint32_t s_tile0[kEmitEntries], s_width[kEmitEntries], s_gid[kEmitEntries];
@@ -357,7 +359,7 @@ size_t emit_lookback_bytes(int n_entries) {
   return sizeof(unsigned long long) * (size_t)((n_entries + kEmitEntries - 1) / kEmitEntries + 1);
 }
 
-cudaError_t launch_emit(const EmitParams &p, const uint32_t *entries, const uint32_t *touched,
+cudaError_t launch_emit(const EmitParams &p, Entries entries, const uint32_t *touched,
                         const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
                         unsigned long long *blk, uint32_t *done_counter, cudaStream_t s) {
   if (p.n_entries <= 0) return cudaSuccess;

@@ -104,19 +104,32 @@ cudaError_t launch_depth_histogram(uint32_t *keys, const uint32_t *d_count, cons
 // pass, counters and lookback are zeroed scratch.  With implicit_vals the first pass takes
 // each pair's value to be its input position.  *result_in_alt tells where the result is.
 // drop_final_keys: the last pass writes only the values (the caller never reads the sorted
-// keys), so the result buffer's keys are left as they were.
+// keys), so the result buffer's keys are left as they were.  final_skip (zeroed by the caller):
+// a last pass that is the identity (its digit the same for every key) is skipped and sets
+// *final_skip; the result is then in the last pass's input buffers (see Entries).
 template <typename K>
 cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
                             bool implicit_vals, const uint32_t *d_count, size_t capacity,
                             const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
                             uint32_t *lookback, uint32_t *status, bool *result_in_alt,
-                            cudaStream_t s, bool small_parts = false, bool drop_final_keys = false);
+                            cudaStream_t s, bool small_parts = false, bool drop_final_keys = false,
+                            uint32_t *final_skip = nullptr);
 
 // The 64-bit pair sort of the public API: workspace = histograms | counters | look-back.
 size_t sort_workspace_bytes(size_t capacity);
 cudaError_t launch_sort(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                         const uint32_t *d_count, size_t capacity, int key_bits, void *workspace,
                         uint32_t *status, bool *result_in_alt, cudaStream_t s);
+
+// The depth-sorted entries: buf[0], or buf[1] when *sel is set (the depth sort skipped its
+// identity last pass, leaving the result in that pass's input).
+struct Entries {
+  const uint32_t *buf[2];
+  const uint32_t *sel;
+  __device__ __forceinline__ const uint32_t *get() const {
+    return (sel != nullptr && *sel != 0u) ? buf[1] : buf[0];
+  }
+};
 
 // Tile binning of the depth-ordered entries (see binning.cu): per-chunk tile counts
 // (bin_count), tile ranges and per-chunk starts (bin_offsets), and the ordered placement of
@@ -142,11 +155,11 @@ size_t bin_smem_bytes(int n_eyes, int tiles_x, int tiles_y);
 // instance counts; inst_total is the render's instance total (preprocess), lookback
 // (bin_plan_lookback_bytes, zeroed by the caller) chains the CTAs' sums.
 size_t bin_plan_lookback_bytes(int n_entries);
-cudaError_t launch_bin_plan(const BinParams &p, const uint32_t *entries, const uint32_t *touched,
+cudaError_t launch_bin_plan(const BinParams &p, Entries entries, const uint32_t *touched,
                             const unsigned long long *inst_total, unsigned long long *lookback,
                             uint32_t *bounds, uint32_t *status, cudaStream_t s);
 // h[c][r] <- chunk c's instances of tile r.
-cudaError_t launch_bin_count(const BinParams &p, const uint32_t *entries, const ushort4 *rect,
+cudaError_t launch_bin_count(const BinParams &p, Entries entries, const ushort4 *rect,
                              const uint32_t *bounds, uint32_t *h, cudaStream_t s);
 // ranges, h[c][r] <- start slot of chunk c's instances of tile r, counts[0] kept, [1] first
 // eye, [3] total; the capacity status when the total exceeds the capacity.  lookback
@@ -155,7 +168,7 @@ size_t bin_lookback_bytes(int n_eyes, int n_tiles);
 cudaError_t launch_bin_offsets(const BinParams &p, uint32_t *h, unsigned long long *lookback,
                                uint2 *ranges, uint32_t *counts, uint32_t *status, cudaStream_t s);
 // vals[slot] <- Gaussian index of every instance, each tile's run in entry order.
-cudaError_t launch_bin_emit(const BinParams &p, const uint32_t *entries, const ushort4 *rect,
+cudaError_t launch_bin_emit(const BinParams &p, Entries entries, const ushort4 *rect,
                             const uint32_t *bounds, const uint32_t *h, uint32_t *vals,
                             cudaStream_t s);
 
@@ -167,7 +180,7 @@ struct EmitParams {
   uint32_t capacity;
 };
 size_t emit_lookback_bytes(int n_entries);
-cudaError_t launch_emit(const EmitParams &p, const uint32_t *entries, const uint32_t *touched,
+cudaError_t launch_emit(const EmitParams &p, Entries entries, const uint32_t *touched,
                         const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
                         unsigned long long *blk, uint32_t *done_counter, cudaStream_t s);
 

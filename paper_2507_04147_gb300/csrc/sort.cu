@@ -133,7 +133,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
                 K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                 const uint32_t *__restrict__ d_count, const uint32_t *__restrict__ hist,
                 uint32_t *__restrict__ part_counter, uint32_t *__restrict__ lookback, int shift,
-                uint32_t mask, uint32_t *__restrict__ status) {
+                uint32_t mask, uint32_t *__restrict__ status, uint32_t *__restrict__ skip_flag) {
   constexpr int PART = kThreads * KPT;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   K *s_keys = reinterpret_cast<K *>(s_dyn);
@@ -154,6 +154,11 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
   const uint32_t part = s_part;
   const uint32_t base = part * PART;
   if (base >= n) return;
+  if (trivial && skip_flag) {
+    // the caller reads the result from this pass's input instead (the pass is the identity)
+    if (t == 0) *skip_flag = 1u;
+    return;
+  }
   if (trivial) {
     const uint32_t end = min(n, base + (uint32_t)PART);
     for (uint32_t i = base + t; i < end; i += kThreads) {
@@ -340,7 +345,7 @@ cudaError_t launch_onesweep_kpt(K *keys, uint32_t *vals, K *keys_alt, uint32_t *
                                 bool implicit_vals, const uint32_t *d_count, size_t capacity,
                                 const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
                                 uint32_t *lookback, uint32_t *status, bool *result_in_alt,
-                                cudaStream_t s, bool drop_final_keys) {
+                                cudaStream_t s, bool drop_final_keys, uint32_t *final_skip) {
   *result_in_alt = false;
   if (capacity == 0) return cudaSuccess;
   cudaError_t e = set_smem_attr<K, KPT>();
@@ -356,7 +361,8 @@ cudaError_t launch_onesweep_kpt(K *keys, uint32_t *vals, K *keys_alt, uint32_t *
     K *kdst = (drop_final_keys && p == plan.passes - 1) ? nullptr : kout;
     onesweep_kernel<K, KPT><<<(unsigned)parts, kThreads, dyn, s>>>(
         kin, vsrc, kdst, vout, d_count, hist + p * kRadix, counters + p,
-        lookback + (size_t)kRadix * parts * p, plan.shift[p], plan.mask, status);
+        lookback + (size_t)kRadix * parts * p, plan.shift[p], plan.mask, status,
+        p == plan.passes - 1 ? final_skip : nullptr);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     K *tk = kin; kin = kout; kout = tk;
@@ -371,14 +377,15 @@ cudaError_t launch_onesweep(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals
                             bool implicit_vals, const uint32_t *d_count, size_t capacity,
                             const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
                             uint32_t *lookback, uint32_t *status, bool *result_in_alt,
-                            cudaStream_t s, bool small_parts, bool drop_final_keys) {
+                            cudaStream_t s, bool small_parts, bool drop_final_keys,
+                            uint32_t *final_skip) {
   if (sizeof(K) == 4 && small_parts)
     return launch_onesweep_kpt<K, 8>(keys, vals, keys_alt, vals_alt, implicit_vals, d_count, capacity,
                                      plan, hist, counters, lookback, status, result_in_alt, s,
-                                     drop_final_keys);
+                                     drop_final_keys, final_skip);
   return launch_onesweep_kpt<K, Part<K>::kKPT>(keys, vals, keys_alt, vals_alt, implicit_vals, d_count,
                                                capacity, plan, hist, counters, lookback, status,
-                                               result_in_alt, s, drop_final_keys);
+                                               result_in_alt, s, drop_final_keys, final_skip);
 }
 
 template cudaError_t launch_histogram<uint32_t>(const uint32_t *, const uint32_t *, size_t,
@@ -386,7 +393,8 @@ template cudaError_t launch_histogram<uint32_t>(const uint32_t *, const uint32_t
 template cudaError_t launch_onesweep<uint32_t>(uint32_t *, uint32_t *, uint32_t *, uint32_t *,
                                                bool, const uint32_t *, size_t, const SortPlan &,
                                                const uint32_t *, uint32_t *, uint32_t *,
-                                               uint32_t *, bool *, cudaStream_t, bool, bool);
+                                               uint32_t *, bool *, cudaStream_t, bool, bool,
+                                               uint32_t *);
 
 // ---- the 64-bit pair sort of the public API (8-bit digits) ----
 constexpr size_t kHistBytes = sizeof(uint32_t) * kMaxSortPasses * kRadix;
