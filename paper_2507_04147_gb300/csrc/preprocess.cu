@@ -40,10 +40,10 @@ __device__ __forceinline__ float exp_cw(float x) {
   return fm(p, scale);
 }
 
+// The SH basis of degree sqrt(K) - 1 at the unit direction (dx, dy, dz).
 template <int K>
-__device__ __forceinline__ void sh_colour(const ShConsts &c, const float *coef, float dx,
-                                          float dy, float dz, float rgb[3]) {
-  float b[16];
+__device__ __forceinline__ void sh_basis(const ShConsts &c, float dx, float dy, float dz,
+                                         float b[16]) {
   b[0] = c.c0;
   if constexpr (K > 1) {
     b[1] = fm(-c.c1, dy);
@@ -67,18 +67,53 @@ __device__ __forceinline__ void sh_colour(const ShConsts &c, const float *coef, 
       b[15] = fm(-c.c3a, fm(dx, fs(xx, fm(3.0f, yy))));
     }
   }
-#pragma unroll
-  for (int ch = 0; ch < 3; ++ch) {
-    float acc = 0.0f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) acc = fa(acc, fm(b[k], coef[3 * k + ch]));
-    rgb[ch] = fmaxf(0.0f, fa(acc, 0.5f));
-  }
 }
 
-// Shared-memory stride of one Gaussian's SH row: 3K floats rounded up to an odd count.
+// SH rows whose 3K floats are whole 16-byte chunks (degrees 1 and 3) are staged by cp.async
+// without padding; with an even number of chunks per row (degree 3: 12) chunk m of thread t's
+// row sits at m ^ ((t >> 1) & 3), so the eight threads of a quarter warp reading the same
+// chunk index hit eight different 16-byte bank groups.
 template <int K>
-constexpr int sh_stride() { return (3 * K) % 2 == 0 ? 3 * K + 1 : 3 * K; }
+constexpr bool sh_chunked() { return (3 * K) % 4 == 0; }
+
+template <int K>
+__device__ __forceinline__ int sh_swz(int m, int t) {
+  return ((3 * K / 4) % 2 == 0) ? (m ^ ((t >> 1) & 3)) : m;
+}
+
+// colour = max(0, sum_k b_k coef_k + 1/2) per channel, the sum over k in ascending order.
+// row: the thread's SH row in shared memory (chunked layout when sh_chunked<K>(), else the
+// padded scalar layout).
+template <int K>
+__device__ __forceinline__ void sh_colour(const ShConsts &c, const float *row, int t, float dx,
+                                          float dy, float dz, float rgb[3]) {
+  float b[16];
+  sh_basis<K>(c, dx, dy, dz, b);
+  float acc[3] = {0.0f, 0.0f, 0.0f};
+  if constexpr (sh_chunked<K>()) {
+    const float4 *row4 = reinterpret_cast<const float4 *>(row);
+#pragma unroll
+    for (int m = 0; m < 3 * K / 4; ++m) {
+      const float4 v = row4[sh_swz<K>(m, t)];
+      const float e[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int f = 4 * m + j;
+        acc[f % 3] = fa(acc[f % 3], fm(b[f / 3], e[j]));
+      }
+    }
+  } else {
+#pragma unroll
+    for (int f = 0; f < 3 * K; ++f) acc[f % 3] = fa(acc[f % 3], fm(b[f / 3], row[f]));
+  }
+#pragma unroll
+  for (int ch = 0; ch < 3; ++ch) rgb[ch] = fmaxf(0.0f, fa(acc[ch], 0.5f));
+}
+
+// Shared-memory stride of one Gaussian's SH row: 3K floats (chunked rows), else rounded up to
+// an odd count so the per-thread scalar reads are free of bank conflicts.
+template <int K>
+constexpr int sh_stride() { return sh_chunked<K>() ? 3 * K : ((3 * K) % 2 == 0 ? 3 * K + 1 : 3 * K); }
 
 // Cooperative coalesced copy of `count` floats starting at src into shared memory,
 // laid out as rows of `row` floats at stride `stride`.  src is 16-byte aligned.
@@ -111,6 +146,29 @@ __device__ __forceinline__ void stage(float *dst, const float *__restrict__ src,
     dst[(f / row) * stride + (f % row)] = __ldg(src + f);
 }
 
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");
+}
+
+// Asynchronous copy of `count` floats from src to dst (both 16-byte aligned); a tail of
+// fewer than four floats is copied with plain loads.
+__device__ __forceinline__ void stage_async(float *dst, const float *__restrict__ src, int count) {
+  const int n4 = count >> 2;
+  for (int i = threadIdx.x; i < n4; i += blockDim.x) cp_async16(dst + 4 * i, src + 4 * i);
+  for (int f = 4 * n4 + threadIdx.x; f < count; f += blockDim.x) dst[f] = __ldg(src + f);
+}
+
+// Asynchronous copy of `cnt` chunked SH rows into the swizzled shared-memory layout.
+template <int K>
+__device__ __forceinline__ void stage_sh_async(float *dst, const float *__restrict__ src, int cnt) {
+  constexpr int kChunks = 3 * K / 4;
+  for (int g = threadIdx.x; g < cnt * kChunks; g += blockDim.x) {
+    const int t = g / kChunks, m = g - t * kChunks;
+    cp_async16(dst + 4 * (t * kChunks + sh_swz<K>(m, t)), src + 4 * g);
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(kPreThreads, 6)
 preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restrict__ means,
@@ -127,17 +185,22 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
   if (threadIdx.x < sizeof(PreParams) / 4)
     reinterpret_cast<uint32_t *>(&s_p)[threadIdx.x] = reinterpret_cast<const uint32_t *>(pp)[threadIdx.x];
   const PreParams &p = s_p;
-  __shared__ float s_mean[kPreThreads * 3];
-  __shared__ float s_scale[kPreThreads * 3];
+  __shared__ __align__(16) float s_mean[kPreThreads * 3];
+  __shared__ __align__(16) float s_scale[kPreThreads * 3];
   __shared__ float4 s_quat[kPreThreads];
-  __shared__ float s_sh[kPreThreads * SS];
+  __shared__ __align__(16) float s_sh[kPreThreads * SS];
 
+  // every copy of the block is in flight at once: one memory round trip per block
   const int i0 = blockIdx.x * kPreThreads;
   const int cnt = min(kPreThreads, n - i0);
-  stage(s_mean, means + 3 * (size_t)i0, 3 * cnt, 3, 3);
-  stage(s_scale, log_scales + 3 * (size_t)i0, 3 * cnt, 3, 3);
-  stage(reinterpret_cast<float *>(s_quat), quats + 4 * (size_t)i0, 4 * cnt, 4, 4);
-  stage(s_sh, sh + (size_t)3 * K * i0, 3 * K * cnt, 3 * K, SS);
+  stage_async(s_mean, means + 3 * (size_t)i0, 3 * cnt);
+  stage_async(s_scale, log_scales + 3 * (size_t)i0, 3 * cnt);
+  stage_async(reinterpret_cast<float *>(s_quat), quats + 4 * (size_t)i0, 4 * cnt);
+  if constexpr (sh_chunked<K>())
+    stage_sh_async<K>(s_sh, sh + (size_t)3 * K * i0, cnt);
+  else
+    stage(s_sh, sh + (size_t)3 * K * i0, 3 * K * cnt, 3 * K, SS);
+  asm volatile("cp.async.wait_all;" ::: "memory");
   __syncthreads();
 
   const int t = threadIdx.x;
@@ -250,7 +313,7 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
         dy = fdv(dy, dn);
         dz = fdv(dz, dn);
         float rgb[3];
-        sh_colour<K>(p.shc, coef, dx, dy, dz, rgb);
+        sh_colour<K>(p.shc, coef, t, dx, dy, dz, rgb);
         const float inv = fdv(1.0f, det);
         o0 = make_float4(u, v, fm(cc, inv), fm(-b, inv));
         o1 = make_float4(fm(a, inv), opacity, rgb[0], rgb[1]);
