@@ -139,6 +139,29 @@ def test_degenerate_scenes():
 
 
 @pytest.mark.parametrize("binning", [a3fr.BINNING_DIRECT, a3fr.BINNING_SORTED])
+def test_depth_range_wider_than_the_rebase(binning):
+    # depths 0.5 .. 40: the visible depth keys span more than 2^24, so they are not rebased
+    # and the top 8-bit digit differs between near and far Gaussians; the last depth pass
+    # then really permutes (the other parity scenes, all at depths 2 .. 6, take the
+    # identity last pass that writes nothing)
+    s = synth.uniform_scene(3000, 1, seed=21)
+    z = np.float32(0.5) * np.exp(np.linspace(0.0, np.log(80.0), s.n)).astype(np.float32)
+    np.random.Generator(np.random.PCG64(22)).shuffle(z)
+    s.means[:, 2] = z
+    s.means[:, 0] *= 0.8 * z
+    s.means[:, 1] *= 0.5 * z
+    key = z.view(np.uint32)
+    assert int(key.max()) - int(key.min()) >= 1 << 24 and (key.max() >> 24) != (key.min() >> 24)
+    cam = synth.pinhole_camera(96, 64)
+    fv, fa = fovea_params()
+    for full in (True, False):
+        r = gh.run(s, [cam], gaze=None if full else [(40.0, 30.0)], fovea=None if full else fa,
+                   full=full, binning=binning)
+        assert r["stats"]["status"] == 0
+        check_eye(r, 0, s, cam, full=full, gaze=(40.0, 30.0), fv=fv)
+
+
+@pytest.mark.parametrize("binning", [a3fr.BINNING_DIRECT, a3fr.BINNING_SORTED])
 def test_capacity_overflow_sets_status_without_fault(binning):
     w = synth.small_single_view()
     cam = w.cameras(0)[0]
