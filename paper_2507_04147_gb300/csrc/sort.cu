@@ -83,19 +83,41 @@ histogram_kernel(K *__restrict__ keys, const uint32_t *__restrict__ d_count, Sor
     for (int i = t; i < kWarps * 4 * kRadix; i += kThreads) (&s_hist[0][0][0])[i] = 0;
     __syncthreads();
     const uint32_t per_block = kThreads * kHistKeysPerThread;
+    // a thread's 8 consecutive 32-bit keys as two 16-byte loads (and stores, when rebased)
+    constexpr bool kVec = sizeof(K) == 4 && kHistKeysPerThread == 8;
+    const bool vec_ok = kVec && (reinterpret_cast<uintptr_t>(keys) & 15u) == 0u;
     for (uint32_t base = blockIdx.x * per_block; base < n; base += gridDim.x * per_block) {
       const uint32_t i0 = base + t * kHistKeysPerThread;
       const uint32_t i1 = min(n, i0 + kHistKeysPerThread);
+      const bool vec = vec_ok && i1 == i0 + kHistKeysPerThread;
+      K kv[kHistKeysPerThread];
+      if constexpr (kVec) {
+        if (vec) {
+          const uint4 a = reinterpret_cast<const uint4 *>(keys + i0)[0];
+          const uint4 b = reinterpret_cast<const uint4 *>(keys + i0)[1];
+          kv[0] = a.x; kv[1] = a.y; kv[2] = a.z; kv[3] = a.w;
+          kv[4] = b.x; kv[5] = b.y; kv[6] = b.z; kv[7] = b.w;
+        }
+      }
+      bool rebased = false;
       uint32_t cur[4] = {0xffffffffu, 0xffffffffu, 0xffffffffu, 0xffffffffu};
       uint32_t run[4] = {0u, 0u, 0u, 0u};
-      for (uint32_t i = i0; i < i1; ++i) {
-        K k = keys[i];
+#pragma unroll
+      for (int j = 0; j < kHistKeysPerThread; ++j) {
+        const uint32_t i = i0 + (uint32_t)j;
+        if (i >= i1) break;
+        K k = vec ? kv[j] : keys[i];
         if (kRebase && p0 == 0) {
           // visible keys are <= max; a range under 2^24 leaves the top digit zero
           const uint32_t kmin = ~range[0], kmax = range[2];
           if (kmax >= kmin && kmax - kmin < (1u << 24)) {
             k = (K)((uint32_t)k <= kmax ? (uint32_t)k - kmin : 0xffffffu);
-            keys[i] = k;
+            if (vec) {
+              kv[j] = k;
+              rebased = true;
+            } else {
+              keys[i] = k;
+            }
           }
         }
 #pragma unroll
@@ -114,6 +136,12 @@ histogram_kernel(K *__restrict__ keys, const uint32_t *__restrict__ d_count, Sor
 #pragma unroll
       for (int q = 0; q < 4; ++q)
         if (q < np && run[q]) atomicAdd(&s_hist[warp][q][cur[q]], run[q]);
+      if constexpr (kVec) {
+        if (rebased) {
+          reinterpret_cast<uint4 *>(keys + i0)[0] = make_uint4(kv[0], kv[1], kv[2], kv[3]);
+          reinterpret_cast<uint4 *>(keys + i0)[1] = make_uint4(kv[4], kv[5], kv[6], kv[7]);
+        }
+      }
     }
     __syncthreads();
     for (int i = t; i < np * kRadix; i += kThreads) {
