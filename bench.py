@@ -405,6 +405,10 @@ def run_ours(args):
     sframes = frames[: min(len(frames), 240)]
     ms_fov_direct, st_fov, stats_fov_direct = timed_loop(False, sframes, graphs=False, stages=True)
     ms_full_direct, st_full, _ = timed_loop(True, sframes, graphs=False, stages=True)
+    # the same frames replayed as graphs with events around the two graphs of each frame (kept
+    # out of the headline loop, which they would slow by a few microseconds): the composite
+    # graph's duration is the dominant kernel's launch time for the roofline
+    _, st_fov_graph, stats_fov_graph = timed_loop(False, sframes, stages=True)
 
     total_fov = reduce_max(float(ms_fov.sum()), world, device)
     total_full = reduce_max(float(ms_full.sum()), world, device)
@@ -465,7 +469,15 @@ def run_ours(args):
 
     stage_mean_fov = {k: float(st_fov[:, i].mean()) for i, k in enumerate(STAGES)}
     stage_mean_full = {k: float(st_full[:, i].mean()) for i, k in enumerate(STAGES)}
-    roof = roofline(w, stats_fov_direct, stage_mean_fov, len(sframes), eyes, scene.tile)
+    # the roofline takes the composite launch time from graph replay: the mean of the
+    # composite graph's events; the direct-launch stages above give the per-stage breakdown
+    # (and pick the dominant stage)
+    comp_graph_ms = float(st_fov_graph[:, STAGES.index("composite")].mean())
+    roof = roofline(w, stats_fov_graph, dict(stage_mean_fov, composite=comp_graph_ms),
+                    len(sframes), eyes, scene.tile)
+    roof["launch_ms_direct"] = stage_mean_fov["composite"]
+    roof["launch_timing"] = ("CUDA events on the render stream around the composite graph of "
+                             "each frame, the headline's frames replayed as graphs (mean)")
 
     line = {"metric": METRIC, "value": fps_fov, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,

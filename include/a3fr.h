@@ -347,7 +347,10 @@ int a3fr_set_keep_aux(a3fr_scene *scene, int keep);
 #define A3FR_N_STAGES 5
 
 /* Record CUDA events around every stage of the next renders on their stream, keeping the
- * last `ring` renders (0 turns timing off and frees the events). */
+ * last `ring` renders (0 turns timing off and frees the events).  A render in graph mode
+ * (a3fr_set_graph_mode) replays two graphs and is timed around them: the precompute graph
+ * (and, foveated, the wait for the gaze) as A3FR_STAGE_PREPROCESS, the composite graph as
+ * A3FR_STAGE_COMPOSITE; its DEPTH_SORT, BIN and EMIT stages read zero. */
 int a3fr_set_stage_timing(a3fr_scene *scene, int ring);
 
 /* Synchronise and write the stage durations (ms) of the last min(max_renders, available)

@@ -136,6 +136,7 @@ struct a3fr_scene {
 
   // CUDA graphs of the precompute and of the composite (foveated / full)
   bool graph_mode = false;
+  bool capturing = false;    // a graph capture is in progress (stage marks are not recorded)
   uint64_t alloc_gen = 1;                    // bumped whenever a workspace buffer moves
   cudaStream_t capture_stream = nullptr;
   ForkStreams fork{};                        // concurrent launches of the 32-pixel composite
@@ -380,9 +381,11 @@ void free_timing(a3fr_scene *s) {
   s->timed_renders = 0;
 }
 
-// Records the boundary event k (0..A3FR_N_STAGES) of the current timed render.
+// Records the boundary event k (0..A3FR_N_STAGES) of the current timed render.  Nothing is
+// recorded into a graph being captured: a graph-mode render records its events around the
+// graph launches instead (render()).
 cudaError_t mark(a3fr_scene *s, int k, cudaStream_t stream) {
-  if (!s->timing_ring) return cudaSuccess;
+  if (!s->timing_ring || s->capturing) return cudaSuccess;
   const int slot = (int)(s->timed_renders % (uint64_t)s->timing_ring);
   return cudaEventRecord(s->timing_events[slot * (A3FR_N_STAGES + 1) + k], stream);
 }
@@ -629,7 +632,9 @@ int capture(a3fr_scene *s, cudaGraphExec_t *exec, uint64_t *kernels, F fn) {
   }
   A3FR_CHECK(cudaStreamBeginCapture(s->capture_stream, cudaStreamCaptureModeRelaxed));
   *kernels = 0;
+  s->capturing = true;
   const int rc = fn(s->capture_stream, kernels);
+  s->capturing = false;
   cudaGraph_t g = nullptr;
   const cudaError_t e = cudaStreamEndCapture(s->capture_stream, &g);
   if (rc != A3FR_OK) {
@@ -674,8 +679,11 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
   if (rc != A3FR_OK) return rc;
 
   uint64_t launches = 0;
-  const bool graphs = s->graph_mode && s->timing_ring == 0 && s->capacity > 0 &&
-                      mode != Mode::kFirstRound && s->desc.n > 0;
+  // with stage timing on, a graph-mode render times its two graphs: the precompute graph as
+  // the preprocess stage (the depth sort, bin and emit stages then read zero) and the
+  // composite graph as the composite stage
+  const bool graphs = s->graph_mode && s->capacity > 0 && mode != Mode::kFirstRound &&
+                      s->desc.n > 0;
   if (graphs) {
     const uint64_t key = s->alloc_gen * 4 + (s->keep_aux ? 2 : 0) + (uint64_t)eyes;
     if (!s->g_pre || s->g_pre_key != key) {
@@ -685,6 +693,7 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
       if (rc != A3FR_OK) return rc;
       s->g_pre_key = key;
     }
+    A3FR_CHECK(mark(s, A3FR_STAGE_PREPROCESS, stream));
     A3FR_CHECK(cudaGraphLaunch(s->g_pre, stream));
     launches += s->g_pre_launches;
   } else {
@@ -719,7 +728,10 @@ int render(a3fr_scene *s, const a3fr_fovea *fv, float *out, cudaStream_t stream,
       if (rc != A3FR_OK) return rc;
       *gk = key;
     }
+    for (int k = A3FR_STAGE_DEPTH_SORT; k <= A3FR_STAGE_COMPOSITE; ++k)
+      A3FR_CHECK(mark(s, k, stream));
     A3FR_CHECK(cudaGraphLaunch(*g, stream));
+    A3FR_CHECK(mark(s, A3FR_N_STAGES, stream));
     launches += (mode == Mode::kFull ? 1 : 2) + (fill ? 1 : 0);
   } else {
     rc = enqueue_comp(s, hp.comp, uniform, cur, fill, stream, &launches);

@@ -243,6 +243,39 @@ def test_graph_mode_matches_direct_launches_bitwise(tile):
     assert st["status"] == 0
 
 
+def test_stage_timing_in_graph_mode():
+    """With stage timing on, a graph-mode render is timed around its two graphs (precompute,
+    composite) and renders the same images as untimed graph renders."""
+    import torch
+    w = synth.stereo_500k(frames=240)
+    scene_np = w.scene.subset(np.arange(40000))
+    traj = synth.gaze_trajectory(240)
+    imgs = {}
+    for timed in (False, True):
+        s = a3fr.Scene.from_numpy(scene_np, tile=32)
+        s.graph_mode(True)
+        out = []
+        for f in (0, 3, 0, 9, 20):
+            for e, c in enumerate(w.cameras(f)):
+                s.set_camera(e, c)
+            s.set_gaze(w.gaze(f, traj))
+            if timed and len(out) == 2:
+                s.stage_timing(8)   # after the graphs were captured untimed
+            out.append(s.render_foveated(a3fr.Fovea()).clone())
+        torch.cuda.synchronize()
+        imgs[timed] = out
+        if timed:
+            st = s.stage_times(8)
+            assert st.shape == (3, 5)
+            assert np.all(st[:, 0] > 0.0) and np.all(st[:, 4] > 0.0)
+            assert np.all(st[:, 1:4] < 0.05 * st[:, 4])
+            s.stage_timing(0)
+        assert s.stats()["status"] == 0
+        s.close()
+    for a, b in zip(imgs[False], imgs[True]):
+        assert torch.equal(a, b)
+
+
 @pytest.mark.parametrize("batch_mult", [1, 2])
 def test_tile32_foveated_and_full(batch_mult):
     """32-pixel tiles (one CTA per tile rendering all its labels) against the oracle run with
