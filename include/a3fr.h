@@ -217,8 +217,9 @@ int a3fr_run_frame(a3fr_scene *scene, const a3fr_fovea *fovea, const a3fr_rounds
  * sits between them, so the precompute still overlaps the tracker.  Per-render parameters
  * (cameras, layer radii, gaze slot, output pointer) live in device memory and one copy per
  * render updates them.  Graphs are captured at the first render that can use them and again
- * whenever a workspace buffer moves; renders with stage timing on, the first render of an
- * automatic-capacity scene and the rounds API launch directly. */
+ * whenever a workspace buffer moves; the first render of an automatic-capacity scene and
+ * the rounds API launch directly (with stage timing on, a graph-mode render is timed around
+ * its two graphs: see a3fr_set_stage_timing). */
 int a3fr_set_graph_mode(a3fr_scene *scene, int on);
 
 /* ------------------------------------------------------------------ tiling and tuning
