@@ -17,6 +17,8 @@ Parity status of each part (pins are the ``-m "not gpu"`` tests in ``tests/``):
     Python sorted())
   * compositing                                      -- pinned (single-Gaussian closed
     form, weight-sum and white-colour invariants, input-order invariance, fp64 brute force)
+  * threshold margin and the flipped-decision colour -- pinned (a Gaussian at alpha = 1/255
+    exactly, a stack whose transmittance lands on 1e-4, closed forms of both margins)
   * foveation level map, live mask, fill             -- pinned (brute-force geometry,
     closed-form disc count)
   * count-based tile levels                          -- pinned (hand-counted cases, ties,
@@ -81,7 +83,7 @@ def lib():
         L.or_tile_ranges.argtypes = [i64, vp, i32, vp]
         L.or_layer_radii2.argtypes = [vp, vp, vp]
         L.or_level_map.argtypes = [vp, i32, vp, vp, vp]
-        L.or_render.argtypes = [i32, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.or_render.argtypes = [i32, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
         L.or_render_eye.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, i32,
                                     vp, vp, vp, vp, vp, vp]
         L.or_num_threads.restype = i32
@@ -203,6 +205,10 @@ class Image:
         self.margin = np.zeros(count, dtype=np.float32)
         self.rendered = np.zeros(count, dtype=np.uint8)
         self.depth = np.zeros(count, dtype=np.float32)   # expected depth sum(alpha T z)
+        # the colour with the pixel's nearest threshold decision (alpha >= 1/255 skip or
+        # T >= 1e-4 stop) taken the other way, for pixels whose margin is below 1e-3
+        # (equal to rgb elsewhere): what a renderer whose exp differs by an ulp may produce
+        self.rgb_alt = np.zeros((count, 3), dtype=np.float32)
 
 
 def render(rec, rect, cam, tile: int, level=None, pixels=None) -> Image:
@@ -219,7 +225,7 @@ def render(rec, rect, cam, tile: int, level=None, pixels=None) -> Image:
     lib().or_render(n, _p(np.ascontiguousarray(rec)), _p(np.ascontiguousarray(rect)),
                     ctypes.byref(c), tile, _p(lv), _p(pix), count if pix is not None else 0,
                     _p(img.rgb), _p(img.t_final), _p(img.n_contrib), _p(img.n_eval),
-                    _p(img.margin), _p(img.rendered), _p(img.depth))
+                    _p(img.margin), _p(img.rendered), _p(img.depth), _p(img.rgb_alt))
     return img
 
 
@@ -238,6 +244,7 @@ def render_eye(scene, cam, tile: int, fv: Fovea | None, gaze=None, pixels=None) 
                         ctypes.byref(fv) if fv is not None else None, _p(g), _p(pix),
                         count if pix is not None else 0, _p(img.rgb), _p(img.t_final),
                         _p(img.n_contrib), _p(img.n_eval), _p(img.margin), _p(img.rendered))
+    img.rgb_alt[:] = img.rgb
     return img
 
 

@@ -355,15 +355,33 @@ static int or_cmp_order(const void *pa, const void *pb) {
   return a->idx < b->idx ? -1 : (a->idx > b->idx ? 1 : 0);
 }
 
-/* Front-to-back volume rendering of one pixel over the global depth-sorted list. */
-static void or_shade(int x, int y, int tile, const float *rec, const int32_t *rect,
-                     const or_order *list, int n_vis, float out[3], float *t_final,
-                     int32_t *n_contrib, int32_t *n_eval, float *margin, float *depth) {
+/* Front-to-back volume rendering of one pixel over the global depth-sorted list.
+ *
+ * Two decisions per Gaussian can be flipped by an ulp-level difference in the falloff exp:
+ * the skip of alpha < 1/255 and the stop before a Gaussian that would bring T below 1e-4.
+ * The walk records, as the pixel's margin, the smallest relative distance of any such
+ * decision to its threshold (|255 raw - 1| for the skip, |10^4 T' - 1| for the stop) and
+ * where it was taken (position in the list and kind).  flip_j >= 0 re-runs the walk with
+ * the decision of kind flip_kind at list position flip_j taken the other way and every
+ * other decision as usual: the image a renderer would produce if only that decision
+ * flipped. */
+enum { OR_FLIP_NONE = -1, OR_FLIP_SKIP = 0, OR_FLIP_STOP = 1 };
+
+typedef struct {
+  float rgb[3], t_final, margin, depth;
+  int32_t n_contrib, n_eval;
+  int32_t min_j, min_kind;   /* where the smallest margin was taken */
+} or_walk_result;
+
+static void or_walk(int x, int y, int tile, const float *rec, const int32_t *rect,
+                    const or_order *list, int n_vis, int flip_j, int flip_kind,
+                    or_walk_result *res) {
   const int ptx = x / tile, pty = y / tile;
   float T = 1.0f, C[3] = {0.0f, 0.0f, 0.0f};
   float Z = 0.0f;   /* expected depth: the blend weights applied to camera-space depth */
   int32_t contrib = 0, evals = 0;
   float m = INFINITY;
+  int32_t min_j = -1, min_kind = OR_FLIP_NONE;
   for (int j = 0; j < n_vis; ++j) {
     const uint32_t g = list[j].idx;
     const int32_t *rc = rect + (size_t)g * 4;
@@ -375,24 +393,56 @@ static void or_shade(int x, int y, int tile, const float *rec, const int32_t *re
     if (power > 0.0f) continue;
     const float raw = o[5] * (float)exp((double)power);
     const float ma = fabsf(raw - (1.0f / 255.0f)) * 255.0f;
-    if (ma < m) m = ma;
+    if (ma < m) { m = ma; min_j = j; min_kind = OR_FLIP_SKIP; }
     const float alpha = fminf(0.99f, raw);
-    if (alpha < 1.0f / 255.0f) continue;
+    int skip = alpha < 1.0f / 255.0f;
+    if (j == flip_j && flip_kind == OR_FLIP_SKIP) skip = !skip;
+    if (skip) continue;
     const float testT = T * (1.0f - alpha);
     const float mt = fabsf(testT - 0.0001f) * 10000.0f;
-    if (mt < m) m = mt;
-    if (testT < 0.0001f) break;
+    if (mt < m) { m = mt; min_j = j; min_kind = OR_FLIP_STOP; }
+    int stop = testT < 0.0001f;
+    if (j == flip_j && flip_kind == OR_FLIP_STOP) stop = !stop;
+    if (stop) break;
     for (int ch = 0; ch < 3; ++ch) C[ch] += o[6 + ch] * alpha * T;
     Z += o[9] * alpha * T;
     T = testT;
     contrib = evals;
   }
-  out[0] = C[0]; out[1] = C[1]; out[2] = C[2];   /* + T * background, background = 0 */
-  *t_final = T;
-  *n_contrib = contrib;
-  *n_eval = evals;
-  *margin = m;
-  if (depth) *depth = Z;
+  res->rgb[0] = C[0]; res->rgb[1] = C[1]; res->rgb[2] = C[2];   /* + T * background, 0 */
+  res->t_final = T;
+  res->n_contrib = contrib;
+  res->n_eval = evals;
+  res->margin = m;
+  res->depth = Z;
+  res->min_j = min_j;
+  res->min_kind = min_kind;
+}
+
+/* Pixels whose margin is below this also get the image with their nearest decision
+ * flipped (rgb_alt); the others get rgb_alt = rgb. */
+static const float OR_ALT_BELOW = 1e-3f;
+
+static void or_shade(int x, int y, int tile, const float *rec, const int32_t *rect,
+                     const or_order *list, int n_vis, float out[3], float *t_final,
+                     int32_t *n_contrib, int32_t *n_eval, float *margin, float *depth,
+                     float *out_alt) {
+  or_walk_result r;
+  or_walk(x, y, tile, rec, rect, list, n_vis, -1, OR_FLIP_NONE, &r);
+  out[0] = r.rgb[0]; out[1] = r.rgb[1]; out[2] = r.rgb[2];
+  *t_final = r.t_final;
+  *n_contrib = r.n_contrib;
+  *n_eval = r.n_eval;
+  *margin = r.margin;
+  if (depth) *depth = r.depth;
+  if (out_alt) {
+    out_alt[0] = r.rgb[0]; out_alt[1] = r.rgb[1]; out_alt[2] = r.rgb[2];
+    if (r.min_j >= 0 && r.margin < OR_ALT_BELOW) {
+      or_walk_result a;
+      or_walk(x, y, tile, rec, rect, list, n_vis, r.min_j, r.min_kind, &a);
+      out_alt[0] = a.rgb[0]; out_alt[1] = a.rgb[1]; out_alt[2] = a.rgb[2];
+    }
+  }
 }
 
 static or_order *or_global_list(int n, const float *rec, int *n_vis) {
@@ -416,11 +466,12 @@ static or_order *or_global_list(int n, const float *rec, int *n_vis) {
  * rgb[3], T_final, n_contrib, n_eval and the threshold margin of the pixel that was
  * actually shaded (the top-left one for inherited pixels); rendered[] is 1 when the
  * pixel itself was shaded; depth (optional) is the expected depth sum(alpha T z) of the
- * blended Gaussians, the usual 3DGS depth render. */
+ * blended Gaussians, the usual 3DGS depth render; rgb_alt (optional) is the colour with
+ * the pixel's nearest threshold decision flipped (see or_shade). */
 void or_render(int n, const float *rec, const int32_t *rect, const or_camera *cam, int tile,
                const uint8_t *level, const int32_t *pix, int n_pix, float *rgb,
                float *t_final, int32_t *n_contrib, int32_t *n_eval, float *margin,
-               uint8_t *rendered, float *depth) {
+               uint8_t *rendered, float *depth, float *rgb_alt) {
   int n_vis = 0;
   or_order *list = or_global_list(n, rec, &n_vis);
   const int W = cam->width, H = cam->height;
@@ -439,7 +490,7 @@ void or_render(int n, const float *rec, const int32_t *rect, const or_camera *ca
       if (!live) { sx = x & ~1; sy = y & ~1; }
     }
     or_shade(sx, sy, tile, rec, rect, list, n_vis, rgb + 3 * p, t_final + p, n_contrib + p,
-             n_eval + p, margin + p, depth ? depth + p : NULL);
+             n_eval + p, margin + p, depth ? depth + p : NULL, rgb_alt ? rgb_alt + 3 * p : NULL);
     if (rendered) rendered[p] = (uint8_t)live;
   }
   free(list);
@@ -463,7 +514,7 @@ void or_render_eye(int n, int degree, const float *means, const float *log_scale
     or_level_map(cam, tile, fv, gaze, level);
   }
   or_render(n, rec, rect, cam, tile, level, pix, n_pix, rgb, t_final, n_contrib, n_eval,
-            margin, rendered, NULL);
+            margin, rendered, NULL, NULL);
   free(level);
   free(touched);
   free(rect);

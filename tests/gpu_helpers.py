@@ -7,13 +7,22 @@ import numpy as np
 import oracle
 import paper_2507_04147_gb300 as a3fr
 
-# Pixel tolerance and threshold-margin exemption.  A pixel whose oracle margin to the
-# alpha >= 1/255 or T >= 1e-4 decision is below DELTA can legitimately flip between an
-# fp32 libm exp and the GPU's ex2.approx (relative error ~2^-22 per evaluation,
-# accumulated over a few hundred blends), so it is counted instead of bounded.
+# Pixel tolerance and the threshold-flip rule.  The GPU evaluates the falloff exp with the
+# MUFU ex2 unit and the oracle with the correctly rounded fp32 value of the fp64 exp; the two
+# differ by ~1e-6 relative, which can flip a pixel's alpha >= 1/255 skip or its T >= 1e-4
+# stop when the oracle's margin to that decision is tiny.  Every pixel must match the oracle
+# within TOL, or -- only where the oracle's margin is below DELTA -- match the oracle's
+# colour with that nearest decision taken the other way (Image.rgb_alt) within TOL.  So
+# no pixel goes unchecked.  The exempt set (margin < DELTA) is decided by the oracle alone;
+# on the parity scenes it measures 4-7e-5 of the pixels, and it must stay below
+# MAX_EXEMPT_FRACTION of the pixels compared plus EXEMPT_SLACK pixels (a sample of a few
+# thousand pixels expects well under one exempt pixel, so the slack absorbs the Poisson
+# spread of small samples): a sanity bound on the scene and on DELTA (the margin pins in
+# test_oracle_margin.py fix how the margin is computed).
 TOL = 2e-4
 DELTA = 1e-5
-MAX_EXEMPT_FRACTION = 2e-3
+MAX_EXEMPT_FRACTION = 2e-4
+EXEMPT_SLACK = 3
 
 
 def run(scene_np, cams, gaze=None, fovea=None, full=False, capacity=0, keep_aux=True,
@@ -59,12 +68,20 @@ def strip_eye(keys, eye, n_tiles):
 
 
 def compare_pixels(gpu_rgb, ref, tol=TOL, delta=DELTA):
-    """gpu_rgb [P,3] vs oracle Image ref over the same P pixels."""
-    err = np.abs(gpu_rgb.reshape(-1, 3).astype(np.float64) - ref.rgb.astype(np.float64)).max(axis=1)
+    """gpu_rgb [P,3] vs oracle Image ref over the same P pixels: each pixel equals the
+    oracle within tol, or, where the oracle's threshold margin is below delta, the oracle's
+    flipped-decision colour within tol."""
+    g = gpu_rgb.reshape(-1, 3).astype(np.float64)
+    err = np.abs(g - ref.rgb.astype(np.float64)).max(axis=1)
+    err_alt = np.abs(g - ref.rgb_alt.astype(np.float64)).max(axis=1)
     exempt = ref.margin < delta
-    bad = (err > tol) & ~exempt
-    info = dict(max_err=float(err[~exempt].max()) if (~exempt).any() else 0.0,
-                exempt=int(exempt.sum()), pixels=int(err.size), bad=int(bad.sum()))
+    ok_main = err <= tol
+    flipped = ~ok_main & exempt & (err_alt <= tol)
+    bad = ~ok_main & ~flipped
+    info = dict(max_err=float(err[ok_main].max()) if ok_main.any() else 0.0,
+                exempt=int(exempt.sum()), flipped=int(flipped.sum()), pixels=int(err.size),
+                bad=int(bad.sum()),
+                worst_bad=float(np.minimum(err, err_alt)[bad].max()) if bad.any() else 0.0)
     assert not bad.any(), info
-    assert exempt.mean() <= MAX_EXEMPT_FRACTION, info
+    assert exempt.sum() <= MAX_EXEMPT_FRACTION * exempt.size + EXEMPT_SLACK, info
     return info

@@ -1,10 +1,11 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
 Bar: per-Gaussian records, tile rectangles, sorted keys, values, tile ranges and tile
-levels bit-exact; pixels within 2e-4 absolute per channel except pixels whose oracle
-threshold margin is below 1e-5 (counted, at most 0.2% of pixels); live pixels of the
-foveated render bit-equal to the full render and inherited pixels equal to their block's
-top-left pixel.
+levels bit-exact; every pixel within 2e-4 absolute per channel of the oracle, or, where the
+oracle's margin to the alpha >= 1/255 skip or the T >= 1e-4 stop is below 1e-5, of the
+oracle's colour with that decision flipped (such pixels at most 2e-4 of those compared);
+live pixels of the foveated render bit-equal to the full render and inherited pixels equal
+to their block's top-left pixel.
 """
 import numpy as np
 import pytest
@@ -346,14 +347,15 @@ def test_interpolating_fill(tile):
         assert np.array_equal(itp["img"][e][live], inh["img"][e][live])
         exact = oracle.fill_interpolate(inh["img"][e], live)
         assert np.array_equal(itp["img"][e], exact)
-        filled_ref = oracle.fill_interpolate(ref.rgb.reshape(136, 200, 3), live)
-        ok = np.ones((136, 200), bool)
-        bad = (ref.margin < gh.DELTA).reshape(136, 200)
-        # a filled pixel inherits the exemption of any neighbour it averages
-        ok &= ~(bad | np.roll(bad, 1, 0) | np.roll(bad, -1, 0) | np.roll(bad, 1, 1) | np.roll(bad, -1, 1)
-                | np.roll(np.roll(bad, 1, 0), 1, 1) | np.roll(np.roll(bad, 1, 0), -1, 1)
-                | np.roll(np.roll(bad, -1, 0), 1, 1) | np.roll(np.roll(bad, -1, 0), -1, 1))
-        assert np.abs(itp["img"][e] - filled_ref).max(axis=-1)[ok].max() <= gh.TOL
+        # the oracle's rendered pixels, each taken as the oracle's colour or -- where the
+        # GPU took a near-threshold decision the other way -- its flipped-decision colour,
+        # then filled by the oracle's rule: every pixel within the tolerance
+        gh.compare_pixels(inh["img"][e].reshape(-1, 3), ref)
+        g = inh["img"][e].reshape(-1, 3).astype(np.float64)
+        alt = ((ref.margin < gh.DELTA) & (np.abs(g - ref.rgb_alt).max(1) < np.abs(g - ref.rgb).max(1)))
+        chosen = np.where(alt[:, None], ref.rgb_alt, ref.rgb).reshape(136, 200, 3)
+        filled_ref = oracle.fill_interpolate(chosen, live)
+        assert np.abs(itp["img"][e] - filled_ref).max() <= gh.TOL
 
 
 @pytest.mark.parametrize("tile", [16, 32])
