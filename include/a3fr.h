@@ -178,6 +178,17 @@ int a3fr_render_round(a3fr_scene *scene, float *out_rgb, void *stream);
 /* Status of the last completed round, read from mapped host memory (no synchronisation). */
 int a3fr_get_round_status(a3fr_scene *scene, a3fr_round_status *status);
 
+/* Fault injection on the host (Sec. 3.3: the tracker runs on a CPU that other work can slow
+ * down).  stall != 0 begins a write of the prediction mailbox and leaves it unfinished, as
+ * when the tracker thread is descheduled in the middle of a write: the sequence word stays
+ * odd, and predictions posted meanwhile update the payload without publishing it.  A round
+ * that runs meanwhile polls the mailbox a bounded number of times (2^16), then gives up,
+ * sets A3FR_STATUS_TIMEOUT in the scene's status word (a3fr_get_stats) and keeps the last
+ * prediction it consumed -- with SIR on it grows the region around that prediction (Eq. 4)
+ * instead of waiting.  stall == 0 finishes the write and publishes the latest payload.
+ * Nothing on the GPU hangs or faults. */
+int a3fr_stall_mailbox(a3fr_scene *scene, int stall);
+
 /* ---- one frame of Algorithm 1, natively timed ---- */
 #define A3FR_DRIVE_A3FR 0  /* rounds overlapped with tracking (SIR per rounds->sir) */
 #define A3FR_DRIVE_SFR 1   /* sequential: wait for the final prediction, then render foveated */
@@ -385,7 +396,10 @@ size_t a3fr_sort_pairs_workspace_bytes(size_t n);
  * sort keyed by tile and depth (Sec. 2.3, "Sorting").  keys/vals (DEVICE uint64/uint32
  * [n]) hold the input and receive the result; keys_alt/vals_alt (DEVICE, [n]) and the
  * DEVICE workspace of a3fr_sort_pairs_workspace_bytes(n) bytes are scratch.  Bits above
- * key_bits must be zero. */
+ * key_bits must be zero.  The sort runs on `stream`, and the call returns once it has
+ * finished there: it synchronises the stream to read the device status word (bytes 16..19
+ * of the workspace), and returns A3FR_ERR_TIMEOUT when a bounded look-back wait gave up --
+ * the pairs are then not validly ordered.  n >= 2^30 returns A3FR_ERR_INVALID_ARG. */
 int a3fr_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t *vals_alt,
                     size_t n, int key_bits, void *workspace, size_t workspace_bytes,
                     void *stream);
@@ -400,10 +414,15 @@ int a3fr_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t
  *
  * keys/vals (DEVICE uint64/uint32 [n]) hold the input and receive the result, as in
  * a3fr_sort_pairs; nothing else is passed in.  The scratch (ping-pong buffers, histograms,
- * look-back words) is one fixed file-scope device array of about 5 MB, which every GPU that
- * loads the library holds until the process exits.  This call allocates nothing: no
- * cudaMalloc, no cudaFree, no allocating library routine.
+ * look-back words) is one fixed file-scope device array of 4,194,560 bytes (4.0 MiB:
+ * 12 bytes per pair of A3FR_NOALLOC_MAX_PAIRS, 1 MiB of histograms and look-back words,
+ * 256 bytes of count and status), which every GPU that loads the library holds until the
+ * process exits.  This call allocates nothing: no cudaMalloc, no cudaFree, no allocating
+ * library routine.
  *  - n > A3FR_NOALLOC_MAX_PAIRS returns A3FR_ERR_CAPACITY and does no work.
+ *  - Like a3fr_sort_pairs, the call returns once the sort has finished on `stream` (it
+ *    synchronises the stream to read the status word from the array) and returns
+ *    A3FR_ERR_TIMEOUT when a bounded look-back wait gave up.
  *  - The first call on a device looks up the array's device address (cudaGetSymbolAddress)
  *    with that device current; make that first call before any stream capture.
  *  - Every call shares the one array, so calls whose work overlaps on the GPU (on different

@@ -22,7 +22,7 @@ from ._lib import A3FRError, BUF_DEPTH, BUF_KEYS, BUF_LEVELS, BUF_N_CONTRIB, BUF
 __all__ = ["Scene", "Fovea", "A3FRError", "camera_struct", "create_scene", "destroy_scene",
            "set_camera", "set_gaze", "render_foveated", "render_full", "get_stats",
            "set_keep_aux", "set_graph_mode", "set_stage_timing", "get_stage_times", "copy_buffer", "sort_pairs", "sort_pairs_workspace_bytes",
-           "sort_pairs_noalloc", "Rounds", "begin_frame", "post_prediction", "render_round",
+           "sort_pairs_noalloc", "Rounds", "begin_frame", "post_prediction", "render_round", "stall_mailbox",
            "get_round_status", "run_frame",
            "error_string"]
 
@@ -218,6 +218,10 @@ def render_round(handle: int, out_rgb, stream=None) -> None:
                "a3fr_render_round")
 
 
+def stall_mailbox(handle: int, stall: bool) -> None:
+    _lib.check(_lib.load().a3fr_stall_mailbox(handle, int(bool(stall))), "a3fr_stall_mailbox")
+
+
 def get_round_status(handle: int) -> dict:
     st = _lib.RoundStatus()
     _lib.check(_lib.load().a3fr_get_round_status(handle, ctypes.byref(st)), "a3fr_get_round_status")
@@ -332,6 +336,9 @@ class Scene:
 
     def round_status(self) -> dict:
         return get_round_status(self.handle)
+
+    def stall_mailbox(self, stall: bool = True):
+        stall_mailbox(self.handle, stall)
 
     def stats(self, reset: bool = False) -> dict:
         return get_stats(self.handle, reset)

@@ -146,6 +146,7 @@ _SIGS = {
                           ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
     "a3fr_post_prediction": ([ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "a3fr_render_round": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p], ctypes.c_int),
+    "a3fr_stall_mailbox": ([ctypes.c_void_p, ctypes.c_int], ctypes.c_int),
     "a3fr_get_round_status": ([ctypes.c_void_p, ctypes.POINTER(RoundStatus)], ctypes.c_int),
     "a3fr_run_frame": ([ctypes.c_void_p, ctypes.POINTER(Fovea), ctypes.POINTER(Rounds),
                         ctypes.POINTER(FrameDriver), ctypes.c_void_p, ctypes.c_void_p,

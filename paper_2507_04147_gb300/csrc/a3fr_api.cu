@@ -123,6 +123,7 @@ struct a3fr_scene {
   RoundStatus *status_host = nullptr;        // mapped pinned host memory
   RoundStatus *status_dev = nullptr;
   std::mutex mbox_mutex;
+  bool mbox_stalled = false;                 // a write begun and not finished (fault injection)
   float *out_round = nullptr;                // the canvas of the frame's rounds
 
   // per-render parameters: device copy, pinned staging ring, completion of the last render
@@ -416,20 +417,40 @@ CompositeParams composite_params(const a3fr_scene *s, int eyes, const a3fr_fovea
 
 enum class Mode { kFull, kFoveated, kFirstRound };
 
-// Writes the mailbox under its sequence lock (any host thread).
+// Writes the mailbox under its sequence lock (any host thread).  While a stalled write is
+// open (a3fr_stall_mailbox) the payload is updated but the sequence stays odd: the GPU sees
+// a write in progress until the stall ends.
 void post_mailbox(a3fr_scene *s, int exit, const float *gaze, int eyes) {
   std::lock_guard<std::mutex> lock(s->mbox_mutex);
   Mailbox *m = s->mbox_host;
   const unsigned int seq = __atomic_load_n(&m->seq, __ATOMIC_RELAXED);
-  __atomic_store_n(&m->seq, seq + 1u, __ATOMIC_RELAXED);
-  std::atomic_thread_fence(std::memory_order_release);
+  if (!s->mbox_stalled) {
+    __atomic_store_n(&m->seq, seq + 1u, __ATOMIC_RELAXED);
+    std::atomic_thread_fence(std::memory_order_release);
+  }
   __atomic_store_n(&m->exit, exit, __ATOMIC_RELAXED);
   for (int q = 0; q < kMaxEyes; ++q)
     for (int k = 0; k < 2; ++k) {
       const float v = (gaze && q < eyes) ? gaze[2 * q + k] : 0.0f;
       __atomic_store(&m->gaze[q][k], &v, __ATOMIC_RELAXED);
     }
-  __atomic_store_n(&m->seq, seq + 2u, __ATOMIC_RELEASE);
+  if (!s->mbox_stalled) __atomic_store_n(&m->seq, seq + 2u, __ATOMIC_RELEASE);
+}
+
+// Opens (stall != 0) or closes a mailbox write that stays in progress: the sequence is made
+// odd and left so, as when the tracker thread is descheduled in the middle of a write.
+void stall_mailbox(a3fr_scene *s, bool stall) {
+  std::lock_guard<std::mutex> lock(s->mbox_mutex);
+  if (stall == s->mbox_stalled) return;
+  Mailbox *m = s->mbox_host;
+  const unsigned int seq = __atomic_load_n(&m->seq, __ATOMIC_RELAXED);
+  if (stall) {
+    __atomic_store_n(&m->seq, seq + 1u, __ATOMIC_RELAXED);
+    std::atomic_thread_fence(std::memory_order_release);
+  } else {
+    __atomic_store_n(&m->seq, seq + 1u, __ATOMIC_RELEASE);
+  }
+  s->mbox_stalled = stall;
 }
 
 // Copies the per-render parameters to the device (pinned staging ring), after the previous
@@ -992,6 +1013,12 @@ int a3fr_post_prediction(a3fr_scene *s, int exit_index, const float *gaze_px) {
   return A3FR_OK;
 }
 
+int a3fr_stall_mailbox(a3fr_scene *s, int stall) {
+  if (!s) return A3FR_ERR_INVALID_ARG;
+  stall_mailbox(s, stall != 0);
+  return A3FR_OK;
+}
+
 int a3fr_render_round(a3fr_scene *s, float *out_rgb, void *stream) {
   if (!s) return A3FR_ERR_INVALID_ARG;
   return render_round(s, out_rgb, static_cast<cudaStream_t>(stream));
@@ -1156,7 +1183,12 @@ int a3fr_sort_pairs(uint64_t *keys, uint32_t *vals, uint64_t *keys_alt, uint32_t
     A3FR_CHECK(cudaMemcpyAsync(keys, keys_alt, sizeof(uint64_t) * n, cudaMemcpyDeviceToDevice, st));
     A3FR_CHECK(cudaMemcpyAsync(vals, vals_alt, sizeof(uint32_t) * n, cudaMemcpyDeviceToDevice, st));
   }
-  return A3FR_OK;
+  // a look-back wait that gave up leaves partitions scattered to wrong offsets: read the
+  // status word once the sort has finished and report it
+  uint32_t host_status = 0;
+  A3FR_CHECK(cudaMemcpyAsync(&host_status, status, sizeof host_status, cudaMemcpyDeviceToHost, st));
+  A3FR_CHECK(cudaStreamSynchronize(st));
+  return (host_status & kStatusTimeout) ? A3FR_ERR_TIMEOUT : A3FR_OK;
 }
 
 const char *a3fr_error_string(int code) {

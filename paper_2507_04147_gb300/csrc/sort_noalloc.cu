@@ -81,5 +81,13 @@ extern "C" int a3fr_sort_pairs_noalloc(uint64_t *keys, uint32_t *vals, size_t n,
             cudaSuccess)
       return A3FR_ERR_CUDA;
   }
-  return A3FR_OK;
+  // the status word the look-back sets when a bounded wait gives up (the result is then
+  // not sorted), read once the sort has finished; a host stack variable, so still nothing
+  // is allocated
+  uint32_t host_status = 0;
+  if (cudaMemcpyAsync(&host_status, state + 4, sizeof host_status, cudaMemcpyDeviceToHost, st) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess)
+    return A3FR_ERR_CUDA;
+  return (host_status & a3fr::kStatusTimeout) ? A3FR_ERR_TIMEOUT : A3FR_OK;
 }

@@ -142,3 +142,59 @@ def test_native_frame_driver_modes():
     assert res[(2, True)]["latency_us"] > 0                  # FRR does not wait
     # the A3FR frame ends no earlier than the final prediction
     assert a["latency_us"] >= times[-1]
+
+
+def test_stalled_mailbox_write_times_out_and_keeps_the_last_prediction():
+    """A tracker thread descheduled in the middle of a mailbox write (Sec. 3.3, the CPU
+    slow-down that SIR is for), injected on the host: the mailbox's sequence word is held
+    odd while a round runs.  The round's bounded read must give up (2^16 polls), set
+    A3FR_STATUS_TIMEOUT, keep the prediction it already consumed and, with SIR on, grow the
+    region around it exactly as the schedule oracle's speculative round does; the GPU stays
+    usable, and once the write finishes the next round consumes the posted prediction."""
+    import time
+    import torch
+    scene_np, cams, s, out = _setup()
+    eyes = len(cams)
+    tile = 16
+    n_tiles = oracle.tiles(200, tile) * oracle.tiles(168, tile)
+    expected = [30.0, 12.0, 0.0]
+    ofv = oracle.fovea((18.0, 36.0), 0.0, (4, 2, 1))
+    gfv = a3fr.Fovea((18.0, 36.0), 0.0, (4, 2, 1))
+    st = torch.cuda.current_stream()
+    s.begin_frame(gfv, a3fr.Rounds(expected, sir=True, sir_step_px=6.0), out=out, stream=st)
+    fr = [orounds.FrameRounds(cams[e], tile, ofv, expected, True, 6.0) for e in range(eyes)]
+    p1 = [[80.0, 60.0], [78.5, 60.0]]
+    p2 = [[95.0, 70.0], [93.5, 70.0]]
+    s.post_prediction(1, p1)
+    s.render_round(out, stream=st)
+    torch.cuda.synchronize()
+    for e in range(eyes):
+        fr[e].round(1, p1[e])
+    assert s.stats(reset=True)["status"] == 0
+    s.stall_mailbox(True)
+    try:
+        s.post_prediction(2, p2)          # written, but not published while the write is open
+        t0 = time.perf_counter()
+        s.render_round(out, stream=st)
+        torch.cuda.synchronize()
+        waited = time.perf_counter() - t0
+    finally:
+        s.stall_mailbox(False)
+    st1 = s.stats(reset=True)
+    assert st1["status"] & a3fr.STATUS_TIMEOUT, st1
+    assert waited < 30.0
+    status = s.round_status()
+    assert status["exit_consumed"] == 1
+    for e in range(eyes):
+        fr[e].round(0, (0.0, 0.0))        # no readable prediction: a speculative round
+    assert np.array_equal(_levels(s, eyes, n_tiles), np.stack([f.level for f in fr]))
+    np.testing.assert_array_equal(np.array(status["radius_px"], np.float32), fr[0].r)
+    # the write has finished: the next round reads prediction 2
+    s.render_round(out, stream=st)
+    torch.cuda.synchronize()
+    for e in range(eyes):
+        fr[e].round(2, p2[e])
+    assert s.stats()["status"] == 0
+    assert s.round_status()["exit_consumed"] == 2
+    assert np.array_equal(_levels(s, eyes, n_tiles), np.stack([f.level for f in fr]))
+    print("bounded mailbox wait gave up after %.3f s" % waited)
