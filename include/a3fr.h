@@ -103,6 +103,8 @@ typedef struct {
   uint64_t records_staged;      /* Gaussian records staged by tile blocks since the reset */
   uint64_t renders;             /* renders since the last reset */
   uint64_t kernel_launches;     /* kernels this library launched since the last reset */
+  uint64_t contributions;       /* (pixel, Gaussian) blends since the last reset, counted by
+                                   renders with keep_aux on only (0 otherwise) */
 } a3fr_stats;
 
 /* Create a scene over caller-owned Gaussians.  instance_capacity bounds the number of

@@ -83,7 +83,7 @@ def lib():
         L.or_tile_ranges.argtypes = [i64, vp, i32, vp]
         L.or_layer_radii2.argtypes = [vp, vp, vp]
         L.or_level_map.argtypes = [vp, i32, vp, vp, vp]
-        L.or_render.argtypes = [i32, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.or_render.argtypes = [i32, vp, vp, vp, i32, vp, vp, i32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.or_render_eye.argtypes = [i32, i32, vp, vp, vp, vp, vp, vp, i32, vp, vp, vp, i32,
                                     vp, vp, vp, vp, vp, vp]
         L.or_num_threads.restype = i32
@@ -201,7 +201,8 @@ class Image:
         self.rgb = np.zeros((count, 3), dtype=np.float32)
         self.t_final = np.zeros(count, dtype=np.float32)
         self.n_contrib = np.zeros(count, dtype=np.int32)
-        self.n_eval = np.zeros(count, dtype=np.int32)
+        self.n_eval = np.zeros(count, dtype=np.int32)    # Gaussians whose rectangle holds the pixel, walked
+        self.n_blend = np.zeros(count, dtype=np.int32)   # Gaussians blended into the pixel
         self.margin = np.zeros(count, dtype=np.float32)
         self.rendered = np.zeros(count, dtype=np.uint8)
         self.depth = np.zeros(count, dtype=np.float32)   # expected depth sum(alpha T z)
@@ -225,7 +226,8 @@ def render(rec, rect, cam, tile: int, level=None, pixels=None) -> Image:
     lib().or_render(n, _p(np.ascontiguousarray(rec)), _p(np.ascontiguousarray(rect)),
                     ctypes.byref(c), tile, _p(lv), _p(pix), count if pix is not None else 0,
                     _p(img.rgb), _p(img.t_final), _p(img.n_contrib), _p(img.n_eval),
-                    _p(img.margin), _p(img.rendered), _p(img.depth), _p(img.rgb_alt))
+                    _p(img.margin), _p(img.rendered), _p(img.depth), _p(img.rgb_alt),
+                    _p(img.n_blend))
     return img
 
 

@@ -349,6 +349,12 @@ static int or_label(int x, int y) {
 /* ------------------------------------------------------------------- compositing */
 typedef struct { uint32_t depth_bits; uint32_t idx; } or_order;
 
+/* One entry of the global depth-ordered list as the per-pixel walk reads it: the
+ * Gaussian's index and a copy of its tile rectangle, so that the walk reads the list
+ * front to back instead of looking each rectangle up by index (the same list, the same
+ * tests, in the same order). */
+typedef struct { uint16_t x0, y0, x1, y1; uint32_t idx; } or_entry;   /* tiles < 2^16 */
+
 static int or_cmp_order(const void *pa, const void *pb) {
   const or_order *a = (const or_order *)pa, *b = (const or_order *)pb;
   if (a->depth_bits != b->depth_bits) return a->depth_bits < b->depth_bits ? -1 : 1;
@@ -369,23 +375,24 @@ enum { OR_FLIP_NONE = -1, OR_FLIP_SKIP = 0, OR_FLIP_STOP = 1 };
 
 typedef struct {
   float rgb[3], t_final, margin, depth;
-  int32_t n_contrib, n_eval;
+  int32_t n_contrib, n_eval, n_blend;
   int32_t min_j, min_kind;   /* where the smallest margin was taken */
 } or_walk_result;
 
 static void or_walk(int x, int y, int tile, const float *rec, const int32_t *rect,
-                    const or_order *list, int n_vis, int flip_j, int flip_kind,
+                    const or_entry *list, int n_vis, int flip_j, int flip_kind,
                     or_walk_result *res) {
   const int ptx = x / tile, pty = y / tile;
   float T = 1.0f, C[3] = {0.0f, 0.0f, 0.0f};
   float Z = 0.0f;   /* expected depth: the blend weights applied to camera-space depth */
-  int32_t contrib = 0, evals = 0;
+  int32_t contrib = 0, evals = 0, blends = 0;
   float m = INFINITY;
   int32_t min_j = -1, min_kind = OR_FLIP_NONE;
   for (int j = 0; j < n_vis; ++j) {
-    const uint32_t g = list[j].idx;
-    const int32_t *rc = rect + (size_t)g * 4;
-    if (ptx < rc[0] || ptx >= rc[2] || pty < rc[1] || pty >= rc[3]) continue;
+    const or_entry *le = list + j;
+    /* the pixel's tile inside the rectangle (one combined test, no short circuit) */
+    if (!((ptx >= le->x0) & (ptx < le->x1) & (pty >= le->y0) & (pty < le->y1))) continue;
+    const uint32_t g = le->idx;
     const float *o = rec + (size_t)g * OR_REC;
     ++evals;
     const float dx = o[0] - (float)x, dy = o[1] - (float)y;
@@ -408,11 +415,13 @@ static void or_walk(int x, int y, int tile, const float *rec, const int32_t *rec
     Z += o[9] * alpha * T;
     T = testT;
     contrib = evals;
+    ++blends;
   }
   res->rgb[0] = C[0]; res->rgb[1] = C[1]; res->rgb[2] = C[2];   /* + T * background, 0 */
   res->t_final = T;
   res->n_contrib = contrib;
   res->n_eval = evals;
+  res->n_blend = blends;
   res->margin = m;
   res->depth = Z;
   res->min_j = min_j;
@@ -424,9 +433,9 @@ static void or_walk(int x, int y, int tile, const float *rec, const int32_t *rec
 static const float OR_ALT_BELOW = 1e-3f;
 
 static void or_shade(int x, int y, int tile, const float *rec, const int32_t *rect,
-                     const or_order *list, int n_vis, float out[3], float *t_final,
+                     const or_entry *list, int n_vis, float out[3], float *t_final,
                      int32_t *n_contrib, int32_t *n_eval, float *margin, float *depth,
-                     float *out_alt) {
+                     float *out_alt, int32_t *n_blend) {
   or_walk_result r;
   or_walk(x, y, tile, rec, rect, list, n_vis, -1, OR_FLIP_NONE, &r);
   out[0] = r.rgb[0]; out[1] = r.rgb[1]; out[2] = r.rgb[2];
@@ -435,6 +444,7 @@ static void or_shade(int x, int y, int tile, const float *rec, const int32_t *re
   *n_eval = r.n_eval;
   *margin = r.margin;
   if (depth) *depth = r.depth;
+  if (n_blend) *n_blend = r.n_blend;
   if (out_alt) {
     out_alt[0] = r.rgb[0]; out_alt[1] = r.rgb[1]; out_alt[2] = r.rgb[2];
     if (r.min_j >= 0 && r.margin < OR_ALT_BELOW) {
@@ -445,16 +455,24 @@ static void or_shade(int x, int y, int tile, const float *rec, const int32_t *re
   }
 }
 
-static or_order *or_global_list(int n, const float *rec, int *n_vis) {
-  or_order *list = (or_order *)malloc(sizeof(or_order) * (size_t)(n > 0 ? n : 1));
+static or_entry *or_global_list(int n, const float *rec, const int32_t *rect, int *n_vis) {
+  or_order *order = (or_order *)malloc(sizeof(or_order) * (size_t)(n > 0 ? n : 1));
   int c = 0;
   for (int i = 0; i < n; ++i)
     if (rec[(size_t)i * OR_REC + 11] != 0.0f) {
-      list[c].depth_bits = or_float_bits(rec[(size_t)i * OR_REC + 9]);
-      list[c].idx = (uint32_t)i;
+      order[c].depth_bits = or_float_bits(rec[(size_t)i * OR_REC + 9]);
+      order[c].idx = (uint32_t)i;
       ++c;
     }
-  qsort(list, (size_t)c, sizeof(or_order), or_cmp_order);
+  qsort(order, (size_t)c, sizeof(or_order), or_cmp_order);
+  or_entry *list = (or_entry *)malloc(sizeof(or_entry) * (size_t)(c > 0 ? c : 1));
+  for (int j = 0; j < c; ++j) {
+    const int32_t *rc = rect + (size_t)order[j].idx * 4;
+    list[j].x0 = (uint16_t)rc[0]; list[j].y0 = (uint16_t)rc[1];
+    list[j].x1 = (uint16_t)rc[2]; list[j].y1 = (uint16_t)rc[3];
+    list[j].idx = order[j].idx;
+  }
+  free(order);
   *n_vis = c;
   return list;
 }
@@ -467,17 +485,18 @@ static or_order *or_global_list(int n, const float *rec, int *n_vis) {
  * actually shaded (the top-left one for inherited pixels); rendered[] is 1 when the
  * pixel itself was shaded; depth (optional) is the expected depth sum(alpha T z) of the
  * blended Gaussians, the usual 3DGS depth render; rgb_alt (optional) is the colour with
- * the pixel's nearest threshold decision flipped (see or_shade). */
+ * the pixel's nearest threshold decision flipped (see or_shade); n_blend (optional) counts
+ * the Gaussians blended into the shaded pixel. */
 void or_render(int n, const float *rec, const int32_t *rect, const or_camera *cam, int tile,
                const uint8_t *level, const int32_t *pix, int n_pix, float *rgb,
                float *t_final, int32_t *n_contrib, int32_t *n_eval, float *margin,
-               uint8_t *rendered, float *depth, float *rgb_alt) {
+               uint8_t *rendered, float *depth, float *rgb_alt, int32_t *n_blend) {
   int n_vis = 0;
-  or_order *list = or_global_list(n, rec, &n_vis);
+  or_entry *list = or_global_list(n, rec, rect, &n_vis);
   const int W = cam->width, H = cam->height;
   const int tiles_x = or_tiles(W, tile);
   const int64_t count = pix ? (int64_t)n_pix : (int64_t)W * H;
-#pragma omp parallel for schedule(dynamic, 64)
+#pragma omp parallel for schedule(dynamic, 1)
   for (int64_t p = 0; p < count; ++p) {
     int x, y;
     if (pix) { x = pix[2 * p]; y = pix[2 * p + 1]; }
@@ -490,7 +509,8 @@ void or_render(int n, const float *rec, const int32_t *rect, const or_camera *ca
       if (!live) { sx = x & ~1; sy = y & ~1; }
     }
     or_shade(sx, sy, tile, rec, rect, list, n_vis, rgb + 3 * p, t_final + p, n_contrib + p,
-             n_eval + p, margin + p, depth ? depth + p : NULL, rgb_alt ? rgb_alt + 3 * p : NULL);
+             n_eval + p, margin + p, depth ? depth + p : NULL, rgb_alt ? rgb_alt + 3 * p : NULL,
+             n_blend ? n_blend + p : NULL);
     if (rendered) rendered[p] = (uint8_t)live;
   }
   free(list);
@@ -514,7 +534,7 @@ void or_render_eye(int n, int degree, const float *means, const float *log_scale
     or_level_map(cam, tile, fv, gaze, level);
   }
   or_render(n, rec, rect, cam, tile, level, pix, n_pix, rgb, t_final, n_contrib, n_eval,
-            margin, rendered, NULL, NULL);
+            margin, rendered, NULL, NULL, NULL);
   free(level);
   free(touched);
   free(rect);

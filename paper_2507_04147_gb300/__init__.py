@@ -134,7 +134,7 @@ def get_stats(handle: int, reset: bool = False) -> dict:
             "instances_eye": [st.instances_eye[0], st.instances_eye[1]],
             "capacity": st.capacity, "evaluations": st.evaluations,
             "records_staged": st.records_staged, "renders": st.renders,
-            "kernel_launches": st.kernel_launches}
+            "kernel_launches": st.kernel_launches, "contributions": st.contributions}
 
 
 def set_stage_timing(handle: int, ring: int) -> None:

@@ -47,7 +47,7 @@ class Stats(ctypes.Structure):
                 ("instances", ctypes.c_int64), ("instances_eye", ctypes.c_int64 * 2),
                 ("capacity", ctypes.c_int64), ("evaluations", ctypes.c_uint64),
                 ("records_staged", ctypes.c_uint64), ("renders", ctypes.c_uint64),
-                ("kernel_launches", ctypes.c_uint64)]
+                ("kernel_launches", ctypes.c_uint64), ("contributions", ctypes.c_uint64)]
 
 
 MAX_EXITS = 8

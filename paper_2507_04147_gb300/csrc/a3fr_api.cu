@@ -86,7 +86,7 @@ struct a3fr_scene {
   void *frame_ws = nullptr;
   size_t frame_ws_bytes = 0;
   uint32_t *counts = nullptr;                // [0] kept, [1..2] per eye, [3] total, [4] entries
-  // persistent device state: status | counters[2] | thresholds[2]
+  // persistent device state: status | counters[3] (evaluations, staged, blends) | thresholds[2]
   uint32_t *status = nullptr;
   unsigned long long *counters = nullptr;
   uint32_t *thresholds = nullptr;            // per-eye heavy-tile count thresholds
@@ -1054,7 +1054,7 @@ int a3fr_get_stats(a3fr_scene *s, a3fr_stats *st, int reset) {
   uint32_t counts[4] = {0, 0, 0, 0};
   if (s->counts) A3FR_CHECK(cudaMemcpy(counts, s->counts, sizeof counts, cudaMemcpyDeviceToHost));
   uint32_t status;
-  unsigned long long ctr[2];
+  unsigned long long ctr[3];
   std::memcpy(&status, buf + 16, sizeof status);
   std::memcpy(ctr, buf + 32, sizeof ctr);
   std::memset(st, 0, sizeof *st);
@@ -1066,11 +1066,12 @@ int a3fr_get_stats(a3fr_scene *s, a3fr_stats *st, int reset) {
   st->capacity = (int64_t)s->capacity;
   st->evaluations = ctr[0];
   st->records_staged = ctr[1];
+  st->contributions = ctr[2];
   st->renders = s->renders;
   st->kernel_launches = s->launches;
   if (reset) {
     A3FR_CHECK(cudaMemset(s->status, 0, sizeof(uint32_t)));
-    A3FR_CHECK(cudaMemset(s->counters, 0, 2 * sizeof(unsigned long long)));
+    A3FR_CHECK(cudaMemset(s->counters, 0, 3 * sizeof(unsigned long long)));
     s->renders = 0;
     s->launches = 0;
   }

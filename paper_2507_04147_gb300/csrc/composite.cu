@@ -293,6 +293,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
   float Z = 0.0f;                      // expected depth (auxiliary output)
   uint32_t last = 0;                   // 1-based position of the last contributor
   uint32_t stop = 0;                   // Gaussians evaluated when the pixel stopped
+  uint32_t blended = 0;                // Gaussians blended into the pixel (auxiliary mode)
   bool done = !inside;
   uint32_t staged = 0;
   if (kFull) {   // compile-time layout: one level-4 tile, the whole CTA stages together
@@ -362,7 +363,10 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
           C0 += rgb.x * w;
           C1 += rgb.y * w;
           C2 += rgb.z * w;
-          if (kAux) Z += cz.y * w;
+          if (kAux) {
+            Z += cz.y * w;
+            blended += upd ? 1u : 0u;
+          }
           T = upd ? tt : T;
           last = upd ? pos : last;
           stop = fin ? pos : stop;
@@ -436,13 +440,18 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
     }
   }
 
-  // ---- statistics: evaluations of this warp, records staged by this staging group
-  unsigned long long ev = stop;
+  // ---- statistics: evaluations of this warp, records staged by this staging group, and
+  // (auxiliary mode) blends
+  unsigned long long ev = stop, bl = blended;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if (kAux) bl += __shfl_xor_sync(0xffffffffu, bl, o);
+  }
   if (lane == 0) {
     if (ev) atomicAdd(counters, ev);
     if (gt == 0 && staged) atomicAdd(counters + 1, (unsigned long long)staged);
+    if (kAux && bl) atomicAdd(counters + 2, bl);
   }
 }
 
@@ -528,6 +537,7 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
 
   float T[P], C0[P], C1[P], C2[P], Z[P];
   uint32_t last[P], stop[P];
+  uint32_t blended = 0;   // Gaussians blended into the lane's pixels (auxiliary mode)
   bool done[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) {
@@ -635,7 +645,10 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
             C0[k] += rgb.x * w;
             C1[k] += rgb.y * w;
             C2[k] += rgb.z * w;
-            if (kAux) Z[k] += cz.y * w;
+            if (kAux) {
+              Z[k] += cz.y * w;
+              blended += upd ? 1u : 0u;
+            }
             T[k] = upd ? tt : T[k];
             last[k] = upd ? pos : last[k];
             stop[k] = fin ? pos : stop[k];
@@ -681,11 +694,16 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
       }
     }
   }
+  unsigned long long bl = blended;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) ev += __shfl_xor_sync(0xffffffffu, ev, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    ev += __shfl_xor_sync(0xffffffffu, ev, o);
+    if (kAux) bl += __shfl_xor_sync(0xffffffffu, bl, o);
+  }
   if (lane == 0) {
     if (ev) atomicAdd(counters, ev);
     if (t == 0 && staged) atomicAdd(counters + 1, (unsigned long long)staged);
+    if (kAux && bl) atomicAdd(counters + 2, bl);
   }
 }
 

@@ -111,6 +111,8 @@ def render64(scene, cam, tile: int):
     H, W = cam.height, cam.width
     img = np.zeros((H, W, 3))
     tfin = np.ones((H, W))
+    n_eval = np.zeros((H, W), np.int64)    # list entries walked (the stopping one included)
+    n_blend = np.zeros((H, W), np.int64)   # Gaussians blended
     vis = np.nonzero(p["visible"])[0]
     for y in range(H):
         for x in range(W):
@@ -120,6 +122,7 @@ def render64(scene, cam, tile: int):
             order = sel[np.lexsort((sel, p["depth"][sel]))]
             T, C = 1.0, np.zeros(3)
             for g in order:
+                n_eval[y, x] += 1
                 dx, dy = p["u"][g] - x, p["v"][g] - y
                 ca, cb, cc = p["conic"][g]
                 power = -0.5 * (ca * dx * dx + cc * dy * dy) - cb * dx * dy
@@ -133,6 +136,8 @@ def render64(scene, cam, tile: int):
                     break
                 C += p["rgb"][g] * alpha * T
                 T = tt
+                n_blend[y, x] += 1
             img[y, x] = C
             tfin[y, x] = T
+    p["n_eval"], p["n_blend"] = n_eval, n_blend
     return img, tfin, p

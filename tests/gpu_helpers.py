@@ -13,15 +13,19 @@ import paper_2507_04147_gb300 as a3fr
 # stop when the oracle's margin to that decision is tiny.  Every pixel must match the oracle
 # within TOL, or -- only where the oracle's margin is below DELTA -- match the oracle's
 # colour with that nearest decision taken the other way (Image.rgb_alt) within TOL.  So
-# no pixel goes unchecked.  The exempt set (margin < DELTA) is decided by the oracle alone;
-# on the parity scenes it measures 4-7e-5 of the pixels, and it must stay below
-# MAX_EXEMPT_FRACTION of the pixels compared plus EXEMPT_SLACK pixels (a sample of a few
-# thousand pixels expects well under one exempt pixel, so the slack absorbs the Poisson
-# spread of small samples): a sanity bound on the scene and on DELTA (the margin pins in
-# test_oracle_margin.py fix how the margin is computed).
+# no pixel goes unchecked.  The exempt set (margin < DELTA) is decided by the oracle alone,
+# and its size is a property of the scene: a Gaussian of opacity o blended into a pixel has
+# alpha within a relative DELTA of 1/255 on a band that is a fraction 2 DELTA / ln(255 o) of
+# its footprint, so the exempt count grows with the blends, and more with faint Gaussians
+# (Beta(0.5, 0.5) opacities).  It must stay below EXEMPT_PER_BLEND per blended
+# (pixel, Gaussian) pair of the compared pixels plus EXEMPT_SLACK pixels (the Poisson spread
+# of small samples): a sanity bound on the scene and on DELTA.  Measured: 4-7e-5 of the
+# pixels (7e-6 per blend) on the uniform scenes, 5 in 7,456 pixels of the heaviest
+# tiles of the 3M clustered frame.  The margin pins in test_oracle_margin.py fix how the
+# margin is computed.
 TOL = 2e-4
 DELTA = 1e-5
-MAX_EXEMPT_FRACTION = 2e-4
+EXEMPT_PER_BLEND = 1e-4
 EXEMPT_SLACK = 3
 
 
@@ -83,5 +87,6 @@ def compare_pixels(gpu_rgb, ref, tol=TOL, delta=DELTA):
                 bad=int(bad.sum()),
                 worst_bad=float(np.minimum(err, err_alt)[bad].max()) if bad.any() else 0.0)
     assert not bad.any(), info
-    assert exempt.sum() <= MAX_EXEMPT_FRACTION * exempt.size + EXEMPT_SLACK, info
+    info["blends"] = int(ref.n_blend.sum())
+    assert exempt.sum() <= EXEMPT_PER_BLEND * info["blends"] + EXEMPT_SLACK, info
     return info

@@ -46,7 +46,7 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(_lib.Camera) == 4 * 19
     assert ctypes.sizeof(_lib.Fovea) == 4 * 11
     assert ctypes.sizeof(_lib.SceneDesc) == 16 + 5 * 8
-    assert ctypes.sizeof(_lib.Stats) == 8 + 8 + 16 + 8 + 32
+    assert ctypes.sizeof(_lib.Stats) == 8 + 8 + 16 + 8 + 40
 
 
 def test_error_strings(lib):

@@ -236,7 +236,7 @@ def test_stack_front_to_back_and_early_stop_closed_form():
     ref = sum(colours[k] * 0.95 * 0.05 ** k for k in range(3))
     np.testing.assert_allclose(img.rgb[p], ref, rtol=1e-5)
     np.testing.assert_allclose(img.t_final[p], 0.05 ** 3, rtol=1e-4)
-    assert img.n_contrib[p] == 3 and img.n_eval[p] == 4
+    assert img.n_contrib[p] == 3 and img.n_eval[p] == 4 and img.n_blend[p] == 3
     # expected depth: the same blend weights applied to the three depths
     np.testing.assert_allclose(img.depth[p], sum(depths[k] * 0.95 * 0.05 ** k for k in range(3)),
                                rtol=1e-5)
@@ -300,6 +300,10 @@ def test_fp64_brute_force_tiny_scene(seed, deg):
     err = np.abs(img.rgb - ref.reshape(-1, 3)).max(axis=1)
     assert err[ok].max() < 1e-5, err[ok].max()
     assert np.abs(img.t_final - tref.reshape(-1))[ok].max() < 1e-5
+    # the work counts of the composite (the flop count's n_eval and n_contrib)
+    assert np.array_equal(img.n_eval[ok], p["n_eval"].reshape(-1)[ok])
+    assert np.array_equal(img.n_blend[ok], p["n_blend"].reshape(-1)[ok])
+    assert (img.n_blend <= img.n_eval).all() and img.n_blend.sum() > 0
 
 
 # ------------------------------------------------------------------ keys, ranges
