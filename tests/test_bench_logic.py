@@ -1,9 +1,10 @@
 """Host arithmetic of bench.py's roofline line, on CPU with a stand-in workload.
 
 The roofline reports the stage with the largest share of the frame: its algorithmic work per
-launch (bytes for the HBM-bound stages, 14 flop per pixel-Gaussian evaluation for the
-composite) over the measured stage time, against the measured HBM bandwidth or the FP32 peak
-derived from the SM count, lanes and clock.
+launch (bytes for the HBM-bound stages; for the composite 10 flop per pixel-Gaussian
+evaluation plus 5 per blend) over the measured launch time, against the measured HBM
+bandwidth or the FP32 peak derived from the SM count, lanes and clock.  A composite timed
+as a replayed graph takes its launch time and its share from the graph-timed frame.
 """
 import json
 import os
@@ -31,18 +32,32 @@ def test_composite_dominant_reports_alu_fraction():
     st = _stats(evals_per_frame=1.0e8, staged_per_frame=2.0e5, frames=10)
     stage_ms = {"preprocess": 0.05, "depth_sort": 0.07, "bin": 0.05, "emit": 0.06,
                 "composite": 0.16}
-    r = bench.roofline(w, st, stage_ms, n_frames=10, eyes=2, tile=32)
+    r = bench.roofline(w, st, stage_ms, n_frames=10, eyes=2, tile=32, blends=3.0e7 * 10)
     assert r["kernel"] == "composite" and r["bound"] == "alu" and r["unit"] == "TFLOP/s"
-    assert r["work_per_launch"] == pytest.approx(14.0e8)
-    assert r["achieved"] == pytest.approx(14.0e8 / 0.16e-3 / 1e12)
+    assert r["work_per_launch"] == pytest.approx(10.0 * 1.0e8 + 5.0 * 3.0e7)
+    assert r["achieved"] == pytest.approx(r["work_per_launch"] / 0.16e-3 / 1e12)
     peaks, _ = bench.measured_peaks()
     mhz = float(peaks.get("sm_max_mhz", 2070.0))
     assert r["peak"] == pytest.approx(152 * 128 * 2 * mhz * 1e6 / 1e12)
     assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
     assert r["share_of_frame"] == pytest.approx(0.16 / 0.39)
+    assert r["work"]["blends_per_frame"] == pytest.approx(3.0e7)
     # algorithmic bytes of the composite: 52 B per staged record + 12 B per pixel
     px = 2 * 1280 * 1280
     assert r["composite_hbm"]["bytes_per_launch"] == pytest.approx(2.0e5 * 52 + px * 12)
+
+
+def test_composite_in_graph_mode_takes_graph_time_and_share():
+    w = _workload()
+    st = _stats(evals_per_frame=1.0e8, staged_per_frame=2.0e5, frames=10)
+    stage_ms = {"preprocess": 0.05, "depth_sort": 0.07, "bin": 0.05, "emit": 0.06,
+                "composite": 0.16}
+    g = {"precompute": 0.21, "composite": 0.17}
+    r = bench.roofline(w, st, stage_ms, n_frames=10, eyes=2, tile=32, blends=0, graph_ms=g)
+    assert r["launch_ms"] == 0.17 and r["launch_ms_direct"] == 0.16
+    assert r["achieved"] == pytest.approx(1.0e9 / 0.17e-3 / 1e12)
+    assert r["share_of_frame"] == pytest.approx(0.17 / 0.38)
+    assert "graph" in r["launch"] and "graph" in r["share_basis"]
 
 
 def test_hbm_stage_dominant_uses_measured_bandwidth():

@@ -56,7 +56,10 @@ def test_frames_shard_without_overlap_and_timing_reduces():
 
 
 def test_single_rank_defaults():
-    assert bench.frames_for_rank(0, 1, 5, 240) == [0, 1, 2, 3, 4]
+    assert bench.frames_for_rank(0, 1, 5, 240) == [0, 48, 96, 144, 192]   # spread evenly
+    assert bench.frames_for_rank(0, 1, 240, 240) == list(range(240))
+    assert bench.frames_for_rank(0, 1, 300, 240)[238:242] == [238, 239, 0, 1]
+    assert bench.frames_for_rank(1, 2, 4, 240) == [30, 90, 150, 210]
     assert bench.reduce_max(3.0, 1) == 3.0
     a = bench.parse_args([])
     assert a.gpus == 1 and a.steps > 0 and a.warmup >= 3
