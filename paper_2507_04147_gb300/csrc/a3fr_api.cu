@@ -140,7 +140,6 @@ struct a3fr_scene {
   bool capturing = false;    // a graph capture is in progress (stage marks are not recorded)
   uint64_t alloc_gen = 1;                    // bumped whenever a workspace buffer moves
   cudaStream_t capture_stream = nullptr;
-  ForkStreams fork{};                        // concurrent launches of the 32-pixel composite
   cudaGraphExec_t g_pre = nullptr, g_fov = nullptr, g_full = nullptr;
   uint64_t g_pre_key = 0, g_fov_key = 0, g_full_key = 0;
   uint64_t g_pre_launches = 0;               // kernels in the precompute graph
@@ -627,15 +626,13 @@ int enqueue_pre(a3fr_scene *s, int eyes, cudaStream_t stream, bool allow_resize,
 int enqueue_comp(a3fr_scene *s, const CompositeParams &cp, int uniform, uint8_t *cur, bool fill,
                  cudaStream_t stream, uint64_t *launches) {
   A3FR_CHECK(mark(s, A3FR_STAGE_COMPOSITE, stream));
+  int kernels = 0;
   A3FR_CHECK(launch_composite(cp, &s->params_dev->comp, s->rec, s->desc.n, s->ranges, s->counts,
                               s->vals, s->gaze_dev, nullptr, uniform, cur, s->plan, s->levels,
                               s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr,
-                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, s->thresholds, stream, &s->fork));
-  // the composite: one kernel (32-pixel tiles, foveated: one per label count), plus the plan
-  // (and the count threshold) of a foveated render
-  *launches += (cp.full ? 0 : 1 + (cp.count_frac > 0.0f && uniform == 0 ? 1 : 0)) +
-                (cp.tile == 32 && !cp.full ? 4 : 1);
+                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, s->thresholds, stream, &kernels));
+  *launches += (uint64_t)kernels;
   if (fill) {
     A3FR_CHECK(launch_fill(cp, &s->params_dev->comp, s->levels, stream));
     ++*launches;
@@ -789,14 +786,15 @@ int render_round(a3fr_scene *s, float *out, cudaStream_t stream) {
   if (rc != A3FR_OK) return rc;
   A3FR_CHECK(launch_round_begin(s->round_cfg, s->mbox_dev, s->round_state, s->round_plan,
                                 s->status_dev, s->status, stream));
+  int kernels = 0;
   A3FR_CHECK(launch_composite(hp.comp, &s->params_dev->comp, s->rec, s->desc.n, s->ranges,
                               s->counts, s->vals, s->gaze_dev, s->round_plan, 0, s->cur_level,
                               s->plan, s->levels, s->keep_aux ? s->t_final : nullptr,
                               s->keep_aux ? s->n_contrib : nullptr,
-                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, s->thresholds, stream, &s->fork));
+                              s->keep_aux ? s->depth : nullptr, s->counters, s->batch_mult, s->thresholds, stream, &kernels));
   rc = finish_render(s, stream);
   if (rc != A3FR_OK) return rc;
-  s->launches += 2 + (s->desc.tile == 32 ? 4 : 1);   // round_begin, plan, composite
+  s->launches += 1 + (uint64_t)kernels;   // round_begin, plan, composite
   s->last_stream = stream;
   s->bw_mode = 0;
   return A3FR_OK;
@@ -873,12 +871,6 @@ int a3fr_create_scene(const a3fr_scene_desc *desc, size_t instance_capacity, a3f
   for (int k = 0; k < kSlots; ++k)
     if ((e = cudaEventCreateWithFlags(&s->params_copied[k], cudaEventDisableTiming)) != cudaSuccess)
       return fail(cuda_fail(e, "cudaEventCreate(params)"));
-  if ((e = cudaEventCreateWithFlags(&s->fork.fork, cudaEventDisableTiming)) != cudaSuccess)
-    return fail(cuda_fail(e, "cudaEventCreate(fork)"));
-  for (int f = 0; f < 3; ++f)
-    if ((e = cudaStreamCreateWithFlags(&s->fork.aux[f], cudaStreamNonBlocking)) != cudaSuccess ||
-        (e = cudaEventCreateWithFlags(&s->fork.join[f], cudaEventDisableTiming)) != cudaSuccess)
-      return fail(cuda_fail(e, "cudaStreamCreate(fork)"));
   if ((e = cudaMalloc(&s->round_state, sizeof(RoundState))) != cudaSuccess ||
       (e = cudaMalloc(&s->round_plan, sizeof(RoundPlan))) != cudaSuccess ||
       (e = cudaMemset(s->round_state, 0, sizeof(RoundState))) != cudaSuccess ||
@@ -920,11 +912,6 @@ int a3fr_destroy_scene(a3fr_scene *s) {
   if (s->g_fov) cudaGraphExecDestroy(s->g_fov);
   if (s->g_full) cudaGraphExecDestroy(s->g_full);
   if (s->capture_stream) cudaStreamDestroy(s->capture_stream);
-  if (s->fork.fork) cudaEventDestroy(s->fork.fork);
-  for (int f = 0; f < 3; ++f) {
-    if (s->fork.aux[f]) cudaStreamDestroy(s->fork.aux[f]);
-    if (s->fork.join[f]) cudaEventDestroy(s->fork.join[f]);
-  }
   if (s->mbox_host) cudaFreeHost(s->mbox_host);
   if (s->status_host) cudaFreeHost(s->status_host);
   if (s->small) cudaFree(s->small);

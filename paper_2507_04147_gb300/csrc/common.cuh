@@ -243,26 +243,23 @@ cudaError_t launch_fill(const CompositeParams &p, const CompositeParams *p_dev, 
 
 // Bytes of the work plan of launch_composite for n_ranges = n_eyes * n_tiles.
 size_t plan_bytes(int n_ranges);
-// One composite launch (plan kernel + composite).  p.full: every tile at level 4, no plan.
-// Otherwise the plan gives each tile labels (lo, hi]: a normal foveated render uses the gaze
-// (round == nullptr, uniform == 0); the first round of a frame renders every tile at level
-// `uniform` from label 0 and sets cur; a later round (round != nullptr) renders from cur up
-// to the level of its gaze and radii, stores only those pixels, and raises cur.  Ranges are
-// clamped to kept[0] (the instances the sort kept).
-// p (host copy) decides the launch shape; the kernels read p_dev (the same values).  With
-// fork (optional), the 32-pixel foveated composite's launches (one per label count) run
-// concurrently on fork->aux, joined back into s.
-struct ForkStreams {
-  cudaStream_t aux[3];
-  cudaEvent_t fork, join[3];
-};
+// One composite: the work plan (tile levels and label intervals) and the compositing.
+// Label intervals: a normal foveated render uses the gaze (round == nullptr, uniform == 0);
+// the first round of a frame renders every tile at level `uniform` from label 0 and sets cur;
+// a later round (round != nullptr) renders from cur up to the level of its gaze and radii,
+// stores only those pixels, and raises cur; p.full renders every tile at level 4.  Ranges
+// are clamped to kept[0] (the instances the sort kept).  32-pixel tiles: the plan cuts tiles
+// into work items (plan32) and one persistent launch renders them all, heaviest first;
+// 16-pixel tiles: the plan buckets tiles by label count (none for p.full) and one launch
+// packs them into CTAs.  p (host copy) decides the launch shape; the kernels read p_dev (the
+// same values).  *kernels (optional) receives the number of kernels launched.
 cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_dev,
                              const float *rec, int n, const uint2 *ranges, const uint32_t *kept,
                              const uint32_t *vals, const float *gaze, const RoundPlan *round,
                              int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, float *depth,
                              unsigned long long *counters, int batch_mult, uint32_t *thresholds,
-                             cudaStream_t s, const ForkStreams *fork = nullptr);
+                             cudaStream_t s, int *kernels = nullptr);
 
 // Incremental rounds (Sec. 3.3, Alg. 1): state on the device, mailbox in mapped host memory.
 struct RoundConfig {

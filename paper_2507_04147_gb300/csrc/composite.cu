@@ -21,6 +21,8 @@
 // folded into the conic.  The blend is branch-free (predicated updates), so a warp whose
 // lanes disagree on the accept test does not run both sides.  Label-1 warps also write the
 // inherited pixels of their blocks.
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace a3fr {
@@ -95,13 +97,48 @@ tile_threshold_kernel(const CompositeParams *__restrict__ pp, const uint2 *__res
   }
 }
 
-// Work plan of one composite launch.  Each tile gets a label interval (lo, hi] to render;
-// entries (tile << 2 | lo) are bucketed by hi - lo in plan[(hi - lo - 1) * n_ranges + slot]
-// with the bucket sizes in plan_counts[0..3].  Three uses:
-//   * a normal foveated render: lo = 0, hi = the tile's level from the gaze mailbox;
-//   * the first round of a frame (uniform > 0): lo = 0, hi = uniform for every tile;
+// Label interval (lo, hi] a composite renders in tile gt (eye-major global tile index), and
+// the tile's bookkeeping (cur, levels).  Three uses:
+//   * a normal foveated render: lo = 0, hi = the tile's level from the gaze mailbox (Eq. 1),
+//     lowered for heavy tiles by the count-based rule when count_frac > 0;
+//   * a uniform render (uniform > 0): lo = 0, hi = uniform for every tile (the first round of
+//     a frame, and the full-resolution render with uniform = 4);
 //   * a later round (round != nullptr): hi = the level from the round's gaze and radii, lo =
-//     the level already rendered (cur); tiles with hi <= lo get no entry; cur becomes hi.
+//     the level already rendered (cur); tiles with hi <= lo render nothing; cur becomes hi.
+__device__ __forceinline__ void tile_interval(const CompositeParams &p, int gt, const float *gaze,
+                                              const RoundPlan *round, int uniform, uint8_t *cur,
+                                              uint8_t *levels, const uint2 *ranges,
+                                              const uint32_t *thresholds, int *lo_out, int *hi_out) {
+  const int eye = gt / p.n_tiles;
+  const int tile = gt - eye * p.n_tiles;
+  int lo = 0, hi;
+  if (uniform > 0) {
+    hi = uniform;
+  } else if (round != nullptr) {
+    hi = 0;
+    if (round->active) {
+      CompositeParams q = p;
+      for (int k = 0; k < 3; ++k) q.r2[eye][k] = round->r2[eye][k];
+      hi = tile_level(q, eye, tile, &round->gaze[0][0]);
+    }
+    lo = cur[gt];
+  } else {
+    hi = tile_level(p, eye, tile, gaze);
+    if (p.count_frac > 0.0f && (hi == 2 || hi == 3)) {
+      // a heavy tile (count >= the k-th largest count of its eye) drops one level
+      const uint2 r = ranges[gt];
+      const uint32_t c = r.y - r.x;
+      if (c > 0u && c >= thresholds[eye]) hi -= 1;
+    }
+  }
+  if (cur != nullptr && hi > lo) cur[gt] = (uint8_t)hi;
+  levels[gt] = (uint8_t)(hi > lo ? hi : lo);
+  *lo_out = lo;
+  *hi_out = hi;
+}
+
+// Work plan of one 16-pixel-tile composite launch: entries (tile << 2 | lo) bucketed by
+// hi - lo in plan[(hi - lo - 1) * n_ranges + slot], the bucket sizes in plan_counts[0..3].
 __global__ void __launch_bounds__(256)
 plan_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ gaze_ring,
             const RoundPlan *__restrict__ round, int uniform, uint8_t *__restrict__ cur,
@@ -115,31 +152,9 @@ plan_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ ga
   const int lane = threadIdx.x & 31;
   int lo = 0, count = 0;
   if (gt < n_ranges) {
-    const int eye = gt / p.n_tiles;
-    const int tile = gt - eye * p.n_tiles;
     int hi;
-    if (uniform > 0) {
-      hi = uniform;
-    } else if (round != nullptr) {
-      hi = 0;
-      if (round->active) {
-        CompositeParams q = p;
-        for (int k = 0; k < 3; ++k) q.r2[eye][k] = round->r2[eye][k];
-        hi = tile_level(q, eye, tile, &round->gaze[0][0]);
-      }
-      lo = cur[gt];
-    } else {
-      hi = tile_level(p, eye, tile, gaze);
-      if (p.count_frac > 0.0f && (hi == 2 || hi == 3)) {
-        // a heavy tile (count >= the k-th largest count of its eye) drops one level
-        const uint2 r = ranges[gt];
-        const uint32_t c = r.y - r.x;
-        if (c > 0u && c >= thresholds[eye]) hi -= 1;
-      }
-    }
+    tile_interval(p, gt, gaze, round, uniform, cur, levels, ranges, thresholds, &lo, &hi);
     count = hi > lo ? hi - lo : 0;
-    if (cur != nullptr && hi > lo) cur[gt] = (uint8_t)hi;
-    levels[gt] = (uint8_t)(hi > lo ? hi : lo);
   }
   for (int c = 1; c <= 4; ++c) {
     const unsigned m = __ballot_sync(0xffffffffu, count == c);
@@ -152,6 +167,40 @@ plan_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ ga
       plan[(size_t)(c - 1) * n_ranges + base + __popc(m & ((1u << lane) - 1u))] =
           ((uint32_t)gt << 2) | (uint32_t)lo;
   }
+}
+
+// Work plan of one 32-pixel-tile composite launch (composite_px_kernel).  A tile rendering
+// the P = hi - lo labels (lo, hi] is two work items, its top and bottom halves; a tile with
+// no instances is one item that only writes background.  Items go into kItemClasses classes by the tile's
+// instance count (class 0: none; class c: 4^(c-1) <= count < 4^c; the last class unbounded)
+// and the composite takes the heaviest class first, so the longest items start first and
+// the short ones fill in behind them.  items[c * 4 * n_ranges + slot] = gt << 6 |
+// (P - 1) << 4 | region << 2 | lo, class sizes in class_counts[0..kItemClasses).
+constexpr int kItemClasses = 8;
+
+__global__ void __launch_bounds__(256)
+plan32_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ gaze_ring,
+              const RoundPlan *__restrict__ round, int uniform, uint8_t *__restrict__ cur,
+              uint8_t *__restrict__ levels, uint32_t *__restrict__ items,
+              uint32_t *__restrict__ class_counts, const uint2 *__restrict__ ranges,
+              const uint32_t *__restrict__ thresholds) {
+  const CompositeParams &p = *pp;
+  const float *gaze = gaze_ring + 4 * p.gaze_slot;
+  const int n_ranges = p.n_eyes * p.n_tiles;
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt >= n_ranges) return;
+  int lo, hi;
+  tile_interval(p, gt, gaze, round, uniform, cur, levels, ranges, thresholds, &lo, &hi);
+  if (hi <= lo) return;
+  const int P = hi - lo;
+  const uint2 r = ranges[gt];
+  const uint32_t count = r.y > r.x ? r.y - r.x : 0u;
+  const int n_items = count == 0u ? 1 : 2;
+  const int cls = count == 0u ? 0 : min(kItemClasses - 1, 1 + (31 - __clz(count)) / 2);
+  const uint32_t slot = atomicAdd(class_counts + cls, (uint32_t)n_items);
+  uint32_t *dst = items + (size_t)cls * 4 * n_ranges + slot;
+  for (int k = 0; k < n_items; ++k)
+    dst[k] = ((uint32_t)gt << 6) | ((uint32_t)(P - 1) << 4) | ((uint32_t)k << 2) | (uint32_t)lo;
 }
 
 // Conservative box of the pixels where a Gaussian can reach alpha >= 1/255: the ellipse
@@ -457,66 +506,64 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
 
 
 // 32 x 32 tiles (the paper's tiling, Sec. 3.5): a tile is 16 x 16 blocks of 2 x 2 pixels and
-// a level-k tile renders the k labels (lo, lo + k] of every block and no others.  One
-// 256-thread CTA renders all the labels a tile needs: launch P (1..4) takes the plan's bucket
-// of tiles with P labels to render, and each lane renders those P pixels of its block, so a
-// tile's Gaussian list is staged once whatever its level and each staged Gaussian is set up
-// once for the lane's P pixels (the per-pixel arithmetic is the same as with one pixel).  A
-// warp covers an 8 x 4 patch of blocks (a 16 x 8 pixel area), which many of the tile's
-// Gaussians cannot reach: each staged Gaussian carries the box where its alpha can reach
-// 1/255, and after staging every warp builds its hit list (box test, then the exact falloff
-// over the patch) -- a Gaussian left out fails the 1/255 test at every pixel of the patch, so
-// the image is unchanged.  A tile rendered from label 0 also writes the inherited pixels of
-// its blocks (the labels above its level take the top-left value).
-template <bool kAux, bool kFull, int kMult, int P>
-__global__ void __launch_bounds__(kThreads, (P == 1 ? 6 : (P == 2 ? 5 : (P == 3 ? 4 : 3))))
-composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
-                   const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
-                   const uint32_t *__restrict__ vals, const uint32_t *__restrict__ plan,
-                   const uint32_t *__restrict__ plan_counts, int incremental,
-                   uint8_t *__restrict__ levels, float *__restrict__ t_final,
-                   uint32_t *__restrict__ n_contrib, float *__restrict__ depth,
-                   unsigned long long *__restrict__ counters) {
+// a tile of labels (lo, hi] renders those P = hi - lo labels of every block and no others (the
+// paper's groups above the level exit; here their pixels are never assigned).  Work items are
+// half tiles (16 x 8 blocks): one persistent launch renders every item of the plan
+// (plan32_kernel) -- both eyes, every layer -- taking items heaviest class first from an
+// atomic counter, so the longest lists start first and the short ones fill in behind them,
+// and a heavy tile is rendered by two CTAs at once.  A 128-thread CTA renders one item: each
+// lane the P pixels of one block, so a staged Gaussian is set up once for the lane's P
+// pixels; each warp covers 8 x 4 blocks (a 16 x 8 pixel area).  Per batch the CTA stages the
+// tile's next Gaussians in shared memory with the box where each can reach alpha = 1/255;
+// every warp builds its hit list (box test, then the exact falloff over its patch: a
+// Gaussian left out has alpha < 1/255 at every pixel of the patch, so no output bit changes)
+// and blends only those, front to back, with the 1/255 skip, the 0.99 clamp and the 1e-4
+// stop.  The per-pixel arithmetic is the same as everywhere else, so images do not depend on
+// how tiles are cut into items.  A tile rendered from label 0 also writes its inherited
+// pixels (the labels above hi take the top-left value).
+constexpr int kHalfThreads = 128;
+constexpr int kBatch = 256;   // Gaussians staged per batch (times the staging multiple)
+
+__device__ __forceinline__ int label_dx(int L) { return (L == 1 || L == 2) ? 1 : 0; }
+__device__ __forceinline__ int label_dy(int L) { return (L == 1 || L == 3) ? 1 : 0; }
+
+struct HalfSmem {
+  float4 geo[kBatch * 2];
+  float2 cz[kBatch * 2];
+  float4 rgb[kBatch * 2];
+  short4 box[kBatch * 2];            // support box, outward-rounded pixels
+  float thr[kBatch * 2];             // log2 falloff needed for alpha = 1/255
+  uint16_t hits[kHalfThreads / 32][kBatch * 2];   // per warp: batch slots that reach its patch
+  int done[kHalfThreads / 32];
+  uint32_t prefix[kItemClasses + 1];  // item index ranges, heaviest class first
+  uint32_t item;
+};
+
+// One item: labels lo .. lo + P - 1 of the blocks of half `half` of tile gtile.
+template <int P, bool kAux, int kMult>
+__device__ __forceinline__ void render_half(HalfSmem &sm, const CompositeParams &p, const float *rec,
+                                            int n, uint2 range, int gtile, int half, int lo,
+                                            bool inherit, const uint32_t *vals, float *t_final,
+                                            uint32_t *n_contrib, float *depth,
+                                            unsigned long long &ev, unsigned long long &bl,
+                                            unsigned long long &staged) {
   constexpr int T32 = 32;
-  constexpr int NB = kThreads * kMult;
-  const CompositeParams &p = *pp;
+  constexpr int NB = kBatch * kMult;
   float *out = p.out;
-  __shared__ float4 s_geo[NB];
-  __shared__ float2 s_cz[NB];
-  __shared__ float4 s_rgb[NB];
-  __shared__ short4 s_box[NB];                     // support box, outward-rounded pixels
-  __shared__ float s_thr[NB];                      // log2 falloff needed for alpha = 1/255
-  __shared__ uint16_t s_hits[kThreads / 32][NB];   // per warp: batch slots that reach its patch
-  __shared__ int s_done[kThreads / 32];
   const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-  const int n_ranges = p.n_eyes * p.n_tiles;
-  int gtile, lo = 0, level = 4;
-  if (kFull) {
-    gtile = blockIdx.x;
-    if (gtile >= n_ranges) return;
-    if (t == 0) levels[gtile] = 4;
-  } else {
-    if (blockIdx.x >= plan_counts[P - 1]) return;
-    const uint32_t entry = plan[(size_t)(P - 1) * n_ranges + blockIdx.x];
-    gtile = (int)(entry >> 2);
-    lo = (int)(entry & 3u);
-    level = lo + P;
-  }
+  const int hi = lo + P;
   const int eye = gtile / p.n_tiles;
   const int tile = gtile - eye * p.n_tiles;
   const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
-  // warp w covers an 8 x 4 patch of blocks (column half w & 1, row quarter w >> 1): a squarer
-  // footprint than a strip, so fewer Gaussian boxes reach it
-  const int bx = (lane & 7) + 8 * (warp & 1), by = (lane >> 3) + 4 * (warp >> 1);
+  const int bx = (lane & 7) + 8 * (warp & 1), by = 8 * half + 4 * (warp >> 1) + (lane >> 3);
   const int px0 = tx * T32 + 2 * bx, py0 = ty * T32 + 2 * by;   // the block's top-left pixel
-  // the lane's pixels: labels lo .. lo + P - 1 of its block (TL, BR, TR, BL)
   float fpx[P], fpy[P];
   bool inside[P];
   int any_ox = 0, all_ox = 1, any_oy = 0, all_oy = 1;
 #pragma unroll
   for (int k = 0; k < P; ++k) {
     const int L = lo + k;
-    const int ox = (L == 1 || L == 2) ? 1 : 0, oy = (L == 1 || L == 3) ? 1 : 0;
+    const int ox = label_dx(L), oy = label_dy(L);
     any_ox |= ox;
     all_ox &= ox;
     any_oy |= oy;
@@ -526,18 +573,13 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
     fpy[k] = (float)(py0 + oy);
   }
   // the warp's patch: the span of its pixels (one label: every other pixel of 16 x 8)
-  const float wx0 = (float)(tx * T32 + 16 * (warp & 1) + all_ox), wx1 = (float)(tx * T32 + 16 * (warp & 1) + 14 + any_ox);
-  const float wy0 = (float)(ty * T32 + 8 * (warp >> 1) + all_oy), wy1 = (float)(ty * T32 + 8 * (warp >> 1) + 6 + any_oy);
-
-  uint2 range = ranges[gtile];
-  const uint32_t n_kept = *kept;
-  range.x = min(range.x, n_kept);
-  range.y = min(range.y, n_kept);
+  const int wxb = tx * T32 + 16 * (warp & 1), wyb = ty * T32 + 16 * half + 8 * (warp >> 1);
+  const float wx0 = (float)(wxb + all_ox), wx1 = (float)(wxb + 14 + any_ox);
+  const float wy0 = (float)(wyb + all_oy), wy1 = (float)(wyb + 6 + any_oy);
   const float *rec_eye = rec + (size_t)eye * n * kRec;
 
   float T[P], C0[P], C1[P], C2[P], Z[P];
   uint32_t last[P], stop[P];
-  uint32_t blended = 0;   // Gaussians blended into the lane's pixels (auxiliary mode)
   bool done[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) {
@@ -552,35 +594,28 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
     for (int k = 0; k < P; ++k) a = a && done[k];
     return a;
   };
-  uint32_t staged = 0;
   for (uint32_t start = range.x; start < range.y; start += NB) {
     const bool wdone = __all_sync(0xffffffffu, all_done());
-    if (lane == 0) s_done[warp] = wdone;
+    if (lane == 0) sm.done[warp] = wdone;
     __syncthreads();
     bool all = true;
 #pragma unroll
-    for (int w = 0; w < kThreads / 32; ++w) all = all && s_done[w];
+    for (int w = 0; w < kHalfThreads / 32; ++w) all = all && sm.done[w];
     if (all) break;
     const uint32_t cnt = min((uint32_t)NB, range.y - start);
-    staged += cnt;
+    if (t == 0) staged += cnt;
 #pragma unroll
-    for (int j = 0; j < kMult; ++j) {
-      const uint32_t slot = (uint32_t)(t + j * kThreads);
+    for (int j = 0; j < NB / kHalfThreads; ++j) {
+      const uint32_t slot = (uint32_t)(t + j * kHalfThreads);
       if (slot < cnt) {
-        const uint32_t gidx = min(vals[start + slot], (uint32_t)(n - 1));
+        const uint32_t gidx = min(vals[start + slot], (uint32_t)(n - 1));   // in range unless a sort failed
         const float4 *r4 = reinterpret_cast<const float4 *>(rec_eye + (size_t)gidx * kRec);
         const float4 a = __ldg(r4), b = __ldg(r4 + 1), c = __ldg(r4 + 2);
-        s_geo[slot] = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
-        s_cz[slot] = make_float2(__fmul_rn(-0.5f * kLog2e, b.x), c.y);
-        s_rgb[slot] = make_float4(b.z, b.w, c.x, b.y);
-        s_box[slot] = int_box(support_box(a.x, a.y, a.z, a.w, b.x, b.y));
-        s_thr[slot] = -__log2f(255.0f * b.y) - 0.01f;
-      } else if (slot < ((cnt + 3u) & ~3u)) {
-        s_geo[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        s_cz[slot] = make_float2(0.0f, 0.0f);
-        s_rgb[slot] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-        s_box[slot] = make_short4(kBoxFar, -kBoxFar, kBoxFar, -kBoxFar);
-        s_thr[slot] = 1.0f;
+        sm.geo[slot] = make_float4(a.x, a.y, __fmul_rn(-0.5f * kLog2e, a.z), __fmul_rn(-kLog2e, a.w));
+        sm.cz[slot] = make_float2(__fmul_rn(-0.5f * kLog2e, b.x), c.y);
+        sm.rgb[slot] = make_float4(b.z, b.w, c.x, b.y);
+        sm.box[slot] = int_box(support_box(a.x, a.y, a.z, a.w, b.x, b.y));
+        sm.thr[slot] = -__log2f(255.0f * b.y) - 0.01f;
       }
     }
     __syncthreads();
@@ -592,16 +627,14 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
         const uint32_t k = base + (uint32_t)lane;
         bool hit = false;
         if (k < cnt) {
-          const short4 box = s_box[k];
+          const short4 box = sm.box[k];
           hit = !((float)box.y < wx0 || (float)box.x > wx1 || (float)box.w < wy0 || (float)box.z > wy1);
         }
         const unsigned m = __ballot_sync(0xffffffffu, hit);
-        if (hit) s_hits[warp][n_hit + __popc(m & ((1u << lane) - 1u))] = (uint16_t)k;
+        if (hit) sm.hits[warp][n_hit + __popc(m & ((1u << lane) - 1u))] = (uint16_t)k;
         n_hit += __popc(m);
       }
       __syncwarp();
-      // second pass over the box hits, 32 at a time with full warps: keep those whose
-      // falloff reaches the threshold on the patch (compacted in place, list order kept)
       {
         int n_keep = 0;
         for (int base = 0; base < n_hit; base += 32) {
@@ -609,14 +642,14 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
           int k = 0;
           bool keep = false;
           if (i < n_hit) {
-            k = s_hits[warp][i];
-            const float4 geo = s_geo[k];
-            keep = falloff_reaches(geo.z, geo.w, s_cz[k].x, s_thr[k], wx0 - geo.x, wx1 - geo.x,
+            k = sm.hits[warp][i];
+            const float4 geo = sm.geo[k];
+            keep = falloff_reaches(geo.z, geo.w, sm.cz[k].x, sm.thr[k], wx0 - geo.x, wx1 - geo.x,
                                    wy0 - geo.y, wy1 - geo.y);
           }
           __syncwarp();
           const unsigned m = __ballot_sync(0xffffffffu, keep);
-          if (keep) s_hits[warp][n_keep + __popc(m & ((1u << lane) - 1u))] = (uint16_t)k;
+          if (keep) sm.hits[warp][n_keep + __popc(m & ((1u << lane) - 1u))] = (uint16_t)k;
           n_keep += __popc(m);
         }
         n_hit = n_keep;
@@ -627,10 +660,10 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
           if (i + j >= n_hit) break;
-          const int e = s_hits[warp][i + j];
-          const float4 geo = s_geo[e];
-          const float2 cz = s_cz[e];
-          const float4 rgb = s_rgb[e];
+          const int e = sm.hits[warp][i + j];
+          const float4 geo = sm.geo[e];
+          const float2 cz = sm.cz[e];
+          const float4 rgb = sm.rgb[e];
           const uint32_t pos = pos0 + (uint32_t)e;
 #pragma unroll
           for (int k = 0; k < P; ++k) {
@@ -647,7 +680,7 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
             C2[k] += rgb.z * w;
             if (kAux) {
               Z[k] += cz.y * w;
-              blended += upd ? 1u : 0u;
+              bl += upd ? 1u : 0u;
             }
             T[k] = upd ? tt : T[k];
             last[k] = upd ? pos : last[k];
@@ -658,13 +691,12 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
         if (__all_sync(0xffffffffu, all_done())) break;
       }
     }
-    __syncthreads();
+    __syncthreads();   // the next batch overwrites the staged Gaussians
   }
-  unsigned long long ev = 0;
 #pragma unroll
   for (int k = 0; k < P; ++k) {
-    if (inside[k] && !done[k]) stop[k] = range.y - range.x;
     if (!inside[k]) continue;
+    if (!done[k]) stop[k] = range.y - range.x;
     ev += stop[k];
     const size_t pix = ((size_t)eye * p.height + (size_t)fpy[k]) * p.width + (size_t)fpx[k];
     out[3 * pix] = C0[k];
@@ -676,25 +708,99 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
       depth[pix] = Z[k];
     }
   }
-  if (!kFull && !incremental && lo == 0 && level < 4 && inside[0]) {
+  if (inherit && inside[0]) {
     // the inherited pixels of the block: the labels above the level take the top-left value
-#pragma unroll
-    for (int L = 1; L < 4; ++L) {
-      if (L < level) continue;
-      const int dx = (L == 1 || L == 2) ? 1 : 0, dy = (L == 1 || L == 3) ? 1 : 0;
-      if (px0 + dx >= p.width || py0 + dy >= p.height) continue;
-      const size_t pix = ((size_t)eye * p.height + py0 + dy) * p.width + px0 + dx;
-      out[3 * pix] = C0[0];
-      out[3 * pix + 1] = C1[0];
-      out[3 * pix + 2] = C2[0];
+    for (int L = hi; L < 4; ++L) {
+      const int x = px0 + label_dx(L), y = py0 + label_dy(L);
+      if (x >= p.width || y >= p.height) continue;
+      const size_t q = ((size_t)eye * p.height + y) * p.width + x;
+      out[3 * q] = C0[0];
+      out[3 * q + 1] = C1[0];
+      out[3 * q + 2] = C2[0];
       if (kAux) {
-        t_final[pix] = T[0];
-        n_contrib[pix] = last[0];
-        depth[pix] = Z[0];
+        t_final[q] = T[0];
+        n_contrib[q] = last[0];
+        depth[q] = Z[0];
       }
     }
   }
-  unsigned long long bl = blended;
+}
+
+template <bool kAux, int kMult>
+__global__ void __launch_bounds__(kHalfThreads, 6)
+composite_px_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
+                    const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
+                    const uint32_t *__restrict__ vals, const uint32_t *__restrict__ items,
+                    const uint32_t *__restrict__ class_counts, uint32_t *__restrict__ work,
+                    int incremental, float *__restrict__ t_final,
+                    uint32_t *__restrict__ n_contrib, float *__restrict__ depth,
+                    unsigned long long *__restrict__ counters) {
+  __shared__ HalfSmem sm;
+  const CompositeParams &p = *pp;
+  float *out = p.out;
+  const int t = threadIdx.x, lane = t & 31;
+  const int n_ranges = p.n_eyes * p.n_tiles;
+  const size_t cap = 4 * (size_t)n_ranges;
+  if (t == 0) {
+    sm.prefix[0] = 0u;
+    for (int i = 0; i < kItemClasses; ++i)
+      sm.prefix[i + 1] = sm.prefix[i] + class_counts[kItemClasses - 1 - i];
+  }
+  __syncthreads();
+  const uint32_t total = sm.prefix[kItemClasses];
+  const uint32_t n_kept = *kept;   // fewer than the instances only after a capacity overflow
+  unsigned long long ev = 0, bl = 0, staged = 0;
+
+  for (;;) {
+    if (t == 0) sm.item = atomicAdd(work, 1u);
+    __syncthreads();
+    const uint32_t w = sm.item;
+    if (w >= total) break;
+    int ci = 0;
+    while (w >= sm.prefix[ci + 1]) ++ci;
+    const uint32_t item = items[(size_t)(kItemClasses - 1 - ci) * cap + (w - sm.prefix[ci])];
+    const int gtile = (int)(item >> 6);
+    const int P = (int)((item >> 4) & 3u) + 1;
+    const int half = (int)((item >> 2) & 3u);
+    const int lo = (int)(item & 3u), hi = lo + P;
+    uint2 range = ranges[gtile];
+    range.x = min(range.x, n_kept);
+    range.y = min(range.y, n_kept);
+    const bool inherit = !incremental && lo == 0 && hi < 4;
+    if (range.y <= range.x) {
+      // no Gaussian reaches the tile: background (0) for every pixel the tile's items would
+      // write (this is the tile's only item)
+      const int eye = gtile / p.n_tiles;
+      const int tile = gtile - eye * p.n_tiles;
+      const int tx = tile % p.tiles_x, ty = tile / p.tiles_x;
+      for (int b = t; b < 256; b += kHalfThreads) {
+        const int px0 = tx * 32 + 2 * (b & 15), py0 = ty * 32 + 2 * (b >> 4);
+        for (int L = lo; L < 4; ++L) {
+          if (L >= hi && !inherit) break;
+          const int x = px0 + label_dx(L), y = py0 + label_dy(L);
+          if (x >= p.width || y >= p.height) continue;
+          const size_t pix = ((size_t)eye * p.height + y) * p.width + x;
+          out[3 * pix] = 0.0f;
+          out[3 * pix + 1] = 0.0f;
+          out[3 * pix + 2] = 0.0f;
+          if (kAux) {
+            t_final[pix] = 1.0f;
+            n_contrib[pix] = 0u;
+            depth[pix] = 0.0f;
+          }
+        }
+      }
+    } else {
+      switch (P) {
+        case 1: render_half<1, kAux, kMult>(sm, p, rec, n, range, gtile, half, lo, inherit, vals, t_final, n_contrib, depth, ev, bl, staged); break;
+        case 2: render_half<2, kAux, kMult>(sm, p, rec, n, range, gtile, half, lo, inherit, vals, t_final, n_contrib, depth, ev, bl, staged); break;
+        case 3: render_half<3, kAux, kMult>(sm, p, rec, n, range, gtile, half, lo, inherit, vals, t_final, n_contrib, depth, ev, bl, staged); break;
+        default: render_half<4, kAux, kMult>(sm, p, rec, n, range, gtile, half, lo, inherit, vals, t_final, n_contrib, depth, ev, bl, staged); break;
+      }
+    }
+    __syncthreads();   // every thread has read sm.item and is done with the staging arrays
+  }
+  // statistics: evaluations, records staged (thread 0 counts its CTA's), blends (aux)
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) {
     ev += __shfl_xor_sync(0xffffffffu, ev, o);
@@ -702,9 +808,9 @@ composite32_kernel(const CompositeParams *__restrict__ pp, const float *__restri
   }
   if (lane == 0) {
     if (ev) atomicAdd(counters, ev);
-    if (t == 0 && staged) atomicAdd(counters + 1, (unsigned long long)staged);
     if (kAux && bl) atomicAdd(counters + 2, bl);
   }
+  if (t == 0 && staged) atomicAdd(counters + 1, staged);
 }
 
 
@@ -757,7 +863,12 @@ fill_kernel(const CompositeParams *__restrict__ pp, const uint8_t *__restrict__ 
 
 }  // namespace
 
-size_t plan_bytes(int n_ranges) { return sizeof(uint32_t) * (4 * (size_t)n_ranges + 4); }
+// The plan buffer: the 16-pixel path's buckets [4 * n_ranges] and counts [4] at its start,
+// the 32-pixel path's items [kItemClasses * 4 * n_ranges], then its class counts
+// [kItemClasses] and work counter.
+size_t plan_bytes(int n_ranges) {
+  return sizeof(uint32_t) * ((size_t)kItemClasses * 4 * (size_t)n_ranges + kItemClasses + 8);
+}
 
 cudaError_t launch_fill(const CompositeParams &p, const CompositeParams *p_dev, const uint8_t *levels,
                         cudaStream_t s) {
@@ -775,89 +886,91 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
                              int uniform, uint8_t *cur, uint32_t *plan, uint8_t *levels,
                              float *t_final, uint32_t *n_contrib, float *depth,
                              unsigned long long *counters, int batch_mult, uint32_t *thresholds,
-                             cudaStream_t s, const ForkStreams *fork) {
+                             cudaStream_t s, int *kernels) {
   const int n_ranges = p.n_eyes * p.n_tiles;
+  if (kernels) *kernels = 0;
   if (n_ranges <= 0) return cudaSuccess;
+  const int inc = round != nullptr ? 1 : 0;
+  const bool aux = t_final != nullptr;
+  const int mult = batch_mult == 2 ? 2 : 1;
+  const bool by_count = !p.full && p.count_frac > 0.0f && round == nullptr && uniform == 0;
+  // shared memory preferred so that registers, not the carveout, set residency
+  auto prefer_smem = [](auto kern, int variant) {
+    static bool carve[64][16] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && variant >= 0 && variant < 16 &&
+        !carve[dev][variant]) {
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                           cudaSharedmemCarveoutMaxShared);
+      carve[dev][variant] = true;
+    }
+  };
+  if (by_count) {
+    tile_threshold_kernel<<<1, 1024, 0, s>>>(p_dev, ranges, thresholds);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (kernels) ++*kernels;
+  }
+  if (p.tile == 32) {
+    // plan (every tile, also for the full render: uniform level 4) + one persistent composite
+    uint32_t *items = plan;
+    uint32_t *class_counts = plan + (size_t)kItemClasses * 4 * n_ranges;
+    uint32_t *work = class_counts + kItemClasses;
+    cudaError_t e = cudaMemsetAsync(class_counts, 0, sizeof(uint32_t) * (kItemClasses + 1), s);
+    if (e != cudaSuccess) return e;
+    plan32_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p_dev, gaze, round, p.full ? 4 : uniform,
+                                                         cur, levels, items, class_counts, ranges,
+                                                         thresholds);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    auto go = [&](auto kern, int variant) -> cudaError_t {
+      prefer_smem(kern, variant);
+      static int per_sm[64][16] = {};
+      int dev = 0;
+      cudaGetDevice(&dev);
+      int occ = (dev >= 0 && dev < 64) ? per_sm[dev][variant] : 0;
+      int sms = 0;
+      if (occ == 0) {
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kHalfThreads, 0) != cudaSuccess || occ < 1)
+          occ = 1;
+        if (dev >= 0 && dev < 64) per_sm[dev][variant] = occ;
+      }
+      if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
+        sms = 1;
+      const long max_items = 2L * n_ranges;
+      const int grid = (int)std::min<long>((long)sms * occ, max_items);
+      kern<<<grid, kHalfThreads, 0, s>>>(p_dev, rec, n, ranges, kept, vals, items, class_counts, work,
+                                     inc, t_final, n_contrib, depth, counters);
+      return cudaGetLastError();
+    };
+    e = aux ? (mult == 2 ? go(composite_px_kernel<true, 2>, 0) : go(composite_px_kernel<true, 1>, 1))
+            : (mult == 2 ? go(composite_px_kernel<false, 2>, 2) : go(composite_px_kernel<false, 1>, 3));
+    if (kernels) *kernels += 2;
+    return e;
+  }
   uint32_t *pc = plan + 4 * (size_t)n_ranges;
   if (!p.full) {
     cudaError_t e = cudaMemsetAsync(pc, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    const bool by_count = p.count_frac > 0.0f && round == nullptr && uniform == 0;
-    if (by_count) {
-      tile_threshold_kernel<<<1, 1024, 0, s>>>(p_dev, ranges, thresholds);
-      e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-    }
     plan_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p_dev, gaze, round, uniform, cur, levels,
                                                        plan, pc, ranges, thresholds);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
+    if (kernels) ++*kernels;
   }
-  const int inc = round != nullptr ? 1 : 0;
-  const bool aux = t_final != nullptr;
-  const int mult = batch_mult == 2 ? 2 : 1;
-  // one composite kernel per (tile, aux, full, batch[, labels]) combination; shared memory
-  // preferred so that registers, not the carveout, set residency
-  auto launch_on = [&](cudaStream_t st, auto kern, int grid, int variant) -> cudaError_t {
-    static bool carve[64][128] = {};
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && dev >= 0 && dev < 64 && variant >= 0 && variant < 128) {
-      if (!carve[dev][variant]) {
-        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
-                             cudaSharedmemCarveoutMaxShared);
-        carve[dev][variant] = true;
-      }
-    }
-    kern<<<grid, kThreads, 0, st>>>(p_dev, rec, n, ranges, kept, vals, plan, pc, p.full ? 0 : inc, levels,
-                                    t_final, n_contrib, depth, counters);
+  auto launch = [&](auto kern, int variant) -> cudaError_t {
+    prefer_smem(kern, 4 + variant);
+    kern<<<n_ranges, kThreads, 0, s>>>(p_dev, rec, n, ranges, kept, vals, plan, pc, p.full ? 0 : inc,
+                                      levels, t_final, n_contrib, depth, counters);
+    if (kernels) ++*kernels;
     return cudaGetLastError();
   };
-  auto launch = [&](auto kern, int grid, int variant) { return launch_on(s, kern, grid, variant); };
-  const int var = (aux ? 64 : 0) + (p.full ? 32 : 0) + (mult == 2 ? 16 : 0);
-  if (p.tile == 32) {
-    // one launch per label count (the full render: every tile renders all four labels)
-#define A3FR_C32(AUX, FULL, MULT, P) launch(composite32_kernel<AUX, FULL, MULT, P>, n_ranges, var + 4 + P)
-#define A3FR_C32_ON(ST, AUX, MULT, P) \
-  launch_on(ST, composite32_kernel<AUX, false, MULT, P>, n_ranges, var + 4 + P)
-#define A3FR_C32_FOV(AUX, MULT)                                                  \
-  {                                                                              \
-    cudaError_t e2 = cudaSuccess;                                                \
-    if (fork) {                                                                  \
-      e2 = cudaEventRecord(fork->fork, s);                                       \
-      for (int f = 0; f < 3 && e2 == cudaSuccess; ++f)                           \
-        e2 = cudaStreamWaitEvent(fork->aux[f], fork->fork, 0);                   \
-    }                                                                            \
-    if (e2 == cudaSuccess) e2 = A3FR_C32_ON(s, AUX, MULT, 4);                    \
-    if (e2 == cudaSuccess) e2 = A3FR_C32_ON(fork ? fork->aux[0] : s, AUX, MULT, 2); \
-    if (e2 == cudaSuccess) e2 = A3FR_C32_ON(fork ? fork->aux[1] : s, AUX, MULT, 1); \
-    if (e2 == cudaSuccess) e2 = A3FR_C32_ON(fork ? fork->aux[2] : s, AUX, MULT, 3); \
-    if (fork) {                                                                  \
-      for (int f = 0; f < 3 && e2 == cudaSuccess; ++f) {                         \
-        e2 = cudaEventRecord(fork->join[f], fork->aux[f]);                       \
-        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, fork->join[f], 0);    \
-      }                                                                          \
-    }                                                                            \
-    return e2;                                                                   \
-  }
-    if (p.full) {
-      if (aux) return mult == 2 ? A3FR_C32(true, true, 2, 4) : A3FR_C32(true, true, 1, 4);
-      return mult == 2 ? A3FR_C32(false, true, 2, 4) : A3FR_C32(false, true, 1, 4);
-    }
-    if (aux) {
-      if (mult == 2) A3FR_C32_FOV(true, 2) else A3FR_C32_FOV(true, 1)
-    }
-    if (mult == 2) A3FR_C32_FOV(false, 2) else A3FR_C32_FOV(false, 1)
-#undef A3FR_C32_FOV
-#undef A3FR_C32_ON
-#undef A3FR_C32
-  }
-  const int g16 = n_ranges;
   if (aux) {
-    if (p.full) return mult == 2 ? launch(composite_kernel<true, true, 2>, g16, var) : launch(composite_kernel<true, true, 1>, g16, var);
-    return mult == 2 ? launch(composite_kernel<true, false, 2>, g16, var) : launch(composite_kernel<true, false, 1>, g16, var);
+    if (p.full) return mult == 2 ? launch(composite_kernel<true, true, 2>, 0) : launch(composite_kernel<true, true, 1>, 1);
+    return mult == 2 ? launch(composite_kernel<true, false, 2>, 2) : launch(composite_kernel<true, false, 1>, 3);
   }
-  if (p.full) return mult == 2 ? launch(composite_kernel<false, true, 2>, g16, var) : launch(composite_kernel<false, true, 1>, g16, var);
-  return mult == 2 ? launch(composite_kernel<false, false, 2>, g16, var) : launch(composite_kernel<false, false, 1>, g16, var);
+  if (p.full) return mult == 2 ? launch(composite_kernel<false, true, 2>, 4) : launch(composite_kernel<false, true, 1>, 5);
+  return mult == 2 ? launch(composite_kernel<false, false, 2>, 6) : launch(composite_kernel<false, false, 1>, 7);
 }
 
 }  // namespace a3fr

@@ -256,7 +256,7 @@ def test_stereo_3m_clustered_full_size(tile):
 def test_graph_mode_matches_direct_launches_bitwise(tile):
     """Replayed CUDA graphs see each render's cameras, gaze and output through device-resident
     parameters, so they must reproduce the directly launched renders exactly (with 32-pixel
-    tiles the foveated composite's launches are parallel branches of the graph)."""
+    tiles the composite is one persistent launch taking work items from a device counter)."""
     import torch
     w = synth.stereo_500k(frames=240)
     scene_np = w.scene.subset(np.arange(60000))
