@@ -99,7 +99,10 @@ typedef struct {
   int64_t instances;            /* tile-Gaussian pairs of the last render (all eyes) */
   int64_t instances_eye[2];     /* the same per eye */
   int64_t capacity;             /* instance capacity of the scene */
-  uint64_t evaluations;         /* (pixel, Gaussian) evaluations since the last reset */
+  uint64_t evaluations;         /* (pixel, Gaussian) evaluations since the last reset: each
+                                   rendered pixel's position in its tile's list where it
+                                   stopped (or the list length); counted by renders with
+                                   keep_aux on only (0 otherwise) */
   uint64_t records_staged;      /* Gaussian records staged by tile blocks since the reset */
   uint64_t renders;             /* renders since the last reset */
   uint64_t kernel_launches;     /* kernels this library launched since the last reset */

@@ -498,7 +498,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
     if (kAux) bl += __shfl_xor_sync(0xffffffffu, bl, o);
   }
   if (lane == 0) {
-    if (ev) atomicAdd(counters, ev);
+    if (kAux && ev) atomicAdd(counters, ev);
     if (gt == 0 && staged) atomicAdd(counters + 1, (unsigned long long)staged);
     if (kAux && bl) atomicAdd(counters + 2, bl);
   }
@@ -527,21 +527,27 @@ constexpr int kBatch = 256;   // Gaussians staged per batch (times the staging m
 __device__ __forceinline__ int label_dx(int L) { return (L == 1 || L == 2) ? 1 : 0; }
 __device__ __forceinline__ int label_dy(int L) { return (L == 1 || L == 3) ? 1 : 0; }
 
+template <int kMult>
 struct HalfSmem {
-  float4 geo[kBatch * 2];
-  float2 cz[kBatch * 2];
-  float4 rgb[kBatch * 2];
-  short4 box[kBatch * 2];            // support box, outward-rounded pixels
-  float thr[kBatch * 2];             // log2 falloff needed for alpha = 1/255
-  uint16_t hits[kHalfThreads / 32][kBatch * 2];   // per warp: batch slots that reach its patch
+  float4 geo[kBatch * kMult];
+  float2 cz[kBatch * kMult];
+  float4 rgb[kBatch * kMult];
+  short4 box[kBatch * kMult];        // support box, outward-rounded pixels
+  float thr[kBatch * kMult];         // log2 falloff needed for alpha = 1/255
+  uint16_t hits[kHalfThreads / 32][kBatch * kMult];   // per warp: batch slots that reach its patch
   int done[kHalfThreads / 32];
   uint32_t prefix[kItemClasses + 1];  // item index ranges, heaviest class first
   uint32_t item;
 };
 
-// One item: labels lo .. lo + P - 1 of the blocks of half `half` of tile gtile.
-template <int P, bool kAux, int kMult>
-__device__ __forceinline__ void render_half(HalfSmem &sm, const CompositeParams &p, const float *rec,
+// One item: labels lo .. lo + P - 1 of the blocks of half `half` of tile gtile (kLo0: lo is
+// 0, so the lane's pixel offsets are known at compile time).  Without the auxiliary outputs
+// a finished pixel is marked by T = 0 (a live pixel keeps T >= 1e-4): skipped Gaussians then
+// blend with alpha 0, which leaves T and the colour bit for bit as they were, and every
+// later Gaussian of a finished pixel stops with weight 0.  With them the loop also keeps the
+// final transmittance, the last contributor and the evaluation and blend counts.
+template <int P, bool kAux, int kMult, bool kLo0>
+__device__ __forceinline__ void render_half(HalfSmem<kMult> &sm, const CompositeParams &p, const float *rec,
                                             int n, uint2 range, int gtile, int half, int lo,
                                             bool inherit, const uint32_t *vals, float *t_final,
                                             uint32_t *n_contrib, float *depth,
@@ -562,7 +568,7 @@ __device__ __forceinline__ void render_half(HalfSmem &sm, const CompositeParams 
   int any_ox = 0, all_ox = 1, any_oy = 0, all_oy = 1;
 #pragma unroll
   for (int k = 0; k < P; ++k) {
-    const int L = lo + k;
+    const int L = kLo0 ? k : lo + k;
     const int ox = label_dx(L), oy = label_dy(L);
     any_ox |= ox;
     all_ox &= ox;
@@ -583,7 +589,7 @@ __device__ __forceinline__ void render_half(HalfSmem &sm, const CompositeParams 
   bool done[P];
 #pragma unroll
   for (int k = 0; k < P; ++k) {
-    T[k] = 1.0f;
+    T[k] = kAux || inside[k] ? 1.0f : 0.0f;
     C0[k] = C1[k] = C2[k] = Z[k] = 0.0f;
     last[k] = stop[k] = 0u;
     done[k] = !inside[k];
@@ -591,7 +597,7 @@ __device__ __forceinline__ void render_half(HalfSmem &sm, const CompositeParams 
   auto all_done = [&]() {
     bool a = true;
 #pragma unroll
-    for (int k = 0; k < P; ++k) a = a && done[k];
+    for (int k = 0; k < P; ++k) a = a && (kAux ? done[k] : T[k] == 0.0f);
     return a;
   };
   for (uint32_t start = range.x; start < range.y; start += NB) {
@@ -670,22 +676,31 @@ __device__ __forceinline__ void render_half(HalfSmem &sm, const CompositeParams 
             const float dx = __fsub_rn(geo.x, fpx[k]), dy = __fsub_rn(geo.y, fpy[k]);
             const float pw = falloff_log2(geo.z, geo.w, cz.x, dx, dy);
             const float alpha = blend_alpha(rgb.w, pw);
-            const float tt = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
-            const bool ok = !done[k] && pw <= 0.0f && alpha >= 1.0f / 255.0f;
-            const bool fin = ok && tt < 0.0001f;
-            const bool upd = ok && !fin;
-            const float w = upd ? alpha * T[k] : 0.0f;
-            C0[k] += rgb.x * w;
-            C1[k] += rgb.y * w;
-            C2[k] += rgb.z * w;
-            if (kAux) {
+            if constexpr (kAux) {
+              const float tt = __fmul_rn(T[k], __fsub_rn(1.0f, alpha));
+              const bool ok = !done[k] && pw <= 0.0f && alpha >= 1.0f / 255.0f;
+              const bool fin = ok && tt < 0.0001f;
+              const bool upd = ok && !fin;
+              const float w = upd ? alpha * T[k] : 0.0f;
+              C0[k] += rgb.x * w;
+              C1[k] += rgb.y * w;
+              C2[k] += rgb.z * w;
               Z[k] += cz.y * w;
               bl += upd ? 1u : 0u;
+              T[k] = upd ? tt : T[k];
+              last[k] = upd ? pos : last[k];
+              stop[k] = fin ? pos : stop[k];
+              done[k] = done[k] || fin;
+            } else {
+              const float a = (pw <= 0.0f && alpha >= 1.0f / 255.0f) ? alpha : 0.0f;
+              const float tt = __fmul_rn(T[k], __fsub_rn(1.0f, a));
+              const bool fin = tt < 0.0001f;   // this Gaussian would end the pixel, or it ended
+              const float w = fin ? 0.0f : a * T[k];
+              C0[k] += rgb.x * w;
+              C1[k] += rgb.y * w;
+              C2[k] += rgb.z * w;
+              T[k] = fin ? 0.0f : tt;
             }
-            T[k] = upd ? tt : T[k];
-            last[k] = upd ? pos : last[k];
-            stop[k] = fin ? pos : stop[k];
-            done[k] = done[k] || fin;
           }
         }
         if (__all_sync(0xffffffffu, all_done())) break;
@@ -696,8 +711,10 @@ __device__ __forceinline__ void render_half(HalfSmem &sm, const CompositeParams 
 #pragma unroll
   for (int k = 0; k < P; ++k) {
     if (!inside[k]) continue;
-    if (!done[k]) stop[k] = range.y - range.x;
-    ev += stop[k];
+    if (kAux) {
+      if (!done[k]) stop[k] = range.y - range.x;
+      ev += stop[k];
+    }
     const size_t pix = ((size_t)eye * p.height + (size_t)fpy[k]) * p.width + (size_t)fpx[k];
     out[3 * pix] = C0[k];
     out[3 * pix + 1] = C1[k];
@@ -727,7 +744,7 @@ __device__ __forceinline__ void render_half(HalfSmem &sm, const CompositeParams 
 }
 
 template <bool kAux, int kMult>
-__global__ void __launch_bounds__(kHalfThreads, 6)
+__global__ void __launch_bounds__(kHalfThreads, kAux ? 6 : 8)
 composite_px_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
                     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
                     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ items,
@@ -735,7 +752,7 @@ composite_px_kernel(const CompositeParams *__restrict__ pp, const float *__restr
                     int incremental, float *__restrict__ t_final,
                     uint32_t *__restrict__ n_contrib, float *__restrict__ depth,
                     unsigned long long *__restrict__ counters) {
-  __shared__ HalfSmem sm;
+  __shared__ HalfSmem<kMult> sm;
   const CompositeParams &p = *pp;
   float *out = p.out;
   const int t = threadIdx.x, lane = t & 31;
@@ -791,24 +808,39 @@ composite_px_kernel(const CompositeParams *__restrict__ pp, const float *__restr
         }
       }
     } else {
-      switch (P) {
-        case 1: render_half<1, kAux, kMult>(sm, p, rec, n, range, gtile, half, lo, inherit, vals, t_final, n_contrib, depth, ev, bl, staged); break;
-        case 2: render_half<2, kAux, kMult>(sm, p, rec, n, range, gtile, half, lo, inherit, vals, t_final, n_contrib, depth, ev, bl, staged); break;
-        case 3: render_half<3, kAux, kMult>(sm, p, rec, n, range, gtile, half, lo, inherit, vals, t_final, n_contrib, depth, ev, bl, staged); break;
-        default: render_half<4, kAux, kMult>(sm, p, rec, n, range, gtile, half, lo, inherit, vals, t_final, n_contrib, depth, ev, bl, staged); break;
+#define A3FR_HALF(PP, LO0) \
+  render_half<PP, kAux, kMult, LO0>(sm, p, rec, n, range, gtile, half, lo, inherit, vals, t_final, \
+                                    n_contrib, depth, ev, bl, staged)
+      if (lo == 0) {
+        switch (P) {
+          case 1: A3FR_HALF(1, true); break;
+          case 2: A3FR_HALF(2, true); break;
+          case 3: A3FR_HALF(3, true); break;
+          default: A3FR_HALF(4, true); break;
+        }
+      } else {   // later rounds: labels above the ones already rendered (lo + P <= 4)
+        switch (P) {
+          case 1: A3FR_HALF(1, false); break;
+          case 2: A3FR_HALF(2, false); break;
+          default: A3FR_HALF(3, false); break;
+        }
       }
+#undef A3FR_HALF
     }
     __syncthreads();   // every thread has read sm.item and is done with the staging arrays
   }
-  // statistics: evaluations, records staged (thread 0 counts its CTA's), blends (aux)
+  // statistics: records staged (thread 0 counts its CTA's); with the auxiliary outputs also
+  // the evaluations and the blends
+  if (kAux) {
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    ev += __shfl_xor_sync(0xffffffffu, ev, o);
-    if (kAux) bl += __shfl_xor_sync(0xffffffffu, bl, o);
-  }
-  if (lane == 0) {
-    if (ev) atomicAdd(counters, ev);
-    if (kAux && bl) atomicAdd(counters + 2, bl);
+    for (int o = 16; o > 0; o >>= 1) {
+      ev += __shfl_xor_sync(0xffffffffu, ev, o);
+      bl += __shfl_xor_sync(0xffffffffu, bl, o);
+    }
+    if (lane == 0) {
+      if (ev) atomicAdd(counters, ev);
+      if (bl) atomicAdd(counters + 2, bl);
+    }
   }
   if (t == 0 && staged) atomicAdd(counters + 1, staged);
 }

@@ -180,6 +180,7 @@ def test_repeated_renders_are_deterministic_and_counters_accumulate():
     s = a3fr.Scene.from_numpy(w.scene)
     s.set_camera(0, cam)
     s.set_gaze([w.fixed_gaze_px])
+    s.keep_aux(True)   # evaluations and blends are counted with the auxiliary outputs
     a = s.render_foveated().clone()
     s.stats(reset=True)
     for _ in range(3):
@@ -188,6 +189,7 @@ def test_repeated_renders_are_deterministic_and_counters_accumulate():
     torch.cuda.synchronize()
     assert torch.equal(a, b)
     assert st["renders"] == 3 and st["evaluations"] > 0 and st["status"] == 0
+    assert 0 < st["contributions"] <= st["evaluations"]
 
 
 @pytest.mark.parametrize("tile,binning", [(16, a3fr.BINNING_SORTED), (32, a3fr.BINNING_DIRECT),
