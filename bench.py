@@ -725,7 +725,9 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
             inherit = out.clone()
             b2 = ev()
             b2.record(render_stream)
+            torch.cuda.nvtx.range_push("learned_fill")   # marks the fill's kernels for profilers
             net.fill(scene, out, stream=render_stream)
+            torch.cuda.nvtx.range_pop()
             c_.record(render_stream)
             levels = scene.buffer(a3fr.BUF_LEVELS, torch.uint8, stream=render_stream)
             i0, i1 = ev(), ev()
