@@ -26,6 +26,7 @@ namespace {
 constexpr int kTile = 16;
 constexpr int kThreads = 256;
 constexpr int kG2 = 9;   // per (eye, Gaussian): du dv dconic_a dconic_b dconic_c dopacity dr dg db
+constexpr int kPreBwdThreads = 128;
 
 __global__ void __launch_bounds__(kThreads)
 composite_backward_kernel(BackwardParams p, const float *__restrict__ rec, const uint2 *__restrict__ ranges,
@@ -265,8 +266,20 @@ __device__ __forceinline__ void sh_basis_vjp(const ShConsts &c, float x, float y
   }
 }
 
+// Shared-memory row stride (floats) of a block's SH coefficients and their gradients: the
+// 3K coefficients rounded up to an odd count, so the threads of a warp, reading the same
+// coefficient of consecutive rows, hit distinct banks.
+template <int K> constexpr int sh_stride() { return (3 * K) % 2 ? 3 * K : 3 * K + 1; }
+template <int K> constexpr size_t backward_smem_bytes() {
+  return 2 * sizeof(float) * (size_t)kPreBwdThreads * sh_stride<K>();
+}
+
+// One thread per Gaussian.  The block's SH coefficients are copied into shared memory with
+// coalesced loads and their gradients accumulated there, then written back coalesced (read
+// and accumulated per thread in global memory, the 48-float rows made every access a
+// separate sector).
 template <int K>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kPreBwdThreads)
 preprocess_backward_kernel(const PreParams *__restrict__ pp, int n, const float *__restrict__ means,
                            const float *__restrict__ log_scales, const float *__restrict__ quats,
                            const float *__restrict__ opacity_logits, const float *__restrict__ sh,
@@ -274,14 +287,29 @@ preprocess_backward_kernel(const PreParams *__restrict__ pp, int n, const float 
                            float *__restrict__ d_means, float *__restrict__ d_log_scales,
                            float *__restrict__ d_quats, float *__restrict__ d_logits,
                            float *__restrict__ d_sh) {
+  constexpr int SS = sh_stride<K>();
+  constexpr int ROW = 3 * K;
   __shared__ PreParams s_p;
-  static_assert(sizeof(PreParams) % 4 == 0 && sizeof(PreParams) / 4 <= 128, "PreParams copy");
+  extern __shared__ float s_sh_dyn[];
+  float *s_coef = s_sh_dyn;                          // [kPreBwdThreads][SS]
+  float *s_dsh = s_sh_dyn + kPreBwdThreads * SS;     // [kPreBwdThreads][SS]
+  static_assert(sizeof(PreParams) % 4 == 0 && sizeof(PreParams) / 4 <= kPreBwdThreads, "PreParams copy");
   if (threadIdx.x < sizeof(PreParams) / 4)
     reinterpret_cast<uint32_t *>(&s_p)[threadIdx.x] = reinterpret_cast<const uint32_t *>(pp)[threadIdx.x];
+  const int i0 = blockIdx.x * kPreBwdThreads;
+  const int rows = min(kPreBwdThreads, n - i0);
+  {
+    const float *src = sh + (size_t)ROW * i0;
+    for (int f = threadIdx.x; f < rows * ROW; f += kPreBwdThreads) {
+      const int r = f / ROW, c = f - r * ROW;
+      s_coef[r * SS + c] = src[f];
+      s_dsh[r * SS + c] = 0.0f;
+    }
+  }
   __syncthreads();
   const PreParams &p = s_p;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
+  const int i = i0 + threadIdx.x;
+  if (i < n) {
 
   const float mx = means[3 * i], my = means[3 * i + 1], mz = means[3 * i + 2];
   float s2[3];
@@ -310,13 +338,12 @@ preprocess_backward_kernel(const PreParams *__restrict__ pp, int n, const float 
     for (int k = 0; k < 3; ++k)
       S[j][k] = R[j][0] * s2[0] * R[k][0] + R[j][1] * s2[1] * R[k][1] + R[j][2] * s2[2] * R[k][2];
   const float opacity = 1.0f / (1.0f + expf(-opacity_logits[i]));
-  const float *coef = sh + (size_t)3 * K * i;
+  const float *coef = s_coef + threadIdx.x * SS;
 
   float dmu[3] = {0.f, 0.f, 0.f};
   float dS[3][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   float dlogit = 0.0f;
-  float *dsh = d_sh + (size_t)3 * K * i;
-  for (int k = 0; k < 3 * K; ++k) dsh[k] = 0.0f;
+  float *dsh = s_dsh + threadIdx.x * SS;
 
   for (int e = 0; e < p.n_eyes; ++e) {
     if (rec[((size_t)e * n + i) * kRec + 11] == 0.0f) continue;   // culled for this eye
@@ -471,6 +498,13 @@ preprocess_backward_kernel(const PreParams *__restrict__ pp, int n, const float 
   d_means[3 * i + 1] = dmu[1];
   d_means[3 * i + 2] = dmu[2];
   d_logits[i] = dlogit;
+  }
+  __syncthreads();
+  float *dst = d_sh + (size_t)ROW * i0;
+  for (int f = threadIdx.x; f < rows * ROW; f += kPreBwdThreads) {
+    const int r = f / ROW, c = f - r * ROW;
+    dst[f] = s_dsh[r * SS + c];
+  }
 }
 
 }  // namespace
@@ -492,30 +526,22 @@ cudaError_t launch_backward(const BackwardParams &bp, const PreParams *pre_dev, 
       bp, rec, ranges, kept, vals, levels, t_final, n_contrib, dl_drgb, g2d);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int blocks = (bp.n + 127) / 128;
+  const int blocks = (bp.n + kPreBwdThreads - 1) / kPreBwdThreads;
+  auto go = [&](auto kern, size_t smem) -> cudaError_t {
+    // per device: the attribute lives in each device's context
+    cudaError_t e2 = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e2 != cudaSuccess) return e2;
+    kern<<<blocks, kPreBwdThreads, smem, s>>>(pre_dev, bp.n, means, log_scales, quats, opacity_logits,
+                                               sh, rec, g2d, d_means, d_log_scales, d_quats, d_logits,
+                                               d_sh);
+    return cudaGetLastError();
+  };
   switch (sh_degree) {
-    case 0:
-      preprocess_backward_kernel<1><<<blocks, 128, 0, s>>>(pre_dev, bp.n, means, log_scales, quats,
-                                                          opacity_logits, sh, rec, g2d, d_means,
-                                                          d_log_scales, d_quats, d_logits, d_sh);
-      break;
-    case 1:
-      preprocess_backward_kernel<4><<<blocks, 128, 0, s>>>(pre_dev, bp.n, means, log_scales, quats,
-                                                          opacity_logits, sh, rec, g2d, d_means,
-                                                          d_log_scales, d_quats, d_logits, d_sh);
-      break;
-    case 2:
-      preprocess_backward_kernel<9><<<blocks, 128, 0, s>>>(pre_dev, bp.n, means, log_scales, quats,
-                                                          opacity_logits, sh, rec, g2d, d_means,
-                                                          d_log_scales, d_quats, d_logits, d_sh);
-      break;
-    default:
-      preprocess_backward_kernel<16><<<blocks, 128, 0, s>>>(pre_dev, bp.n, means, log_scales, quats,
-                                                           opacity_logits, sh, rec, g2d, d_means,
-                                                           d_log_scales, d_quats, d_logits, d_sh);
-      break;
+    case 0: return go(preprocess_backward_kernel<1>, backward_smem_bytes<1>());
+    case 1: return go(preprocess_backward_kernel<4>, backward_smem_bytes<4>());
+    case 2: return go(preprocess_backward_kernel<9>, backward_smem_bytes<9>());
+    default: return go(preprocess_backward_kernel<16>, backward_smem_bytes<16>());
   }
-  return cudaGetLastError();
 }
 
 }  // namespace a3fr
