@@ -192,18 +192,21 @@ def source_hash(*names) -> str:
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if still current."""
+def ncu_traffic(stage: str, workload_name: str):
+    """DRAM bytes per launch of `stage` on `workload_name` from the committed ncu summary, if
+    that entry exists and its sources are unchanged since the capture."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
-            entries = json.load(f)
-    except (OSError, ValueError):
+            entries = json.load(f).get("entries", [])
+    except (OSError, ValueError, AttributeError):
         return None
-    e = entries.get(kernel)
-    if not e or e.get("source_hash") != source_hash(*e.get("sources", [])):
-        return None
-    return e.get("dram_bytes_per_launch_full_workload")
+    for e in entries:
+        if e.get("stage") == stage and e.get("workload") == workload_name:
+            if e.get("source_hash") == source_hash(*e.get("sources", [])):
+                return e.get("dram_bytes_per_launch")
+            return None
+    return None
 
 
 # ----------------------------------------------------------------------------- oracle
@@ -916,7 +919,7 @@ def roofline(w, stats, stage_ms, n_frames, eyes, tile=16, blends=None, graph_ms=
     share = (t_ms / max(sum(graph_ms.values()), 1e-9)) if graph else \
         stage_ms[dom] / max(sum(stage_ms.values()), 1e-9)
     res = {"kernel": dom, "bound": bound, "achieved": achieved, "peak": peak, "unit": unit,
-           "frac": achieved / peak, "traffic": ncu_traffic(dom),
+           "frac": achieved / peak, "traffic": ncu_traffic(dom, getattr(w, "name", "")),
            "peak_source": f"{how} MEASURED_PEAKS.json" if bound == "hbm" else
            f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sm_max_mhz of {how} peaks)",
            "work_per_launch": work, "launch_ms": t_ms, "share_of_frame": share,

@@ -77,19 +77,22 @@ def test_hbm_stage_dominant_uses_measured_bandwidth():
 
 def test_traffic_only_while_sources_are_unchanged(tmp_path, monkeypatch):
     with open(os.path.join(bench.ROOT, "profiles", "ncu_traffic.json")) as f:
-        entries = json.load(f)
-    comp = entries["composite"]
+        doc = json.load(f)
+    comp = next(e for e in doc["entries"] if e["stage"] == "composite")
+    wl = comp["workload"]
     if comp["source_hash"] == bench.source_hash(*comp["sources"]):
-        assert bench.ncu_traffic("composite") == comp["dram_bytes_per_launch_full_workload"]
+        assert bench.ncu_traffic("composite", wl) == comp["dram_bytes_per_launch"]
+    # another workload's capture is not this workload's traffic
+    assert bench.ncu_traffic("composite", wl + " (another workload)") is None
     # a stale hash reads as no measurement
-    entries["composite"]["source_hash"] = "0" * 16
+    comp["source_hash"] = "0" * 16
     (tmp_path / "profiles").mkdir()
-    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(entries))
+    (tmp_path / "profiles" / "ncu_traffic.json").write_text(json.dumps(doc))
     src = tmp_path / "paper_2507_04147_gb300" / "csrc"
     src.mkdir(parents=True)
     for name in comp["sources"]:
         with open(os.path.join(bench.ROOT, "paper_2507_04147_gb300", "csrc", name), "rb") as f:
             (src / name).write_bytes(f.read())
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
-    assert bench.ncu_traffic("composite") is None
-    assert bench.ncu_traffic("no_such_kernel") is None
+    assert bench.ncu_traffic("composite", wl) is None
+    assert bench.ncu_traffic("no_such_kernel", wl) is None
