@@ -105,16 +105,21 @@ def test_stereo_sh3_ragged_image(binning):
         print(e, check_eye(r, e, scene, cams[e], gaze=gaze[e], fv=ofv))
 
 
+@pytest.mark.parametrize("tile", [16, 32])
 @pytest.mark.parametrize("levels,theta,dtheta", [((4,), (), 0.0), ((4, 1), (18.0,), 2.1),
                                                  ((4, 3, 2, 1), (10.0, 20.0, 35.0), 0.0)])
-def test_layer_configurations(levels, theta, dtheta):
+def test_layer_configurations(levels, theta, dtheta, tile):
+    """Every label count a tile can take (the 4-layer case makes 3-label tiles), at both
+    tilings: with 32-pixel tiles each count is its own instantiation of the composite."""
     scene = synth.uniform_scene(4000, 1, seed=5)
     cam = synth.pinhole_camera(160, 144, 90.0, -2.0)
     gaze = (101.3, 40.7)
     ofv = oracle.fovea(theta, dtheta, levels)
     gfv = a3fr.Fovea(theta, dtheta, levels)
-    r = gh.run(scene, [cam], gaze=[gaze], fovea=gfv)
-    print(check_eye(r, 0, scene, cam, gaze=gaze, fv=ofv))
+    r = gh.run(scene, [cam], gaze=[gaze], fovea=gfv, tile=tile)
+    print(check_eye(r, 0, scene, cam, tile=tile, gaze=gaze, fv=ofv))
+    n_tiles = oracle.tiles(160, tile) * oracle.tiles(144, tile)
+    assert set(levels) <= set(r["levels"][:n_tiles].tolist()) | {1}
 
 
 def test_degenerate_scenes():
@@ -215,10 +220,10 @@ def test_stereo_500k_sh3_sampled_pixels(tile, binning):
         print(e, check_eye(r, e, w.scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv, pixels=pix))
 
 
-@pytest.mark.parametrize("tile", [32, 16])
-def test_stereo_3m_clustered_full_size(tile):
-    """The 3M-Gaussian clustered stereo 2064x2208 frame at full size, foveated, in the
-    binning the library picks there (sort-based: 8,970 tiles at 32 pixels, 35,604 at 16):
+@pytest.mark.parametrize("tile,full", [(32, False), (16, False), (32, True)])
+def test_stereo_3m_clustered_full_size(tile, full):
+    """The 3M-Gaussian clustered stereo 2064x2208 frame at full size, foveated (and at full
+    resolution with 32-pixel tiles), in the binning the library picks there (sort-based: 8,970 tiles at 32 pixels, 35,604 at 16):
     records, rectangles, every sorted key and value (about 22M and 50M instances per
     frame) and the tile ranges of both eyes bit-exact; pixels within the parity bar on a
     random sample, on the tile row through the gaze (all three layers) and on every pixel
@@ -230,7 +235,7 @@ def test_stereo_3m_clustered_full_size(tile):
     cams = w.cameras(frame)
     gaze = w.gaze(frame, traj)
     ofv, gfv = fovea_params()
-    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False, tile=tile)
+    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False, tile=tile, full=full)
     assert r["stats"]["status"] == 0
     W, H = cams[0].width, cams[0].height
     tx, ty = oracle.tiles(W, tile), oracle.tiles(H, tile)
@@ -250,7 +255,8 @@ def test_stereo_3m_clustered_full_size(tile):
             pix.append(np.stack([xs.reshape(-1), ys.reshape(-1)], axis=1))
         pix = np.concatenate(pix).astype(np.int32)
         print(e, "heaviest tile instances", int(cnt.max()),
-              check_eye(r, e, w.scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv, pixels=pix))
+              check_eye(r, e, w.scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv, pixels=pix,
+                        full=full))
     r["scene"].close()
 
 
