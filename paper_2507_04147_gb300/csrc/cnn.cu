@@ -214,6 +214,13 @@ conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *
     const int y = y0 + m / kConvTW, x = x0 + (m % kConvTW);
     const bool inside = y < d.H && x < d.W;
     const size_t pix = inside ? ((size_t)b * d.H + y) * d.W + x : 0;
+    // the epilogue's residual input, loaded now so that its latency overlaps the waits for this
+    // tile's MMAs and the next halo
+    uint4 rv[COUT / 8];
+#pragma unroll
+    for (int g = 0; g < COUT / 8; ++g)
+      rv[g] = (inside && (flags & kEpiResid)) ? __ldg(reinterpret_cast<const uint4 *>(R + pix * COUT) + g)
+                                              : make_uint4(0u, 0u, 0u, 0u);
     if (!tc::mbar_wait(&s_bar, (uint32_t)(k & 1)) && lane == 0) atomicOr(status, kStatusTimeout);
     cp_async_wait_all();   // halo k + 1 has landed
     tc::fence_proxy_async();
@@ -241,8 +248,7 @@ conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *
           if (flags & kEpiRelu) o[c] = fmaxf(o[c], 0.0f);
         }
         if (flags & kEpiResid) {
-          const uint4 rv = __ldg(reinterpret_cast<const uint4 *>(R + pix * COUT) + g);
-          const __nv_bfloat16 *rb = reinterpret_cast<const __nv_bfloat16 *>(&rv);
+          const __nv_bfloat16 *rb = reinterpret_cast<const __nv_bfloat16 *>(&rv[g]);
 #pragma unroll
           for (int c = 0; c < 8; ++c) o[c] += __bfloat162float(rb[c]);
         }
@@ -481,23 +487,53 @@ __global__ void loss_kernel(const float *__restrict__ r, const float *__restrict
 
 // Final image of a foveated render: rendered pixels kept, the others = bilinear base +
 // residual (the base reads only top-left pixels, which every level renders, so the pixels
-// this kernel writes are never read by it).
+// this kernel writes are never read by it).  One thread per 2x2 block: the block's level
+// (its tile's), its 12 residuals in three 16-byte loads, the top-left pixels it needs once,
+// then the skipped sub-pixels -- top-right (label 3), bottom-left (4), bottom-right (2) --
+// with the same sums as base_px.
 __global__ void compose_kernel(const float *__restrict__ r, float *__restrict__ img,
                                const uint8_t *__restrict__ levels, int B, int H, int W, int tile,
                                int tiles_x, int n_tiles) {
-  const size_t n = (size_t)B * H * W;
   const int H2 = (H + 1) / 2, W2 = (W + 1) / 2;
+  const size_t n = (size_t)B * H2 * W2;
   for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % W);
-    const size_t rr = i / W;
-    const int y = (int)(rr % H), b = (int)(rr / H);
-    const int bx = x & 1, by = y & 1;
-    const int lab = bx == by ? (bx ? 1 : 0) : (bx ? 2 : 3);
+    const int x2 = (int)(i % W2);
+    const size_t rr = i / W2;
+    const int y2 = (int)(rr % H2), b = (int)(rr / H2);
+    const int x = 2 * x2, y = 2 * y2;
     const int lv = levels[b * n_tiles + (y / tile) * tiles_x + x / tile];
-    if (lab < lv) continue;   // rendered
-    const size_t ri = (((size_t)b * H2 + y / 2) * W2 + x / 2) * 16 + 2 * by + bx;
+    if (lv >= 4) continue;   // every pixel of the block rendered
+    // residual of colour c, sub-pixel s = 2 dy + dx, at r[16 i + 4 c + s] (channels 12..15
+    // are unused)
+    const float4 *r4 = reinterpret_cast<const float4 *>(r + i * 16);
+    const float4 q0 = r4[0], q1 = r4[1], q2 = r4[2];
+    const float res[3][4] = {{q0.x, q0.y, q0.z, q0.w}, {q1.x, q1.y, q1.z, q1.w}, {q2.x, q2.y, q2.z, q2.w}};
+    const int xr = min(x2 + 1, W2 - 1), yd = min(y2 + 1, H2 - 1);
+    auto tl = [&](int yy, int xx, int c) { return img[3 * (((size_t)b * H + 2 * yy) * W + 2 * xx) + c]; };
+    float a[3], right[3], down[3], diag[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) img[3 * i + c] = base_px(img, b, H, W, y / 2, x / 2, by, bx, c) + r[ri + 4 * c];
+    for (int c = 0; c < 3; ++c) {
+      a[c] = tl(y2, x2, c);
+      right[c] = tl(y2, xr, c);
+      down[c] = lv <= 3 ? tl(yd, x2, c) : 0.0f;
+      diag[c] = lv <= 1 ? tl(yd, xr, c) : 0.0f;
+    }
+    auto put = [&](int dy, int dx, const float *base) {
+      if (y + dy >= H || x + dx >= W) return;
+      float *o = img + 3 * (((size_t)b * H + y + dy) * W + x + dx);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) o[c] = base[c] + res[c][2 * dy + dx];
+    };
+    float bt[3], bb[3], bd[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      bt[c] = __fmul_rn(__fadd_rn(a[c], right[c]), 0.5f);                                   // top-right
+      bb[c] = __fmul_rn(__fadd_rn(a[c], down[c]), 0.5f);                                    // bottom-left
+      bd[c] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(a[c], right[c]), down[c]), diag[c]), 0.25f);   // bottom-right
+    }
+    if (lv <= 2) put(0, 1, bt);   // top-right: label 3, rendered from level 3
+    if (lv <= 3) put(1, 0, bb);   // bottom-left: label 4, rendered at level 4
+    if (lv <= 1) put(1, 1, bd);   // bottom-right: label 2, rendered from level 2
   }
 }
 
@@ -878,7 +914,7 @@ int a3fr_cnn_fill(a3fr_cnn *n, a3fr_scene *scene, float *out_rgb, void *stream) 
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   int rc = forward(n, out_rgb, v.depth, v.eyes, v.height, v.width, s);
   if (rc != A3FR_OK) return rc;
-  const size_t total = (size_t)v.eyes * v.height * v.width;
+  const size_t total = (size_t)v.eyes * ((v.height + 1) / 2) * ((v.width + 1) / 2);
   compose_kernel<<<grid_1d(total), 256, 0, s>>>(n->r, out_rgb, v.levels, v.eyes, v.height, v.width, v.tile,
                                                 v.tiles_x, v.n_tiles);
   CNN_CHECK(cudaGetLastError());
