@@ -923,9 +923,9 @@ def roofline(w, stats, stage_ms, n_frames, eyes, tile=16, blends=None, graph_ms=
            "peak_source": f"{how} MEASURED_PEAKS.json" if bound == "hbm" else
            f"152 SMs x 128 FP32 lanes x 2 flop x {sm_mhz:.0f} MHz (sm_max_mhz of {how} peaks)",
            "work_per_launch": work, "launch_ms": t_ms, "share_of_frame": share,
-           "launch": ("the composite graph: the plan kernel and the composite launches (at "
-                      "32-pixel tiles four launches forked on side streams), events on the render "
-                      "stream around it, graph replay" if graph else
+           "launch": ("the composite graph: the plan kernel and the composite launch (at "
+                      "32-pixel tiles one persistent launch over half-tile work items), events on "
+                      "the render stream around it, graph replay" if graph else
                       "the stage's kernels, events on the render stream, direct launches"),
            "share_basis": ("composite graph / (precompute graph + composite graph), graph replay"
                            if graph else "stage / sum of the stages, direct launches")}
