@@ -122,27 +122,30 @@ def test_layer_configurations(levels, theta, dtheta, tile):
     assert set(levels) <= set(r["levels"][:n_tiles].tolist()) | {1}
 
 
-def test_degenerate_scenes():
+@pytest.mark.parametrize("tile", [16, 32])
+def test_degenerate_scenes(tile):
     cam = synth.pinhole_camera(64, 48)
-    # no Gaussians
+    # no Gaussians (foveated and full: every tile is an empty work item)
     empty = synth.uniform_scene(0, 0, seed=1)
-    r = gh.run(empty, [cam], full=True)
+    r = gh.run(empty, [cam], full=True, tile=tile)
+    assert r["stats"]["instances"] == 0 and np.all(r["img"] == 0)
+    r = gh.run(empty, [cam], gaze=[(20.0, 20.0)], fovea=a3fr.Fovea(), tile=tile)
     assert r["stats"]["instances"] == 0 and np.all(r["img"] == 0)
     # one Gaussian, visible; one behind the camera
     one = synth.uniform_scene(1, 0, seed=2)
-    r = gh.run(one, [cam], full=True)
-    check_eye(r, 0, one, cam, full=True)
+    r = gh.run(one, [cam], full=True, tile=tile)
+    check_eye(r, 0, one, cam, tile=tile, full=True)
     behind = synth.uniform_scene(1, 0, seed=2)
     behind.means[:, 2] = -3.0
-    r = gh.run(behind, [cam], full=True)
+    r = gh.run(behind, [cam], full=True, tile=tile)
     assert r["stats"]["instances"] == 0 and np.all(r["img"] == 0)
     # a huge Gaussian covering every tile in front of small ones
     s = synth.uniform_scene(500, 2, seed=4)
     s.means[0] = [0.0, 0.0, 2.05]
     s.log_scales[0] = [0.5, 0.5, 0.5]
-    r = gh.run(s, [cam], gaze=[(0.0, 0.0)], fovea=a3fr.Fovea())
-    check_eye(r, 0, s, cam, gaze=(0.0, 0.0), fv=oracle.fovea())
-    assert r["rect"][0, 0].tolist() == [0, 0, 4, 3]
+    r = gh.run(s, [cam], gaze=[(0.0, 0.0)], fovea=a3fr.Fovea(), tile=tile)
+    check_eye(r, 0, s, cam, tile=tile, gaze=(0.0, 0.0), fv=oracle.fovea())
+    assert r["rect"][0, 0].tolist() == [0, 0, oracle.tiles(64, tile), oracle.tiles(48, tile)]
 
 
 @pytest.mark.parametrize("binning", [a3fr.BINNING_DIRECT, a3fr.BINNING_SORTED])
@@ -168,14 +171,18 @@ def test_depth_range_wider_than_the_rebase(binning):
         check_eye(r, 0, s, cam, full=full, gaze=(40.0, 30.0), fv=fv)
 
 
+@pytest.mark.parametrize("tile", [16, 32])
 @pytest.mark.parametrize("binning", [a3fr.BINNING_DIRECT, a3fr.BINNING_SORTED])
-def test_capacity_overflow_sets_status_without_fault(binning):
+def test_capacity_overflow_sets_status_without_fault(binning, tile):
     w = synth.small_single_view()
     cam = w.cameras(0)[0]
-    r = gh.run(w.scene, [cam], full=True, capacity=1000, binning=binning)
-    st = r["stats"]
-    assert st["status"] & a3fr.STATUS_CAPACITY
-    assert st["instances"] == 1000 and st["capacity"] == 1000
+    for full in (True, False):
+        r = gh.run(w.scene, [cam], full=full, gaze=[w.fixed_gaze_px], fovea=a3fr.Fovea(),
+                   capacity=1000, binning=binning, tile=tile)
+        st = r["stats"]
+        assert st["status"] & a3fr.STATUS_CAPACITY
+        assert st["instances"] == 1000 and st["capacity"] == 1000
+        assert np.isfinite(r["img"]).all()
 
 
 def test_repeated_renders_are_deterministic_and_counters_accumulate():
