@@ -72,6 +72,7 @@ struct a3fr_scene {
   uint32_t *tkeys[2] = {nullptr, nullptr};
   uint32_t *vals_alt = nullptr;
   uint32_t *tile_lb = nullptr;               // the tile sort's look-back (capacity-sized)
+  uint32_t *pstart = nullptr;                // first entry of every tile-sort partition
   size_t tile_lb_bytes = 0;
   uint32_t *plan = nullptr;                  // tiles bucketed by level (foveated composite)
   uint8_t *levels = nullptr;
@@ -219,6 +220,7 @@ void free_sort_buffers(a3fr_scene *s) {
   for (int b = 0; b < 2; ++b) dfree(s->tkeys[b]);
   dfree(s->vals_alt);
   dfree(s->tile_lb);
+  dfree(s->pstart);
   s->tile_lb_bytes = 0;
 }
 
@@ -240,6 +242,7 @@ int ensure_sort_buffers(a3fr_scene *s) {
   A3FR_CHECK(cudaMalloc(&s->vals_alt, sizeof(uint32_t) * s->capacity));
   s->tile_lb_bytes = onesweep_lookback_bytes(s->capacity, passes, false, false);
   A3FR_CHECK(cudaMalloc(&s->tile_lb, s->tile_lb_bytes));
+  A3FR_CHECK(cudaMalloc(&s->pstart, sizeof(uint32_t) * (s->capacity / kGenPart + 2)));
   return A3FR_OK;
 }
 
@@ -543,13 +546,28 @@ int enqueue_bin_sorted(a3fr_scene *s, int eyes, Entries entries, const FrameLayo
     uint32_t *v0 = tile_plan.passes % 2 ? s->vals_alt : s->vals;
     uint32_t *v1 = tile_plan.passes % 2 ? s->vals : s->vals_alt;
     A3FR_CHECK(cudaMemsetAsync(s->tile_lb, 0, s->tile_lb_bytes, stream));
-    A3FR_CHECK(launch_emit(ep, entries, s->touched, s->rect, s->tkeys[0], v0, emit_lb, counts + 6,
-                           stream));
+    // the entries' instance offsets go to the depth sort's first key buffer, free once the
+    // depth sort has run
+    uint32_t *off = s->dkeys[0];
+    const int n_parts = (int)((s->capacity + kGenPart - 1) / kGenPart);
+    A3FR_CHECK(launch_emit_offsets(ep, entries, s->touched, emit_lb, off, s->pstart, n_parts, counts + 6,
+                                   s->status, stream));
+    EmitSource src{};
+    src.entries = entries;
+    src.rect = s->rect;
+    src.off = off;
+    src.pstart = s->pstart;
+    src.total = emit_lb + (ep.n_entries + 1023) / 1024;
+    src.n_parts = n_parts;
+    src.n_entries = ep.n_entries;
+    src.n = n;
+    src.n_tiles = s->n_tiles;
+    src.tiles_x = s->TX;
     bool in_alt = false;
-    A3FR_CHECK(launch_onesweep<uint32_t>(s->tkeys[0], v0, s->tkeys[1], v1, false, counts, s->capacity,
-                                         tile_plan, tile_hist, tile_ctr, s->tile_lb, s->status,
-                                         &in_alt, stream, false, /*drop_final_keys=*/true));
-    *launches += 2 + tile_plan.passes;
+    A3FR_CHECK(launch_emit_onesweep(src, s->tkeys[0], v0, s->tkeys[1], v1, counts, s->capacity, tile_plan,
+                                    tile_hist, tile_ctr, s->tile_lb, s->status, &in_alt, stream,
+                                    /*drop_final_keys=*/true));
+    *launches += 1 + tile_plan.passes;
   }
   return A3FR_OK;
 }

@@ -36,9 +36,6 @@ constexpr int kPlanEntries = kPlanThreads * kPlanPer;
 constexpr int kOffsetThreads = 1024;
 constexpr int kMaxChunks = kBinMaxChunks;
 constexpr int kSegUnroll = 16;              // bin_offsets loads in flight per thread
-constexpr unsigned long long kAggFlag = 1ull << 62, kPrefixFlag = 2ull << 62;
-constexpr unsigned long long kVal62 = (1ull << 62) - 1ull;
-constexpr uint32_t kSpinLimit = 1u << 16;   // with back-off: well over a second
 constexpr int kMap = 256;                   // instances a bin_emit warp expands per window
 constexpr int kBandTiles = 3200;            // tiles per bin_emit band (12.8 KB of cursors)
 constexpr int kMapPad = kMap + kMap / 32;   // one pad word per 32 (fewer bank conflicts)
@@ -52,15 +49,6 @@ __device__ __forceinline__ T warp_incl_scan(T v, int lane) {
     const T n = __shfl_up_sync(0xffffffffu, v, o);
     if (lane >= o) v += n;
   }
-  return v;
-}
-
-__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v) {
-  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
-}
-__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
-  unsigned long long v;
-  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
   return v;
 }
 
@@ -90,40 +78,6 @@ bin_count_kernel(BinParams p, Entries ents, const ushort4 *__restrict__ rect,
   __syncthreads();
   uint32_t *out = h + (size_t)blockIdx.x * p.row;
   for (int r = t; r < n_ranges; r += kCountThreads) out[r] = s_hist[r];
-}
-
-// Exclusive prefix of block b's aggregate over the blocks before it, by warp 0: windows of
-// 32 predecessors (lane k reads block b-1-k) summed nearest first up to the first
-// inclusive prefix; an unpublished predecessor is polled again after a back-off.
-__device__ unsigned long long block_lookback(unsigned long long *lookback, int b, uint32_t *status) {
-  const int lane = threadIdx.x & 31;
-  unsigned long long excl = 0;
-  int j = b - 1;
-  uint32_t spins = 0;
-  while (j >= 0) {
-    const unsigned long long w = j - lane >= 0 ? ld_relaxed64(lookback + (j - lane)) : kPrefixFlag;
-    const unsigned long long flag = w & ~kVal62;
-    const unsigned ready = __ballot_sync(0xffffffffu, flag != 0ull);
-    const unsigned pref = __ballot_sync(0xffffffffu, flag == kPrefixFlag);
-    // lanes up to the nearest inclusive prefix, if every one of them is published
-    const int lim = pref ? __ffs(pref) - 1 : 31;
-    const unsigned need = lim == 31 ? 0xffffffffu : ((2u << lim) - 1u);
-    if ((ready & need) != need) {
-      if (++spins > kSpinLimit) {
-        if (lane == 0) atomicOr(status, kStatusTimeout);
-        break;
-      }
-      __nanosleep(spins < 8 ? 32u << spins : 4096u);
-      continue;
-    }
-    unsigned long long v = lane <= lim ? (w & kVal62) : 0ull;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    excl += v;
-    if (pref) break;
-    j -= 32;
-  }
-  return excl;
 }
 
 // Chunk plan: bounds[c] = the first entry j whose preceding instances P_j (prefix of the

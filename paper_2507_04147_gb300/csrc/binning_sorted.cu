@@ -15,12 +15,11 @@
 // each tile's run, i.e. the tile ranges; the digit histograms of that sort follow from the
 // same prefix sums.
 //
-// emit: instance offsets by reduce-then-scan over blocks of 1024 depth-ordered entries (a
-// count kernel whose last block scans the block sums; no block ever waits on another), then
-// each block expands its instances load-balanced: each output slot of its contiguous run is
-// one thread's work (its entry found by binary search over the block's exclusive offsets), so
-// a Gaussian covering hundreds of tiles does not hold its warp, and consecutive threads store
-// consecutive slots.
+// emit: the instance offset of every depth-ordered entry (a chained scan over blocks of 1024
+// entries) and the entry holding the first slot of each partition of the tile sort.  The
+// instances themselves are not written: the first pass of the tile sort generates them from
+// these offsets (sort.cu), so a Gaussian covering hundreds of tiles costs one slot per thread
+// like any other.
 #include "common.cuh"
 
 namespace a3fr {
@@ -30,132 +29,83 @@ constexpr int kEmitThreads = 256;
 constexpr int kEmitWarps = kEmitThreads / 32;
 constexpr int kEmitPer = 4;                                // entries per thread
 constexpr int kEmitEntries = kEmitThreads * kEmitPer;      // entries per block
-// Instance count of every block of kEmitEntries depth-ordered entries; the last block to
-// finish (fence + counter: the blocks never wait on one another) turns the sums into
-// exclusive prefixes in place, with the total after the last block.
+// Instance offsets of the depth-ordered entries, one block of kEmitEntries entries per CTA:
+// the CTAs take consecutive blocks from a ticket counter and chain their instance sums by
+// decoupled look-back, then every entry stores its global offset off[j], every entry holding
+// the first slot of a partition of kGenPart slots (the generated sort pass's unit) stores its
+// index in pstart[k], and the last block stores the total after the look-back words.
 __global__ void __launch_bounds__(kEmitThreads)
-emit_count_kernel(EmitParams p, Entries ents, const uint32_t *__restrict__ touched,
-                  unsigned long long *__restrict__ blk, uint32_t *__restrict__ done_counter) {
+emit_scan_kernel(EmitParams p, Entries ents, const uint32_t *__restrict__ touched,
+                 unsigned long long *__restrict__ lookback, uint32_t *__restrict__ off,
+                 uint32_t *__restrict__ pstart, int n_parts, uint32_t *__restrict__ ticket,
+                 uint32_t *__restrict__ status) {
   const uint32_t *__restrict__ entries = ents.get();
-  __shared__ unsigned long long s_w[kEmitWarps];
-  __shared__ unsigned long long s_carry;
-  __shared__ bool s_last;
+  __shared__ uint32_t s_wsum[kEmitWarps];
+  __shared__ uint32_t s_b;
+  __shared__ unsigned long long s_before;
   const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  unsigned long long sum = 0;
-#pragma unroll
-  for (int k = 0; k < kEmitPer; ++k) {
-    const uint32_t j = blockIdx.x * kEmitEntries + t * kEmitPer + k;
-    if (j < (uint32_t)p.n_entries) sum += touched[entries[j]];
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if (lane == 0) s_w[warp] = sum;
+  if (t == 0) s_b = atomicAdd(ticket, 1u);
   __syncthreads();
-  if (t == 0) {
-    unsigned long long total = 0;
-    for (int w = 0; w < kEmitWarps; ++w) total += s_w[w];
-    blk[blockIdx.x] = total;
-    __threadfence();
-    s_last = atomicAdd(done_counter, 1u) == gridDim.x - 1;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (t == 0) s_carry = 0;
-  __syncthreads();
-  const int nb = gridDim.x;
-  for (int base = 0; base < nb; base += kEmitThreads) {
-    const int i = base + t;
-    const unsigned long long v = i < nb ? __ldcg(blk + i) : 0ull;
-    unsigned long long incl = v;
+  const uint32_t b = s_b;
+  const uint32_t j0 = b * kEmitEntries + t * kEmitPer;
+  uint32_t c[kEmitPer], mine = 0;
+  if (j0 + kEmitPer <= (uint32_t)p.n_entries && (reinterpret_cast<uintptr_t>(entries) & 15u) == 0u) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(entries + j0);
+    c[0] = touched[v.x];
+    c[1] = touched[v.y];
+    c[2] = touched[v.z];
+    c[3] = touched[v.w];
+  } else {
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long n = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += n;
-    }
-    if (lane == 31) s_w[warp] = incl;
-    __syncthreads();
-    unsigned long long before = s_carry;
-    for (int w = 0; w < warp; ++w) before += s_w[w];
-    if (i < nb) blk[i] = before + incl - v;
-    __syncthreads();
-    if (t == kEmitThreads - 1) s_carry = before + incl;
-    __syncthreads();
+    for (int k = 0; k < kEmitPer; ++k) c[k] = j0 + k < (uint32_t)p.n_entries ? touched[entries[j0 + k]] : 0u;
   }
-  if (t == 0) blk[nb] = s_carry;
-}
-
-// Instances of block blockIdx.x's entries at [blk[blockIdx.x], +count): each thread reads
-// kEmitPer consecutive entries, the block scans them, and the block's run is expanded
-// load-balanced: one output slot per thread at a time (consecutive threads, consecutive
-// slots), its entry found by binary search over the block's exclusive offsets.
-__global__ void __launch_bounds__(kEmitThreads)
-emit_kernel(EmitParams p, Entries ents, const uint32_t *__restrict__ touched,
-            const ushort4 *__restrict__ rect, uint32_t *__restrict__ tile_keys,
-            uint32_t *__restrict__ vals, const unsigned long long *__restrict__ blk) {
-  const uint32_t *__restrict__ entries = ents.get();
-  __shared__ uint32_t s_warp_total[kEmitWarps];
-  __shared__ uint32_t s_excl[kEmitEntries + 1];   // exclusive instance offsets of the entries
-  __shared__ uint32_t s_tile0[kEmitEntries], s_width[kEmitEntries], s_gid[kEmitEntries];
-  const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-  uint32_t cnt[kEmitPer], mine = 0;
 #pragma unroll
-  for (int k = 0; k < kEmitPer; ++k) {
-    const int le = t * kEmitPer + k;
-    const uint32_t j = blockIdx.x * kEmitEntries + le;
-    uint32_t c = 0, tile0 = 0, width = 1, gid = 0;
-    if (j < (uint32_t)p.n_entries) {
-      const uint32_t v = entries[j];          // e * n + i
-      c = touched[v];
-      if (c) {
-        const uint32_t eye = v >= (uint32_t)p.n ? 1u : 0u;
-        gid = v - eye * (uint32_t)p.n;
-        const ushort4 rc = rect[v];
-        tile0 = eye * (uint32_t)p.n_tiles + (uint32_t)rc.y * (uint32_t)p.tiles_x + rc.x;
-        width = (uint32_t)(rc.z - rc.x);
-      }
-    }
-    cnt[k] = c;
-    mine += c;
-    s_tile0[le] = tile0;
-    s_width[le] = width;
-    s_gid[le] = gid;
-  }
+  for (int k = 0; k < kEmitPer; ++k) mine += c[k];
+  // block-exclusive offsets of this thread's entries (a block holds < 2^32 instances)
   uint32_t incl = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t n = __shfl_up_sync(0xffffffffu, incl, o);
-    if (lane >= o) incl += n;
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
   }
-  if (lane == 31) s_warp_total[warp] = incl;
+  if (lane == 31) s_wsum[warp] = incl;
   __syncthreads();
-  uint32_t excl = incl - mine;
-  for (int w = 0; w < warp; ++w) excl += s_warp_total[w];
+  uint32_t excl = incl - mine, agg = 0;
+  for (int w = 0; w < kEmitWarps; ++w) {
+    excl += w < warp ? s_wsum[w] : 0u;
+    agg += s_wsum[w];
+  }
+  if (warp == 0) {
+    unsigned long long before = 0;
+    if (b == 0) {
+      if (lane == 0) st_relaxed64(lookback, kPrefixFlag | agg);
+    } else {
+      if (lane == 0) st_relaxed64(lookback + b, kAggFlag | agg);
+      before = block_lookback(lookback, (int)b, status);
+      if (lane == 0) st_relaxed64(lookback + b, kPrefixFlag | ((before + agg) & kVal62));
+    }
+    if (lane == 0) {
+      s_before = before;
+      if (b == gridDim.x - 1) lookback[gridDim.x] = before + agg;   // the total
+    }
+  }
+  __syncthreads();
+  unsigned long long g = s_before + excl;
+  uint32_t o4[kEmitPer];
 #pragma unroll
   for (int k = 0; k < kEmitPer; ++k) {
-    s_excl[t * kEmitPer + k] = excl;
-    excl += cnt[k];
+    o4[k] = (uint32_t)(g < 0xffffffffull ? g : 0xffffffffull);
+    // the partitions whose first slot lies in this entry's run [g, g + c)
+    for (unsigned long long q = (g + kGenPart - 1) / kGenPart; q < (unsigned long long)n_parts && q * kGenPart < g + c[k]; ++q)
+      pstart[q] = j0 + k;
+    g += c[k];
   }
-  if (t == kEmitThreads - 1) s_excl[kEmitEntries] = excl;
-  __syncthreads();
-  const unsigned long long prefix = blk[blockIdx.x];
-  const uint32_t total = s_excl[kEmitEntries];
-  for (uint32_t q = t; q < total; q += kEmitThreads) {
-    int lo = 0, hi = kEmitEntries;   // s_excl[lo] <= q < s_excl[hi]
+  if (j0 + kEmitPer <= (uint32_t)p.n_entries && (reinterpret_cast<uintptr_t>(off) & 15u) == 0u) {
+    *reinterpret_cast<uint4 *>(off + j0) = make_uint4(o4[0], o4[1], o4[2], o4[3]);
+  } else {
 #pragma unroll
-    for (int step = 0; step < 10; ++step) {
-      const int mid = (lo + hi) >> 1;
-      if (s_excl[mid] <= q) lo = mid;
-      else hi = mid;
-    }
-    const uint32_t r = q - s_excl[lo];
-    const uint32_t w = s_width[lo];
-    const uint32_t dy = r / w, dx = r - dy * w;
-    const unsigned long long off = prefix + q;
-    if (off < p.capacity) {
-      tile_keys[off] = s_tile0[lo] + dy * (uint32_t)p.tiles_x + dx;
-      vals[off] = s_gid[lo];
-    }
+    for (int k = 0; k < kEmitPer; ++k)
+      if (j0 + k < (uint32_t)p.n_entries) off[j0 + k] = o4[k];
   }
 }
 
@@ -359,15 +309,13 @@ size_t emit_lookback_bytes(int n_entries) {
   return sizeof(unsigned long long) * (size_t)((n_entries + kEmitEntries - 1) / kEmitEntries + 1);
 }
 
-cudaError_t launch_emit(const EmitParams &p, Entries entries, const uint32_t *touched,
-                        const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
-                        unsigned long long *blk, uint32_t *done_counter, cudaStream_t s) {
+cudaError_t launch_emit_offsets(const EmitParams &p, Entries entries, const uint32_t *touched,
+                                unsigned long long *lookback, uint32_t *off, uint32_t *pstart, int n_parts,
+                                uint32_t *ticket, uint32_t *status, cudaStream_t s) {
   if (p.n_entries <= 0) return cudaSuccess;
   const int blocks = (p.n_entries + kEmitEntries - 1) / kEmitEntries;
-  emit_count_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, blk, done_counter);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  emit_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, rect, tile_keys, vals, blk);
+  emit_scan_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, lookback, off, pstart, n_parts,
+                                                    ticket, status);
   return cudaGetLastError();
 }
 

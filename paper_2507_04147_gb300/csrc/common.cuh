@@ -14,6 +14,57 @@ constexpr int kMaxEyes = 2;
 constexpr uint32_t kStatusCapacity = 1u;
 constexpr uint32_t kStatusTimeout = 2u;
 
+// Decoupled look-back (prefix sums chained across CTAs): one word per CTA, a flag -- the
+// CTA's own aggregate, or its inclusive prefix -- above a 62-bit value.  Every wait is
+// bounded: after kLookbackSpins polls the status word gets kStatusTimeout and the CTA goes
+// on with what it has (its writes stay in bounds).
+constexpr unsigned long long kAggFlag = 1ull << 62, kPrefixFlag = 2ull << 62;
+constexpr unsigned long long kVal62 = (1ull << 62) - 1ull;
+constexpr uint32_t kLookbackSpins = 1u << 16;   // with back-off: well over a second
+
+__device__ __forceinline__ void st_relaxed64(unsigned long long *p, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+__device__ __forceinline__ unsigned long long ld_relaxed64(const unsigned long long *p) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Exclusive prefix of CTA b's aggregate over the CTAs before it, by one warp: windows of
+// 32 predecessors (lane k reads CTA b-1-k) summed nearest first up to the first inclusive
+// prefix; an unpublished predecessor is polled again after a back-off.
+__device__ inline unsigned long long block_lookback(unsigned long long *lookback, int b, uint32_t *status) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long excl = 0;
+  int j = b - 1;
+  uint32_t spins = 0;
+  while (j >= 0) {
+    const unsigned long long w = j - lane >= 0 ? ld_relaxed64(lookback + (j - lane)) : kPrefixFlag;
+    const unsigned long long flag = w & ~kVal62;
+    const unsigned ready = __ballot_sync(0xffffffffu, flag != 0ull);
+    const unsigned pref = __ballot_sync(0xffffffffu, flag == kPrefixFlag);
+    // lanes up to the nearest inclusive prefix, if every one of them is published
+    const int lim = pref ? __ffs(pref) - 1 : 31;
+    const unsigned need = lim == 31 ? 0xffffffffu : ((2u << lim) - 1u);
+    if ((ready & need) != need) {
+      if (++spins > kLookbackSpins) {
+        if (lane == 0) atomicOr(status, kStatusTimeout);
+        break;
+      }
+      __nanosleep(spins < 8 ? 32u << spins : 4096u);
+      continue;
+    }
+    unsigned long long v = lane <= lim ? (w & kVal62) : 0ull;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (pref) break;
+    j -= 32;
+  }
+  return excl;
+}
+
 // Preprocess block size; the instance scan works on the same blocking.
 constexpr int kPreThreads = 128;
 
@@ -179,10 +230,32 @@ struct EmitParams {
   int n, n_entries, n_tiles, tiles_x;
   uint32_t capacity;
 };
+// Instance offsets of the depth-ordered entries: off[j] <- the instances of the entries before
+// j (u32 [n_entries]); pstart[k] (k < n_parts) <- the entry holding instance slot k kGenPart,
+// for every such slot below the total; lookback[n_blocks] <- the total, n_blocks = entries /
+// 1024 rounded up.  lookback (emit_lookback_bytes) and ticket: zeroed by the caller.
+constexpr int kGenPart = 4096;   // slots per partition of the generated tile-sort pass
 size_t emit_lookback_bytes(int n_entries);
-cudaError_t launch_emit(const EmitParams &p, Entries entries, const uint32_t *touched,
-                        const ushort4 *rect, uint32_t *tile_keys, uint32_t *vals,
-                        unsigned long long *blk, uint32_t *done_counter, cudaStream_t s);
+cudaError_t launch_emit_offsets(const EmitParams &p, Entries entries, const uint32_t *touched,
+                                unsigned long long *lookback, uint32_t *off, uint32_t *pstart, int n_parts,
+                                uint32_t *ticket, uint32_t *status, cudaStream_t s);
+// The instance array those offsets describe (slot off[j] + r = tile r of entry j's rectangle,
+// row-major), sorted stably by tile index: the onesweep sort of launch_onesweep whose first
+// pass generates its (tile, Gaussian) pairs from the entries instead of reading them, so the
+// unsorted instances are never stored.  Same buffers and result convention as
+// launch_onesweep (keys/vals are the first pass's would-be input, unread).
+struct EmitSource {
+  Entries entries;
+  const ushort4 *rect;
+  const uint32_t *off, *pstart;
+  const unsigned long long *total;
+  int n_entries, n, n_tiles, tiles_x, n_parts;
+};
+cudaError_t launch_emit_onesweep(const EmitSource &src, uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
+                                 uint32_t *vals_alt, const uint32_t *d_count, size_t capacity,
+                                 const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
+                                 uint32_t *lookback, uint32_t *status, bool *result_in_alt,
+                                 cudaStream_t s, bool drop_final_keys);
 
 // Per-tile instance counts without enumerating instances: every tile rectangle adds
 // +1/-1/-1/+1 at its four corners in a per-eye 2-D difference grid (tiles_y+1 rows of

@@ -155,10 +155,152 @@ histogram_kernel(K *__restrict__ keys, const uint32_t *__restrict__ d_count, Sor
   }
 }
 
-template <typename K, int KPT>
+// Where a pass's pairs come from.  MemSource reads them from memory (the value may be the
+// input position); a pass whose digit is the same for every key may copy them through.
+template <typename K>
+struct MemSource {
+  const K *keys;
+  const uint32_t *vals;   // null: the value is the input position
+  static constexpr bool kCopyable = true;
+  // item k of lane l of warp w: position base + w*32*KPT + k*32 + l
+  template <int KPT>
+  __device__ __forceinline__ void load(uint32_t base, uint32_t n, K (&key)[KPT], uint32_t (&val)[KPT],
+                                       unsigned char *) const {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const uint32_t wbase = base + warp * 32 * KPT + lane;
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const uint32_t i = wbase + k * 32;
+      const bool valid = i < n;
+      key[k] = valid ? keys[i] : K(0);
+      val[k] = valid ? (vals ? vals[i] : i) : 0u;
+    }
+  }
+  __device__ __forceinline__ void copy(uint32_t i, K *keys_out, uint32_t *vals_out) const {
+    if (keys_out) keys_out[i] = keys[i];
+    vals_out[i] = vals ? vals[i] : i;
+  }
+};
+
+// The tile instances of the depth-ordered entries, generated in place of being read: slot q of
+// the instance array is instance q - off[j] of the entry j with off[j] <= q < off[j + 1]
+// (exclusive instance offsets); instance r of an entry whose tile rectangle is w tiles wide is
+// tile (x0 + r mod w, y0 + r div w), so the slots list every entry's tiles row-major, entries
+// in depth order -- the array an emit of the instances would write, here never stored.  Per
+// partition: its first and last entries (pstart); the entries between them staged in shared
+// memory as (offset, first tile, width, Gaussian), one thread per entry, each entry with
+// instances marking its first slot; the marks spread over the slots by a running maximum (no
+// per-slot search); then each slot reads its entry's record.
+static_assert(kGenPart == kThreads * 16, "a generated partition is one 32-bit-key partition");
+constexpr int kGenWin = 2048;   // entries per window: a partition's whenever its entries average
+                                // two or more instances (else several windows)
+constexpr size_t kGenSmem = (size_t)kGenWin * 16 + (size_t)kGenPart * 2;
+
+struct GenSource {
+  EmitSource e;
+  static constexpr bool kCopyable = false;
+
+  // offset of entry j relative to slot base, at most kGenPart (past the entries: the total)
+  __device__ __forceinline__ int rel_off(uint32_t j, uint32_t base, unsigned long long total) const {
+    const unsigned long long o = j < (uint32_t)e.n_entries ? (unsigned long long)e.off[j] : total;
+    const long long d = (long long)o - (long long)base;
+    return (int)(d < kGenPart ? d : kGenPart);
+  }
+
+  template <int KPT>
+  __device__ __forceinline__ void load(uint32_t base, uint32_t n, uint32_t (&key)[KPT],
+                                       uint32_t (&val)[KPT], unsigned char *smem) const {
+    static_assert(kThreads * KPT == kGenPart, "one slot per item");
+    uint4 *s_rec = reinterpret_cast<uint4 *>(smem);                      // per window entry
+    uint16_t *s_ent = reinterpret_cast<uint16_t *>(smem + 16 * kGenWin);  // slot -> window entry
+    __shared__ uint32_t s_wmax[kWarps];
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    // every item below n is generated by exactly one window; the others stay unset (the pass
+    // marks them invalid and never reads them)
+    const uint32_t *__restrict__ entries = e.entries.get();
+    const unsigned long long total = *e.total;
+    const uint32_t part = base / kGenPart;
+    // the entries holding this partition's first slot and the next partition's first slot
+    // (or the last entry): every slot of the partition lies between them
+    uint32_t jw = e.pstart[part];
+    const uint32_t j_last = (unsigned long long)base + kGenPart < total && part + 1 < (uint32_t)e.n_parts
+                                ? e.pstart[part + 1] : (uint32_t)e.n_entries - 1u;
+    const int q_end = (int)min(n - base, (uint32_t)kGenPart);   // this partition's slots
+    int win_lo = 0;
+    for (;;) {
+      const uint32_t cnt = min((uint32_t)kGenWin, j_last + 1u - jw);   // entries of this window
+      for (int i = t; i < kGenPart / 8; i += kThreads) reinterpret_cast<uint4 *>(s_ent)[i] = make_uint4(0u, 0u, 0u, 0u);
+      __syncthreads();
+      for (uint32_t i = t; i < cnt; i += kThreads) {
+        const uint32_t j = jw + i;
+        const uint32_t v = entries[j];
+        const int o = rel_off(j, base, total), o1 = rel_off(j + 1, base, total);
+        const ushort4 rc = e.rect[v];
+        const uint32_t eye = v >= (uint32_t)e.n ? 1u : 0u;
+        s_rec[i] = make_uint4((uint32_t)o, eye * (uint32_t)e.n_tiles + (uint32_t)rc.y * (uint32_t)e.tiles_x + rc.x,
+                              (uint32_t)(rc.z - rc.x), v - eye * (uint32_t)e.n);
+        // every entry with instances marks its first slot (those offsets strictly increase)
+        if (o >= 0 && o < kGenPart && o1 > o) s_ent[o] = (uint16_t)i;
+      }
+      const int next = rel_off(jw + cnt, base, total);   // the first offset past the window
+      __syncthreads();
+      // running maximum over the slots (thread t: slots 16t .. 16t + 15): each slot's entry is
+      // the last one marked at or before it; unmarked leading slots keep entry 0
+      {
+        uint4 *p = reinterpret_cast<uint4 *>(s_ent) + 2 * t;
+        const uint4 a = p[0], c = p[1];
+        uint32_t w[8] = {a.x, a.y, a.z, a.w, c.x, c.y, c.z, c.w};
+        uint32_t run = 0;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) run = max(run, max(w[i] & 0xffffu, w[i] >> 16));
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl = max(incl, v);
+        }
+        if (lane == 31) s_wmax[warp] = incl;
+        uint32_t prev = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) prev = 0;
+        __syncthreads();
+        for (int ww = 0; ww < warp; ++ww) prev = max(prev, s_wmax[ww]);
+        run = prev;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const uint32_t lo16 = max(run, w[i] & 0xffffu);
+          const uint32_t hi16 = max(lo16, w[i] >> 16);
+          w[i] = lo16 | (hi16 << 16);
+          run = hi16;
+        }
+        p[0] = make_uint4(w[0], w[1], w[2], w[3]);
+        p[1] = make_uint4(w[4], w[5], w[6], w[7]);
+      }
+      __syncthreads();
+      const bool last = jw + cnt > j_last;
+      const int win_hi = last ? kGenPart : next;
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        const int q = warp * 32 * KPT + k * 32 + lane;
+        if (q < q_end && q >= win_lo && q < win_hi) {
+          const uint4 rec = s_rec[s_ent[q]];   // (offset, first tile, width, Gaussian)
+          const uint32_t r = (uint32_t)(q - (int)rec.x);
+          const uint32_t dy = r / rec.z, dx = r - dy * rec.z;
+          key[k] = rec.y + dy * (uint32_t)e.tiles_x + dx;
+          val[k] = rec.w;
+        }
+      }
+      if (last || next >= q_end) break;
+      __syncthreads();   // the next window reuses the staging
+      win_lo = next;
+      jw += cnt;
+    }
+  }
+  __device__ __forceinline__ void copy(uint32_t, uint32_t *, uint32_t *) const {}
+};
+
+template <typename K, int KPT, class Src>
 __global__ void __launch_bounds__(kThreads, 3)
-onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals_in,
-                K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
+onesweep_kernel(Src src, K *__restrict__ keys_out, uint32_t *__restrict__ vals_out,
                 const uint32_t *__restrict__ d_count, const uint32_t *__restrict__ hist,
                 uint32_t *__restrict__ part_counter, uint32_t *__restrict__ lookback, int shift,
                 uint32_t mask, uint32_t *__restrict__ status, uint32_t *__restrict__ skip_flag) {
@@ -178,7 +320,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
   const uint32_t n = *d_count;
   // a pass whose digit is the same for every key is the identity permutation (the sort is
   // stable): each partition just copies itself
-  const bool trivial = __syncthreads_or(n > 0 && hist[t] == n) != 0;
+  const bool trivial = __syncthreads_or(n > 0 && hist[t] == n) != 0 && Src::kCopyable;
   const uint32_t part = s_part;
   const uint32_t base = part * PART;
   if (base >= n) return;
@@ -189,10 +331,7 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
   }
   if (trivial) {
     const uint32_t end = min(n, base + (uint32_t)PART);
-    for (uint32_t i = base + t; i < end; i += kThreads) {
-      if (keys_out) keys_out[i] = keys_in[i];
-      vals_out[i] = vals_in ? vals_in[i] : i;
-    }
+    for (uint32_t i = base + t; i < end; i += kThreads) src.copy(i, keys_out, vals_out);
     return;
   }
 
@@ -200,14 +339,12 @@ onesweep_kernel(const K *__restrict__ keys_in, const uint32_t *__restrict__ vals
   K key[KPT];
   uint32_t val[KPT];
   uint32_t dr[KPT];   // digit (9 bits, 256 = invalid) << 16 | rank in warp
+  src.template load<KPT>(base, n, key, val, s_dyn);
   const uint32_t wbase = base + warp * 32 * KPT + lane;
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const uint32_t i = wbase + k * 32;
-    const bool valid = i < n;
-    key[k] = valid ? keys_in[i] : K(0);
-    val[k] = valid ? (vals_in ? vals_in[i] : i) : 0u;
-    dr[k] = valid ? ((uint32_t)(key[k] >> shift) & mask) : 256u;
+    dr[k] = i < n ? ((uint32_t)(key[k] >> shift) & mask) : 256u;
   }
   const unsigned lt_mask = (1u << lane) - 1u;
 #pragma unroll
@@ -308,7 +445,13 @@ int sm_count() {
   return sms;
 }
 
-template <typename K, int KPT>
+template <typename K, int KPT, class Src>
+constexpr size_t onesweep_smem() {
+  constexpr size_t staging = (sizeof(K) + sizeof(uint32_t)) * kThreads * KPT;
+  return Src::kCopyable ? staging : (staging > kGenSmem ? staging : kGenSmem);
+}
+
+template <typename K, int KPT, class Src>
 cudaError_t set_smem_attr() {
   // per device: the attribute lives in each device's context
   constexpr int kMaxDev = 64;
@@ -317,9 +460,8 @@ cudaError_t set_smem_attr() {
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   if (dev >= 0 && dev < kMaxDev && done[dev]) return cudaSuccess;
-  constexpr int PART = kThreads * KPT;
-  e = cudaFuncSetAttribute(onesweep_kernel<K, KPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)((sizeof(K) + sizeof(uint32_t)) * PART));
+  e = cudaFuncSetAttribute(onesweep_kernel<K, KPT, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)onesweep_smem<K, KPT, Src>());
   if (e == cudaSuccess && dev >= 0 && dev < kMaxDev) done[dev] = true;
   return e;
 }
@@ -368,6 +510,31 @@ cudaError_t launch_depth_histogram(uint32_t *keys, const uint32_t *d_count, cons
   return cudaGetLastError();
 }
 
+// Passes first .. plan.passes - 1 over (kin, vin) -> (kout, vout), ping-ponging.
+template <typename K, int KPT>
+cudaError_t run_passes(int first, K *kin, uint32_t *vin, K *kout, uint32_t *vout, bool implicit_vals,
+                       const uint32_t *d_count, size_t parts, const SortPlan &plan, const uint32_t *hist,
+                       uint32_t *counters, uint32_t *lookback, uint32_t *status, cudaStream_t s,
+                       bool drop_final_keys, uint32_t *final_skip) {
+  cudaError_t e = set_smem_attr<K, KPT, MemSource<K>>();
+  if (e != cudaSuccess) return e;
+  constexpr size_t dyn = onesweep_smem<K, KPT, MemSource<K>>();
+  for (int p = first; p < plan.passes; ++p) {
+    // the first pass may take the values to be the input positions (vals unread)
+    const MemSource<K> src{kin, (p == 0 && implicit_vals) ? nullptr : vin};
+    K *kdst = (drop_final_keys && p == plan.passes - 1) ? nullptr : kout;
+    onesweep_kernel<K, KPT, MemSource<K>><<<(unsigned)parts, kThreads, dyn, s>>>(
+        src, kdst, vout, d_count, hist + p * kRadix, counters + p,
+        lookback + (size_t)kRadix * parts * p, plan.shift[p], plan.mask, status,
+        p == plan.passes - 1 ? final_skip : nullptr);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    K *tk = kin; kin = kout; kout = tk;
+    uint32_t *tv = vin; vin = vout; vout = tv;
+  }
+  return cudaSuccess;
+}
+
 template <typename K, int KPT>
 cudaError_t launch_onesweep_kpt(K *keys, uint32_t *vals, K *keys_alt, uint32_t *vals_alt,
                                 bool implicit_vals, const uint32_t *d_count, size_t capacity,
@@ -376,26 +543,11 @@ cudaError_t launch_onesweep_kpt(K *keys, uint32_t *vals, K *keys_alt, uint32_t *
                                 cudaStream_t s, bool drop_final_keys, uint32_t *final_skip) {
   *result_in_alt = false;
   if (capacity == 0) return cudaSuccess;
-  cudaError_t e = set_smem_attr<K, KPT>();
-  if (e != cudaSuccess) return e;
   constexpr int PART = kThreads * KPT;
   const size_t parts = (capacity + PART - 1) / PART;
-  const size_t dyn = (sizeof(K) + sizeof(uint32_t)) * PART;
-  K *kin = keys, *kout = keys_alt;
-  uint32_t *vin = vals, *vout = vals_alt;
-  for (int p = 0; p < plan.passes; ++p) {
-    // the first pass may take the values to be the input positions (vals unread)
-    const uint32_t *vsrc = (p == 0 && implicit_vals) ? nullptr : vin;
-    K *kdst = (drop_final_keys && p == plan.passes - 1) ? nullptr : kout;
-    onesweep_kernel<K, KPT><<<(unsigned)parts, kThreads, dyn, s>>>(
-        kin, vsrc, kdst, vout, d_count, hist + p * kRadix, counters + p,
-        lookback + (size_t)kRadix * parts * p, plan.shift[p], plan.mask, status,
-        p == plan.passes - 1 ? final_skip : nullptr);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    K *tk = kin; kin = kout; kout = tk;
-    uint32_t *tv = vin; vin = vout; vout = tv;
-  }
+  cudaError_t e = run_passes<K, KPT>(0, keys, vals, keys_alt, vals_alt, implicit_vals, d_count, parts, plan,
+                                     hist, counters, lookback, status, s, drop_final_keys, final_skip);
+  if (e != cudaSuccess) return e;
   *result_in_alt = (plan.passes % 2) == 1;
   return cudaSuccess;
 }
@@ -423,6 +575,30 @@ template cudaError_t launch_onesweep<uint32_t>(uint32_t *, uint32_t *, uint32_t 
                                                const uint32_t *, uint32_t *, uint32_t *,
                                                uint32_t *, bool *, cudaStream_t, bool, bool,
                                                uint32_t *);
+
+cudaError_t launch_emit_onesweep(const EmitSource &src, uint32_t *keys, uint32_t *vals, uint32_t *keys_alt,
+                                 uint32_t *vals_alt, const uint32_t *d_count, size_t capacity,
+                                 const SortPlan &plan, const uint32_t *hist, uint32_t *counters,
+                                 uint32_t *lookback, uint32_t *status, bool *result_in_alt,
+                                 cudaStream_t s, bool drop_final_keys) {
+  *result_in_alt = false;
+  if (capacity == 0 || plan.passes < 1) return cudaSuccess;
+  constexpr int KPT = Part<uint32_t>::kKPT;
+  const size_t parts = (capacity + kGenPart - 1) / kGenPart;
+  cudaError_t e = set_smem_attr<uint32_t, KPT, GenSource>();
+  if (e != cudaSuccess) return e;
+  // pass 0 generates its pairs and writes the alternate buffers
+  onesweep_kernel<uint32_t, KPT, GenSource><<<(unsigned)parts, kThreads, onesweep_smem<uint32_t, KPT, GenSource>(), s>>>(
+      GenSource{src}, (drop_final_keys && plan.passes == 1) ? nullptr : keys_alt, vals_alt, d_count, hist,
+      counters, lookback, plan.shift[0], plan.mask, status, nullptr);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  e = run_passes<uint32_t, KPT>(1, keys_alt, vals_alt, keys, vals, false, d_count, parts, plan, hist, counters,
+                                lookback, status, s, drop_final_keys, nullptr);
+  if (e != cudaSuccess) return e;
+  *result_in_alt = (plan.passes % 2) == 1;
+  return cudaSuccess;
+}
 
 // ---- the 64-bit pair sort of the public API (8-bit digits) ----
 constexpr size_t kHistBytes = sizeof(uint32_t) * kMaxSortPasses * kRadix;
