@@ -31,7 +31,7 @@ constexpr int kRadix = 256;
 constexpr uint32_t kFlagAgg = 1u << 30;
 constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValMask = (1u << 30) - 1u;
-constexpr uint32_t kSpinLimit = 1u << 16;   // with back-off: well over a second
+constexpr uint32_t kSpinLimit = 1u << 22;   // polls 256 ns apart: about a second
 constexpr int kWin = 8;   // look-back window (predecessor partitions read at once)
 
 template <typename K> struct Part;
@@ -408,7 +408,7 @@ onesweep_kernel(Src src, K *__restrict__ keys_out, uint32_t *__restrict__ vals_o
           atomicOr(status, kStatusTimeout);
           break;
         }
-        __nanosleep(spins < 8 ? 32u << spins : 4096u);
+        __nanosleep(spins < 3 ? 32u << spins : 256u);
       }
     }
     st_relaxed(my_lb, kFlagPrefix | ((excl + total) & kValMask));
