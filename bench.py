@@ -247,12 +247,20 @@ def oracle_frame(w, frame: int, traj, budget_s: float, pixel_fraction_cap: float
         t1 = time.perf_counter()
         oracle.render(rec, rect, cam, tile, level=lv, pixels=probe)
         t_probe = time.perf_counter() - t1
-        per_px = t_probe / max(len(probe), 1)
-        remaining = max(per_eye_budget - t_fixed - t_probe, 0.0)
-        n_more = int(min(remaining / max(per_px, 1e-9), n_live * pixel_fraction_cap))
         t_pix, n_pix = t_probe, len(probe)
-        if n_more > 256:
-            more = live_xy[rng.choice(n_live, size=n_more, replace=False)]
+        # grow the sample batch by batch (a small batch overstates the per-pixel time on many
+        # threads) until the eye's budget is spent or the cap is reached
+        order = rng.permutation(n_live)
+        used = 0
+        cap = int(n_live * pixel_fraction_cap)
+        for _ in range(6):
+            remaining = per_eye_budget - (time.perf_counter() - t0)
+            per_px = t_pix / max(n_pix, 1)
+            n_more = int(min(0.9 * remaining / max(per_px, 1e-9), cap - used))
+            if n_more < 256:
+                break
+            more = live_xy[order[used:used + n_more]]
+            used += n_more
             t2 = time.perf_counter()
             oracle.render(rec, rect, cam, tile, level=lv, pixels=more)
             t_pix += time.perf_counter() - t2
