@@ -172,6 +172,26 @@ def test_depth_range_wider_than_the_rebase(binning):
 
 
 @pytest.mark.parametrize("tile", [16, 32])
+def test_sorted_binning_of_single_tile_gaussians(tile):
+    # tiny Gaussians cover one tile (a few near tile borders two or four) and some lie behind
+    # the camera: the tile sort's first pass then sees a partition's 4,096 instance slots
+    # spread over more entries than it stages at once (several windows per partition), and
+    # entries without instances at the end of the depth order
+    s = synth.uniform_scene(24000, 0, seed=31, log_scale_mean=-9.0)
+    s.means[::7, 2] = -s.means[::7, 2]
+    cam = synth.pinhole_camera(256, 256)
+    rec, rect, touched, keys, vals = gh.oracle_eye(s, cam, tile)
+    vis = touched > 0
+    assert (~vis).sum() > 1000 and len(keys) < 2 * vis.sum()
+    fv, fa = fovea_params()
+    for full in (True, False):
+        r = gh.run(s, [cam], gaze=None if full else [(100.0, 150.0)], fovea=None if full else fa,
+                   full=full, binning=a3fr.BINNING_SORTED, tile=tile)
+        assert r["stats"]["status"] == 0
+        check_eye(r, 0, s, cam, tile=tile, full=full, gaze=(100.0, 150.0), fv=fv)
+
+
+@pytest.mark.parametrize("tile", [16, 32])
 @pytest.mark.parametrize("binning", [a3fr.BINNING_DIRECT, a3fr.BINNING_SORTED])
 def test_capacity_overflow_sets_status_without_fault(binning, tile):
     w = synth.small_single_view()
