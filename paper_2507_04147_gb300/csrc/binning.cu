@@ -57,6 +57,7 @@ __device__ __forceinline__ T warp_incl_scan(T v, int lane) {
 __global__ void __launch_bounds__(kCountThreads)
 bin_count_kernel(BinParams p, Entries ents, const ushort4 *__restrict__ rect,
                  const uint32_t *__restrict__ bounds, uint32_t *__restrict__ h) {
+  pdl_begin();
   const uint32_t *__restrict__ entries = ents.get();
   extern __shared__ uint32_t s_hist[];
   const int t = threadIdx.x;
@@ -91,6 +92,7 @@ bin_plan_kernel(BinParams p, Entries ents, const uint32_t *__restrict__ touched,
                 const unsigned long long *__restrict__ inst_total,
                 unsigned long long *__restrict__ lookback, uint32_t *__restrict__ bounds,
                 uint32_t *__restrict__ status) {
+  pdl_begin();
   const uint32_t *__restrict__ entries = ents.get();
   __shared__ unsigned long long s_warp[kPlanThreads / 32];
   __shared__ unsigned long long s_before;
@@ -157,6 +159,7 @@ __global__ void __launch_bounds__(kOffsetThreads)
 bin_offsets_kernel(BinParams p, uint32_t *__restrict__ h, unsigned long long *__restrict__ lookback,
                    uint2 *__restrict__ ranges, uint32_t *__restrict__ counts,
                    uint32_t *__restrict__ status) {
+  pdl_begin();
   extern __shared__ uint32_t s_seg[];
   __shared__ uint32_t s_part[32][33];
   __shared__ unsigned long long s_before;
@@ -254,6 +257,7 @@ __global__ void __launch_bounds__(32)
 bin_emit_kernel(BinParams p, Entries ents, const ushort4 *__restrict__ rect,
                 const uint32_t *__restrict__ bounds, const uint32_t *__restrict__ h,
                 uint32_t *__restrict__ vals) {
+  pdl_begin();
   const uint32_t *__restrict__ entries = ents.get();
   extern __shared__ __align__(16) uint32_t s_dyn[];
   __shared__ uint32_t s_map_tile[kMapPad];
@@ -440,8 +444,11 @@ cudaError_t launch_bin_plan(const BinParams &p, Entries entries, const uint32_t 
                             const unsigned long long *inst_total, unsigned long long *lookback,
                             uint32_t *bounds, uint32_t *status, cudaStream_t s) {
   const int blocks = p.n_entries > 0 ? (p.n_entries + kPlanEntries - 1) / kPlanEntries : 1;
-  bin_plan_kernel<<<blocks, kPlanThreads, 0, s>>>(p, entries, touched, inst_total, lookback, bounds,
-                                                  status);
+  {
+    const cudaError_t e_ = launch_pdl(bin_plan_kernel, blocks, kPlanThreads, 0, s, p, entries, touched,
+                                      inst_total, lookback, bounds, status);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -451,7 +458,11 @@ cudaError_t launch_bin_count(const BinParams &p, Entries entries, const ushort4 
   cudaError_t e = cudaFuncSetAttribute(bin_count_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  bin_count_kernel<<<p.n_chunks, kCountThreads, smem, s>>>(p, entries, rect, bounds, h);
+  {
+    const cudaError_t e_ = launch_pdl(bin_count_kernel, p.n_chunks, kCountThreads, smem, s, p, entries, rect,
+                                      bounds, h);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -467,8 +478,11 @@ cudaError_t launch_bin_offsets(const BinParams &p, uint32_t *h, unsigned long lo
   cudaError_t e = cudaFuncSetAttribute(bin_offsets_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  bin_offsets_kernel<<<blocks > 0 ? blocks : 1, kOffsetThreads, smem, s>>>(p, h, lookback, ranges,
-                                                                           counts, status);
+  {
+    const cudaError_t e_ = launch_pdl(bin_offsets_kernel,
+                                      blocks > 0 ? blocks : 1, kOffsetThreads, smem, s, p, h, lookback, ranges, counts, status);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -480,7 +494,11 @@ cudaError_t launch_bin_emit(const BinParams &p, Entries entries, const ushort4 *
   cudaError_t e = cudaFuncSetAttribute(bin_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
-  bin_emit_kernel<<<p.n_chunks * p.n_bands, 32, smem, s>>>(p, entries, rect, bounds, h, vals);
+  {
+    const cudaError_t e_ = launch_pdl(bin_emit_kernel, p.n_chunks * p.n_bands, 32, smem, s, p, entries, rect,
+                                      bounds, h, vals);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 

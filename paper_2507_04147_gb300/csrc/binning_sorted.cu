@@ -39,6 +39,7 @@ emit_scan_kernel(EmitParams p, Entries ents, const uint32_t *__restrict__ touche
                  unsigned long long *__restrict__ lookback, uint32_t *__restrict__ off,
                  uint32_t *__restrict__ pstart, int n_parts, uint32_t *__restrict__ ticket,
                  uint32_t *__restrict__ status) {
+  pdl_begin();
   const uint32_t *__restrict__ entries = ents.get();
   __shared__ uint32_t s_wsum[kEmitWarps];
   __shared__ uint32_t s_b;
@@ -116,6 +117,7 @@ constexpr int kCountThreads = 512;
 __global__ void __launch_bounds__(kCountThreads)
 tile_count_kernel(TileScanParams p, const ushort4 *__restrict__ rect,
                   uint32_t *__restrict__ partials) {
+  pdl_begin();
   extern __shared__ uint32_t s_grid[];
   const int gw = p.tiles_x + 1, gh = p.tiles_y + 1;
   const int cells = p.n_eyes * gw * gh;
@@ -147,6 +149,7 @@ constexpr int kReduceParts = 19;
 __global__ void __launch_bounds__(256)
 tile_reduce_kernel(const uint32_t *__restrict__ partials, int parts, int cells,
                    uint32_t *__restrict__ grid) {
+  pdl_begin();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= cells) return;
   const int b0 = blockIdx.y * kReduceParts, b1 = min(parts, b0 + kReduceParts);
@@ -177,6 +180,7 @@ __global__ void __launch_bounds__(1024)
 tile_scan_kernel(TileScanParams p, const uint32_t *__restrict__ diff, uint2 *__restrict__ ranges,
                  uint32_t *__restrict__ tile_hist, uint32_t *__restrict__ counts,
                  uint32_t *__restrict__ status) {
+  pdl_begin();
   extern __shared__ uint32_t s_grid[];
   __shared__ unsigned long long s_warp[32];
   __shared__ uint32_t s_hist[kMaxSortPasses][256];
@@ -314,8 +318,11 @@ cudaError_t launch_emit_offsets(const EmitParams &p, Entries entries, const uint
                                 uint32_t *ticket, uint32_t *status, cudaStream_t s) {
   if (p.n_entries <= 0) return cudaSuccess;
   const int blocks = (p.n_entries + kEmitEntries - 1) / kEmitEntries;
-  emit_scan_kernel<<<blocks, kEmitThreads, 0, s>>>(p, entries, touched, lookback, off, pstart, n_parts,
-                                                    ticket, status);
+  {
+    const cudaError_t e_ = launch_pdl(emit_scan_kernel, blocks, kEmitThreads, 0, s, p, entries, touched,
+                                      lookback, off, pstart, n_parts, ticket, status);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -342,13 +349,19 @@ cudaError_t launch_tile_count(const TileScanParams &p, const ushort4 *rect, uint
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int parts = tile_count_blocks();
-  tile_count_kernel<<<parts, kCountThreads, smem, s>>>(p, rect, partials);
+  {
+    const cudaError_t e_ = launch_pdl(tile_count_kernel, parts, kCountThreads, smem, s, p, rect, partials);
+    if (e_ != cudaSuccess) return e_;
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = cudaMemsetAsync(grid, 0, sizeof(uint32_t) * cells, s);
   if (e != cudaSuccess) return e;
   const dim3 rb((unsigned)((cells + 255) / 256), (unsigned)((parts + kReduceParts - 1) / kReduceParts));
-  tile_reduce_kernel<<<rb, 256, 0, s>>>(partials, parts, (int)cells, grid);
+  {
+    const cudaError_t e_ = launch_pdl(tile_reduce_kernel, rb, 256, 0, s, partials, parts, (int)cells, grid);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -359,7 +372,11 @@ cudaError_t launch_tile_scan(const TileScanParams &p, const uint32_t *grid, uint
   cudaError_t e = cudaFuncSetAttribute(tile_scan_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  tile_scan_kernel<<<1, 1024, smem, s>>>(p, grid, ranges, tile_hist, counts, status);
+  {
+    const cudaError_t e_ = launch_pdl(tile_scan_kernel, 1, 1024, smem, s, p, grid, ranges, tile_hist, counts,
+                                      status);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 

@@ -65,6 +65,32 @@ __device__ inline unsigned long long block_lookback(unsigned long long *lookback
   return excl;
 }
 
+// Programmatic dependent launch: the kernels of a render run back to back in one stream, each
+// launched with programmatic stream serialisation (launch_pdl), so the next kernel's CTAs can
+// be scheduled while this one's last CTAs finish.  Every such kernel starts with pdl_begin():
+// it lets the next kernel be scheduled once all of its own CTAs have started, then waits until
+// the previous kernel has completed and its writes are visible -- before touching any memory.
+// Both instructions are no-ops in a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_begin() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
+template <typename... P, typename... A>
+inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                              A &&...args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
+}
+
 // Preprocess block size; the instance scan works on the same blocking.
 constexpr int kPreThreads = 128;
 

@@ -54,6 +54,7 @@ __device__ __forceinline__ int tile_level(const CompositeParams &p, int eye, int
 __global__ void __launch_bounds__(1024)
 tile_threshold_kernel(const CompositeParams *__restrict__ pp, const uint2 *__restrict__ ranges,
                       uint32_t *__restrict__ thresholds) {
+  pdl_begin();
   const CompositeParams &p = *pp;
   __shared__ uint32_t s_hist[256];
   __shared__ uint32_t s_prefix, s_k;
@@ -145,6 +146,7 @@ plan_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ ga
             uint8_t *__restrict__ levels, uint32_t *__restrict__ plan,
             uint32_t *__restrict__ plan_counts, const uint2 *__restrict__ ranges,
             const uint32_t *__restrict__ thresholds) {
+  pdl_begin();
   const CompositeParams &p = *pp;
   const float *gaze = gaze_ring + 4 * p.gaze_slot;
   const int n_ranges = p.n_eyes * p.n_tiles;
@@ -184,6 +186,7 @@ plan32_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ 
               uint8_t *__restrict__ levels, uint32_t *__restrict__ items,
               uint32_t *__restrict__ class_counts, const uint2 *__restrict__ ranges,
               const uint32_t *__restrict__ thresholds) {
+  pdl_begin();
   const CompositeParams &p = *pp;
   const float *gaze = gaze_ring + 4 * p.gaze_slot;
   const int n_ranges = p.n_eyes * p.n_tiles;
@@ -265,6 +268,7 @@ composite_kernel(const CompositeParams *__restrict__ pp, const float *__restrict
                  uint8_t *__restrict__ levels, float *__restrict__ t_final,
                  uint32_t *__restrict__ n_contrib, float *__restrict__ depth,
                  unsigned long long *__restrict__ counters) {
+  pdl_begin();
   const CompositeParams &p = *pp;   // per-render parameters in device memory
   float *out = p.out;
   __shared__ float4 s_geo[kThreads * kMult];   // u, v, -0.5 log2e a, -log2e b
@@ -752,6 +756,7 @@ composite_px_kernel(const CompositeParams *__restrict__ pp, const float *__restr
                     int incremental, float *__restrict__ t_final,
                     uint32_t *__restrict__ n_contrib, float *__restrict__ depth,
                     unsigned long long *__restrict__ counters) {
+  pdl_begin();
   __shared__ HalfSmem<kMult> sm;
   const CompositeParams &p = *pp;
   float *out = p.out;
@@ -861,6 +866,7 @@ __device__ __forceinline__ bool rendered_px(const CompositeParams &p, const uint
 
 __global__ void __launch_bounds__(256)
 fill_kernel(const CompositeParams *__restrict__ pp, const uint8_t *__restrict__ levels) {
+  pdl_begin();
   const CompositeParams &p = *pp;
   float *out = p.out;
   const size_t total = (size_t)p.n_eyes * p.height * p.width;
@@ -908,7 +914,10 @@ cudaError_t launch_fill(const CompositeParams &p, const CompositeParams *p_dev, 
   if (total == 0) return cudaSuccess;
   const size_t want = (total + 255) / 256;
   const int grid = (int)(want < 152 * 16 ? want : 152 * 16);
-  fill_kernel<<<grid, 256, 0, s>>>(p_dev, levels);
+  {
+    const cudaError_t e_ = launch_pdl(fill_kernel, grid, 256, 0, s, p_dev, levels);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -938,7 +947,10 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
     }
   };
   if (by_count) {
-    tile_threshold_kernel<<<1, 1024, 0, s>>>(p_dev, ranges, thresholds);
+    {
+      const cudaError_t e_ = launch_pdl(tile_threshold_kernel, 1, 1024, 0, s, p_dev, ranges, thresholds);
+      if (e_ != cudaSuccess) return e_;
+    }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (kernels) ++*kernels;
@@ -950,9 +962,12 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
     uint32_t *work = class_counts + kItemClasses;
     cudaError_t e = cudaMemsetAsync(class_counts, 0, sizeof(uint32_t) * (kItemClasses + 1), s);
     if (e != cudaSuccess) return e;
-    plan32_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p_dev, gaze, round, p.full ? 4 : uniform,
-                                                         cur, levels, items, class_counts, ranges,
-                                                         thresholds);
+    {
+      const cudaError_t e_ = launch_pdl(plan32_kernel, (n_ranges + 255) / 256, 256, 0, s, p_dev, gaze, round,
+                                        p.full ? 4 : uniform, cur, levels, items, class_counts, ranges,
+                                        thresholds);
+      if (e_ != cudaSuccess) return e_;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     auto go = [&](auto kern, int variant) -> cudaError_t {
@@ -971,8 +986,12 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
         sms = 1;
       const long max_items = 2L * n_ranges;
       const int grid = (int)std::min<long>((long)sms * occ, max_items);
-      kern<<<grid, kHalfThreads, 0, s>>>(p_dev, rec, n, ranges, kept, vals, items, class_counts, work,
-                                     inc, t_final, n_contrib, depth, counters);
+      {
+        const cudaError_t e_ = launch_pdl(kern, grid, kHalfThreads, 0, s, p_dev, rec, n, ranges, kept, vals,
+                                          items, class_counts, work, inc, t_final, n_contrib, depth,
+                                          counters);
+        if (e_ != cudaSuccess) return e_;
+      }
       return cudaGetLastError();
     };
     e = aux ? (mult == 2 ? go(composite_px_kernel<true, 2>, 0) : go(composite_px_kernel<true, 1>, 1))
@@ -984,16 +1003,23 @@ cudaError_t launch_composite(const CompositeParams &p, const CompositeParams *p_
   if (!p.full) {
     cudaError_t e = cudaMemsetAsync(pc, 0, 4 * sizeof(uint32_t), s);
     if (e != cudaSuccess) return e;
-    plan_kernel<<<(n_ranges + 255) / 256, 256, 0, s>>>(p_dev, gaze, round, uniform, cur, levels,
-                                                       plan, pc, ranges, thresholds);
+    {
+      const cudaError_t e_ = launch_pdl(plan_kernel, (n_ranges + 255) / 256, 256, 0, s, p_dev, gaze, round,
+                                        uniform, cur, levels, plan, pc, ranges, thresholds);
+      if (e_ != cudaSuccess) return e_;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (kernels) ++*kernels;
   }
   auto launch = [&](auto kern, int variant) -> cudaError_t {
     prefer_smem(kern, 4 + variant);
-    kern<<<n_ranges, kThreads, 0, s>>>(p_dev, rec, n, ranges, kept, vals, plan, pc, p.full ? 0 : inc,
-                                      levels, t_final, n_contrib, depth, counters);
+    {
+      const cudaError_t e_ = launch_pdl(kern, n_ranges, kThreads, 0, s, p_dev, rec, n, ranges, kept, vals,
+                                        plan, pc, p.full ? 0 : inc, levels, t_final, n_contrib, depth,
+                                        counters);
+      if (e_ != cudaSuccess) return e_;
+    }
     if (kernels) ++*kernels;
     return cudaGetLastError();
   };

@@ -177,6 +177,7 @@ preprocess_kernel(const PreParams *__restrict__ pp, int n, const float *__restri
                   float *__restrict__ rec, ushort4 *__restrict__ rect,
                   uint32_t *__restrict__ touched, uint32_t *__restrict__ dkeys,
                   uint32_t *__restrict__ depth_count) {
+  pdl_begin();
   constexpr int SS = sh_stride<K>();
   // per-render parameters: device memory (so a captured graph sees each render's cameras),
   // copied once per block into shared memory
@@ -376,24 +377,36 @@ cudaError_t launch_preprocess(const PreParams *p, int n, int sh_degree, const fl
   const int blocks = (n + kPreThreads - 1) / kPreThreads;
   switch (sh_degree) {
     case 0:
-      preprocess_kernel<1><<<blocks, kPreThreads, 0, s>>>(p, n, means, log_scales, quats,
-                                                          opacity_logits, sh, rec, rect, touched,
-                                                          dkeys, depth_count);
+      {
+        const cudaError_t e_ = launch_pdl(preprocess_kernel<1>, blocks, kPreThreads, 0, s, p, n, means,
+                                          log_scales, quats, opacity_logits, sh, rec, rect, touched, dkeys,
+                                          depth_count);
+        if (e_ != cudaSuccess) return e_;
+      }
       break;
     case 1:
-      preprocess_kernel<4><<<blocks, kPreThreads, 0, s>>>(p, n, means, log_scales, quats,
-                                                          opacity_logits, sh, rec, rect, touched,
-                                                          dkeys, depth_count);
+      {
+        const cudaError_t e_ = launch_pdl(preprocess_kernel<4>, blocks, kPreThreads, 0, s, p, n, means,
+                                          log_scales, quats, opacity_logits, sh, rec, rect, touched, dkeys,
+                                          depth_count);
+        if (e_ != cudaSuccess) return e_;
+      }
       break;
     case 2:
-      preprocess_kernel<9><<<blocks, kPreThreads, 0, s>>>(p, n, means, log_scales, quats,
-                                                          opacity_logits, sh, rec, rect, touched,
-                                                          dkeys, depth_count);
+      {
+        const cudaError_t e_ = launch_pdl(preprocess_kernel<9>, blocks, kPreThreads, 0, s, p, n, means,
+                                          log_scales, quats, opacity_logits, sh, rec, rect, touched, dkeys,
+                                          depth_count);
+        if (e_ != cudaSuccess) return e_;
+      }
       break;
     default:
-      preprocess_kernel<16><<<blocks, kPreThreads, 0, s>>>(p, n, means, log_scales, quats,
-                                                           opacity_logits, sh, rec, rect,
-                                                           touched, dkeys, depth_count);
+      {
+        const cudaError_t e_ = launch_pdl(preprocess_kernel<16>, blocks, kPreThreads, 0, s, p, n, means,
+                                          log_scales, quats, opacity_logits, sh, rec, rect, touched, dkeys,
+                                          depth_count);
+        if (e_ != cudaSuccess) return e_;
+      }
       break;
   }
   return cudaGetLastError();

@@ -75,6 +75,7 @@ template <typename K, bool kRebase>
 __global__ void __launch_bounds__(kThreads)
 histogram_kernel(K *__restrict__ keys, const uint32_t *__restrict__ d_count, SortPlan plan,
                  uint32_t *__restrict__ hist, const uint32_t *__restrict__ range) {
+  pdl_begin();
   __shared__ uint32_t s_hist[kWarps][4][kRadix];   // per warp, up to 4 passes per launch
   const int t = threadIdx.x, warp = t >> 5;
   const uint32_t n = *d_count;
@@ -304,6 +305,7 @@ onesweep_kernel(Src src, K *__restrict__ keys_out, uint32_t *__restrict__ vals_o
                 const uint32_t *__restrict__ d_count, const uint32_t *__restrict__ hist,
                 uint32_t *__restrict__ part_counter, uint32_t *__restrict__ lookback, int shift,
                 uint32_t mask, uint32_t *__restrict__ status, uint32_t *__restrict__ skip_flag) {
+  pdl_begin();
   constexpr int PART = kThreads * KPT;
   extern __shared__ __align__(16) unsigned char s_dyn[];
   K *s_keys = reinterpret_cast<K *>(s_dyn);
@@ -497,16 +499,22 @@ int histogram_blocks(size_t capacity) {
 template <typename K>
 cudaError_t launch_histogram(const K *keys, const uint32_t *d_count, size_t capacity,
                              const SortPlan &plan, uint32_t *hist, cudaStream_t s) {
-  histogram_kernel<K, false><<<histogram_blocks(capacity), kThreads, 0, s>>>(
-      const_cast<K *>(keys), d_count, plan, hist, nullptr);
+  {
+    const cudaError_t e_ = launch_pdl(histogram_kernel<K, false>, histogram_blocks(capacity), kThreads, 0, s,
+                                      const_cast<K *>(keys), d_count, plan, hist, nullptr);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
 cudaError_t launch_depth_histogram(uint32_t *keys, const uint32_t *d_count, const uint32_t *range,
                                    size_t capacity, const SortPlan &plan, uint32_t *hist,
                                    cudaStream_t s) {
-  histogram_kernel<uint32_t, true><<<histogram_blocks(capacity), kThreads, 0, s>>>(
-      keys, d_count, plan, hist, range);
+  {
+    const cudaError_t e_ = launch_pdl(histogram_kernel<uint32_t, true>, histogram_blocks(capacity), kThreads,
+                                      0, s, keys, d_count, plan, hist, range);
+    if (e_ != cudaSuccess) return e_;
+  }
   return cudaGetLastError();
 }
 
@@ -523,10 +531,13 @@ cudaError_t run_passes(int first, K *kin, uint32_t *vin, K *kout, uint32_t *vout
     // the first pass may take the values to be the input positions (vals unread)
     const MemSource<K> src{kin, (p == 0 && implicit_vals) ? nullptr : vin};
     K *kdst = (drop_final_keys && p == plan.passes - 1) ? nullptr : kout;
-    onesweep_kernel<K, KPT, MemSource<K>><<<(unsigned)parts, kThreads, dyn, s>>>(
-        src, kdst, vout, d_count, hist + p * kRadix, counters + p,
-        lookback + (size_t)kRadix * parts * p, plan.shift[p], plan.mask, status,
-        p == plan.passes - 1 ? final_skip : nullptr);
+    {
+      const cudaError_t e_ = launch_pdl(onesweep_kernel<K, KPT, MemSource<K>>, (unsigned)parts, kThreads, dyn,
+                                        s, src, kdst, vout, d_count, hist + p * kRadix, counters + p,
+                                        lookback + (size_t)kRadix * parts * p, plan.shift[p], plan.mask,
+                                        status, p == plan.passes - 1 ? final_skip : nullptr);
+      if (e_ != cudaSuccess) return e_;
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     K *tk = kin; kin = kout; kout = tk;
@@ -588,9 +599,14 @@ cudaError_t launch_emit_onesweep(const EmitSource &src, uint32_t *keys, uint32_t
   cudaError_t e = set_smem_attr<uint32_t, KPT, GenSource>();
   if (e != cudaSuccess) return e;
   // pass 0 generates its pairs and writes the alternate buffers
-  onesweep_kernel<uint32_t, KPT, GenSource><<<(unsigned)parts, kThreads, onesweep_smem<uint32_t, KPT, GenSource>(), s>>>(
-      GenSource{src}, (drop_final_keys && plan.passes == 1) ? nullptr : keys_alt, vals_alt, d_count, hist,
-      counters, lookback, plan.shift[0], plan.mask, status, nullptr);
+  {
+    const cudaError_t e_ = launch_pdl(onesweep_kernel<uint32_t, KPT, GenSource>, (unsigned)parts, kThreads,
+                                      onesweep_smem<uint32_t, KPT, GenSource>(), s, GenSource{src},
+                                      (drop_final_keys && plan.passes == 1) ? nullptr : keys_alt, vals_alt,
+                                      d_count, hist, counters, lookback, plan.shift[0], plan.mask, status,
+                                      nullptr);
+    if (e_ != cudaSuccess) return e_;
+  }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = run_passes<uint32_t, KPT>(1, keys_alt, vals_alt, keys, vals, false, d_count, parts, plan, hist, counters,
