@@ -131,6 +131,70 @@ __device__ __forceinline__ void load_halo_async(uint8_t *hs, const __nv_bfloat16
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// The image side of the learned fill, for the two convolutions that touch it when the fill
+// runs fused: the first reads its input straight from the render (kSrcImage), the last
+// composes the skipped pixels in its epilogue (kDstCompose) -- the same values the separate
+// gather and compose kernels produce, without their intermediate tensors.
+struct FillIO {
+  const float *depth;     // [B][H][W] expected depth of the render
+  float *img;             // [B][H][W][3]: top-left pixels read, skipped pixels written
+  const uint8_t *levels;  // tile levels [B][n_tiles]
+  int H, W, tile, tiles_x, n_tiles;
+};
+enum : int { kSrcTensor = 0, kSrcImage = 1 };
+enum : int { kDstTensor = 0, kDstCompose = 1 };
+
+// The 16 input channels of block (y2, x2): r, g, b of its top-left pixel and depth / 8 in
+// BF16, then zeros (the first eight as one 16-byte group; the second group is all zero).
+__device__ __forceinline__ uint4 block_input(const float *__restrict__ img, const float *__restrict__ depth,
+                                             int b, int H, int W, int y2, int x2) {
+  const size_t src = ((size_t)b * H + 2 * y2) * W + 2 * x2;
+  uint4 lo;
+  __nv_bfloat162 *l2 = reinterpret_cast<__nv_bfloat162 *>(&lo);
+  l2[0] = __floats2bfloat162_rn(img[3 * src], img[3 * src + 1]);
+  l2[1] = __floats2bfloat162_rn(img[3 * src + 2], depth[src] * 0.125f);
+  l2[2] = __floats2bfloat162_rn(0.0f, 0.0f);
+  l2[3] = l2[2];
+  return lo;
+}
+
+// Final image of a foveated render at block (y2, x2) from its 12 residuals res[c][2 dy + dx]:
+// rendered pixels kept, the skipped sub-pixels -- top-right (label 3), bottom-left (4),
+// bottom-right (2) -- set to the bilinear base of the blocks' top-left pixels (the last block
+// repeated past the edge) plus the residual.  The base reads only top-left pixels, which every
+// level renders and nobody writes.
+__device__ __forceinline__ void compose_block(float *__restrict__ img, int b, int H, int W, int y2, int x2, int lv,
+                                              const float (&res)[3][4]) {
+  const int H2 = (H + 1) / 2, W2 = (W + 1) / 2;
+  const int x = 2 * x2, y = 2 * y2;
+  const int xr = min(x2 + 1, W2 - 1), yd = min(y2 + 1, H2 - 1);
+  auto tl = [&](int yy, int xx, int c) { return img[3 * (((size_t)b * H + 2 * yy) * W + 2 * xx) + c]; };
+  float a[3], right[3], down[3], diag[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a[c] = tl(y2, x2, c);
+    right[c] = tl(y2, xr, c);
+    down[c] = lv <= 3 ? tl(yd, x2, c) : 0.0f;
+    diag[c] = lv <= 1 ? tl(yd, xr, c) : 0.0f;
+  }
+  auto put = [&](int dy, int dx, const float *base) {
+    if (y + dy >= H || x + dx >= W) return;
+    float *o = img + 3 * (((size_t)b * H + y + dy) * W + x + dx);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c] = base[c] + res[c][2 * dy + dx];
+  };
+  float bt[3], bb[3], bd[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    bt[c] = __fmul_rn(__fadd_rn(a[c], right[c]), 0.5f);                                   // top-right
+    bb[c] = __fmul_rn(__fadd_rn(a[c], down[c]), 0.5f);                                    // bottom-left
+    bd[c] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(a[c], right[c]), down[c]), diag[c]), 0.25f);   // bottom-right
+  }
+  if (lv <= 2) put(0, 1, bt);   // top-right: label 3, rendered from level 3
+  if (lv <= 3) put(1, 0, bb);   // bottom-left: label 4, rendered at level 4
+  if (lv <= 1) put(1, 1, bd);   // bottom-right: label 2, rendered from level 2
+}
+
 template <int CIN, int COUT>
 constexpr int conv_smem_bytes() {
   return 2 * (CIN / 8) * (kConvTH + 2) * (kConvTW + 2) * 16 + 9 * (CIN / 8) * COUT * 16;
@@ -143,14 +207,22 @@ constexpr int conv_smem_bytes() {
 // epilogue (tensor-memory read, bias, ReLU, residual, mask, store) runs while tile k+1's MMAs
 // do.  One thread issues the 9 x (CIN/16) MMAs of a tile and commits them to the mbarrier;
 // tile k completes phase k.
-template <int CIN, int COUT>
+//
+// kSrcImage (16 input channels): the halo is formed from the render (block_input) instead of
+// copied from a tensor -- its loads issued before tile k's epilogue, stored to shared memory
+// after it.  kDstCompose (16 output channels): the epilogue composes the block's skipped
+// pixels into the image (compose_block) instead of storing the residuals.
+template <int CIN, int COUT, int SRC = kSrcTensor, int DST = kDstTensor>
 __global__ void __launch_bounds__(128)
 conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *__restrict__ Wpk,
                   const float *__restrict__ bias, const __nv_bfloat16 *__restrict__ R,
                   const __nv_bfloat16 *__restrict__ Mk, void *__restrict__ Y, int flags,
-                  uint32_t *__restrict__ status) {
+                  uint32_t *__restrict__ status, FillIO io) {
+  static_assert(SRC == kSrcTensor || CIN == 16, "the image input has 16 channels");
+  static_assert(DST == kDstTensor || COUT == 16, "the composed residuals have 16 channels");
   constexpr int CG = CIN / 8, HR = kConvTH + 2, HC = kConvTW + 2;
   constexpr int HALO = CG * HR * HC * 16, WBYTES = 9 * CG * COUT * 16;
+  constexpr int kGPer = (HR * HC + 127) / 128;   // halo pixels per thread (image input)
   extern __shared__ __align__(1024) uint8_t smem[];
   uint8_t *const ws = smem + 2 * HALO;
   __shared__ uint32_t s_tmem;
@@ -168,9 +240,40 @@ conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *
     y0 = (r % tiles_y) * kConvTH;
     b = r / tiles_y;
   };
+  // image input: the halo pixels of a tile, loaded into registers, then stored as BF16 groups
+  // (the second 8-channel group stays zero: it is cleared once here)
+  uint4 gv[kGPer];
+  auto gather_load = [&](int k) {
+    int b, y0, x0;
+    origin(k, b, y0, x0);
+#pragma unroll
+    for (int j = 0; j < kGPer; ++j) {
+      const int q = t + 128 * j, r = q / HC, c = q - r * HC;
+      const int y = y0 - 1 + r, x = x0 - 1 + c;
+      gv[j] = make_uint4(0u, 0u, 0u, 0u);
+      if (q < HR * HC && y >= 0 && y < d.H && x >= 0 && x < d.W)
+        gv[j] = block_input(io.img, io.depth, b, io.H, io.W, y, x);
+    }
+  };
+  auto gather_store = [&](uint8_t *hs) {
+#pragma unroll
+    for (int j = 0; j < kGPer; ++j) {
+      const int q = t + 128 * j;
+      if (q < HR * HC) *reinterpret_cast<uint4 *>(hs + (size_t)q * 16) = gv[j];
+    }
+  };
   if (warp == 0) tc::tmem_alloc(&s_tmem, 64);
   for (int i = t; i < WBYTES / 16; i += 128) reinterpret_cast<uint4 *>(ws)[i] = __ldg(Wpk + i);
-  if (my_n > 0) {
+  if constexpr (SRC == kSrcImage) {
+    for (int i = t; i < 2 * HR * HC; i += 128) {   // group 1 of both halo buffers
+      const int buf = i / (HR * HC), q = i - buf * (HR * HC);
+      *reinterpret_cast<uint4 *>(smem + buf * HALO + (size_t)(HR * HC + q) * 16) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (my_n > 0) {
+      gather_load(0);
+      gather_store(smem);
+    }
+  } else if (my_n > 0) {
     int b, y0, x0;
     origin(0, b, y0, x0);
     load_halo_async<CG>(smem, X, b, y0, x0, HR, HC, d.H, d.W);
@@ -203,9 +306,14 @@ conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *
   };
   if (t == 0 && my_n > 0) issue(0);
   if (my_n > 1) {   // buffer 1 is free: start tile 1's halo
-    int b, y0, x0;
-    origin(1, b, y0, x0);
-    load_halo_async<CG>(smem + HALO, X, b, y0, x0, HR, HC, d.H, d.W);
+    if constexpr (SRC == kSrcImage) {
+      gather_load(1);
+      gather_store(smem + HALO);
+    } else {
+      int b, y0, x0;
+      origin(1, b, y0, x0);
+      load_halo_async<CG>(smem + HALO, X, b, y0, x0, HR, HC, d.H, d.W);
+    }
   }
   for (int k = 0; k < my_n; ++k) {
     int b, y0, x0;
@@ -229,16 +337,33 @@ conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *
     tc::fence_after_sync();
     if (t == 0 && k + 1 < my_n) issue(k + 1);
     if (k + 2 < my_n) {   // buffer k & 1 was read by tile k, which completed
-      int b, y0, x0;
-      origin(k + 2, b, y0, x0);
-      load_halo_async<CG>(smem + (k & 1) * HALO, X, b, y0, x0, HR, HC, d.H, d.W);
+      if constexpr (SRC == kSrcImage) {
+        gather_load(k + 2);   // stored after this tile's epilogue
+      } else {
+        int b, y0, x0;
+        origin(k + 2, b, y0, x0);
+        load_halo_async<CG>(smem + (k & 1) * HALO, X, b, y0, x0, HR, HC, d.H, d.W);
+      }
     }
     // epilogue of tile k
     float v[32];
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)((k & 1) * 32);
     if (COUT == 32) tc::tmem_ld32(taddr, v);
     else tc::tmem_ld16(taddr, v);
-    if (inside) {
+    if constexpr (DST == kDstCompose) {
+      if (inside) {
+        const int lv = io.levels[b * io.n_tiles + ((2 * y) / io.tile) * io.tiles_x + (2 * x) / io.tile];
+        if (lv < 4) {   // else every pixel of the block was rendered
+          // residual of colour c, sub-pixel s = 2 dy + dx: channel 4 c + s (12..15 unused)
+          float res[3][4];
+#pragma unroll
+          for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) res[c][q] = v[4 * c + q] + s_bias[4 * c + q];
+          compose_block(io.img, b, io.H, io.W, y, x, lv, res);
+        }
+      }
+    } else if (inside) {
 #pragma unroll
       for (int g = 0; g < COUT / 8; ++g) {
         float o[8];
@@ -270,6 +395,9 @@ conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *
           reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(Y) + pix * COUT)[g] = pk;
         }
       }
+    }
+    if constexpr (SRC == kSrcImage) {
+      if (k + 2 < my_n) gather_store(smem + (k & 1) * HALO);
     }
   }
   tc::fence_before_sync();
@@ -411,16 +539,9 @@ __global__ void gather_input_kernel(const float *__restrict__ img, const float *
     const int x2 = (int)(i % W2);
     const size_t r = i / W2;
     const int y2 = (int)(r % H2), b = (int)(r / H2);
-    const size_t src = ((size_t)b * H + 2 * y2) * W + 2 * x2;
-    uint4 lo, hi = make_uint4(0, 0, 0, 0);
-    __nv_bfloat162 *l2 = reinterpret_cast<__nv_bfloat162 *>(&lo);
-    l2[0] = __floats2bfloat162_rn(img[3 * src], img[3 * src + 1]);
-    l2[1] = __floats2bfloat162_rn(img[3 * src + 2], depth[src] * 0.125f);
-    l2[2] = __floats2bfloat162_rn(0.0f, 0.0f);
-    l2[3] = l2[2];
     uint4 *dst = reinterpret_cast<uint4 *>(x0 + i * 16);
-    dst[0] = lo;
-    dst[1] = hi;
+    dst[0] = block_input(img, depth, b, H, W, y2, x2);
+    dst[1] = make_uint4(0u, 0u, 0u, 0u);
   }
 }
 
@@ -483,58 +604,6 @@ __global__ void loss_kernel(const float *__restrict__ r, const float *__restrict
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if ((threadIdx.x & 31) == 0) atomicAdd(loss_acc, acc);
-}
-
-// Final image of a foveated render: rendered pixels kept, the others = bilinear base +
-// residual (the base reads only top-left pixels, which every level renders, so the pixels
-// this kernel writes are never read by it).  One thread per 2x2 block: the block's level
-// (its tile's), its 12 residuals in three 16-byte loads, the top-left pixels it needs once,
-// then the skipped sub-pixels -- top-right (label 3), bottom-left (4), bottom-right (2) --
-// with the same sums as base_px.
-__global__ void compose_kernel(const float *__restrict__ r, float *__restrict__ img,
-                               const uint8_t *__restrict__ levels, int B, int H, int W, int tile,
-                               int tiles_x, int n_tiles) {
-  const int H2 = (H + 1) / 2, W2 = (W + 1) / 2;
-  const size_t n = (size_t)B * H2 * W2;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
-    const int x2 = (int)(i % W2);
-    const size_t rr = i / W2;
-    const int y2 = (int)(rr % H2), b = (int)(rr / H2);
-    const int x = 2 * x2, y = 2 * y2;
-    const int lv = levels[b * n_tiles + (y / tile) * tiles_x + x / tile];
-    if (lv >= 4) continue;   // every pixel of the block rendered
-    // residual of colour c, sub-pixel s = 2 dy + dx, at r[16 i + 4 c + s] (channels 12..15
-    // are unused)
-    const float4 *r4 = reinterpret_cast<const float4 *>(r + i * 16);
-    const float4 q0 = r4[0], q1 = r4[1], q2 = r4[2];
-    const float res[3][4] = {{q0.x, q0.y, q0.z, q0.w}, {q1.x, q1.y, q1.z, q1.w}, {q2.x, q2.y, q2.z, q2.w}};
-    const int xr = min(x2 + 1, W2 - 1), yd = min(y2 + 1, H2 - 1);
-    auto tl = [&](int yy, int xx, int c) { return img[3 * (((size_t)b * H + 2 * yy) * W + 2 * xx) + c]; };
-    float a[3], right[3], down[3], diag[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      a[c] = tl(y2, x2, c);
-      right[c] = tl(y2, xr, c);
-      down[c] = lv <= 3 ? tl(yd, x2, c) : 0.0f;
-      diag[c] = lv <= 1 ? tl(yd, xr, c) : 0.0f;
-    }
-    auto put = [&](int dy, int dx, const float *base) {
-      if (y + dy >= H || x + dx >= W) return;
-      float *o = img + 3 * (((size_t)b * H + y + dy) * W + x + dx);
-#pragma unroll
-      for (int c = 0; c < 3; ++c) o[c] = base[c] + res[c][2 * dy + dx];
-    };
-    float bt[3], bb[3], bd[3];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      bt[c] = __fmul_rn(__fadd_rn(a[c], right[c]), 0.5f);                                   // top-right
-      bb[c] = __fmul_rn(__fadd_rn(a[c], down[c]), 0.5f);                                    // bottom-left
-      bd[c] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(a[c], right[c]), down[c]), diag[c]), 0.25f);   // bottom-right
-    }
-    if (lv <= 2) put(0, 1, bt);   // top-right: label 3, rendered from level 3
-    if (lv <= 3) put(1, 0, bb);   // bottom-left: label 4, rendered at level 4
-    if (lv <= 1) put(1, 1, bd);   // bottom-right: label 2, rendered from level 2
-  }
 }
 
 // Adam on the fp32 master parameters.
@@ -643,24 +712,24 @@ int ensure_acts(a3fr_cnn *n, size_t px) {
   return A3FR_OK;
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, int SRC = kSrcTensor, int DST = kDstTensor>
 cudaError_t conv(const ConvDims &d, const __nv_bfloat16 *X, const __nv_bfloat16 *W, const float *bias,
                  const __nv_bfloat16 *R, const __nv_bfloat16 *M, void *Y, int flags, uint32_t *status,
-                 cudaStream_t s) {
+                 cudaStream_t s, const FillIO &io = FillIO{}) {
   constexpr int smem = conv_smem_bytes<CIN, COUT>();
   static bool attr[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev >= 0 && dev < 64 && !attr[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, COUT>,
+    cudaError_t e = cudaFuncSetAttribute(conv3x3_tc_kernel<CIN, COUT, SRC, DST>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr[dev] = true;
   }
   const int tiles = d.B * ((d.W + kConvTW - 1) / kConvTW) * ((d.H + kConvTH - 1) / kConvTH);
   const int grid = tiles < 152 * 5 ? tiles : 152 * 5;
-  conv3x3_tc_kernel<CIN, COUT><<<grid, 128, smem, s>>>(d, X, reinterpret_cast<const uint4 *>(W), bias, R,
-                                                       M, Y, flags, status);
+  conv3x3_tc_kernel<CIN, COUT, SRC, DST><<<grid, 128, smem, s>>>(d, X, reinterpret_cast<const uint4 *>(W), bias,
+                                                                 R, M, Y, flags, status, io);
   return cudaGetLastError();
 }
 
@@ -700,24 +769,38 @@ int pack_all(a3fr_cnn *n, cudaStream_t s) {
   return A3FR_OK;
 }
 
-int forward(a3fr_cnn *n, const float *img, const float *depth, int B, int H, int W, cudaStream_t s) {
+// The prediction r (training, a3fr_cnn_forward: io null) or, for the fill (io set), the
+// composed image: the first convolution then reads its input from the render and the last
+// composes the skipped pixels, with neither x0 nor r stored.
+int forward(a3fr_cnn *n, const float *img, const float *depth, int B, int H, int W, cudaStream_t s,
+            const FillIO *io = nullptr) {
   const ConvDims d{B, (H + 1) / 2, (W + 1) / 2};
   const size_t px = (size_t)d.B * d.H * d.W;
   const int rc = ensure_acts(n, px);
   if (rc != A3FR_OK) return rc;
-  gather_input_kernel<<<grid_1d(px), 256, 0, s>>>(img, depth, B, H, W, n->x0);
-  CNN_CHECK(cudaGetLastError());
   const float *P = n->params;
-  CNN_CHECK((conv<16, 32>(d, n->x0, n->wf[0], P + bias_offset(0), nullptr, nullptr, n->h[0],
-                          kEpiBias | kEpiRelu, n->status, s)));
+  if (io) {
+    CNN_CHECK((conv<16, 32, kSrcImage>(d, nullptr, n->wf[0], P + bias_offset(0), nullptr, nullptr, n->h[0],
+                                       kEpiBias | kEpiRelu, n->status, s, *io)));
+  } else {
+    gather_input_kernel<<<grid_1d(px), 256, 0, s>>>(img, depth, B, H, W, n->x0);
+    CNN_CHECK(cudaGetLastError());
+    CNN_CHECK((conv<16, 32>(d, n->x0, n->wf[0], P + bias_offset(0), nullptr, nullptr, n->h[0],
+                            kEpiBias | kEpiRelu, n->status, s)));
+  }
   for (int b = 0; b < 4; ++b) {
     CNN_CHECK((conv<32, 32>(d, n->h[b], n->wf[1 + 2 * b], P + bias_offset(1 + 2 * b), nullptr, nullptr,
                             n->t[b], kEpiBias | kEpiRelu, n->status, s)));
     CNN_CHECK((conv<32, 32>(d, n->t[b], n->wf[2 + 2 * b], P + bias_offset(2 + 2 * b), n->h[b], nullptr,
                             n->h[b + 1], kEpiBias | kEpiResid, n->status, s)));
   }
-  CNN_CHECK((conv<32, 16>(d, n->h[4], n->wf[9], P + bias_offset(9), nullptr, nullptr, n->r,
-                          kEpiBias | kEpiF32, n->status, s)));
+  if (io) {
+    CNN_CHECK((conv<32, 16, kSrcTensor, kDstCompose>(d, n->h[4], n->wf[9], P + bias_offset(9), nullptr, nullptr,
+                                                     nullptr, kEpiBias, n->status, s, *io)));
+  } else {
+    CNN_CHECK((conv<32, 16>(d, n->h[4], n->wf[9], P + bias_offset(9), nullptr, nullptr, n->r,
+                            kEpiBias | kEpiF32, n->status, s)));
+  }
   return A3FR_OK;
 }
 
@@ -912,13 +995,8 @@ int a3fr_cnn_fill(a3fr_cnn *n, a3fr_scene *scene, float *out_rgb, void *stream) 
   FillView v{};
   if (!scene_fill_view(scene, &v)) return A3FR_ERR_NOT_READY;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
-  int rc = forward(n, out_rgb, v.depth, v.eyes, v.height, v.width, s);
-  if (rc != A3FR_OK) return rc;
-  const size_t total = (size_t)v.eyes * ((v.height + 1) / 2) * ((v.width + 1) / 2);
-  compose_kernel<<<grid_1d(total), 256, 0, s>>>(n->r, out_rgb, v.levels, v.eyes, v.height, v.width, v.tile,
-                                                v.tiles_x, v.n_tiles);
-  CNN_CHECK(cudaGetLastError());
-  return A3FR_OK;
+  const FillIO io{v.depth, out_rgb, v.levels, v.height, v.width, v.tile, v.tiles_x, v.n_tiles};
+  return forward(n, out_rgb, v.depth, v.eyes, v.height, v.width, s, &io);
 }
 
 }  // extern "C"
