@@ -154,30 +154,42 @@ composite_backward_kernel(BackwardParams p, const float *__restrict__ rec, const
         }
       }
       if (__ballot_sync(0xffffffffu, ok)) {
+        // warp sums of the nine partials by recursive halving: at each of the first three
+        // steps a lane keeps half of its values and sends the other half to its partner, so
+        // the first eight cost 4 + 2 + 1 + 1 + 1 shuffles instead of 8 x 5; value j ends in
+        // the lanes whose bits 4, 3, 2 spell j, and eight lanes add them to memory at once
+        float h[8] = {vu, vv, va, vb, vc, vo, vr, vg};
+        {
+          const bool up = (lane & 16) != 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          vu += __shfl_xor_sync(0xffffffffu, vu, o);
-          vv += __shfl_xor_sync(0xffffffffu, vv, o);
-          va += __shfl_xor_sync(0xffffffffu, va, o);
-          vb += __shfl_xor_sync(0xffffffffu, vb, o);
-          vc += __shfl_xor_sync(0xffffffffu, vc, o);
-          vo += __shfl_xor_sync(0xffffffffu, vo, o);
-          vr += __shfl_xor_sync(0xffffffffu, vr, o);
-          vg += __shfl_xor_sync(0xffffffffu, vg, o);
-          vbl += __shfl_xor_sync(0xffffffffu, vbl, o);
+          for (int j = 0; j < 4; ++j) {
+            const float keep = up ? h[j + 4] : h[j], send = up ? h[j] : h[j + 4];
+            h[j] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+          }
         }
-        if (lane == 0) {
-          float *d = g_eye + (size_t)s_gid[k] * kG2;
-          atomicAdd(d + 0, vu);
-          atomicAdd(d + 1, vv);
-          atomicAdd(d + 2, va);
-          atomicAdd(d + 3, vb);
-          atomicAdd(d + 4, vc);
-          atomicAdd(d + 5, vo);
-          atomicAdd(d + 6, vr);
-          atomicAdd(d + 7, vg);
-          atomicAdd(d + 8, vbl);
+        {
+          const bool up = (lane & 8) != 0;
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            const float keep = up ? h[j + 2] : h[j], send = up ? h[j] : h[j + 2];
+            h[j] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+          }
         }
+        {
+          const bool up = (lane & 4) != 0;
+          const float keep = up ? h[1] : h[0], send = up ? h[0] : h[1];
+          h[0] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+        }
+        h[0] += __shfl_xor_sync(0xffffffffu, h[0], 2);
+        h[0] += __shfl_xor_sync(0xffffffffu, h[0], 1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) vbl += __shfl_xor_sync(0xffffffffu, vbl, o);
+        float *d = g_eye + (size_t)s_gid[k] * kG2;
+        if ((lane & 3) == 0) {
+          const int j = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+          atomicAdd(d + j, h[0]);
+        }
+        if (lane == 1) atomicAdd(d + 8, vbl);
       }
     }
   }
