@@ -229,15 +229,6 @@ bin_offsets_kernel(BinParams p, uint32_t *__restrict__ h, unsigned long long *__
   }
 }
 
-// floor(r / w) for r < 2^24, 1 <= w < 2^16: a float estimate, then corrected to the exact
-// integer quotient (so the estimate's rounding never matters).
-__device__ __forceinline__ uint32_t div_small(uint32_t r, uint32_t w) {
-  uint32_t d = (uint32_t)((float)r * __frcp_rn((float)w));
-  if (d * w > r) --d;
-  else if ((d + 1u) * w <= r) ++d;
-  return d;
-}
-
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(gmem) : "memory");

@@ -91,6 +91,17 @@ inline cudaError_t launch_pdl(void (*kernel)(P...), dim3 grid, dim3 block, size_
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<A &&>(args)...);
 }
 
+// floor(r / w) for r < 2^21, 1 <= w < 2^16: the float estimate r * (1/w) is within 2^-23
+// relative of r / w, i.e. within 1/4 of the quotient, so its truncation is off by at most one
+// and one correction step gives the exact integer quotient.  (r is an instance index inside
+// one Gaussian's tile rectangle, below the tiles of an eye.)
+__device__ __forceinline__ uint32_t div_small(uint32_t r, uint32_t w) {
+  uint32_t d = (uint32_t)((float)r * __frcp_rn((float)w));
+  if (d * w > r) --d;
+  else if ((d + 1u) * w <= r) ++d;
+  return d;
+}
+
 // Preprocess block size; the instance scan works on the same blocking.
 constexpr int kPreThreads = 128;
 

@@ -284,8 +284,8 @@ struct GenSource {
         const int q = warp * 32 * KPT + k * 32 + lane;
         if (q < q_end && q >= win_lo && q < win_hi) {
           const uint4 rec = s_rec[s_ent[q]];   // (offset, first tile, width, Gaussian)
-          const uint32_t r = (uint32_t)(q - (int)rec.x);
-          const uint32_t dy = r / rec.z, dx = r - dy * rec.z;
+          const uint32_t r = (uint32_t)(q - (int)rec.x);   // < 2^16 instances per entry
+          const uint32_t dy = div_small(r, rec.z), dx = r - dy * rec.z;
           key[k] = rec.y + dy * (uint32_t)e.tiles_x + dx;
           val[k] = rec.w;
         }
