@@ -247,10 +247,11 @@ def test_stereo_500k_sh3_sampled_pixels(tile, binning):
         print(e, check_eye(r, e, w.scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv, pixels=pix))
 
 
-@pytest.mark.parametrize("tile,full", [(32, False), (16, False), (32, True)])
-def test_stereo_3m_clustered_full_size(tile, full):
+@pytest.mark.parametrize("tile,full,batch_mult", [(32, False, 1), (16, False, 1), (32, True, 1), (32, False, 2)])
+def test_stereo_3m_clustered_full_size(tile, full, batch_mult):
     """The 3M-Gaussian clustered stereo 2064x2208 frame at full size, foveated (and at full
-    resolution with 32-pixel tiles), in the binning the library picks there (sort-based: 8,970 tiles at 32 pixels, 35,604 at 16):
+    resolution with 32-pixel tiles; and with the staging batch the autotuner picks for this
+    workload, 32-pixel tiles x 2), in the binning the library picks there (sort-based: 8,970 tiles at 32 pixels, 35,604 at 16):
     records, rectangles, every sorted key and value (about 22M and 50M instances per
     frame) and the tile ranges of both eyes bit-exact; pixels within the parity bar on a
     random sample, on the tile row through the gaze (all three layers) and on every pixel
@@ -262,7 +263,8 @@ def test_stereo_3m_clustered_full_size(tile, full):
     cams = w.cameras(frame)
     gaze = w.gaze(frame, traj)
     ofv, gfv = fovea_params()
-    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False, tile=tile, full=full)
+    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False, tile=tile, full=full,
+               batch_mult=batch_mult)
     assert r["stats"]["status"] == 0
     W, H = cams[0].width, cams[0].height
     tx, ty = oracle.tiles(W, tile), oracle.tiles(H, tile)
