@@ -531,6 +531,34 @@ constexpr int kBatch = 256;   // Gaussians staged per batch (times the staging m
 __device__ __forceinline__ int label_dx(int L) { return (L == 1 || L == 2) ? 1 : 0; }
 __device__ __forceinline__ int label_dy(int L) { return (L == 1 || L == 3) ? 1 : 0; }
 
+// Two fp32 values in one 64-bit register pair, and the packed fp32 arithmetic of sm_100 and
+// later (add / mul / fma .rn.f32x2: each half rounded exactly as the scalar instruction), so
+// two pixels of a lane take one instruction where the arithmetic is the same for both.
+using f32x2 = unsigned long long;
+__device__ __forceinline__ f32x2 f2_pack(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f32x2 v, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ f32x2 f2_add(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
+  f32x2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 template <int kMult>
 struct HalfSmem {
   float4 geo[kBatch * kMult];
@@ -675,8 +703,45 @@ __device__ __forceinline__ void render_half(HalfSmem<kMult> &sm, const Composite
           const float2 cz = sm.cz[e];
           const float4 rgb = sm.rgb[e];
           const uint32_t pos = pos0 + (uint32_t)e;
+          if constexpr (!kAux && P >= 2) {
+            // pixel pairs (0, 1) and (2, 3): the same operations as the scalar loop below, two
+            // pixels per instruction wherever both take the same one
+            const f32x2 gx = f2_pack(geo.x, geo.x), gy = f2_pack(geo.y, geo.y);
+            const f32x2 ca = f2_pack(geo.z, geo.z), cb = f2_pack(geo.w, geo.w), cc = f2_pack(cz.x, cz.x);
+            const f32x2 op = f2_pack(rgb.w, rgb.w);
+            const f32x2 cr = f2_pack(rgb.x, rgb.x), cg = f2_pack(rgb.y, rgb.y), cbl = f2_pack(rgb.z, rgb.z);
+            const f32x2 one = f2_pack(1.0f, 1.0f), mone = f2_pack(-1.0f, -1.0f);
+#pragma unroll
+            for (int k = 0; k + 1 < P; k += 2) {
+              const f32x2 dx = f2_add(gx, f2_pack(-fpx[k], -fpx[k + 1]));
+              const f32x2 dy = f2_add(gy, f2_pack(-fpy[k], -fpy[k + 1]));
+              // falloff_log2: (A dx + B dy) dx + (C dy) dy, rounded step by step
+              const f32x2 pw2 = f2_fma(f2_fma(ca, dx, f2_mul(cb, dy)), dx, f2_mul(f2_mul(cc, dy), dy));
+              float pw0, pw1;
+              f2_unpack(pw2, pw0, pw1);
+              float oe0, oe1;
+              f2_unpack(f2_mul(op, f2_pack(ex2_approx(pw0), ex2_approx(pw1))), oe0, oe1);
+              const float al0 = fminf(0.99f, oe0), al1 = fminf(0.99f, oe1);
+              const float a0 = (pw0 <= 0.0f && al0 >= 1.0f / 255.0f) ? al0 : 0.0f;
+              const float a1 = (pw1 <= 0.0f && al1 >= 1.0f / 255.0f) ? al1 : 0.0f;
+              const f32x2 a2 = f2_pack(a0, a1), t2 = f2_pack(T[k], T[k + 1]);
+              float tt0, tt1, at0, at1;
+              f2_unpack(f2_mul(t2, f2_fma(a2, mone, one)), tt0, tt1);   // T (1 - a)
+              f2_unpack(f2_mul(a2, t2), at0, at1);
+              const bool fin0 = tt0 < 0.0001f, fin1 = tt1 < 0.0001f;
+              const f32x2 w2 = f2_pack(fin0 ? 0.0f : at0, fin1 ? 0.0f : at1);
+              f2_unpack(f2_fma(cr, w2, f2_pack(C0[k], C0[k + 1])), C0[k], C0[k + 1]);
+              f2_unpack(f2_fma(cg, w2, f2_pack(C1[k], C1[k + 1])), C1[k], C1[k + 1]);
+              f2_unpack(f2_fma(cbl, w2, f2_pack(C2[k], C2[k + 1])), C2[k], C2[k + 1]);
+              T[k] = fin0 ? 0.0f : tt0;
+              T[k + 1] = fin1 ? 0.0f : tt1;
+            }
+          }
 #pragma unroll
           for (int k = 0; k < P; ++k) {
+            if constexpr (!kAux && P >= 2) {
+              if (k + 1 < P || P % 2 == 0) continue;   // done in pairs above (all but an odd last)
+            }
             const float dx = __fsub_rn(geo.x, fpx[k]), dy = __fsub_rn(geo.y, fpy[k]);
             const float pw = falloff_log2(geo.z, geo.w, cz.x, dx, dy);
             const float alpha = blend_alpha(rgb.w, pw);
@@ -699,10 +764,10 @@ __device__ __forceinline__ void render_half(HalfSmem<kMult> &sm, const Composite
               const float a = (pw <= 0.0f && alpha >= 1.0f / 255.0f) ? alpha : 0.0f;
               const float tt = __fmul_rn(T[k], __fsub_rn(1.0f, a));
               const bool fin = tt < 0.0001f;   // this Gaussian would end the pixel, or it ended
-              const float w = fin ? 0.0f : a * T[k];
-              C0[k] += rgb.x * w;
-              C1[k] += rgb.y * w;
-              C2[k] += rgb.z * w;
+              const float w = fin ? 0.0f : __fmul_rn(a, T[k]);
+              C0[k] = __fmaf_rn(rgb.x, w, C0[k]);
+              C1[k] = __fmaf_rn(rgb.y, w, C1[k]);
+              C2[k] = __fmaf_rn(rgb.z, w, C2[k]);
               T[k] = fin ? 0.0f : tt;
             }
           }
