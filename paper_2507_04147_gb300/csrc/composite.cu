@@ -813,7 +813,7 @@ __device__ __forceinline__ void render_half(HalfSmem<kMult> &sm, const Composite
 }
 
 template <bool kAux, int kMult>
-__global__ void __launch_bounds__(kHalfThreads, kAux ? 6 : 8)
+__global__ void __launch_bounds__(kHalfThreads, kAux ? 6 : 7)
 composite_px_kernel(const CompositeParams *__restrict__ pp, const float *__restrict__ rec, int n,
                     const uint2 *__restrict__ ranges, const uint32_t *__restrict__ kept,
                     const uint32_t *__restrict__ vals, const uint32_t *__restrict__ items,
