@@ -553,6 +553,12 @@ __device__ __forceinline__ f32x2 f2_mul(f32x2 a, f32x2 b) {
   asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
 }
+// 1.0f where a >= b, else 0.0f (one instruction instead of a compare and a select)
+__device__ __forceinline__ float ge_factor(float a, float b) {
+  float r;
+  asm("set.ge.f32.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+  return r;
+}
 __device__ __forceinline__ f32x2 f2_fma(f32x2 a, f32x2 b, f32x2 c) {
   f32x2 r;
   asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
@@ -725,16 +731,17 @@ __device__ __forceinline__ void render_half(HalfSmem<kMult> &sm, const Composite
               const float a0 = (pw0 <= 0.0f && al0 >= 1.0f / 255.0f) ? al0 : 0.0f;
               const float a1 = (pw1 <= 0.0f && al1 >= 1.0f / 255.0f) ? al1 : 0.0f;
               const f32x2 a2 = f2_pack(a0, a1), t2 = f2_pack(T[k], T[k + 1]);
-              float tt0, tt1, at0, at1;
-              f2_unpack(f2_mul(t2, f2_fma(a2, mone, one)), tt0, tt1);   // T (1 - a)
-              f2_unpack(f2_mul(a2, t2), at0, at1);
-              const bool fin0 = tt0 < 0.0001f, fin1 = tt1 < 0.0001f;
-              const f32x2 w2 = f2_pack(fin0 ? 0.0f : at0, fin1 ? 0.0f : at1);
+              const f32x2 tt2 = f2_mul(t2, f2_fma(a2, mone, one));   // T (1 - a)
+              float tt0, tt1;
+              f2_unpack(tt2, tt0, tt1);
+              // 1 while the pixel goes on, 0 once this Gaussian would end it (or it ended):
+              // multiplying by it equals the scalar path's selects bit for bit (T, a T >= 0)
+              const f32x2 keep = f2_pack(ge_factor(tt0, 0.0001f), ge_factor(tt1, 0.0001f));
+              const f32x2 w2 = f2_mul(f2_mul(a2, t2), keep);
               f2_unpack(f2_fma(cr, w2, f2_pack(C0[k], C0[k + 1])), C0[k], C0[k + 1]);
               f2_unpack(f2_fma(cg, w2, f2_pack(C1[k], C1[k + 1])), C1[k], C1[k + 1]);
               f2_unpack(f2_fma(cbl, w2, f2_pack(C2[k], C2[k + 1])), C2[k], C2[k + 1]);
-              T[k] = fin0 ? 0.0f : tt0;
-              T[k + 1] = fin1 ? 0.0f : tt1;
+              f2_unpack(f2_mul(tt2, keep), T[k], T[k + 1]);
             }
           }
 #pragma unroll
