@@ -352,7 +352,15 @@ onesweep_kernel(Src src, K *__restrict__ keys_out, uint32_t *__restrict__ vals_o
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const uint32_t d = dr[k];
-    const unsigned peers = __match_any_sync(0xffffffffu, d);
+    // the lanes holding the same digit: one ballot per digit bit (the digits have at most 8),
+    // restricted to the lanes with a key
+    unsigned peers = __ballot_sync(0xffffffffu, d < 256u);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const bool bit = (d >> b) & 1u;
+      const unsigned v = __ballot_sync(0xffffffffu, bit);
+      peers &= bit ? v : ~v;
+    }
     uint32_t rank = 0, cnt = 0;
     if (d < 256u) {
       cnt = s_whist[warp][d];
