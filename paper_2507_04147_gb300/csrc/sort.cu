@@ -9,7 +9,7 @@
 // the digits of all passes at once; then each pass is ONE kernel that
 //   1. takes a partition index from an atomic counter (so partitions start in order),
 //   2. ranks its keys stably inside the CTA with warp-level multisplit
-//      (__match_any_sync + per-warp digit counters),
+//      (the peers of a digit from one ballot per digit bit + per-warp digit counters),
 //   3. publishes its per-digit counts and resolves the exclusive prefix of every digit by
 //      decoupled look-back over earlier partitions (flag + 30-bit count in one word),
 //      reading a window of 8 predecessors per step so a single wave of partitions does
