@@ -744,9 +744,52 @@ __device__ __forceinline__ void render_half(HalfSmem<kMult> &sm, const Composite
               f2_unpack(f2_mul(tt2, keep), T[k], T[k + 1]);
             }
           }
+          if constexpr (kAux && P >= 2) {
+            // the same pairs with the auxiliary outputs: the arithmetic packed, the bookkeeping
+            // (done, last contributor, stop position, blend count) per pixel
+            const f32x2 gx = f2_pack(geo.x, geo.x), gy = f2_pack(geo.y, geo.y);
+            const f32x2 ca = f2_pack(geo.z, geo.z), cb = f2_pack(geo.w, geo.w), cc = f2_pack(cz.x, cz.x);
+            const f32x2 op = f2_pack(rgb.w, rgb.w);
+            const f32x2 cr = f2_pack(rgb.x, rgb.x), cg = f2_pack(rgb.y, rgb.y), cbl = f2_pack(rgb.z, rgb.z);
+            const f32x2 cdz = f2_pack(cz.y, cz.y);
+            const f32x2 one = f2_pack(1.0f, 1.0f), mone = f2_pack(-1.0f, -1.0f);
+#pragma unroll
+            for (int k = 0; k + 1 < P; k += 2) {
+              const f32x2 dx = f2_add(gx, f2_pack(-fpx[k], -fpx[k + 1]));
+              const f32x2 dy = f2_add(gy, f2_pack(-fpy[k], -fpy[k + 1]));
+              const f32x2 pw2 = f2_fma(f2_fma(ca, dx, f2_mul(cb, dy)), dx, f2_mul(f2_mul(cc, dy), dy));
+              float pw0, pw1;
+              f2_unpack(pw2, pw0, pw1);
+              float oe0, oe1;
+              f2_unpack(f2_mul(op, f2_pack(ex2_approx(pw0), ex2_approx(pw1))), oe0, oe1);
+              const float al0 = fminf(0.99f, oe0), al1 = fminf(0.99f, oe1);
+              const f32x2 al2 = f2_pack(al0, al1), t2 = f2_pack(T[k], T[k + 1]);
+              float tt0, tt1, at0, at1;
+              f2_unpack(f2_mul(t2, f2_fma(al2, mone, one)), tt0, tt1);   // T (1 - alpha)
+              f2_unpack(f2_mul(al2, t2), at0, at1);
+              const bool ok0 = !done[k] && pw0 <= 0.0f && al0 >= 1.0f / 255.0f;
+              const bool ok1 = !done[k + 1] && pw1 <= 0.0f && al1 >= 1.0f / 255.0f;
+              const bool fin0 = ok0 && tt0 < 0.0001f, fin1 = ok1 && tt1 < 0.0001f;
+              const bool upd0 = ok0 && !fin0, upd1 = ok1 && !fin1;
+              const f32x2 w2 = f2_pack(upd0 ? at0 : 0.0f, upd1 ? at1 : 0.0f);
+              f2_unpack(f2_fma(cr, w2, f2_pack(C0[k], C0[k + 1])), C0[k], C0[k + 1]);
+              f2_unpack(f2_fma(cg, w2, f2_pack(C1[k], C1[k + 1])), C1[k], C1[k + 1]);
+              f2_unpack(f2_fma(cbl, w2, f2_pack(C2[k], C2[k + 1])), C2[k], C2[k + 1]);
+              f2_unpack(f2_fma(cdz, w2, f2_pack(Z[k], Z[k + 1])), Z[k], Z[k + 1]);
+              bl += (upd0 ? 1u : 0u) + (upd1 ? 1u : 0u);
+              T[k] = upd0 ? tt0 : T[k];
+              T[k + 1] = upd1 ? tt1 : T[k + 1];
+              last[k] = upd0 ? pos : last[k];
+              last[k + 1] = upd1 ? pos : last[k + 1];
+              stop[k] = fin0 ? pos : stop[k];
+              stop[k + 1] = fin1 ? pos : stop[k + 1];
+              done[k] = done[k] || fin0;
+              done[k + 1] = done[k + 1] || fin1;
+            }
+          }
 #pragma unroll
           for (int k = 0; k < P; ++k) {
-            if constexpr (!kAux && P >= 2) {
+            if constexpr (P >= 2) {
               if (k + 1 < P || P % 2 == 0) continue;   // done in pairs above (all but an odd last)
             }
             const float dx = __fsub_rn(geo.x, fpx[k]), dy = __fsub_rn(geo.y, fpy[k]);
@@ -757,11 +800,11 @@ __device__ __forceinline__ void render_half(HalfSmem<kMult> &sm, const Composite
               const bool ok = !done[k] && pw <= 0.0f && alpha >= 1.0f / 255.0f;
               const bool fin = ok && tt < 0.0001f;
               const bool upd = ok && !fin;
-              const float w = upd ? alpha * T[k] : 0.0f;
-              C0[k] += rgb.x * w;
-              C1[k] += rgb.y * w;
-              C2[k] += rgb.z * w;
-              Z[k] += cz.y * w;
+              const float w = upd ? __fmul_rn(alpha, T[k]) : 0.0f;
+              C0[k] = __fmaf_rn(rgb.x, w, C0[k]);
+              C1[k] = __fmaf_rn(rgb.y, w, C1[k]);
+              C2[k] = __fmaf_rn(rgb.z, w, C2[k]);
+              Z[k] = __fmaf_rn(cz.y, w, Z[k]);
               bl += upd ? 1u : 0u;
               T[k] = upd ? tt : T[k];
               last[k] = upd ? pos : last[k];
