@@ -93,16 +93,22 @@ def test_small_single_view_foveated_and_full():
     assert np.array_equal(fov[~live], tl[~live])
 
 
+@pytest.mark.parametrize("tile", [16, 32])
 @pytest.mark.parametrize("binning", [a3fr.BINNING_DIRECT, a3fr.BINNING_SORTED])
-def test_stereo_sh3_ragged_image(binning):
+def test_stereo_sh3_ragged_image(binning, tile):
+    # 200 x 136 leaves partial tiles on the right and bottom edges (at 32-pixel tiles a lane's
+    # pixel pair can straddle the image edge)
     scene = synth.uniform_scene(6000, 3, seed=3)
     cams = synth.stereo_cameras(200, 136, yaw_deg=3.0)
     gaze = np.array([[20.0, 120.0], [25.5, 118.25]], np.float32)
     ofv, gfv = fovea_params()
-    r = gh.run(scene, cams, gaze=gaze, fovea=gfv, binning=binning)
+    r = gh.run(scene, cams, gaze=gaze, fovea=gfv, binning=binning, tile=tile)
     assert r["stats"]["status"] == 0 and r["stats"]["n_eyes"] == 2
     for e in range(2):
-        print(e, check_eye(r, e, scene, cams[e], gaze=gaze[e], fv=ofv))
+        print(e, check_eye(r, e, scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv))
+    rf = gh.run(scene, cams, full=True, binning=binning, tile=tile)
+    for e in range(2):
+        print(e, "full", check_eye(rf, e, scene, cams[e], tile=tile, full=True))
 
 
 @pytest.mark.parametrize("tile", [16, 32])
