@@ -230,18 +230,20 @@ def test_repeated_renders_are_deterministic_and_counters_accumulate():
     assert 0 < st["contributions"] <= st["evaluations"]
 
 
-@pytest.mark.parametrize("tile,binning", [(16, a3fr.BINNING_SORTED), (32, a3fr.BINNING_DIRECT),
-                                         (16, a3fr.BINNING_DIRECT)])
-def test_stereo_500k_sh3_sampled_pixels(tile, binning):
+@pytest.mark.parametrize("tile,binning,full", [(16, a3fr.BINNING_SORTED, False), (32, a3fr.BINNING_DIRECT, False),
+                                              (16, a3fr.BINNING_DIRECT, False), (32, a3fr.BINNING_DIRECT, True)])
+def test_stereo_500k_sh3_sampled_pixels(tile, binning, full):
     """The benchmark workload at full size: records and keys in full, pixels sampled, under
-    both binning paths (16-pixel tiles: 12,800 tiles, 4 bands per chunk in the direct path)."""
+    both binning paths (16-pixel tiles: 12,800 tiles, 4 bands per chunk in the direct path),
+    and the benchmark's configuration (32-pixel tiles, direct binning) also at full
+    resolution."""
     w = synth.stereo_500k(frames=240)
     traj = synth.gaze_trajectory(240)
     frame = 137
     cams = w.cameras(frame)
     gaze = w.gaze(frame, traj)
     ofv, gfv = fovea_params()
-    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False, tile=tile, binning=binning)
+    r = gh.run(w.scene, cams, gaze=gaze, fovea=gfv, keep_aux=False, tile=tile, binning=binning, full=full)
     assert r["stats"]["status"] == 0
     rng = np.random.default_rng(frame)
     for e in range(2):
@@ -250,7 +252,7 @@ def test_stereo_500k_sh3_sampled_pixels(tile, binning):
         gy = int(np.clip(gaze[e][1], 0, 1279)) // tile * tile
         band = np.stack(np.meshgrid(np.arange(0, 1280, 3), np.arange(gy, gy + tile, 5)), -1).reshape(-1, 2)
         pix = np.concatenate([pix, band]).astype(np.int32)
-        print(e, check_eye(r, e, w.scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv, pixels=pix))
+        print(e, check_eye(r, e, w.scene, cams[e], tile=tile, gaze=gaze[e], fv=ofv, pixels=pix, full=full))
 
 
 @pytest.mark.parametrize("tile,full,batch_mult", [(32, False, 1), (16, False, 1), (32, True, 1), (32, False, 2)])
