@@ -18,7 +18,12 @@ the tensor-core kernels implement, as plain PyTorch CPU operations in float64 (a
   (1, 1) -- where only top-left pixels are rendered this is the interpolating fill of
   Sec. 3.4 ("inherit or interpolate"), so the network learns a correction to it.
 
-Convolutions use zero padding of one pixel; weights are [out, in, 3, 3] and rounded to BF16.
+The compact network (``forward_compact``) keeps conv0 and replaces the rest by two per-block
+layers: t = ReLU(W1 h + b1) (1x1, 32 -> 32, BF16), r = W2 t + b2 (1x1, 32 -> 16, FP32), the
+same channel meaning for r -- a prediction from the 3x3-block neighbourhood of each block.
+
+Convolutions use zero padding of one pixel; weights are [out, in, 3, 3] (1x1 layers:
+[out, in, 1, 1]) and rounded to BF16.
 Gradients are float64 autograd of the same operations with the roundings passed straight
 through (the GPU rounds its gradient tensors to BF16 as well, so the two agree to BF16
 precision, not bit for bit).
@@ -49,6 +54,9 @@ def bf16(x: torch.Tensor) -> torch.Tensor:
     return x + (r - x).detach()
 
 
+COMPACT_LAYERS = [(IN_CH, CH, 3), (CH, CH, 1), (CH, OUT_CH, 1)]   # (in, out, kernel size)
+
+
 def init_params(seed: int = 0):
     """He-initialised weights [out, in, 3, 3] (float32) and zero biases, seeded."""
     rng = np.random.default_rng(seed)
@@ -74,6 +82,34 @@ def forward(x0: torch.Tensor, ws, bs) -> torch.Tensor:
         t = bf16(F.relu(F.conv2d(h, wq[1 + 2 * b], bs[1 + 2 * b], padding=1)))
         h = bf16(h + F.conv2d(t, wq[2 + 2 * b], bs[2 + 2 * b], padding=1))
     r = F.conv2d(h, wq[N_CONV - 1], bs[N_CONV - 1], padding=1)
+    return r.permute(0, 2, 3, 1)
+
+
+def init_compact_params(seed: int = 0):
+    """He-initialised weights [out, in, k, k] (float32) and zero biases of the compact
+    network, seeded; as in the residual network the unused input channels and the last layer
+    start at zero, so the initial prediction is the base."""
+    rng = np.random.default_rng(seed)
+    ws, bs = [], []
+    for li, (cin, cout, k) in enumerate(COMPACT_LAYERS):
+        fan_in = (4 if li == 0 else cin) * k * k
+        w = rng.normal(0.0, np.sqrt(2.0 / fan_in), size=(cout, cin, k, k)).astype(np.float32)
+        if li == 0:
+            w[:, 4:] = 0.0
+        if li == len(COMPACT_LAYERS) - 1:
+            w[:] = 0.0
+        ws.append(w)
+        bs.append(np.zeros(cout, dtype=np.float32))
+    return ws, bs
+
+
+def forward_compact(x0: torch.Tensor, ws, bs) -> torch.Tensor:
+    """r [B, H2, W2, 16] (float64) of the compact network; ws [out, in, k, k], bs float64."""
+    h = bf16(x0).permute(0, 3, 1, 2)
+    wq = [bf16(w) for w in ws]
+    h = bf16(F.relu(F.conv2d(h, wq[0], bs[0], padding=1)))
+    t = bf16(F.relu(F.conv2d(h, wq[1], bs[1])))
+    r = F.conv2d(t, wq[2], bs[2])
     return r.permute(0, 2, 3, 1)
 
 
@@ -111,12 +147,14 @@ def make_input(img: np.ndarray, depth: np.ndarray):
     return x0, tl
 
 
-def loss_and_grads(x0: np.ndarray, tl: np.ndarray, target: np.ndarray, ws, bs):
-    """Mean squared error of the prediction over [B, H, W, 3] and its gradients (float64)."""
+def loss_and_grads(x0: np.ndarray, tl: np.ndarray, target: np.ndarray, ws, bs, net=None):
+    """Mean squared error of the prediction over [B, H, W, 3] and its gradients (float64);
+    ``net`` is ``forward`` (default) or ``forward_compact``."""
+    net = forward if net is None else net
     W_ = [torch.tensor(np.asarray(w, np.float64), requires_grad=True) for w in ws]
     B_ = [torch.tensor(np.asarray(b, np.float64), requires_grad=True) for b in bs]
     H, W = target.shape[1:3]
-    r = forward(torch.tensor(x0, dtype=torch.float64), W_, B_)
+    r = net(torch.tensor(x0, dtype=torch.float64), W_, B_)
     pred = shuffle(r, torch.tensor(tl, dtype=torch.float64), H, W)
     loss = ((pred - torch.tensor(target, dtype=torch.float64)) ** 2).mean()
     loss.backward()
@@ -135,4 +173,19 @@ def conv3x3_loops(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
         for xx in range(W):
             patch = xp[y:y + 3, xx:xx + 3, :]            # [3, 3, Cin]
             out[y, xx] = np.einsum("kli,okli->o", patch, w.transpose(0, 2, 3, 1)) + b
+    return out
+
+
+def conv1x1_loops(x: np.ndarray, w: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """Plain-loop per-pixel layer x [H, W, Cin] -> [H, W, Cout] with w [Cout, Cin] (float64)."""
+    H, W, cin = x.shape
+    cout = w.shape[0]
+    out = np.zeros((H, W, cout))
+    for y in range(H):
+        for xx in range(W):
+            for o in range(cout):
+                acc = b[o]
+                for i in range(cin):
+                    acc += w[o, i] * x[y, xx, i]
+                out[y, xx, o] = acc
     return out
