@@ -677,28 +677,35 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
         sc = a3fr.Scene.from_numpy(make(1_000_000, 3, seed=40 + k))
         sc.keep_aux(True)
         scenes.append(sc)
+    # the residual network and the compact one train on the same crops (peak learning rates
+    # 3e-5 and 1e-3, cosine decay to a tenth)
     net = periphery.Periphery(seed=0)
+    net_c = periphery.Periphery(seed=0, arch=periphery.COMPACT)
+    lr_peak = {"residual": 3e-5, "compact": 1e-3}
     # a fixed probe batch (not trained on) measures the loss before and after training
     probe = periphery.render_crops(scenes[0], [synth.pinhole_camera(1024, 1024, yaw_deg=41.0)], crop,
                                    batch, np.random.default_rng(99), stream=render_stream)
     torch.cuda.synchronize()
-    probe_before = net.grads(probe[0], probe[1], probe[0])[1]
+    probe_before = [n_.grads(probe[0], probe[1], probe[0])[1] for n_ in (net, net_c)]
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    losses = []
+    losses, losses_c = [], []
     with torch.cuda.stream(render_stream):
         for step in range(steps):
             sc = scenes[step % len(scenes)]
             cam = synth.pinhole_camera(1024, 1024, yaw_deg=float(rng.uniform(-30.0, 30.0)))
             imgs, deps = periphery.render_crops(sc, [cam], crop, batch, rng, stream=render_stream)
-            lr = 3e-5 * (0.1 + 0.9 * 0.5 * (1.0 + math.cos(math.pi * step / steps)))
-            loss = net.train_step(imgs, deps, imgs, lr, sync=(step % 250 == 0 or step == steps - 1),
-                                  stream=render_stream)
+            decay = 0.1 + 0.9 * 0.5 * (1.0 + math.cos(math.pi * step / steps))
+            sync = step % 250 == 0 or step == steps - 1
+            loss = net.train_step(imgs, deps, imgs, lr_peak["residual"] * decay, sync=sync, stream=render_stream)
+            loss_c = net_c.train_step(imgs, deps, imgs, lr_peak["compact"] * decay, sync=sync,
+                                      stream=render_stream)
             if loss is not None:
                 losses.append(loss)
+                losses_c.append(loss_c)
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
-    probe_after = net.grads(probe[0], probe[1], probe[0])[1]
+    probe_after = [n_.grads(probe[0], probe[1], probe[0])[1] for n_ in (net, net_c)]
     for sc in scenes:
         sc.close()
     # held-out evaluation at 2064x2208 stereo
@@ -721,8 +728,8 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
     scene.keep_aux(True)
     fv_itp = a3fr.Fovea(w.theta_deg, 0.0, (4, 2, 1), fill=a3fr.FILL_INTERPOLATE)
     itp_out = torch.empty_like(out)
-    stats = {"inherit": [], "interpolate": [], "learned": []}
-    t_render, t_fill, t_full, t_itp = [], [], [], []
+    stats = {"inherit": [], "interpolate": [], "learned": [], "learned_compact": []}
+    t_render, t_fill, t_fill_c, t_full, t_itp = [], [], [], [], []
     ev = lambda: torch.cuda.Event(enable_timing=True)
     for k, f in enumerate(np.linspace(0, 239, eval_frames).astype(int)):
         for e, c in enumerate(w.cameras(f)):
@@ -734,12 +741,17 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
             scene.render_foveated(fv, out=out, stream=render_stream)
             b.record(render_stream)
             inherit = out.clone()
+            out_c = out.clone()
             b2 = ev()
             b2.record(render_stream)
             torch.cuda.nvtx.range_push("learned_fill")   # marks the fill's kernels for profilers
             net.fill(scene, out, stream=render_stream)
             torch.cuda.nvtx.range_pop()
             c_.record(render_stream)
+            d0, d1 = ev(), ev()
+            d0.record(render_stream)
+            net_c.fill(scene, out_c, stream=render_stream)
+            d1.record(render_stream)
             levels = scene.buffer(a3fr.BUF_LEVELS, torch.uint8, stream=render_stream)
             i0, i1 = ev(), ev()
             i0.record(render_stream)
@@ -753,24 +765,32 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
         if k > 0:   # the first frame warms up
             t_render.append(a.elapsed_time(b))
             t_fill.append(b2.elapsed_time(c_))
+            t_fill_c.append(d0.elapsed_time(d1))
             t_full.append(f0.elapsed_time(f1))
             t_itp.append(i0.elapsed_time(i1))
         tl = scene.tile
         ty, tx = (H + tl - 1) // tl, (W + tl - 1) // tl
         per = (levels.reshape(eyes, ty, tx) == 1).repeat_interleave(tl, 1).repeat_interleave(tl, 2)[:, :H, :W]
-        for name, img in (("inherit", inherit), ("interpolate", itp_out), ("learned", out)):
+        for name, img in (("inherit", inherit), ("interpolate", itp_out), ("learned", out),
+                          ("learned_compact", out_c)):
             stats[name].append((periphery.psnr(img, full, per), periphery.psnr(img, full),
                                 periphery.ssim(img, full)))
     scene.close()
     net.close()
+    net_c.close()
     res = {"workload": "train: %d steps x %d crops %dx%d from four seeded 1M-G SH3 scenes; eval: %s, %d frames"
                        % (steps, batch, crop, crop, w.name, eval_frames),
-           "train_s": train_s,
-           "probe_loss_before_after": [probe_before, probe_after],
+           "networks": {"learned": "residual: ten 3x3 convs (32 channels, four residual blocks), one kernel each",
+                        "learned_compact": "compact: 3x3 conv 16->32, per-block layers 32->32 and 32->16, "
+                                           "the whole fill one fused tcgen05 kernel"},
+           "lr_peak": lr_peak,
+           "train_s_both": train_s,
+           "probe_loss_before_after": {"residual": [probe_before[0], probe_after[0]],
+                                       "compact": [probe_before[1], probe_after[1]]},
            "probe": "16 crops 256x256 of a held-out view (yaw 41 deg) of the first training scene; mean squared error",
-           "batch_loss_first_last": [losses[0], losses[-1]],
+           "batch_loss_first_last": {"residual": [losses[0], losses[-1]], "compact": [losses_c[0], losses_c[-1]]},
            "crops": steps * batch}
-    for name in ("inherit", "interpolate", "learned"):
+    for name in ("inherit", "interpolate", "learned", "learned_compact"):
         arr = np.array(stats[name])
         res[name] = {"psnr_periphery_db": float(arr[:, 0].mean()), "psnr_whole_db": float(arr[:, 1].mean()),
                      "ssim_whole": float(arr[:, 2].mean())}
@@ -778,6 +798,9 @@ def learned_periphery_section(a3fr, torch, device, render_stream, gaze_stream, s
                          "foveated_render_interpolate_p50": float(np.percentile(t_itp, 50)),
                          "learned_fill_p50": float(np.percentile(t_fill, 50)),
                          "foveated_plus_learned_fill_p50": float(np.percentile(np.array(t_render) + np.array(t_fill), 50)),
+                         "learned_compact_fill_p50": float(np.percentile(t_fill_c, 50)),
+                         "foveated_plus_learned_compact_fill_p50":
+                             float(np.percentile(np.array(t_render) + np.array(t_fill_c), 50)),
                          "full_render_p50": float(np.percentile(t_full, 50)),
                          "tiling": {"tile": tuned["tile"], "batch_mult": tuned["batch_mult"]},
                          "note": "direct launches, auxiliary outputs on (the fill reads the depth); "

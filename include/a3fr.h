@@ -325,10 +325,21 @@ int a3fr_tc_tile_gemm(const uint16_t *A, const uint16_t *B, float *D, int n, int
  * host thread. */
 typedef struct a3fr_cnn a3fr_cnn;
 
-size_t a3fr_cnn_param_count(void);
-int a3fr_cnn_create(a3fr_cnn **out);                    /* zero parameters */
+/* Architectures.  RESIDUAL: the network above.  COMPACT: 3x3 conv 16->32 + ReLU, per-block
+ * layer 32->32 + ReLU, per-block layer 32->16 (same output channels and base) -- its fill is
+ * one fused kernel with every activation kept on chip.  Parameters, layer by layer, the
+ * weights ([out][in][3][3] for 3x3 layers, [out][in] for per-block ones), then the biases. */
+#define A3FR_CNN_RESIDUAL 0
+#define A3FR_CNN_COMPACT 1
+
+size_t a3fr_cnn_param_count(void);                      /* of the RESIDUAL network */
+size_t a3fr_cnn_arch_param_count(int arch);             /* 0 for an unknown architecture */
+int a3fr_cnn_create(a3fr_cnn **out);                    /* RESIDUAL, zero parameters */
+/* A3FR_ERR_INVALID_ARG for an unknown architecture. */
+int a3fr_cnn_create_arch(a3fr_cnn **out, int arch);
 int a3fr_cnn_destroy(a3fr_cnn *net);
-/* host fp32 [a3fr_cnn_param_count()]; set resets the Adam state; both synchronous */
+/* host fp32 [a3fr_cnn_arch_param_count(arch of net)]; set resets the Adam state; both
+ * synchronous; A3FR_ERR_INVALID_ARG when count differs */
 int a3fr_cnn_set_params(a3fr_cnn *net, const float *host, size_t count);
 int a3fr_cnn_get_params(a3fr_cnn *net, float *host, size_t count);
 /* img: DEVICE fp32 [b][h][w][3], depth: DEVICE fp32 [b][h][w] (expected depth).  Runs the
@@ -338,7 +349,7 @@ int a3fr_cnn_forward(a3fr_cnn *net, const float *img, const float *depth, int b,
                      float *residual_out, void *stream);
 /* Mean squared error of the prediction (base + correction at every pixel) against
  * target (DEVICE fp32 [b][h][w][3]) and its gradient with respect to every parameter, into
- * host_grads (host fp32 [a3fr_cnn_param_count()]) and *loss; synchronous. */
+ * host_grads (host fp32 [a3fr_cnn_arch_param_count(arch of net)]) and *loss; synchronous. */
 int a3fr_cnn_grads(a3fr_cnn *net, const float *img, const float *depth, const float *target, int b,
                    int h, int w, float *host_grads, float *loss, void *stream);
 /* One Adam step (beta 0.9 / 0.999) on the same loss; *loss (optional) makes it synchronous.

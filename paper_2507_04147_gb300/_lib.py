@@ -120,6 +120,8 @@ _SIGS = {
                            ctypes.c_int, ctypes.c_void_p], ctypes.c_int),
     "a3fr_cnn_param_count": ([], ctypes.c_size_t),
     "a3fr_cnn_create": ([ctypes.POINTER(ctypes.c_void_p)], ctypes.c_int),
+    "a3fr_cnn_arch_param_count": ([ctypes.c_int], ctypes.c_size_t),
+    "a3fr_cnn_create_arch": ([ctypes.POINTER(ctypes.c_void_p), ctypes.c_int], ctypes.c_int),
     "a3fr_cnn_destroy": ([ctypes.c_void_p], ctypes.c_int),
     "a3fr_cnn_set_params": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),
     "a3fr_cnn_get_params": ([ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t], ctypes.c_int),

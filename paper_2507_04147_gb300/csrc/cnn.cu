@@ -405,6 +405,270 @@ conv3x3_tc_kernel(ConvDims d, const __nv_bfloat16 *__restrict__ X, const uint4 *
   if (warp == 0) tc::tmem_dealloc(tmem, 64);
 }
 
+// The compact network's whole fill in one persistent kernel, per 16 x 16 block tile made of two
+// halves of 8 x 16 blocks side by side, each half one MMA of M = 128 rows (row m of half h =
+// block (y0 + m / 8, x0 + 8 h + m % 8)); thread t holds row t of both halves in the epilogues:
+//   layer 0: the 3x3 convolution 16 -> 32 on the tile's 18 x 18 input halo, formed from the
+//            render: per half 9 MMAs, N 32, K 16;
+//   layer 1: the per-block layer 32 -> 32: per half 2 MMAs (K 32);
+//   layer 2: the per-block layer 32 -> 16: per half 2 MMAs, the epilogue composing the block's
+//            skipped pixels.
+// The halo sits in shared memory as [row][column][8 channels] (16 bytes per block): a half's A
+// operand for tap (ky, kx) starts ky rows, kx + 8 h columns in, its core matrices (8 blocks of
+// one row) one halo row apart (SBO).  Input channels 8..15 are zero: the MMA's second K group
+// reads the first group's blocks again (leading byte offset 0) against a zero block of weights,
+// so those products are exactly zero.  The epilogues of layers 0 and 1 read the accumulators
+// from tensor memory, add the bias, apply the ReLU, round to BF16 and write the next layer's A
+// operands to shared memory as [half][K group of 8][row][8 channels] -- K-major core matrices,
+// rows 16 bytes apart (SBO 128), K groups 2,048 bytes apart (LBO) -- so no activation leaves
+// the SM.  The per-block layers' weights are the centre taps of their 3x3 packs.  The halo's
+// FP32 colours stay beside it, so the compose step reads its top-left pixels in shared memory.
+// The three layers of a tile reuse two 32-column accumulators (one per half); the CTAs sharing
+// an SM overlap one another's serial chains, and the next tile's halo and levels load into
+// registers while this tile's layers run.  Tiles whose blocks are all fully rendered (level 4)
+// skip the network.
+constexpr int kCmpTW = 2 * kConvTW, kCmpTH = kConvTH;   // 16 x 16 blocks
+constexpr int kCmpHR = kCmpTH + 2, kCmpHC = kCmpTW + 2;
+constexpr int kCmpHalo = kCmpHR * kCmpHC * 16;       // input group 0 (BF16) per halo block
+constexpr int kCmpRgb = kCmpHR * kCmpHC * 16;        // FP32 r, g, b (and a pad) per halo block
+constexpr int kCmpW0 = 9 * 32 * 16;                  // [tap][cout][8 cin] of input group 0
+constexpr int kCmpZero = 32 * 16;                    // zero weights of input group 1
+constexpr int kCmpW1 = 4 * 32 * 16;                  // [cin group][cout][8 cin]
+constexpr int kCmpW2 = 4 * 16 * 16;
+constexpr int kCmpAct = 2 * 4 * 128 * 16;            // [half][K group][row][8]
+constexpr int kCmpSmem = kCmpHalo + kCmpRgb + kCmpW0 + kCmpZero + kCmpW1 + kCmpW2 + kCmpAct;
+constexpr int kCmpCtas = 6;                          // CTAs per SM
+static_assert(kCmpHalo % 16 == 0 && kCmpRgb % 16 == 0 && kCmpW0 % 16 == 0 && kCmpZero % 16 == 0 &&
+              kCmpW1 % 16 == 0 && kCmpW2 % 16 == 0, "operands start on 16-byte boundaries");
+
+__global__ void __launch_bounds__(128, kCmpCtas)
+compact_fill_tc_kernel(ConvDims d, const uint4 *__restrict__ W0, const uint4 *__restrict__ W1,
+                       const uint4 *__restrict__ W2, const float *__restrict__ bias,
+                       uint32_t *__restrict__ status, FillIO io) {
+  constexpr int HR = kCmpHR, HC = kCmpHC;
+  constexpr int kGPer = (HR * HC + 127) / 128;
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint8_t *const halo = smem;
+  float4 *const rgb = reinterpret_cast<float4 *>(smem + kCmpHalo);
+  uint8_t *const w0s = smem + kCmpHalo + kCmpRgb;
+  uint8_t *const zs = w0s + kCmpW0;
+  uint8_t *const w1s = zs + kCmpZero;
+  uint8_t *const w2s = w1s + kCmpW1;
+  uint8_t *const act = w2s + kCmpW2;
+  __shared__ uint32_t s_tmem;
+  __shared__ __align__(8) uint64_t s_bar;
+  __shared__ float s_bias[80];   // b0 [32], b1 [32], b2 [16]
+  const int t = threadIdx.x, warp = t >> 5;
+  const int ty = t / kConvTW, tx = t % kConvTW;   // this thread's block within a half
+  if (t < 80) s_bias[t] = bias[t];
+  const int tiles_x = (d.W + kCmpTW - 1) / kCmpTW, tiles_y = (d.H + kCmpTH - 1) / kCmpTH;
+  const int n_tiles = d.B * tiles_x * tiles_y;
+  const int my_n = (int)blockIdx.x < n_tiles ? (n_tiles - (int)blockIdx.x + (int)gridDim.x - 1) / (int)gridDim.x : 0;
+  const int lsh = io.tile == 32 ? 5 : 4;   // pixel -> tile shift (tiles of 16 or 32 pixels)
+  // a tile's origin, halo blocks (r, g, b of the top-left pixel, depth; zero outside the image)
+  // and the levels of this thread's two blocks (4 outside the image), loaded into registers
+  float4 gv[kGPer];
+  int nb = 0, ny0 = 0, nx0 = 0, lv_next[2] = {4, 4};
+  auto gather_load = [&](int k) {
+    const int tt = (int)blockIdx.x + k * (int)gridDim.x;
+    const int r = tt / tiles_x;
+    nx0 = (tt - r * tiles_x) * kCmpTW;
+    nb = r / tiles_y;
+    ny0 = (r - nb * tiles_y) * kCmpTH;
+    const float *img = io.img + (size_t)nb * io.H * io.W * 3;
+    const float *dep = io.depth + (size_t)nb * io.H * io.W;
+#pragma unroll
+    for (int j = 0; j < kGPer; ++j) {
+      const int q = t + 128 * j, rr = q / HC, c = q - rr * HC;
+      const int y = ny0 - 1 + rr, x = nx0 - 1 + c;
+      gv[j] = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+      if (q < HR * HC && y >= 0 && y < d.H && x >= 0 && x < d.W) {
+        const unsigned src = (unsigned)(2 * y) * (unsigned)io.W + (unsigned)(2 * x);
+        gv[j] = make_float4(img[3 * src], img[3 * src + 1], img[3 * src + 2], dep[src]);
+      }
+    }
+    const uint8_t *lrow = io.levels + nb * io.n_tiles + ((2 * (ny0 + ty)) >> lsh) * io.tiles_x;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int y = ny0 + ty, x = nx0 + 8 * h + tx;
+      lv_next[h] = y < d.H && x < d.W ? lrow[(2 * x) >> lsh] : 4;
+    }
+  };
+  // the BF16 operand (r, g, b, depth / 8, then zeros: the conversion of block_input's first
+  // group) ...
+  auto store_operand = [&]() {
+#pragma unroll
+    for (int j = 0; j < kGPer; ++j) {
+      const int q = t + 128 * j;
+      if (q < HR * HC) {
+        uint4 lo;
+        __nv_bfloat162 *l2 = reinterpret_cast<__nv_bfloat162 *>(&lo);
+        l2[0] = __floats2bfloat162_rn(gv[j].x, gv[j].y);
+        l2[1] = __floats2bfloat162_rn(gv[j].z, gv[j].w * 0.125f);
+        l2[2] = __floats2bfloat162_rn(0.0f, 0.0f);
+        l2[3] = l2[2];
+        *reinterpret_cast<uint4 *>(halo + (size_t)q * 16) = lo;
+      }
+    }
+  };
+  // ... and the FP32 colours
+  auto store_colours = [&]() {
+#pragma unroll
+    for (int j = 0; j < kGPer; ++j) {
+      const int q = t + 128 * j;
+      if (q < HR * HC) rgb[q] = gv[j];
+    }
+  };
+  if (warp == 0) tc::tmem_alloc(&s_tmem, 64);
+  for (int i = t; i < kCmpW0 / 16; i += 128) {   // input group 0 of each tap: the first 32 of 64 rows
+    const int tap = i / 32, row = i - tap * 32;
+    reinterpret_cast<uint4 *>(w0s)[i] = __ldg(W0 + tap * 64 + row);
+  }
+  for (int i = t; i < kCmpZero / 16; i += 128) reinterpret_cast<uint4 *>(zs)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = t; i < kCmpW1 / 16; i += 128) reinterpret_cast<uint4 *>(w1s)[i] = __ldg(W1 + i);
+  for (int i = t; i < kCmpW2 / 16; i += 128) reinterpret_cast<uint4 *>(w2s)[i] = __ldg(W2 + i);
+  if (my_n > 0) {
+    gather_load(0);
+    store_operand();
+  }
+  tc::fence_proxy_async();
+  if (t == 0) tc::mbar_init(&s_bar, 1);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = s_tmem;
+  const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+  const uint32_t h0 = tc::smem_u32(halo), a0 = tc::smem_u32(act);
+  const uint32_t b0 = tc::smem_u32(w0s), b1 = tc::smem_u32(w1s), b2 = tc::smem_u32(w2s);
+  uint32_t phase = 0;
+  // one thread waits for the MMAs (bounded); the others wait at the barrier, issuing nothing
+  auto wait_mma = [&]() {
+    if (t == 0) {
+      if (!tc::mbar_wait(&s_bar, phase)) atomicOr(status, kStatusTimeout);
+      tc::fence_before_sync();
+    }
+    phase ^= 1u;
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  // bias (+ ReLU) of both halves' 32-column accumulators, rounded to BF16 as the next layer's
+  // A operands
+  auto to_act = [&](int boff) {
+#pragma unroll 1
+    for (int h = 0; h < 2; ++h) {
+      float v[32];
+      tc::tmem_ld32(taddr + 32 * h, v);
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        uint4 pk;
+        __nv_bfloat162 *p2 = reinterpret_cast<__nv_bfloat162 *>(&pk);
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+          p2[c] = __floats2bfloat162_rn(fmaxf(v[g * 8 + 2 * c] + s_bias[boff + g * 8 + 2 * c], 0.0f),
+                                        fmaxf(v[g * 8 + 2 * c + 1] + s_bias[boff + g * 8 + 2 * c + 1], 0.0f));
+        *reinterpret_cast<uint4 *>(act + h * 8192 + g * 2048 + t * 16) = pk;
+      }
+    }
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+  };
+  // the per-block layer (N = 16 or 32) of both halves, issued by thread 0
+  auto issue_block_layer = [&](uint32_t bw0, int n) {
+    const uint32_t idesc = tc::idesc_bf16_f32(128, n);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk)
+        tc::mma_bf16(tmem + 32 * h, tc::smem_desc(a0 + h * 8192 + kk * 4096, 2048, 128),
+                     tc::smem_desc(bw0 + kk * (2 * n * 16), n * 16, 128), idesc, kk > 0);
+    tc::mma_commit(&s_bar);
+  };
+  const int bh = (io.H + 1) / 2, bw = (io.W + 1) / 2;   // blocks per column and row
+  for (int k = 0; k < my_n; ++k) {
+    const int b = nb, y0 = ny0, x0 = nx0, lv0 = lv_next[0], lv1 = lv_next[1];
+    // operand k stored and fenced by every thread; the last tile's tensor-memory reads and
+    // colour reads done
+    const bool need = __syncthreads_or(lv0 < 4 || lv1 < 4) != 0;
+    tc::fence_after_sync();
+    store_colours();   // read by this tile's compose, after the barriers below
+    if (need && t == 0) {
+      const uint32_t idesc = tc::idesc_bf16_f32(128, 32);
+#pragma unroll
+      for (int h = 0; h < 2; ++h)
+#pragma unroll
+        for (int tap = 0; tap < 9; ++tap) {
+          const int ky = tap / 3, kx = tap - 3 * ky;
+          tc::mma_bf16(tmem + 32 * h, tc::smem_desc(h0 + (ky * HC + kx + 8 * h) * 16, 0, HC * 16),
+                       tc::smem_desc(b0 + tap * 512, (9 - tap) * 512, 128), idesc, tap > 0);
+        }
+      tc::mma_commit(&s_bar);
+    }
+    if (k + 1 < my_n) gather_load(k + 1);   // in flight while this tile's layers run
+    if (need) {
+      wait_mma();
+      to_act(0);
+      if (t == 0) issue_block_layer(b1, 32);
+      wait_mma();
+      to_act(32);
+      if (t == 0) issue_block_layer(b2, 16);
+      wait_mma();
+      const int y = y0 + ty, rd = min(y + 1, bh - 1) - y0 + 1, Y = 2 * y;
+      float *const img = io.img + (size_t)b * io.H * io.W * 3;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int lv = h ? lv1 : lv0;
+        float v[16];
+        tc::tmem_ld16(taddr + 32 * h, v);
+        if (lv >= 4) continue;   // outside the image or every pixel of the block rendered
+        // the top-left pixels of the block, its right and lower neighbours and the diagonal one
+        // (the last block repeated past the edge) from the halo's colours; then the same
+        // arithmetic as compose_block
+        const int cx = tx + 8 * h, x = x0 + cx;
+        const int cr = min(x + 1, bw - 1) - x0 + 1;
+        const float4 a = rgb[(ty + 1) * HC + cx + 1], right = rgb[(ty + 1) * HC + cr];
+        const float4 down = rgb[rd * HC + cx + 1], diag = rgb[rd * HC + cr];
+        const float av[3] = {a.x, a.y, a.z}, rv[3] = {right.x, right.y, right.z};
+        const float dv[3] = {down.x, down.y, down.z}, gv3[3] = {diag.x, diag.y, diag.z};
+        const int X = 2 * x;
+        auto put = [&](int dy, int dx, const float *base, int s) {
+          if (Y + dy >= io.H || X + dx >= io.W) return;
+          float *o = img + 3 * ((unsigned)(Y + dy) * (unsigned)io.W + (unsigned)(X + dx));
+#pragma unroll
+          for (int c = 0; c < 3; ++c) o[c] = base[c] + (v[4 * c + s] + s_bias[64 + 4 * c + s]);
+        };
+        float bt[3], bb[3], bd[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          bt[c] = __fmul_rn(__fadd_rn(av[c], rv[c]), 0.5f);
+          bb[c] = __fmul_rn(__fadd_rn(av[c], dv[c]), 0.5f);
+          bd[c] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(av[c], rv[c]), dv[c]), gv3[c]), 0.25f);
+        }
+        if (lv <= 2) put(0, 1, bt, 1);   // top-right: label 3, rendered from level 3
+        float *const o1 = img + 3 * ((unsigned)(Y + 1) * (unsigned)io.W + (unsigned)X);
+        if (lv <= 1 && Y + 1 < io.H && X + 1 < io.W && (reinterpret_cast<uintptr_t>(o1) & 7u) == 0) {
+          // bottom-left and bottom-right: six consecutive floats, three 8-byte stores
+          float2 *o2 = reinterpret_cast<float2 *>(o1);
+          auto res = [&](int c, int s) { return v[4 * c + s] + s_bias[64 + 4 * c + s]; };
+          o2[0] = make_float2(bb[0] + res(0, 2), bb[1] + res(1, 2));
+          o2[1] = make_float2(bb[2] + res(2, 2), bd[0] + res(0, 3));
+          o2[2] = make_float2(bd[1] + res(1, 3), bd[2] + res(2, 3));
+        } else {
+          if (lv <= 3) put(1, 0, bb, 2);   // bottom-left: label 4, rendered at level 4
+          if (lv <= 1) put(1, 1, bd, 3);   // bottom-right: label 2, rendered from level 2
+        }
+      }
+    }
+    if (k + 1 < my_n) store_operand();   // layer 0 of this tile, if any, has completed
+    tc::fence_proxy_async();
+    tc::fence_before_sync();
+  }
+  __syncthreads();
+  tc::fence_after_sync();
+  if (warp == 0) tc::tmem_dealloc(tmem, 64);
+}
+
 // Weight gradient  dW[cout][cin][tap] += sum over pixels of X[pixel + tap][cin] dY[pixel][cout]
 // as D[(tap, cin)][cout] = A[(tap, cin)][pixel] B[cout][pixel]^T with K = pixels: per 8 x 8
 // pixel tile the CTA transposes the halo into A (K-major, one M-tile per 128 (tap, cin) rows)
@@ -622,11 +886,13 @@ __global__ void adam_kernel(float *__restrict__ p, const float *__restrict__ g, 
 
 // BF16 packs of one layer's weights W[cout][cin][9]: forward [tap][cin/8][cout][8 cin] and the
 // data-gradient conv's [tap'][cout/8][cin][8 cout] with W'[cin][cout][tap'] = W[cout][cin][8 - tap'].
-__global__ void pack_kernel(const float *__restrict__ w, int cin, int cout, __nv_bfloat16 *__restrict__ fwd,
-                            __nv_bfloat16 *__restrict__ bwd) {
-  const int n = cin * cout * 9;
+// A per-block (1x1) layer, W[cout][cin] with taps = 1, is the centre tap (4) of a 3x3 pack whose
+// other taps stay zero, so the 3x3 kernels train it unchanged.
+__global__ void pack_kernel(const float *__restrict__ w, int cin, int cout, int taps,
+                            __nv_bfloat16 *__restrict__ fwd, __nv_bfloat16 *__restrict__ bwd) {
+  const int n = cin * cout * taps;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const int tap = i % 9, rest = i / 9;
+    const int tap = taps == 9 ? i % 9 : 4, rest = taps == 9 ? i / 9 : i;
     const int ci = rest % cin, co = rest / cin;
     const __nv_bfloat16 v = __float2bfloat16_rn(w[i]);
     fwd[((size_t)(tap * (cin / 8) + ci / 8) * cout + co) * 8 + (ci & 7)] = v;
@@ -634,23 +900,30 @@ __global__ void pack_kernel(const float *__restrict__ w, int cin, int cout, __nv
   }
 }
 
+// dW[cout][cin] += the centre tap of a 3x3 weight gradient g[cout][cin][9].
+__global__ void centre_tap_kernel(const float *__restrict__ g, int n, float *__restrict__ dW) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) dW[i] += g[i * 9 + 4];
+}
 
-constexpr int kLayers = 10;
-__host__ __device__ constexpr int layer_in(int l) { return l == 0 ? 16 : 32; }
-__host__ __device__ constexpr int layer_out(int l) { return l == kLayers - 1 ? 16 : 32; }
+// Layer tables.  Residual network: ten 3x3 convolutions (16 -> 32, eight 32 -> 32, 32 -> 16).
+// Compact network: 3x3 16 -> 32, then the per-block layers 32 -> 32 and 32 -> 16.
+constexpr int kLayers = 10;   // the most layers of either network
+int n_layers(int arch) { return arch == A3FR_CNN_COMPACT ? 3 : kLayers; }
+int layer_in(int arch, int l) { return l == 0 ? 16 : 32; }
+int layer_out(int arch, int l) { return l == n_layers(arch) - 1 ? 16 : 32; }
+int layer_taps(int arch, int l) { return arch == A3FR_CNN_COMPACT && l > 0 ? 1 : 9; }
 
-size_t weight_offset(int l) {
+size_t weight_offset(int arch, int l) {
   size_t o = 0;
-  for (int k = 0; k < l; ++k) o += (size_t)layer_in(k) * layer_out(k) * 9;
+  for (int k = 0; k < l; ++k) o += (size_t)layer_in(arch, k) * layer_out(arch, k) * layer_taps(arch, k);
   return o;
 }
-size_t n_weights() { return weight_offset(kLayers); }
-size_t bias_offset(int l) {
-  size_t o = n_weights();
-  for (int k = 0; k < l; ++k) o += layer_out(k);
+size_t bias_offset(int arch, int l) {
+  size_t o = weight_offset(arch, n_layers(arch));
+  for (int k = 0; k < l; ++k) o += layer_out(arch, k);
   return o;
 }
-size_t n_params() { return bias_offset(kLayers); }
+size_t n_params(int arch) { return bias_offset(arch, n_layers(arch)); }
 
 int grid_1d(size_t n) {
   const size_t b = (n + 255) / 256;
@@ -661,7 +934,9 @@ int grid_1d(size_t n) {
 }  // namespace a3fr
 
 struct a3fr_cnn {
+  int arch = A3FR_CNN_RESIDUAL;
   float *params = nullptr, *grads = nullptr, *adam_m = nullptr, *adam_v = nullptr;
+  float *wscratch = nullptr;   // a per-block layer's 3x3 weight gradient [32][32][9]
   __nv_bfloat16 *wf[a3fr::kLayers] = {}, *wb[a3fr::kLayers] = {};
   size_t cap_px = 0;
   __nv_bfloat16 *x0 = nullptr, *h[5] = {}, *t[4] = {}, *g_r = nullptr, *gA = nullptr, *gB = nullptr, *gT = nullptr;
@@ -733,6 +1008,27 @@ cudaError_t conv(const ConvDims &d, const __nv_bfloat16 *X, const __nv_bfloat16 
   return cudaGetLastError();
 }
 
+cudaError_t compact_fill(const ConvDims &d, const a3fr_cnn *n, uint32_t *status, cudaStream_t s, const FillIO &io) {
+  static bool attr[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 0 && dev < 64 && !attr[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(compact_fill_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kCmpSmem);
+    if (e != cudaSuccess) return e;
+    attr[dev] = true;
+  }
+  const int tiles = d.B * ((d.W + kCmpTW - 1) / kCmpTW) * ((d.H + kCmpTH - 1) / kCmpTH);
+  const int grid = tiles < 152 * kCmpCtas ? tiles : 152 * kCmpCtas;
+  const int A = A3FR_CNN_COMPACT;
+  // the per-block layers' weights: the centre tap (4) of their 3x3 packs [tap][cin/8][cout][8]
+  const uint4 *w1 = reinterpret_cast<const uint4 *>(n->wf[1] + 4 * 32 * 32);
+  const uint4 *w2 = reinterpret_cast<const uint4 *>(n->wf[2] + 4 * 32 * 16);
+  compact_fill_tc_kernel<<<grid, 128, kCmpSmem, s>>>(d, reinterpret_cast<const uint4 *>(n->wf[0]), w1, w2,
+                                                     n->params + bias_offset(A, 0), status, io);
+  return cudaGetLastError();
+}
+
 template <int CIN, int COUT>
 cudaError_t wgrad(const ConvDims &d, const __nv_bfloat16 *X, const __nv_bfloat16 *dY, float *dW, float *db,
                   uint32_t *status, cudaStream_t s) {
@@ -760,47 +1056,73 @@ cudaError_t wgrad(const ConvDims &d, const __nv_bfloat16 *X, const __nv_bfloat16
   } while (0)
 
 int pack_all(a3fr_cnn *n, cudaStream_t s) {
-  for (int l = 0; l < kLayers; ++l) {
-    const int cin = layer_in(l), cout = layer_out(l);
-    pack_kernel<<<grid_1d((size_t)cin * cout * 9), 256, 0, s>>>(n->params + weight_offset(l), cin, cout,
-                                                               n->wf[l], l > 0 ? n->wb[l] : nullptr);
+  for (int l = 0; l < n_layers(n->arch); ++l) {
+    const int cin = layer_in(n->arch, l), cout = layer_out(n->arch, l), taps = layer_taps(n->arch, l);
+    pack_kernel<<<grid_1d((size_t)cin * cout * taps), 256, 0, s>>>(n->params + weight_offset(n->arch, l), cin,
+                                                                  cout, taps, n->wf[l], l > 0 ? n->wb[l] : nullptr);
     CNN_CHECK(cudaGetLastError());
   }
   return A3FR_OK;
 }
 
 // The prediction r (training, a3fr_cnn_forward: io null) or, for the fill (io set), the
-// composed image: the first convolution then reads its input from the render and the last
-// composes the skipped pixels, with neither x0 nor r stored.
+// composed image.  Residual network, fill: the first convolution reads its input from the
+// render and the last composes the skipped pixels, with neither x0 nor r stored.  Compact
+// network, fill: one fused kernel (no activation tensors at all); training: the 3x3 kernels,
+// the per-block layers as centre-tap packs.
 int forward(a3fr_cnn *n, const float *img, const float *depth, int B, int H, int W, cudaStream_t s,
             const FillIO *io = nullptr) {
   const ConvDims d{B, (H + 1) / 2, (W + 1) / 2};
   const size_t px = (size_t)d.B * d.H * d.W;
+  const int A = n->arch;
+  if (A == A3FR_CNN_COMPACT && io) {
+    CNN_CHECK(compact_fill(d, n, n->status, s, *io));
+    return A3FR_OK;
+  }
   const int rc = ensure_acts(n, px);
   if (rc != A3FR_OK) return rc;
   const float *P = n->params;
   if (io) {
-    CNN_CHECK((conv<16, 32, kSrcImage>(d, nullptr, n->wf[0], P + bias_offset(0), nullptr, nullptr, n->h[0],
+    CNN_CHECK((conv<16, 32, kSrcImage>(d, nullptr, n->wf[0], P + bias_offset(A, 0), nullptr, nullptr, n->h[0],
                                        kEpiBias | kEpiRelu, n->status, s, *io)));
   } else {
     gather_input_kernel<<<grid_1d(px), 256, 0, s>>>(img, depth, B, H, W, n->x0);
     CNN_CHECK(cudaGetLastError());
-    CNN_CHECK((conv<16, 32>(d, n->x0, n->wf[0], P + bias_offset(0), nullptr, nullptr, n->h[0],
+    CNN_CHECK((conv<16, 32>(d, n->x0, n->wf[0], P + bias_offset(A, 0), nullptr, nullptr, n->h[0],
                             kEpiBias | kEpiRelu, n->status, s)));
   }
+  if (A == A3FR_CNN_COMPACT) {
+    CNN_CHECK((conv<32, 32>(d, n->h[0], n->wf[1], P + bias_offset(A, 1), nullptr, nullptr, n->t[0],
+                            kEpiBias | kEpiRelu, n->status, s)));
+    CNN_CHECK((conv<32, 16>(d, n->t[0], n->wf[2], P + bias_offset(A, 2), nullptr, nullptr, n->r,
+                            kEpiBias | kEpiF32, n->status, s)));
+    return A3FR_OK;
+  }
   for (int b = 0; b < 4; ++b) {
-    CNN_CHECK((conv<32, 32>(d, n->h[b], n->wf[1 + 2 * b], P + bias_offset(1 + 2 * b), nullptr, nullptr,
+    CNN_CHECK((conv<32, 32>(d, n->h[b], n->wf[1 + 2 * b], P + bias_offset(A, 1 + 2 * b), nullptr, nullptr,
                             n->t[b], kEpiBias | kEpiRelu, n->status, s)));
-    CNN_CHECK((conv<32, 32>(d, n->t[b], n->wf[2 + 2 * b], P + bias_offset(2 + 2 * b), n->h[b], nullptr,
+    CNN_CHECK((conv<32, 32>(d, n->t[b], n->wf[2 + 2 * b], P + bias_offset(A, 2 + 2 * b), n->h[b], nullptr,
                             n->h[b + 1], kEpiBias | kEpiResid, n->status, s)));
   }
   if (io) {
-    CNN_CHECK((conv<32, 16, kSrcTensor, kDstCompose>(d, n->h[4], n->wf[9], P + bias_offset(9), nullptr, nullptr,
+    CNN_CHECK((conv<32, 16, kSrcTensor, kDstCompose>(d, n->h[4], n->wf[9], P + bias_offset(A, 9), nullptr, nullptr,
                                                      nullptr, kEpiBias, n->status, s, *io)));
   } else {
-    CNN_CHECK((conv<32, 16>(d, n->h[4], n->wf[9], P + bias_offset(9), nullptr, nullptr, n->r,
+    CNN_CHECK((conv<32, 16>(d, n->h[4], n->wf[9], P + bias_offset(A, 9), nullptr, nullptr, n->r,
                             kEpiBias | kEpiF32, n->status, s)));
   }
+  return A3FR_OK;
+}
+
+// Weight gradient of a per-block layer: the 3x3 kernel into the scratch, its centre tap added
+// to dW[cout][cin]; the bias gradient directly.
+template <int CIN, int COUT>
+int wgrad_1x1(a3fr_cnn *n, const ConvDims &d, const __nv_bfloat16 *X, const __nv_bfloat16 *dY, float *dW,
+              float *db, cudaStream_t s) {
+  CNN_CHECK(cudaMemsetAsync(n->wscratch, 0, sizeof(float) * CIN * COUT * 9, s));
+  CNN_CHECK((wgrad<CIN, COUT>(d, X, dY, n->wscratch, db, n->status, s)));
+  centre_tap_kernel<<<grid_1d((size_t)CIN * COUT), 256, 0, s>>>(n->wscratch, CIN * COUT, dW);
+  CNN_CHECK(cudaGetLastError());
   return A3FR_OK;
 }
 
@@ -808,27 +1130,39 @@ int forward(a3fr_cnn *n, const float *img, const float *depth, int B, int H, int
 int backward(a3fr_cnn *n, const float *img, const float *target, int B, int H, int W, cudaStream_t s) {
   const ConvDims d{B, (H + 1) / 2, (W + 1) / 2};
   const size_t px = (size_t)d.B * d.H * d.W;
+  const int A = n->arch;
   float *G = n->grads;
-  CNN_CHECK(cudaMemsetAsync(G, 0, sizeof(float) * n_params(), s));
+  CNN_CHECK(cudaMemsetAsync(G, 0, sizeof(float) * n_params(A), s));
   CNN_CHECK(cudaMemsetAsync(n->loss_acc, 0, sizeof(float), s));
   loss_kernel<<<grid_1d(px), 256, 0, s>>>(n->r, img, target, B, H, W, 1.0f / (3.0f * B * H * W), n->g_r,
                                           n->loss_acc);
   CNN_CHECK(cudaGetLastError());
-  CNN_CHECK((wgrad<32, 16>(d, n->h[4], n->g_r, G + weight_offset(9), G + bias_offset(9), n->status, s)));
+  if (A == A3FR_CNN_COMPACT) {
+    // r = W2 t + b2;  t = ReLU(W1 h + b1);  h = ReLU(conv0(x0) + b0)
+    int rc = wgrad_1x1<32, 16>(n, d, n->t[0], n->g_r, G + weight_offset(A, 2), G + bias_offset(A, 2), s);
+    if (rc != A3FR_OK) return rc;
+    CNN_CHECK((conv<16, 32>(d, n->g_r, n->wb[2], nullptr, nullptr, n->t[0], n->gA, kEpiMask, n->status, s)));
+    rc = wgrad_1x1<32, 32>(n, d, n->h[0], n->gA, G + weight_offset(A, 1), G + bias_offset(A, 1), s);
+    if (rc != A3FR_OK) return rc;
+    CNN_CHECK((conv<32, 32>(d, n->gA, n->wb[1], nullptr, nullptr, n->h[0], n->gB, kEpiMask, n->status, s)));
+    CNN_CHECK((wgrad<16, 32>(d, n->x0, n->gB, G + weight_offset(A, 0), G + bias_offset(A, 0), n->status, s)));
+    return A3FR_OK;
+  }
+  CNN_CHECK((wgrad<32, 16>(d, n->h[4], n->g_r, G + weight_offset(A, 9), G + bias_offset(A, 9), n->status, s)));
   CNN_CHECK((conv<16, 32>(d, n->g_r, n->wb[9], nullptr, nullptr, nullptr, n->gA, 0, n->status, s)));
   __nv_bfloat16 *cur = n->gA, *nxt = n->gB;
   for (int b = 3; b >= 0; --b) {
     const int l2 = 2 + 2 * b, l1 = 1 + 2 * b;
-    CNN_CHECK((wgrad<32, 32>(d, n->t[b], cur, G + weight_offset(l2), G + bias_offset(l2), n->status, s)));
+    CNN_CHECK((wgrad<32, 32>(d, n->t[b], cur, G + weight_offset(A, l2), G + bias_offset(A, l2), n->status, s)));
     CNN_CHECK((conv<32, 32>(d, cur, n->wb[l2], nullptr, nullptr, n->t[b], n->gT, kEpiMask, n->status, s)));
-    CNN_CHECK((wgrad<32, 32>(d, n->h[b], n->gT, G + weight_offset(l1), G + bias_offset(l1), n->status, s)));
+    CNN_CHECK((wgrad<32, 32>(d, n->h[b], n->gT, G + weight_offset(A, l1), G + bias_offset(A, l1), n->status, s)));
     CNN_CHECK((conv<32, 32>(d, n->gT, n->wb[l1], nullptr, cur, b == 0 ? n->h[0] : nullptr, nxt,
                             kEpiResid | (b == 0 ? kEpiMask : 0), n->status, s)));
     __nv_bfloat16 *tmp = cur;
     cur = nxt;
     nxt = tmp;
   }
-  CNN_CHECK((wgrad<16, 32>(d, n->x0, cur, G + weight_offset(0), G + bias_offset(0), n->status, s)));
+  CNN_CHECK((wgrad<16, 32>(d, n->x0, cur, G + weight_offset(A, 0), G + bias_offset(A, 0), n->status, s)));
   return A3FR_OK;
 }
 
@@ -869,23 +1203,32 @@ extern "C" int a3fr_tc_tile_gemm(const uint16_t *A, const uint16_t *B, float *D,
 
 extern "C" {
 
-size_t a3fr_cnn_param_count(void) { return n_params(); }
+size_t a3fr_cnn_param_count(void) { return n_params(A3FR_CNN_RESIDUAL); }
 
-int a3fr_cnn_create(a3fr_cnn **out) {
-  if (!out) return A3FR_ERR_INVALID_ARG;
+size_t a3fr_cnn_arch_param_count(int arch) {
+  return arch == A3FR_CNN_RESIDUAL || arch == A3FR_CNN_COMPACT ? n_params(arch) : 0;
+}
+
+int a3fr_cnn_create(a3fr_cnn **out) { return a3fr_cnn_create_arch(out, A3FR_CNN_RESIDUAL); }
+
+int a3fr_cnn_create_arch(a3fr_cnn **out, int arch) {
+  if (!out || (arch != A3FR_CNN_RESIDUAL && arch != A3FR_CNN_COMPACT)) return A3FR_ERR_INVALID_ARG;
   *out = nullptr;
   a3fr_cnn *n = new (std::nothrow) a3fr_cnn();
   if (!n) return A3FR_ERR_OOM;
-  const size_t np = n_params();
+  n->arch = arch;
+  const size_t np = n_params(arch);
   bool ok = cudaMalloc(&n->params, np * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->grads, np * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->adam_m, np * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->adam_v, np * sizeof(float)) == cudaSuccess &&
+            cudaMalloc(&n->wscratch, 32 * 32 * 9 * sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->loss_acc, sizeof(float)) == cudaSuccess &&
             cudaMalloc(&n->status, sizeof(uint32_t)) == cudaSuccess;
-  for (int l = 0; l < kLayers && ok; ++l) {
-    const size_t w = (size_t)layer_in(l) * layer_out(l) * 9 * sizeof(__nv_bfloat16);
-    ok = cudaMalloc(&n->wf[l], w) == cudaSuccess && cudaMalloc(&n->wb[l], w) == cudaSuccess;
+  for (int l = 0; l < n_layers(arch) && ok; ++l) {   // 3x3 packs (a per-block layer: its centre tap)
+    const size_t w = (size_t)layer_in(arch, l) * layer_out(arch, l) * 9 * sizeof(__nv_bfloat16);
+    ok = cudaMalloc(&n->wf[l], w) == cudaSuccess && cudaMalloc(&n->wb[l], w) == cudaSuccess &&
+         cudaMemset(n->wf[l], 0, w) == cudaSuccess && cudaMemset(n->wb[l], 0, w) == cudaSuccess;
   }
   if (ok) ok = cudaMemset(n->params, 0, np * sizeof(float)) == cudaSuccess &&
                cudaMemset(n->adam_m, 0, np * sizeof(float)) == cudaSuccess &&
@@ -908,6 +1251,7 @@ int a3fr_cnn_destroy(a3fr_cnn *n) {
   dfree2(n->grads);
   dfree2(n->adam_m);
   dfree2(n->adam_v);
+  dfree2(n->wscratch);
   dfree2(n->loss_acc);
   dfree2(n->status);
   for (int l = 0; l < kLayers; ++l) {
@@ -919,7 +1263,7 @@ int a3fr_cnn_destroy(a3fr_cnn *n) {
 }
 
 int a3fr_cnn_set_params(a3fr_cnn *n, const float *host, size_t count) {
-  if (!n || !host || count != n_params()) return A3FR_ERR_INVALID_ARG;
+  if (!n || !host || count != n_params(n->arch)) return A3FR_ERR_INVALID_ARG;
   CNN_CHECK(cudaMemcpy(n->params, host, count * sizeof(float), cudaMemcpyHostToDevice));
   CNN_CHECK(cudaMemset(n->adam_m, 0, count * sizeof(float)));
   CNN_CHECK(cudaMemset(n->adam_v, 0, count * sizeof(float)));
@@ -931,7 +1275,7 @@ int a3fr_cnn_set_params(a3fr_cnn *n, const float *host, size_t count) {
 }
 
 int a3fr_cnn_get_params(a3fr_cnn *n, float *host, size_t count) {
-  if (!n || !host || count != n_params()) return A3FR_ERR_INVALID_ARG;
+  if (!n || !host || count != n_params(n->arch)) return A3FR_ERR_INVALID_ARG;
   CNN_CHECK(cudaDeviceSynchronize());
   CNN_CHECK(cudaMemcpy(host, n->params, count * sizeof(float), cudaMemcpyDeviceToHost));
   return A3FR_OK;
@@ -957,7 +1301,7 @@ int a3fr_cnn_grads(a3fr_cnn *n, const float *img, const float *depth, const floa
   int rc = forward(n, img, depth, b, h, w, s);
   if (rc == A3FR_OK) rc = backward(n, img, target, b, h, w, s);
   if (rc != A3FR_OK) return rc;
-  CNN_CHECK(cudaMemcpyAsync(host_grads, n->grads, n_params() * sizeof(float), cudaMemcpyDeviceToHost, s));
+  CNN_CHECK(cudaMemcpyAsync(host_grads, n->grads, n_params(n->arch) * sizeof(float), cudaMemcpyDeviceToHost, s));
   float acc = 0.0f;
   CNN_CHECK(cudaMemcpyAsync(&acc, n->loss_acc, sizeof(float), cudaMemcpyDeviceToHost, s));
   rc = read_status(n, s);
@@ -975,8 +1319,8 @@ int a3fr_cnn_train_step(a3fr_cnn *n, const float *img, const float *depth, const
   n->step++;
   const float b1 = 0.9f, b2 = 0.999f;
   const float c1 = 1.0f / (1.0f - powf(b1, (float)n->step)), c2 = 1.0f / (1.0f - powf(b2, (float)n->step));
-  adam_kernel<<<grid_1d(n_params()), 256, 0, s>>>(n->params, n->grads, n->adam_m, n->adam_v, (int)n_params(),
-                                                  lr, b1, b2, 1e-8f, c1, c2);
+  adam_kernel<<<grid_1d(n_params(n->arch)), 256, 0, s>>>(n->params, n->grads, n->adam_m, n->adam_v,
+                                                         (int)n_params(n->arch), lr, b1, b2, 1e-8f, c1, c2);
   CNN_CHECK(cudaGetLastError());
   rc = pack_all(n, s);
   if (rc != A3FR_OK) return rc;

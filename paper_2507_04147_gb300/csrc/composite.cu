@@ -970,47 +970,63 @@ composite_px_kernel(const CompositeParams *__restrict__ pp, const float *__restr
 // tile's level skipped becomes the mean of its rendered 4-neighbours (summed up, down, left,
 // right), else of its rendered diagonal neighbours (up-left, up-right, down-left, down-right),
 // else keeps the inherited top-left value.  Reads only rendered pixels and writes only skipped
-// ones, so the pixels of one launch never race.
-__device__ __forceinline__ bool rendered_px(const CompositeParams &p, const uint8_t *levels, int e, int x,
-                                            int y) {
+// ones, so the pixels of one launch never race.  Tiles are 16 or 32 pixels (shift `sh`).
+__device__ __forceinline__ bool rendered_px(const CompositeParams &p, const uint8_t *__restrict__ levels, int sh,
+                                            int e, int x, int y) {
   if (x < 0 || y < 0 || x >= p.width || y >= p.height) return false;
   const int bx = x & 1, by = y & 1;
   const int lab = bx == by ? (bx ? 1 : 0) : (bx ? 2 : 3);
-  return lab < levels[e * p.n_tiles + (y / p.tile) * p.tiles_x + x / p.tile];
+  return lab < __ldg(levels + e * p.n_tiles + (y >> sh) * p.tiles_x + (x >> sh));
 }
 
+__device__ __forceinline__ void fill_px(const CompositeParams &p, const uint8_t *__restrict__ levels, int sh,
+                                        float *out, int e, int x, int y) {
+  if (x >= p.width || y >= p.height) return;
+  const int nb[2][4][2] = {{{0, -1}, {0, 1}, {-1, 0}, {1, 0}}, {{-1, -1}, {1, -1}, {-1, 1}, {1, 1}}};
+  const size_t row = (size_t)e * p.height;
+#pragma unroll
+  for (int ring = 0; ring < 2; ++ring) {
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    int cnt = 0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int xx = x + nb[ring][k][0], yy = y + nb[ring][k][1];
+      if (!rendered_px(p, levels, sh, e, xx, yy)) continue;
+      const float *q = out + ((row + yy) * p.width + xx) * 3;
+      a0 = __fadd_rn(a0, q[0]);
+      a1 = __fadd_rn(a1, q[1]);
+      a2 = __fadd_rn(a2, q[2]);
+      ++cnt;
+    }
+    if (cnt) {
+      const float c = (float)cnt;
+      float *o = out + ((row + y) * p.width + x) * 3;
+      o[0] = __fdiv_rn(a0, c);
+      o[1] = __fdiv_rn(a1, c);
+      o[2] = __fdiv_rn(a2, c);
+      return;
+    }
+  }
+}
+
+// One thread per 2x2 block: its skipped pixels are top-right (label 2) below level 3,
+// bottom-left (label 3) below level 4 and bottom-right (label 1) at level 1.
 __global__ void __launch_bounds__(256)
 fill_kernel(const CompositeParams *__restrict__ pp, const uint8_t *__restrict__ levels) {
   pdl_begin();
   const CompositeParams &p = *pp;
   float *out = p.out;
-  const size_t total = (size_t)p.n_eyes * p.height * p.width;
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
-    const int x = (int)(i % p.width);
-    const size_t r = i / p.width;
-    const int y = (int)(r % p.height), e = (int)(r / p.height);
-    if (rendered_px(p, levels, e, x, y)) continue;
-    const int nb[2][4][2] = {{{0, -1}, {0, 1}, {-1, 0}, {1, 0}}, {{-1, -1}, {1, -1}, {-1, 1}, {1, 1}}};
-    for (int ring = 0; ring < 2; ++ring) {
-      float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-      int cnt = 0;
-      for (int k = 0; k < 4; ++k) {
-        const int xx = x + nb[ring][k][0], yy = y + nb[ring][k][1];
-        if (!rendered_px(p, levels, e, xx, yy)) continue;
-        const float *q = out + (((size_t)e * p.height + yy) * p.width + xx) * 3;
-        a0 = __fadd_rn(a0, q[0]);
-        a1 = __fadd_rn(a1, q[1]);
-        a2 = __fadd_rn(a2, q[2]);
-        ++cnt;
-      }
-      if (cnt) {
-        const float c = (float)cnt;
-        out[3 * i] = __fdiv_rn(a0, c);
-        out[3 * i + 1] = __fdiv_rn(a1, c);
-        out[3 * i + 2] = __fdiv_rn(a2, c);
-        break;
-      }
-    }
+  const int sh = p.tile == 32 ? 5 : 4;
+  const unsigned W2 = (unsigned)(p.width + 1) >> 1, H2 = (unsigned)(p.height + 1) >> 1;
+  const unsigned total = (unsigned)p.n_eyes * W2 * H2;
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const unsigned r = i / W2, x2 = i - r * W2;
+    const unsigned e = r / H2, y2 = r - e * H2;
+    const int x = (int)(2 * x2), y = (int)(2 * y2);
+    const int lv = __ldg(levels + e * p.n_tiles + (y >> sh) * p.tiles_x + (x >> sh));
+    if (lv <= 2) fill_px(p, levels, sh, out, (int)e, x + 1, y);
+    if (lv <= 3) fill_px(p, levels, sh, out, (int)e, x, y + 1);
+    if (lv <= 1) fill_px(p, levels, sh, out, (int)e, x + 1, y + 1);
   }
 }
 
@@ -1025,7 +1041,7 @@ size_t plan_bytes(int n_ranges) {
 
 cudaError_t launch_fill(const CompositeParams &p, const CompositeParams *p_dev, const uint8_t *levels,
                         cudaStream_t s) {
-  const size_t total = (size_t)p.n_eyes * p.height * p.width;
+  const size_t total = (size_t)p.n_eyes * ((p.height + 1) / 2) * ((p.width + 1) / 2);   // 2x2 blocks
   if (total == 0) return cudaSuccess;
   const size_t want = (total + 255) / 256;
   const int grid = (int)(want < 152 * 16 ? want : 152 * 16);

@@ -13,21 +13,26 @@ import numpy as np
 
 from . import _lib, _ptr, _stream_ptr, _torch
 
-LAYERS = [(16, 32)] + [(32, 32)] * 8 + [(32, 16)]   # (in, out) channels of the ten 3x3 convs
+RESIDUAL, COMPACT = 0, 1   # A3FR_CNN_RESIDUAL, A3FR_CNN_COMPACT
+# (in, out, kernel size) of each layer: ten 3x3 convs; or a 3x3 conv and two per-block layers
+ARCH_LAYERS = {RESIDUAL: [(16, 32, 3)] + [(32, 32, 3)] * 8 + [(32, 16, 3)],
+               COMPACT: [(16, 32, 3), (32, 32, 1), (32, 16, 1)]}
+LAYERS = [(i, o) for i, o, _ in ARCH_LAYERS[RESIDUAL]]
 
 
-def init_params(seed: int = 0) -> np.ndarray:
+def init_params(seed: int = 0, arch: int = RESIDUAL) -> np.ndarray:
     """He-initialised parameters (flat fp32): input channels 4..15 of layer 0 are zero and the
     last layer is zero, so the initial prediction is its bilinear base exactly (the
     interpolating fill of the periphery) and training only refines it."""
     rng = np.random.default_rng(seed)
+    layers = ARCH_LAYERS[arch]
     ws, bs = [], []
-    for li, (cin, cout) in enumerate(LAYERS):
-        fan_in = (4 if li == 0 else cin) * 9
-        w = rng.normal(0.0, math.sqrt(2.0 / fan_in), size=(cout, cin, 3, 3)).astype(np.float32)
+    for li, (cin, cout, k) in enumerate(layers):
+        fan_in = (4 if li == 0 else cin) * k * k
+        w = rng.normal(0.0, math.sqrt(2.0 / fan_in), size=(cout, cin, k, k)).astype(np.float32)
         if li == 0:
             w[:, 4:] = 0.0
-        if li == len(LAYERS) - 1:
+        if li == len(layers) - 1:
             w[:] = 0.0
         ws.append(w)
         bs.append(np.zeros(cout, dtype=np.float32))
@@ -39,13 +44,15 @@ def pack(ws, bs) -> np.ndarray:
                           [np.asarray(b, np.float32).ravel() for b in bs])
 
 
-def unpack(flat: np.ndarray):
+def unpack(flat: np.ndarray, arch: int = RESIDUAL):
+    """(weights [out, in, k, k], biases) of a flat parameter vector."""
     ws, bs, o = [], [], 0
-    for cin, cout in LAYERS:
-        n = cin * cout * 9
-        ws.append(flat[o:o + n].reshape(cout, cin, 3, 3))
+    layers = ARCH_LAYERS[arch]
+    for cin, cout, k in layers:
+        n = cin * cout * k * k
+        ws.append(flat[o:o + n].reshape(cout, cin, k, k))
         o += n
-    for _, cout in LAYERS:
+    for _, cout, _ in layers:
         bs.append(flat[o:o + cout])
         o += cout
     return ws, bs
@@ -54,13 +61,14 @@ def unpack(flat: np.ndarray):
 class Periphery:
     """A network object of the library (parameters, Adam state and workspaces on the GPU)."""
 
-    def __init__(self, params: np.ndarray | None = None, seed: int = 0):
+    def __init__(self, params: np.ndarray | None = None, seed: int = 0, arch: int = RESIDUAL):
         L = _lib.load()
         h = ctypes.c_void_p()
-        _lib.check(L.a3fr_cnn_create(ctypes.byref(h)), "a3fr_cnn_create")
+        _lib.check(L.a3fr_cnn_create_arch(ctypes.byref(h), int(arch)), "a3fr_cnn_create_arch")
         self.handle = h.value
-        self.n_params = int(L.a3fr_cnn_param_count())
-        self.set_params(init_params(seed) if params is None else params)
+        self.arch = int(arch)
+        self.n_params = int(L.a3fr_cnn_arch_param_count(self.arch))
+        self.set_params(init_params(seed, self.arch) if params is None else params)
 
     def set_params(self, flat: np.ndarray) -> None:
         flat = np.ascontiguousarray(flat, dtype=np.float32)

@@ -414,12 +414,13 @@ def test_autotune_picks_a_configuration_and_renders_it():
 
 
 @pytest.mark.parametrize("tile", [16, 32])
-def test_interpolating_fill(tile):
+@pytest.mark.parametrize("width,height", [(200, 136), (201, 137)])
+def test_interpolating_fill(tile, width, height):
     """Skipped pixels interpolated from rendered neighbours: bit-equal to the oracle's rule
     applied to the GPU's rendered pixels, rendered pixels unchanged, and within the pixel
-    tolerance of the oracle's own filled image."""
+    tolerance of the oracle's own filled image.  Odd sizes cut the last blocks."""
     scene = synth.uniform_scene(6000, 3, seed=3)
-    cams = synth.stereo_cameras(200, 136, yaw_deg=3.0)
+    cams = synth.stereo_cameras(width, height, yaw_deg=3.0)
     gaze = np.array([[60.0, 70.0], [58.5, 70.0]], np.float32)
     ofv = oracle.fovea((18.0, 36.0), 0.0, (4, 2, 1))
     inh = gh.run(scene, cams, gaze=gaze, fovea=a3fr.Fovea((18.0, 36.0), 0.0, (4, 2, 1)), tile=tile)
@@ -428,7 +429,7 @@ def test_interpolating_fill(tile):
     for e in range(2):
         lv = oracle.level_map(cams[e], tile, ofv, gaze[e])
         ref = oracle.render(*oracle.preprocess(scene, cams[e], tile)[:2], cams[e], tile, level=lv)
-        live = ref.rendered.reshape(136, 200).astype(bool)
+        live = ref.rendered.reshape(height, width).astype(bool)
         assert np.array_equal(itp["img"][e][live], inh["img"][e][live])
         exact = oracle.fill_interpolate(inh["img"][e], live)
         assert np.array_equal(itp["img"][e], exact)
@@ -438,9 +439,62 @@ def test_interpolating_fill(tile):
         gh.compare_pixels(inh["img"][e].reshape(-1, 3), ref)
         g = inh["img"][e].reshape(-1, 3).astype(np.float64)
         alt = ((ref.margin < gh.DELTA) & (np.abs(g - ref.rgb_alt).max(1) < np.abs(g - ref.rgb).max(1)))
-        chosen = np.where(alt[:, None], ref.rgb_alt, ref.rgb).reshape(136, 200, 3)
+        chosen = np.where(alt[:, None], ref.rgb_alt, ref.rgb).reshape(height, width, 3)
         filled_ref = oracle.fill_interpolate(chosen, live)
         assert np.abs(itp["img"][e] - filled_ref).max() <= gh.TOL
+
+
+def test_interpolating_fill_3m_full_size_sampled():
+    """The interpolating fill on the 3M clustered stereo 2064x2208 frame (32-pixel tiles):
+    every rendered pixel unchanged, and sampled skipped pixels -- random ones plus every pixel
+    of the tile row through the gaze and of the tile boundaries it crosses -- bit-equal to the
+    oracle's rule applied to the pixel's neighbourhood in the inherit render (a window of
+    3x3 pixels cut at the image edge, as the image cuts the rule)."""
+    import torch
+    w = synth.stereo_3m_clustered(frames=240)
+    traj = synth.gaze_trajectory(240)
+    frame = 97
+    cams = w.cameras(frame)
+    gaze = w.gaze(frame, traj)
+    ofv, gfv = fovea_params()
+    tile = 32
+    s = a3fr.Scene.from_numpy(w.scene, tile=tile)
+    for e, c in enumerate(cams):
+        s.set_camera(e, c)
+    s.set_gaze(gaze)
+    inh = s.render_foveated(gfv).clone()
+    itp = s.render_foveated(a3fr.Fovea((18.0, 36.0), 0.0, (4, 2, 1), fill=a3fr.FILL_INTERPOLATE)).clone()
+    st = s.stats()
+    torch.cuda.synchronize()
+    s.close()
+    assert st["status"] == 0
+    inh, itp = inh.cpu().numpy(), itp.cpu().numpy()
+    W, H = cams[0].width, cams[0].height
+    ys, xs = np.mgrid[0:H, 0:W]
+    label = np.where((xs & 1) == (ys & 1), np.where(xs & 1, 1, 0), np.where(xs & 1, 2, 3))
+    rng = np.random.default_rng(frame)
+    for e in range(2):
+        lv = oracle.level_map(cams[e], tile, ofv, gaze[e]).reshape(oracle.tiles(H, tile), oracle.tiles(W, tile))
+        live = label < lv[ys // tile, xs // tile]
+        assert (~live).any() and live.any()
+        assert np.array_equal(itp[e][live], inh[e][live])
+        skipped = np.argwhere(~live)                                   # (y, x)
+        pick = [skipped[rng.choice(len(skipped), 3000, replace=False)]]
+        gy = int(np.clip(gaze[e][1], 0, H - 1)) // tile * tile
+        row = skipped[(skipped[:, 0] >= gy) & (skipped[:, 0] < gy + tile)]
+        pick.append(row[::3])
+        edge = skipped[((skipped[:, 1] % tile) == 0) | ((skipped[:, 1] % tile) == tile - 1) |
+                       ((skipped[:, 0] % tile) == 0) | ((skipped[:, 0] % tile) == tile - 1)]
+        pick.append(edge[rng.choice(len(edge), 2000, replace=False)])
+        pick.append(np.array([[H - 1, W - 1], [H - 1, 0], [0, W - 1]]))
+        bad = 0
+        for y, x in np.concatenate(pick):
+            if live[y, x]:
+                continue
+            y0, y1, x0, x1 = max(y - 1, 0), min(y + 2, H), max(x - 1, 0), min(x + 2, W)
+            want = oracle.fill_interpolate(inh[e][y0:y1, x0:x1], live[y0:y1, x0:x1])[y - y0, x - x0]
+            bad += int(not np.array_equal(itp[e][y, x], want))
+        assert bad == 0, (e, bad)
 
 
 @pytest.mark.parametrize("tile", [16, 32])
