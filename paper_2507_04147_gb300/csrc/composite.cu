@@ -970,63 +970,100 @@ composite_px_kernel(const CompositeParams *__restrict__ pp, const float *__restr
 // tile's level skipped becomes the mean of its rendered 4-neighbours (summed up, down, left,
 // right), else of its rendered diagonal neighbours (up-left, up-right, down-left, down-right),
 // else keeps the inherited top-left value.  Reads only rendered pixels and writes only skipped
-// ones, so the pixels of one launch never race.  Tiles are 16 or 32 pixels (shift `sh`).
-__device__ __forceinline__ bool rendered_px(const CompositeParams &p, const uint8_t *__restrict__ levels, int sh,
-                                            int e, int x, int y) {
-  if (x < 0 || y < 0 || x >= p.width || y >= p.height) return false;
-  const int bx = x & 1, by = y & 1;
-  const int lab = bx == by ? (bx ? 1 : 0) : (bx ? 2 : 3);
-  return lab < __ldg(levels + e * p.n_tiles + (y >> sh) * p.tiles_x + (x >> sh));
+// ones, so the pixels of one launch never race.
+//
+// One thread per 2x2 block at (x, y) = (2 x2, 2 y2).  A pixel is rendered when its label --
+// top-left 0, bottom-right 1, top-right 2, bottom-left 3 -- is below the level of its tile.
+// The thread loads the levels of the blocks around its own once (L[by][bx], block offsets
+// -1..1; 0 outside the image: nothing rendered there); every neighbour of a skipped pixel lies
+// at a fixed offset, so its label and block are compile-time constants.
+struct FillCtx {
+  const float *p;   // pixel (x, y) of the eye's image
+  int L[3][3];      // levels of the blocks at offsets (bx - 1, by - 1)
+  int room_x, room_y, W;   // pixels from x to the right edge, from y to the bottom edge; width
+};
+
+template <int OX, int OY>
+__device__ __forceinline__ bool fill_rendered(const FillCtx &c) {
+  constexpr int bx = (OX + 2) >> 1, by = (OY + 2) >> 1;   // offsets -1 | 0, 1 | 2 -> 0 | 1 | 2
+  constexpr int px = OX & 1, py = OY & 1;
+  constexpr int lab = px == py ? px : (px ? 2 : 3);
+  return OX < c.room_x && OY < c.room_y && lab < c.L[by][bx];   // negative offsets: L is 0 outside
 }
 
-__device__ __forceinline__ void fill_px(const CompositeParams &p, const uint8_t *__restrict__ levels, int sh,
-                                        float *out, int e, int x, int y) {
-  if (x >= p.width || y >= p.height) return;
-  const int nb[2][4][2] = {{{0, -1}, {0, 1}, {-1, 0}, {1, 0}}, {{-1, -1}, {1, -1}, {-1, 1}, {1, 1}}};
-  const size_t row = (size_t)e * p.height;
-#pragma unroll
-  for (int ring = 0; ring < 2; ++ring) {
-    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-    int cnt = 0;
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int xx = x + nb[ring][k][0], yy = y + nb[ring][k][1];
-      if (!rendered_px(p, levels, sh, e, xx, yy)) continue;
-      const float *q = out + ((row + yy) * p.width + xx) * 3;
-      a0 = __fadd_rn(a0, q[0]);
-      a1 = __fadd_rn(a1, q[1]);
-      a2 = __fadd_rn(a2, q[2]);
-      ++cnt;
-    }
-    if (cnt) {
-      const float c = (float)cnt;
-      float *o = out + ((row + y) * p.width + x) * 3;
-      o[0] = __fdiv_rn(a0, c);
-      o[1] = __fdiv_rn(a1, c);
-      o[2] = __fdiv_rn(a2, c);
-      return;
-    }
+template <int OX, int OY>
+__device__ __forceinline__ void fill_add(const FillCtx &c, float &a0, float &a1, float &a2, int &cnt) {
+  if (!fill_rendered<OX, OY>(c)) return;
+  const float *q = c.p + 3 * (OY * c.W + OX);
+  a0 = __fadd_rn(a0, q[0]);
+  a1 = __fadd_rn(a1, q[1]);
+  a2 = __fadd_rn(a2, q[2]);
+  ++cnt;
+}
+
+template <int PX, int PY>
+__device__ __forceinline__ void fill_px(const FillCtx &c, float *out_px) {
+  if (PX >= c.room_x || PY >= c.room_y) return;
+  float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+  int cnt = 0;
+  fill_add<PX, PY - 1>(c, a0, a1, a2, cnt);   // up
+  fill_add<PX, PY + 1>(c, a0, a1, a2, cnt);   // down
+  fill_add<PX - 1, PY>(c, a0, a1, a2, cnt);   // left
+  fill_add<PX + 1, PY>(c, a0, a1, a2, cnt);   // right
+  if (!cnt) {
+    fill_add<PX - 1, PY - 1>(c, a0, a1, a2, cnt);   // up-left
+    fill_add<PX + 1, PY - 1>(c, a0, a1, a2, cnt);   // up-right
+    fill_add<PX - 1, PY + 1>(c, a0, a1, a2, cnt);   // down-left
+    fill_add<PX + 1, PY + 1>(c, a0, a1, a2, cnt);   // down-right
+  }
+  if (cnt) {
+    const float n = (float)cnt;
+    float *o = out_px + 3 * (PY * c.W + PX);
+    o[0] = __fdiv_rn(a0, n);
+    o[1] = __fdiv_rn(a1, n);
+    o[2] = __fdiv_rn(a2, n);
   }
 }
 
-// One thread per 2x2 block: its skipped pixels are top-right (label 2) below level 3,
-// bottom-left (label 3) below level 4 and bottom-right (label 1) at level 1.
+// Skipped pixels of a block: top-right (label 2) below level 3, bottom-left (label 3) below
+// level 4, bottom-right (label 1) at level 1.
 __global__ void __launch_bounds__(256)
 fill_kernel(const CompositeParams *__restrict__ pp, const uint8_t *__restrict__ levels) {
   pdl_begin();
   const CompositeParams &p = *pp;
   float *out = p.out;
-  const int sh = p.tile == 32 ? 5 : 4;
-  const unsigned W2 = (unsigned)(p.width + 1) >> 1, H2 = (unsigned)(p.height + 1) >> 1;
+  const int sh = p.tile == 32 ? 5 : 4;   // tiles of 16 or 32 pixels
+  const int W = p.width, H = p.height;
+  const unsigned W2 = (unsigned)(W + 1) >> 1, H2 = (unsigned)(H + 1) >> 1;
   const unsigned total = (unsigned)p.n_eyes * W2 * H2;
   for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
     const unsigned r = i / W2, x2 = i - r * W2;
     const unsigned e = r / H2, y2 = r - e * H2;
     const int x = (int)(2 * x2), y = (int)(2 * y2);
-    const int lv = __ldg(levels + e * p.n_tiles + (y >> sh) * p.tiles_x + (x >> sh));
-    if (lv <= 2) fill_px(p, levels, sh, out, (int)e, x + 1, y);
-    if (lv <= 3) fill_px(p, levels, sh, out, (int)e, x, y + 1);
-    if (lv <= 1) fill_px(p, levels, sh, out, (int)e, x + 1, y + 1);
+    const uint8_t *lv_e = levels + e * p.n_tiles;
+    const int lv = __ldg(lv_e + (y >> sh) * p.tiles_x + (x >> sh));
+    if (lv >= 4) continue;
+    FillCtx c;
+    c.W = W;
+    c.room_x = W - x;
+    c.room_y = H - y;
+    c.p = out + 3 * ((size_t)e * H * W + (unsigned)y * (unsigned)W + (unsigned)x);
+#pragma unroll
+    for (int by = 0; by < 3; ++by) {
+      const int yy = y + 2 * (by - 1);
+      const bool yin = yy >= 0 && yy < H;
+      const int row = (yy >> sh) * p.tiles_x;
+#pragma unroll
+      for (int bx = 0; bx < 3; ++bx) {
+        const int xx = x + 2 * (bx - 1);
+        c.L[by][bx] = (by == 1 && bx == 1) ? lv
+                      : (yin && xx >= 0 && xx < W && !(by == 0 && bx == 0)) ? __ldg(lv_e + row + (xx >> sh)) : 0;
+      }
+    }
+    float *o = out + 3 * ((size_t)e * H * W + (unsigned)y * (unsigned)W + (unsigned)x);
+    if (lv <= 2) fill_px<1, 0>(c, o);
+    if (lv <= 3) fill_px<0, 1>(c, o);
+    if (lv <= 1) fill_px<1, 1>(c, o);
   }
 }
 
