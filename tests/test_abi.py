@@ -78,6 +78,21 @@ def test_invalid_arguments_rejected_before_cuda(lib):
     assert lib.a3fr_sort_pairs_workspace_bytes(10**6) > 0
 
 
+def test_periphery_parameter_counts_match_the_layer_tables(lib):
+    """Host-only arithmetic of the library: the flat parameter count of each network equals
+    the Python layer tables' (weights [out][in][k][k], then biases); unknown ones are 0 and
+    cannot be created."""
+    from paper_2507_04147_gb300 import periphery
+    for arch, layers in periphery.ARCH_LAYERS.items():
+        want = sum(i * o * k * k + o for i, o, k in layers)
+        assert lib.a3fr_cnn_arch_param_count(arch) == want
+    assert lib.a3fr_cnn_param_count() == lib.a3fr_cnn_arch_param_count(periphery.RESIDUAL)
+    assert lib.a3fr_cnn_arch_param_count(7) == 0
+    out = ctypes.c_void_p()
+    assert lib.a3fr_cnn_create_arch(ctypes.byref(out), 7) == -1
+    assert lib.a3fr_cnn_create_arch(None, periphery.COMPACT) == -1
+
+
 def test_missing_library_fails_loudly(tmp_path):
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         _lib.load.__wrapped__(str(tmp_path / "nope.so")) if hasattr(_lib.load, "__wrapped__") \
