@@ -981,6 +981,7 @@ struct FillCtx {
   const float *p;   // pixel (x, y) of the eye's image
   int L[3][3];      // levels of the blocks at offsets (bx - 1, by - 1)
   int room_x, room_y, W;   // pixels from x to the right edge, from y to the bottom edge; width
+  float tl[2][2][3];       // colours of the top-left pixels at offsets (0|2, 0|2), if inside
 };
 
 template <int OX, int OY>
@@ -994,10 +995,20 @@ __device__ __forceinline__ bool fill_rendered(const FillCtx &c) {
 template <int OX, int OY>
 __device__ __forceinline__ void fill_add(const FillCtx &c, float &a0, float &a1, float &a2, int &cnt) {
   if (!fill_rendered<OX, OY>(c)) return;
-  const float *q = c.p + 3 * (OY * c.W + OX);
-  a0 = __fadd_rn(a0, q[0]);
-  a1 = __fadd_rn(a1, q[1]);
-  a2 = __fadd_rn(a2, q[2]);
+  float q0, q1, q2;
+  if constexpr (OX >= 0 && OY >= 0 && OX % 2 == 0 && OY % 2 == 0) {   // a top-left pixel: loaded
+    q0 = c.tl[OY / 2][OX / 2][0];
+    q1 = c.tl[OY / 2][OX / 2][1];
+    q2 = c.tl[OY / 2][OX / 2][2];
+  } else {
+    const float *q = c.p + 3 * (OY * c.W + OX);
+    q0 = q[0];
+    q1 = q[1];
+    q2 = q[2];
+  }
+  a0 = __fadd_rn(a0, q0);
+  a1 = __fadd_rn(a1, q1);
+  a2 = __fadd_rn(a2, q2);
   ++cnt;
 }
 
@@ -1041,13 +1052,14 @@ fill_kernel(const CompositeParams *__restrict__ pp, const uint8_t *__restrict__ 
     const unsigned e = r / H2, y2 = r - e * H2;
     const int x = (int)(2 * x2), y = (int)(2 * y2);
     const uint8_t *lv_e = levels + e * p.n_tiles;
-    const int lv = __ldg(lv_e + (y >> sh) * p.tiles_x + (x >> sh));
-    if (lv >= 4) continue;
     FillCtx c;
     c.W = W;
     c.room_x = W - x;
     c.room_y = H - y;
     c.p = out + 3 * ((size_t)e * H * W + (unsigned)y * (unsigned)W + (unsigned)x);
+    // every load of the block at once: its level and its neighbours' (the block up-left is
+    // never needed), and the top-left colours of the block and of the blocks right, below
+    // and diagonal -- the neighbours a level-1 block interpolates from
 #pragma unroll
     for (int by = 0; by < 3; ++by) {
       const int yy = y + 2 * (by - 1);
@@ -1056,10 +1068,20 @@ fill_kernel(const CompositeParams *__restrict__ pp, const uint8_t *__restrict__ 
 #pragma unroll
       for (int bx = 0; bx < 3; ++bx) {
         const int xx = x + 2 * (bx - 1);
-        c.L[by][bx] = (by == 1 && bx == 1) ? lv
-                      : (yin && xx >= 0 && xx < W && !(by == 0 && bx == 0)) ? __ldg(lv_e + row + (xx >> sh)) : 0;
+        c.L[by][bx] = (yin && xx >= 0 && xx < W && !(by == 0 && bx == 0)) ? __ldg(lv_e + row + (xx >> sh)) : 0;
       }
     }
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const bool in = 2 * i < c.room_x && 2 * j < c.room_y;
+        const float *q = c.p + 3 * (2 * j * W + 2 * i);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) c.tl[j][i][ch] = in ? q[ch] : 0.0f;
+      }
+    const int lv = c.L[1][1];
+    if (lv >= 4) continue;
     float *o = out + 3 * ((size_t)e * H * W + (unsigned)y * (unsigned)W + (unsigned)x);
     if (lv <= 2) fill_px<1, 0>(c, o);
     if (lv <= 3) fill_px<0, 1>(c, o);
