@@ -146,55 +146,60 @@ def test_learned_fill_beats_inherit_and_interpolating_fills(arch, lr0, min_gain_
 
 
 @pytest.mark.parametrize("arch", [periphery.RESIDUAL, periphery.COMPACT])
-@pytest.mark.parametrize("tile,width,height", [(16, 201, 137), (32, 256, 192)])
-def test_fused_fill_equals_forward_plus_compose(tile, width, height, arch):
+@pytest.mark.parametrize("tile,width,height,eyes", [(16, 201, 137, 1), (32, 256, 192, 1), (32, 203, 141, 2)])
+def test_fused_fill_equals_forward_plus_compose(tile, width, height, eyes, arch):
     """The fill runs its first convolution on the render directly and composes in the last
     one's epilogue (the compact network: all three layers in one kernel); its image equals
     the training forward's residuals composed here: rendered pixels kept, each skipped
     sub-pixel = bilinear base of the top-left pixels (last block repeated past the edge) + its
-    residual, bit for bit.  Ragged blocks at odd sizes.  The compact network's training
-    forward runs its per-block layers as 3x3 convolutions whose other taps are zero (18 MMAs
-    where the fused kernel issues 2): the zero products leave every accumulator unchanged."""
+    residual, bit for bit.  Ragged blocks at odd sizes; a stereo frame whose second eye starts
+    4 bytes off an 8-byte boundary (odd pixel count).  The compact network's training forward
+    runs its per-block layers as 3x3 convolutions whose other taps are zero (18 MMAs where the
+    fused kernel issues 2): the zero products leave every accumulator unchanged."""
     import paper_2507_04147_gb300 as a3fr
     scene_np = synth.uniform_scene(20000, 1, seed=5, log_scale_mean=-3.6)
     scene = a3fr.Scene.from_numpy(scene_np, tile=tile)
     scene.keep_aux(True)
-    cam = synth.pinhole_camera(width, height)
-    scene.set_camera(0, cam)
-    scene.set_gaze([[0.3 * width, 0.4 * height]])
+    cams = [synth.pinhole_camera(width, height)] if eyes == 1 else synth.stereo_cameras(width, height, yaw_deg=4.0)
+    for e, cam in enumerate(cams):
+        scene.set_camera(e, cam)
+    scene.set_gaze([[0.3 * width, 0.4 * height], [0.6 * width, 0.5 * height]][:eyes])
     fv = a3fr.Fovea((18.0, 36.0), 0.0, (4, 2, 1))
-    got = _t.empty((1, height, width, 3), dtype=_t.float32, device="cuda")
+    got = _t.empty((eyes, height, width, 3), dtype=_t.float32, device="cuda")
     scene.render_foveated(fv, out=got)
     img = got.clone()
-    depth = scene.buffer(a3fr.BUF_DEPTH, _t.float32).reshape(1, height, width)
+    depth = scene.buffer(a3fr.BUF_DEPTH, _t.float32).reshape(eyes, height, width)
     tx = (width + tile - 1) // tile
-    levels = scene.buffer(a3fr.BUF_LEVELS, _t.uint8).reshape(-1, tx).long()
+    ty = (height + tile - 1) // tile
+    levels_all = scene.buffer(a3fr.BUF_LEVELS, _t.uint8).reshape(eyes, ty, tx).long()
     net = periphery.Periphery(random_params(11, arch), arch=arch)
-    r = net.forward(img, depth)                      # [1, H2, W2, 16]
+    r = net.forward(img, depth)                      # [eyes, H2, W2, 16]
     net.fill(scene, got)
     _t.cuda.synchronize()
     net.close()
     scene.close()
     # compose the reference from img and r (fp32, the kernel's order of operations)
     H2, W2 = (height + 1) // 2, (width + 1) // 2
-    tl = img[0, 0::2, 0::2]                           # [H2, W2, 3]
     xr = _t.clamp(_t.arange(W2, device="cuda") + 1, max=W2 - 1)
     yd = _t.clamp(_t.arange(H2, device="cuda") + 1, max=H2 - 1)
-    a, right, down, diag = tl, tl[:, xr], tl[yd], tl[yd][:, xr]
     ys, xs = _t.meshgrid(_t.arange(H2, device="cuda"), _t.arange(W2, device="cuda"), indexing="ij")
-    lv = levels[(2 * ys) // tile, (2 * xs) // tile][..., None]
-    res = r[0]
-    ref = img.clone()[0]
-    bt = (a + right) * 0.5
-    bb = (a + down) * 0.5
-    bd = (((a + right) + down) + diag) * 0.25
-    for dy, dx, base, need in ((0, 1, bt, 2), (1, 0, bb, 3), (1, 1, bd, 1)):
-        val = base + res[..., [4 * c + 2 * dy + dx for c in range(3)]]
-        sel = (lv <= need).expand_as(val)
-        ry, rx = 2 * ys + dy, 2 * xs + dx
-        ok = ((ry < height) & (rx < width))[..., None].expand_as(val) & sel
-        cur = ref[ry.clamp(max=height - 1), rx.clamp(max=width - 1)]
-        ref[ry[ok[..., 0]], rx[ok[..., 0]]] = _t.where(ok, val, cur)[ok[..., 0]]
-    assert bool((levels < 4).any()) and bool((levels == 4).any())
-    diff = (got[0] - ref).abs().max().item()
-    assert _t.equal(got[0], ref), diff
+    for e in range(eyes):
+        levels = levels_all[e]
+        tl = img[e, 0::2, 0::2]                       # [H2, W2, 3]
+        a, right, down, diag = tl, tl[:, xr], tl[yd], tl[yd][:, xr]
+        lv = levels[(2 * ys) // tile, (2 * xs) // tile][..., None]
+        res = r[e]
+        ref = img.clone()[e]
+        bt = (a + right) * 0.5
+        bb = (a + down) * 0.5
+        bd = (((a + right) + down) + diag) * 0.25
+        for dy, dx, base, need in ((0, 1, bt, 2), (1, 0, bb, 3), (1, 1, bd, 1)):
+            val = base + res[..., [4 * c + 2 * dy + dx for c in range(3)]]
+            sel = (lv <= need).expand_as(val)
+            ry, rx = 2 * ys + dy, 2 * xs + dx
+            ok = ((ry < height) & (rx < width))[..., None].expand_as(val) & sel
+            cur = ref[ry.clamp(max=height - 1), rx.clamp(max=width - 1)]
+            ref[ry[ok[..., 0]], rx[ok[..., 0]]] = _t.where(ok, val, cur)[ok[..., 0]]
+        assert bool((levels < 4).any()) and bool((levels == 4).any())
+        diff = (got[e] - ref).abs().max().item()
+        assert _t.equal(got[e], ref), (e, diff)
