@@ -1,6 +1,8 @@
-// cnn.cu -- tensor-core (tcgen05) kernels of the learned periphery: a small residual CNN in
-// BF16 with FP32 accumulation that reconstructs full-resolution RGB from the quarter-density
-// peripheral layer (the level-1 pixels of Sec. 3.4) and its depth.
+// cnn.cu -- tensor-core (tcgen05) kernels of the learned periphery: small CNNs in BF16 with
+// FP32 accumulation that reconstruct full-resolution RGB from the quarter-density peripheral
+// layer (the level-1 pixels of Sec. 3.4) and its depth -- a residual network of ten 3x3
+// convolutions, and a compact one (a 3x3 convolution and two per-block layers) whose whole
+// fill is one fused kernel.
 //
 // This file starts with the single-tile GEMM that validates the operand encodings (shared-
 // memory descriptors, instruction descriptor, tensor-memory round trip) before the

@@ -1,6 +1,8 @@
-"""Learned periphery: the tensor-core CNN that fills the pixels a foveated render skipped.
+"""Learned periphery: the tensor-core CNNs that fill the pixels a foveated render skipped --
+a residual network of ten 3x3 convolutions (``RESIDUAL``) and a compact one, a 3x3 convolution
+and two per-block layers, whose fill is a single fused kernel (``COMPACT``).
 
-The network and its kernels live in the CUDA library (``a3fr_cnn_*``, see ``include/a3fr.h``);
+The networks and their kernels live in the CUDA library (``a3fr_cnn_*``, see ``include/a3fr.h``);
 this module marshals arguments, initialises parameters, cuts training crops out of the
 rasterizer's own renders and computes the image metrics the comparison is reported in.
 """
